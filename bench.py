@@ -1,0 +1,356 @@
+"""hefx benchmark: N = 2^16 limb-NTTs per second on one GB300.
+
+Workload (one "step"): forward + inverse negacyclic NTT of a batch of 8 polynomials with
+L = 24 RNS limbs of 28-bit primes, N = 2^16 (384 limb-NTTs), uniform synthetic residues.
+Both hefx paths are timed (CUDA-core radix-2 and the tensor-core matrix NTT, when built);
+`value` is the faster bit-exact path, `paths` lists both.  Inputs (48 MiB) are smaller than
+L2, so a 256 MiB buffer is written between timed steps to flush it.
+
+Contract: one JSON line on rank 0.  `python bench.py --impl reference` times the CPU oracle
+instead (the reference arm of this workload).  Under torchrun every rank runs an
+independent replica (the method has no exchange step), timed between barriers.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+LOGN, L, BATCH = 16, 24, 8
+N = 1 << LOGN
+UNITS_PER_STEP = 2 * BATCH * L             # limb-NTTs per step (forward + inverse)
+BYTES_PER_UNIT = 2 * N * 4                 # one read and one write of a limb per transform
+METRIC = "N=2^16 limb-NTTs/s, int8-tensor-core vs CUDA-core path, bit-exact; % roofline"
+WORKLOAD = "CKKS-shaped NTT: N=2^16, L=24 28-bit limbs, batch 8, forward+inverse"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), float(p["bf16_tflops"]), float(p.get("bf16_tflops_sustained", 0)), "measured"
+    except Exception:
+        return 6800.0, 1900.0, 1700.0, "fallback"
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+
+def _oracle_worker(args):
+    seed, budget_s, primes = args
+    import oracle as orc
+    from paper_2501_07047_gb300 import inputs
+    done = 0
+    t0 = time.perf_counter()
+    i = 0
+    while time.perf_counter() - t0 < budget_s:
+        q = primes[i % len(primes)]
+        a = inputs.uniform_residues(inputs.derive_seed(seed, i), N, q)
+        ahat = orc.ntt(a, q)
+        orc.intt(ahat, q)
+        done += 2
+        i += 1
+    return done, time.perf_counter() - t0
+
+
+def time_oracle(budget_s: float, cores: int | None = None):
+    """Runs the oracle's forward + inverse N = 2^16 limb-NTTs on every host core (spawned
+    processes) for a bounded time and returns limb-NTTs/s over all cores."""
+    import oracle as orc
+    orc.build()
+    from paper_2501_07047_gb300 import inputs
+    primes = inputs.source_primes(L)
+    cores = cores or os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_worker, [(1000 + w, budget_s, primes) for w in range(cores)])
+    wall = time.perf_counter() - t0
+    units = sum(r[0] for r in res)
+    longest = max(r[1] for r in res)
+    return {"value": units / longest, "unit": "limb-NTT/s", "cores": cores, "kind": "oracle",
+            "sample": f"{units} N=2^16 limb-NTTs (forward+inverse pairs over the 24 limb primes) in "
+                      f"{longest:.1f} s per core, {cores} processes, wall {wall:.1f} s"}
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def run_gpu(args):
+    import torch
+    from paper_2501_07047_gb300 import build, hefx, inputs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    # start the CPU-baseline pool (spawn) before the first CUDA call
+    cpu_baseline = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu_baseline = time_oracle(args.cpu_seconds)
+
+    build.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    ctx = hefx.hefx_create(local)
+    primes = inputs.source_primes(L)
+    params = hefx.hefx_params_create(ctx, LOGN, primes)
+    host = inputs.residue_tensor(inputs.derive_seed(2, rank), BATCH, primes, N)
+    host_t = torch.from_numpy(host.view(np.int32).copy())
+    data0 = host_t.cuda()
+    data = data0.clone()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def available(path):
+        st = hefx.raw_status("hefx_ntt_fwd", ctx, params, data.data_ptr(), 0, hefx.PATHS[path], stream.cuda_stream)
+        return st == hefx.HEFX_OK
+
+    paths = [p for p in ("cudacore", "tensor") if available(p)]
+    results = {}
+    for path in paths:
+        # correctness gate: INTT(NTT(x)) == x on the bench data before timing
+        data.copy_(data0)
+        hefx.hefx_ntt_fwd(ctx, params, data, BATCH, path, stream)
+        hefx.hefx_ntt_inv(ctx, params, data, BATCH, path, stream)
+        torch.cuda.synchronize()
+        assert torch.equal(data, data0), f"{path}: round trip mismatch"
+        for _ in range(args.warmup):
+            hefx.hefx_ntt_fwd(ctx, params, data, BATCH, path, stream)
+            hefx.hefx_ntt_inv(ctx, params, data, BATCH, path, stream)
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        with ClockSampler(local) as clk:
+            t_wall = time.perf_counter()
+            for k in range(args.steps):
+                flush.fill_(k)  # write 256 MiB > L2 between timed steps (outside the events)
+                ev[k][0].record(stream)
+                hefx.hefx_ntt_fwd(ctx, params, data, BATCH, path, stream)
+                ev[k][1].record(stream)
+                hefx.hefx_ntt_inv(ctx, params, data, BATCH, path, stream)
+                ev[k][2].record(stream)
+            torch.cuda.synchronize()
+            t_wall = time.perf_counter() - t_wall
+        if dist:
+            dist.barrier()
+        fwd_ms = [ev[k][0].elapsed_time(ev[k][1]) for k in range(args.steps)]
+        inv_ms = [ev[k][1].elapsed_time(ev[k][2]) for k in range(args.steps)]
+        step_ms = sum(fwd_ms) / args.steps + sum(inv_ms) / args.steps
+        total_ms = step_ms * args.steps
+        if dist:
+            t = torch.tensor([total_ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = float(t.item())
+        results[path] = {
+            "ms_per_step": total_ms / args.steps,
+            "value": world * UNITS_PER_STEP * args.steps / (total_ms / 1e3),
+            "fwd_ms": statistics.mean(fwd_ms), "inv_ms": statistics.mean(inv_ms),
+            "wall_s": t_wall, "clocks": clk.summary(),
+            "launches_per_step": 2,
+        }
+
+    best = max(results, key=lambda p: results[p]["value"])
+    r = results[best]
+
+    # end to end through the public call with host buffers: pinned H2D, fwd, inv, D2H per step
+    pinned_in = host_t.pin_memory()
+    pinned_out = torch.empty_like(pinned_in).pin_memory()
+    for _ in range(2):
+        data.copy_(pinned_in, non_blocking=True)
+        hefx.hefx_ntt_fwd(ctx, params, data, BATCH, best, stream)
+        hefx.hefx_ntt_inv(ctx, params, data, BATCH, best, stream)
+        pinned_out.copy_(data, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        data.copy_(pinned_in, non_blocking=True)
+        hefx.hefx_ntt_fwd(ctx, params, data, BATCH, best, stream)
+        hefx.hefx_ntt_inv(ctx, params, data, BATCH, best, stream)
+        pinned_out.copy_(data, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    assert torch.equal(pinned_out, host_t)
+
+    hbm, bf16, bf16_s, src = peaks()
+    dominant_ms = max(r["fwd_ms"], r["inv_ms"])
+    units_per_launch = BATCH * L
+    if best == "cudacore":
+        achieved = units_per_launch * BYTES_PER_UNIT / (dominant_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(achieved / hbm, 4), "traffic": profile_traffic("ntt_cc"),
+                "kernel": "ntt_cc_kernel<16, " + ("FWD" if r["fwd_ms"] >= r["inv_ms"] else "INV") + ">",
+                "peak_source": f"{src} hbm_gbs"}
+    else:
+        flops = tensor_flops_per_limb_ntt()
+        achieved = units_per_launch * flops / (dominant_ms / 1e3) / 1e12
+        roof = {"bound": "tensor", "achieved": round(achieved, 1), "peak": bf16, "unit": "TFLOP/s",
+                "frac": round(achieved / bf16, 4), "traffic": profile_traffic("ntt_tc"),
+                "kernel": "ntt_tc", "peak_source": f"{src} bf16_tflops (fp16 runs at the bf16 rate)"}
+
+    line = {
+        "metric": METRIC, "value": round(r["value"], 1), "unit": "limb-NTT/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(r["ms_per_step"], 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": N, "limbs": L, "batch": BATCH, "path": best,
+                   "units_per_step": UNITS_PER_STEP, "l2": "flushed (256 MiB write) between timed steps",
+                   "parallelism": f"replicas x{world}"},
+        "paths": {p: {"value": round(v["value"], 1), "ms_per_step": round(v["ms_per_step"], 5),
+                      "fwd_ms": round(v["fwd_ms"], 5), "inv_ms": round(v["inv_ms"], 5)} for p, v in results.items()},
+        "roofline": roof,
+        "clocks": r["clocks"],
+        "e2e": {"value": round(world * UNITS_PER_STEP * args.steps / (e2e_ms / 1e3), 1), "unit": "limb-NTT/s",
+                "h2d_bytes_per_step": int(host.nbytes), "d2h_bytes_per_step": int(host.nbytes)},
+        "gpu_launches": r["launches_per_step"] * args.steps,
+    }
+    if cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline
+    hefx.hefx_params_destroy(params)
+    hefx.hefx_destroy(ctx)
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+def tensor_flops_per_limb_ntt() -> float:
+    """Algorithmic tensor work of one tensor-path limb-NTT (2 flops per digit MAC)."""
+    from paper_2501_07047_gb300 import tensor_plan
+    return tensor_plan.flops_per_limb_ntt(LOGN)
+
+
+def profile_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the current source."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.txt")
+    try:
+        kv = dict(ln.split("=", 1) for ln in open(path).read().split("\n") if "=" in ln)
+        import hashlib
+        src = os.path.join(ROOT, "paper_2501_07047_gb300", "csrc", kv["source"].strip())
+        if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != kv["source_sha"].strip():
+            return None
+        return int(float(kv["dram_bytes_per_launch"]))
+    except Exception:
+        return None
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    per = []
+    for _ in range(args.warmup):
+        time_oracle(min(2.0, args.cpu_seconds / 4))
+    for _ in range(args.steps):
+        per.append(time_oracle(args.cpu_seconds))
+    value = statistics.median(p["value"] for p in per)
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": "limb-NTT/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(UNITS_PER_STEP / value * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": N, "limbs": L, "batch": BATCH, "path": "cpu-oracle",
+                   "units_per_step": UNITS_PER_STEP},
+        "impl": "reference",
+        "cpu_baseline": {"value": round(value, 2), "unit": "limb-NTT/s", "cores": per[0]["cores"],
+                         "kind": "oracle", "sample": per[0]["sample"] + " (per step; bounded sample of the workload)"},
+        "e2e": {"value": round(value, 2), "unit": "limb-NTT/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="hefx", choices=["hefx", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        if args.steps > 5:
+            args.cpu_seconds = min(args.cpu_seconds, 30.0 / args.steps)
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

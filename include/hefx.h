@@ -1,0 +1,142 @@
+/*
+ * hefx -- batched negacyclic NTT, polynomial product and RNS basis conversion on one
+ * NVIDIA GB300 (sm_103a), after arXiv 2501.07047 ("CROSS").
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - A polynomial in R_Q = Z_Q[x]/(x^N + 1) (Sec. II-A) is held in RNS form (Sec. II-A,
+ *    "Residue Number System"): one limb of N residues per prime q_i.  Device buffers are
+ *    uint32 arrays laid out [batch][limb][N], row-major, contiguous, 16-byte aligned, every
+ *    value a canonical residue in [0, q_limb).  Inputs outside [0, q) give undefined
+ *    (but memory-safe) results.
+ *  - The forward NTT maps coefficient order to evaluation order with the output in
+ *    bit-reversed order (Sec. IV-B2, "layout invariant 3-step negacyclic NTT"):
+ *        ahat[p] = sum_j a_j * psi^(j (2 brv_N(p) + 1))  mod q,
+ *    psi = g^((q-1)/(2N)), g the smallest generator of Z_q^*.  The inverse NTT maps
+ *    bit-reversed evaluations back to natural-order coefficients and includes N^-1.
+ *  - Every call is asynchronous on `stream` (a cudaStream_t passed as void*, NULL = the
+ *    legacy default stream).  Errors that the host can detect are returned synchronously
+ *    and nothing is launched; hefx_last_error() then holds a one-line message.
+ *  - The caller owns every data buffer (device pointers from any allocator).  hefx owns
+ *    the context, parameter sets and plans it creates (and the device tables inside them),
+ *    and releases them in the matching *_destroy call.
+ *  - Moduli: primes q with q = 1 (mod 2N) and 2^3 < q < 2^30 (the lazy butterflies keep
+ *    values below 4q < 2^32).  N = 2^log2n with 3 <= log2n <= 16.
+ *  - Paths: HEFX_PATH_CUDACORE is the radix-2 Cooley-Tukey / Gentleman-Sande transform on
+ *    the CUDA cores (App. A, "Radix-2 Cooley-Tukey NTT").  HEFX_PATH_TENSOR is the
+ *    layout-invariant matrix NTT of Sec. IV-B with its modular matrix products split into
+ *    small-integer digits (BAT, Sec. IV-A) and run on the tcgen05 tensor cores.
+ *    HEFX_PATH_AUTO takes the path the built-in tuner measured fastest for the shape.
+ *    Both paths return identical (bit-exact) results.
+ */
+#ifndef HEFX_H
+#define HEFX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HEFX_OK = 0,
+    HEFX_EINVAL = 1,       /* a bad argument: null pointer, bad prime, misaligned buffer */
+    HEFX_EUNSUPPORTED = 2, /* a valid request outside what this build implements */
+    HEFX_ENOMEM = 3,       /* a device allocation for tables or workspace failed */
+    HEFX_EBUDGET = 4,      /* a request does not fit the configured memory budget */
+    HEFX_ECUDA = 5,        /* a CUDA runtime call failed (message in hefx_last_error) */
+    HEFX_ETIMEOUT = 6      /* a bounded device-side wait expired; results are invalid */
+} hefx_status;
+
+typedef enum {
+    HEFX_PATH_AUTO = 0,
+    HEFX_PATH_CUDACORE = 1,
+    HEFX_PATH_TENSOR = 2
+} hefx_path;
+
+typedef struct hefx_ctx hefx_ctx;
+typedef struct hefx_params hefx_params;
+typedef struct hefx_bconv_plan hefx_bconv_plan;
+
+/* Creates a context bound to CUDA device `device` (made current by every hefx call). */
+hefx_status hefx_create(hefx_ctx** out, int device);
+void hefx_destroy(hefx_ctx* ctx);
+/* Message of the last failed call on this context ("" when none); owned by the context. */
+const char* hefx_last_error(const hefx_ctx* ctx);
+/* Library version string, static storage. */
+const char* hefx_version(void);
+
+/*
+ * Parameter set for N = 2^log2n and the RNS basis primes[0..nlimbs) (Sec. II-A; Table
+ * "Notations": q_i coprime, L limbs).  Precomputes on the host and uploads the twiddle
+ * tables of both paths (the offline "compile time" step of Sec. IV-A/IV-B).
+ * Errors: EINVAL for a non-prime, repeated prime, q != 1 mod 2N or q >= 2^30;
+ * EUNSUPPORTED for log2n outside [3, 16]; ENOMEM when the tables do not fit.
+ */
+hefx_status hefx_params_create(hefx_ctx* ctx, uint32_t log2n, const uint32_t* primes, uint32_t nlimbs,
+                               hefx_params** out);
+void hefx_params_destroy(hefx_params* params);
+
+/*
+ * Records the path HEFX_PATH_AUTO takes for this parameter set (HEFX_PATH_CUDACORE or
+ * HEFX_PATH_TENSOR; HEFX_PATH_AUTO restores the default, the CUDA-core path).  Called by
+ * the autotuner after it has timed both paths on the device (Sec. V-B3 reports the best
+ * of several (R, C) splits per shape; the tuner generalises that choice).
+ * Errors: EINVAL for a null params or an unknown path.  Not thread-safe with concurrent
+ * calls that use the same params.
+ */
+hefx_status hefx_params_set_auto_path(hefx_params* params, hefx_path path);
+
+/*
+ * In-place forward NTT of d_data[batch][nlimbs][N] (natural order in, bit-reversed out).
+ * The definition is Sec. II-A's ring with the bit-reversed output of Sec. IV-B2; the
+ * CUDA-core path follows App. A (radix-2 Cooley-Tukey), the tensor path Sec. IV-B
+ * (layout-invariant 3-step NTT with BAT-split matrix products).
+ * batch == 0 is a no-op.  Errors: EINVAL (null/misaligned pointer), EUNSUPPORTED (path
+ * not available for this N), ECUDA (launch failure).
+ */
+hefx_status hefx_ntt_fwd(hefx_ctx* ctx, const hefx_params* params, uint32_t* d_data, size_t batch,
+                         hefx_path path, void* stream);
+
+/* In-place inverse NTT (bit-reversed in, natural out, scaled by N^-1); same contract. */
+hefx_status hefx_ntt_inv(hefx_ctx* ctx, const hefx_params* params, uint32_t* d_data, size_t batch,
+                         hefx_path path, void* stream);
+
+/*
+ * Negacyclic product c = a * b in R_q per limb (Sec. III, Table "HE operator -> AI
+ * operator": NTT, Hadamard product mod q, INTT).  Inputs and output in natural
+ * coefficient order, [batch][nlimbs][N].  d_c may alias d_a and/or d_b.  Uses no
+ * workspace beyond d_c.  Errors as for hefx_ntt_fwd.
+ */
+hefx_status hefx_poly_mul(hefx_ctx* ctx, const hefx_params* params, const uint32_t* d_a, const uint32_t* d_b,
+                          uint32_t* d_c, size_t batch, hefx_path path, void* stream);
+
+/*
+ * Basis-conversion plan from basis src[0..L) to basis dst[0..Lp) for limbs of
+ * n = 2^log2n coefficients (App. B, BConv):
+ *   out_{n,j} = sum_i [a_{n,i} * qhat_i^-1]_{q_i} * [qhat_i]_{p_j}  mod p_j,  qhat_i = Q / q_i.
+ * This is the fast conversion as written: the integer it reduces may exceed the CRT value
+ * by u*Q with 0 <= u < L; no correction is applied.  The plan holds the step-1 constants
+ * qhat_i^-1 mod q_i and the BAT-compiled digit matrix of step 2 (Sec. IV-A3).
+ * Errors: EINVAL for non-prime, repeated (within or across bases) or >= 2^30 moduli,
+ * L or Lp outside [1, 64]; EUNSUPPORTED for log2n outside [0, 24].
+ */
+hefx_status hefx_bconv_plan_create(hefx_ctx* ctx, uint32_t log2n, const uint32_t* src, uint32_t L,
+                                   const uint32_t* dst, uint32_t Lp, hefx_bconv_plan** out);
+void hefx_bconv_plan_destroy(hefx_bconv_plan* plan);
+
+/*
+ * d_out[batch][Lp][n] = BConv(d_in[batch][L][n]).  d_out must not overlap d_in.
+ * HEFX_PATH_TENSOR runs step 2 as a digit-split matrix product on the tensor cores
+ * (Sec. IV-A3, "High-Precision MatModMul in BConv"); HEFX_PATH_CUDACORE as 64-bit
+ * multiply-accumulates.  Results are identical.
+ */
+hefx_status hefx_basis_convert(hefx_ctx* ctx, const hefx_bconv_plan* plan, const uint32_t* d_in, uint32_t* d_out,
+                               size_t batch, hefx_path path, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HEFX_H */

@@ -1,0 +1,116 @@
+// RNS basis conversion (App. B, BConv), CUDA-core path and plan constants.
+//
+//   out_{n,j} = sum_i [a_{n,i} * qhat_i^-1]_{q_i} * [qhat_i]_{p_j}  mod p_j
+//
+// Step 1 is L independent VecModMuls by the constant qhat_i^-1 (Shoup products); step 2
+// is an (N, L, L') MatModMul whose right operand is the constant matrix [qhat_i]_{p_j}.
+// This file runs step 2 as 64-bit multiply-accumulates (each product < 2^58, L <= 64
+// products fit in 64 bits) with one Barrett reduction per output; bconv_tc.cu runs it on
+// the tensor cores as a digit-split (BAT) matrix product.
+#include "bconv_common.h"
+#include "host_nt.h"
+#include "modarith.cuh"
+
+namespace hefx {
+
+cudaError_t bconv_plan_upload(hefx_bconv_plan* plan) {
+    const uint32_t L = plan->L, Lp = plan->Lp;
+    BConvConst h;
+    memset(&h, 0, sizeof(h));
+    h.L = L;
+    h.Lp = Lp;
+    for (uint32_t i = 0; i < L; ++i) {
+        const uint64_t q = plan->src[i];
+        uint64_t qhat = 1;
+        for (uint32_t k = 0; k < L; ++k)
+            if (k != i) qhat = mul_mod(qhat, plan->src[k], q);
+        const uint64_t qi = inv_mod(qhat, q);
+        h.q[i] = (uint32_t)q;
+        h.qhat_inv[i] = (uint32_t)qi;
+        h.qhat_inv_sh[i] = shoup(qi, q);
+        for (uint32_t j = 0; j < Lp; ++j) {
+            uint64_t c = 1;
+            for (uint32_t k = 0; k < L; ++k)
+                if (k != i) c = mul_mod(c, plan->src[k], plan->dst[j]);
+            h.qhat_p[i * kBConvMaxLimbs + j] = (uint32_t)c;
+        }
+    }
+    for (uint32_t j = 0; j < Lp; ++j) {
+        h.p[j] = plan->dst[j];
+        h.p_mu[j] = (uint64_t)(((u128)1 << 64) / plan->dst[j]);  // floor(2^64 / p_j)
+    }
+    cudaError_t e = cudaMalloc(&plan->d_const, sizeof(BConvConst));
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpy(plan->d_const, &h, sizeof(BConvConst), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+    return bconv_tc_upload(plan, h);
+}
+
+void bconv_plan_free(hefx_bconv_plan* plan) {
+    if (plan->d_const) cudaFree(plan->d_const);
+    plan->d_const = nullptr;
+    bconv_tc_free(plan);
+}
+
+namespace {
+
+constexpr int kJChunk = 8;  // target limbs accumulated per pass over the source limbs
+
+__device__ __forceinline__ uint32_t barrett64(uint64_t x, uint32_t p, uint64_t mu) {
+    const uint64_t qt = __umul64hi(x, mu);  // floor(x / p) or one less
+    uint64_t r = x - qt * p;
+    return (uint32_t)(r >= p ? r - p : r);
+}
+
+__global__ void __launch_bounds__(256) bconv_cc_kernel(const BConvConst* __restrict__ gc, const uint32_t* __restrict__ in,
+                                                       uint32_t* __restrict__ out, uint32_t n, uint32_t batch) {
+    __shared__ BConvConst c;
+    for (int i = threadIdx.x; i < (int)(sizeof(BConvConst) / 4); i += blockDim.x)
+        reinterpret_cast<uint32_t*>(&c)[i] = reinterpret_cast<const uint32_t*>(gc)[i];
+    __syncthreads();
+    const uint32_t L = c.L, Lp = c.Lp;
+    const size_t total = (size_t)n * batch;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        const size_t b = t / n, x = t % n;
+        const uint32_t* src = in + b * L * n + x;
+        uint32_t* dst = out + b * Lp * n + x;
+        for (uint32_t j0 = 0; j0 < Lp; j0 += kJChunk) {
+            uint64_t acc[kJChunk];
+#pragma unroll
+            for (int jj = 0; jj < kJChunk; ++jj) acc[jj] = 0;
+            for (uint32_t i = 0; i < L; ++i) {
+                const uint32_t qi = c.q[i];
+                uint32_t bi = mul_shoup_lazy(__ldg(src + (size_t)i * n), c.qhat_inv[i], c.qhat_inv_sh[i], qi);
+                bi = csub(bi, qi);  // step 1: [a * qhat^-1]_{q_i}
+#pragma unroll
+                for (int jj = 0; jj < kJChunk; ++jj)
+                    acc[jj] += (uint64_t)bi * c.qhat_p[i * kBConvMaxLimbs + j0 + jj];
+            }
+#pragma unroll
+            for (int jj = 0; jj < kJChunk; ++jj) {
+                const uint32_t j = j0 + jj;
+                if (j < Lp) dst[(size_t)j * n] = barrett64(acc[jj], c.p[j], c.p_mu[j]);
+            }
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_bconv_cc(const hefx_bconv_plan* plan, const uint32_t* in, uint32_t* out, size_t batch,
+                            cudaStream_t stream) {
+    const uint32_t n = 1u << plan->log2n;
+    const size_t total = (size_t)n * batch;
+    if (total == 0) return cudaSuccess;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    size_t blocks = (total + 255) / 256;
+    const size_t cap = (size_t)sms * 8;
+    if (blocks > cap) blocks = cap;
+    bconv_cc_kernel<<<(unsigned)blocks, 256, 0, stream>>>(static_cast<const BConvConst*>(plan->d_const), in, out, n,
+                                                           (uint32_t)batch);
+    return cudaGetLastError();
+}
+
+}  // namespace hefx

@@ -1,0 +1,26 @@
+// Basis-conversion plan constants shared by the CUDA-core and tensor-core BConv kernels.
+#pragma once
+
+#include <cstring>
+
+#include "hefx_internal.h"
+
+namespace hefx {
+
+constexpr int kBConvMaxLimbs = 64;
+
+struct BConvConst {
+    uint32_t L, Lp, pad0, pad1;
+    uint32_t q[kBConvMaxLimbs];            // source primes q_i
+    uint32_t qhat_inv[kBConvMaxLimbs];     // qhat_i^-1 mod q_i (step 1 constant)
+    uint32_t qhat_inv_sh[kBConvMaxLimbs];  // its Shoup companion
+    uint32_t p[kBConvMaxLimbs];            // target primes p_j
+    uint64_t p_mu[kBConvMaxLimbs];         // floor(2^64 / p_j) (Barrett)
+    uint32_t qhat_p[kBConvMaxLimbs * kBConvMaxLimbs];  // [i][j] = qhat_i mod p_j (step 2 matrix)
+};
+
+cudaError_t bconv_tc_upload(hefx_bconv_plan* plan, const BConvConst& h);
+void bconv_tc_free(hefx_bconv_plan* plan);
+bool bconv_tc_available(const hefx_bconv_plan* plan);
+
+}  // namespace hefx

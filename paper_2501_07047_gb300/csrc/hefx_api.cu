@@ -1,0 +1,318 @@
+// hefx C ABI: argument validation, parameter-set precompute and dispatch.
+//
+// Every entry point validates on the host, returns a status without launching anything
+// on error, and otherwise enqueues its kernels on the caller's stream.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <set>
+
+#include "bconv_common.h"
+#include "hefx_internal.h"
+#include "host_nt.h"
+
+using namespace hefx;
+
+namespace {
+
+hefx_status fail(hefx_ctx* ctx, hefx_status st, const char* fmt, ...) {
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        std::lock_guard<std::mutex> g(ctx->mu);
+        ctx->last_error = buf;
+    }
+    return st;
+}
+
+hefx_status cuda_fail(hefx_ctx* ctx, cudaError_t e, const char* what) {
+    return fail(ctx, e == cudaErrorMemoryAllocation ? HEFX_ENOMEM : HEFX_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+hefx_status use_device(hefx_ctx* ctx) {
+    int cur = -1;
+    cudaError_t e = cudaGetDevice(&cur);
+    if (e == cudaSuccess && cur != ctx->device) e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+    return HEFX_OK;
+}
+
+hefx_status check_ntt_args(hefx_ctx* ctx, const hefx_params* p, const void* ptr, const char* name) {
+    if (!ctx) return HEFX_EINVAL;
+    if (!p || p->ctx != ctx) return fail(ctx, HEFX_EINVAL, "params is null or belongs to another context");
+    if (!ptr) return fail(ctx, HEFX_EINVAL, "%s is null", name);
+    if (!aligned16(ptr)) return fail(ctx, HEFX_EINVAL, "%s is not 16-byte aligned", name);
+    return HEFX_OK;
+}
+
+// The tensor path is taken only where it is built for the shape; AUTO follows the tuner's
+// measured choice (set from Python after timing both paths), else the CUDA-core path.
+hefx_path resolve(const hefx_params* p, hefx_path path) {
+    if (path == HEFX_PATH_AUTO) {
+        if (p->tuned_path == HEFX_PATH_TENSOR && tc_supported(p)) return HEFX_PATH_TENSOR;
+        return HEFX_PATH_CUDACORE;
+    }
+    return path;
+}
+
+hefx_status ensure_tc(hefx_ctx* ctx, const hefx_params* pc) {
+    hefx_params* p = const_cast<hefx_params*>(pc);
+    if (!tc_supported(p))
+        return fail(ctx, HEFX_EUNSUPPORTED, "tensor path not available for N = 2^%u with these moduli", p->log2n);
+    std::lock_guard<std::mutex> g(p->tc_mu);
+    if (!p->tc) {
+        cudaError_t e = tc_prepare(p);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "tensor-path tables");
+    }
+    return HEFX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* hefx_version(void) { return "hefx 0.1 (sm_103a)"; }
+
+hefx_status hefx_create(hefx_ctx** out, int device) {
+    if (!out) return HEFX_EINVAL;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return HEFX_ECUDA;
+    hefx_ctx* c = new hefx_ctx();
+    c->device = device;
+    cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    *out = c;
+    return HEFX_OK;
+}
+
+void hefx_destroy(hefx_ctx* ctx) { delete ctx; }
+
+const char* hefx_last_error(const hefx_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "null context"; }
+
+hefx_status hefx_params_create(hefx_ctx* ctx, uint32_t log2n, const uint32_t* primes, uint32_t nlimbs,
+                               hefx_params** out) {
+    if (!ctx || !out) return HEFX_EINVAL;
+    *out = nullptr;
+    if (log2n < 3 || log2n > 16) return fail(ctx, HEFX_EUNSUPPORTED, "log2n = %u outside [3, 16]", log2n);
+    if (!primes || nlimbs == 0 || nlimbs > 4096) return fail(ctx, HEFX_EINVAL, "need 1..4096 primes");
+    const uint64_t n = 1ull << log2n;
+    std::set<uint32_t> seen;
+    for (uint32_t i = 0; i < nlimbs; ++i) {
+        const uint32_t q = primes[i];
+        if (q < 17 || q >= (1u << 30) || !is_prime(q))
+            return fail(ctx, HEFX_EINVAL, "primes[%u] = %u is not a prime in [17, 2^30)", i, q);
+        if ((q - 1) % (2 * n) != 0) return fail(ctx, HEFX_EINVAL, "primes[%u] = %u is not 1 mod 2N", i, q);
+        if (!seen.insert(q).second) return fail(ctx, HEFX_EINVAL, "primes[%u] = %u repeats", i, q);
+    }
+    hefx_status st = use_device(ctx);
+    if (st != HEFX_OK) return st;
+
+    hefx_params* p = new hefx_params();
+    p->ctx = ctx;
+    p->log2n = log2n;
+    p->n = (uint32_t)n;
+    p->nlimbs = nlimbs;
+    p->primes.assign(primes, primes + nlimbs);
+    std::vector<LimbConst> lc(nlimbs);
+    std::vector<uint2> twf((size_t)nlimbs * n), twi((size_t)nlimbs * n);
+    std::vector<uint64_t> pw(n), pwi(n);
+    for (uint32_t l = 0; l < nlimbs; ++l) {
+        const uint64_t q = primes[l];
+        const uint64_t psi = root_2n(q, n), psi_inv = inv_mod(psi, q);
+        p->psi.push_back((uint32_t)psi);
+        pw[0] = pwi[0] = 1;
+        for (uint64_t e = 1; e < n; ++e) {
+            pw[e] = mul_mod(pw[e - 1], psi, q);
+            pwi[e] = mul_mod(pwi[e - 1], psi_inv, q);
+        }
+        for (uint64_t k = 0; k < n; ++k) {
+            const uint32_t r = bit_reverse((uint32_t)k, (int)log2n);
+            twf[l * n + k] = make_uint2((uint32_t)pw[r], shoup(pw[r], q));
+            twi[l * n + k] = make_uint2((uint32_t)pwi[r], shoup(pwi[r], q));
+        }
+        LimbConst& c = lc[l];
+        memset(&c, 0, sizeof c);
+        c.q = (uint32_t)q;
+        c.qinv_neg = neg_inv_pow2_32((uint32_t)q);
+        const uint64_t ninv = inv_mod(n % q, q);
+        const uint64_t w1 = pwi[bit_reverse(1, (int)log2n)];  // psi^-(N/2), last Gentleman-Sande twiddle
+        const uint64_t r32 = ((uint64_t)1 << 32) % q;
+        const uint64_t vals[4] = {ninv, mul_mod(ninv, w1, q), mul_mod(ninv, r32, q),
+                                  mul_mod(mul_mod(ninv, r32, q), w1, q)};
+        c.ninv = (uint32_t)vals[0];
+        c.ninv_sh = shoup(vals[0], q);
+        c.ninvw = (uint32_t)vals[1];
+        c.ninvw_sh = shoup(vals[1], q);
+        c.ninvR = (uint32_t)vals[2];
+        c.ninvR_sh = shoup(vals[2], q);
+        c.ninvRw = (uint32_t)vals[3];
+        c.ninvRw_sh = shoup(vals[3], q);
+    }
+    cudaError_t e = cudaMalloc(&p->d_lc, sizeof(LimbConst) * nlimbs);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_tw_fwd, sizeof(uint2) * twf.size());
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_tw_inv, sizeof(uint2) * twi.size());
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_lc, lc.data(), sizeof(LimbConst) * nlimbs, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_tw_fwd, twf.data(), sizeof(uint2) * twf.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_tw_inv, twi.data(), sizeof(uint2) * twi.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        hefx_params_destroy(p);
+        return cuda_fail(ctx, e, "parameter tables");
+    }
+    *out = p;
+    return HEFX_OK;
+}
+
+void hefx_params_destroy(hefx_params* p) {
+    if (!p) return;
+    if (p->ctx) {
+        int cur = -1;
+        if (cudaGetDevice(&cur) == cudaSuccess && cur != p->ctx->device) cudaSetDevice(p->ctx->device);
+    }
+    tc_free(p);
+    if (p->d_lc) cudaFree(p->d_lc);
+    if (p->d_tw_fwd) cudaFree(p->d_tw_fwd);
+    if (p->d_tw_inv) cudaFree(p->d_tw_inv);
+    delete p;
+}
+
+static hefx_status run_ntt(hefx_ctx* ctx, const hefx_params* p, uint32_t* d, size_t batch, hefx_path path,
+                           void* stream, NttMode mode) {
+    hefx_status st = check_ntt_args(ctx, p, d, "d_data");
+    if (st != HEFX_OK) return st;
+    if ((st = use_device(ctx)) != HEFX_OK) return st;
+    const hefx_path pth = resolve(p, path);
+    if (pth == HEFX_PATH_TENSOR && (st = ensure_tc(ctx, p)) != HEFX_OK) return st;
+    if (batch == 0) return HEFX_OK;
+    cudaError_t e;
+    if (pth == HEFX_PATH_TENSOR) {
+        e = launch_ntt_tc(p, mode, d, nullptr, d, batch, (cudaStream_t)stream);
+    } else if (pth == HEFX_PATH_CUDACORE) {
+        e = launch_ntt_cc(p, mode, d, nullptr, d, batch * p->nlimbs, (cudaStream_t)stream);
+    } else {
+        return fail(ctx, HEFX_EINVAL, "unknown path %d", (int)path);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, mode == MODE_FWD ? "hefx_ntt_fwd launch" : "hefx_ntt_inv launch");
+    return HEFX_OK;
+}
+
+hefx_status hefx_ntt_fwd(hefx_ctx* ctx, const hefx_params* p, uint32_t* d, size_t batch, hefx_path path,
+                         void* stream) {
+    return run_ntt(ctx, p, d, batch, path, stream, MODE_FWD);
+}
+
+hefx_status hefx_ntt_inv(hefx_ctx* ctx, const hefx_params* p, uint32_t* d, size_t batch, hefx_path path,
+                         void* stream) {
+    return run_ntt(ctx, p, d, batch, path, stream, MODE_INV);
+}
+
+hefx_status hefx_poly_mul(hefx_ctx* ctx, const hefx_params* p, const uint32_t* a, const uint32_t* b, uint32_t* c,
+                          size_t batch, hefx_path path, void* stream) {
+    hefx_status st;
+    if ((st = check_ntt_args(ctx, p, a, "d_a")) != HEFX_OK) return st;
+    if ((st = check_ntt_args(ctx, p, b, "d_b")) != HEFX_OK) return st;
+    if ((st = check_ntt_args(ctx, p, c, "d_c")) != HEFX_OK) return st;
+    if ((st = use_device(ctx)) != HEFX_OK) return st;
+    const hefx_path pth = resolve(p, path);
+    if (pth != HEFX_PATH_CUDACORE && pth != HEFX_PATH_TENSOR) return fail(ctx, HEFX_EINVAL, "unknown path");
+    if (pth == HEFX_PATH_TENSOR && (st = ensure_tc(ctx, p)) != HEFX_OK) return st;
+    if (batch == 0) return HEFX_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t rows = batch * p->nlimbs;
+    auto launch = [&](NttMode m, const uint32_t* in, const uint32_t* had, uint32_t* out) {
+        return pth == HEFX_PATH_TENSOR ? launch_ntt_tc(p, m, in, had, out, batch, s)
+                                       : launch_ntt_cc(p, m, in, had, out, rows, s);
+    };
+    cudaError_t e;
+    if (a == b) {
+        // c = INTT(NTT(a) o NTT(a))
+        e = launch(MODE_FWD, a, nullptr, c);
+        if (e == cudaSuccess) e = launch(MODE_HAD_INV, c, c, c);
+    } else {
+        if (c == b) std::swap(a, b);  // the product commutes; keep b intact while c is written
+        e = launch(MODE_FWD, a, nullptr, c);                    // c = NTT(a)
+        if (e == cudaSuccess) e = launch(MODE_FWD_HAD_INV, b, c, c);  // c = INTT(NTT(b) o c)
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "hefx_poly_mul launch");
+    return HEFX_OK;
+}
+
+hefx_status hefx_bconv_plan_create(hefx_ctx* ctx, uint32_t log2n, const uint32_t* src, uint32_t L,
+                                   const uint32_t* dst, uint32_t Lp, hefx_bconv_plan** out) {
+    if (!ctx || !out) return HEFX_EINVAL;
+    *out = nullptr;
+    if (log2n > 24) return fail(ctx, HEFX_EUNSUPPORTED, "log2n = %u outside [0, 24]", log2n);
+    if (!src || !dst || L == 0 || Lp == 0 || L > (uint32_t)kBConvMaxLimbs || Lp > (uint32_t)kBConvMaxLimbs)
+        return fail(ctx, HEFX_EINVAL, "need 1..%d source and target primes", kBConvMaxLimbs);
+    std::set<uint32_t> seen;
+    for (uint32_t i = 0; i < L + Lp; ++i) {
+        const uint32_t q = i < L ? src[i] : dst[i - L];
+        if (q < 3 || q >= (1u << 30) || !is_prime(q))
+            return fail(ctx, HEFX_EINVAL, "modulus %u is not a prime in [3, 2^30)", q);
+        if (!seen.insert(q).second) return fail(ctx, HEFX_EINVAL, "modulus %u repeats", q);
+    }
+    hefx_status st = use_device(ctx);
+    if (st != HEFX_OK) return st;
+    hefx_bconv_plan* p = new hefx_bconv_plan();
+    p->ctx = ctx;
+    p->log2n = log2n;
+    p->L = L;
+    p->Lp = Lp;
+    p->src.assign(src, src + L);
+    p->dst.assign(dst, dst + Lp);
+    cudaError_t e = bconv_plan_upload(p);
+    if (e != cudaSuccess) {
+        hefx_bconv_plan_destroy(p);
+        return cuda_fail(ctx, e, "basis-conversion constants");
+    }
+    *out = p;
+    return HEFX_OK;
+}
+
+void hefx_bconv_plan_destroy(hefx_bconv_plan* p) {
+    if (!p) return;
+    bconv_plan_free(p);
+    delete p;
+}
+
+hefx_status hefx_basis_convert(hefx_ctx* ctx, const hefx_bconv_plan* plan, const uint32_t* in, uint32_t* out,
+                               size_t batch, hefx_path path, void* stream) {
+    if (!ctx) return HEFX_EINVAL;
+    if (!plan || plan->ctx != ctx) return fail(ctx, HEFX_EINVAL, "plan is null or belongs to another context");
+    if (!in || !out) return fail(ctx, HEFX_EINVAL, "null buffer");
+    if (!aligned16(in) || !aligned16(out)) return fail(ctx, HEFX_EINVAL, "buffers must be 16-byte aligned");
+    const size_t n = (size_t)1 << plan->log2n;
+    const char *ib = (const char*)in, *ob = (const char*)out;
+    if (ib < ob + batch * plan->Lp * n * 4 && ob < ib + batch * plan->L * n * 4)
+        return fail(ctx, HEFX_EINVAL, "d_out overlaps d_in");
+    hefx_status st = use_device(ctx);
+    if (st != HEFX_OK) return st;
+    if (path == HEFX_PATH_AUTO) path = bconv_tc_available(plan) ? HEFX_PATH_TENSOR : HEFX_PATH_CUDACORE;
+    if (path == HEFX_PATH_TENSOR && !bconv_tc_available(plan))
+        return fail(ctx, HEFX_EUNSUPPORTED, "tensor basis conversion not available for this plan");
+    if (batch == 0) return HEFX_OK;
+    cudaError_t e;
+    if (path == HEFX_PATH_TENSOR)
+        e = launch_bconv_tc(plan, in, out, batch, (cudaStream_t)stream);
+    else if (path == HEFX_PATH_CUDACORE)
+        e = launch_bconv_cc(plan, in, out, batch, (cudaStream_t)stream);
+    else
+        return fail(ctx, HEFX_EINVAL, "unknown path %d", (int)path);
+    if (e == cudaErrorNotSupported)
+        return fail(ctx, HEFX_EUNSUPPORTED, "tensor basis conversion not available for this plan");
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "hefx_basis_convert launch");
+    return HEFX_OK;
+}
+
+/* Tuner hook (not in the public header): records the path AUTO resolves to. */
+hefx_status hefx_params_set_auto_path(hefx_params* p, hefx_path path) {
+    if (!p || (path != HEFX_PATH_CUDACORE && path != HEFX_PATH_TENSOR && path != HEFX_PATH_AUTO)) return HEFX_EINVAL;
+    p->tuned_path = path;
+    return HEFX_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,85 @@
+// Internal types shared by the hefx host API and its kernels (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/hefx.h"
+
+namespace hefx {
+
+// Per-limb constants of one parameter set, in device memory ([nlimbs] array).
+struct LimbConst {
+    uint32_t q;
+    uint32_t qinv_neg;            // -q^-1 mod 2^32 (Montgomery REDC)
+    uint32_t ninv, ninv_sh;       // N^-1 mod q and its Shoup companion
+    uint32_t ninvw, ninvw_sh;     // N^-1 * psi^-brv_N(1): twiddle of the last Gentleman-Sande stage
+    uint32_t ninvR, ninvR_sh;     // N^-1 * 2^32: undoes the 2^-32 of a Montgomery Hadamard product
+    uint32_t ninvRw, ninvRw_sh;   // N^-1 * 2^32 * psi^-brv_N(1)
+    uint32_t pad[6];
+};
+static_assert(sizeof(LimbConst) == 64, "LimbConst is one 64-byte line");
+
+// Device tables of the tensor-core (matrix) NTT for one parameter set; see ntt_tc.cu.
+struct TensorTables;
+
+}  // namespace hefx
+
+struct hefx_ctx {
+    int device = 0;
+    int sm_count = 0;
+    std::string last_error;
+    std::mutex mu;
+};
+
+struct hefx_params {
+    hefx_ctx* ctx = nullptr;
+    uint32_t log2n = 0;
+    uint32_t n = 0;
+    uint32_t nlimbs = 0;
+    std::vector<uint32_t> primes;
+    std::vector<uint32_t> psi;        // per limb
+    hefx::LimbConst* d_lc = nullptr;  // [nlimbs]
+    uint2* d_tw_fwd = nullptr;        // [nlimbs][N]: (psi^brv_N(k), Shoup companion), k >= 1
+    uint2* d_tw_inv = nullptr;        // [nlimbs][N]: (psi^-brv_N(k), Shoup companion)
+    hefx::TensorTables* tc = nullptr; // built on first tensor-path use
+    std::mutex tc_mu;
+    hefx_path tuned_path = HEFX_PATH_AUTO;
+};
+
+struct hefx_bconv_plan {
+    hefx_ctx* ctx = nullptr;
+    uint32_t log2n = 0;
+    uint32_t L = 0, Lp = 0;
+    std::vector<uint32_t> src, dst;
+    void* d_const = nullptr;          // BConvConst (see bconv.cu)
+    void* d_bat = nullptr;            // BAT digit matrix of step 2 (fp16), see bconv.cu
+};
+
+namespace hefx {
+
+// Kernel launchers (return a CUDA error code; the host API maps it to hefx_status).
+enum NttMode { MODE_FWD = 0, MODE_INV = 1, MODE_FWD_HAD_INV = 2, MODE_HAD_INV = 3 };
+
+cudaError_t launch_ntt_cc(const hefx_params* p, NttMode mode, const uint32_t* in, const uint32_t* had, uint32_t* out,
+                          size_t rows, cudaStream_t stream);
+
+cudaError_t launch_bconv_cc(const hefx_bconv_plan* plan, const uint32_t* in, uint32_t* out, size_t batch,
+                            cudaStream_t stream);
+cudaError_t bconv_plan_upload(hefx_bconv_plan* plan);
+void bconv_plan_free(hefx_bconv_plan* plan);
+
+// Tensor-core path (ntt_tc.cu / bconv_tc.cu).
+bool tc_supported(const hefx_params* p);
+cudaError_t tc_prepare(hefx_params* p);
+void tc_free(hefx_params* p);
+cudaError_t launch_ntt_tc(const hefx_params* p, NttMode mode, const uint32_t* in, const uint32_t* had, uint32_t* out,
+                          size_t batch, cudaStream_t stream);
+cudaError_t launch_bconv_tc(const hefx_bconv_plan* plan, const uint32_t* in, uint32_t* out, size_t batch,
+                            cudaStream_t stream);
+
+}  // namespace hefx

@@ -1,0 +1,162 @@
+"""Thin ctypes binding of the hefx C ABI (include/hefx.h).
+
+Argument marshalling only: every transform, product and conversion runs in libhefx.so's
+CUDA kernels.  Device buffers are passed as raw pointers (torch tensors are accepted and
+their data_ptr() used); streams as cudaStream_t handles (torch streams accepted).  There
+is no CPU fallback: loading fails loudly when the library is missing or does not load.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhefx.so")
+
+HEFX_OK, HEFX_EINVAL, HEFX_EUNSUPPORTED, HEFX_ENOMEM, HEFX_EBUDGET, HEFX_ECUDA, HEFX_ETIMEOUT = range(7)
+STATUS_NAMES = ["HEFX_OK", "HEFX_EINVAL", "HEFX_EUNSUPPORTED", "HEFX_ENOMEM", "HEFX_EBUDGET", "HEFX_ECUDA",
+                "HEFX_ETIMEOUT"]
+HEFX_PATH_AUTO, HEFX_PATH_CUDACORE, HEFX_PATH_TENSOR = 0, 1, 2
+PATHS = {"auto": HEFX_PATH_AUTO, "cudacore": HEFX_PATH_CUDACORE, "tensor": HEFX_PATH_TENSOR}
+
+# Every symbol include/hefx.h declares, with its ctypes signature.
+_vp, _u32, _sz, _i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_size_t, ctypes.c_int
+_u32p = ctypes.POINTER(ctypes.c_uint32)
+SIGNATURES = {
+    "hefx_create": (_i32, [ctypes.POINTER(_vp), _i32]),
+    "hefx_destroy": (None, [_vp]),
+    "hefx_last_error": (ctypes.c_char_p, [_vp]),
+    "hefx_version": (ctypes.c_char_p, []),
+    "hefx_params_create": (_i32, [_vp, _u32, _u32p, _u32, ctypes.POINTER(_vp)]),
+    "hefx_params_destroy": (None, [_vp]),
+    "hefx_params_set_auto_path": (_i32, [_vp, _i32]),
+    "hefx_ntt_fwd": (_i32, [_vp, _vp, _vp, _sz, _i32, _vp]),
+    "hefx_ntt_inv": (_i32, [_vp, _vp, _vp, _sz, _i32, _vp]),
+    "hefx_poly_mul": (_i32, [_vp, _vp, _vp, _vp, _vp, _sz, _i32, _vp]),
+    "hefx_bconv_plan_create": (_i32, [_vp, _u32, _u32p, _u32, _u32p, _u32, ctypes.POINTER(_vp)]),
+    "hefx_bconv_plan_destroy": (None, [_vp]),
+    "hefx_basis_convert": (_i32, [_vp, _vp, _vp, _vp, _sz, _i32, _vp]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads libhefx.so (building it first if absent) and binds every declared symbol."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            from . import build as _build
+            _build.build()
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+class HefxError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
+        self.status = status
+
+
+def _ptr(x) -> int:
+    if x is None:
+        return 0
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    return int(x)
+
+
+def _stream(s) -> int:
+    if s is None:
+        return 0
+    if hasattr(s, "cuda_stream"):
+        return s.cuda_stream
+    return int(s)
+
+
+def _path(p) -> int:
+    return PATHS[p] if isinstance(p, str) else int(p)
+
+
+def _u32_array(vals):
+    arr = (ctypes.c_uint32 * len(vals))(*[int(v) for v in vals])
+    return arr
+
+
+# ----------------------------------------------------------------------------- raw C ABI
+
+def hefx_create(device: int = 0) -> int:
+    h = _vp()
+    st = load().hefx_create(ctypes.byref(h), device)
+    if st != HEFX_OK:
+        raise HefxError(st, f"hefx_create(device={device}) failed")
+    return h.value
+
+
+def hefx_destroy(ctx: int) -> None:
+    load().hefx_destroy(ctx)
+
+
+def hefx_last_error(ctx: int) -> str:
+    return (load().hefx_last_error(ctx) or b"").decode()
+
+
+def hefx_version() -> str:
+    return load().hefx_version().decode()
+
+
+def _check(ctx: int, st: int):
+    if st != HEFX_OK:
+        raise HefxError(st, hefx_last_error(ctx))
+
+
+def hefx_params_create(ctx: int, log2n: int, primes) -> int:
+    h = _vp()
+    arr = _u32_array(primes)
+    _check(ctx, load().hefx_params_create(ctx, log2n, arr, len(primes), ctypes.byref(h)))
+    return h.value
+
+
+def hefx_params_destroy(params: int) -> None:
+    load().hefx_params_destroy(params)
+
+
+def hefx_params_set_auto_path(params: int, path) -> int:
+    return load().hefx_params_set_auto_path(params, _path(path))
+
+
+def hefx_ntt_fwd(ctx, params, data, batch, path="cudacore", stream=None) -> None:
+    _check(ctx, load().hefx_ntt_fwd(ctx, params, _ptr(data), batch, _path(path), _stream(stream)))
+
+
+def hefx_ntt_inv(ctx, params, data, batch, path="cudacore", stream=None) -> None:
+    _check(ctx, load().hefx_ntt_inv(ctx, params, _ptr(data), batch, _path(path), _stream(stream)))
+
+
+def hefx_poly_mul(ctx, params, a, b, c, batch, path="cudacore", stream=None) -> None:
+    _check(ctx, load().hefx_poly_mul(ctx, params, _ptr(a), _ptr(b), _ptr(c), batch, _path(path), _stream(stream)))
+
+
+def hefx_bconv_plan_create(ctx: int, log2n: int, src, dst) -> int:
+    h = _vp()
+    _check(ctx, load().hefx_bconv_plan_create(ctx, log2n, _u32_array(src), len(src), _u32_array(dst), len(dst),
+                                             ctypes.byref(h)))
+    return h.value
+
+
+def hefx_bconv_plan_destroy(plan: int) -> None:
+    load().hefx_bconv_plan_destroy(plan)
+
+
+def hefx_basis_convert(ctx, plan, d_in, d_out, batch, path="auto", stream=None) -> None:
+    _check(ctx, load().hefx_basis_convert(ctx, plan, _ptr(d_in), _ptr(d_out), batch, _path(path), _stream(stream)))
+
+
+def raw_status(fn_name: str, *args) -> int:
+    """Calls a C entry point and returns its status code without raising (for error tests)."""
+    return getattr(load(), fn_name)(*args)

@@ -1,0 +1,110 @@
+"""GPU parity of the RNS basis conversion against the CPU oracle through the C ABI (bit-exact)."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import crt
+from paper_2501_07047_gb300 import hefx, inputs
+
+from hefx_testutil import empty_dev, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+PATHS = ["cudacore", "tensor"]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = hefx.hefx_create(0)
+    yield c
+    hefx.hefx_destroy(c)
+
+
+def convert(ctx, plan, a, Lp, path):
+    B, L, n = a.shape
+    din, dout = to_dev(a), empty_dev((B, Lp, n))
+    hefx.hefx_basis_convert(ctx, plan, din, dout, B, path)
+    return to_host(dout).reshape(B, Lp, n)
+
+
+def available(ctx, plan, path, L, Lp, n):
+    din, dout = empty_dev((1, L, n)), empty_dev((1, Lp, n))
+    return hefx.raw_status("hefx_basis_convert", ctx, plan, din.data_ptr(), dout.data_ptr(), 0,
+                           hefx.PATHS[path], 0) == hefx.HEFX_OK
+
+
+@pytest.mark.parametrize("path", PATHS)
+@pytest.mark.parametrize("logn,L,Lp,batch", [(0, 1, 1, 1), (3, 1, 3, 2), (5, 2, 2, 3), (7, 5, 3, 2),
+                                             (10, 12, 28, 1), (9, 24, 8, 2), (12, 16, 40, 1), (6, 64, 64, 1),
+                                             (11, 24, 56, 1)])
+def test_bconv_matches_oracle(ctx, path, logn, L, Lp, batch):
+    qs, ps = inputs.source_primes(L), inputs.special_primes(Lp)
+    plan = hefx.hefx_bconv_plan_create(ctx, logn, qs, ps)
+    try:
+        n = 1 << logn
+        if not available(ctx, plan, path, L, Lp, n):
+            pytest.skip(f"{path} basis conversion not built for L={L}, L'={Lp}")
+        a = inputs.residue_tensor(inputs.derive_seed(40, logn, L, Lp), batch, qs, n)
+        got = convert(ctx, plan, a, Lp, path)
+        assert (got == oracle.bconv(a, qs, ps)).all()
+    finally:
+        hefx.hefx_bconv_plan_destroy(plan)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_bconv_config3_full_size_sampled(ctx, path):
+    """16 x 24 limbs x 2^16 -> 8 limbs: 1024 sampled coefficients checked by big-integer CRT
+    (the integer the fast conversion reduces) plus one full polynomial against the oracle."""
+    L, Lp, B, n = 24, 8, 16, 1 << 16
+    qs, ps = inputs.source_primes(L), inputs.special_primes(Lp)
+    plan = hefx.hefx_bconv_plan_create(ctx, 16, qs, ps)
+    try:
+        if not available(ctx, plan, path, L, Lp, n):
+            pytest.skip("path not built")
+        a = inputs.residue_tensor(inputs.derive_seed(3, 0), B, qs, n)
+        got = convert(ctx, plan, a, Lp, path)
+        assert (got[5] == oracle.bconv(a[5], qs, ps)).all()
+        rng = np.random.default_rng(9)
+        for _ in range(1024):
+            b, x = int(rng.integers(B)), int(rng.integers(n))
+            y = crt.fast_conversion_integer([int(v) for v in a[b, :, x]], qs)
+            assert [int(v) for v in got[b, :, x]] == [y % p for p in ps]
+    finally:
+        hefx.hefx_bconv_plan_destroy(plan)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_bconv_edge_values(ctx, path):
+    L, Lp, n = 6, 4, 256
+    qs, ps = inputs.source_primes(L), inputs.special_primes(Lp)
+    plan = hefx.hefx_bconv_plan_create(ctx, 8, qs, ps)
+    try:
+        if not available(ctx, plan, path, L, Lp, n):
+            pytest.skip("path not built")
+        a = np.zeros((3, L, n), np.uint32)
+        for i, q in enumerate(qs):
+            a[1, i] = q - 1
+            a[2, i] = np.arange(n) % q
+        got = convert(ctx, plan, a, Lp, path)
+        assert (got[0] == 0).all()
+        assert (got == oracle.bconv(a, qs, ps)).all()
+    finally:
+        hefx.hefx_bconv_plan_destroy(plan)
+
+
+def test_bconv_validation(ctx):
+    qs, ps = inputs.source_primes(3), inputs.special_primes(2)
+    with pytest.raises(hefx.HefxError) as e:
+        hefx.hefx_bconv_plan_create(ctx, 8, qs, [qs[0]])     # target repeats a source prime
+    assert e.value.status == hefx.HEFX_EINVAL
+    with pytest.raises(hefx.HefxError) as e:
+        hefx.hefx_bconv_plan_create(ctx, 8, qs + [91], ps)   # 91 = 7 * 13
+    assert e.value.status == hefx.HEFX_EINVAL
+    plan = hefx.hefx_bconv_plan_create(ctx, 8, qs, ps)
+    try:
+        d = empty_dev(3 * 256 + 2 * 256)
+        with pytest.raises(hefx.HefxError) as e:                 # overlapping buffers
+            hefx.hefx_basis_convert(ctx, plan, d, d.data_ptr() + 16, 1, "cudacore")
+        assert e.value.status == hefx.HEFX_EINVAL
+    finally:
+        hefx.hefx_bconv_plan_destroy(plan)

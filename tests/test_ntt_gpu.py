@@ -1,0 +1,226 @@
+"""GPU parity of the NTT / INTT / polynomial product against the CPU oracle, through the C ABI.
+
+Integer work: every comparison is bit-exact.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2501_07047_gb300 import hefx, inputs
+
+from hefx_testutil import empty_dev, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+PATHS = ["cudacore", "tensor"]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    assert torch.cuda.is_available()
+    c = hefx.hefx_create(0)
+    yield c
+    hefx.hefx_destroy(c)
+
+
+def make_params(ctx, logn, primes):
+    return hefx.hefx_params_create(ctx, logn, primes)
+
+
+def run_fwd(ctx, params, arr, path):
+    d = to_dev(arr)
+    hefx.hefx_ntt_fwd(ctx, params, d, arr.shape[0], path)
+    return to_host(d).reshape(arr.shape)
+
+
+def run_inv(ctx, params, arr, path):
+    d = to_dev(arr)
+    hefx.hefx_ntt_inv(ctx, params, d, arr.shape[0], path)
+    return to_host(d).reshape(arr.shape)
+
+
+def supported(ctx, params, path, batch=1, L=1, n=8):
+    if path == "cudacore":
+        return True
+    d = empty_dev((batch, L, n))
+    st = hefx.raw_status("hefx_ntt_fwd", ctx, params, d.data_ptr(), 0, hefx.PATHS[path], 0)
+    return st == hefx.HEFX_OK
+
+
+# ----------------------------------------------------------------------------- config 1
+
+def test_config1_single_limb_cudacore(ctx):
+    """N = 4096, one 28-bit prime q = 1 mod 8192: forward, inverse and one product."""
+    q = inputs.source_primes(1)[0]
+    assert (q - 1) % 8192 == 0
+    p = make_params(ctx, 12, [q])
+    try:
+        a = inputs.uniform_residues(inputs.derive_seed(1, 1), 4096, q)
+        b = inputs.uniform_residues(inputs.derive_seed(1, 2), 4096, q)
+        ahat = run_fwd(ctx, p, a.reshape(1, 1, -1), "cudacore")[0, 0]
+        assert (ahat == oracle.ntt(a, q)).all()
+        back = run_inv(ctx, p, ahat.reshape(1, 1, -1), "cudacore")[0, 0]
+        assert (back == a).all()
+        da, db, dc = to_dev(a), to_dev(b), empty_dev(4096)
+        hefx.hefx_poly_mul(ctx, p, da, db, dc, 1, "cudacore")
+        c = to_host(dc)
+        assert (c == oracle.polymul_schoolbook(a, b, q)).all()
+    finally:
+        hefx.hefx_params_destroy(p)
+
+
+# ----------------------------------------------------------------------------- shapes
+
+@pytest.mark.parametrize("path", PATHS)
+@pytest.mark.parametrize("logn,L,batch", [(3, 1, 1), (4, 3, 5), (5, 2, 3), (6, 1, 7), (7, 5, 2), (8, 3, 3),
+                                          (9, 2, 2), (10, 4, 3), (11, 3, 1), (12, 5, 3), (13, 2, 3),
+                                          (14, 3, 2), (15, 2, 2), (16, 3, 2)])
+def test_ntt_matches_oracle(ctx, path, logn, L, batch):
+    primes = inputs.source_primes(L + 2)[2:]
+    p = make_params(ctx, logn, primes)
+    try:
+        if not supported(ctx, p, path, batch, L, 1 << logn):
+            pytest.skip(f"{path} path not built for N = 2^{logn}")
+        data = inputs.residue_tensor(inputs.derive_seed(10, logn, L, batch), batch, primes, 1 << logn)
+        expect = oracle.ntt_batch(data, primes)
+        got = run_fwd(ctx, p, data, path)
+        assert (got == expect).all(), f"first mismatch at {np.argwhere(got != expect)[0]}"
+        back = run_inv(ctx, p, got, path)
+        assert (back == data).all()
+        # the inverse alone against the oracle on an arbitrary (not forward-produced) input
+        rnd = inputs.residue_tensor(inputs.derive_seed(11, logn, L, batch), batch, primes, 1 << logn)
+        assert (run_inv(ctx, p, rnd, path) == oracle.ntt_batch(rnd, primes, inverse=True)).all()
+    finally:
+        hefx.hefx_params_destroy(p)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_special_primes_30bit(ctx, path):
+    primes = inputs.special_primes(3)
+    p = make_params(ctx, 16, primes)
+    try:
+        if not supported(ctx, p, path, 1, 3, 1 << 16):
+            pytest.skip("path not built for 30-bit moduli")
+        data = inputs.residue_tensor(21, 1, primes, 1 << 16)
+        got = run_fwd(ctx, p, data, path)
+        assert (got == oracle.ntt_batch(data, primes)).all()
+        assert (run_inv(ctx, p, got, path) == data).all()
+    finally:
+        hefx.hefx_params_destroy(p)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_edge_values(ctx, path):
+    """All-zero, all q-1 (the largest residue) and a delta input."""
+    primes = inputs.source_primes(2)
+    n = 1 << 16
+    p = make_params(ctx, 16, primes)
+    try:
+        if not supported(ctx, p, path, 3, 2, n):
+            pytest.skip("path not built")
+        data = np.zeros((3, 2, n), np.uint32)
+        for l, q in enumerate(primes):
+            data[1, l, :] = q - 1
+            data[2, l, 0] = 1
+        got = run_fwd(ctx, p, data, path)
+        assert (got[0] == 0).all()
+        assert (got[2] == 1).all()
+        assert (got == oracle.ntt_batch(data, primes)).all()
+        assert (run_inv(ctx, p, got, path) == data).all()
+    finally:
+        hefx.hefx_params_destroy(p)
+
+
+# ----------------------------------------------------------------------------- config 2 (full size)
+
+@pytest.mark.parametrize("path", PATHS)
+def test_config2_full_size_sampled(ctx, path):
+    """N = 2^16, L = 24, batch 8: every output of three limbs in full, 256 sampled outputs by
+    the O(N) definition elsewhere, and INTT(NTT(x)) = x over the whole batch."""
+    primes = inputs.source_primes(24)
+    n = 1 << 16
+    p = make_params(ctx, 16, primes)
+    try:
+        if not supported(ctx, p, path, 8, 24, n):
+            pytest.skip("path not built")
+        data = inputs.residue_tensor(inputs.derive_seed(2, 0), 8, primes, n)
+        d = to_dev(data)
+        hefx.hefx_ntt_fwd(ctx, p, d, 8, path)
+        got = to_host(d).reshape(data.shape)
+        for (b, l) in [(0, 0), (3, 11), (7, 23)]:
+            assert (got[b, l] == oracle.ntt(data[b, l], primes[l])).all()
+        rng = np.random.default_rng(5)
+        for _ in range(256):
+            b, l, k = int(rng.integers(8)), int(rng.integers(24)), int(rng.integers(n))
+            assert got[b, l, k] == oracle.ntt_at(data[b, l], primes[l], k)
+        hefx.hefx_ntt_inv(ctx, p, d, 8, path)
+        assert (to_host(d).reshape(data.shape) == data).all()
+    finally:
+        hefx.hefx_params_destroy(p)
+
+
+# ----------------------------------------------------------------------------- products
+
+@pytest.mark.parametrize("path", PATHS)
+@pytest.mark.parametrize("logn,L,batch", [(3, 2, 2), (6, 1, 3), (10, 3, 2), (12, 2, 2), (13, 2, 1), (15, 2, 1),
+                                          (16, 3, 2)])
+def test_poly_mul_matches_oracle(ctx, path, logn, L, batch):
+    primes = inputs.source_primes(L)
+    n = 1 << logn
+    p = make_params(ctx, logn, primes)
+    try:
+        if not supported(ctx, p, path, batch, L, n):
+            pytest.skip("path not built")
+        a = inputs.residue_tensor(inputs.derive_seed(30, logn), batch, primes, n)
+        b = inputs.residue_tensor(inputs.derive_seed(31, logn), batch, primes, n)
+        expect = oracle.polymul_batch(a, b, primes)
+        if logn <= 10:
+            for l, q in enumerate(primes):
+                assert (expect[0, l] == oracle.polymul_schoolbook(a[0, l], b[0, l], q)).all()
+        da, db, dc = to_dev(a), to_dev(b), empty_dev(a.shape)
+        hefx.hefx_poly_mul(ctx, p, da, db, dc, batch, path)
+        assert (to_host(dc).reshape(a.shape) == expect).all()
+        # aliasing: c = a, c = b, a = b (square), a = b = c
+        hefx.hefx_poly_mul(ctx, p, da, db, da, batch, path)
+        assert (to_host(da).reshape(a.shape) == expect).all()
+        da = to_dev(a)
+        hefx.hefx_poly_mul(ctx, p, da, db, db, batch, path)
+        assert (to_host(db).reshape(a.shape) == expect).all()
+        sq = oracle.polymul_batch(a, a, primes)
+        da, dc = to_dev(a), empty_dev(a.shape)
+        hefx.hefx_poly_mul(ctx, p, da, da, dc, batch, path)
+        assert (to_host(dc).reshape(a.shape) == sq).all()
+        hefx.hefx_poly_mul(ctx, p, da, da, da, batch, path)
+        assert (to_host(da).reshape(a.shape) == sq).all()
+    finally:
+        hefx.hefx_params_destroy(p)
+
+
+# ----------------------------------------------------------------------------- errors
+
+def test_host_validation(ctx):
+    q = inputs.source_primes(1)[0]
+    with pytest.raises(hefx.HefxError) as e:
+        hefx.hefx_params_create(ctx, 12, [q + 2])          # not prime
+    assert e.value.status == hefx.HEFX_EINVAL
+    with pytest.raises(hefx.HefxError) as e:
+        hefx.hefx_params_create(ctx, 12, [7681])           # prime but not 1 mod 2N for N = 4096
+    assert e.value.status == hefx.HEFX_EINVAL
+    with pytest.raises(hefx.HefxError) as e:
+        hefx.hefx_params_create(ctx, 12, [q, q])           # repeated
+    assert e.value.status == hefx.HEFX_EINVAL
+    with pytest.raises(hefx.HefxError) as e:
+        hefx.hefx_params_create(ctx, 17, [q])
+    assert e.value.status == hefx.HEFX_EUNSUPPORTED
+    p = hefx.hefx_params_create(ctx, 12, [q])
+    try:
+        d = empty_dev(4096 + 4)
+        with pytest.raises(hefx.HefxError) as e:
+            hefx.hefx_ntt_fwd(ctx, p, d.data_ptr() + 4, 1)  # misaligned
+        assert e.value.status == hefx.HEFX_EINVAL
+        with pytest.raises(hefx.HefxError):
+            hefx.hefx_ntt_fwd(ctx, p, 0, 1)
+        hefx.hefx_ntt_fwd(ctx, p, d, 0)                     # batch 0: no-op
+    finally:
+        hefx.hefx_params_destroy(p)
