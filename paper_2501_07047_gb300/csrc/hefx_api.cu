@@ -130,10 +130,34 @@ hefx_status hefx_params_create(hefx_ctx* ctx, uint32_t log2n, const uint32_t* pr
             pw[e] = mul_mod(pw[e - 1], psi, q);
             pwi[e] = mul_mod(pwi[e - 1], psi_inv, q);
         }
+        // Twiddle tables in bit-reversed order (entry k = psi^(+-brv(k))), except that the
+        // stages of the smallest-stride register pass are stored group-major: the group
+        // G = J 2^v + g of sub-transform J sits at stage_base + g * (N / 2^RS) + J, so the
+        // lanes of a warp (consecutive J) read consecutive entries (MAT's offline
+        // reordering of constants, Sec. IV-B, applied to the table layout).
+        const int RS = ntt_cc_small_radix((int)log2n);
+        const uint64_t nsub = n >> RS;
+        auto fwd_pos = [&](uint64_t k) -> uint64_t {
+            if (k == 0) return 0;
+            int s = 63 - __builtin_clzll(k);  // stage of entry k: k in [2^s, 2^(s+1))
+            if (s < (int)log2n - RS) return k;
+            const int v = s - ((int)log2n - RS);
+            const uint64_t G = k - (1ull << s), J = G >> v, g = G & ((1ull << v) - 1);
+            return (1ull << s) + g * nsub + J;
+        };
+        auto inv_pos = [&](uint64_t k) -> uint64_t {
+            if (k == 0) return 0;
+            int hb = 63 - __builtin_clzll(k);  // entry k belongs to stage e = log2n - 1 - hb
+            const int e = (int)log2n - 1 - hb;
+            if (e >= RS) return k;
+            const int w = RS - 1 - e;
+            const uint64_t G = k - (1ull << hb), J = G >> w, g = G & ((1ull << w) - 1);
+            return (1ull << hb) + g * nsub + J;
+        };
         for (uint64_t k = 0; k < n; ++k) {
             const uint32_t r = bit_reverse((uint32_t)k, (int)log2n);
-            twf[l * n + k] = make_uint2((uint32_t)pw[r], shoup(pw[r], q));
-            twi[l * n + k] = make_uint2((uint32_t)pwi[r], shoup(pwi[r], q));
+            twf[l * n + fwd_pos(k)] = make_uint2((uint32_t)pw[r], shoup(pw[r], q));
+            twi[l * n + inv_pos(k)] = make_uint2((uint32_t)pwi[r], shoup(pwi[r], q));
         }
         LimbConst& c = lc[l];
         memset(&c, 0, sizeof c);

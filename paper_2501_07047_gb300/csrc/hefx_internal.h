@@ -24,6 +24,13 @@ struct LimbConst {
 };
 static_assert(sizeof(LimbConst) == 64, "LimbConst is one 64-byte line");
 
+// Number of stages in the CUDA-core NTT's smallest-stride register pass for N = 2^log2n.
+// The twiddle entries of those stages are stored permuted (see hefx_params_create) so that
+// the per-lane loads of that pass are coalesced.
+inline constexpr int ntt_cc_small_radix(int log2n) {
+    return (log2n >= 16 ? log2n - 1 : log2n) < 5 ? (log2n >= 16 ? log2n - 1 : log2n) : 5;
+}
+
 // Device tables of the tensor-core (matrix) NTT for one parameter set; see ntt_tc.cu.
 struct TensorTables;
 

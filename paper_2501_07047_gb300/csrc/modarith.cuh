@@ -27,7 +27,8 @@ __device__ __forceinline__ uint32_t mul_mont_lazy(uint32_t x, uint32_t y, uint32
     return hi + __umulhi(m, q) + (lo != 0u);
 }
 
-__device__ __forceinline__ uint32_t csub(uint32_t x, uint32_t bound) { return x >= bound ? x - bound : x; }
+// x >= bound ? x - bound : x, as one unsigned min (x - bound wraps above x when x < bound).
+__device__ __forceinline__ uint32_t csub(uint32_t x, uint32_t bound) { return umin(x, x - bound); }
 
 // [0, 4q) -> [0, q)
 __device__ __forceinline__ uint32_t reduce4(uint32_t x, uint32_t q) { return csub(csub(x, 2 * q), q); }

@@ -56,9 +56,170 @@ struct KArgs {
     uint32_t L;
 };
 
-// Forward pass over global stages s0 .. s0+R-1 (stage s pairs j, j + N/2^(s+1)).
+// Where a register pass takes its inputs and puts its outputs.
+enum : int { SRC_SMEM = 0, SRC_GLOBAL = 1, SRC_SPLIT0 = 2, SRC_GLOBAL_HAD = 3 };
+enum : int { DST_SMEM = 0, DST_GLOBAL = 1, DST_GLOBAL_REDUCE = 2 };
+
+// The CTA's share of the batch: rows [row0, row0 + nrows) (or one half of row row0).
+struct Seg {
+    uint32_t row0, gbase, half;
+    int nrows;
+};
+
+// Loads the 2^R elements jb + k * 2^logs (k < 2^R) of local row `row` into x.
+template <int R, int LOGN, int logs, int SRC>
+__device__ __forceinline__ void load_elems(uint32_t (&x)[1 << R], const uint32_t* sm, const KArgs& a, const Seg& sg,
+                                           int row, int jb, const LimbConst& lc, const uint2* tw) {
+    using C = Cfg<LOGN>;
+    constexpr int N = 1 << LOGN;
+    if constexpr (SRC == SRC_SMEM) {
+#pragma unroll
+        for (int k = 0; k < (1 << R); ++k) x[k] = sm[pad(row * C::m + jb + (k << logs))];
+    } else {
+        const bool valid = row < sg.nrows;
+        const size_t grow = (size_t)(sg.row0 + row) * N;
+        if constexpr (SRC == SRC_SPLIT0) {
+            // first forward stage (pairs j, j + N/2) computed while loading: this CTA keeps
+            // X + w Y (half 0) or X - w Y (half 1), w = psi^brv(1)
+            const uint2 w = __ldg(&tw[1]);
+            const uint32_t q = lc.q;
+#pragma unroll
+            for (int k = 0; k < (1 << R); ++k) {
+                const size_t g = grow + jb + (k << logs);
+                const uint32_t X = __ldg(a.in + g), Y = __ldg(a.in + g + N / 2);
+                const uint32_t t = mul_shoup_lazy(Y, w.x, w.y, q);
+                x[k] = sg.half ? X - t + 2 * q : X + t;
+            }
+        } else if constexpr (logs == 0 && R >= 2) {
+            const uint4* src = reinterpret_cast<const uint4*>(a.in + grow + sg.gbase + jb);
+            const uint4* hs = reinterpret_cast<const uint4*>(a.had + grow + sg.gbase + jb);
+#pragma unroll
+            for (int k = 0; k < (1 << R); k += 4) {
+                uint4 v = valid ? __ldg(src + k / 4) : make_uint4(0, 0, 0, 0);
+                if constexpr (SRC == SRC_GLOBAL_HAD) {
+                    const uint4 h = valid ? __ldg(hs + k / 4) : make_uint4(0, 0, 0, 0);
+                    v.x = mul_mont_lazy(v.x, h.x, lc.q, lc.qinv_neg);
+                    v.y = mul_mont_lazy(v.y, h.y, lc.q, lc.qinv_neg);
+                    v.z = mul_mont_lazy(v.z, h.z, lc.q, lc.qinv_neg);
+                    v.w = mul_mont_lazy(v.w, h.w, lc.q, lc.qinv_neg);
+                }
+                x[k] = v.x;
+                x[k + 1] = v.y;
+                x[k + 2] = v.z;
+                x[k + 3] = v.w;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < (1 << R); ++k) {
+                const size_t g = grow + sg.gbase + jb + (k << logs);
+                uint32_t v = valid ? __ldg(a.in + g) : 0u;
+                if constexpr (SRC == SRC_GLOBAL_HAD) v = mul_mont_lazy(v, valid ? __ldg(a.had + g) : 0u, lc.q, lc.qinv_neg);
+                x[k] = v;
+            }
+        }
+    }
+}
+
+template <int R, int LOGN, int logs, int DST>
+__device__ __forceinline__ void store_elems(const uint32_t (&x)[1 << R], uint32_t* sm, const KArgs& a, const Seg& sg,
+                                            int row, int jb, uint32_t q) {
+    using C = Cfg<LOGN>;
+    constexpr int N = 1 << LOGN;
+    if constexpr (DST == DST_SMEM) {
+#pragma unroll
+        for (int k = 0; k < (1 << R); ++k) sm[pad(row * C::m + jb + (k << logs))] = x[k];
+    } else {
+        if (row >= sg.nrows) return;
+        uint32_t* dst = a.out + (size_t)(sg.row0 + row) * N + sg.gbase + jb;
+        if constexpr (logs == 0 && R >= 2) {
+#pragma unroll
+            for (int k = 0; k < (1 << R); k += 4) {
+                uint4 v = make_uint4(x[k], x[k + 1], x[k + 2], x[k + 3]);
+                if constexpr (DST == DST_GLOBAL_REDUCE) {
+                    v.x = reduce4(v.x, q);
+                    v.y = reduce4(v.y, q);
+                    v.z = reduce4(v.z, q);
+                    v.w = reduce4(v.w, q);
+                }
+                reinterpret_cast<uint4*>(dst)[k / 4] = v;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < (1 << R); ++k) dst[k << logs] = DST == DST_GLOBAL_REDUCE ? reduce4(x[k], q) : x[k];
+        }
+    }
+}
+
+// R forward (Cooley-Tukey) stages s0 .. s0+R-1 on registers; stage s pairs j, j + N/2^(s+1)
+// and uses twiddle psi^brv(2^s + G) for group G (one load per group, reused by its
+// butterflies).
 template <int R, int LOGN, int s0>
-__device__ __forceinline__ void fwd_pass(uint32_t* sm, uint32_t gbase, uint32_t row0, const KArgs& a) {
+__device__ __forceinline__ void fwd_stages(uint32_t (&x)[1 << R], uint32_t g0, const uint2* tw, uint32_t q) {
+    // the smallest-stride pass reads the group-major part of the table
+    constexpr bool PERM = (s0 + R == LOGN);
+    const uint32_t two_q = 2 * q;
+#pragma unroll
+    for (int v = 0; v < R; ++v) {
+        const int half = 1 << (R - 1 - v);
+        uint2 w = make_uint2(0, 0);
+#pragma unroll
+        for (int b = 0; b < (1 << (R - 1)); ++b) {
+            const int g = b >> (R - 1 - v);
+            const int k = (g << (R - v)) + (b & (half - 1));
+            if ((b & (half - 1)) == 0)
+                w = __ldg(&tw[PERM ? (1u << (s0 + v)) + ((uint32_t)g << s0) + g0 : (1u << (s0 + v)) + (g0 << v) + g]);
+            const uint32_t xa = umin(x[k], x[k] - two_q);
+            const uint32_t t = mul_shoup_lazy(x[k + half], w.x, w.y, q);
+            x[k] = xa + t;
+            x[k + half] = xa - t + two_q;
+        }
+    }
+}
+
+// R inverse (Gentleman-Sande) stages e0 .. e0+R-1 on registers; stage e pairs j, j + 2^e with
+// twiddle psi^-brv(N/2^(e+1) + G).  SCALE folds N^-1 (1) or N^-1 2^32 (2) into stage LOGN-1.
+template <int R, int LOGN, int SCALE, int e0>
+__device__ __forceinline__ void inv_stages(uint32_t (&x)[1 << R], uint32_t gbase, int j_hi, const uint2* tw,
+                                           const LimbConst& lc) {
+    constexpr int N = 1 << LOGN;
+    constexpr bool PERM = (e0 == 0);  // the smallest-stride pass reads the group-major table part
+    const uint32_t q = lc.q, two_q = 2 * q;
+    const uint32_t J = (gbase >> R) + (uint32_t)j_hi;  // global index of the sub-transform (e0 == 0)
+#pragma unroll
+    for (int v = 0; v < R; ++v) {
+        const int e = e0 + v;
+        const int h = 1 << v;
+        if (SCALE && e == LOGN - 1) {
+            const uint32_t s = SCALE == 1 ? lc.ninv : lc.ninvR, ssh = SCALE == 1 ? lc.ninv_sh : lc.ninvR_sh;
+            const uint32_t w = SCALE == 1 ? lc.ninvw : lc.ninvRw, wsh = SCALE == 1 ? lc.ninvw_sh : lc.ninvRw_sh;
+#pragma unroll
+            for (int kk = 0; kk < (1 << (R - 1)); ++kk) {
+                const uint32_t X = x[kk], Y = x[kk + h];
+                const uint32_t s0v = mul_shoup_lazy(X + Y, s, ssh, q), s1v = mul_shoup_lazy(X - Y + two_q, w, wsh, q);
+                x[kk] = umin(s0v, s0v - q);
+                x[kk + h] = umin(s1v, s1v - q);
+            }
+            continue;
+        }
+        const uint32_t hbase = (uint32_t)(N >> (e + 1)) + (gbase >> (e + 1)) + ((uint32_t)j_hi << (R - v - 1));
+        uint2 w = make_uint2(0, 0);
+#pragma unroll
+        for (int b = 0; b < (1 << (R - 1)); ++b) {
+            const int g = b >> v;
+            const int k = (g << (v + 1)) + (b & (h - 1));
+            if ((b & (h - 1)) == 0)
+                w = __ldg(&tw[PERM ? (uint32_t)(N >> (e + 1)) + ((uint32_t)g << (LOGN - R)) + J : hbase + g]);
+            const uint32_t X = x[k], Y = x[k + h];
+            const uint32_t sum = X + Y;
+            x[k] = umin(sum, sum - two_q);
+            x[k + h] = mul_shoup_lazy(X - Y + two_q, w.x, w.y, q);
+        }
+    }
+}
+
+// Forward register pass over stages s0 .. s0+R-1 of every sub-transform of the CTA.
+template <int R, int LOGN, int s0, int SRC, int DST>
+__device__ __forceinline__ void fwd_pass(uint32_t* sm, const Seg& sg, const KArgs& a) {
     using C = Cfg<LOGN>;
     constexpr int N = 1 << LOGN;
     constexpr int logtl = LOGN - s0 - R;  // log2 of the smallest stride of the pass
@@ -69,36 +230,21 @@ __device__ __forceinline__ void fwd_pass(uint32_t* sm, uint32_t gbase, uint32_t 
         const int uu = u & (nsub - 1);
         const int j_lo = uu & ((1 << logtl) - 1);
         const int j_hi = uu >> logtl;
-        const int jb = row * C::m + (j_hi << (logtl + R)) + j_lo;
-        const uint32_t g0 = (gbase >> (logtl + R)) + (uint32_t)j_hi;
-        const uint32_t limb = (row0 + row) % a.L;
-        const uint32_t q = a.lc[limb].q;
+        const int jb = (j_hi << (logtl + R)) + j_lo;
+        const uint32_t g0 = (sg.gbase >> (logtl + R)) + (uint32_t)j_hi;
+        const uint32_t limb = (sg.row0 + row) % a.L;
+        const LimbConst& lc = a.lc[limb];
         const uint2* tw = a.tw_f + (size_t)limb * N;
         uint32_t x[1 << R];
-#pragma unroll
-        for (int k = 0; k < (1 << R); ++k) x[k] = sm[pad(jb + (k << logtl))];
-        // constant trip counts at every loop level so that full unrolling keeps x[] in registers
-#pragma unroll
-        for (int v = 0; v < R; ++v) {
-#pragma unroll
-            for (int b = 0; b < (1 << (R - 1)); ++b) {
-                const int half = 1 << (R - 1 - v);
-                const int g = b >> (R - 1 - v);
-                const int k = (g << (R - v)) + (b & (half - 1));
-                const uint2 w = __ldg(&tw[(1u << (s0 + v)) + (g0 << v) + g]);
-                ct_bfly(x[k], x[k + half], w.x, w.y, q);
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < (1 << R); ++k) sm[pad(jb + (k << logtl))] = x[k];
+        load_elems<R, LOGN, logtl, SRC>(x, sm, a, sg, row, jb, lc, tw);
+        fwd_stages<R, LOGN, s0>(x, g0, tw, lc.q);
+        store_elems<R, LOGN, logtl, DST>(x, sm, a, sg, row, jb, lc.q);
     }
 }
 
-// Inverse pass over Gentleman-Sande stages e0 .. e0+R-1 (stage e pairs j, j + 2^e).
-// SCALE selects the N^-1 factor folded into the last stage of the whole transform
-// (0: none, 1: N^-1, 2: N^-1 * 2^32 after a Montgomery Hadamard product).
-template <int R, int LOGN, int SCALE, int e0>
-__device__ __forceinline__ void inv_pass(uint32_t* sm, uint32_t gbase, uint32_t row0, const KArgs& a) {
+// Inverse register pass over stages e0 .. e0+R-1.
+template <int R, int LOGN, int SCALE, int e0, int SRC, int DST>
+__device__ __forceinline__ void inv_pass(uint32_t* sm, const Seg& sg, const KArgs& a) {
     using C = Cfg<LOGN>;
     constexpr int N = 1 << LOGN;
     constexpr int lognsub = C::logm - R;
@@ -108,209 +254,168 @@ __device__ __forceinline__ void inv_pass(uint32_t* sm, uint32_t gbase, uint32_t 
         const int uu = u & (nsub - 1);
         const int j_lo = uu & ((1 << e0) - 1);
         const int j_hi = uu >> e0;
-        const int jb = row * C::m + (j_hi << (e0 + R)) + j_lo;
-        const uint32_t limb = (row0 + row) % a.L;
+        const int jb = (j_hi << (e0 + R)) + j_lo;
+        const uint32_t limb = (sg.row0 + row) % a.L;
         const LimbConst& lc = a.lc[limb];
-        const uint32_t q = lc.q;
         const uint2* tw = a.tw_i + (size_t)limb * N;
         uint32_t x[1 << R];
-#pragma unroll
-        for (int k = 0; k < (1 << R); ++k) x[k] = sm[pad(jb + (k << e0))];
-#pragma unroll
-        for (int v = 0; v < R; ++v) {
-            const int e = e0 + v;
-            const int h = 1 << v;
-            if (SCALE && e == LOGN - 1) {
-                // last stage of the transform: one group, twiddle psi^-brv(1), times N^-1
-                const uint32_t s = SCALE == 1 ? lc.ninv : lc.ninvR, ssh = SCALE == 1 ? lc.ninv_sh : lc.ninvR_sh;
-                const uint32_t w = SCALE == 1 ? lc.ninvw : lc.ninvRw, wsh = SCALE == 1 ? lc.ninvw_sh : lc.ninvRw_sh;
-#pragma unroll
-                for (int kk = 0; kk < (1 << (R - 1)); ++kk) {
-                    const uint32_t X = x[kk], Y = x[kk + h];
-                    x[kk] = csub(mul_shoup_lazy(X + Y, s, ssh, q), q);
-                    x[kk + h] = csub(mul_shoup_lazy(X - Y + 2 * q, w, wsh, q), q);
-                }
-                continue;
-            }
-            const uint32_t hbase = (uint32_t)(N >> (e + 1)) + (gbase >> (e + 1)) + ((uint32_t)j_hi << (R - v - 1));
-#pragma unroll
-            for (int b = 0; b < (1 << (R - 1)); ++b) {
-                const int g = b >> v;
-                const int k = (g << (v + 1)) + (b & (h - 1));
-                const uint2 w = __ldg(&tw[hbase + g]);
-                gs_bfly(x[k], x[k + h], w.x, w.y, q);
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < (1 << R); ++k) sm[pad(jb + (k << e0))] = x[k];
+        load_elems<R, LOGN, e0, SRC>(x, sm, a, sg, row, jb, lc, tw);
+        inv_stages<R, LOGN, SCALE, e0>(x, sg.gbase, j_hi, tw, lc);
+        store_elems<R, LOGN, e0, DST>(x, sm, a, sg, row, jb, lc.q);
     }
 }
 
+// The polynomial product's middle: the forward pass over the smallest strides, the Hadamard
+// product with `had` (Montgomery, 2^-32 folded into the final scale) and the inverse pass
+// over the same strides, on the same registers.
+template <int R, int LOGN, int s0, int SRC, int DST>
+__device__ __forceinline__ void fwd_had_inv_pass(uint32_t* sm, const Seg& sg, const KArgs& a) {
+    using C = Cfg<LOGN>;
+    constexpr int N = 1 << LOGN;
+    constexpr int lognsub = C::logm - R;
+    constexpr int nsub = 1 << lognsub;
+    static_assert(LOGN - s0 - R == 0, "the fused pass covers the smallest strides");
+    for (int u = threadIdx.x; u < C::rows * nsub; u += C::threads) {
+        const int row = u >> lognsub;
+        const int j_hi = u & (nsub - 1);
+        const int jb = j_hi << R;
+        const uint32_t g0 = (sg.gbase >> R) + (uint32_t)j_hi;
+        const uint32_t limb = (sg.row0 + row) % a.L;
+        const LimbConst& lc = a.lc[limb];
+        uint32_t x[1 << R];
+        load_elems<R, LOGN, 0, SRC>(x, sm, a, sg, row, jb, lc, a.tw_f + (size_t)limb * N);
+        fwd_stages<R, LOGN, s0>(x, g0, a.tw_f + (size_t)limb * N, lc.q);
+        const bool valid = row < sg.nrows;
+        const uint4* hs = reinterpret_cast<const uint4*>(a.had + (size_t)(sg.row0 + row) * N + sg.gbase + jb);
+#pragma unroll
+        for (int k = 0; k < (1 << R); k += 4) {
+            const uint4 h = valid ? __ldg(hs + k / 4) : make_uint4(0, 0, 0, 0);
+            x[k] = mul_mont_lazy(x[k], h.x, lc.q, lc.qinv_neg);
+            x[k + 1] = mul_mont_lazy(x[k + 1], h.y, lc.q, lc.qinv_neg);
+            x[k + 2] = mul_mont_lazy(x[k + 2], h.z, lc.q, lc.qinv_neg);
+            x[k + 3] = mul_mont_lazy(x[k + 3], h.w, lc.q, lc.qinv_neg);
+        }
+        inv_stages<R, LOGN, 2, 0>(x, sg.gbase, j_hi, a.tw_i + (size_t)limb * N, lc);
+        store_elems<R, LOGN, 0, DST>(x, sm, a, sg, row, jb, lc.q);
+    }
+}
+
+template <bool SPLIT>
+__device__ __forceinline__ void sync_all() {
+    if constexpr (SPLIT) cg::this_cluster().sync();
+    else __syncthreads();
+}
+
+// Forward passes I .. nrest-1 (big strides), SMEM -> SMEM except the first (from global).
 template <int LOGN, int I, int s>
-__device__ __forceinline__ void run_fwd_from(uint32_t* sm, uint32_t gbase, uint32_t row0, const KArgs& a) {
+__device__ __forceinline__ void fwd_big(uint32_t* sm, const Seg& sg, const KArgs& a) {
     using C = Cfg<LOGN>;
     if constexpr (I < C::nrest) {
         constexpr int r = C::big(I);
-        fwd_pass<r, LOGN, s>(sm, gbase, row0, a);
-        __syncthreads();
-        run_fwd_from<LOGN, I + 1, s + r>(sm, gbase, row0, a);
-    } else {
-        fwd_pass<C::r_small, LOGN, s>(sm, gbase, row0, a);
-        __syncthreads();
+        constexpr int SRC = I == 0 ? (C::split ? SRC_SPLIT0 : SRC_GLOBAL) : SRC_SMEM;
+        fwd_pass<r, LOGN, s, SRC, DST_SMEM>(sm, sg, a);
+        if constexpr (I == 0) sync_all<C::split>();  // every global read done before any write
+        else __syncthreads();
+        fwd_big<LOGN, I + 1, s + r>(sm, sg, a);
     }
 }
 
-template <int LOGN>
-__device__ __forceinline__ void run_fwd(uint32_t* sm, uint32_t gbase, uint32_t row0, const KArgs& a) {
-    run_fwd_from<LOGN, 0, Cfg<LOGN>::split ? 1 : 0>(sm, gbase, row0, a);
-}
-
+// Inverse passes over big strides, from I down to 0; the last one writes global memory
+// unless the transform is split (then the cross-CTA stage follows).
 template <int LOGN, int SCALE, int I, int e>
-__device__ __forceinline__ void run_inv_from(uint32_t* sm, uint32_t gbase, uint32_t row0, const KArgs& a) {
+__device__ __forceinline__ void inv_big(uint32_t* sm, const Seg& sg, const KArgs& a) {
     using C = Cfg<LOGN>;
     if constexpr (I >= 0) {
         constexpr int r = C::big(I);
-        inv_pass<r, LOGN, SCALE, e>(sm, gbase, row0, a);
-        __syncthreads();
-        run_inv_from<LOGN, SCALE, I - 1, e + r>(sm, gbase, row0, a);
+        if constexpr (I == 0 && !C::split) {
+            inv_pass<r, LOGN, SCALE, e, SRC_SMEM, DST_GLOBAL>(sm, sg, a);
+        } else {
+            inv_pass<r, LOGN, C::split ? 0 : SCALE, e, SRC_SMEM, DST_SMEM>(sm, sg, a);
+            __syncthreads();
+            inv_big<LOGN, SCALE, I - 1, e + r>(sm, sg, a);
+        }
     }
 }
 
+// Last stage of a split inverse: pairs (j, j + N/2) live in the two CTAs of the cluster.
 template <int LOGN, int SCALE>
-__device__ __forceinline__ void run_inv(uint32_t* sm, uint32_t gbase, uint32_t row0, const KArgs& a) {
+__device__ __forceinline__ void split_last_stage(uint32_t* sm, const Seg& sg, const KArgs& a) {
     using C = Cfg<LOGN>;
-    inv_pass<C::r_small, LOGN, SCALE, 0>(sm, gbase, row0, a);
-    __syncthreads();
-    run_inv_from<LOGN, SCALE, C::nrest - 1, C::r_small>(sm, gbase, row0, a);
+    constexpr int N = 1 << LOGN;
+    cg::cluster_group cluster = cg::this_cluster();
+    cluster.sync();
+    const uint32_t* s0 = cluster.map_shared_rank(sm, 0);
+    const uint32_t* s1 = cluster.map_shared_rank(sm, 1);
+    const LimbConst& lc = a.lc[sg.row0 % a.L];
+    const uint32_t q = lc.q;
+    const uint32_t s = SCALE == 1 ? lc.ninv : lc.ninvR, ssh = SCALE == 1 ? lc.ninv_sh : lc.ninvR_sh;
+    const uint32_t w = SCALE == 1 ? lc.ninvw : lc.ninvRw, wsh = SCALE == 1 ? lc.ninvw_sh : lc.ninvRw_sh;
+    uint32_t* out = a.out + (size_t)sg.row0 * N;
+    for (int i = threadIdx.x * 4; i < N / 4; i += C::threads * 4) {
+        const int j = sg.half * (N / 4) + i;
+        uint32_t r0[4], r1[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const uint32_t X = s0[pad(j + t)], Y = s1[pad(j + t)];
+            const uint32_t u0 = mul_shoup_lazy(X + Y, s, ssh, q), u1 = mul_shoup_lazy(X - Y + 2 * q, w, wsh, q);
+            r0[t] = umin(u0, u0 - q);
+            r1[t] = umin(u1, u1 - q);
+        }
+        *reinterpret_cast<uint4*>(out + j) = make_uint4(r0[0], r0[1], r0[2], r0[3]);
+        *reinterpret_cast<uint4*>(out + j + N / 2) = make_uint4(r1[0], r1[1], r1[2], r1[3]);
+    }
+    cluster.sync();  // keep this CTA's shared memory alive until the peer has read it
 }
 
 template <int LOGN, int MODE>
 __global__ void __launch_bounds__(Cfg<LOGN>::threads) ntt_cc_kernel(KArgs a) {
     using C = Cfg<LOGN>;
-    constexpr int N = 1 << LOGN;
     extern __shared__ __align__(16) uint32_t sm[];
-    uint32_t row0, half = 0;
-    if (C::split) {
-        row0 = blockIdx.x >> 1;
-        half = blockIdx.x & 1;
+    Seg sg;
+    if constexpr (C::split) {
+        sg.row0 = blockIdx.x >> 1;
+        sg.half = blockIdx.x & 1;
+        sg.nrows = 1;
     } else {
-        row0 = blockIdx.x * C::rows;
+        sg.row0 = blockIdx.x * C::rows;
+        sg.half = 0;
+        sg.nrows = (int)min((uint32_t)C::rows, a.rows - sg.row0);
     }
-    const uint32_t gbase = half * C::m;
-    const int nrows = C::split ? 1 : (int)min((uint32_t)C::rows, a.rows - row0);
+    sg.gbase = sg.half * C::m;
+    constexpr int RS = C::r_small;
+    constexpr int S_FIRST = C::split ? 1 : 0;     // first global stage run by the CTA
+    constexpr int S_SMALL = LOGN - RS;            // first stage of the smallest-stride pass
+    constexpr int SRC0 = C::split ? SRC_SPLIT0 : SRC_GLOBAL;
 
-    // ---- copy-in (coalesced, 4 consecutive words per thread)
-    for (int i = threadIdx.x * 4; i < C::elems; i += C::threads * 4) {
-        const int row = i >> C::logm;
-        const int j = i & (C::m - 1);
-        uint4 v = make_uint4(0, 0, 0, 0);
-        if (row < nrows) {
-            const size_t g = (size_t)(row0 + row) * N + gbase + j;
-            const uint32_t limb = (row0 + row) % a.L;
-            const LimbConst& lc = a.lc[limb];
-            if (C::split && (MODE == MODE_FWD || MODE == MODE_FWD_HAD_INV)) {
-                // first forward stage fused: X + w Y (half 0) or X - w Y (half 1), w = psi^brv(1)
-                const size_t g0 = (size_t)(row0 + row) * N + j;
-                const uint4 X = *reinterpret_cast<const uint4*>(a.in + g0);
-                const uint4 Y = *reinterpret_cast<const uint4*>(a.in + g0 + N / 2);
-                const uint2 w = __ldg(&a.tw_f[(size_t)limb * N + 1]);
-                const uint32_t q = lc.q;
-                uint32_t xs[4] = {X.x, X.y, X.z, X.w}, ys[4] = {Y.x, Y.y, Y.z, Y.w};
-#pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    const uint32_t tt = mul_shoup_lazy(ys[t], w.x, w.y, q);
-                    xs[t] = half ? xs[t] - tt + 2 * q : xs[t] + tt;
-                }
-                v = make_uint4(xs[0], xs[1], xs[2], xs[3]);
-            } else {
-                v = *reinterpret_cast<const uint4*>(a.in + g);
-                if (MODE == MODE_HAD_INV) {
-                    const uint4 h = *reinterpret_cast<const uint4*>(a.had + g);
-                    v.x = mul_mont_lazy(v.x, h.x, lc.q, lc.qinv_neg);
-                    v.y = mul_mont_lazy(v.y, h.y, lc.q, lc.qinv_neg);
-                    v.z = mul_mont_lazy(v.z, h.z, lc.q, lc.qinv_neg);
-                    v.w = mul_mont_lazy(v.w, h.w, lc.q, lc.qinv_neg);
-                }
-            }
+    if constexpr (MODE == MODE_FWD) {
+        if constexpr (C::nrest == 0) {
+            fwd_pass<RS, LOGN, S_FIRST, SRC0, DST_GLOBAL_REDUCE>(sm, sg, a);
+        } else {
+            fwd_big<LOGN, 0, S_FIRST>(sm, sg, a);
+            fwd_pass<RS, LOGN, S_SMALL, SRC_SMEM, DST_GLOBAL_REDUCE>(sm, sg, a);
         }
-        sm[pad(i)] = v.x;
-        sm[pad(i + 1)] = v.y;
-        sm[pad(i + 2)] = v.z;
-        sm[pad(i + 3)] = v.w;
-    }
-    if (C::split) {
-        cg::this_cluster().sync();  // both CTAs finished reading before anyone writes (in-place safety)
-    } else {
-        __syncthreads();
-    }
-
-    if (MODE == MODE_FWD || MODE == MODE_FWD_HAD_INV) run_fwd<LOGN>(sm, gbase, row0, a);
-
-    if (MODE == MODE_FWD_HAD_INV) {
-        for (int i = threadIdx.x; i < C::elems; i += C::threads) {
-            const int row = i >> C::logm;
-            if (row < nrows) {
-                const LimbConst& lc = a.lc[(row0 + row) % a.L];
-                const uint32_t h = a.had[(size_t)(row0 + row) * N + gbase + (i & (C::m - 1))];
-                sm[pad(i)] = mul_mont_lazy(sm[pad(i)], h, lc.q, lc.qinv_neg);
-            }
+    } else if constexpr (MODE == MODE_INV || MODE == MODE_HAD_INV) {
+        constexpr int SCALE = MODE == MODE_INV ? 1 : 2;
+        constexpr int SRC = MODE == MODE_INV ? SRC_GLOBAL : SRC_GLOBAL_HAD;
+        if constexpr (C::nrest == 0 && !C::split) {
+            inv_pass<RS, LOGN, SCALE, 0, SRC, DST_GLOBAL>(sm, sg, a);
+        } else {
+            inv_pass<RS, LOGN, C::split ? 0 : SCALE, 0, SRC, DST_SMEM>(sm, sg, a);
+            __syncthreads();
+            inv_big<LOGN, SCALE, C::nrest - 1, RS>(sm, sg, a);
+            if constexpr (C::split) split_last_stage<LOGN, SCALE>(sm, sg, a);
         }
-        __syncthreads();
-    }
-
-    if (MODE == MODE_FWD) {
-        for (int i = threadIdx.x * 4; i < C::elems; i += C::threads * 4) {
-            const int row = i >> C::logm;
-            if (row >= nrows) continue;
-            const uint32_t q = a.lc[(row0 + row) % a.L].q;
-            uint4 v;
-            v.x = reduce4(sm[pad(i)], q);
-            v.y = reduce4(sm[pad(i + 1)], q);
-            v.z = reduce4(sm[pad(i + 2)], q);
-            v.w = reduce4(sm[pad(i + 3)], q);
-            *reinterpret_cast<uint4*>(a.out + (size_t)(row0 + row) * N + gbase + (i & (C::m - 1))) = v;
-        }
-        return;
-    }
-
-    constexpr int SCALE = (MODE == MODE_INV) ? 1 : 2;
-    if (!C::split) {
-        run_inv<LOGN, SCALE>(sm, gbase, row0, a);
-        for (int i = threadIdx.x * 4; i < C::elems; i += C::threads * 4) {
-            const int row = i >> C::logm;
-            if (row >= nrows) continue;
-            const uint4 v = make_uint4(sm[pad(i)], sm[pad(i + 1)], sm[pad(i + 2)], sm[pad(i + 3)]);
-            *reinterpret_cast<uint4*>(a.out + (size_t)(row0 + row) * N + gbase + (i & (C::m - 1))) = v;
-        }
-        return;
-    }
-
-    // split inverse: stages with stride < N/2 are local; the last one pairs the two halves
-    run_inv<LOGN, 0>(sm, gbase, row0, a);
-    cg::cluster_group cluster = cg::this_cluster();
-    cluster.sync();
-    {
-        const uint32_t* s0 = cluster.map_shared_rank(sm, 0);
-        const uint32_t* s1 = cluster.map_shared_rank(sm, 1);
-        const LimbConst& lc = a.lc[row0 % a.L];
-        const uint32_t q = lc.q;
-        const uint32_t s = SCALE == 1 ? lc.ninv : lc.ninvR, ssh = SCALE == 1 ? lc.ninv_sh : lc.ninvR_sh;
-        const uint32_t w = SCALE == 1 ? lc.ninvw : lc.ninvRw, wsh = SCALE == 1 ? lc.ninvw_sh : lc.ninvRw_sh;
-        uint32_t* out = a.out + (size_t)row0 * N;
-        for (int i = threadIdx.x * 4; i < N / 4; i += C::threads * 4) {
-            const int j = half * (N / 4) + i;
-            uint32_t r0[4], r1[4];
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const uint32_t X = s0[pad(j + t)], Y = s1[pad(j + t)];
-                r0[t] = csub(mul_shoup_lazy(X + Y, s, ssh, q), q);
-                r1[t] = csub(mul_shoup_lazy(X - Y + 2 * q, w, wsh, q), q);
-            }
-            *reinterpret_cast<uint4*>(out + j) = make_uint4(r0[0], r0[1], r0[2], r0[3]);
-            *reinterpret_cast<uint4*>(out + j + N / 2) = make_uint4(r1[0], r1[1], r1[2], r1[3]);
+    } else {  // MODE_FWD_HAD_INV
+        if constexpr (C::nrest == 0 && !C::split) {
+            fwd_had_inv_pass<RS, LOGN, S_SMALL, SRC0, DST_GLOBAL>(sm, sg, a);
+        } else {
+            fwd_big<LOGN, 0, S_FIRST>(sm, sg, a);
+            fwd_had_inv_pass<RS, LOGN, S_SMALL, SRC_SMEM, DST_SMEM>(sm, sg, a);
+            __syncthreads();
+            inv_big<LOGN, 2, C::nrest - 1, RS>(sm, sg, a);
+            if constexpr (C::split) split_last_stage<LOGN, 2>(sm, sg, a);
         }
     }
-    cluster.sync();  // keep this CTA's shared memory alive until the peer has read it
 }
 
 template <int LOGN, int MODE>
@@ -321,10 +426,6 @@ cudaError_t launch_one(const KArgs& a, size_t rows, cudaStream_t stream) {
     if (!attr_done) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::smem_bytes);
         if (e != cudaSuccess) return e;
-        if (C::split) {
-            e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 0);
-            (void)e;
-        }
         attr_done = true;
     }
     cudaLaunchConfig_t cfg = {};
