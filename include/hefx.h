@@ -135,6 +135,15 @@ void hefx_bconv_plan_destroy(hefx_bconv_plan* plan);
 hefx_status hefx_basis_convert(hefx_ctx* ctx, const hefx_bconv_plan* plan, const uint32_t* d_in, uint32_t* d_out,
                                size_t batch, hefx_path path, void* stream);
 
+/*
+ * Waits for `stream`, then reports whether a bounded device-side wait of the tensor-path
+ * kernels launched with `params` expired since the last check (HEFX_ETIMEOUT; the results of
+ * those calls are invalid) and clears that record.  The tcgen05 pipelines wait on mbarriers
+ * with a time limit instead of spinning forever, so a failure ends the kernel with a
+ * recorded code rather than a hung device.  Errors: EINVAL, ECUDA, ETIMEOUT.
+ */
+hefx_status hefx_stream_check(hefx_ctx* ctx, const hefx_params* params, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

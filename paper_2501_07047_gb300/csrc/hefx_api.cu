@@ -247,9 +247,13 @@ hefx_status hefx_poly_mul(hefx_ctx* ctx, const hefx_params* p, const uint32_t* a
     if (batch == 0) return HEFX_OK;
     cudaStream_t s = (cudaStream_t)stream;
     const size_t rows = batch * p->nlimbs;
+    if (pth == HEFX_PATH_TENSOR) {
+        cudaError_t e = launch_polymul_tc(const_cast<hefx_params*>(p), a, b, c, batch, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "hefx_poly_mul (tensor path)");
+        return HEFX_OK;
+    }
     auto launch = [&](NttMode m, const uint32_t* in, const uint32_t* had, uint32_t* out) {
-        return pth == HEFX_PATH_TENSOR ? launch_ntt_tc(p, m, in, had, out, batch, s)
-                                       : launch_ntt_cc(p, m, in, had, out, rows, s);
+        return launch_ntt_cc(p, m, in, had, out, rows, s);
     };
     cudaError_t e;
     if (a == b) {
@@ -332,7 +336,20 @@ hefx_status hefx_basis_convert(hefx_ctx* ctx, const hefx_bconv_plan* plan, const
     return HEFX_OK;
 }
 
-/* Tuner hook (not in the public header): records the path AUTO resolves to. */
+hefx_status hefx_stream_check(hefx_ctx* ctx, const hefx_params* p, void* stream) {
+    if (!ctx) return HEFX_EINVAL;
+    if (!p || p->ctx != ctx) return fail(ctx, HEFX_EINVAL, "params is null or belongs to another context");
+    hefx_status st = use_device(ctx);
+    if (st != HEFX_OK) return st;
+    uint32_t code = 0;
+    cudaError_t e = tc_check(p, (cudaStream_t)stream, &code);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "hefx_stream_check");
+    if (code) return fail(ctx, HEFX_ETIMEOUT, "a bounded device wait expired (code %u); results are invalid", code);
+    return HEFX_OK;
+}
+
+/* Tuner hook: records the path AUTO resolves to. */
 hefx_status hefx_params_set_auto_path(hefx_params* p, hefx_path path) {
     if (!p || (path != HEFX_PATH_CUDACORE && path != HEFX_PATH_TENSOR && path != HEFX_PATH_AUTO)) return HEFX_EINVAL;
     p->tuned_path = path;

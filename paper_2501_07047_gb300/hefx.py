@@ -36,6 +36,7 @@ SIGNATURES = {
     "hefx_bconv_plan_create": (_i32, [_vp, _u32, _u32p, _u32, _u32p, _u32, ctypes.POINTER(_vp)]),
     "hefx_bconv_plan_destroy": (None, [_vp]),
     "hefx_basis_convert": (_i32, [_vp, _vp, _vp, _vp, _sz, _i32, _vp]),
+    "hefx_stream_check": (_i32, [_vp, _vp, _vp]),
 }
 
 _lib = None
@@ -155,6 +156,10 @@ def hefx_bconv_plan_destroy(plan: int) -> None:
 
 def hefx_basis_convert(ctx, plan, d_in, d_out, batch, path="auto", stream=None) -> None:
     _check(ctx, load().hefx_basis_convert(ctx, plan, _ptr(d_in), _ptr(d_out), batch, _path(path), _stream(stream)))
+
+
+def hefx_stream_check(ctx, params, stream=None) -> None:
+    _check(ctx, load().hefx_stream_check(ctx, params, _stream(stream)))
 
 
 def raw_status(fn_name: str, *args) -> int:

@@ -31,12 +31,14 @@ def make_params(ctx, logn, primes):
 def run_fwd(ctx, params, arr, path):
     d = to_dev(arr)
     hefx.hefx_ntt_fwd(ctx, params, d, arr.shape[0], path)
+    hefx.hefx_stream_check(ctx, params)
     return to_host(d).reshape(arr.shape)
 
 
 def run_inv(ctx, params, arr, path):
     d = to_dev(arr)
     hefx.hefx_ntt_inv(ctx, params, d, arr.shape[0], path)
+    hefx.hefx_stream_check(ctx, params)
     return to_host(d).reshape(arr.shape)
 
 
@@ -147,6 +149,7 @@ def test_config2_full_size_sampled(ctx, path):
         data = inputs.residue_tensor(inputs.derive_seed(2, 0), 8, primes, n)
         d = to_dev(data)
         hefx.hefx_ntt_fwd(ctx, p, d, 8, path)
+        hefx.hefx_stream_check(ctx, p)
         got = to_host(d).reshape(data.shape)
         for (b, l) in [(0, 0), (3, 11), (7, 23)]:
             assert (got[b, l] == oracle.ntt(data[b, l], primes[l])).all()
@@ -180,6 +183,7 @@ def test_poly_mul_matches_oracle(ctx, path, logn, L, batch):
                 assert (expect[0, l] == oracle.polymul_schoolbook(a[0, l], b[0, l], q)).all()
         da, db, dc = to_dev(a), to_dev(b), empty_dev(a.shape)
         hefx.hefx_poly_mul(ctx, p, da, db, dc, batch, path)
+        hefx.hefx_stream_check(ctx, p)
         assert (to_host(dc).reshape(a.shape) == expect).all()
         # aliasing: c = a, c = b, a = b (square), a = b = c
         hefx.hefx_poly_mul(ctx, p, da, db, da, batch, path)
