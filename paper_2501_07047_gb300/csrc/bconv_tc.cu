@@ -1,11 +1,299 @@
-// Tensor-core basis conversion -- under construction.
+// Tensor-core basis conversion (path c): App. B's BConv with its step-2 MatModMul turned
+// into a BAT digit-split matrix product (Sec. IV-A3, "High-Precision MatModMul in BConv").
+//
+//   D[n][(j, o)] = sum_{(i, d)} digit_d(b_{n,i}) * chunk_o([qhat_i]_{p_j} 2^32 2^(7d) mod p_j)
+//   out_{n,j}    = REDC_{p_j}( sum_o D[n][(j, o)] 2^(6o) )
+//
+// b_{n,i} = [a_{n,i} qhat_i^-1]_{q_i} is step 1 (a Shoup product in the prologue); digits are
+// 7 bits (b < q_i < 2^28), chunks 6 bits (constants < p_j < 2^30), and every partial sum is
+// below 4 * 64 * 127 * 63 < 2^23, so fp16 operands with fp32 accumulation are exact.
+//
+// GB300 mapping: a persistent kernel streams 128-coefficient tiles.  Four producer warps
+// read the L source residues of a tile (coalesced), apply step 1 and write the digits into a
+// double-buffered K-major 128B-swizzled A tile; one thread issues the tcgen05 MMAs against
+// the constant B operand (resident in shared memory for the whole kernel) into one of two
+// TMEM accumulators; four epilogue warps merge, reduce mod p_j and store while the next tile
+// is being produced.  The operation is HBM-bound (16 B per source residue in, 4 per
+// target residue out per coefficient), so the tensor pipe is mostly idle by design.
+#include <cstring>
+#include <vector>
+
 #include "bconv_common.h"
+#include "host_nt.h"
+#include "modarith.cuh"
+#include "tc_common.cuh"
 
 namespace hefx {
-cudaError_t bconv_tc_upload(hefx_bconv_plan*, const BConvConst&) { return cudaSuccess; }
-void bconv_tc_free(hefx_bconv_plan*) {}
-bool bconv_tc_available(const hefx_bconv_plan*) { return false; }
-cudaError_t launch_bconv_tc(const hefx_bconv_plan*, const uint32_t*, uint32_t*, size_t, cudaStream_t) {
-    return cudaErrorNotSupported;
+
+namespace {
+
+constexpr int KO = 5;
+constexpr int THREADS = 384;  // warps 0-3 producer, 4-7 epilogue, 8 MMA
+constexpr int MAX_L = 64, MAX_LP = 32;
+
+struct BcTcConst {
+    uint32_t L, Lp, kpad, npad;      // K = 4L padded to 64, N = 8 columns per target limb, padded to 16
+    uint32_t q[MAX_L], qhat_inv[MAX_L], qhat_inv_sh[MAX_L];
+    uint32_t p[MAX_LP], pinv_neg[MAX_LP];
+};
+
+struct BcTcPlan {
+    BcTcConst* d_const = nullptr;
+    uint8_t* d_bimage = nullptr;  // constant B operand, already in the swizzled smem layout
+    uint32_t bimage_bytes = 0;
+    uint32_t kpad = 0, npad = 0, tmem_cols = 0;
+    uint32_t* d_err = nullptr;
+};
+
+uint16_t half_bits_small(uint32_t d) {
+    if (d == 0) return 0;
+    int e = 31 - __builtin_clz(d);
+    return (uint16_t)(((e + 15) << 10) | ((d << (10 - e)) & 0x3FFu));
 }
+
+uint32_t sw128_offset_host(uint32_t row, uint32_t k) {
+    const uint32_t chunk = (k >> 3) & 7u;
+    return row * 128u + ((chunk ^ (row & 7u)) << 4) + ((k & 7u) << 1);
+}
+
+size_t smem_bytes(const BcTcPlan& tp) {
+    return 1024 + 2ull * 128 * tp.kpad * 2 + tp.bimage_bytes + 256;
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+    bconv_tc_kernel(const BcTcConst* __restrict__ gc, const uint8_t* __restrict__ bimage, uint32_t bimage_bytes,
+                    const uint32_t* __restrict__ in, uint32_t* __restrict__ out, uint32_t n, uint32_t batch,
+                    uint32_t tmem_cols, uint32_t* err) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    __shared__ BcTcConst c;
+    const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (uint32_t i = tid; i < sizeof(BcTcConst) / 4; i += THREADS)
+        reinterpret_cast<uint32_t*>(&c)[i] = reinterpret_cast<const uint32_t*>(gc)[i];
+    const uint32_t kpad0 = gc->kpad;
+    const uint32_t abytes = 128 * kpad0 * 2;  // one A tile: 128 rows x K fp16
+    uint8_t* a_s[2] = {smem, smem + abytes};
+    uint8_t* b_s = smem + 2 * abytes;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(b_s + bimage_bytes);
+    uint64_t* a_full = bars;       // [2] producer -> MMA
+    uint64_t* a_empty = bars + 2;  // [2] MMA -> producer
+    uint64_t* acc_full = bars + 4; // [2] MMA -> epilogue
+    uint64_t* acc_empty = bars + 6;// [2] epilogue -> MMA
+    uint64_t* mma_done = bars + 8;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 9);
+
+    // constant B operand and zeroed A tiles (K padding stays zero for the whole kernel)
+    for (uint32_t i = tid; i < bimage_bytes / 16; i += THREADS)
+        reinterpret_cast<uint4*>(b_s)[i] = reinterpret_cast<const uint4*>(bimage)[i];
+    for (uint32_t i = tid; i < 2 * abytes / 16; i += THREADS) reinterpret_cast<uint4*>(smem)[i] = make_uint4(0, 0, 0, 0);
+    if (tid == 0) {
+        for (int s = 0; s < 2; ++s) {
+            tc::mbar_init(&a_full[s], 128);
+            tc::mbar_init(&a_empty[s], 1);
+            tc::mbar_init(&acc_full[s], 1);
+            tc::mbar_init(&acc_empty[s], 128);
+        }
+        tc::mbar_init(mma_done, 1);
+        tc::fence_mbar_init();
+    }
+    if (warp == 8) tc::tmem_alloc(tmem_slot, tmem_cols);
+    tc::fence_proxy_async_smem();
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t L = c.L, Lp = c.Lp, kpad = c.kpad, npad = c.npad;
+    const uint32_t tiles_per_poly = n / 128;
+    const uint32_t ntiles = tiles_per_poly * batch;
+
+    if (warp < 4) {  // ---- producer: step 1 and digit split
+        uint32_t it = 0;
+        for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+            const uint32_t s = it & 1, ph = (it >> 1) & 1;
+            if (!tc::mbar_wait(&a_empty[s], ph ^ 1u, err, tc::ERR_TIMEOUT_EMPTY)) break;
+            const uint32_t b = t / tiles_per_poly, x = (t % tiles_per_poly) * 128 + tid;
+            const uint32_t* src = in + (size_t)b * L * n + x;
+            uint8_t* A = a_s[s];
+            for (uint32_t i0 = 0; i0 < L; i0 += 8) {
+                uint32_t v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[u] = (i0 + u < L) ? __ldg(src + (size_t)(i0 + u) * n) : 0u;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const uint32_t i = i0 + u;
+                    if (i >= L) break;
+                    const uint32_t qi = c.q[i];
+                    const uint32_t bi = csub(mul_shoup_lazy(v[u], c.qhat_inv[i], c.qhat_inv_sh[i], qi), qi);
+                    const uint2 d = tc::split_digits4(bi);
+                    const uint32_t k = 4 * i;
+                    *reinterpret_cast<uint2*>(A + (k >> 6) * (128 * 128) + tc::sw128_offset(tid, k & 63)) = d;
+                }
+            }
+            tc::fence_proxy_async_smem();
+            tc::mbar_arrive(&a_full[s]);
+        }
+    } else if (warp < 8) {  // ---- epilogue: merge, reduce mod p_j, store
+        const uint32_t lq = (warp - 4) * 32;
+        uint32_t it = 0;
+        for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+            const uint32_t s = it & 1, ph = (it >> 1) & 1;
+            if (!tc::mbar_wait(&acc_full[s], ph, err, tc::ERR_TIMEOUT_ACC)) break;
+            tc::tc_fence_after();
+            const uint32_t b = t / tiles_per_poly, x = (t % tiles_per_poly) * 128 + lq + lane;
+            uint32_t* dst = out + (size_t)b * Lp * n + x;
+            // columns: output j's five chunk sums sit at 8j .. 8j+4, two outputs per 16 columns
+            for (uint32_t cb = 0; cb < npad; cb += 16) {
+                uint32_t r[16];
+                tc::tmem_ld16(tmem + (lq << 16) + s * npad + cb, r);
+                tc::tmem_ld_wait();
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const uint32_t j = cb / 8 + h;
+                    if (j < Lp) {
+                        const uint64_t z = (uint64_t)tc::acc_to_u32(r[8 * h]) +
+                                           ((uint64_t)tc::acc_to_u32(r[8 * h + 1]) << 6) +
+                                           ((uint64_t)tc::acc_to_u32(r[8 * h + 2]) << 12) +
+                                           ((uint64_t)tc::acc_to_u32(r[8 * h + 3]) << 18) +
+                                           ((uint64_t)tc::acc_to_u32(r[8 * h + 4]) << 24);
+                        const uint32_t pj = c.p[j];
+                        const uint32_t zl = (uint32_t)z, zh = (uint32_t)(z >> 32);
+                        const uint32_t rr = zh + __umulhi(zl * c.pinv_neg[j], pj) + (zl != 0u);
+                        dst[(size_t)j * n] = csub(rr, pj);
+                    }
+                }
+            }
+            tc::tc_fence_before();
+            tc::mbar_arrive(&acc_empty[s]);
+        }
+    } else if (warp == 8 && lane == 0) {  // ---- MMA issuer
+        const uint32_t idesc = tc::idesc_f16_f32(128, npad);
+        const uint32_t ksteps = (4 * L + 15) / 16;
+        uint32_t it = 0;
+        for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+            const uint32_t s = it & 1, ph = (it >> 1) & 1;
+            if (!tc::mbar_wait(&a_full[s], ph, err, tc::ERR_TIMEOUT_FULL)) break;
+            if (!tc::mbar_wait(&acc_empty[s], ph ^ 1u, err, tc::ERR_TIMEOUT_ACC)) break;
+            tc::tc_fence_after();
+            for (uint32_t ks = 0; ks < ksteps; ++ks) {
+                const uint32_t kc = ks >> 2, kin = ks & 3;
+                const uint32_t ab = tc::smem_u32(a_s[s] + kc * (128 * 128)) + kin * 32;
+                const uint32_t bb = tc::smem_u32(b_s + kc * (npad * 128)) + kin * 32;
+                tc::mma_f16(tmem + s * npad, tc::sw128_desc(ab), tc::sw128_desc(bb), idesc, ks != 0);
+            }
+            tc::mma_commit(&acc_full[s]);
+            tc::mma_commit(&a_empty[s]);
+        }
+        tc::mma_commit(mma_done);
+        tc::mbar_wait(mma_done, 0, err, tc::ERR_TIMEOUT_ACC);
+    }
+    (void)kpad;
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 8) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem, tmem_cols);
+    }
+}
+
+}  // namespace
+
+bool bconv_tc_available(const hefx_bconv_plan* plan) {
+    return plan->d_bat != nullptr && plan->log2n >= 7;
+}
+
+// Offline compile of the step-2 constant (OfflineCompileLeft of Alg. 2 for the right-hand
+// constant matrix): row (j, o), column (i, d) holds chunk_o([qhat_i]_{p_j} 2^32 2^(7d) mod p_j),
+// laid out exactly as the kernel's shared-memory B tile (K-major, 128B swizzle).
+cudaError_t bconv_tc_upload(hefx_bconv_plan* plan, const BConvConst& h) {
+    const uint32_t L = plan->L, Lp = plan->Lp;
+    for (uint32_t i = 0; i < L; ++i)
+        if (plan->src[i] >= (1u << 28)) return cudaSuccess;  // digits need 28-bit sources
+    if (L > (uint32_t)MAX_L || Lp > (uint32_t)MAX_LP) return cudaSuccess;  // CUDA-core path only
+    BcTcPlan* tp = new BcTcPlan();
+    tp->kpad = ((4 * L + 63) / 64) * 64;
+    tp->npad = ((8 * Lp + 15) / 16) * 16;
+    uint32_t cols = 32;
+    while (cols < 2 * tp->npad) cols *= 2;
+    tp->tmem_cols = cols;
+    tp->bimage_bytes = tp->npad * tp->kpad * 2;
+    std::vector<uint8_t> img(tp->bimage_bytes, 0);
+    for (uint32_t j = 0; j < Lp; ++j) {
+        const uint64_t p = plan->dst[j];
+        const uint64_t r32 = ((uint64_t)1 << 32) % p;
+        for (uint32_t i = 0; i < L; ++i) {
+            uint64_t cst = mul_mod(h.qhat_p[i * kBConvMaxLimbs + j], r32, p);
+            for (uint32_t d = 0; d < 4; ++d) {
+                const uint32_t k = 4 * i + d;
+                for (int o = 0; o < KO; ++o) {
+                    const uint32_t row = 8 * j + o;
+                    const uint16_t hb = half_bits_small((uint32_t)((cst >> (6 * o)) & 63u));
+                    const size_t off = (size_t)(k / 64) * (tp->npad * 128) + sw128_offset_host(row, k % 64);
+                    memcpy(&img[off], &hb, 2);
+                }
+                cst = (cst << 7) % p;
+            }
+        }
+    }
+    BcTcConst hc;
+    memset(&hc, 0, sizeof hc);
+    hc.L = L;
+    hc.Lp = Lp;
+    hc.kpad = tp->kpad;
+    hc.npad = tp->npad;
+    for (uint32_t i = 0; i < L; ++i) {
+        hc.q[i] = h.q[i];
+        hc.qhat_inv[i] = h.qhat_inv[i];
+        hc.qhat_inv_sh[i] = h.qhat_inv_sh[i];
+    }
+    for (uint32_t j = 0; j < Lp; ++j) {
+        hc.p[j] = h.p[j];
+        hc.pinv_neg[j] = neg_inv_pow2_32(h.p[j]);
+    }
+    cudaError_t e = cudaMalloc(&tp->d_const, sizeof hc);
+    if (e == cudaSuccess) e = cudaMemcpy(tp->d_const, &hc, sizeof hc, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&tp->d_bimage, img.size());
+    if (e == cudaSuccess) e = cudaMemcpy(tp->d_bimage, img.data(), img.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&tp->d_err, 4);
+    if (e == cudaSuccess) e = cudaMemset(tp->d_err, 0, 4);
+    plan->d_bat = tp;
+    if (e != cudaSuccess) {
+        bconv_tc_free(plan);
+        return e;
+    }
+    return cudaSuccess;
+}
+
+void bconv_tc_free(hefx_bconv_plan* plan) {
+    BcTcPlan* tp = static_cast<BcTcPlan*>(plan->d_bat);
+    if (!tp) return;
+    if (tp->d_const) cudaFree(tp->d_const);
+    if (tp->d_bimage) cudaFree(tp->d_bimage);
+    if (tp->d_err) cudaFree(tp->d_err);
+    delete tp;
+    plan->d_bat = nullptr;
+}
+
+cudaError_t launch_bconv_tc(const hefx_bconv_plan* plan, const uint32_t* in, uint32_t* out, size_t batch,
+                            cudaStream_t stream) {
+    const BcTcPlan* tp = static_cast<const BcTcPlan*>(plan->d_bat);
+    if (!tp || plan->log2n < 7) return cudaErrorNotSupported;
+    const uint32_t n = 1u << plan->log2n;
+    const size_t ntiles = (size_t)(n / 128) * batch;
+    if (ntiles == 0) return cudaSuccess;
+    const size_t smem = smem_bytes(*tp);
+    static size_t attr = 0;
+    if (attr < smem) {
+        cudaError_t e = cudaFuncSetAttribute(bconv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = smem;
+    }
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned grid = (unsigned)std::min<size_t>(ntiles, 2 * (size_t)sms);  // two CTAs fit per SM
+    bconv_tc_kernel<<<grid, THREADS, smem, stream>>>(tp->d_const, tp->d_bimage, tp->bimage_bytes, in, out, n,
+                                                      (uint32_t)batch, tp->tmem_cols, tp->d_err);
+    return cudaGetLastError();
+}
+
 }  // namespace hefx

@@ -62,7 +62,7 @@ struct TensorTables {
 namespace {
 
 constexpr int NT = 64;              // data rows per CTA tile (MMA N)
-constexpr int STAGES = 4;           // constant pipeline depth
+constexpr int STAGES = 6;           // constant pipeline depth
 constexpr int KO = 5;               // 6-bit constant chunks = TMEM accumulators
 constexpr uint32_t TMEM_COLS = 512;
 constexpr int THREADS = 256;
@@ -129,26 +129,50 @@ __global__ void __launch_bounds__(THREADS, 1) bat_ntt_gemm(const __grid_constant
     if (warp == 2) tc::tmem_alloc(tmem_slot, TMEM_COLS);
     if (threadIdx.x == 32) tc::prefetch_tmap(&cmap);
 
-    // ---- prologue: 7-bit digits of the data tile, K-major, 128B-swizzled
+    // ---- prologue: 7-bit digits of the data tile, K-major, 128B-swizzled.  Loads are
+    // issued in groups of UNR before any digit is written, to keep several in flight.
+    constexpr int UNR = 8;
     if constexpr (!TRANS) {
         const uint32_t pairs = a.cols / 2;
-        for (uint32_t t = threadIdx.x; t < NT * pairs; t += THREADS) {
-            const uint32_t rr = t / pairs, c = (t % pairs) * 2;
-            const uint2 v = __ldg(reinterpret_cast<const uint2*>(a.in + base + (size_t)(n0 + rr) * a.cols + c));
-            const uint2 d0 = tc::split_digits4(v.x), d1 = tc::split_digits4(v.y);
-            const uint32_t k = c * 4;
-            uint8_t* dst = data_s + (k >> 6) * (NT * 128) + tc::sw128_offset(rr, k & 63);
-            *reinterpret_cast<uint4*>(dst) = make_uint4(d0.x, d0.y, d1.x, d1.y);
+        const uint32_t total = NT * pairs;  // multiple of THREADS * UNR for cols >= 128
+        for (uint32_t t0 = threadIdx.x; t0 < total; t0 += THREADS * UNR) {
+            uint2 v[UNR];
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) {
+                const uint32_t t = t0 + u * THREADS;
+                const uint32_t rr = t / pairs, c = (t % pairs) * 2;
+                v[u] = __ldg(reinterpret_cast<const uint2*>(a.in + base + (size_t)(n0 + rr) * a.cols + c));
+            }
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) {
+                const uint32_t t = t0 + u * THREADS;
+                const uint32_t rr = t / pairs, c = (t % pairs) * 2;
+                const uint2 d0 = tc::split_digits4(v[u].x), d1 = tc::split_digits4(v[u].y);
+                const uint32_t k = c * 4;
+                uint8_t* dst = data_s + (k >> 6) * (NT * 128) + tc::sw128_offset(rr, k & 63);
+                *reinterpret_cast<uint4*>(dst) = make_uint4(d0.x, d0.y, d1.x, d1.y);
+            }
         }
     } else {
-        for (uint32_t t = threadIdx.x; t < NT * (a.rows / 2); t += THREADS) {
-            const uint32_t cc = t % NT, r = (t / NT) * 2;
-            const uint32_t x0 = __ldg(a.in + base + (size_t)r * a.cols + n0 + cc);
-            const uint32_t x1 = __ldg(a.in + base + (size_t)(r + 1) * a.cols + n0 + cc);
-            const uint2 d0 = tc::split_digits4(x0), d1 = tc::split_digits4(x1);
-            const uint32_t k = r * 4;
-            uint8_t* dst = data_s + (k >> 6) * (NT * 128) + tc::sw128_offset(cc, k & 63);
-            *reinterpret_cast<uint4*>(dst) = make_uint4(d0.x, d0.y, d1.x, d1.y);
+        const uint32_t total = NT * (a.rows / 2);
+        for (uint32_t t0 = threadIdx.x; t0 < total; t0 += THREADS * UNR) {
+            uint32_t x0[UNR], x1[UNR];
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) {
+                const uint32_t t = t0 + u * THREADS;
+                const uint32_t cc = t % NT, r = (t / NT) * 2;
+                x0[u] = __ldg(a.in + base + (size_t)r * a.cols + n0 + cc);
+                x1[u] = __ldg(a.in + base + (size_t)(r + 1) * a.cols + n0 + cc);
+            }
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) {
+                const uint32_t t = t0 + u * THREADS;
+                const uint32_t cc = t % NT, r = (t / NT) * 2;
+                const uint2 d0 = tc::split_digits4(x0[u]), d1 = tc::split_digits4(x1[u]);
+                const uint32_t k = r * 4;
+                uint8_t* dst = data_s + (k >> 6) * (NT * 128) + tc::sw128_offset(cc, k & 63);
+                *reinterpret_cast<uint4*>(dst) = make_uint4(d0.x, d0.y, d1.x, d1.y);
+            }
         }
     }
     tc::fence_proxy_async_smem();
