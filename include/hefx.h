@@ -136,6 +136,44 @@ hefx_status hefx_basis_convert(hefx_ctx* ctx, const hefx_bconv_plan* plan, const
                                size_t batch, hefx_path path, void* stream);
 
 /*
+ * Batched polynomial products of uneven shape (the batching pattern of the build; the
+ * paper's batching study is Sec. V-B3, "TPUs favor large batch").  Each job multiplies two
+ * polynomials of ring degree N = 2^params->log2n over the first `nlimbs` primes of
+ * `params` (limb i uses prime i), data laid out [nlimbs][N] in natural coefficient order.
+ * d_c may alias d_a and/or d_b; distinct jobs must not overlap.
+ */
+typedef struct {
+    const hefx_params* params;
+    uint32_t nlimbs;
+    const uint32_t* d_a;
+    const uint32_t* d_b;
+    uint32_t* d_c;
+} hefx_job;
+
+typedef struct hefx_batch_plan hefx_batch_plan;
+
+/*
+ * Builds the device work lists of a batch once: jobs are grouped by parameter set (one size
+ * class per ring degree) and every limb of every job becomes one row descriptor.  The
+ * buffers named by the jobs must stay valid for the plan's lifetime.  path: AUTO or
+ * CUDACORE (the persistent row-list kernels); TENSOR gives EUNSUPPORTED.
+ * Errors: EINVAL (null/misaligned pointer, nlimbs out of range, params of another context),
+ * EUNSUPPORTED, ENOMEM.
+ */
+hefx_status hefx_batch_plan_create(hefx_ctx* ctx, const hefx_job* jobs, size_t njobs, hefx_path path,
+                                   hefx_batch_plan** out);
+void hefx_batch_plan_destroy(hefx_batch_plan* plan);
+
+/*
+ * Runs every job of the plan: per size class, one persistent launch computes NTT(a) into c
+ * and one computes INTT(NTT(b) o c) into c.  On a non-default stream that is not already
+ * being captured, the first call captures these launches into a CUDA graph and every call
+ * replays it (one graph launch per batch); on the legacy default stream, or inside a
+ * caller's own capture, the kernels are launched directly.  Errors: EINVAL, ECUDA.
+ */
+hefx_status hefx_batch_polymul(hefx_ctx* ctx, hefx_batch_plan* plan, void* stream);
+
+/*
  * Waits for `stream`, then reports whether a bounded device-side wait of the tensor-path
  * kernels launched with `params` expired since the last check (HEFX_ETIMEOUT; the results of
  * those calls are invalid) and clears that record.  The tcgen05 pipelines wait on mbarriers

@@ -336,6 +336,137 @@ hefx_status hefx_basis_convert(hefx_ctx* ctx, const hefx_bconv_plan* plan, const
     return HEFX_OK;
 }
 
+hefx_status hefx_batch_plan_create(hefx_ctx* ctx, const hefx_job* jobs, size_t njobs, hefx_path path,
+                                   hefx_batch_plan** out) {
+    if (!ctx || !out) return HEFX_EINVAL;
+    *out = nullptr;
+    if (njobs && !jobs) return fail(ctx, HEFX_EINVAL, "jobs is null");
+    if (path == HEFX_PATH_TENSOR)
+        return fail(ctx, HEFX_EUNSUPPORTED, "batched jobs run on the CUDA-core row-list kernels");
+    if (path != HEFX_PATH_AUTO && path != HEFX_PATH_CUDACORE) return fail(ctx, HEFX_EINVAL, "unknown path");
+    // group rows by (parameter set, launch kind): NTT(a) -> c; INTT(NTT(b) o c); INTT(c o c)
+    std::vector<const hefx_params*> order;
+    std::vector<std::vector<RowDesc>> fwd, fhi, sq;
+    for (size_t j = 0; j < njobs; ++j) {
+        const hefx_job& jb = jobs[j];
+        if (!jb.params || jb.params->ctx != ctx)
+            return fail(ctx, HEFX_EINVAL, "job %zu: params null or of another context", j);
+        if (jb.nlimbs == 0 || jb.nlimbs > jb.params->nlimbs)
+            return fail(ctx, HEFX_EINVAL, "job %zu: nlimbs %u outside [1, %u]", j, jb.nlimbs, jb.params->nlimbs);
+        if (!jb.d_a || !jb.d_b || !jb.d_c || !aligned16(jb.d_a) || !aligned16(jb.d_b) || !aligned16(jb.d_c))
+            return fail(ctx, HEFX_EINVAL, "job %zu: null or misaligned buffer", j);
+        size_t g = 0;
+        while (g < order.size() && order[g] != jb.params) ++g;
+        if (g == order.size()) {
+            order.push_back(jb.params);
+            fwd.emplace_back();
+            fhi.emplace_back();
+            sq.emplace_back();
+        }
+        const size_t n = jb.params->n;
+        const uint32_t *a = jb.d_a, *b = jb.d_b;
+        if (a != b && jb.d_c == b) std::swap(a, b);  // keep b intact while c is written
+        for (uint32_t l = 0; l < jb.nlimbs; ++l) {
+            RowDesc r0 = {a + l * n, nullptr, jb.d_c + l * n, l, 0};
+            fwd[g].push_back(r0);
+            if (a == b) {
+                RowDesc r1 = {jb.d_c + l * n, jb.d_c + l * n, jb.d_c + l * n, l, 0};
+                sq[g].push_back(r1);
+            } else {
+                RowDesc r1 = {b + l * n, jb.d_c + l * n, jb.d_c + l * n, l, 0};
+                fhi[g].push_back(r1);
+            }
+        }
+    }
+    hefx_status st = use_device(ctx);
+    if (st != HEFX_OK) return st;
+    hefx_batch_plan* plan = new hefx_batch_plan();
+    plan->ctx = ctx;
+    std::vector<RowDesc> all;
+    auto add = [&](const hefx_params* pr, NttMode m, const std::vector<RowDesc>& rows) {
+        if (rows.empty()) return;
+        plan->launches.push_back({pr, (NttModeTag)m, all.size(), rows.size()});
+        all.insert(all.end(), rows.begin(), rows.end());
+    };
+    for (size_t g = 0; g < order.size(); ++g) add(order[g], MODE_FWD, fwd[g]);
+    for (size_t g = 0; g < order.size(); ++g) {
+        add(order[g], MODE_FWD_HAD_INV, fhi[g]);
+        add(order[g], MODE_HAD_INV, sq[g]);
+    }
+    plan->total_rows = all.size();
+    for (const auto& l : plan->launches) {
+        cudaError_t e = prepare_ntt_cc(l.params, (NttMode)l.mode);
+        if (e != cudaSuccess) {
+            hefx_batch_plan_destroy(plan);
+            return cuda_fail(ctx, e, "batch plan kernel attributes");
+        }
+    }
+    if (!all.empty()) {
+        cudaError_t e = cudaMalloc(&plan->d_rows, all.size() * sizeof(RowDesc));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(plan->d_rows, all.data(), all.size() * sizeof(RowDesc), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            hefx_batch_plan_destroy(plan);
+            return cuda_fail(ctx, e, "batch plan upload");
+        }
+    }
+    *out = plan;
+    return HEFX_OK;
+}
+
+void hefx_batch_plan_destroy(hefx_batch_plan* plan) {
+    if (!plan) return;
+    if (plan->exec) cudaGraphExecDestroy(plan->exec);
+    if (plan->graph) cudaGraphDestroy(plan->graph);
+    if (plan->d_rows) cudaFree(plan->d_rows);
+    delete plan;
+}
+
+static cudaError_t batch_launch_all(hefx_batch_plan* plan, cudaStream_t s) {
+    const RowDesc* rows = static_cast<const RowDesc*>(plan->d_rows);
+    for (const auto& l : plan->launches) {
+        cudaError_t e = launch_ntt_cc_rows(l.params, (NttMode)l.mode, rows + l.offset, l.nrows, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+hefx_status hefx_batch_polymul(hefx_ctx* ctx, hefx_batch_plan* plan, void* stream) {
+    if (!ctx) return HEFX_EINVAL;
+    if (!plan || plan->ctx != ctx) return fail(ctx, HEFX_EINVAL, "plan is null or belongs to another context");
+    hefx_status st = use_device(ctx);
+    if (st != HEFX_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (plan->launches.empty()) return HEFX_OK;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = s ? cudaStreamIsCapturing(s, &cap) : cudaSuccess;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamIsCapturing");
+    if (!s || cap != cudaStreamCaptureStatusNone) {  // legacy stream or caller's own capture
+        e = batch_launch_all(plan, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "hefx_batch_polymul launch");
+        return HEFX_OK;
+    }
+    if (!plan->exec) {
+        e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t le = batch_launch_all(plan, s);
+            e = cudaStreamEndCapture(s, &plan->graph);
+            if (le != cudaSuccess) e = le;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&plan->exec, plan->graph, 0);
+        if (e != cudaSuccess) {
+            if (plan->graph) cudaGraphDestroy(plan->graph);
+            plan->graph = nullptr;
+            plan->exec = nullptr;
+            return cuda_fail(ctx, e, "hefx_batch_polymul graph capture");
+        }
+        plan->graph_stream = s;
+    }
+    e = cudaGraphLaunch(plan->exec, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "hefx_batch_polymul graph launch");
+    return HEFX_OK;
+}
+
 hefx_status hefx_stream_check(hefx_ctx* ctx, const hefx_params* p, void* stream) {
     if (!ctx) return HEFX_EINVAL;
     if (!p || p->ctx != ctx) return fail(ctx, HEFX_EINVAL, "params is null or belongs to another context");

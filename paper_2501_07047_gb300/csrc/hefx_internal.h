@@ -12,6 +12,8 @@
 
 namespace hefx {
 
+typedef int NttModeTag;  // an NttMode value, stored by plans
+
 // Per-limb constants of one parameter set, in device memory ([nlimbs] array).
 struct LimbConst {
     uint32_t q;
@@ -30,6 +32,16 @@ static_assert(sizeof(LimbConst) == 64, "LimbConst is one 64-byte line");
 inline constexpr int ntt_cc_small_radix(int log2n) {
     return (log2n >= 16 ? log2n - 1 : log2n) < 5 ? (log2n >= 16 ? log2n - 1 : log2n) : 5;
 }
+
+// One row (limb of one polynomial) of a batched job: where its operands live and which limb
+// of the parameter set's basis it is reduced by.
+struct RowDesc {
+    const uint32_t* in;
+    const uint32_t* had;
+    uint32_t* out;
+    uint32_t limb;
+    uint32_t pad;
+};
 
 // Device tables of the tensor-core (matrix) NTT for one parameter set; see ntt_tc.cu.
 struct TensorTables;
@@ -58,6 +70,22 @@ struct hefx_params {
     hefx_path tuned_path = HEFX_PATH_AUTO;
 };
 
+struct hefx_batch_plan {
+    hefx_ctx* ctx = nullptr;
+    struct Launch {
+        const hefx_params* params;
+        hefx::NttModeTag mode;
+        size_t offset;  // first RowDesc of this launch in d_rows
+        size_t nrows;
+    };
+    std::vector<Launch> launches;
+    void* d_rows = nullptr;  // RowDesc array
+    size_t total_rows = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t graph_stream = nullptr;  // stream the graph was captured on
+};
+
 struct hefx_bconv_plan {
     hefx_ctx* ctx = nullptr;
     uint32_t log2n = 0;
@@ -74,6 +102,11 @@ enum NttMode { MODE_FWD = 0, MODE_INV = 1, MODE_FWD_HAD_INV = 2, MODE_HAD_INV = 
 
 cudaError_t launch_ntt_cc(const hefx_params* p, NttMode mode, const uint32_t* in, const uint32_t* had, uint32_t* out,
                           size_t rows, cudaStream_t stream);
+// Sets the kernel attributes of (N, mode) ahead of time (no launch), e.g. before a capture.
+cudaError_t prepare_ntt_cc(const hefx_params* p, NttMode mode);
+// Same kernels over an explicit list of rows (device array of RowDesc), persistent grid.
+cudaError_t launch_ntt_cc_rows(const hefx_params* p, NttMode mode, const RowDesc* d_rows, size_t nrows,
+                               cudaStream_t stream);
 
 cudaError_t launch_bconv_cc(const hefx_bconv_plan* plan, const uint32_t* in, uint32_t* out, size_t batch,
                             cudaStream_t stream);

@@ -17,6 +17,8 @@
 //    stored in bit-reversed order, as MAT folds permutations into constants, Sec. IV-B).
 #include <cooperative_groups.h>
 
+#include <algorithm>
+
 #include "hefx_internal.h"
 #include "modarith.cuh"
 
@@ -52,9 +54,28 @@ struct KArgs {
     const uint2* tw_f;  // forward twiddles [L][N]
     const uint2* tw_i;  // inverse twiddles [L][N]
     const LimbConst* lc;
+    const RowDesc* desc;  // per-row pointers and limb (batched jobs), or null: [rows][N] layout
     uint32_t rows;
     uint32_t L;
 };
+
+// Row r's input / Hadamard operand / output and limb, from the descriptor list when there
+// is one, else from the contiguous [batch][L][N] layout.
+template <int N>
+__device__ __forceinline__ const uint32_t* row_in(const KArgs& a, uint32_t r) {
+    return a.desc ? a.desc[r].in : a.in + (size_t)r * N;
+}
+template <int N>
+__device__ __forceinline__ const uint32_t* row_had(const KArgs& a, uint32_t r) {
+    return a.desc ? a.desc[r].had : a.had + (size_t)r * N;
+}
+template <int N>
+__device__ __forceinline__ uint32_t* row_out(const KArgs& a, uint32_t r) {
+    return a.desc ? a.desc[r].out : a.out + (size_t)r * N;
+}
+__device__ __forceinline__ uint32_t row_limb(const KArgs& a, uint32_t r) {
+    return a.desc ? a.desc[r].limb : r % a.L;
+}
 
 // Where a register pass takes its inputs and puts its outputs.
 enum : int { SRC_SMEM = 0, SRC_GLOBAL = 1, SRC_SPLIT0 = 2, SRC_GLOBAL_HAD = 3 };
@@ -77,7 +98,9 @@ __device__ __forceinline__ void load_elems(uint32_t (&x)[1 << R], const uint32_t
         for (int k = 0; k < (1 << R); ++k) x[k] = sm[pad(row * C::m + jb + (k << logs))];
     } else {
         const bool valid = row < sg.nrows;
-        const size_t grow = (size_t)(sg.row0 + row) * N;
+        const uint32_t grow_r = valid ? sg.row0 + row : sg.row0;
+        const uint32_t* rin = row_in<N>(a, grow_r);
+        const uint32_t* rhad = SRC == SRC_GLOBAL_HAD ? row_had<N>(a, grow_r) : nullptr;
         if constexpr (SRC == SRC_SPLIT0) {
             // first forward stage (pairs j, j + N/2) computed while loading: this CTA keeps
             // X + w Y (half 0) or X - w Y (half 1), w = psi^brv(1)
@@ -85,14 +108,14 @@ __device__ __forceinline__ void load_elems(uint32_t (&x)[1 << R], const uint32_t
             const uint32_t q = lc.q;
 #pragma unroll
             for (int k = 0; k < (1 << R); ++k) {
-                const size_t g = grow + jb + (k << logs);
-                const uint32_t X = __ldg(a.in + g), Y = __ldg(a.in + g + N / 2);
+                const size_t g = jb + (k << logs);
+                const uint32_t X = __ldg(rin + g), Y = __ldg(rin + g + N / 2);
                 const uint32_t t = mul_shoup_lazy(Y, w.x, w.y, q);
                 x[k] = sg.half ? X - t + 2 * q : X + t;
             }
         } else if constexpr (logs == 0 && R >= 2) {
-            const uint4* src = reinterpret_cast<const uint4*>(a.in + grow + sg.gbase + jb);
-            const uint4* hs = reinterpret_cast<const uint4*>(a.had + grow + sg.gbase + jb);
+            const uint4* src = reinterpret_cast<const uint4*>(rin + sg.gbase + jb);
+            const uint4* hs = reinterpret_cast<const uint4*>(rhad + sg.gbase + jb);
 #pragma unroll
             for (int k = 0; k < (1 << R); k += 4) {
                 uint4 v = valid ? __ldg(src + k / 4) : make_uint4(0, 0, 0, 0);
@@ -111,9 +134,9 @@ __device__ __forceinline__ void load_elems(uint32_t (&x)[1 << R], const uint32_t
         } else {
 #pragma unroll
             for (int k = 0; k < (1 << R); ++k) {
-                const size_t g = grow + sg.gbase + jb + (k << logs);
-                uint32_t v = valid ? __ldg(a.in + g) : 0u;
-                if constexpr (SRC == SRC_GLOBAL_HAD) v = mul_mont_lazy(v, valid ? __ldg(a.had + g) : 0u, lc.q, lc.qinv_neg);
+                const size_t g = sg.gbase + jb + (k << logs);
+                uint32_t v = valid ? __ldg(rin + g) : 0u;
+                if constexpr (SRC == SRC_GLOBAL_HAD) v = mul_mont_lazy(v, valid ? __ldg(rhad + g) : 0u, lc.q, lc.qinv_neg);
                 x[k] = v;
             }
         }
@@ -130,7 +153,7 @@ __device__ __forceinline__ void store_elems(const uint32_t (&x)[1 << R], uint32_
         for (int k = 0; k < (1 << R); ++k) sm[pad(row * C::m + jb + (k << logs))] = x[k];
     } else {
         if (row >= sg.nrows) return;
-        uint32_t* dst = a.out + (size_t)(sg.row0 + row) * N + sg.gbase + jb;
+        uint32_t* dst = row_out<N>(a, sg.row0 + row) + sg.gbase + jb;
         if constexpr (logs == 0 && R >= 2) {
 #pragma unroll
             for (int k = 0; k < (1 << R); k += 4) {
@@ -232,7 +255,7 @@ __device__ __forceinline__ void fwd_pass(uint32_t* sm, const Seg& sg, const KArg
         const int j_hi = uu >> logtl;
         const int jb = (j_hi << (logtl + R)) + j_lo;
         const uint32_t g0 = (sg.gbase >> (logtl + R)) + (uint32_t)j_hi;
-        const uint32_t limb = (sg.row0 + row) % a.L;
+        const uint32_t limb = row_limb(a, row < sg.nrows ? sg.row0 + row : sg.row0);
         const LimbConst& lc = a.lc[limb];
         const uint2* tw = a.tw_f + (size_t)limb * N;
         uint32_t x[1 << R];
@@ -255,7 +278,7 @@ __device__ __forceinline__ void inv_pass(uint32_t* sm, const Seg& sg, const KArg
         const int j_lo = uu & ((1 << e0) - 1);
         const int j_hi = uu >> e0;
         const int jb = (j_hi << (e0 + R)) + j_lo;
-        const uint32_t limb = (sg.row0 + row) % a.L;
+        const uint32_t limb = row_limb(a, row < sg.nrows ? sg.row0 + row : sg.row0);
         const LimbConst& lc = a.lc[limb];
         const uint2* tw = a.tw_i + (size_t)limb * N;
         uint32_t x[1 << R];
@@ -280,13 +303,13 @@ __device__ __forceinline__ void fwd_had_inv_pass(uint32_t* sm, const Seg& sg, co
         const int j_hi = u & (nsub - 1);
         const int jb = j_hi << R;
         const uint32_t g0 = (sg.gbase >> R) + (uint32_t)j_hi;
-        const uint32_t limb = (sg.row0 + row) % a.L;
+        const uint32_t limb = row_limb(a, row < sg.nrows ? sg.row0 + row : sg.row0);
         const LimbConst& lc = a.lc[limb];
         uint32_t x[1 << R];
         load_elems<R, LOGN, 0, SRC>(x, sm, a, sg, row, jb, lc, a.tw_f + (size_t)limb * N);
         fwd_stages<R, LOGN, s0>(x, g0, a.tw_f + (size_t)limb * N, lc.q);
         const bool valid = row < sg.nrows;
-        const uint4* hs = reinterpret_cast<const uint4*>(a.had + (size_t)(sg.row0 + row) * N + sg.gbase + jb);
+        const uint4* hs = reinterpret_cast<const uint4*>(row_had<N>(a, valid ? sg.row0 + row : sg.row0) + sg.gbase + jb);
 #pragma unroll
         for (int k = 0; k < (1 << R); k += 4) {
             const uint4 h = valid ? __ldg(hs + k / 4) : make_uint4(0, 0, 0, 0);
@@ -346,11 +369,11 @@ __device__ __forceinline__ void split_last_stage(uint32_t* sm, const Seg& sg, co
     cluster.sync();
     const uint32_t* s0 = cluster.map_shared_rank(sm, 0);
     const uint32_t* s1 = cluster.map_shared_rank(sm, 1);
-    const LimbConst& lc = a.lc[sg.row0 % a.L];
+    const LimbConst& lc = a.lc[row_limb(a, sg.row0)];
     const uint32_t q = lc.q;
     const uint32_t s = SCALE == 1 ? lc.ninv : lc.ninvR, ssh = SCALE == 1 ? lc.ninv_sh : lc.ninvR_sh;
     const uint32_t w = SCALE == 1 ? lc.ninvw : lc.ninvRw, wsh = SCALE == 1 ? lc.ninvw_sh : lc.ninvRw_sh;
-    uint32_t* out = a.out + (size_t)sg.row0 * N;
+    uint32_t* out = row_out<N>(a, sg.row0);
     for (int i = threadIdx.x * 4; i < N / 4; i += C::threads * 4) {
         const int j = sg.half * (N / 4) + i;
         uint32_t r0[4], r1[4];
@@ -368,20 +391,8 @@ __device__ __forceinline__ void split_last_stage(uint32_t* sm, const Seg& sg, co
 }
 
 template <int LOGN, int MODE>
-__global__ void __launch_bounds__(Cfg<LOGN>::threads) ntt_cc_kernel(KArgs a) {
+__device__ __forceinline__ void run_task(uint32_t* sm, const Seg& sg, const KArgs& a) {
     using C = Cfg<LOGN>;
-    extern __shared__ __align__(16) uint32_t sm[];
-    Seg sg;
-    if constexpr (C::split) {
-        sg.row0 = blockIdx.x >> 1;
-        sg.half = blockIdx.x & 1;
-        sg.nrows = 1;
-    } else {
-        sg.row0 = blockIdx.x * C::rows;
-        sg.half = 0;
-        sg.nrows = (int)min((uint32_t)C::rows, a.rows - sg.row0);
-    }
-    sg.gbase = sg.half * C::m;
     constexpr int RS = C::r_small;
     constexpr int S_FIRST = C::split ? 1 : 0;     // first global stage run by the CTA
     constexpr int S_SMALL = LOGN - RS;            // first stage of the smallest-stride pass
@@ -419,6 +430,33 @@ __global__ void __launch_bounds__(Cfg<LOGN>::threads) ntt_cc_kernel(KArgs a) {
 }
 
 template <int LOGN, int MODE>
+__global__ void __launch_bounds__(Cfg<LOGN>::threads) ntt_cc_kernel(KArgs a) {
+    using C = Cfg<LOGN>;
+    extern __shared__ __align__(16) uint32_t sm[];
+    // persistent: each CTA (or CTA pair) walks a strided sequence of tasks; a task is one
+    // row (split N) or C::rows rows
+    const uint32_t ntasks = C::split ? a.rows : (a.rows + C::rows - 1) / C::rows;
+    const uint32_t first = C::split ? blockIdx.x >> 1 : blockIdx.x;
+    const uint32_t stride = C::split ? gridDim.x >> 1 : gridDim.x;
+    for (uint32_t task = first; task < ntasks; task += stride) {
+        Seg sg;
+        if constexpr (C::split) {
+            sg.row0 = task;
+            sg.half = blockIdx.x & 1;
+            sg.nrows = 1;
+        } else {
+            sg.row0 = task * C::rows;
+            sg.half = 0;
+            sg.nrows = (int)min((uint32_t)C::rows, a.rows - sg.row0);
+        }
+        sg.gbase = sg.half * C::m;
+        run_task<LOGN, MODE>(sm, sg, a);
+        __syncthreads();  // shared memory is reused by the next task
+    }
+}
+
+// rows == 0: set the kernel's attributes only (done before a stream capture).
+template <int LOGN, int MODE>
 cudaError_t launch_one(const KArgs& a, size_t rows, cudaStream_t stream) {
     using C = Cfg<LOGN>;
     auto kern = ntt_cc_kernel<LOGN, MODE>;
@@ -428,13 +466,19 @@ cudaError_t launch_one(const KArgs& a, size_t rows, cudaStream_t stream) {
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
+    if (rows == 0) return cudaSuccess;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     cfg.blockDim = dim3(C::threads);
     cfg.dynamicSmemBytes = C::smem_bytes;
     cfg.stream = stream;
+    int dev = 0, sms = 148, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::threads, C::smem_bytes);
+    const size_t resident = (size_t)sms * (size_t)(per_sm > 0 ? per_sm : 1);
     if (C::split) {
-        cfg.gridDim = dim3((unsigned)(rows * 2));
+        cfg.gridDim = dim3((unsigned)(2 * std::min(rows, resident / 2)));
         attr[0].id = cudaLaunchAttributeClusterDimension;
         attr[0].val.clusterDim.x = 2;
         attr[0].val.clusterDim.y = 1;
@@ -442,7 +486,7 @@ cudaError_t launch_one(const KArgs& a, size_t rows, cudaStream_t stream) {
         cfg.attrs = attr;
         cfg.numAttrs = 1;
     } else {
-        cfg.gridDim = dim3((unsigned)((rows + C::rows - 1) / C::rows));
+        cfg.gridDim = dim3((unsigned)std::min((rows + C::rows - 1) / C::rows, resident));
     }
     return cudaLaunchKernelEx(&cfg, kern, a);
 }
@@ -459,6 +503,8 @@ cudaError_t launch_mode(NttMode mode, const KArgs& a, size_t rows, cudaStream_t 
 
 }  // namespace
 
+cudaError_t launch_dispatch(const hefx_params* p, NttMode mode, const KArgs& a, size_t rows, cudaStream_t stream);
+
 cudaError_t launch_ntt_cc(const hefx_params* p, NttMode mode, const uint32_t* in, const uint32_t* had, uint32_t* out,
                           size_t rows, cudaStream_t stream) {
     KArgs a;
@@ -468,9 +514,35 @@ cudaError_t launch_ntt_cc(const hefx_params* p, NttMode mode, const uint32_t* in
     a.tw_f = p->d_tw_fwd;
     a.tw_i = p->d_tw_inv;
     a.lc = p->d_lc;
+    a.desc = nullptr;
     a.rows = (uint32_t)rows;
     a.L = p->nlimbs;
     if (rows == 0) return cudaSuccess;
+    return launch_dispatch(p, mode, a, rows, stream);
+}
+
+cudaError_t prepare_ntt_cc(const hefx_params* p, NttMode mode) {
+    KArgs a = {};
+    return launch_dispatch(p, mode, a, 0, nullptr);
+}
+
+cudaError_t launch_ntt_cc_rows(const hefx_params* p, NttMode mode, const RowDesc* d_rows, size_t nrows,
+                               cudaStream_t stream) {
+    KArgs a;
+    a.in = nullptr;
+    a.had = nullptr;
+    a.out = nullptr;
+    a.tw_f = p->d_tw_fwd;
+    a.tw_i = p->d_tw_inv;
+    a.lc = p->d_lc;
+    a.desc = d_rows;
+    a.rows = (uint32_t)nrows;
+    a.L = p->nlimbs;
+    if (nrows == 0) return cudaSuccess;
+    return launch_dispatch(p, mode, a, nrows, stream);
+}
+
+cudaError_t launch_dispatch(const hefx_params* p, NttMode mode, const KArgs& a, size_t rows, cudaStream_t stream) {
     switch (p->log2n) {
         case 3: return launch_mode<3>(mode, a, rows, stream);
         case 4: return launch_mode<4>(mode, a, rows, stream);

@@ -37,7 +37,15 @@ SIGNATURES = {
     "hefx_bconv_plan_destroy": (None, [_vp]),
     "hefx_basis_convert": (_i32, [_vp, _vp, _vp, _vp, _sz, _i32, _vp]),
     "hefx_stream_check": (_i32, [_vp, _vp, _vp]),
+    "hefx_batch_plan_create": (_i32, [_vp, _vp, _sz, _i32, ctypes.POINTER(_vp)]),
+    "hefx_batch_plan_destroy": (None, [_vp]),
+    "hefx_batch_polymul": (_i32, [_vp, _vp, _vp]),
 }
+
+
+class hefx_job(ctypes.Structure):
+    _fields_ = [("params", ctypes.c_void_p), ("nlimbs", ctypes.c_uint32), ("d_a", ctypes.c_void_p),
+                ("d_b", ctypes.c_void_p), ("d_c", ctypes.c_void_p)]
 
 _lib = None
 
@@ -160,6 +168,25 @@ def hefx_basis_convert(ctx, plan, d_in, d_out, batch, path="auto", stream=None) 
 
 def hefx_stream_check(ctx, params, stream=None) -> None:
     _check(ctx, load().hefx_stream_check(ctx, params, _stream(stream)))
+
+
+def hefx_batch_plan_create(ctx, jobs, path="auto") -> int:
+    """jobs: iterable of (params, nlimbs, a, b, c) with device buffers or pointers."""
+    jobs = list(jobs)
+    arr = (hefx_job * max(1, len(jobs)))()
+    for i, (params, nl, a, b, c) in enumerate(jobs):
+        arr[i] = hefx_job(params, nl, _ptr(a), _ptr(b), _ptr(c))
+    h = _vp()
+    _check(ctx, load().hefx_batch_plan_create(ctx, ctypes.cast(arr, _vp), len(jobs), _path(path), ctypes.byref(h)))
+    return h.value
+
+
+def hefx_batch_plan_destroy(plan) -> None:
+    load().hefx_batch_plan_destroy(plan)
+
+
+def hefx_batch_polymul(ctx, plan, stream=None) -> None:
+    _check(ctx, load().hefx_batch_polymul(ctx, plan, _stream(stream)))
 
 
 def raw_status(fn_name: str, *args) -> int:

@@ -1,0 +1,108 @@
+"""GPU parity of batched uneven polynomial products (one graph launch) against the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2501_07047_gb300 import hefx, inputs
+from paper_2501_07047_gb300.batch import UnevenBatch
+
+from hefx_testutil import to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = hefx.hefx_create(0)
+    yield c
+    hefx.hefx_destroy(c)
+
+
+def expect(batch, j):
+    logn, L = batch.shapes[j]
+    a, b = batch.host_inputs(j)
+    return oracle.polymul_batch(a[None], b[None], batch.primes[:L])[0]
+
+
+def test_small_mix_graph_replay(ctx):
+    shapes = [(3, 1), (6, 2), (10, 3), (12, 5), (13, 2), (14, 1), (15, 2), (16, 3), (12, 1), (16, 1), (4, 4), (11, 2)]
+    batch = UnevenBatch(ctx, shapes, seed=41, lmax=8)
+    try:
+        s = torch.cuda.Stream()
+        for rep in range(3):  # first call captures the graph, the others replay it
+            for c in batch.c:
+                c.zero_()
+            with torch.cuda.stream(s):
+                batch.run(s)
+            s.synchronize()
+            for j in range(len(shapes)):
+                assert (batch.c[j].cpu().numpy().view(np.uint32) == expect(batch, j)).all(), (rep, j, shapes[j])
+    finally:
+        batch.close()
+
+
+def test_aliasing_and_default_stream(ctx):
+    primes = inputs.source_primes(4)
+    p12 = hefx.hefx_params_create(ctx, 12, primes)
+    p16 = hefx.hefx_params_create(ctx, 16, primes)
+    try:
+        ha = inputs.residue_tensor(5, 1, primes[:3], 4096)[0]
+        hb = inputs.residue_tensor(6, 1, primes[:3], 4096)[0]
+        ga = inputs.residue_tensor(7, 1, primes[:2], 65536)[0]
+        a1, b1 = to_dev(ha), to_dev(hb)          # c aliases a
+        a2, b2 = to_dev(ha), to_dev(hb)          # c aliases b
+        a3 = to_dev(ga)                          # a == b == c (square in place)
+        a4, c4 = to_dev(ga), torch.empty((2, 65536), dtype=torch.int32, device="cuda")  # a == b
+        jobs = [(p12, 3, a1, b1, a1), (p12, 3, a2, b2, b2), (p16, 2, a3, a3, a3), (p16, 2, a4, a4, c4)]
+        plan = hefx.hefx_batch_plan_create(ctx, jobs)
+        try:
+            hefx.hefx_batch_polymul(ctx, plan, None)  # legacy stream: direct launches
+            ab = oracle.polymul_batch(ha[None], hb[None], primes[:3])[0]
+            sq = oracle.polymul_batch(ga[None], ga[None], primes[:2])[0]
+            assert (to_host(a1).reshape(ab.shape) == ab).all()
+            assert (to_host(b2).reshape(ab.shape) == ab).all()
+            assert (to_host(a3).reshape(sq.shape) == sq).all()
+            assert (to_host(c4).reshape(sq.shape) == sq).all()
+        finally:
+            hefx.hefx_batch_plan_destroy(plan)
+        with pytest.raises(hefx.HefxError) as e:
+            hefx.hefx_batch_plan_create(ctx, [(p12, 5, a1, b1, a1)])  # more limbs than the params hold
+        assert e.value.status == hefx.HEFX_EINVAL
+        with pytest.raises(hefx.HefxError) as e:
+            hefx.hefx_batch_plan_create(ctx, [(p12, 1, a1, b1, a1)], "tensor")
+        assert e.value.status == hefx.HEFX_EUNSUPPORTED
+    finally:
+        hefx.hefx_params_destroy(p12)
+        hefx.hefx_params_destroy(p16)
+
+
+def test_config4_full_size_sampled(ctx):
+    """256 jobs, N uniform in {2^12..2^16}, L uniform in [4, 32]: one graph launch; 24 sampled
+    limbs (every size class) checked in full against the oracle."""
+    shapes = inputs.uneven_jobs(inputs.derive_seed(4), 256)
+    batch = UnevenBatch(ctx, shapes, seed=4)
+    try:
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            batch.run(s)
+            batch.run(s)  # replay: same inputs, same outputs
+        s.synchronize()
+        rng = np.random.default_rng(11)
+        seen = set()
+        picks = []
+        for j in rng.permutation(len(shapes)):
+            if len(picks) >= 24:
+                break
+            if shapes[j][0] not in seen or len(seen) == 5:
+                seen.add(shapes[j][0])
+                picks.append(int(j))
+        for j in picks:
+            logn, L = shapes[j]
+            l = int(rng.integers(L))
+            a, b = batch.host_inputs(j)
+            q = batch.primes[l]
+            got = batch.c[j][l].cpu().numpy().view(np.uint32)
+            assert (got == oracle.polymul(a[l], b[l], q)).all(), (j, l, shapes[j])
+    finally:
+        batch.close()
