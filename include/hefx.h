@@ -136,6 +136,23 @@ hefx_status hefx_basis_convert(hefx_ctx* ctx, const hefx_bconv_plan* plan, const
                                size_t batch, hefx_path path, void* stream);
 
 /*
+ * z = x o y mod q per limb (VecModMul of Table "HE operator -> AI operator"), elementwise over
+ * [batch][nlimbs][N]; any of the buffers may alias.  Errors as for hefx_ntt_fwd.
+ */
+hefx_status hefx_vec_mod_mul(hefx_ctx* ctx, const hefx_params* params, const uint32_t* d_x, const uint32_t* d_y,
+                             uint32_t* d_z, size_t batch, void* stream);
+
+/*
+ * Tensor product of two ciphertexts (a0, a1), (b0, b1) in evaluation (NTT) form, the first
+ * step of HE-Mult (Sec. III; App. A: HE-Mult is built from NTT, INTT, BConv, VecModMul and
+ * VecModAdd): d0 = a0 o b0, d1 = a0 o b1 + a1 o b0, d2 = a1 o b1 mod q, elementwise over
+ * [batch][nlimbs][N].  Outputs must not alias inputs.  Errors as for hefx_ntt_fwd.
+ */
+hefx_status hefx_tensor_product(hefx_ctx* ctx, const hefx_params* params, const uint32_t* d_a0, const uint32_t* d_a1,
+                                const uint32_t* d_b0, const uint32_t* d_b1, uint32_t* d_d0, uint32_t* d_d1,
+                                uint32_t* d_d2, size_t batch, void* stream);
+
+/*
  * Batched polynomial products of uneven shape (the batching pattern of the build; the
  * paper's batching study is Sec. V-B3, "TPUs favor large batch").  Each job multiplies two
  * polynomials of ring degree N = 2^params->log2n over the first `nlimbs` primes of

@@ -176,6 +176,7 @@ hefx_status hefx_params_create(hefx_ctx* ctx, uint32_t log2n, const uint32_t* pr
         c.ninvR_sh = shoup(vals[2], q);
         c.ninvRw = (uint32_t)vals[3];
         c.ninvRw_sh = shoup(vals[3], q);
+        c.r2 = (uint32_t)mul_mod(r32, r32, q);
     }
     cudaError_t e = cudaMalloc(&p->d_lc, sizeof(LimbConst) * nlimbs);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_tw_fwd, sizeof(uint2) * twf.size());
@@ -333,6 +334,36 @@ hefx_status hefx_basis_convert(hefx_ctx* ctx, const hefx_bconv_plan* plan, const
     if (e == cudaErrorNotSupported)
         return fail(ctx, HEFX_EUNSUPPORTED, "tensor basis conversion not available for this plan");
     if (e != cudaSuccess) return cuda_fail(ctx, e, "hefx_basis_convert launch");
+    return HEFX_OK;
+}
+
+hefx_status hefx_vec_mod_mul(hefx_ctx* ctx, const hefx_params* p, const uint32_t* x, const uint32_t* y, uint32_t* z,
+                             size_t batch, void* stream) {
+    hefx_status st;
+    if ((st = check_ntt_args(ctx, p, x, "d_x")) != HEFX_OK) return st;
+    if ((st = check_ntt_args(ctx, p, y, "d_y")) != HEFX_OK) return st;
+    if ((st = check_ntt_args(ctx, p, z, "d_z")) != HEFX_OK) return st;
+    if (batch == 0) return HEFX_OK;
+    if ((st = use_device(ctx)) != HEFX_OK) return st;
+    cudaError_t e = launch_vec_mod_mul(p, x, y, z, batch * p->nlimbs, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "hefx_vec_mod_mul launch");
+    return HEFX_OK;
+}
+
+hefx_status hefx_tensor_product(hefx_ctx* ctx, const hefx_params* p, const uint32_t* a0, const uint32_t* a1,
+                                const uint32_t* b0, const uint32_t* b1, uint32_t* d0, uint32_t* d1, uint32_t* d2,
+                                size_t batch, void* stream) {
+    const void* ptrs[7] = {a0, a1, b0, b1, d0, d1, d2};
+    const char* names[7] = {"d_a0", "d_a1", "d_b0", "d_b1", "d_d0", "d_d1", "d_d2"};
+    for (int i = 0; i < 7; ++i) {
+        hefx_status st = check_ntt_args(ctx, p, ptrs[i], names[i]);
+        if (st != HEFX_OK) return st;
+    }
+    if (batch == 0) return HEFX_OK;
+    hefx_status st = use_device(ctx);
+    if (st != HEFX_OK) return st;
+    cudaError_t e = launch_tensor_product(p, a0, a1, b0, b1, d0, d1, d2, batch * p->nlimbs, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "hefx_tensor_product launch");
     return HEFX_OK;
 }
 

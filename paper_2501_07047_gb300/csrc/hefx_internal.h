@@ -22,7 +22,8 @@ struct LimbConst {
     uint32_t ninvw, ninvw_sh;     // N^-1 * psi^-brv_N(1): twiddle of the last Gentleman-Sande stage
     uint32_t ninvR, ninvR_sh;     // N^-1 * 2^32: undoes the 2^-32 of a Montgomery Hadamard product
     uint32_t ninvRw, ninvRw_sh;   // N^-1 * 2^32 * psi^-brv_N(1)
-    uint32_t pad[6];
+    uint32_t r2;                  // 2^64 mod q: two Montgomery products give a plain one
+    uint32_t pad[5];
 };
 static_assert(sizeof(LimbConst) == 64, "LimbConst is one 64-byte line");
 
@@ -102,6 +103,13 @@ enum NttMode { MODE_FWD = 0, MODE_INV = 1, MODE_FWD_HAD_INV = 2, MODE_HAD_INV = 
 
 cudaError_t launch_ntt_cc(const hefx_params* p, NttMode mode, const uint32_t* in, const uint32_t* had, uint32_t* out,
                           size_t rows, cudaStream_t stream);
+// Elementwise products of the HE-Mult request (elementwise.cu).
+cudaError_t launch_vec_mod_mul(const hefx_params* p, const uint32_t* x, const uint32_t* y, uint32_t* z, size_t rows,
+                               cudaStream_t s);
+cudaError_t launch_tensor_product(const hefx_params* p, const uint32_t* a0, const uint32_t* a1, const uint32_t* b0,
+                                  const uint32_t* b1, uint32_t* d0, uint32_t* d1, uint32_t* d2, size_t rows,
+                                  cudaStream_t s);
+
 // Sets the kernel attributes of (N, mode) ahead of time (no launch), e.g. before a capture.
 cudaError_t prepare_ntt_cc(const hefx_params* p, NttMode mode);
 // Same kernels over an explicit list of rows (device array of RowDesc), persistent grid.

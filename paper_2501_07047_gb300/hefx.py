@@ -37,6 +37,8 @@ SIGNATURES = {
     "hefx_bconv_plan_destroy": (None, [_vp]),
     "hefx_basis_convert": (_i32, [_vp, _vp, _vp, _vp, _sz, _i32, _vp]),
     "hefx_stream_check": (_i32, [_vp, _vp, _vp]),
+    "hefx_vec_mod_mul": (_i32, [_vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "hefx_tensor_product": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "hefx_batch_plan_create": (_i32, [_vp, _vp, _sz, _i32, ctypes.POINTER(_vp)]),
     "hefx_batch_plan_destroy": (None, [_vp]),
     "hefx_batch_polymul": (_i32, [_vp, _vp, _vp]),
@@ -168,6 +170,15 @@ def hefx_basis_convert(ctx, plan, d_in, d_out, batch, path="auto", stream=None) 
 
 def hefx_stream_check(ctx, params, stream=None) -> None:
     _check(ctx, load().hefx_stream_check(ctx, params, _stream(stream)))
+
+
+def hefx_vec_mod_mul(ctx, params, x, y, z, batch, stream=None) -> None:
+    _check(ctx, load().hefx_vec_mod_mul(ctx, params, _ptr(x), _ptr(y), _ptr(z), batch, _stream(stream)))
+
+
+def hefx_tensor_product(ctx, params, a0, a1, b0, b1, d0, d1, d2, batch, stream=None) -> None:
+    _check(ctx, load().hefx_tensor_product(ctx, params, _ptr(a0), _ptr(a1), _ptr(b0), _ptr(b1), _ptr(d0), _ptr(d1),
+                                           _ptr(d2), batch, _stream(stream)))
 
 
 def hefx_batch_plan_create(ctx, jobs, path="auto") -> int:

@@ -1,0 +1,282 @@
+"""Continuous-batching server for ciphertext-multiply requests on one GPU.
+
+A request carries two ciphertexts (a0, a1), (b0, b1) of an RNS polynomial ring (degree N,
+L limbs of 28-bit primes) in evaluation form and asks for the HE-Mult front half that the
+hefx kernels cover (Sec. III, HE-Mult; Sec. V-B: NTT/INTT/BConv dominate it):
+
+    d0 = a0 o b0,  d1 = a0 o b1 + a1 o b0,  d2 = a1 o b1          (tensor product)
+    c  = INTT(d2)                                                   (to coefficients)
+    p  = BConv_{Q -> P}(c) over 8 special 30-bit primes, then NTT(p) (ModUp of d2)
+    e_k = (d2 | p) o key_k  over the L + 8 limbs of Q u P, k = 0, 1 (key products)
+
+and returns (d0, d1, e0, e1).  Key material is synthetic and seeded per shape.
+
+Serving policy
+ - Requests wait in arrival order.  One is admitted as soon as its device memory
+   (inputs, outputs and temporaries, all device-resident while it runs) fits in the
+   remaining budget and a slot is free; a request that can never fit is rejected.
+ - Each admitted request is enqueued on its own CUDA stream out of a small pool, so
+   requests that arrive while others are running overlap on the device.
+ - Completion is observed through a CUDA event; the outputs are read back to pinned host
+   memory, the request's memory returns to the budget and its latency
+   (completion - arrival) is recorded.
+
+The admission and budget logic is device-independent (`Admission`) and is tested on the
+CPU; `GpuExecutor` runs the stages through the hefx C ABI.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import time
+
+import numpy as np
+
+from . import inputs
+
+N_SPECIAL = 8  # auxiliary primes P of the key-switching basis
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    logn: int
+    L: int
+    arrival: float           # seconds since the start of the run
+    variant: int = 0         # which pre-generated input set to use
+    admitted: float = -1.0
+    completed: float = -1.0
+    status: str = "pending"  # pending | running | done | rejected
+    outputs: tuple = ()
+
+
+def request_bytes(logn: int, L: int) -> int:
+    """Device bytes of one request: 4 input, 2 + 2 output and 2 temporary limbs-sets over Q,
+    2 output and 1 temporary limb-sets over P (uint32 residues)."""
+    n = 1 << logn
+    return 4 * n * (10 * L + 3 * N_SPECIAL)
+
+
+class Admission:
+    """FIFO admission against a device-memory budget and a slot limit."""
+
+    def __init__(self, budget_bytes: int, max_slots: int):
+        self.budget = int(budget_bytes)
+        self.max_slots = int(max_slots)
+        self.in_use = 0
+        self.active = 0
+        self.high_water = 0
+        self.queue = collections.deque()
+
+    def submit(self, req: Request) -> None:
+        if request_bytes(req.logn, req.L) > self.budget:
+            req.status = "rejected"
+            return
+        self.queue.append(req)
+
+    def admit(self):
+        """Yields the requests that can start now, in arrival order (head-of-line blocking)."""
+        while self.queue and self.active < self.max_slots:
+            need = request_bytes(self.queue[0].logn, self.queue[0].L)
+            if self.in_use + need > self.budget:
+                break
+            req = self.queue.popleft()
+            self.in_use += need
+            self.active += 1
+            self.high_water = max(self.high_water, self.in_use)
+            req.status = "running"
+            yield req
+
+    def release(self, req: Request) -> None:
+        self.in_use -= request_bytes(req.logn, req.L)
+        self.active -= 1
+        assert self.in_use >= 0 and self.active >= 0
+
+
+class GpuExecutor:
+    """Runs requests through the hefx C ABI on a pool of CUDA streams."""
+
+    def __init__(self, ctx: int, nstreams: int = 8, seed: int = 5, variants: int = 2):
+        import torch
+
+        from . import hefx
+        self.torch, self.hefx = torch, hefx
+        self.ctx = ctx
+        self.streams = [torch.cuda.Stream() for _ in range(nstreams)]
+        self.next_stream = 0
+        self.seed = seed
+        self.variants = variants
+        self.shapes = {}
+        self.pools = {}
+        self.pparams_cache = {}
+        self.qprimes = inputs.source_primes(36)
+        self.pprimes = inputs.special_primes(N_SPECIAL)
+
+    # ---------------------------------------------------------------- per-shape resources
+    def pool(self, logn: int):
+        """Inputs and keys for ring degree N over all 36 Q limbs (+ 8 P limbs); a request with
+        L limbs uses the first L rows, which are uniform residues of q_0 .. q_{L-1}."""
+        if logn in self.pools:
+            return self.pools[logn]
+        torch = self.torch
+        n, LQ = 1 << logn, len(self.qprimes)
+        ks = inputs.derive_seed(self.seed, 1000, logn)
+
+        def dev(arr):
+            return torch.from_numpy(np.ascontiguousarray(arr).view(np.int32).copy()).cuda()
+
+        pl = {
+            "kQ": [dev(inputs.residue_tensor(inputs.derive_seed(ks, k, 0), 1, self.qprimes, n)[0]) for k in range(2)],
+            "kP": [dev(inputs.residue_tensor(inputs.derive_seed(ks, k, 1), 1, self.pprimes, n)[0]) for k in range(2)],
+            "host_in": [],
+        }
+        for v in range(self.variants):
+            sv = inputs.derive_seed(self.seed, 2000, logn, v)
+            arrs = [inputs.residue_tensor(inputs.derive_seed(sv, c), 1, self.qprimes, n)[0] for c in range(4)]
+            pl["host_in"].append([torch.from_numpy(a.view(np.int32).copy()).pin_memory() for a in arrs])
+        assert all(a.shape[0] == LQ for a in pl["host_in"][0])
+        self.pools[logn] = pl
+        return pl
+
+    def shape(self, logn: int, L: int):
+        key = (logn, L)
+        if key in self.shapes:
+            return self.shapes[key]
+        hefx = self.hefx
+        qs = self.qprimes[:L]
+        res = {
+            "pQ": hefx.hefx_params_create(self.ctx, logn, qs),
+            "pP": self.pparams(logn),
+            "bc": hefx.hefx_bconv_plan_create(self.ctx, logn, qs, self.pprimes),
+        }
+        self.shapes[key] = res
+        return res
+
+    def pparams(self, logn: int):
+        if logn not in self.pparams_cache:
+            self.pparams_cache[logn] = self.hefx.hefx_params_create(self.ctx, logn, self.pprimes)
+        return self.pparams_cache[logn]
+
+    def warm(self, logn: int, L: int) -> None:
+        self.pool(logn)
+        self.shape(logn, L)
+
+    # ---------------------------------------------------------------- request lifecycle
+    def launch(self, req: Request):
+        torch, hefx = self.torch, self.hefx
+        res = self.shape(req.logn, req.L)
+        pl = self.pool(req.logn)
+        n, L = 1 << req.logn, req.L
+        s = self.streams[self.next_stream]
+        self.next_stream = (self.next_stream + 1) % len(self.streams)
+        with torch.cuda.stream(s):
+            q = torch.empty((10 * L + 3 * N_SPECIAL, n), dtype=torch.int32, device="cuda")
+            a0, a1, b0, b1 = (q[i * L:(i + 1) * L] for i in range(4))
+            d0, d1, d2, c = (q[(4 + i) * L:(5 + i) * L] for i in range(4))
+            e0q, e1q = q[8 * L:9 * L], q[9 * L:10 * L]
+            base = 10 * L
+            p, e0p, e1p = (q[base + i * N_SPECIAL: base + (i + 1) * N_SPECIAL] for i in range(3))
+            for dst, src in zip((a0, a1, b0, b1), pl["host_in"][req.variant % self.variants]):
+                dst.copy_(src[:L], non_blocking=True)
+            st = s.cuda_stream
+            hefx.hefx_tensor_product(self.ctx, res["pQ"], a0, a1, b0, b1, d0, d1, d2, 1, st)
+            c.copy_(d2)
+            hefx.hefx_ntt_inv(self.ctx, res["pQ"], c, 1, "cudacore", st)
+            hefx.hefx_basis_convert(self.ctx, res["bc"], c, p, 1, "auto", st)
+            hefx.hefx_ntt_fwd(self.ctx, res["pP"], p, 1, "cudacore", st)
+            hefx.hefx_vec_mod_mul(self.ctx, res["pQ"], d2, pl["kQ"][0][:L], e0q, 1, st)
+            hefx.hefx_vec_mod_mul(self.ctx, res["pQ"], d2, pl["kQ"][1][:L], e1q, 1, st)
+            hefx.hefx_vec_mod_mul(self.ctx, res["pP"], p, pl["kP"][0], e0p, 1, st)
+            hefx.hefx_vec_mod_mul(self.ctx, res["pP"], p, pl["kP"][1], e1p, 1, st)
+            out = torch.empty((4 * L + 2 * N_SPECIAL, n), dtype=torch.int32, pin_memory=True)
+            out[0:L].copy_(d0, non_blocking=True)
+            out[L:2 * L].copy_(d1, non_blocking=True)
+            out[2 * L:3 * L].copy_(e0q, non_blocking=True)
+            out[3 * L:4 * L].copy_(e1q, non_blocking=True)
+            out[4 * L:4 * L + N_SPECIAL].copy_(e0p, non_blocking=True)
+            out[4 * L + N_SPECIAL:].copy_(e1p, non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(s)
+        return {"ev": ev, "buf": q, "out": out, "stream": s}
+
+    def done(self, handle) -> bool:
+        return handle["ev"].query()
+
+    def outputs(self, req: Request, handle):
+        L = req.L
+        o = handle["out"].numpy().view(np.uint32)
+        return (o[0:L].copy(), o[L:2 * L].copy(), np.concatenate([o[2 * L:3 * L], o[4 * L:4 * L + N_SPECIAL]]),
+                np.concatenate([o[3 * L:4 * L], o[4 * L + N_SPECIAL:]]))
+
+    def inputs_of(self, req: Request):
+        """Host copies of the request's four input polynomials and its keys (for checks)."""
+        pl = self.pool(req.logn)
+        ins = [t[:req.L].numpy().view(np.uint32) for t in pl["host_in"][req.variant % self.variants]]
+        keys = [np.concatenate([pl["kQ"][k][:req.L].cpu().numpy().view(np.uint32),
+                                pl["kP"][k].cpu().numpy().view(np.uint32)]) for k in range(2)]
+        return ins, keys
+
+    def close(self):
+        for res in self.shapes.values():
+            self.hefx.hefx_bconv_plan_destroy(res["bc"])
+            self.hefx.hefx_params_destroy(res["pQ"])
+        for p in self.pparams_cache.values():
+            self.hefx.hefx_params_destroy(p)
+        self.shapes, self.pparams_cache, self.pools = {}, {}, {}
+
+
+def serve(requests, executor, budget_bytes: int = 40 << 30, max_slots: int = 512, keep_outputs: bool = False):
+    """Runs the requests (sorted by arrival) to completion in real time; returns stats."""
+    requests = sorted(requests, key=lambda r: r.arrival)
+    adm = Admission(budget_bytes, max_slots)
+    running = []
+    t0 = time.perf_counter()
+    i = 0
+    max_active = 0
+    while i < len(requests) or adm.queue or running:
+        now = time.perf_counter() - t0
+        while i < len(requests) and requests[i].arrival <= now:
+            adm.submit(requests[i])
+            i += 1
+        for req in adm.admit():
+            req.admitted = time.perf_counter() - t0
+            running.append((req, executor.launch(req)))
+        max_active = max(max_active, len(running))
+        still = []
+        for req, h in running:
+            if executor.done(h):
+                req.completed = time.perf_counter() - t0
+                req.status = "done"
+                if keep_outputs:
+                    req.outputs = executor.outputs(req, h)
+                adm.release(req)
+            else:
+                still.append((req, h))
+        running = still
+        if not running and not adm.queue and i < len(requests):
+            wait = requests[i].arrival - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(min(wait, 0.01))
+    done = [r for r in requests if r.status == "done"]
+    lat = np.array([r.completed - r.arrival for r in done]) if done else np.zeros(1)
+    span = (max(r.completed for r in done) - min(r.arrival for r in done)) if done else 0.0
+    return {
+        "requests": len(requests), "completed": len(done),
+        "rejected": sum(r.status == "rejected" for r in requests),
+        "throughput_rps": len(done) / span if span > 0 else 0.0,
+        "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+        "max_active": max_active, "memory_high_water_bytes": adm.high_water,
+    }
+
+
+def poisson_requests(seed: int, count: int, rate_hz: float, logn_choices=(13, 14, 15, 16), lmin=8, lmax=36,
+                     variants: int = 2):
+    """Seeded Poisson arrivals with N and L drawn uniformly per request."""
+    t = inputs.poisson_arrivals(seed, count, rate_hz)
+    r = inputs.splitmix64(inputs.derive_seed(seed, 7), 3 * count)
+    out = []
+    for k in range(count):
+        logn = logn_choices[int(r[3 * k] % np.uint64(len(logn_choices)))]
+        L = lmin + int(r[3 * k + 1] % np.uint64(lmax - lmin + 1))
+        out.append(Request(k, logn, L, float(t[k]), variant=int(r[3 * k + 2] % np.uint64(variants))))
+    return out

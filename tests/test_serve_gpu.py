@@ -1,0 +1,83 @@
+"""Serving loop on the GPU: every result is the same alone and in the mix (bit-exact), and
+one request is checked stage by stage against the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2501_07047_gb300 import hefx, inputs
+from paper_2501_07047_gb300.serve import GpuExecutor, N_SPECIAL, Request, poisson_requests, request_bytes, serve
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = hefx.hefx_create(0)
+    yield c
+    hefx.hefx_destroy(c)
+
+
+def oracle_request(ex, req):
+    (a0, a1, b0, b1), (k0, k1) = ex.inputs_of(req)
+    qs = ex.qprimes[:req.L]
+    ps = ex.pprimes
+    q = np.array(qs, dtype=np.uint64)[:, None]
+    A0, A1, B0, B1 = (x.astype(np.uint64) for x in (a0, a1, b0, b1))
+    d0 = (A0 * B0) % q
+    d1 = ((A0 * B1) % q + (A1 * B0) % q) % q
+    d2 = (A1 * B1) % q
+    c = np.stack([oracle.intt(d2[i].astype(np.uint32), qs[i]) for i in range(req.L)])
+    p = oracle.bconv(c, qs, ps)
+    pn = np.stack([oracle.ntt(p[j], ps[j]) for j in range(N_SPECIAL)])
+    ext = np.concatenate([d2, pn.astype(np.uint64)])
+    mods = np.array(list(qs) + list(ps), dtype=np.uint64)[:, None]
+    e0 = (ext * k0.astype(np.uint64)) % mods
+    e1 = (ext * k1.astype(np.uint64)) % mods
+    return [x.astype(np.uint32) for x in (d0, d1, e0, e1)]
+
+
+def test_request_matches_oracle(ctx):
+    ex = GpuExecutor(ctx, nstreams=2, seed=9)
+    try:
+        req = Request(0, 13, 8, 0.0, variant=1)
+        st = serve([req], ex, keep_outputs=True)
+        assert st["completed"] == 1
+        for got, exp in zip(req.outputs, oracle_request(ex, req)):
+            assert (got == exp).all()
+    finally:
+        ex.close()
+
+
+def test_alone_equals_mix(ctx):
+    ex = GpuExecutor(ctx, nstreams=8, seed=10)
+    try:
+        shapes = [(13, 8), (16, 36), (14, 20), (15, 11), (16, 9), (13, 30), (14, 8), (15, 36)]
+        alone = []
+        for k, (logn, L) in enumerate(shapes):
+            r = Request(k, logn, L, 0.0, variant=k % 2)
+            serve([r], ex, keep_outputs=True)
+            alone.append(r.outputs)
+        mix = [Request(k, logn, L, 0.0, variant=k % 2) for k, (logn, L) in enumerate(shapes)]
+        st = serve(mix, ex, keep_outputs=True, max_slots=8)
+        assert st["completed"] == len(shapes) and st["max_active"] >= 2
+        for r, ref in zip(mix, alone):
+            for got, exp in zip(r.outputs, ref):
+                assert (got == exp).all(), (r.rid, r.logn, r.L)
+    finally:
+        ex.close()
+
+
+def test_budget_limits_concurrency(ctx):
+    ex = GpuExecutor(ctx, nstreams=4, seed=11)
+    try:
+        reqs = poisson_requests(12, 30, rate_hz=5000.0, logn_choices=(13, 14), lmin=8, lmax=12)
+        for r in reqs:
+            ex.warm(r.logn, r.L)
+        budget = 2 * request_bytes(14, 12)
+        st = serve(reqs, ex, budget_bytes=budget, max_slots=64)
+        assert st["completed"] == 30 and st["memory_high_water_bytes"] <= budget
+        big = Request(99, 16, 36, 0.0)
+        st2 = serve([big], ex, budget_bytes=budget)
+        assert big.status == "rejected" and st2["rejected"] == 1
+    finally:
+        ex.close()
