@@ -113,6 +113,29 @@ hefx_status hefx_poly_mul(hefx_ctx* ctx, const hefx_params* params, const uint32
                           uint32_t* d_c, size_t batch, hefx_path path, void* stream);
 
 /*
+ * Same product as hefx_poly_mul on the tensor path, for callers that must not allocate
+ * device memory once they are running: code whose memory is planned up front (a fixed arena
+ * handed out by a host framework), or a latency-critical loop where a cudaMalloc could
+ * block on device-wide synchronization or fail under memory pressure.  hefx_poly_mul's
+ * tensor path allocates (and may grow) a workspace for the second factor's forward
+ * transform; this variant uses instead a fixed 8 MiB array compiled into the library
+ * (2^21 residues), which every GPU that loads the library keeps until the process exits.
+ * There is no counterpart in the paper: this is a deployment variant of the same math.
+ *  - Calls no cudaMalloc, cudaFree or allocating library routine.  The parameter set's
+ *    tensor tables must exist already: make one tensor-path call with `params` first
+ *    (e.g. hefx_poly_mul with HEFX_PATH_TENSOR), else HEFX_EUNSUPPORTED.
+ *  - batch * nlimbs * N must not exceed 2^21, else HEFX_EINVAL (split the batch).
+ *  - The first call on each device looks up the array's device address (with that device
+ *    current); make that first call before any stream capture.
+ *  - All calls share the one array and it keeps the last call's contents (each call writes
+ *    it fully before reading it, so nothing needs clearing).  Calls whose work overlaps on
+ *    the GPU (different streams, or different host threads) race on it: serialize them.
+ *  - Layout, aliasing and errors otherwise as for hefx_poly_mul.
+ */
+hefx_status hefx_poly_mul_noalloc(hefx_ctx* ctx, const hefx_params* params, const uint32_t* d_a,
+                                  const uint32_t* d_b, uint32_t* d_c, size_t batch, void* stream);
+
+/*
  * Basis-conversion plan from basis src[0..L) to basis dst[0..Lp) for limbs of
  * n = 2^log2n coefficients (App. B, BConv):
  *   out_{n,j} = sum_i [a_{n,i} * qhat_i^-1]_{q_i} * [qhat_i]_{p_j}  mod p_j,  qhat_i = Q / q_i.

@@ -498,6 +498,31 @@ hefx_status hefx_batch_polymul(hefx_ctx* ctx, hefx_batch_plan* plan, void* strea
     return HEFX_OK;
 }
 
+hefx_status hefx_poly_mul_noalloc(hefx_ctx* ctx, const hefx_params* p, const uint32_t* a, const uint32_t* b,
+                                  uint32_t* c, size_t batch, void* stream) {
+    hefx_status st;
+    if ((st = check_ntt_args(ctx, p, a, "d_a")) != HEFX_OK) return st;
+    if ((st = check_ntt_args(ctx, p, b, "d_b")) != HEFX_OK) return st;
+    if ((st = check_ntt_args(ctx, p, c, "d_c")) != HEFX_OK) return st;
+    if ((st = use_device(ctx)) != HEFX_OK) return st;
+    if (!tc_supported(p))
+        return fail(ctx, HEFX_EUNSUPPORTED, "tensor path not available for N = 2^%u with these moduli", p->log2n);
+    if (!p->tc)
+        return fail(ctx, HEFX_EUNSUPPORTED,
+                    "tensor tables of these params are not built yet; make one tensor-path call "
+                    "(for example hefx_poly_mul with HEFX_PATH_TENSOR) before using the no-allocation variant");
+    const size_t words = batch * p->nlimbs * (size_t)p->n;
+    if (words > noalloc_scratch_words())
+        return fail(ctx, HEFX_EINVAL,
+                    "batch * nlimbs * N = %zu residues exceeds the %zu-residue static workspace of "
+                    "hefx_poly_mul_noalloc; split the batch",
+                    words, noalloc_scratch_words());
+    if (batch == 0) return HEFX_OK;
+    cudaError_t e = polymul_tc_noalloc(p, a, b, c, batch, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "hefx_poly_mul_noalloc");
+    return HEFX_OK;
+}
+
 hefx_status hefx_stream_check(hefx_ctx* ctx, const hefx_params* p, void* stream) {
     if (!ctx) return HEFX_EINVAL;
     if (!p || p->ctx != ctx) return fail(ctx, HEFX_EINVAL, "params is null or belongs to another context");

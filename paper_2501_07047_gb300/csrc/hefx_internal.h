@@ -130,6 +130,9 @@ cudaError_t launch_ntt_tc(const hefx_params* p, NttMode mode, const uint32_t* in
 cudaError_t launch_polymul_tc(hefx_params* p, const uint32_t* a, const uint32_t* b, uint32_t* c, size_t batch,
                               cudaStream_t stream);
 cudaError_t tc_check(const hefx_params* p, cudaStream_t stream, uint32_t* code);
+size_t noalloc_scratch_words();
+cudaError_t polymul_tc_noalloc(const hefx_params* p, const uint32_t* a, const uint32_t* b, uint32_t* c, size_t batch,
+                               cudaStream_t stream);
 cudaError_t launch_bconv_tc(const hefx_bconv_plan* plan, const uint32_t* in, uint32_t* out, size_t batch,
                             cudaStream_t stream);
 

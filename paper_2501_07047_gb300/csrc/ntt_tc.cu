@@ -31,6 +31,7 @@
 #include <cuda.h>
 
 #include <cstring>
+#include <mutex>
 #include <thread>
 #include <vector>
 
@@ -547,6 +548,57 @@ cudaError_t launch_polymul_tc(hefx_params* p, const uint32_t* a, const uint32_t*
         if (e == cudaSuccess) e = run_step(p, FWD3, OP_PLAIN, c, nullptr, c, batch, s);  // c = NTT(a)
         if (e == cudaSuccess) e = run_step(p, FWD1, OP_TW, b, nullptr, S, batch, s);
         if (e == cudaSuccess) e = run_step(p, FWD3, OP_HAD, S, c, c, batch, s);          // c = NTT(b) o c
+    }
+    if (e == cudaSuccess) e = run_step(p, INV1, OP_TW, c, nullptr, c, batch, s);
+    if (e == cudaSuccess) e = run_step(p, INV3, OP_PLAIN, c, nullptr, c, batch, s);
+    return e;
+}
+
+// ------------------------------------------------------------------ no-allocation product
+// Workspace of hefx_poly_mul_noalloc: a fixed device array in the library image, so that
+// call never allocates.  Every device that loads the library holds these bytes until the
+// process exits; every call on a device shares them.
+constexpr size_t kNoallocScratchWords = (size_t)1 << 21;  // 8 MiB
+static __device__ __align__(256) uint32_t g_noalloc_scratch[kNoallocScratchWords];
+
+namespace {
+// Device address of g_noalloc_scratch per device ordinal, looked up once with that device
+// current (the host-side name is only a stand-in for the symbol, not a device address).
+std::mutex g_noalloc_mu;
+uint32_t* g_noalloc_ptr[128] = {};
+}  // namespace
+
+size_t noalloc_scratch_words() { return kNoallocScratchWords; }
+
+cudaError_t polymul_tc_noalloc(const hefx_params* p, const uint32_t* a, const uint32_t* b, uint32_t* c, size_t batch,
+                               cudaStream_t s) {
+    if (batch == 0) return cudaSuccess;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+    uint32_t* S;
+    {
+        std::lock_guard<std::mutex> g(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void* ptr = nullptr;
+            e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+            if (e != cudaSuccess) return e;
+            g_noalloc_ptr[dev] = static_cast<uint32_t*>(ptr);
+        }
+        S = g_noalloc_ptr[dev];
+    }
+    // the step sequence of the tensor-path product, with the static array as the workspace;
+    // S is fully written (forward step 1) before it is read, so nothing needs clearing
+    if (a == b) {
+        e = run_step(p, FWD1, OP_TW, a, nullptr, S, batch, s);
+        if (e == cudaSuccess) e = run_step(p, FWD3, OP_SQUARE, S, nullptr, c, batch, s);
+    } else {
+        if (c == b) std::swap(a, b);
+        e = run_step(p, FWD1, OP_TW, a, nullptr, c, batch, s);
+        if (e == cudaSuccess) e = run_step(p, FWD3, OP_PLAIN, c, nullptr, c, batch, s);
+        if (e == cudaSuccess) e = run_step(p, FWD1, OP_TW, b, nullptr, S, batch, s);
+        if (e == cudaSuccess) e = run_step(p, FWD3, OP_HAD, S, c, c, batch, s);
     }
     if (e == cudaSuccess) e = run_step(p, INV1, OP_TW, c, nullptr, c, batch, s);
     if (e == cudaSuccess) e = run_step(p, INV3, OP_PLAIN, c, nullptr, c, batch, s);

@@ -33,6 +33,7 @@ SIGNATURES = {
     "hefx_ntt_fwd": (_i32, [_vp, _vp, _vp, _sz, _i32, _vp]),
     "hefx_ntt_inv": (_i32, [_vp, _vp, _vp, _sz, _i32, _vp]),
     "hefx_poly_mul": (_i32, [_vp, _vp, _vp, _vp, _vp, _sz, _i32, _vp]),
+    "hefx_poly_mul_noalloc": (_i32, [_vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "hefx_bconv_plan_create": (_i32, [_vp, _u32, _u32p, _u32, _u32p, _u32, ctypes.POINTER(_vp)]),
     "hefx_bconv_plan_destroy": (None, [_vp]),
     "hefx_basis_convert": (_i32, [_vp, _vp, _vp, _vp, _sz, _i32, _vp]),
@@ -151,6 +152,12 @@ def hefx_ntt_inv(ctx, params, data, batch, path="cudacore", stream=None) -> None
 
 def hefx_poly_mul(ctx, params, a, b, c, batch, path="cudacore", stream=None) -> None:
     _check(ctx, load().hefx_poly_mul(ctx, params, _ptr(a), _ptr(b), _ptr(c), batch, _path(path), _stream(stream)))
+
+
+def hefx_poly_mul_noalloc(ctx, params, a, b, c, batch, stream=None) -> None:
+    """Tensor-path product whose workspace is a fixed array inside the library (no device
+    allocation); see include/hefx.h for the size limit and the sharing rules."""
+    _check(ctx, load().hefx_poly_mul_noalloc(ctx, params, _ptr(a), _ptr(b), _ptr(c), batch, _stream(stream)))
 
 
 def hefx_bconv_plan_create(ctx: int, log2n: int, src, dst) -> int:
