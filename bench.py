@@ -281,11 +281,112 @@ def run_gpu(args):
     if cpu_baseline:
         line["cpu_baseline"] = cpu_baseline
     hefx.hefx_params_destroy(params)
+    del data, data0, flush
+    torch.cuda.empty_cache()
+    if not args.no_extras and world == 1:
+        line["extra"] = {"bconv_config3": bench_bconv(ctx, args), "batch_config4": bench_batch(ctx, args)}
+        if args.serve:
+            line["extra"]["serving_config5"] = bench_serving(ctx, args)
     hefx.hefx_destroy(ctx)
     if rank == 0:
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
+
+
+def _events_time(fn, steps, flush, stream):
+    import torch
+    ms = []
+    for k in range(steps):
+        flush.fill_(k)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return statistics.median(ms)
+
+
+def bench_bconv(ctx, args):
+    """RNS basis conversion 16 x 24 limbs x 2^16 -> 8 limbs, both paths."""
+    import torch
+    from paper_2501_07047_gb300 import hefx, inputs
+    B, Lq, Lp, logn = 16, 24, 8, 16
+    n = 1 << logn
+    qs, ps = inputs.source_primes(Lq), inputs.special_primes(Lp)
+    plan = hefx.hefx_bconv_plan_create(ctx, logn, qs, ps)
+    x = inputs.residue_tensor(inputs.derive_seed(3, 0), B, qs, n)
+    dx = torch.from_numpy(x.view(np.int32).copy()).cuda()
+    dy = torch.empty((B, Lp, n), dtype=torch.int32, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    s = torch.cuda.current_stream()
+    hbm, _, _, src = peaks()
+    out = {"workload": "BConv 16 x 24 limbs (28-bit) x 2^16 -> 8 limbs (30-bit)", "bytes_per_call": (Lq + Lp) * 4 * n * B}
+    ref = None
+    for path in ("cudacore", "tensor"):
+        hefx.hefx_basis_convert(ctx, plan, dx, dy, B, path, s)
+        torch.cuda.synchronize()
+        if ref is None:
+            ref = dy.clone()
+        assert torch.equal(dy, ref), "paths disagree"
+        for _ in range(3):
+            hefx.hefx_basis_convert(ctx, plan, dx, dy, B, path, s)
+        ms = _events_time(lambda: hefx.hefx_basis_convert(ctx, plan, dx, dy, B, path, s), args.steps, flush, s)
+        gbs = out["bytes_per_call"] / (ms / 1e3) / 1e9
+        out[path] = {"ms": round(ms, 5), "coeffs_per_s": round(B * n / (ms / 1e3), 1), "GB_s": round(gbs, 1),
+                     "hbm_frac": round(gbs / hbm, 4)}
+    out["peak"] = f"{hbm} GB/s ({src} hbm_gbs)"
+    hefx.hefx_bconv_plan_destroy(plan)
+    return out
+
+
+def bench_batch(ctx, args):
+    """256 uneven polynomial-product jobs, one graph launch per batch."""
+    import torch
+    from paper_2501_07047_gb300 import inputs
+    from paper_2501_07047_gb300.batch import UnevenBatch
+    shapes = inputs.uneven_jobs(inputs.derive_seed(4), 256)
+    batch = UnevenBatch(ctx, shapes, seed=4, fill=False)
+    try:
+        s = torch.cuda.Stream()
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+        with torch.cuda.stream(s):
+            for _ in range(3):
+                batch.run(s)
+            ms = _events_time(lambda: batch.run(s), max(5, args.steps // 4), flush, s)
+        cl = batch.coeff_limbs()
+        return {"workload": "256 jobs, N in {2^12..2^16}, L in [4, 32]; NTT(a), INTT(NTT(b) o NTT(a))",
+                "ms_per_batch": round(ms, 4), "jobs_per_s": round(256 / (ms / 1e3), 1),
+                "coeff_limbs_per_s": round(cl / (ms / 1e3), 1), "coeff_limbs": cl,
+                "hbm_bytes_per_batch": 20 * cl, "GB_s": round(20 * cl / (ms / 1e3) / 1e9, 1),
+                "launches_per_batch": 2 * len({l for l, _ in shapes}), "graph": True}
+    finally:
+        batch.close()
+
+
+def bench_serving(ctx, args):
+    """Poisson arrival-rate sweep of ciphertext-multiply requests, 40 GB admission budget."""
+    from paper_2501_07047_gb300.serve import GpuExecutor, poisson_requests, serve
+    ex = GpuExecutor(ctx, nstreams=8)
+    res = {"workload": "HE-Mult front half, N in {2^13..2^16}, L in [8, 36], 8 special primes", "budget_GB": 40}
+    try:
+        for rate in (100, 400, 1600):
+            reqs = poisson_requests(inputs_seed(5, rate), 120, rate)
+            for r in reqs:
+                ex.warm(r.logn, r.L)
+            serve(reqs[:8], ex)  # warm kernels on this request mix
+            reqs = poisson_requests(inputs_seed(5, rate), 120, rate)
+            st = serve(reqs, ex, budget_bytes=40 << 30)
+            res[f"rate_{rate}"] = {k: (round(v, 3) if isinstance(v, float) else v) for k, v in st.items()}
+    finally:
+        ex.close()
+    return res
+
+
+def inputs_seed(*parts):
+    from paper_2501_07047_gb300 import inputs
+    return inputs.derive_seed(*parts)
 
 
 def tensor_flops_per_limb_ntt() -> float:
@@ -343,6 +444,8 @@ def main():
     ap.add_argument("--impl", default="hefx", choices=["hefx", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the BConv and batch measurements")
+    ap.add_argument("--serve", action="store_true", help="also run the serving arrival-rate sweep")
     args = ap.parse_args()
     if args.impl == "reference":
         if args.steps > 5:

@@ -61,20 +61,26 @@ struct KArgs {
 
 // Row r's input / Hadamard operand / output and limb, from the descriptor list when there
 // is one, else from the contiguous [batch][L][N] layout.
-template <int N>
+// DESC is a compile-time switch so that the contiguous-layout kernels carry no descriptor code.
+template <int N, bool DESC>
 __device__ __forceinline__ const uint32_t* row_in(const KArgs& a, uint32_t r) {
-    return a.desc ? a.desc[r].in : a.in + (size_t)r * N;
+    if constexpr (DESC) return a.desc[r].in;
+    else return a.in + (size_t)r * N;
 }
-template <int N>
+template <int N, bool DESC>
 __device__ __forceinline__ const uint32_t* row_had(const KArgs& a, uint32_t r) {
-    return a.desc ? a.desc[r].had : a.had + (size_t)r * N;
+    if constexpr (DESC) return a.desc[r].had;
+    else return a.had + (size_t)r * N;
 }
-template <int N>
+template <int N, bool DESC>
 __device__ __forceinline__ uint32_t* row_out(const KArgs& a, uint32_t r) {
-    return a.desc ? a.desc[r].out : a.out + (size_t)r * N;
+    if constexpr (DESC) return a.desc[r].out;
+    else return a.out + (size_t)r * N;
 }
+template <bool DESC>
 __device__ __forceinline__ uint32_t row_limb(const KArgs& a, uint32_t r) {
-    return a.desc ? a.desc[r].limb : r % a.L;
+    if constexpr (DESC) return a.desc[r].limb;
+    else return r % a.L;
 }
 
 // Where a register pass takes its inputs and puts its outputs.
@@ -88,7 +94,7 @@ struct Seg {
 };
 
 // Loads the 2^R elements jb + k * 2^logs (k < 2^R) of local row `row` into x.
-template <int R, int LOGN, int logs, int SRC>
+template <int R, int LOGN, int logs, int SRC, bool DESC>
 __device__ __forceinline__ void load_elems(uint32_t (&x)[1 << R], const uint32_t* sm, const KArgs& a, const Seg& sg,
                                            int row, int jb, const LimbConst& lc, const uint2* tw) {
     using C = Cfg<LOGN>;
@@ -99,8 +105,8 @@ __device__ __forceinline__ void load_elems(uint32_t (&x)[1 << R], const uint32_t
     } else {
         const bool valid = row < sg.nrows;
         const uint32_t grow_r = valid ? sg.row0 + row : sg.row0;
-        const uint32_t* rin = row_in<N>(a, grow_r);
-        const uint32_t* rhad = SRC == SRC_GLOBAL_HAD ? row_had<N>(a, grow_r) : nullptr;
+        const uint32_t* rin = row_in<N, DESC>(a, grow_r);
+        const uint32_t* rhad = SRC == SRC_GLOBAL_HAD ? row_had<N, DESC>(a, grow_r) : nullptr;
         if constexpr (SRC == SRC_SPLIT0) {
             // first forward stage (pairs j, j + N/2) computed while loading: this CTA keeps
             // X + w Y (half 0) or X - w Y (half 1), w = psi^brv(1)
@@ -143,7 +149,7 @@ __device__ __forceinline__ void load_elems(uint32_t (&x)[1 << R], const uint32_t
     }
 }
 
-template <int R, int LOGN, int logs, int DST>
+template <int R, int LOGN, int logs, int DST, bool DESC>
 __device__ __forceinline__ void store_elems(const uint32_t (&x)[1 << R], uint32_t* sm, const KArgs& a, const Seg& sg,
                                             int row, int jb, uint32_t q) {
     using C = Cfg<LOGN>;
@@ -153,7 +159,7 @@ __device__ __forceinline__ void store_elems(const uint32_t (&x)[1 << R], uint32_
         for (int k = 0; k < (1 << R); ++k) sm[pad(row * C::m + jb + (k << logs))] = x[k];
     } else {
         if (row >= sg.nrows) return;
-        uint32_t* dst = row_out<N>(a, sg.row0 + row) + sg.gbase + jb;
+        uint32_t* dst = row_out<N, DESC>(a, sg.row0 + row) + sg.gbase + jb;
         if constexpr (logs == 0 && R >= 2) {
 #pragma unroll
             for (int k = 0; k < (1 << R); k += 4) {
@@ -241,7 +247,7 @@ __device__ __forceinline__ void inv_stages(uint32_t (&x)[1 << R], uint32_t gbase
 }
 
 // Forward register pass over stages s0 .. s0+R-1 of every sub-transform of the CTA.
-template <int R, int LOGN, int s0, int SRC, int DST>
+template <int R, int LOGN, int s0, int SRC, int DST, bool DESC>
 __device__ __forceinline__ void fwd_pass(uint32_t* sm, const Seg& sg, const KArgs& a) {
     using C = Cfg<LOGN>;
     constexpr int N = 1 << LOGN;
@@ -255,18 +261,18 @@ __device__ __forceinline__ void fwd_pass(uint32_t* sm, const Seg& sg, const KArg
         const int j_hi = uu >> logtl;
         const int jb = (j_hi << (logtl + R)) + j_lo;
         const uint32_t g0 = (sg.gbase >> (logtl + R)) + (uint32_t)j_hi;
-        const uint32_t limb = row_limb(a, row < sg.nrows ? sg.row0 + row : sg.row0);
+        const uint32_t limb = row_limb<DESC>(a, row < sg.nrows ? sg.row0 + row : sg.row0);
         const LimbConst& lc = a.lc[limb];
         const uint2* tw = a.tw_f + (size_t)limb * N;
         uint32_t x[1 << R];
-        load_elems<R, LOGN, logtl, SRC>(x, sm, a, sg, row, jb, lc, tw);
+        load_elems<R, LOGN, logtl, SRC, DESC>(x, sm, a, sg, row, jb, lc, tw);
         fwd_stages<R, LOGN, s0>(x, g0, tw, lc.q);
-        store_elems<R, LOGN, logtl, DST>(x, sm, a, sg, row, jb, lc.q);
+        store_elems<R, LOGN, logtl, DST, DESC>(x, sm, a, sg, row, jb, lc.q);
     }
 }
 
 // Inverse register pass over stages e0 .. e0+R-1.
-template <int R, int LOGN, int SCALE, int e0, int SRC, int DST>
+template <int R, int LOGN, int SCALE, int e0, int SRC, int DST, bool DESC>
 __device__ __forceinline__ void inv_pass(uint32_t* sm, const Seg& sg, const KArgs& a) {
     using C = Cfg<LOGN>;
     constexpr int N = 1 << LOGN;
@@ -278,20 +284,20 @@ __device__ __forceinline__ void inv_pass(uint32_t* sm, const Seg& sg, const KArg
         const int j_lo = uu & ((1 << e0) - 1);
         const int j_hi = uu >> e0;
         const int jb = (j_hi << (e0 + R)) + j_lo;
-        const uint32_t limb = row_limb(a, row < sg.nrows ? sg.row0 + row : sg.row0);
+        const uint32_t limb = row_limb<DESC>(a, row < sg.nrows ? sg.row0 + row : sg.row0);
         const LimbConst& lc = a.lc[limb];
         const uint2* tw = a.tw_i + (size_t)limb * N;
         uint32_t x[1 << R];
-        load_elems<R, LOGN, e0, SRC>(x, sm, a, sg, row, jb, lc, tw);
+        load_elems<R, LOGN, e0, SRC, DESC>(x, sm, a, sg, row, jb, lc, tw);
         inv_stages<R, LOGN, SCALE, e0>(x, sg.gbase, j_hi, tw, lc);
-        store_elems<R, LOGN, e0, DST>(x, sm, a, sg, row, jb, lc.q);
+        store_elems<R, LOGN, e0, DST, DESC>(x, sm, a, sg, row, jb, lc.q);
     }
 }
 
 // The polynomial product's middle: the forward pass over the smallest strides, the Hadamard
 // product with `had` (Montgomery, 2^-32 folded into the final scale) and the inverse pass
 // over the same strides, on the same registers.
-template <int R, int LOGN, int s0, int SRC, int DST>
+template <int R, int LOGN, int s0, int SRC, int DST, bool DESC>
 __device__ __forceinline__ void fwd_had_inv_pass(uint32_t* sm, const Seg& sg, const KArgs& a) {
     using C = Cfg<LOGN>;
     constexpr int N = 1 << LOGN;
@@ -303,13 +309,13 @@ __device__ __forceinline__ void fwd_had_inv_pass(uint32_t* sm, const Seg& sg, co
         const int j_hi = u & (nsub - 1);
         const int jb = j_hi << R;
         const uint32_t g0 = (sg.gbase >> R) + (uint32_t)j_hi;
-        const uint32_t limb = row_limb(a, row < sg.nrows ? sg.row0 + row : sg.row0);
+        const uint32_t limb = row_limb<DESC>(a, row < sg.nrows ? sg.row0 + row : sg.row0);
         const LimbConst& lc = a.lc[limb];
         uint32_t x[1 << R];
-        load_elems<R, LOGN, 0, SRC>(x, sm, a, sg, row, jb, lc, a.tw_f + (size_t)limb * N);
+        load_elems<R, LOGN, 0, SRC, DESC>(x, sm, a, sg, row, jb, lc, a.tw_f + (size_t)limb * N);
         fwd_stages<R, LOGN, s0>(x, g0, a.tw_f + (size_t)limb * N, lc.q);
         const bool valid = row < sg.nrows;
-        const uint4* hs = reinterpret_cast<const uint4*>(row_had<N>(a, valid ? sg.row0 + row : sg.row0) + sg.gbase + jb);
+        const uint4* hs = reinterpret_cast<const uint4*>(row_had<N, DESC>(a, valid ? sg.row0 + row : sg.row0) + sg.gbase + jb);
 #pragma unroll
         for (int k = 0; k < (1 << R); k += 4) {
             const uint4 h = valid ? __ldg(hs + k / 4) : make_uint4(0, 0, 0, 0);
@@ -319,7 +325,7 @@ __device__ __forceinline__ void fwd_had_inv_pass(uint32_t* sm, const Seg& sg, co
             x[k + 3] = mul_mont_lazy(x[k + 3], h.w, lc.q, lc.qinv_neg);
         }
         inv_stages<R, LOGN, 2, 0>(x, sg.gbase, j_hi, a.tw_i + (size_t)limb * N, lc);
-        store_elems<R, LOGN, 0, DST>(x, sm, a, sg, row, jb, lc.q);
+        store_elems<R, LOGN, 0, DST, DESC>(x, sm, a, sg, row, jb, lc.q);
     }
 }
 
@@ -330,38 +336,38 @@ __device__ __forceinline__ void sync_all() {
 }
 
 // Forward passes I .. nrest-1 (big strides), SMEM -> SMEM except the first (from global).
-template <int LOGN, int I, int s>
+template <int LOGN, int I, int s, bool DESC>
 __device__ __forceinline__ void fwd_big(uint32_t* sm, const Seg& sg, const KArgs& a) {
     using C = Cfg<LOGN>;
     if constexpr (I < C::nrest) {
         constexpr int r = C::big(I);
         constexpr int SRC = I == 0 ? (C::split ? SRC_SPLIT0 : SRC_GLOBAL) : SRC_SMEM;
-        fwd_pass<r, LOGN, s, SRC, DST_SMEM>(sm, sg, a);
+        fwd_pass<r, LOGN, s, SRC, DST_SMEM, DESC>(sm, sg, a);
         if constexpr (I == 0) sync_all<C::split>();  // every global read done before any write
         else __syncthreads();
-        fwd_big<LOGN, I + 1, s + r>(sm, sg, a);
+        fwd_big<LOGN, I + 1, s + r, DESC>(sm, sg, a);
     }
 }
 
 // Inverse passes over big strides, from I down to 0; the last one writes global memory
 // unless the transform is split (then the cross-CTA stage follows).
-template <int LOGN, int SCALE, int I, int e>
+template <int LOGN, int SCALE, int I, int e, bool DESC>
 __device__ __forceinline__ void inv_big(uint32_t* sm, const Seg& sg, const KArgs& a) {
     using C = Cfg<LOGN>;
     if constexpr (I >= 0) {
         constexpr int r = C::big(I);
         if constexpr (I == 0 && !C::split) {
-            inv_pass<r, LOGN, SCALE, e, SRC_SMEM, DST_GLOBAL>(sm, sg, a);
+            inv_pass<r, LOGN, SCALE, e, SRC_SMEM, DST_GLOBAL, DESC>(sm, sg, a);
         } else {
-            inv_pass<r, LOGN, C::split ? 0 : SCALE, e, SRC_SMEM, DST_SMEM>(sm, sg, a);
+            inv_pass<r, LOGN, C::split ? 0 : SCALE, e, SRC_SMEM, DST_SMEM, DESC>(sm, sg, a);
             __syncthreads();
-            inv_big<LOGN, SCALE, I - 1, e + r>(sm, sg, a);
+            inv_big<LOGN, SCALE, I - 1, e + r, DESC>(sm, sg, a);
         }
     }
 }
 
 // Last stage of a split inverse: pairs (j, j + N/2) live in the two CTAs of the cluster.
-template <int LOGN, int SCALE>
+template <int LOGN, int SCALE, bool DESC>
 __device__ __forceinline__ void split_last_stage(uint32_t* sm, const Seg& sg, const KArgs& a) {
     using C = Cfg<LOGN>;
     constexpr int N = 1 << LOGN;
@@ -369,11 +375,11 @@ __device__ __forceinline__ void split_last_stage(uint32_t* sm, const Seg& sg, co
     cluster.sync();
     const uint32_t* s0 = cluster.map_shared_rank(sm, 0);
     const uint32_t* s1 = cluster.map_shared_rank(sm, 1);
-    const LimbConst& lc = a.lc[row_limb(a, sg.row0)];
+    const LimbConst& lc = a.lc[row_limb<DESC>(a, sg.row0)];
     const uint32_t q = lc.q;
     const uint32_t s = SCALE == 1 ? lc.ninv : lc.ninvR, ssh = SCALE == 1 ? lc.ninv_sh : lc.ninvR_sh;
     const uint32_t w = SCALE == 1 ? lc.ninvw : lc.ninvRw, wsh = SCALE == 1 ? lc.ninvw_sh : lc.ninvRw_sh;
-    uint32_t* out = row_out<N>(a, sg.row0);
+    uint32_t* out = row_out<N, DESC>(a, sg.row0);
     for (int i = threadIdx.x * 4; i < N / 4; i += C::threads * 4) {
         const int j = sg.half * (N / 4) + i;
         uint32_t r0[4], r1[4];
@@ -390,7 +396,7 @@ __device__ __forceinline__ void split_last_stage(uint32_t* sm, const Seg& sg, co
     cluster.sync();  // keep this CTA's shared memory alive until the peer has read it
 }
 
-template <int LOGN, int MODE>
+template <int LOGN, int MODE, bool DESC>
 __device__ __forceinline__ void run_task(uint32_t* sm, const Seg& sg, const KArgs& a) {
     using C = Cfg<LOGN>;
     constexpr int RS = C::r_small;
@@ -400,36 +406,36 @@ __device__ __forceinline__ void run_task(uint32_t* sm, const Seg& sg, const KArg
 
     if constexpr (MODE == MODE_FWD) {
         if constexpr (C::nrest == 0) {
-            fwd_pass<RS, LOGN, S_FIRST, SRC0, DST_GLOBAL_REDUCE>(sm, sg, a);
+            fwd_pass<RS, LOGN, S_FIRST, SRC0, DST_GLOBAL_REDUCE, DESC>(sm, sg, a);
         } else {
-            fwd_big<LOGN, 0, S_FIRST>(sm, sg, a);
-            fwd_pass<RS, LOGN, S_SMALL, SRC_SMEM, DST_GLOBAL_REDUCE>(sm, sg, a);
+            fwd_big<LOGN, 0, S_FIRST, DESC>(sm, sg, a);
+            fwd_pass<RS, LOGN, S_SMALL, SRC_SMEM, DST_GLOBAL_REDUCE, DESC>(sm, sg, a);
         }
     } else if constexpr (MODE == MODE_INV || MODE == MODE_HAD_INV) {
         constexpr int SCALE = MODE == MODE_INV ? 1 : 2;
         constexpr int SRC = MODE == MODE_INV ? SRC_GLOBAL : SRC_GLOBAL_HAD;
         if constexpr (C::nrest == 0 && !C::split) {
-            inv_pass<RS, LOGN, SCALE, 0, SRC, DST_GLOBAL>(sm, sg, a);
+            inv_pass<RS, LOGN, SCALE, 0, SRC, DST_GLOBAL, DESC>(sm, sg, a);
         } else {
-            inv_pass<RS, LOGN, C::split ? 0 : SCALE, 0, SRC, DST_SMEM>(sm, sg, a);
+            inv_pass<RS, LOGN, C::split ? 0 : SCALE, 0, SRC, DST_SMEM, DESC>(sm, sg, a);
             __syncthreads();
-            inv_big<LOGN, SCALE, C::nrest - 1, RS>(sm, sg, a);
-            if constexpr (C::split) split_last_stage<LOGN, SCALE>(sm, sg, a);
+            inv_big<LOGN, SCALE, C::nrest - 1, RS, DESC>(sm, sg, a);
+            if constexpr (C::split) split_last_stage<LOGN, SCALE, DESC>(sm, sg, a);
         }
     } else {  // MODE_FWD_HAD_INV
         if constexpr (C::nrest == 0 && !C::split) {
-            fwd_had_inv_pass<RS, LOGN, S_SMALL, SRC0, DST_GLOBAL>(sm, sg, a);
+            fwd_had_inv_pass<RS, LOGN, S_SMALL, SRC0, DST_GLOBAL, DESC>(sm, sg, a);
         } else {
-            fwd_big<LOGN, 0, S_FIRST>(sm, sg, a);
-            fwd_had_inv_pass<RS, LOGN, S_SMALL, SRC_SMEM, DST_SMEM>(sm, sg, a);
+            fwd_big<LOGN, 0, S_FIRST, DESC>(sm, sg, a);
+            fwd_had_inv_pass<RS, LOGN, S_SMALL, SRC_SMEM, DST_SMEM, DESC>(sm, sg, a);
             __syncthreads();
-            inv_big<LOGN, 2, C::nrest - 1, RS>(sm, sg, a);
-            if constexpr (C::split) split_last_stage<LOGN, 2>(sm, sg, a);
+            inv_big<LOGN, 2, C::nrest - 1, RS, DESC>(sm, sg, a);
+            if constexpr (C::split) split_last_stage<LOGN, 2, DESC>(sm, sg, a);
         }
     }
 }
 
-template <int LOGN, int MODE>
+template <int LOGN, int MODE, bool DESC>
 __global__ void __launch_bounds__(Cfg<LOGN>::threads) ntt_cc_kernel(KArgs a) {
     using C = Cfg<LOGN>;
     extern __shared__ __align__(16) uint32_t sm[];
@@ -450,16 +456,16 @@ __global__ void __launch_bounds__(Cfg<LOGN>::threads) ntt_cc_kernel(KArgs a) {
             sg.nrows = (int)min((uint32_t)C::rows, a.rows - sg.row0);
         }
         sg.gbase = sg.half * C::m;
-        run_task<LOGN, MODE>(sm, sg, a);
+        run_task<LOGN, MODE, DESC>(sm, sg, a);
         __syncthreads();  // shared memory is reused by the next task
     }
 }
 
 // rows == 0: set the kernel's attributes only (done before a stream capture).
-template <int LOGN, int MODE>
+template <int LOGN, int MODE, bool DESC>
 cudaError_t launch_one(const KArgs& a, size_t rows, cudaStream_t stream) {
     using C = Cfg<LOGN>;
-    auto kern = ntt_cc_kernel<LOGN, MODE>;
+    auto kern = ntt_cc_kernel<LOGN, MODE, DESC>;
     static bool attr_done = false;  // per template instance; benign race (idempotent call)
     if (!attr_done) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::smem_bytes);
@@ -476,7 +482,9 @@ cudaError_t launch_one(const KArgs& a, size_t rows, cudaStream_t stream) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::threads, C::smem_bytes);
-    const size_t resident = (size_t)sms * (size_t)(per_sm > 0 ? per_sm : 1);
+    // row lists run persistent (a grid of resident CTAs walking the list); the contiguous
+    // layout launches one CTA (pair) per task
+    const size_t resident = DESC ? (size_t)sms * (size_t)(per_sm > 0 ? per_sm : 1) : (size_t)-1 / 4;
     if (C::split) {
         cfg.gridDim = dim3((unsigned)(2 * std::min(rows, resident / 2)));
         attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -491,14 +499,19 @@ cudaError_t launch_one(const KArgs& a, size_t rows, cudaStream_t stream) {
     return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
+template <int LOGN, bool DESC>
+cudaError_t launch_mode_d(NttMode mode, const KArgs& a, size_t rows, cudaStream_t s) {
+    switch (mode) {
+        case MODE_FWD: return launch_one<LOGN, MODE_FWD, DESC>(a, rows, s);
+        case MODE_INV: return launch_one<LOGN, MODE_INV, DESC>(a, rows, s);
+        case MODE_FWD_HAD_INV: return launch_one<LOGN, MODE_FWD_HAD_INV, DESC>(a, rows, s);
+        default: return launch_one<LOGN, MODE_HAD_INV, DESC>(a, rows, s);
+    }
+}
+
 template <int LOGN>
 cudaError_t launch_mode(NttMode mode, const KArgs& a, size_t rows, cudaStream_t s) {
-    switch (mode) {
-        case MODE_FWD: return launch_one<LOGN, MODE_FWD>(a, rows, s);
-        case MODE_INV: return launch_one<LOGN, MODE_INV>(a, rows, s);
-        case MODE_FWD_HAD_INV: return launch_one<LOGN, MODE_FWD_HAD_INV>(a, rows, s);
-        default: return launch_one<LOGN, MODE_HAD_INV>(a, rows, s);
-    }
+    return a.desc ? launch_mode_d<LOGN, true>(mode, a, rows, s) : launch_mode_d<LOGN, false>(mode, a, rows, s);
 }
 
 }  // namespace
@@ -522,7 +535,9 @@ cudaError_t launch_ntt_cc(const hefx_params* p, NttMode mode, const uint32_t* in
 }
 
 cudaError_t prepare_ntt_cc(const hefx_params* p, NttMode mode) {
+    static const RowDesc dummy = {};
     KArgs a = {};
+    a.desc = &dummy;  // selects the row-list kernels; rows == 0 sets attributes without launching
     return launch_dispatch(p, mode, a, 0, nullptr);
 }
 

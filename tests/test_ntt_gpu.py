@@ -228,3 +228,18 @@ def test_host_validation(ctx):
         hefx.hefx_ntt_fwd(ctx, p, d, 0)                     # batch 0: no-op
     finally:
         hefx.hefx_params_destroy(p)
+
+
+def test_autotune_sets_auto_path(ctx, tmp_path, monkeypatch):
+    from paper_2501_07047_gb300 import autotune
+    monkeypatch.setattr(autotune, "CACHE", str(tmp_path / "tune.json"))
+    primes = inputs.source_primes(4)
+    p = make_params(ctx, 16, primes)
+    try:
+        best = autotune.tune(ctx, p, 16, primes)
+        assert best in ("cudacore", "tensor")
+        assert (tmp_path / "tune.json").exists()
+        data = inputs.residue_tensor(inputs.derive_seed(12, 16), 2, primes, 1 << 16)
+        assert (run_fwd(ctx, p, data, "auto") == oracle.ntt_batch(data, primes)).all()
+    finally:
+        hefx.hefx_params_destroy(p)
