@@ -2,6 +2,7 @@
 //
 // Every entry point validates on the host, returns a status without launching anything
 // on error, and otherwise enqueues its kernels on the caller's stream.
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -118,6 +119,7 @@ hefx_status hefx_params_create(hefx_ctx* ctx, uint32_t log2n, const uint32_t* pr
     p->n = (uint32_t)n;
     p->nlimbs = nlimbs;
     p->primes.assign(primes, primes + nlimbs);
+    for (uint32_t i = 0; i < nlimbs; ++i) p->max_prime = std::max(p->max_prime, primes[i]);
     std::vector<LimbConst> lc(nlimbs);
     std::vector<uint2> twf((size_t)nlimbs * n), twi((size_t)nlimbs * n);
     std::vector<uint64_t> pw(n), pwi(n);

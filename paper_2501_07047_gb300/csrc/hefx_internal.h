@@ -63,6 +63,7 @@ struct hefx_params {
     uint32_t nlimbs = 0;
     std::vector<uint32_t> primes;
     std::vector<uint32_t> psi;        // per limb
+    uint32_t max_prime = 0;
     hefx::LimbConst* d_lc = nullptr;  // [nlimbs]
     uint2* d_tw_fwd = nullptr;        // [nlimbs][N]: (psi^brv_N(k), Shoup companion), k >= 1
     uint2* d_tw_inv = nullptr;        // [nlimbs][N]: (psi^-brv_N(k), Shoup companion)

@@ -1,0 +1,547 @@
+// CUDA-core negacyclic NTT / INTT (path a): radix-2 Cooley-Tukey forward and
+// Gentleman-Sande inverse (App. A, "Radix-2 Cooley-Tukey NTT"; the garbled loop indices of
+// the printed algorithm are replaced by the textbook ones), with lazy Shoup butterflies.
+//
+// GB300 mapping
+//  - One CTA holds a whole limb (N <= 2^15) or half of one (N = 2^16) in shared memory,
+//    so each limb is read from and written to HBM once per transform (512 KiB per
+//    N = 2^16 limb-NTT).  A CTA with N < 2^13 holds 2^13 / N limbs.
+//  - N = 2^16 uses a 2-CTA cluster.  Forward: the first stage (pairs j, j + N/2) is
+//    computed while loading, each CTA producing its own half (both read the whole limb,
+//    the second read hits L2).  Inverse: the last stage is exchanged through distributed
+//    shared memory.
+//  - Stages run in register passes of up to 5 stages (radix-32 sub-transforms); each pass
+//    reads and writes shared memory once.  Shared memory is padded by one word per 32 so
+//    that both strided and contiguous sub-transform accesses are bank-conflict free.
+//  - The forward output is in bit-reversed order with no shuffle (the twiddle table is
+//    stored in bit-reversed order, as MAT folds permutations into constants, Sec. IV-B).
+#pragma once
+#include <cooperative_groups.h>
+
+#include <algorithm>
+
+#include "hefx_internal.h"
+#include "modarith.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace hefx {
+namespace cc {
+
+__device__ __forceinline__ int pad(int j) { return j + (j >> 5); }
+
+template <int LOGN>
+struct Cfg {
+    static constexpr bool split = LOGN >= 16;
+    static constexpr int logm = split ? LOGN - 1 : LOGN;  // elements of one row segment
+    static constexpr int m = 1 << logm;
+    static constexpr int rows = logm >= 13 ? 1 : (1 << (13 - logm));  // row segments per CTA
+    static constexpr int elems = m * rows;
+    static constexpr int threads = elems >= (1 << 14) ? 512 : 256;
+    static constexpr int smem_bytes = (elems + elems / 32) * 4;
+    static constexpr int S = logm;                  // stages run inside the CTA
+    static constexpr int r_small = S < 5 ? S : 5;   // pass over the smallest strides
+    static constexpr int rest = S - r_small;
+    static constexpr int nrest = (rest + 4) / 5;
+    __host__ __device__ static constexpr int big(int i) {
+        return nrest == 0 ? 0 : rest / nrest + (i < rest % nrest ? 1 : 0);
+    }
+};
+
+struct KArgs {
+    const uint32_t* in;
+    const uint32_t* had;
+    uint32_t* out;
+    const uint2* tw_f;  // forward twiddles [L][N]
+    const uint2* tw_i;  // inverse twiddles [L][N]
+    const LimbConst* lc;
+    const RowDesc* desc;  // per-row pointers and limb (batched jobs), or null: [rows][N] layout
+    uint32_t rows;
+    uint32_t L;
+};
+
+// Row r's input / Hadamard operand / output and limb, from the descriptor list when there
+// is one, else from the contiguous [batch][L][N] layout.
+// F is a compile-time switch so that the contiguous-layout kernels carry no descriptor code.
+template <int N, int F>
+__device__ __forceinline__ const uint32_t* row_in(const KArgs& a, uint32_t r) {
+    if constexpr ((F & 1) != 0) return a.desc[r].in;
+    else return a.in + (size_t)r * N;
+}
+template <int N, int F>
+__device__ __forceinline__ const uint32_t* row_had(const KArgs& a, uint32_t r) {
+    if constexpr ((F & 1) != 0) return a.desc[r].had;
+    else return a.had + (size_t)r * N;
+}
+template <int N, int F>
+__device__ __forceinline__ uint32_t* row_out(const KArgs& a, uint32_t r) {
+    if constexpr ((F & 1) != 0) return a.desc[r].out;
+    else return a.out + (size_t)r * N;
+}
+template <int F>
+__device__ __forceinline__ uint32_t row_limb(const KArgs& a, uint32_t r) {
+    if constexpr ((F & 1) != 0) return a.desc[r].limb;
+    else return r % a.L;
+}
+
+// Where a register pass takes its inputs and puts its outputs.
+enum : int { SRC_SMEM = 0, SRC_GLOBAL = 1, SRC_SPLIT0 = 2, SRC_GLOBAL_HAD = 3 };
+enum : int { DST_SMEM = 0, DST_GLOBAL = 1, DST_GLOBAL_REDUCE = 2 };
+
+// The CTA's share of the batch: rows [row0, row0 + nrows) (or one half of row row0).
+struct Seg {
+    uint32_t row0, gbase, half;
+    int nrows;
+};
+
+// Canonical value of a forward output: from [0, 4q) (Harvey ranges) or [0, 16q) (lazy ranges).
+template <int F>
+__device__ __forceinline__ uint32_t reduce_out(uint32_t x, uint32_t q) {
+    if constexpr ((F & 2) != 0) x = csub(csub(x, 8 * q), 4 * q);
+    return csub(csub(x, 2 * q), q);
+}
+
+// Loads the 2^R elements jb + k * 2^logs (k < 2^R) of local row `row` into x.
+template <int R, int LOGN, int logs, int SRC, int F>
+__device__ __forceinline__ void load_elems(uint32_t (&x)[1 << R], const uint32_t* sm, const KArgs& a, const Seg& sg,
+                                           int row, int jb, const LimbConst& lc, const uint2* tw) {
+    using C = Cfg<LOGN>;
+    constexpr int N = 1 << LOGN;
+    if constexpr (SRC == SRC_SMEM) {
+#pragma unroll
+        for (int k = 0; k < (1 << R); ++k) x[k] = sm[pad(row * C::m + jb + (k << logs))];
+    } else {
+        const bool valid = row < sg.nrows;
+        const uint32_t grow_r = valid ? sg.row0 + row : sg.row0;
+        const uint32_t* rin = row_in<N, F>(a, grow_r);
+        const uint32_t* rhad = SRC == SRC_GLOBAL_HAD ? row_had<N, F>(a, grow_r) : nullptr;
+        if constexpr (SRC == SRC_SPLIT0) {
+            // first forward stage (pairs j, j + N/2) computed while loading: this CTA keeps
+            // X + w Y (half 0) or X - w Y (half 1), w = psi^brv(1)
+            const uint2 w = __ldg(&tw[1]);
+            const uint32_t q = lc.q;
+#pragma unroll
+            for (int k = 0; k < (1 << R); ++k) {
+                const size_t g = jb + (k << logs);
+                const uint32_t X = __ldg(rin + g), Y = __ldg(rin + g + N / 2);
+                const uint32_t t = mul_shoup_lazy(Y, w.x, w.y, q);
+                x[k] = sg.half ? X - t + 2 * q : X + t;
+            }
+        } else if constexpr (logs == 0 && R >= 2) {
+            const uint4* src = reinterpret_cast<const uint4*>(rin + sg.gbase + jb);
+            const uint4* hs = reinterpret_cast<const uint4*>(rhad + sg.gbase + jb);
+#pragma unroll
+            for (int k = 0; k < (1 << R); k += 4) {
+                uint4 v = valid ? __ldg(src + k / 4) : make_uint4(0, 0, 0, 0);
+                if constexpr (SRC == SRC_GLOBAL_HAD) {
+                    const uint4 h = valid ? __ldg(hs + k / 4) : make_uint4(0, 0, 0, 0);
+                    v.x = mul_mont_lazy(v.x, h.x, lc.q, lc.qinv_neg);
+                    v.y = mul_mont_lazy(v.y, h.y, lc.q, lc.qinv_neg);
+                    v.z = mul_mont_lazy(v.z, h.z, lc.q, lc.qinv_neg);
+                    v.w = mul_mont_lazy(v.w, h.w, lc.q, lc.qinv_neg);
+                }
+                x[k] = v.x;
+                x[k + 1] = v.y;
+                x[k + 2] = v.z;
+                x[k + 3] = v.w;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < (1 << R); ++k) {
+                const size_t g = sg.gbase + jb + (k << logs);
+                uint32_t v = valid ? __ldg(rin + g) : 0u;
+                if constexpr (SRC == SRC_GLOBAL_HAD) v = mul_mont_lazy(v, valid ? __ldg(rhad + g) : 0u, lc.q, lc.qinv_neg);
+                x[k] = v;
+            }
+        }
+    }
+}
+
+template <int R, int LOGN, int logs, int DST, int F>
+__device__ __forceinline__ void store_elems(const uint32_t (&x)[1 << R], uint32_t* sm, const KArgs& a, const Seg& sg,
+                                            int row, int jb, uint32_t q) {
+    using C = Cfg<LOGN>;
+    constexpr int N = 1 << LOGN;
+    if constexpr (DST == DST_SMEM) {
+#pragma unroll
+        for (int k = 0; k < (1 << R); ++k) sm[pad(row * C::m + jb + (k << logs))] = x[k];
+    } else {
+        if (row >= sg.nrows) return;
+        uint32_t* dst = row_out<N, F>(a, sg.row0 + row) + sg.gbase + jb;
+        if constexpr (logs == 0 && R >= 2) {
+#pragma unroll
+            for (int k = 0; k < (1 << R); k += 4) {
+                uint4 v = make_uint4(x[k], x[k + 1], x[k + 2], x[k + 3]);
+                if constexpr (DST == DST_GLOBAL_REDUCE) {
+                    v.x = reduce_out<F>(v.x, q);
+                    v.y = reduce_out<F>(v.y, q);
+                    v.z = reduce_out<F>(v.z, q);
+                    v.w = reduce_out<F>(v.w, q);
+                }
+                reinterpret_cast<uint4*>(dst)[k / 4] = v;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < (1 << R); ++k) dst[k << logs] = DST == DST_GLOBAL_REDUCE ? reduce_out<F>(x[k], q) : x[k];
+        }
+    }
+}
+
+// Lazy-range schedule of the forward transform for moduli below 2^28 (flag F & 2): values
+// may grow to 16q < 2^32, so the conditional subtraction of the butterfly's first input is
+// only needed where the bound entering a stage (in units of q) would pass 16 after the stage.
+// s_first / b_first: first stage run by the kernel and the bound of its inputs.
+__host__ __device__ constexpr int lazy_bound_in(int s_first, int b_first, int s) {
+    int b = b_first;
+    for (int t = s_first; t < s; ++t) b = (b + 2 > 16 ? 8 : b) + 2;
+    return b;
+}
+
+// R forward (Cooley-Tukey) stages s0 .. s0+R-1 on registers; stage s pairs j, j + N/2^(s+1)
+// and uses twiddle psi^brv(2^s + G) for group G (one load per group, reused by its
+// butterflies).  Without F & 2 every butterfly keeps Harvey's [0, 4q) range (q < 2^30).
+template <int R, int LOGN, int s0, int F>
+__device__ __forceinline__ void fwd_stages(uint32_t (&x)[1 << R], uint32_t g0, const uint2* tw, uint32_t q) {
+    // the smallest-stride pass reads the group-major part of the table
+    constexpr bool PERM = (s0 + R == LOGN);
+    constexpr bool LAZY = (F & 2) != 0;
+    constexpr int S_FIRST = LOGN >= 16 ? 1 : 0, B_FIRST = LOGN >= 16 ? 3 : 1;
+    const uint32_t two_q = 2 * q, eight_q = 8 * q;
+#pragma unroll
+    for (int v = 0; v < R; ++v) {
+        const int half = 1 << (R - 1 - v);
+        const bool corr = !LAZY || lazy_bound_in(S_FIRST, B_FIRST, s0 + v) + 2 > 16;
+        uint2 w = make_uint2(0, 0);
+#pragma unroll
+        for (int b = 0; b < (1 << (R - 1)); ++b) {
+            const int g = b >> (R - 1 - v);
+            const int k = (g << (R - v)) + (b & (half - 1));
+            if ((b & (half - 1)) == 0)
+                w = __ldg(&tw[PERM ? (1u << (s0 + v)) + ((uint32_t)g << s0) + g0 : (1u << (s0 + v)) + (g0 << v) + g]);
+            const uint32_t xa = !corr ? x[k] : (LAZY ? umin(x[k], x[k] - eight_q) : umin(x[k], x[k] - two_q));
+            const uint32_t t = mul_shoup_lazy(x[k + half], w.x, w.y, q);
+            x[k] = xa + t;
+            x[k + half] = xa - t + two_q;
+        }
+    }
+}
+
+// R inverse (Gentleman-Sande) stages e0 .. e0+R-1 on registers; stage e pairs j, j + 2^e with
+// twiddle psi^-brv(N/2^(e+1) + G).  SCALE folds N^-1 (1) or N^-1 2^32 (2) into stage LOGN-1.
+template <int R, int LOGN, int SCALE, int e0>
+__device__ __forceinline__ void inv_stages(uint32_t (&x)[1 << R], uint32_t gbase, int j_hi, const uint2* tw,
+                                           const LimbConst& lc) {
+    constexpr int N = 1 << LOGN;
+    constexpr bool PERM = (e0 == 0);  // the smallest-stride pass reads the group-major table part
+    const uint32_t q = lc.q, two_q = 2 * q;
+    const uint32_t J = (gbase >> R) + (uint32_t)j_hi;  // global index of the sub-transform (e0 == 0)
+#pragma unroll
+    for (int v = 0; v < R; ++v) {
+        const int e = e0 + v;
+        const int h = 1 << v;
+        if (SCALE && e == LOGN - 1) {
+            const uint32_t s = SCALE == 1 ? lc.ninv : lc.ninvR, ssh = SCALE == 1 ? lc.ninv_sh : lc.ninvR_sh;
+            const uint32_t w = SCALE == 1 ? lc.ninvw : lc.ninvRw, wsh = SCALE == 1 ? lc.ninvw_sh : lc.ninvRw_sh;
+#pragma unroll
+            for (int kk = 0; kk < (1 << (R - 1)); ++kk) {
+                const uint32_t X = x[kk], Y = x[kk + h];
+                const uint32_t s0v = mul_shoup_lazy(X + Y, s, ssh, q), s1v = mul_shoup_lazy(X - Y + two_q, w, wsh, q);
+                x[kk] = umin(s0v, s0v - q);
+                x[kk + h] = umin(s1v, s1v - q);
+            }
+            continue;
+        }
+        const uint32_t hbase = (uint32_t)(N >> (e + 1)) + (gbase >> (e + 1)) + ((uint32_t)j_hi << (R - v - 1));
+        uint2 w = make_uint2(0, 0);
+#pragma unroll
+        for (int b = 0; b < (1 << (R - 1)); ++b) {
+            const int g = b >> v;
+            const int k = (g << (v + 1)) + (b & (h - 1));
+            if ((b & (h - 1)) == 0)
+                w = __ldg(&tw[PERM ? (uint32_t)(N >> (e + 1)) + ((uint32_t)g << (LOGN - R)) + J : hbase + g]);
+            const uint32_t X = x[k], Y = x[k + h];
+            const uint32_t sum = X + Y;
+            x[k] = umin(sum, sum - two_q);
+            x[k + h] = mul_shoup_lazy(X - Y + two_q, w.x, w.y, q);
+        }
+    }
+}
+
+// Forward register pass over stages s0 .. s0+R-1 of every sub-transform of the CTA.
+template <int R, int LOGN, int s0, int SRC, int DST, int F>
+__device__ __forceinline__ void fwd_pass(uint32_t* sm, const Seg& sg, const KArgs& a) {
+    using C = Cfg<LOGN>;
+    constexpr int N = 1 << LOGN;
+    constexpr int logtl = LOGN - s0 - R;  // log2 of the smallest stride of the pass
+    constexpr int lognsub = C::logm - R;
+    constexpr int nsub = 1 << lognsub;
+    for (int u = threadIdx.x; u < C::rows * nsub; u += C::threads) {
+        const int row = u >> lognsub;
+        const int uu = u & (nsub - 1);
+        const int j_lo = uu & ((1 << logtl) - 1);
+        const int j_hi = uu >> logtl;
+        const int jb = (j_hi << (logtl + R)) + j_lo;
+        const uint32_t g0 = (sg.gbase >> (logtl + R)) + (uint32_t)j_hi;
+        const uint32_t limb = row_limb<F>(a, row < sg.nrows ? sg.row0 + row : sg.row0);
+        const LimbConst& lc = a.lc[limb];
+        const uint2* tw = a.tw_f + (size_t)limb * N;
+        uint32_t x[1 << R];
+        load_elems<R, LOGN, logtl, SRC, F>(x, sm, a, sg, row, jb, lc, tw);
+        fwd_stages<R, LOGN, s0, F>(x, g0, tw, lc.q);
+        store_elems<R, LOGN, logtl, DST, F>(x, sm, a, sg, row, jb, lc.q);
+    }
+}
+
+// Inverse register pass over stages e0 .. e0+R-1.
+template <int R, int LOGN, int SCALE, int e0, int SRC, int DST, int F>
+__device__ __forceinline__ void inv_pass(uint32_t* sm, const Seg& sg, const KArgs& a) {
+    using C = Cfg<LOGN>;
+    constexpr int N = 1 << LOGN;
+    constexpr int lognsub = C::logm - R;
+    constexpr int nsub = 1 << lognsub;
+    for (int u = threadIdx.x; u < C::rows * nsub; u += C::threads) {
+        const int row = u >> lognsub;
+        const int uu = u & (nsub - 1);
+        const int j_lo = uu & ((1 << e0) - 1);
+        const int j_hi = uu >> e0;
+        const int jb = (j_hi << (e0 + R)) + j_lo;
+        const uint32_t limb = row_limb<F>(a, row < sg.nrows ? sg.row0 + row : sg.row0);
+        const LimbConst& lc = a.lc[limb];
+        const uint2* tw = a.tw_i + (size_t)limb * N;
+        uint32_t x[1 << R];
+        load_elems<R, LOGN, e0, SRC, F>(x, sm, a, sg, row, jb, lc, tw);
+        inv_stages<R, LOGN, SCALE, e0>(x, sg.gbase, j_hi, tw, lc);
+        store_elems<R, LOGN, e0, DST, F>(x, sm, a, sg, row, jb, lc.q);
+    }
+}
+
+// The polynomial product's middle: the forward pass over the smallest strides, the Hadamard
+// product with `had` (Montgomery, 2^-32 folded into the final scale) and the inverse pass
+// over the same strides, on the same registers.
+template <int R, int LOGN, int s0, int SRC, int DST, int F>
+__device__ __forceinline__ void fwd_had_inv_pass(uint32_t* sm, const Seg& sg, const KArgs& a) {
+    using C = Cfg<LOGN>;
+    constexpr int N = 1 << LOGN;
+    constexpr int lognsub = C::logm - R;
+    constexpr int nsub = 1 << lognsub;
+    static_assert(LOGN - s0 - R == 0, "the fused pass covers the smallest strides");
+    for (int u = threadIdx.x; u < C::rows * nsub; u += C::threads) {
+        const int row = u >> lognsub;
+        const int j_hi = u & (nsub - 1);
+        const int jb = j_hi << R;
+        const uint32_t g0 = (sg.gbase >> R) + (uint32_t)j_hi;
+        const uint32_t limb = row_limb<F>(a, row < sg.nrows ? sg.row0 + row : sg.row0);
+        const LimbConst& lc = a.lc[limb];
+        uint32_t x[1 << R];
+        load_elems<R, LOGN, 0, SRC, F>(x, sm, a, sg, row, jb, lc, a.tw_f + (size_t)limb * N);
+        fwd_stages<R, LOGN, s0, F>(x, g0, a.tw_f + (size_t)limb * N, lc.q);
+        const bool valid = row < sg.nrows;
+        const uint4* hs = reinterpret_cast<const uint4*>(row_had<N, F>(a, valid ? sg.row0 + row : sg.row0) + sg.gbase + jb);
+#pragma unroll
+        for (int k = 0; k < (1 << R); k += 4) {
+            const uint4 h = valid ? __ldg(hs + k / 4) : make_uint4(0, 0, 0, 0);
+            x[k] = mul_mont_lazy(x[k], h.x, lc.q, lc.qinv_neg);
+            x[k + 1] = mul_mont_lazy(x[k + 1], h.y, lc.q, lc.qinv_neg);
+            x[k + 2] = mul_mont_lazy(x[k + 2], h.z, lc.q, lc.qinv_neg);
+            x[k + 3] = mul_mont_lazy(x[k + 3], h.w, lc.q, lc.qinv_neg);
+        }
+        inv_stages<R, LOGN, 2, 0>(x, sg.gbase, j_hi, a.tw_i + (size_t)limb * N, lc);
+        store_elems<R, LOGN, 0, DST, F>(x, sm, a, sg, row, jb, lc.q);
+    }
+}
+
+template <bool SPLIT>
+__device__ __forceinline__ void sync_all() {
+    if constexpr (SPLIT) cg::this_cluster().sync();
+    else __syncthreads();
+}
+
+// Forward passes I .. nrest-1 (big strides), SMEM -> SMEM except the first (from global).
+template <int LOGN, int I, int s, int F>
+__device__ __forceinline__ void fwd_big(uint32_t* sm, const Seg& sg, const KArgs& a) {
+    using C = Cfg<LOGN>;
+    if constexpr (I < C::nrest) {
+        constexpr int r = C::big(I);
+        constexpr int SRC = I == 0 ? (C::split ? SRC_SPLIT0 : SRC_GLOBAL) : SRC_SMEM;
+        fwd_pass<r, LOGN, s, SRC, DST_SMEM, F>(sm, sg, a);
+        if constexpr (I == 0) sync_all<C::split>();  // every global read done before any write
+        else __syncthreads();
+        fwd_big<LOGN, I + 1, s + r, F>(sm, sg, a);
+    }
+}
+
+// Inverse passes over big strides, from I down to 0; the last one writes global memory
+// unless the transform is split (then the cross-CTA stage follows).
+template <int LOGN, int SCALE, int I, int e, int F>
+__device__ __forceinline__ void inv_big(uint32_t* sm, const Seg& sg, const KArgs& a) {
+    using C = Cfg<LOGN>;
+    if constexpr (I >= 0) {
+        constexpr int r = C::big(I);
+        if constexpr (I == 0 && !C::split) {
+            inv_pass<r, LOGN, SCALE, e, SRC_SMEM, DST_GLOBAL, F>(sm, sg, a);
+        } else {
+            inv_pass<r, LOGN, C::split ? 0 : SCALE, e, SRC_SMEM, DST_SMEM, F>(sm, sg, a);
+            __syncthreads();
+            inv_big<LOGN, SCALE, I - 1, e + r, F>(sm, sg, a);
+        }
+    }
+}
+
+// Last stage of a split inverse: pairs (j, j + N/2) live in the two CTAs of the cluster.
+template <int LOGN, int SCALE, int F>
+__device__ __forceinline__ void split_last_stage(uint32_t* sm, const Seg& sg, const KArgs& a) {
+    using C = Cfg<LOGN>;
+    constexpr int N = 1 << LOGN;
+    cg::cluster_group cluster = cg::this_cluster();
+    cluster.sync();
+    const uint32_t* s0 = cluster.map_shared_rank(sm, 0);
+    const uint32_t* s1 = cluster.map_shared_rank(sm, 1);
+    const LimbConst& lc = a.lc[row_limb<F>(a, sg.row0)];
+    const uint32_t q = lc.q;
+    const uint32_t s = SCALE == 1 ? lc.ninv : lc.ninvR, ssh = SCALE == 1 ? lc.ninv_sh : lc.ninvR_sh;
+    const uint32_t w = SCALE == 1 ? lc.ninvw : lc.ninvRw, wsh = SCALE == 1 ? lc.ninvw_sh : lc.ninvRw_sh;
+    uint32_t* out = row_out<N, F>(a, sg.row0);
+    for (int i = threadIdx.x * 4; i < N / 4; i += C::threads * 4) {
+        const int j = sg.half * (N / 4) + i;
+        uint32_t r0[4], r1[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const uint32_t X = s0[pad(j + t)], Y = s1[pad(j + t)];
+            const uint32_t u0 = mul_shoup_lazy(X + Y, s, ssh, q), u1 = mul_shoup_lazy(X - Y + 2 * q, w, wsh, q);
+            r0[t] = umin(u0, u0 - q);
+            r1[t] = umin(u1, u1 - q);
+        }
+        *reinterpret_cast<uint4*>(out + j) = make_uint4(r0[0], r0[1], r0[2], r0[3]);
+        *reinterpret_cast<uint4*>(out + j + N / 2) = make_uint4(r1[0], r1[1], r1[2], r1[3]);
+    }
+    cluster.sync();  // keep this CTA's shared memory alive until the peer has read it
+}
+
+template <int LOGN, int MODE, int F>
+__device__ __forceinline__ void run_task(uint32_t* sm, const Seg& sg, const KArgs& a) {
+    using C = Cfg<LOGN>;
+    constexpr int RS = C::r_small;
+    constexpr int S_FIRST = C::split ? 1 : 0;     // first global stage run by the CTA
+    constexpr int S_SMALL = LOGN - RS;            // first stage of the smallest-stride pass
+    constexpr int SRC0 = C::split ? SRC_SPLIT0 : SRC_GLOBAL;
+
+    if constexpr (MODE == MODE_FWD) {
+        if constexpr (C::nrest == 0) {
+            fwd_pass<RS, LOGN, S_FIRST, SRC0, DST_GLOBAL_REDUCE, F>(sm, sg, a);
+        } else {
+            fwd_big<LOGN, 0, S_FIRST, F>(sm, sg, a);
+            fwd_pass<RS, LOGN, S_SMALL, SRC_SMEM, DST_GLOBAL_REDUCE, F>(sm, sg, a);
+        }
+    } else if constexpr (MODE == MODE_INV || MODE == MODE_HAD_INV) {
+        constexpr int SCALE = MODE == MODE_INV ? 1 : 2;
+        constexpr int SRC = MODE == MODE_INV ? SRC_GLOBAL : SRC_GLOBAL_HAD;
+        if constexpr (C::nrest == 0 && !C::split) {
+            inv_pass<RS, LOGN, SCALE, 0, SRC, DST_GLOBAL, F>(sm, sg, a);
+        } else {
+            inv_pass<RS, LOGN, C::split ? 0 : SCALE, 0, SRC, DST_SMEM, F>(sm, sg, a);
+            __syncthreads();
+            inv_big<LOGN, SCALE, C::nrest - 1, RS, F>(sm, sg, a);
+            if constexpr (C::split) split_last_stage<LOGN, SCALE, F>(sm, sg, a);
+        }
+    } else {  // MODE_FWD_HAD_INV
+        if constexpr (C::nrest == 0 && !C::split) {
+            fwd_had_inv_pass<RS, LOGN, S_SMALL, SRC0, DST_GLOBAL, F>(sm, sg, a);
+        } else {
+            fwd_big<LOGN, 0, S_FIRST, F>(sm, sg, a);
+            fwd_had_inv_pass<RS, LOGN, S_SMALL, SRC_SMEM, DST_SMEM, F>(sm, sg, a);
+            __syncthreads();
+            inv_big<LOGN, 2, C::nrest - 1, RS, F>(sm, sg, a);
+            if constexpr (C::split) split_last_stage<LOGN, 2, F>(sm, sg, a);
+        }
+    }
+}
+
+template <int LOGN, int MODE, int F>
+__global__ void __launch_bounds__(Cfg<LOGN>::threads) ntt_cc_kernel(KArgs a) {
+    using C = Cfg<LOGN>;
+    extern __shared__ __align__(16) uint32_t sm[];
+    // persistent: each CTA (or CTA pair) walks a strided sequence of tasks; a task is one
+    // row (split N) or C::rows rows
+    const uint32_t ntasks = C::split ? a.rows : (a.rows + C::rows - 1) / C::rows;
+    const uint32_t first = C::split ? blockIdx.x >> 1 : blockIdx.x;
+    const uint32_t stride = C::split ? gridDim.x >> 1 : gridDim.x;
+    for (uint32_t task = first; task < ntasks; task += stride) {
+        Seg sg;
+        if constexpr (C::split) {
+            sg.row0 = task;
+            sg.half = blockIdx.x & 1;
+            sg.nrows = 1;
+        } else {
+            sg.row0 = task * C::rows;
+            sg.half = 0;
+            sg.nrows = (int)min((uint32_t)C::rows, a.rows - sg.row0);
+        }
+        sg.gbase = sg.half * C::m;
+        run_task<LOGN, MODE, F>(sm, sg, a);
+        __syncthreads();  // shared memory is reused by the next task
+    }
+}
+
+// rows == 0: set the kernel's attributes only (done before a stream capture).
+template <int LOGN, int MODE, int F>
+cudaError_t launch_one(const KArgs& a, size_t rows, cudaStream_t stream) {
+    using C = Cfg<LOGN>;
+    auto kern = ntt_cc_kernel<LOGN, MODE, F>;
+    static bool attr_done = false;  // per template instance; benign race (idempotent call)
+    if (!attr_done) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::smem_bytes);
+        if (e != cudaSuccess) return e;
+        attr_done = true;
+    }
+    if (rows == 0) return cudaSuccess;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cfg.blockDim = dim3(C::threads);
+    cfg.dynamicSmemBytes = C::smem_bytes;
+    cfg.stream = stream;
+    int dev = 0, sms = 148, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::threads, C::smem_bytes);
+    // row lists run persistent (a grid of resident CTAs walking the list); the contiguous
+    // layout launches one CTA (pair) per task
+    const size_t resident = F ? (size_t)sms * (size_t)(per_sm > 0 ? per_sm : 1) : (size_t)-1 / 4;
+    if (C::split) {
+        cfg.gridDim = dim3((unsigned)(2 * std::min(rows, resident / 2)));
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+    } else {
+        cfg.gridDim = dim3((unsigned)std::min((rows + C::rows - 1) / C::rows, resident));
+    }
+    return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
+template <int LOGN, int F>
+cudaError_t launch_mode_d(NttMode mode, const KArgs& a, size_t rows, cudaStream_t s) {
+    switch (mode) {
+        case MODE_FWD: return launch_one<LOGN, MODE_FWD, F>(a, rows, s);
+        case MODE_INV: return launch_one<LOGN, MODE_INV, F & 1>(a, rows, s);
+        case MODE_FWD_HAD_INV: return launch_one<LOGN, MODE_FWD_HAD_INV, F>(a, rows, s);
+        default: return launch_one<LOGN, MODE_HAD_INV, F & 1>(a, rows, s);
+    }
+}
+
+// lazy: every modulus of the parameter set is below 2^28
+template <int LOGN>
+cudaError_t launch_mode(NttMode mode, const KArgs& a, size_t rows, cudaStream_t s, bool lazy) {
+    if (a.desc) return lazy ? launch_mode_d<LOGN, 3>(mode, a, rows, s) : launch_mode_d<LOGN, 1>(mode, a, rows, s);
+    return lazy ? launch_mode_d<LOGN, 2>(mode, a, rows, s) : launch_mode_d<LOGN, 0>(mode, a, rows, s);
+}
+
+// One LOGN range of the dispatcher, compiled in its own translation unit (build time).
+cudaError_t launch_range_a(int logn, NttMode mode, const KArgs& a, size_t rows, cudaStream_t s, bool lazy);
+cudaError_t launch_range_b(int logn, NttMode mode, const KArgs& a, size_t rows, cudaStream_t s, bool lazy);
+cudaError_t launch_range_c(int logn, NttMode mode, const KArgs& a, size_t rows, cudaStream_t s, bool lazy);
+cudaError_t launch_range_d(int logn, NttMode mode, const KArgs& a, size_t rows, cudaStream_t s, bool lazy);
+
+}  // namespace cc
+}  // namespace hefx
