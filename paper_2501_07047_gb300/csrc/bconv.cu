@@ -78,13 +78,21 @@ __global__ void __launch_bounds__(256) bconv_cc_kernel(const BConvConst* __restr
             uint64_t acc[kJChunk];
 #pragma unroll
             for (int jj = 0; jj < kJChunk; ++jj) acc[jj] = 0;
-            for (uint32_t i = 0; i < L; ++i) {
-                const uint32_t qi = c.q[i];
-                uint32_t bi = mul_shoup_lazy(__ldg(src + (size_t)i * n), c.qhat_inv[i], c.qhat_inv_sh[i], qi);
-                bi = csub(bi, qi);  // step 1: [a * qhat^-1]_{q_i}
+            // source residues in groups of 8 independent loads (latency overlap)
+            for (uint32_t i0 = 0; i0 < L; i0 += 8) {
+                uint32_t v[8];
 #pragma unroll
-                for (int jj = 0; jj < kJChunk; ++jj)
-                    acc[jj] += (uint64_t)bi * c.qhat_p[i * kBConvMaxLimbs + j0 + jj];
+                for (int u = 0; u < 8; ++u) v[u] = (i0 + u < L) ? __ldg(src + (size_t)(i0 + u) * n) : 0u;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const uint32_t i = i0 + u;
+                    if (i >= L) break;
+                    const uint32_t qi = c.q[i];
+                    const uint32_t bi = csub(mul_shoup_lazy(v[u], c.qhat_inv[i], c.qhat_inv_sh[i], qi), qi);  // step 1
+#pragma unroll
+                    for (int jj = 0; jj < kJChunk; ++jj)
+                        acc[jj] += (uint64_t)bi * c.qhat_p[i * kBConvMaxLimbs + j0 + jj];  // step 2
+                }
             }
 #pragma unroll
             for (int jj = 0; jj < kJChunk; ++jj) {
@@ -105,9 +113,11 @@ cudaError_t launch_bconv_cc(const hefx_bconv_plan* plan, const uint32_t* in, uin
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // one coefficient per thread, many short blocks: no ragged persistent tail
     size_t blocks = (total + 255) / 256;
-    const size_t cap = (size_t)sms * 8;
+    const size_t cap = (size_t)1 << 20;
     if (blocks > cap) blocks = cap;
+    (void)sms;
     bconv_cc_kernel<<<(unsigned)blocks, 256, 0, stream>>>(static_cast<const BConvConst*>(plan->d_const), in, out, n,
                                                            (uint32_t)batch);
     return cudaGetLastError();

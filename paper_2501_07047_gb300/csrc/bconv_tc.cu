@@ -8,9 +8,10 @@
 // 7 bits (b < q_i < 2^28), chunks 6 bits (constants < p_j < 2^30), and every partial sum is
 // below 4 * 64 * 127 * 63 < 2^23, so fp16 operands with fp32 accumulation are exact.
 //
-// GB300 mapping: a persistent kernel streams 128-coefficient tiles.  Four producer warps
-// read the L source residues of a tile (coalesced), apply step 1 and write the digits into a
-// double-buffered K-major 128B-swizzled A tile; one thread issues the tcgen05 MMAs against
+// GB300 mapping: a persistent kernel streams 128-coefficient tiles.  One thread keeps four
+// raw residue tiles (L rows x 128 coefficients) in flight with TMA; four producer warps apply
+// step 1 to a staged tile and write the digits into a double-buffered K-major 128B-swizzled
+// A tile; one thread issues the tcgen05 MMAs against
 // the constant B operand (resident in shared memory for the whole kernel) into one of two
 // TMEM accumulators; four epilogue warps merge, reduce mod p_j and store while the next tile
 // is being produced.  The operation is HBM-bound (16 B per source residue in, 4 per
@@ -29,7 +30,7 @@ namespace {
 
 constexpr int KO = 5;
 constexpr int THREADS = 384;  // warps 0-3 producer, 4-7 epilogue, 8 MMA
-constexpr int MAX_L = 64, MAX_LP = 32;
+constexpr int MAX_L = 48, MAX_LP = 32;  // MAX_L: 4 staged raw tiles fit in shared memory
 
 struct BcTcConst {
     uint32_t L, Lp, kpad, npad;      // K = 4L padded to 64, N = 8 columns per target limb, padded to 16
@@ -56,31 +57,42 @@ uint32_t sw128_offset_host(uint32_t row, uint32_t k) {
     return row * 128u + ((chunk ^ (row & 7u)) << 4) + ((k & 7u) << 1);
 }
 
-size_t smem_bytes(const BcTcPlan& tp) {
-    return 1024 + 2ull * 128 * tp.kpad * 2 + tp.bimage_bytes + 256;
+constexpr int RAW_STAGES = 4;
+
+// raw residue tile: L rows (source limbs) x 128 coefficients, uint32, dense
+size_t raw_bytes(uint32_t L) { return (size_t)L * 128 * 4; }
+
+size_t smem_bytes(const BcTcPlan& tp, uint32_t L) {
+    return 1024 + 2ull * 128 * tp.kpad * 2 + tp.bimage_bytes + RAW_STAGES * raw_bytes(L) + 256;
 }
 
+// Warp roles: 0-3 producers (step 1 + digits), 4-7 epilogue, 8 MMA issuer + TMEM owner,
+// 9 TMA issuer of raw residue tiles.
 __global__ void __launch_bounds__(THREADS, 1)
-    bconv_tc_kernel(const BcTcConst* __restrict__ gc, const uint8_t* __restrict__ bimage, uint32_t bimage_bytes,
-                    const uint32_t* __restrict__ in, uint32_t* __restrict__ out, uint32_t n, uint32_t batch,
-                    uint32_t tmem_cols, uint32_t* err) {
+    bconv_tc_kernel(const __grid_constant__ CUtensorMap in_map, const BcTcConst* __restrict__ gc,
+                    const uint8_t* __restrict__ bimage, uint32_t bimage_bytes, uint32_t* __restrict__ out, uint32_t n,
+                    uint32_t batch, uint32_t tmem_cols, uint32_t* err) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     __shared__ BcTcConst c;
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (uint32_t i = tid; i < sizeof(BcTcConst) / 4; i += THREADS)
         reinterpret_cast<uint32_t*>(&c)[i] = reinterpret_cast<const uint32_t*>(gc)[i];
-    const uint32_t kpad0 = gc->kpad;
+    const uint32_t kpad0 = gc->kpad, L0 = gc->L;
     const uint32_t abytes = 128 * kpad0 * 2;  // one A tile: 128 rows x K fp16
+    const uint32_t rbytes = L0 * 128 * 4;
     uint8_t* a_s[2] = {smem, smem + abytes};
     uint8_t* b_s = smem + 2 * abytes;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(b_s + bimage_bytes);
-    uint64_t* a_full = bars;       // [2] producer -> MMA
-    uint64_t* a_empty = bars + 2;  // [2] MMA -> producer
-    uint64_t* acc_full = bars + 4; // [2] MMA -> epilogue
-    uint64_t* acc_empty = bars + 6;// [2] epilogue -> MMA
+    uint8_t* raw_s = b_s + bimage_bytes;  // RAW_STAGES x rbytes (16-byte aligned)
+    uint64_t* bars = reinterpret_cast<uint64_t*>(raw_s + RAW_STAGES * rbytes);
+    uint64_t* a_full = bars;        // [2] producer -> MMA
+    uint64_t* a_empty = bars + 2;   // [2] MMA -> producer
+    uint64_t* acc_full = bars + 4;  // [2] MMA -> epilogue
+    uint64_t* acc_empty = bars + 6; // [2] epilogue -> MMA
     uint64_t* mma_done = bars + 8;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 9);
+    uint64_t* raw_full = bars + 9;                // [RAW_STAGES] TMA -> producer
+    uint64_t* raw_empty = raw_full + RAW_STAGES;  // [RAW_STAGES] producer -> TMA
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(raw_empty + RAW_STAGES);
 
     // constant B operand and zeroed A tiles (K padding stays zero for the whole kernel)
     for (uint32_t i = tid; i < bimage_bytes / 16; i += THREADS)
@@ -93,42 +105,59 @@ __global__ void __launch_bounds__(THREADS, 1)
             tc::mbar_init(&acc_full[s], 1);
             tc::mbar_init(&acc_empty[s], 128);
         }
+        for (int s = 0; s < RAW_STAGES; ++s) {
+            tc::mbar_init(&raw_full[s], 1);
+            tc::mbar_init(&raw_empty[s], 128);
+        }
         tc::mbar_init(mma_done, 1);
         tc::fence_mbar_init();
     }
     if (warp == 8) tc::tmem_alloc(tmem_slot, tmem_cols);
+    if (tid == 9 * 32) tc::prefetch_tmap(&in_map);
     tc::fence_proxy_async_smem();
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    const uint32_t L = c.L, Lp = c.Lp, kpad = c.kpad, npad = c.npad;
+    const uint32_t L = c.L, Lp = c.Lp, npad = c.npad;
     const uint32_t tiles_per_poly = n / 128;
     const uint32_t ntiles = tiles_per_poly * batch;
 
-    if (warp < 4) {  // ---- producer: step 1 and digit split
+    if (warp == 9) {  // ---- TMA issuer: raw residue tiles, RAW_STAGES in flight
+        if (lane == 0) {
+            uint32_t it = 0;
+            bool issued[RAW_STAGES];
+            uint32_t par[RAW_STAGES];
+            for (int s = 0; s < RAW_STAGES; ++s) issued[s] = false;
+            for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+                const uint32_t s = it % RAW_STAGES, ph = (it / RAW_STAGES) & 1;
+                if (!tc::mbar_wait(&raw_empty[s], ph ^ 1u, err, tc::ERR_TIMEOUT_EMPTY)) break;
+                const uint32_t b = t / tiles_per_poly, x0 = (t % tiles_per_poly) * 128;
+                tc::mbar_arrive_expect_tx(&raw_full[s], rbytes);
+                tc::tma_load_2d(raw_s + s * rbytes, &in_map, (int32_t)x0, (int32_t)(b * L), &raw_full[s]);
+                issued[s] = true;
+                par[s] = ph;
+            }
+            for (int s = 0; s < RAW_STAGES; ++s)
+                if (issued[s]) tc::mbar_wait(&raw_full[s], par[s], err, tc::ERR_TIMEOUT_FULL);
+        }
+    } else if (warp < 4) {  // ---- producer: step 1 and digit split from the staged tile
         uint32_t it = 0;
         for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
             const uint32_t s = it & 1, ph = (it >> 1) & 1;
+            const uint32_t rs = it % RAW_STAGES, rph = (it / RAW_STAGES) & 1;
+            if (!tc::mbar_wait(&raw_full[rs], rph, err, tc::ERR_TIMEOUT_FULL)) break;
             if (!tc::mbar_wait(&a_empty[s], ph ^ 1u, err, tc::ERR_TIMEOUT_EMPTY)) break;
-            const uint32_t b = t / tiles_per_poly, x = (t % tiles_per_poly) * 128 + tid;
-            const uint32_t* src = in + (size_t)b * L * n + x;
+            const uint32_t* raw = reinterpret_cast<const uint32_t*>(raw_s + rs * rbytes) + tid;
             uint8_t* A = a_s[s];
-            for (uint32_t i0 = 0; i0 < L; i0 += 8) {
-                uint32_t v[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) v[u] = (i0 + u < L) ? __ldg(src + (size_t)(i0 + u) * n) : 0u;
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const uint32_t i = i0 + u;
-                    if (i >= L) break;
-                    const uint32_t qi = c.q[i];
-                    const uint32_t bi = csub(mul_shoup_lazy(v[u], c.qhat_inv[i], c.qhat_inv_sh[i], qi), qi);
-                    const uint2 d = tc::split_digits4(bi);
-                    const uint32_t k = 4 * i;
-                    *reinterpret_cast<uint2*>(A + (k >> 6) * (128 * 128) + tc::sw128_offset(tid, k & 63)) = d;
-                }
+            for (uint32_t i = 0; i < L; ++i) {
+                const uint32_t qi = c.q[i];
+                const uint32_t bi = csub(mul_shoup_lazy(raw[i * 128], c.qhat_inv[i], c.qhat_inv_sh[i], qi), qi);
+                const uint2 d = tc::split_digits4(bi);
+                const uint32_t k = 4 * i;
+                *reinterpret_cast<uint2*>(A + (k >> 6) * (128 * 128) + tc::sw128_offset(tid, k & 63)) = d;
             }
+            tc::mbar_arrive(&raw_empty[rs]);
             tc::fence_proxy_async_smem();
             tc::mbar_arrive(&a_full[s]);
         }
@@ -186,7 +215,6 @@ __global__ void __launch_bounds__(THREADS, 1)
         tc::mma_commit(mma_done);
         tc::mbar_wait(mma_done, 0, err, tc::ERR_TIMEOUT_ACC);
     }
-    (void)kpad;
     tc::tc_fence_before();
     __syncthreads();
     if (warp == 8) {
@@ -216,6 +244,10 @@ cudaError_t bconv_tc_upload(hefx_bconv_plan* plan, const BConvConst& h) {
     while (cols < 2 * tp->npad) cols *= 2;
     tp->tmem_cols = cols;
     tp->bimage_bytes = tp->npad * tp->kpad * 2;
+    if (smem_bytes(*tp, L) > 232448) {  // does not fit one CTA's shared memory: CUDA-core path only
+        delete tp;
+        return cudaSuccess;
+    }
     std::vector<uint8_t> img(tp->bimage_bytes, 0);
     for (uint32_t j = 0; j < Lp; ++j) {
         const uint64_t p = plan->dst[j];
@@ -280,7 +312,12 @@ cudaError_t launch_bconv_tc(const hefx_bconv_plan* plan, const uint32_t* in, uin
     const uint32_t n = 1u << plan->log2n;
     const size_t ntiles = (size_t)(n / 128) * batch;
     if (ntiles == 0) return cudaSuccess;
-    const size_t smem = smem_bytes(*tp);
+    // raw residues of the batch as a 2D array: rows (b, i) of n coefficients
+    CUtensorMap in_map;
+    if (!encode_map_2d(&in_map, CU_TENSOR_MAP_DATA_TYPE_UINT32, const_cast<uint32_t*>(in), n, batch * plan->L,
+                       (uint64_t)n * 4, 128, plan->L, CU_TENSOR_MAP_SWIZZLE_NONE))
+        return cudaErrorInvalidValue;
+    const size_t smem = smem_bytes(*tp, plan->L);
     static size_t attr = 0;
     if (attr < smem) {
         cudaError_t e = cudaFuncSetAttribute(bconv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -290,8 +327,8 @@ cudaError_t launch_bconv_tc(const hefx_bconv_plan* plan, const uint32_t* in, uin
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const unsigned grid = (unsigned)std::min<size_t>(ntiles, 2 * (size_t)sms);  // two CTAs fit per SM
-    bconv_tc_kernel<<<grid, THREADS, smem, stream>>>(tp->d_const, tp->d_bimage, tp->bimage_bytes, in, out, n,
+    const unsigned grid = (unsigned)std::min<size_t>(ntiles, (size_t)sms);
+    bconv_tc_kernel<<<grid, THREADS, smem, stream>>>(in_map, tp->d_const, tp->d_bimage, tp->bimage_bytes, out, n,
                                                       (uint32_t)batch, tp->tmem_cols, tp->d_err);
     return cudaGetLastError();
 }

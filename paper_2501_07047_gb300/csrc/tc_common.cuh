@@ -182,4 +182,9 @@ __device__ __forceinline__ uint32_t acc_to_u32(uint32_t acc_bits) {
 }
 
 }  // namespace tc
+
+// Host: encodes a 2D tiled TMA map (row-major, `row_bytes` apart) -- defined in ntt_tc.cu.
+bool encode_map_2d(CUtensorMap* map, CUtensorMapDataType dtype, void* base, uint64_t inner, uint64_t rows,
+                   uint64_t row_bytes, uint32_t box_inner, uint32_t box_rows, CUtensorMapSwizzle swz);
+
 }  // namespace hefx
