@@ -62,6 +62,8 @@ __device__ __forceinline__ uint32_t barrett64(uint64_t x, uint32_t p, uint64_t m
     return (uint32_t)(r >= p ? r - p : r);
 }
 
+// kCoef coefficients per thread: each constant load serves kCoef products (1 for n < 4).
+template <int kCoef>
 __global__ void __launch_bounds__(256) bconv_cc_kernel(const BConvConst* __restrict__ gc, const uint32_t* __restrict__ in,
                                                        uint32_t* __restrict__ out, uint32_t n, uint32_t batch) {
     __shared__ BConvConst c;
@@ -69,35 +71,42 @@ __global__ void __launch_bounds__(256) bconv_cc_kernel(const BConvConst* __restr
         reinterpret_cast<uint32_t*>(&c)[i] = reinterpret_cast<const uint32_t*>(gc)[i];
     __syncthreads();
     const uint32_t L = c.L, Lp = c.Lp;
-    const size_t total = (size_t)n * batch;
-    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-        const size_t b = t / n, x = t % n;
-        const uint32_t* src = in + b * L * n + x;
-        uint32_t* dst = out + b * Lp * n + x;
+    const size_t groups = (size_t)n * batch / kCoef;  // n is a multiple of kCoef
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < groups; t += (size_t)gridDim.x * blockDim.x) {
+        // kCoef coefficients x, x + stride, ... of one polynomial (stride keeps warps coalesced)
+        const size_t per_poly = n / kCoef;
+        const size_t b = t / per_poly, x0 = t % per_poly;
+        const uint32_t* src = in + b * L * n + x0;
+        uint32_t* dst = out + b * Lp * n + x0;
         for (uint32_t j0 = 0; j0 < Lp; j0 += kJChunk) {
-            uint64_t acc[kJChunk];
+            uint64_t acc[kCoef][kJChunk];
 #pragma unroll
-            for (int jj = 0; jj < kJChunk; ++jj) acc[jj] = 0;
-            // source residues in groups of 8 independent loads (latency overlap)
-            for (uint32_t i0 = 0; i0 < L; i0 += 8) {
-                uint32_t v[8];
+            for (int u = 0; u < kCoef; ++u)
 #pragma unroll
-                for (int u = 0; u < 8; ++u) v[u] = (i0 + u < L) ? __ldg(src + (size_t)(i0 + u) * n) : 0u;
+                for (int jj = 0; jj < kJChunk; ++jj) acc[u][jj] = 0;
+            for (uint32_t i = 0; i < L; ++i) {
+                uint32_t v[kCoef];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const uint32_t i = i0 + u;
-                    if (i >= L) break;
-                    const uint32_t qi = c.q[i];
-                    const uint32_t bi = csub(mul_shoup_lazy(v[u], c.qhat_inv[i], c.qhat_inv_sh[i], qi), qi);  // step 1
+                for (int u = 0; u < kCoef; ++u) v[u] = __ldg(src + (size_t)i * n + u * per_poly);
+                const uint32_t qi = c.q[i], w = c.qhat_inv[i], wsh = c.qhat_inv_sh[i];
+                uint32_t cst[kJChunk];
 #pragma unroll
-                    for (int jj = 0; jj < kJChunk; ++jj)
-                        acc[jj] += (uint64_t)bi * c.qhat_p[i * kBConvMaxLimbs + j0 + jj];  // step 2
+                for (int jj = 0; jj < kJChunk; ++jj) cst[jj] = c.qhat_p[i * kBConvMaxLimbs + j0 + jj];
+#pragma unroll
+                for (int u = 0; u < kCoef; ++u) {
+                    const uint32_t bi = csub(mul_shoup_lazy(v[u], w, wsh, qi), qi);  // step 1
+#pragma unroll
+                    for (int jj = 0; jj < kJChunk; ++jj) acc[u][jj] += (uint64_t)bi * cst[jj];  // step 2
                 }
             }
 #pragma unroll
             for (int jj = 0; jj < kJChunk; ++jj) {
                 const uint32_t j = j0 + jj;
-                if (j < Lp) dst[(size_t)j * n] = barrett64(acc[jj], c.p[j], c.p_mu[j]);
+                if (j < Lp) {
+#pragma unroll
+                    for (int u = 0; u < kCoef; ++u)
+                        dst[(size_t)j * n + u * per_poly] = barrett64(acc[u][jj], c.p[j], c.p_mu[j]);
+                }
             }
         }
     }
@@ -113,13 +122,17 @@ cudaError_t launch_bconv_cc(const hefx_bconv_plan* plan, const uint32_t* in, uin
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    // one coefficient per thread, many short blocks: no ragged persistent tail
-    size_t blocks = (total + 255) / 256;
+    const int kc = 1;  // measured: 4 coefficients per thread (95 registers) is slower than 1
+    // kc coefficients per thread, many short blocks: no ragged persistent tail
+    size_t blocks = (total / kc + 255) / 256;
     const size_t cap = (size_t)1 << 20;
     if (blocks > cap) blocks = cap;
     (void)sms;
-    bconv_cc_kernel<<<(unsigned)blocks, 256, 0, stream>>>(static_cast<const BConvConst*>(plan->d_const), in, out, n,
-                                                           (uint32_t)batch);
+    const BConvConst* gc = static_cast<const BConvConst*>(plan->d_const);
+    if (kc == 4)
+        bconv_cc_kernel<4><<<(unsigned)blocks, 256, 0, stream>>>(gc, in, out, n, (uint32_t)batch);
+    else
+        bconv_cc_kernel<1><<<(unsigned)blocks, 256, 0, stream>>>(gc, in, out, n, (uint32_t)batch);
     return cudaGetLastError();
 }
 

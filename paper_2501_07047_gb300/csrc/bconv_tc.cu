@@ -29,7 +29,7 @@ namespace hefx {
 namespace {
 
 constexpr int KO = 5;
-constexpr int THREADS = 384;  // warps 0-3 producer, 4-7 epilogue, 8 MMA
+constexpr int THREADS = 448;  // warps 0-3 and 8-11 producer, 4-7 epilogue, 12 MMA, 13 TMA
 constexpr int MAX_L = 48, MAX_LP = 32;  // MAX_L: 4 staged raw tiles fit in shared memory
 
 struct BcTcConst {
@@ -66,8 +66,8 @@ size_t smem_bytes(const BcTcPlan& tp, uint32_t L) {
     return 1024 + 2ull * 128 * tp.kpad * 2 + tp.bimage_bytes + RAW_STAGES * raw_bytes(L) + 256;
 }
 
-// Warp roles: 0-3 producers (step 1 + digits), 4-7 epilogue, 8 MMA issuer + TMEM owner,
-// 9 TMA issuer of raw residue tiles.
+// Warp roles: 0-3 and 8-11 producers (step 1 + digits; the two groups split the source limbs
+// of a tile), 4-7 epilogue, 12 MMA issuer + TMEM owner, 13 TMA issuer of raw residue tiles.
 __global__ void __launch_bounds__(THREADS, 1)
     bconv_tc_kernel(const __grid_constant__ CUtensorMap in_map, const BcTcConst* __restrict__ gc,
                     const uint8_t* __restrict__ bimage, uint32_t bimage_bytes, uint32_t* __restrict__ out, uint32_t n,
@@ -100,20 +100,20 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (uint32_t i = tid; i < 2 * abytes / 16; i += THREADS) reinterpret_cast<uint4*>(smem)[i] = make_uint4(0, 0, 0, 0);
     if (tid == 0) {
         for (int s = 0; s < 2; ++s) {
-            tc::mbar_init(&a_full[s], 128);
+            tc::mbar_init(&a_full[s], 256);
             tc::mbar_init(&a_empty[s], 1);
             tc::mbar_init(&acc_full[s], 1);
             tc::mbar_init(&acc_empty[s], 128);
         }
         for (int s = 0; s < RAW_STAGES; ++s) {
             tc::mbar_init(&raw_full[s], 1);
-            tc::mbar_init(&raw_empty[s], 128);
+            tc::mbar_init(&raw_empty[s], 256);
         }
         tc::mbar_init(mma_done, 1);
         tc::fence_mbar_init();
     }
-    if (warp == 8) tc::tmem_alloc(tmem_slot, tmem_cols);
-    if (tid == 9 * 32) tc::prefetch_tmap(&in_map);
+    if (warp == 12) tc::tmem_alloc(tmem_slot, tmem_cols);
+    if (tid == 13 * 32) tc::prefetch_tmap(&in_map);
     tc::fence_proxy_async_smem();
     tc::tc_fence_before();
     __syncthreads();
@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     const uint32_t tiles_per_poly = n / 128;
     const uint32_t ntiles = tiles_per_poly * batch;
 
-    if (warp == 9) {  // ---- TMA issuer: raw residue tiles, RAW_STAGES in flight
+    if (warp == 13) {  // ---- TMA issuer: raw residue tiles, RAW_STAGES in flight
         if (lane == 0) {
             uint32_t it = 0;
             bool issued[RAW_STAGES];
@@ -141,27 +141,28 @@ __global__ void __launch_bounds__(THREADS, 1)
             for (int s = 0; s < RAW_STAGES; ++s)
                 if (issued[s]) tc::mbar_wait(&raw_full[s], par[s], err, tc::ERR_TIMEOUT_FULL);
         }
-    } else if (warp < 4) {  // ---- producer: step 1 and digit split from the staged tile
+    } else if (warp < 4 || (warp >= 8 && warp < 12)) {  // ---- producers: step 1 and digit split
+        const uint32_t row = tid & 127, grp = warp >= 8 ? 1u : 0u;  // coefficient row, limb parity
         uint32_t it = 0;
         for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
             const uint32_t s = it & 1, ph = (it >> 1) & 1;
             const uint32_t rs = it % RAW_STAGES, rph = (it / RAW_STAGES) & 1;
             if (!tc::mbar_wait(&raw_full[rs], rph, err, tc::ERR_TIMEOUT_FULL)) break;
             if (!tc::mbar_wait(&a_empty[s], ph ^ 1u, err, tc::ERR_TIMEOUT_EMPTY)) break;
-            const uint32_t* raw = reinterpret_cast<const uint32_t*>(raw_s + rs * rbytes) + tid;
+            const uint32_t* raw = reinterpret_cast<const uint32_t*>(raw_s + rs * rbytes) + row;
             uint8_t* A = a_s[s];
-            for (uint32_t i = 0; i < L; ++i) {
+            for (uint32_t i = grp; i < L; i += 2) {
                 const uint32_t qi = c.q[i];
                 const uint32_t bi = csub(mul_shoup_lazy(raw[i * 128], c.qhat_inv[i], c.qhat_inv_sh[i], qi), qi);
                 const uint2 d = tc::split_digits4(bi);
                 const uint32_t k = 4 * i;
-                *reinterpret_cast<uint2*>(A + (k >> 6) * (128 * 128) + tc::sw128_offset(tid, k & 63)) = d;
+                *reinterpret_cast<uint2*>(A + (k >> 6) * (128 * 128) + tc::sw128_offset(row, k & 63)) = d;
             }
             tc::mbar_arrive(&raw_empty[rs]);
             tc::fence_proxy_async_smem();
             tc::mbar_arrive(&a_full[s]);
         }
-    } else if (warp < 8) {  // ---- epilogue: merge, reduce mod p_j, store
+    } else if (warp >= 4 && warp < 8) {  // ---- epilogue: merge, reduce mod p_j, store
         const uint32_t lq = (warp - 4) * 32;
         uint32_t it = 0;
         for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
@@ -194,7 +195,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             tc::tc_fence_before();
             tc::mbar_arrive(&acc_empty[s]);
         }
-    } else if (warp == 8 && lane == 0) {  // ---- MMA issuer
+    } else if (warp == 12 && lane == 0) {  // ---- MMA issuer
         const uint32_t idesc = tc::idesc_f16_f32(128, npad);
         const uint32_t ksteps = (4 * L + 15) / 16;
         uint32_t it = 0;
@@ -217,7 +218,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     tc::tc_fence_before();
     __syncthreads();
-    if (warp == 8) {
+    if (warp == 12) {
         tc::tc_fence_after();
         tc::tmem_dealloc(tmem, tmem_cols);
     }
