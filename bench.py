@@ -219,7 +219,7 @@ def run_gpu(args):
             "value": world * UNITS_PER_STEP * args.steps / (total_ms / 1e3),
             "fwd_ms": statistics.mean(fwd_ms), "inv_ms": statistics.mean(inv_ms),
             "wall_s": t_wall, "clocks": clk.summary(),
-            "launches_per_step": 2,
+            "launches_per_step": 2 if path == "cudacore" else 6,
         }
 
     best = max(results, key=lambda p: results[p]["value"])

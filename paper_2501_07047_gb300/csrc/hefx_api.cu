@@ -70,6 +70,10 @@ hefx_status ensure_tc(hefx_ctx* ctx, const hefx_params* pc) {
         cudaError_t e = tc_prepare(p);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "tensor-path tables");
     }
+    if (!p->tc2) {
+        cudaError_t e = tc2_prepare(p);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "tensor-path tables (pipelined)");
+    }
     return HEFX_OK;
 }
 
@@ -217,7 +221,9 @@ static hefx_status run_ntt(hefx_ctx* ctx, const hefx_params* p, uint32_t* d, siz
     if (batch == 0) return HEFX_OK;
     cudaError_t e;
     if (pth == HEFX_PATH_TENSOR) {
-        e = launch_ntt_tc(p, mode, d, nullptr, d, batch, (cudaStream_t)stream);
+        hefx_params* pm = const_cast<hefx_params*>(p);
+        e = mode == MODE_FWD ? tc2_forward(pm, d, d, 0, nullptr, batch, (cudaStream_t)stream)
+                             : tc2_inverse(pm, d, d, batch, (cudaStream_t)stream);
     } else if (pth == HEFX_PATH_CUDACORE) {
         e = launch_ntt_cc(p, mode, d, nullptr, d, batch * p->nlimbs, (cudaStream_t)stream);
     } else {
@@ -251,7 +257,7 @@ hefx_status hefx_poly_mul(hefx_ctx* ctx, const hefx_params* p, const uint32_t* a
     cudaStream_t s = (cudaStream_t)stream;
     const size_t rows = batch * p->nlimbs;
     if (pth == HEFX_PATH_TENSOR) {
-        cudaError_t e = launch_polymul_tc(const_cast<hefx_params*>(p), a, b, c, batch, s);
+        cudaError_t e = tc2_polymul(const_cast<hefx_params*>(p), a, b, c, batch, s);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "hefx_poly_mul (tensor path)");
         return HEFX_OK;
     }
@@ -530,8 +536,14 @@ hefx_status hefx_stream_check(hefx_ctx* ctx, const hefx_params* p, void* stream)
     if (!p || p->ctx != ctx) return fail(ctx, HEFX_EINVAL, "params is null or belongs to another context");
     hefx_status st = use_device(ctx);
     if (st != HEFX_OK) return st;
-    uint32_t code = 0;
+    uint32_t code = 0, code2 = 0;
     cudaError_t e = tc_check(p, (cudaStream_t)stream, &code);
+    if (e == cudaSuccess && tc2_err(p)) {
+        e = cudaMemcpyAsync(&code2, tc2_err(p), 4, cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+        if (e == cudaSuccess && code2) e = cudaMemsetAsync(tc2_err(p), 0, 4, (cudaStream_t)stream);
+        if (!code) code = code2;
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "hefx_stream_check");
     if (code) return fail(ctx, HEFX_ETIMEOUT, "a bounded device wait expired (code %u); results are invalid", code);

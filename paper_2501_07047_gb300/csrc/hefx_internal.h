@@ -44,8 +44,10 @@ struct RowDesc {
     uint32_t pad;
 };
 
-// Device tables of the tensor-core (matrix) NTT for one parameter set; see ntt_tc.cu.
+// Device tables of the tensor-core (matrix) NTT for one parameter set: the single-pass GEMMs
+// of ntt_tc.cu (used by the no-allocation product) and the pipelined GEMMs of ntt_tc2.cu.
 struct TensorTables;
+struct Tc2Tables;
 
 }  // namespace hefx
 
@@ -68,6 +70,7 @@ struct hefx_params {
     uint2* d_tw_fwd = nullptr;        // [nlimbs][N]: (psi^brv_N(k), Shoup companion), k >= 1
     uint2* d_tw_inv = nullptr;        // [nlimbs][N]: (psi^-brv_N(k), Shoup companion)
     hefx::TensorTables* tc = nullptr; // built on first tensor-path use
+    hefx::Tc2Tables* tc2 = nullptr;   // built on first tensor-path use
     std::mutex tc_mu;
     hefx_path tuned_path = HEFX_PATH_AUTO;
 };
@@ -132,6 +135,14 @@ cudaError_t launch_polymul_tc(hefx_params* p, const uint32_t* a, const uint32_t*
                               cudaStream_t stream);
 cudaError_t tc_check(const hefx_params* p, cudaStream_t stream, uint32_t* code);
 size_t noalloc_scratch_words();
+cudaError_t tc2_prepare(hefx_params* p);
+void tc2_free(hefx_params* p);
+uint32_t* tc2_err(const hefx_params* p);
+cudaError_t tc2_forward(hefx_params* p, const uint32_t* in, uint32_t* out, int mul, const uint32_t* had, size_t batch,
+                        cudaStream_t s);
+cudaError_t tc2_inverse(hefx_params* p, const uint32_t* in, uint32_t* out, size_t batch, cudaStream_t s);
+cudaError_t tc2_polymul(hefx_params* p, const uint32_t* a, const uint32_t* b, uint32_t* c, size_t batch,
+                        cudaStream_t s);
 cudaError_t polymul_tc_noalloc(const hefx_params* p, const uint32_t* a, const uint32_t* b, uint32_t* c, size_t batch,
                                cudaStream_t stream);
 cudaError_t launch_bconv_tc(const hefx_bconv_plan* plan, const uint32_t* in, uint32_t* out, size_t batch,

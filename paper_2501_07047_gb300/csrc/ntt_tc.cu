@@ -346,6 +346,7 @@ bool tc_supported(const hefx_params* p) {
 }
 
 void tc_free(hefx_params* p) {
+    tc2_free(p);
     TensorTables* t = p->tc;
     if (!t) return;
     for (int i = 0; i < 4; ++i)

@@ -1,0 +1,596 @@
+// Tensor-core NTT, pipelined form: each matrix step of the layout-invariant 3-step NTT
+// (Sec. IV-B) is one streamed digit GEMM
+//
+//     D[n][(out, o)] = sum_k Dig[n][k] * Cst[(out, o)][k],   k = (reduction index v, digit i)
+//
+// with the data digits as the A operand (128 data rows per CTA) and the BAT-compiled constant
+// (Alg. 2, OfflineCompileLeft) as the B operand: 64 outputs x 4 chunks = 256 columns per tile.
+// Data digits and constant chunks are both 7 bits (fp16-exact), so partial sums stay below
+// 4 * 256 * 127 * 127 < 2^24 and the fp32 accumulation is exact; cvt.rni recovers them.
+//
+// GB300 mapping
+//  - A (data digits, K-major) and B (constant, K-major) both arrive by TMA with the 128-byte
+//    swizzle, 4 stages of 16 KiB + 32 KiB.  Four CTAs of a cluster work on four 128-row data
+//    blocks of the same limb; each loads a quarter of every constant stage and multicasts it
+//    to all four, so the constant is read from L2 once per 512 data rows.
+//  - Two 256-column TMEM accumulators: the epilogue of one 64-output tile overlaps the MMAs
+//    of the next.  The epilogue merges the 4 chunk sums (sum_o p_o 2^(7o) < 2^46), reduces
+//    with one Montgomery REDC (2^32 folded into the constants), applies the twiddle or
+//    Hadamard product and writes either the final residues or -- after a first step -- the
+//    7-bit digits of the next step's A operand, already transposed where that step needs it.
+//  - Warp roles: warp 0 TMA producer, warp 1 MMA issuer and TMEM owner, warps 2-5 epilogue
+//    (TMEM lane quadrants 2, 3, 0, 1).  Every mbarrier wait is bounded.
+#include <cuda.h>
+
+#include <algorithm>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+#include "hefx_internal.h"
+#include "host_nt.h"
+#include "modarith.cuh"
+#include "tc_common.cuh"
+
+namespace hefx {
+namespace tc2 {
+
+constexpr int BM = 128;                // data rows per CTA (MMA M)
+constexpr int OUTS = 64;               // outputs per tile
+constexpr int KO = 4;                  // 7-bit constant chunks
+constexpr int BN = OUTS * KO;          // 256 (MMA N)
+constexpr int BK = 64;                 // K elements per stage (128 bytes of fp16)
+constexpr int STAGES = 4;
+constexpr uint32_t A_BYTES = BM * BK * 2;  // 16 KiB
+constexpr uint32_t B_BYTES = BN * BK * 2;  // 32 KiB
+constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int THREADS = 192;
+constexpr uint32_t TMEM_COLS = 512;
+constexpr size_t SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + 256;
+
+enum Step { FWD1 = 0, FWD3 = 1, INV1 = 2, INV3 = 3 };
+// epilogue output
+enum : int { OUT_DIGITS_T = 0, OUT_U32_ROW_DATA = 1, OUT_U32_ROW_OUT = 2 };
+// epilogue multiplier
+enum : int { MUL_NONE = 0, MUL_TW_OUT_ROW = 1, MUL_TW_DATA_ROW = 2, MUL_HAD = 3, MUL_SQUARE = 4 };
+
+struct Limb {
+    uint32_t q, qinv_neg, r2, pad;
+};
+
+struct Args {
+    uint32_t* out;          // u32 results [poly][limb][R][C]
+    uint16_t* out_digits;   // digits of the next step [poly][limb][OUT][4 DN] (fp16 bits)
+    const uint32_t* had;    // Hadamard operand, same layout as out
+    const uint2* tw;        // [L][R][C] Shoup twiddles
+    const Limb* limbs;
+    uint32_t* err;
+    uint32_t L, batch;
+    uint32_t R, C;          // data matrix shape
+    uint32_t DN;            // data rows per polynomial limb (A operand rows)
+    uint32_t OUT;           // outputs per data row
+    uint32_t K;             // 4 * reduction length
+    uint32_t cs;            // CTAs per cluster (1, 2 or 4)
+};
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// TMA 2D load multicast to the CTAs in `mask` (same shared offset and mbarrier offset in each).
+__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* map, int32_t x, int32_t y, uint64_t* bar,
+                                              uint16_t mask) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+        " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(tc::smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(tc::smem_u32(bar)), "h"(mask)
+        : "memory");
+}
+
+// Arrives on `bar` in every CTA of `mask` when this thread's tcgen05 operations complete.
+__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            tc::smem_u32(bar)),
+        "h"(mask)
+        : "memory");
+}
+
+template <int OUTK, int MUL>
+__global__ void __launch_bounds__(THREADS, 1)
+    gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bmap, Args a) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+    uint64_t* empty = full + STAGES;
+    uint64_t* acc_full = empty + STAGES;   // [2]
+    uint64_t* acc_empty = acc_full + 2;    // [2]
+    uint64_t* mma_done = acc_empty + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 1);
+
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t cs = a.cs;
+    const uint32_t rank = cs > 1 ? cluster_rank() : 0;
+    // data block of this CTA: blocks of one limb are (poly, 128-row block) pairs; a cluster
+    // takes cs consecutive blocks of the same limb
+    const uint32_t blocks_per_limb = a.batch * (a.DN / BM);
+    const uint32_t blk = blockIdx.x % blocks_per_limb;
+    const uint32_t limb = blockIdx.x / blocks_per_limb;
+    const uint32_t poly = blk / (a.DN / BM), drow0 = (blk % (a.DN / BM)) * BM;
+    const uint32_t pl = poly * a.L + limb;
+    const uint32_t a_row0 = pl * a.DN + drow0;          // A rows: [poly][limb][DN]
+    const uint32_t b_row0 = limb * a.OUT * KO;          // B rows: [limb][OUT x KO]
+    const uint32_t ntiles = a.OUT / OUTS, kstages = a.K / BK;
+    const uint32_t slice = BN / cs;                     // constant rows loaded by this CTA
+    const uint16_t mask = (uint16_t)((1u << cs) - 1u);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], cs);  // one MMA commit from every CTA of the cluster
+        }
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(&acc_full[b], 1);
+            tc::mbar_init(&acc_empty[b], 128);
+        }
+        tc::mbar_init(mma_done, 1);
+        tc::fence_mbar_init();
+    }
+    if (warp == 1) tc::tmem_alloc(tmem_slot, TMEM_COLS);
+    if (threadIdx.x == 32) {
+        tc::prefetch_tmap(&amap);
+        tc::prefetch_tmap(&bmap);
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (cs > 1) cluster_sync_all();  // peers' barriers are initialised before any multicast
+    tc::tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {  // ---- TMA producer
+            uint32_t stage = 0, phase = 0;
+            bool ok = true;
+            for (uint32_t nt = 0; nt < ntiles && ok; ++nt)
+                for (uint32_t kc = 0; kc < kstages; ++kc) {
+                    if (!tc::mbar_wait(&empty[stage], phase ^ 1u, a.err, tc::ERR_TIMEOUT_EMPTY)) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t* st = smem + stage * STAGE_BYTES;
+                    tc::mbar_arrive_expect_tx(&full[stage], STAGE_BYTES);
+                    tc::tma_load_2d(st, &amap, (int32_t)(kc * BK), (int32_t)a_row0, &full[stage]);
+                    uint8_t* bdst = st + A_BYTES + rank * slice * 128;
+                    const int32_t by = (int32_t)(b_row0 + nt * BN + rank * slice);
+                    if (cs > 1)
+                        tma_load_2d_mc(bdst, &bmap, (int32_t)(kc * BK), by, &full[stage], mask);
+                    else
+                        tc::tma_load_2d(bdst, &bmap, (int32_t)(kc * BK), by, &full[stage]);
+                    if (++stage == STAGES) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            // drain: this CTA's last loads have landed (its own full barrier covers them)
+            if (ok) {
+                for (int s = 0; s < STAGES; ++s) {
+                    uint32_t p = phase;
+                    if ((uint32_t)s >= stage) p ^= 1u;  // stages not yet reused in the last lap
+                    tc::mbar_wait(&full[s], p, a.err, tc::ERR_TIMEOUT_FULL);
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {  // ---- MMA issuer
+            const uint32_t idesc = tc::idesc_f16_f32(BM, BN);
+            uint32_t stage = 0, phase = 0;
+            bool ok = true;
+            for (uint32_t nt = 0; nt < ntiles && ok; ++nt) {
+                const uint32_t acc = nt & 1;
+                if (nt >= 2 && !tc::mbar_wait(&acc_empty[acc], ((nt - 2) >> 1) & 1u, a.err, tc::ERR_TIMEOUT_ACC)) break;
+                tc::tc_fence_after();
+                for (uint32_t kc = 0; kc < kstages; ++kc) {
+                    if (!tc::mbar_wait(&full[stage], phase, a.err, tc::ERR_TIMEOUT_FULL)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::tc_fence_after();
+                    const uint32_t ab = tc::smem_u32(smem + stage * STAGE_BYTES);
+                    const uint32_t bb = ab + A_BYTES;
+#pragma unroll
+                    for (int ks = 0; ks < BK / 16; ++ks)
+                        tc::mma_f16(tmem + acc * BN, tc::sw128_desc(ab + ks * 32), tc::sw128_desc(bb + ks * 32), idesc,
+                                    (kc | ks) != 0);
+                    if (cs > 1)
+                        mma_commit_mc(&empty[stage], mask);
+                    else
+                        tc::mma_commit(&empty[stage]);
+                    if (++stage == STAGES) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+                if (ok) tc::mma_commit(&acc_full[acc]);
+            }
+            tc::mma_commit(mma_done);
+            tc::mbar_wait(mma_done, 0, a.err, tc::ERR_TIMEOUT_ACC);
+        }
+    } else {  // ---- epilogue: warps 2..5 own TMEM lane quadrants (warp % 4)
+        const uint32_t quad = warp & 3;
+        const uint32_t drow = drow0 + quad * 32 + lane;  // data row held by this thread
+        const Limb lc = a.limbs[limb];
+        const size_t mat = (size_t)pl * a.R * a.C;      // start of this polynomial limb
+        for (uint32_t nt = 0; nt < ntiles; ++nt) {
+            const uint32_t acc = nt & 1;
+            if (!tc::mbar_wait(&acc_full[acc], (nt >> 1) & 1u, a.err, tc::ERR_TIMEOUT_ACC)) break;
+            tc::tc_fence_after();
+#pragma unroll 1
+            for (int cb = 0; cb < BN; cb += 16) {
+                uint32_t r[16];
+                tc::tmem_ld16(tmem + ((quad * 32) << 16) + acc * BN + cb, r);
+                tc::tmem_ld_wait();
+                uint32_t res[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const uint32_t p0 = __float2uint_rn(__uint_as_float(r[4 * u]));
+                    const uint32_t p1 = __float2uint_rn(__uint_as_float(r[4 * u + 1]));
+                    const uint32_t p2 = __float2uint_rn(__uint_as_float(r[4 * u + 2]));
+                    const uint32_t p3 = __float2uint_rn(__uint_as_float(r[4 * u + 3]));
+                    const uint64_t z = (uint64_t)p0 + ((uint64_t)p1 << 7) + ((uint64_t)p2 << 14) + ((uint64_t)p3 << 21);
+                    const uint32_t zl = (uint32_t)z, zh = (uint32_t)(z >> 32);
+                    uint32_t v = zh + __umulhi(zl * lc.qinv_neg, lc.q) + (zl != 0u);  // z 2^-32 mod q, [0, 2q)
+                    const uint32_t out = nt * OUTS + cb / 4 + u;
+                    if constexpr (MUL == MUL_TW_OUT_ROW || MUL == MUL_TW_DATA_ROW) {
+                        const size_t ti = MUL == MUL_TW_OUT_ROW ? (size_t)out * a.C + drow : (size_t)drow * a.C + out;
+                        const uint2 w = __ldg(a.tw + (size_t)limb * a.R * a.C + ti);
+                        v = mul_shoup_lazy(v, w.x, w.y, lc.q);
+                    } else if constexpr (MUL == MUL_HAD) {
+                        const uint32_t h = __ldg(a.had + mat + (size_t)drow * a.C + out);
+                        v = mul_mont_lazy(mul_mont_lazy(v, h, lc.q, lc.qinv_neg), lc.r2, lc.q, lc.qinv_neg);
+                    } else if constexpr (MUL == MUL_SQUARE) {
+                        const uint32_t vc = csub(v, lc.q);
+                        v = mul_mont_lazy(mul_mont_lazy(vc, vc, lc.q, lc.qinv_neg), lc.r2, lc.q, lc.qinv_neg);
+                    }
+                    res[u] = csub(v, lc.q);
+                }
+                const uint32_t out0 = nt * OUTS + cb / 4;
+                if constexpr (OUTK == OUT_DIGITS_T) {
+                    // next step's A operand: row = output index, digits of this data row at 4 drow
+                    uint16_t* base = a.out_digits + ((size_t)pl * a.OUT) * (4 * a.DN) + (size_t)drow * 4;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const uint2 d = tc::split_digits4(res[u]);
+                        *reinterpret_cast<uint2*>(base + (size_t)(out0 + u) * (4 * a.DN)) = d;
+                    }
+                } else if constexpr (OUTK == OUT_U32_ROW_DATA) {
+                    *reinterpret_cast<uint4*>(a.out + mat + (size_t)drow * a.C + out0) =
+                        make_uint4(res[0], res[1], res[2], res[3]);
+                } else {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) a.out[mat + (size_t)(out0 + u) * a.C + drow] = res[u];
+                }
+            }
+            tc::tc_fence_before();
+            tc::mbar_arrive(&acc_empty[acc]);
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (cs > 1) cluster_sync_all();  // no CTA leaves while a peer may still multicast into it
+    if (warp == 1) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem, TMEM_COLS);
+    }
+}
+
+// Digits of the first step's A operand: TRANS (forward step 1) reads the data matrix by
+// columns (rows of the A operand are the data's columns, K over its rows), otherwise rows.
+template <bool TRANS>
+__global__ void __launch_bounds__(256) digitize_kernel(const uint32_t* __restrict__ in, uint16_t* __restrict__ dig,
+                                                       uint32_t R, uint32_t C, size_t mats) {
+    const size_t per = (size_t)R * C / 4;  // 4 elements per thread
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < mats * per; t += (size_t)gridDim.x * blockDim.x) {
+        const size_t m = t / per, w = t % per;
+        const uint32_t* src = in + m * R * C;
+        uint16_t* dst = dig + m * R * C * 4;
+        uint32_t x[4];
+        size_t doff;
+        if constexpr (TRANS) {
+            // thread: column c, rows r0..r0+3 -> A row c, K = 4 r0 .. 4 r0 + 15
+            const uint32_t c = (uint32_t)(w % C), r0 = (uint32_t)(w / C) * 4;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) x[u] = __ldg(src + (size_t)(r0 + u) * C + c);
+            doff = (size_t)c * (4 * R) + 4 * r0;
+        } else {
+            const uint4 v = __ldg(reinterpret_cast<const uint4*>(src) + w);
+            x[0] = v.x, x[1] = v.y, x[2] = v.z, x[3] = v.w;
+            const uint32_t r = (uint32_t)((w * 4) / C), c0 = (uint32_t)((w * 4) % C);
+            doff = (size_t)r * (4 * C) + 4 * c0;
+        }
+        const uint2 d0 = tc::split_digits4(x[0]), d1 = tc::split_digits4(x[1]);
+        const uint2 d2 = tc::split_digits4(x[2]), d3 = tc::split_digits4(x[3]);
+        uint4* o = reinterpret_cast<uint4*>(dst + doff);
+        o[0] = make_uint4(d0.x, d0.y, d1.x, d1.y);
+        o[1] = make_uint4(d2.x, d2.y, d3.x, d3.y);
+    }
+}
+
+uint16_t half_bits_small(uint32_t d) {
+    if (d == 0) return 0;
+    int e = 31 - __builtin_clz(d);
+    return (uint16_t)(((e + 15) << 10) | ((d << (10 - e)) & 0x3FFu));
+}
+
+}  // namespace tc2
+
+// ------------------------------------------------------------------ host side
+
+struct Tc2Tables {
+    uint32_t R = 0, C = 0;
+    uint16_t* cst[4] = {nullptr, nullptr, nullptr, nullptr};  // fp16 [L][OUT x 4][4V]
+    CUtensorMap bmaps[4][3];                                   // per step, per cluster size 4/2/1
+    uint2* T = nullptr;
+    uint2* Tinv = nullptr;
+    tc2::Limb* limbs = nullptr;
+    uint32_t* err = nullptr;
+    uint16_t* dig1 = nullptr;  // first-step digits
+    uint16_t* dig3 = nullptr;  // second-step digits
+    uint32_t* scratch = nullptr;
+    size_t dig_elems = 0, scratch_words = 0;
+};
+
+namespace {
+
+int cs_index(uint32_t cs) { return cs == 4 ? 0 : cs == 2 ? 1 : 2; }
+
+}  // namespace
+
+// Offline precompute: BAT digit matrices with 7-bit input digits and 7-bit output chunks,
+// constants times 2^32 (Montgomery), rows (out, chunk) interleaved so that one output's four
+// chunk sums land in four consecutive accumulator columns.
+cudaError_t tc2_prepare(hefx_params* p) {
+    using namespace tc2;
+    const uint32_t logn = p->log2n, N = p->n, L = p->nlimbs;
+    const uint32_t logR = logn / 2, R = 1u << logR, C = N / R, logC = logn - logR;
+    Tc2Tables* t = new Tc2Tables();
+    t->R = R;
+    t->C = C;
+    const uint32_t outs[4] = {R, C, C, R}, Vs[4] = {R, C, C, R};
+    std::vector<std::vector<uint16_t>> hc(4);
+    for (int s = 0; s < 4; ++s) hc[s].assign((size_t)L * outs[s] * KO * 4 * Vs[s], 0);
+    std::vector<uint2> hT((size_t)L * N), hTi((size_t)L * N);
+    std::vector<Limb> hl(L);
+    auto work = [&](uint32_t l) {
+        const uint64_t q = p->primes[l], psi = p->psi[l], twoN = 2ull * N;
+        std::vector<uint64_t> pw(twoN);
+        pw[0] = 1;
+        for (uint64_t e = 1; e < twoN; ++e) pw[e] = mul_mod(pw[e - 1], psi, q);
+        auto P = [&](uint64_t e) { return pw[e % twoN]; };
+        auto Pn = [&](uint64_t e) { return pw[(twoN - e % twoN) % twoN]; };
+        const uint64_t r32 = ((uint64_t)1 << 32) % q, ninv = inv_mod(N % q, q);
+        hl[l] = {(uint32_t)q, neg_inv_pow2_32((uint32_t)q), (uint32_t)mul_mod(r32, r32, q), 0};
+        auto put = [&](int s, uint32_t out, uint32_t v, uint64_t w) {
+            const uint32_t K = 4 * Vs[s];
+            uint64_t c = mul_mod(w, r32, q);
+            for (uint32_t i = 0; i < 4; ++i) {
+                for (int o = 0; o < KO; ++o) {
+                    const uint32_t chunk = (uint32_t)((c >> (7 * o)) & 127u);
+                    hc[s][(((size_t)l * outs[s] + out) * KO + o) * K + v * 4 + i] = half_bits_small(chunk);
+                }
+                c = (c << 7) % q;
+            }
+        };
+        for (uint32_t p1 = 0; p1 < R; ++p1) {
+            const uint64_t kodd = 2ull * bit_reverse(p1, (int)logR) + 1;
+            for (uint32_t j1 = 0; j1 < R; ++j1) {
+                put(FWD1, p1, j1, P((uint64_t)C * j1 * kodd));
+                put(INV3, j1, p1, mul_mod(ninv, Pn((uint64_t)C * j1 * kodd), q));
+            }
+            for (uint32_t j2 = 0; j2 < C; ++j2) {
+                const uint64_t w = P((uint64_t)j2 * kodd), wi = Pn((uint64_t)j2 * kodd);
+                hT[(size_t)l * N + (size_t)p1 * C + j2] = make_uint2((uint32_t)w, shoup(w, q));
+                hTi[(size_t)l * N + (size_t)p1 * C + j2] = make_uint2((uint32_t)wi, shoup(wi, q));
+            }
+        }
+        for (uint32_t p2 = 0; p2 < C; ++p2) {
+            const uint64_t kb = bit_reverse(p2, (int)logC);
+            for (uint32_t j2 = 0; j2 < C; ++j2) {
+                put(FWD3, p2, j2, P(2ull * R * j2 * kb));
+                put(INV1, j2, p2, Pn(2ull * R * j2 * kb));
+            }
+        }
+    };
+    {
+        std::vector<std::thread> th;
+        const uint32_t nth = std::max(1u, std::min(L, std::thread::hardware_concurrency()));
+        for (uint32_t w = 0; w < nth; ++w)
+            th.emplace_back([&, w] {
+                for (uint32_t l = w; l < L; l += nth) work(l);
+            });
+        for (auto& x : th) x.join();
+    }
+    cudaError_t e = cudaSuccess;
+    for (int s = 0; s < 4 && e == cudaSuccess; ++s) {
+        e = cudaMalloc(&t->cst[s], hc[s].size() * 2);
+        if (e == cudaSuccess) e = cudaMemcpy(t->cst[s], hc[s].data(), hc[s].size() * 2, cudaMemcpyHostToDevice);
+        const uint32_t cs_list[3] = {4, 2, 1};
+        for (int c = 0; c < 3 && e == cudaSuccess; ++c)
+            if (!encode_map_2d(&t->bmaps[s][c], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, t->cst[s], 4ull * Vs[s],
+                               (uint64_t)L * outs[s] * KO, 8ull * Vs[s], BK, BN / cs_list[c],
+                               CU_TENSOR_MAP_SWIZZLE_128B))
+                e = cudaErrorInvalidValue;
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&t->T, hT.size() * sizeof(uint2));
+    if (e == cudaSuccess) e = cudaMemcpy(t->T, hT.data(), hT.size() * sizeof(uint2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&t->Tinv, hTi.size() * sizeof(uint2));
+    if (e == cudaSuccess) e = cudaMemcpy(t->Tinv, hTi.data(), hTi.size() * sizeof(uint2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&t->limbs, L * sizeof(Limb));
+    if (e == cudaSuccess) e = cudaMemcpy(t->limbs, hl.data(), L * sizeof(Limb), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&t->err, 4);
+    if (e == cudaSuccess) e = cudaMemset(t->err, 0, 4);
+    p->tc2 = t;
+    if (e != cudaSuccess) tc2_free(p);
+    return e;
+}
+
+void tc2_free(hefx_params* p) {
+    Tc2Tables* t = p->tc2;
+    if (!t) return;
+    for (int s = 0; s < 4; ++s)
+        if (t->cst[s]) cudaFree(t->cst[s]);
+    if (t->T) cudaFree(t->T);
+    if (t->Tinv) cudaFree(t->Tinv);
+    if (t->limbs) cudaFree(t->limbs);
+    if (t->err) cudaFree(t->err);
+    if (t->dig1) cudaFree(t->dig1);
+    if (t->dig3) cudaFree(t->dig3);
+    if (t->scratch) cudaFree(t->scratch);
+    delete t;
+    p->tc2 = nullptr;
+}
+
+uint32_t* tc2_err(const hefx_params* p) { return p->tc2 ? p->tc2->err : nullptr; }
+
+namespace {
+
+cudaError_t ensure_workspace(Tc2Tables* t, size_t elems) {
+    if (t->dig_elems >= elems) return cudaSuccess;
+    cudaError_t e = cudaDeviceSynchronize();  // the old buffers may still be in use
+    if (e != cudaSuccess) return e;
+    if (t->dig1) cudaFree(t->dig1);
+    if (t->dig3) cudaFree(t->dig3);
+    t->dig1 = t->dig3 = nullptr;
+    t->dig_elems = 0;
+    e = cudaMalloc(&t->dig1, elems * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&t->dig3, elems * 8);
+    if (e == cudaSuccess) t->dig_elems = elems;
+    return e;
+}
+
+template <int OUTK, int MUL>
+cudaError_t launch_gemm(const CUtensorMap& amap, const CUtensorMap& bmap, const tc2::Args& g, cudaStream_t s) {
+    using namespace tc2;
+    auto kern = gemm_kernel<OUTK, MUL>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    cfg.gridDim = dim3(g.L * g.batch * (g.DN / BM));
+    cfg.blockDim = dim3(THREADS);
+    cfg.dynamicSmemBytes = SMEM_BYTES;
+    cfg.stream = s;
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = g.cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, amap, bmap, g);
+}
+
+// one GEMM step: A digits from `adig` ([poly][limb][DN][K]); output per OUTK
+cudaError_t step(const hefx_params* p, int stp, int outk, int mul, const uint16_t* adig, uint16_t* odig, uint32_t* out,
+                 const uint32_t* had, size_t batch, cudaStream_t s) {
+    using namespace tc2;
+    const Tc2Tables* t = p->tc2;
+    const bool trans_data = (stp == FWD1 || stp == INV3);  // A rows are the data's columns
+    Args g;
+    g.out = out;
+    g.out_digits = odig;
+    g.had = had;
+    g.tw = (stp == FWD1) ? t->T : t->Tinv;
+    g.limbs = t->limbs;
+    g.err = t->err;
+    g.L = p->nlimbs;
+    g.batch = (uint32_t)batch;
+    g.R = t->R;
+    g.C = t->C;
+    g.DN = trans_data ? t->C : t->R;
+    g.OUT = trans_data ? t->R : t->C;
+    g.K = 4 * g.OUT;  // reduction length equals the output count (square matrices)
+    const uint32_t blocks = g.batch * (g.DN / BM);
+    g.cs = blocks % 4 == 0 ? 4 : blocks % 2 == 0 ? 2 : 1;
+    CUtensorMap amap;
+    if (!encode_map_2d(&amap, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, const_cast<uint16_t*>(adig), g.K,
+                       (uint64_t)batch * g.L * g.DN, 2ull * g.K, BK, BM, CU_TENSOR_MAP_SWIZZLE_128B))
+        return cudaErrorInvalidValue;
+    const CUtensorMap& bmap = t->bmaps[stp][cs_index(g.cs)];
+    if (outk == OUT_DIGITS_T) {
+        if (mul == MUL_TW_OUT_ROW) return launch_gemm<OUT_DIGITS_T, MUL_TW_OUT_ROW>(amap, bmap, g, s);
+        return launch_gemm<OUT_DIGITS_T, MUL_TW_DATA_ROW>(amap, bmap, g, s);
+    }
+    if (outk == OUT_U32_ROW_OUT) return launch_gemm<OUT_U32_ROW_OUT, MUL_NONE>(amap, bmap, g, s);
+    switch (mul) {
+        case MUL_HAD: return launch_gemm<OUT_U32_ROW_DATA, MUL_HAD>(amap, bmap, g, s);
+        case MUL_SQUARE: return launch_gemm<OUT_U32_ROW_DATA, MUL_SQUARE>(amap, bmap, g, s);
+        default: return launch_gemm<OUT_U32_ROW_DATA, MUL_NONE>(amap, bmap, g, s);
+    }
+}
+
+cudaError_t digitize(const hefx_params* p, const uint32_t* in, uint16_t* dig, bool trans, size_t batch,
+                     cudaStream_t s) {
+    const Tc2Tables* t = p->tc2;
+    const size_t mats = batch * p->nlimbs;
+    const size_t work = mats * p->n / 4;
+    const unsigned grid = (unsigned)std::min<size_t>((work + 255) / 256, (size_t)1 << 20);
+    if (trans)
+        tc2::digitize_kernel<true><<<grid, 256, 0, s>>>(in, dig, t->R, t->C, mats);
+    else
+        tc2::digitize_kernel<false><<<grid, 256, 0, s>>>(in, dig, t->R, t->C, mats);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// forward: digits(A^T) -> [W1 step, x T] -> digits -> [W3 step] -> out
+cudaError_t tc2_forward(hefx_params* p, const uint32_t* in, uint32_t* out, int mul, const uint32_t* had, size_t batch,
+                        cudaStream_t s) {
+    using namespace tc2;
+    Tc2Tables* t = p->tc2;
+    const size_t elems = batch * p->nlimbs * (size_t)p->n;
+    cudaError_t e = ensure_workspace(t, elems);
+    if (e == cudaSuccess) e = digitize(p, in, t->dig1, true, batch, s);
+    if (e == cudaSuccess) e = step(p, FWD1, OUT_DIGITS_T, MUL_TW_OUT_ROW, t->dig1, t->dig3, nullptr, nullptr, batch, s);
+    if (e == cudaSuccess) e = step(p, FWD3, OUT_U32_ROW_DATA, mul, t->dig3, nullptr, out, had, batch, s);
+    return e;
+}
+
+// inverse: digits(Ahat) -> [V3 step, x Tinv] -> digits (transposed) -> [V1 step, N^-1] -> out
+cudaError_t tc2_inverse(hefx_params* p, const uint32_t* in, uint32_t* out, size_t batch, cudaStream_t s) {
+    using namespace tc2;
+    Tc2Tables* t = p->tc2;
+    const size_t elems = batch * p->nlimbs * (size_t)p->n;
+    cudaError_t e = ensure_workspace(t, elems);
+    if (e == cudaSuccess) e = digitize(p, in, t->dig1, false, batch, s);
+    if (e == cudaSuccess) e = step(p, INV1, OUT_DIGITS_T, MUL_TW_DATA_ROW, t->dig1, t->dig3, nullptr, nullptr, batch, s);
+    if (e == cudaSuccess) e = step(p, INV3, OUT_U32_ROW_OUT, MUL_NONE, t->dig3, nullptr, out, nullptr, batch, s);
+    return e;
+}
+
+// c = INTT(NTT(a) o NTT(b)); c may alias a and/or b
+cudaError_t tc2_polymul(hefx_params* p, const uint32_t* a, const uint32_t* b, uint32_t* c, size_t batch,
+                        cudaStream_t s) {
+    using namespace tc2;
+    cudaError_t e;
+    if (a == b) {
+        e = tc2_forward(p, a, c, MUL_SQUARE, nullptr, batch, s);
+    } else {
+        if (c == b) std::swap(a, b);
+        e = tc2_forward(p, a, c, MUL_NONE, nullptr, batch, s);            // c = NTT(a)
+        if (e == cudaSuccess) e = tc2_forward(p, b, c, MUL_HAD, c, batch, s);  // c = NTT(b) o c
+    }
+    if (e == cudaSuccess) e = tc2_inverse(p, c, c, batch, s);
+    return e;
+}
+
+}  // namespace hefx
