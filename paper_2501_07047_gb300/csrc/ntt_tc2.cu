@@ -10,16 +10,19 @@
 //
 // GB300 mapping
 //  - A (data digits, K-major) and B (constant, K-major) both arrive by TMA with the 128-byte
-//    swizzle, 4 stages of 16 KiB + 32 KiB.  Four CTAs of a cluster work on four 128-row data
-//    blocks of the same limb; each loads a quarter of every constant stage and multicasts it
-//    to all four, so the constant is read from L2 once per 512 data rows.
+//    swizzle, 4 stages of 16 KiB + 32 KiB.  The CTAs of a cluster (2 by default) work on
+//    128-row data blocks of the same limb; each loads its share of every constant stage and
+//    multicasts it to the others, so the constant is read from L2 once per cluster.
 //  - Two 256-column TMEM accumulators: the epilogue of one 64-output tile overlaps the MMAs
 //    of the next.  The epilogue merges the 4 chunk sums (sum_o p_o 2^(7o) < 2^46), reduces
 //    with one Montgomery REDC (2^32 folded into the constants), applies the twiddle or
 //    Hadamard product and writes either the final residues or -- after a first step -- the
 //    7-bit digits of the next step's A operand, already transposed where that step needs it.
-//  - Warp roles: warp 0 TMA producer, warp 1 MMA issuer and TMEM owner, warps 2-5 epilogue
-//    (TMEM lane quadrants 2, 3, 0, 1).  Every mbarrier wait is bounded.
+//  - Persistent clusters (as many as fit at once) walk the work items (limb, group of data
+//    blocks); the two accumulators carry across items, so an item's last epilogue overlaps
+//    the next item's MMAs.
+//  - Warp roles: warp 0 TMA producer, warp 1 MMA issuer and TMEM owner, warps 2-9 epilogue
+//    (two per TMEM lane quadrant, splitting the columns).  Every mbarrier wait is bounded.
 #include <cuda.h>
 
 #include <algorithm>
@@ -44,7 +47,7 @@ constexpr int STAGES = 4;
 constexpr uint32_t A_BYTES = BM * BK * 2;  // 16 KiB
 constexpr uint32_t B_BYTES = BN * BK * 2;  // 32 KiB
 constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int THREADS = 192;
+constexpr int THREADS = 320;  // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue (two per TMEM lane quadrant)
 constexpr uint32_t TMEM_COLS = 512;
 constexpr size_t SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + 256;
 
@@ -117,18 +120,22 @@ __global__ void __launch_bounds__(THREADS, 1)
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t cs = a.cs;
     const uint32_t rank = cs > 1 ? cluster_rank() : 0;
-    // data block of this CTA: blocks of one limb are (poly, 128-row block) pairs; a cluster
-    // takes cs consecutive blocks of the same limb
+    // work items: (limb, group of cs consecutive data blocks of that limb); a data block is a
+    // (poly, 128-row block) pair.  Clusters walk the items with a stride.
     const uint32_t blocks_per_limb = a.batch * (a.DN / BM);
-    const uint32_t blk = blockIdx.x % blocks_per_limb;
-    const uint32_t limb = blockIdx.x / blocks_per_limb;
-    const uint32_t poly = blk / (a.DN / BM), drow0 = (blk % (a.DN / BM)) * BM;
-    const uint32_t pl = poly * a.L + limb;
-    const uint32_t a_row0 = pl * a.DN + drow0;          // A rows: [poly][limb][DN]
-    const uint32_t b_row0 = limb * a.OUT * KO;          // B rows: [limb][OUT x KO]
+    const uint32_t groups_per_limb = blocks_per_limb / cs;
+    const uint32_t items = a.L * groups_per_limb;
+    const uint32_t cid = blockIdx.x / cs, nclusters = gridDim.x / cs;
     const uint32_t ntiles = a.OUT / OUTS, kstages = a.K / BK;
     const uint32_t slice = BN / cs;                     // constant rows loaded by this CTA
     const uint16_t mask = (uint16_t)((1u << cs) - 1u);
+    auto item_rows = [&](uint32_t item, uint32_t& limb, uint32_t& pl, uint32_t& drow0) {
+        limb = item / groups_per_limb;
+        const uint32_t blk = (item % groups_per_limb) * cs + rank;
+        const uint32_t poly = blk / (a.DN / BM);
+        drow0 = (blk % (a.DN / BM)) * BM;
+        pl = poly * a.L + limb;
+    };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -137,7 +144,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         for (int b = 0; b < 2; ++b) {
             tc::mbar_init(&acc_full[b], 1);
-            tc::mbar_init(&acc_empty[b], 128);
+            tc::mbar_init(&acc_empty[b], 256);
         }
         tc::mbar_init(mma_done, 1);
         tc::fence_mbar_init();
@@ -157,127 +164,146 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (lane == 0) {  // ---- TMA producer
             uint32_t stage = 0, phase = 0;
             bool ok = true;
-            for (uint32_t nt = 0; nt < ntiles && ok; ++nt)
-                for (uint32_t kc = 0; kc < kstages; ++kc) {
-                    if (!tc::mbar_wait(&empty[stage], phase ^ 1u, a.err, tc::ERR_TIMEOUT_EMPTY)) {
-                        ok = false;
-                        break;
+            for (uint32_t item = cid; item < items && ok; item += nclusters) {
+                uint32_t limb, pl, drow0;
+                item_rows(item, limb, pl, drow0);
+                const uint32_t a_row0 = pl * a.DN + drow0;   // A rows: [poly][limb][DN]
+                const uint32_t b_row0 = limb * a.OUT * KO;  // B rows: [limb][OUT x KO]
+                for (uint32_t nt = 0; nt < ntiles && ok; ++nt)
+                    for (uint32_t kc = 0; kc < kstages; ++kc) {
+                        if (!tc::mbar_wait(&empty[stage], phase ^ 1u, a.err, tc::ERR_TIMEOUT_EMPTY)) {
+                            ok = false;
+                            break;
+                        }
+                        uint8_t* st = smem + stage * STAGE_BYTES;
+                        tc::mbar_arrive_expect_tx(&full[stage], STAGE_BYTES);
+                        tc::tma_load_2d(st, &amap, (int32_t)(kc * BK), (int32_t)a_row0, &full[stage]);
+                        uint8_t* bdst = st + A_BYTES + rank * slice * 128;
+                        const int32_t by = (int32_t)(b_row0 + nt * BN + rank * slice);
+                        if (cs > 1)
+                            tma_load_2d_mc(bdst, &bmap, (int32_t)(kc * BK), by, &full[stage], mask);
+                        else
+                            tc::tma_load_2d(bdst, &bmap, (int32_t)(kc * BK), by, &full[stage]);
+                        if (++stage == STAGES) {
+                            stage = 0;
+                            phase ^= 1u;
+                        }
                     }
-                    uint8_t* st = smem + stage * STAGE_BYTES;
-                    tc::mbar_arrive_expect_tx(&full[stage], STAGE_BYTES);
-                    tc::tma_load_2d(st, &amap, (int32_t)(kc * BK), (int32_t)a_row0, &full[stage]);
-                    uint8_t* bdst = st + A_BYTES + rank * slice * 128;
-                    const int32_t by = (int32_t)(b_row0 + nt * BN + rank * slice);
-                    if (cs > 1)
-                        tma_load_2d_mc(bdst, &bmap, (int32_t)(kc * BK), by, &full[stage], mask);
-                    else
-                        tc::tma_load_2d(bdst, &bmap, (int32_t)(kc * BK), by, &full[stage]);
-                    if (++stage == STAGES) {
-                        stage = 0;
-                        phase ^= 1u;
-                    }
-                }
-            // drain: this CTA's last loads have landed (its own full barrier covers them)
-            if (ok) {
-                for (int s = 0; s < STAGES; ++s) {
-                    uint32_t p = phase;
-                    if ((uint32_t)s >= stage) p ^= 1u;  // stages not yet reused in the last lap
-                    tc::mbar_wait(&full[s], p, a.err, tc::ERR_TIMEOUT_FULL);
-                }
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {  // ---- MMA issuer
             const uint32_t idesc = tc::idesc_f16_f32(BM, BN);
-            uint32_t stage = 0, phase = 0;
+            uint32_t stage = 0, phase = 0, t = 0;  // t: tiles issued by this CTA so far
             bool ok = true;
-            for (uint32_t nt = 0; nt < ntiles && ok; ++nt) {
-                const uint32_t acc = nt & 1;
-                if (nt >= 2 && !tc::mbar_wait(&acc_empty[acc], ((nt - 2) >> 1) & 1u, a.err, tc::ERR_TIMEOUT_ACC)) break;
-                tc::tc_fence_after();
-                for (uint32_t kc = 0; kc < kstages; ++kc) {
-                    if (!tc::mbar_wait(&full[stage], phase, a.err, tc::ERR_TIMEOUT_FULL)) {
-                        ok = false;
+            for (uint32_t item = cid; item < items && ok; item += nclusters)
+                for (uint32_t nt = 0; nt < ntiles && ok; ++nt, ++t) {
+                    const uint32_t acc = t & 1;
+                    if (t >= 2 && !tc::mbar_wait(&acc_empty[acc], ((t - 2) >> 1) & 1u, a.err, tc::ERR_TIMEOUT_ACC))
                         break;
-                    }
                     tc::tc_fence_after();
-                    const uint32_t ab = tc::smem_u32(smem + stage * STAGE_BYTES);
-                    const uint32_t bb = ab + A_BYTES;
+                    for (uint32_t kc = 0; kc < kstages; ++kc) {
+                        if (!tc::mbar_wait(&full[stage], phase, a.err, tc::ERR_TIMEOUT_FULL)) {
+                            ok = false;
+                            break;
+                        }
+                        tc::tc_fence_after();
+                        const uint32_t ab = tc::smem_u32(smem + stage * STAGE_BYTES);
+                        const uint32_t bb = ab + A_BYTES;
 #pragma unroll
-                    for (int ks = 0; ks < BK / 16; ++ks)
-                        tc::mma_f16(tmem + acc * BN, tc::sw128_desc(ab + ks * 32), tc::sw128_desc(bb + ks * 32), idesc,
-                                    (kc | ks) != 0);
-                    if (cs > 1)
-                        mma_commit_mc(&empty[stage], mask);
-                    else
-                        tc::mma_commit(&empty[stage]);
-                    if (++stage == STAGES) {
-                        stage = 0;
-                        phase ^= 1u;
+                        for (int ks = 0; ks < BK / 16; ++ks)
+                            tc::mma_f16(tmem + acc * BN, tc::sw128_desc(ab + ks * 32), tc::sw128_desc(bb + ks * 32),
+                                        idesc, (kc | ks) != 0);
+                        if (cs > 1)
+                            mma_commit_mc(&empty[stage], mask);
+                        else
+                            tc::mma_commit(&empty[stage]);
+                        if (++stage == STAGES) {
+                            stage = 0;
+                            phase ^= 1u;
+                        }
                     }
+                    if (ok) tc::mma_commit(&acc_full[acc]);
                 }
-                if (ok) tc::mma_commit(&acc_full[acc]);
-            }
             tc::mma_commit(mma_done);
             tc::mbar_wait(mma_done, 0, a.err, tc::ERR_TIMEOUT_ACC);
         }
-    } else {  // ---- epilogue: warps 2..5 own TMEM lane quadrants (warp % 4)
-        const uint32_t quad = warp & 3;
-        const uint32_t drow = drow0 + quad * 32 + lane;  // data row held by this thread
-        const Limb lc = a.limbs[limb];
-        const size_t mat = (size_t)pl * a.R * a.C;      // start of this polynomial limb
-        for (uint32_t nt = 0; nt < ntiles; ++nt) {
-            const uint32_t acc = nt & 1;
-            if (!tc::mbar_wait(&acc_full[acc], (nt >> 1) & 1u, a.err, tc::ERR_TIMEOUT_ACC)) break;
-            tc::tc_fence_after();
-#pragma unroll 1
-            for (int cb = 0; cb < BN; cb += 16) {
-                uint32_t r[16];
-                tc::tmem_ld16(tmem + ((quad * 32) << 16) + acc * BN + cb, r);
-                tc::tmem_ld_wait();
-                uint32_t res[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const uint32_t p0 = __float2uint_rn(__uint_as_float(r[4 * u]));
-                    const uint32_t p1 = __float2uint_rn(__uint_as_float(r[4 * u + 1]));
-                    const uint32_t p2 = __float2uint_rn(__uint_as_float(r[4 * u + 2]));
-                    const uint32_t p3 = __float2uint_rn(__uint_as_float(r[4 * u + 3]));
-                    const uint64_t z = (uint64_t)p0 + ((uint64_t)p1 << 7) + ((uint64_t)p2 << 14) + ((uint64_t)p3 << 21);
-                    const uint32_t zl = (uint32_t)z, zh = (uint32_t)(z >> 32);
-                    uint32_t v = zh + __umulhi(zl * lc.qinv_neg, lc.q) + (zl != 0u);  // z 2^-32 mod q, [0, 2q)
-                    const uint32_t out = nt * OUTS + cb / 4 + u;
-                    if constexpr (MUL == MUL_TW_OUT_ROW || MUL == MUL_TW_DATA_ROW) {
-                        const size_t ti = MUL == MUL_TW_OUT_ROW ? (size_t)out * a.C + drow : (size_t)drow * a.C + out;
-                        const uint2 w = __ldg(a.tw + (size_t)limb * a.R * a.C + ti);
-                        v = mul_shoup_lazy(v, w.x, w.y, lc.q);
-                    } else if constexpr (MUL == MUL_HAD) {
-                        const uint32_t h = __ldg(a.had + mat + (size_t)drow * a.C + out);
-                        v = mul_mont_lazy(mul_mont_lazy(v, h, lc.q, lc.qinv_neg), lc.r2, lc.q, lc.qinv_neg);
-                    } else if constexpr (MUL == MUL_SQUARE) {
-                        const uint32_t vc = csub(v, lc.q);
-                        v = mul_mont_lazy(mul_mont_lazy(vc, vc, lc.q, lc.qinv_neg), lc.r2, lc.q, lc.qinv_neg);
-                    }
-                    res[u] = csub(v, lc.q);
+    } else {  // ---- epilogue: warps 2..9; warp % 4 is the TMEM lane quadrant, (warp - 2) / 4 the column half
+        const uint32_t quad = warp & 3, half = (warp - 2) >> 2;
+        uint32_t t = 0;
+        for (uint32_t item = cid; item < items; item += nclusters) {
+            uint32_t limb, pl, drow0;
+            item_rows(item, limb, pl, drow0);
+            const uint32_t drow = drow0 + quad * 32 + lane;  // data row held by this thread
+            const Limb lc = a.limbs[limb];
+            const size_t mat = (size_t)pl * a.R * a.C;      // start of this polynomial limb
+            bool ok = true;
+            for (uint32_t nt = 0; nt < ntiles; ++nt, ++t) {
+                const uint32_t acc = t & 1;
+                if (!tc::mbar_wait(&acc_full[acc], (t >> 1) & 1u, a.err, tc::ERR_TIMEOUT_ACC)) {
+                    ok = false;
+                    break;
                 }
-                const uint32_t out0 = nt * OUTS + cb / 4;
-                if constexpr (OUTK == OUT_DIGITS_T) {
-                    // next step's A operand: row = output index, digits of this data row at 4 drow
-                    uint16_t* base = a.out_digits + ((size_t)pl * a.OUT) * (4 * a.DN) + (size_t)drow * 4;
+                tc::tc_fence_after();
+#pragma unroll 1
+                for (int cb = half * (BN / 2); cb < (int)(half + 1) * (BN / 2); cb += 16) {
+                    uint32_t r[16];
+                    tc::tmem_ld16(tmem + ((quad * 32) << 16) + acc * BN + cb, r);
+                    tc::tmem_ld_wait();
+                    const uint32_t out0 = nt * OUTS + cb / 4;
+                    uint2 tw[4];
+                    if constexpr (MUL == MUL_TW_OUT_ROW || MUL == MUL_TW_DATA_ROW) {
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            // forward step 1: T[out][drow]; inverse step 1: the transposed table Tinv^T[out][drow]
+                            const size_t ti = MUL == MUL_TW_OUT_ROW ? (size_t)(out0 + u) * a.C + drow
+                                                                    : (size_t)(out0 + u) * a.R + drow;
+                            tw[u] = __ldg(a.tw + (size_t)limb * a.R * a.C + ti);
+                        }
+                    }
+                    uint32_t res[4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        const uint2 d = tc::split_digits4(res[u]);
-                        *reinterpret_cast<uint2*>(base + (size_t)(out0 + u) * (4 * a.DN)) = d;
+                        const uint32_t p0 = __float2uint_rn(__uint_as_float(r[4 * u]));
+                        const uint32_t p1 = __float2uint_rn(__uint_as_float(r[4 * u + 1]));
+                        const uint32_t p2 = __float2uint_rn(__uint_as_float(r[4 * u + 2]));
+                        const uint32_t p3 = __float2uint_rn(__uint_as_float(r[4 * u + 3]));
+                        const uint64_t z =
+                            (uint64_t)p0 + ((uint64_t)p1 << 7) + ((uint64_t)p2 << 14) + ((uint64_t)p3 << 21);
+                        const uint32_t zl = (uint32_t)z, zh = (uint32_t)(z >> 32);
+                        uint32_t v = zh + __umulhi(zl * lc.qinv_neg, lc.q) + (zl != 0u);  // z 2^-32 mod q, [0, 2q)
+                        const uint32_t out = out0 + u;
+                        if constexpr (MUL == MUL_TW_OUT_ROW || MUL == MUL_TW_DATA_ROW) {
+                            v = mul_shoup_lazy(v, tw[u].x, tw[u].y, lc.q);
+                        } else if constexpr (MUL == MUL_HAD) {
+                            const uint32_t h = __ldg(a.had + mat + (size_t)drow * a.C + out);
+                            v = mul_mont_lazy(mul_mont_lazy(v, h, lc.q, lc.qinv_neg), lc.r2, lc.q, lc.qinv_neg);
+                        } else if constexpr (MUL == MUL_SQUARE) {
+                            const uint32_t vc = csub(v, lc.q);
+                            v = mul_mont_lazy(mul_mont_lazy(vc, vc, lc.q, lc.qinv_neg), lc.r2, lc.q, lc.qinv_neg);
+                        }
+                        res[u] = csub(v, lc.q);
                     }
-                } else if constexpr (OUTK == OUT_U32_ROW_DATA) {
-                    *reinterpret_cast<uint4*>(a.out + mat + (size_t)drow * a.C + out0) =
-                        make_uint4(res[0], res[1], res[2], res[3]);
-                } else {
+                    if constexpr (OUTK == OUT_DIGITS_T) {
+                        // next step's A operand: row = output index, digits of this data row at 4 drow
+                        uint16_t* base = a.out_digits + ((size_t)pl * a.OUT) * (4 * a.DN) + (size_t)drow * 4;
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) a.out[mat + (size_t)(out0 + u) * a.C + drow] = res[u];
+                        for (int u = 0; u < 4; ++u) {
+                            const uint2 d = tc::split_digits4(res[u]);
+                            *reinterpret_cast<uint2*>(base + (size_t)(out0 + u) * (4 * a.DN)) = d;
+                        }
+                    } else if constexpr (OUTK == OUT_U32_ROW_DATA) {
+                        *reinterpret_cast<uint4*>(a.out + mat + (size_t)drow * a.C + out0) =
+                            make_uint4(res[0], res[1], res[2], res[3]);
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) a.out[mat + (size_t)(out0 + u) * a.C + drow] = res[u];
+                    }
                 }
+                tc::tc_fence_before();
+                tc::mbar_arrive(&acc_empty[acc]);
             }
-            tc::tc_fence_before();
-            tc::mbar_arrive(&acc_empty[acc]);
+            if (!ok) break;
         }
     }
     tc::tc_fence_before();
@@ -336,7 +362,7 @@ struct Tc2Tables {
     uint16_t* cst[4] = {nullptr, nullptr, nullptr, nullptr};  // fp16 [L][OUT x 4][4V]
     CUtensorMap bmaps[4][3];                                   // per step, per cluster size 4/2/1
     uint2* T = nullptr;
-    uint2* Tinv = nullptr;
+    uint2* Tinv = nullptr;  // transposed: [L][C][R]
     tc2::Limb* limbs = nullptr;
     uint32_t* err = nullptr;
     uint16_t* dig1 = nullptr;  // first-step digits
@@ -395,7 +421,9 @@ cudaError_t tc2_prepare(hefx_params* p) {
             for (uint32_t j2 = 0; j2 < C; ++j2) {
                 const uint64_t w = P((uint64_t)j2 * kodd), wi = Pn((uint64_t)j2 * kodd);
                 hT[(size_t)l * N + (size_t)p1 * C + j2] = make_uint2((uint32_t)w, shoup(w, q));
-                hTi[(size_t)l * N + (size_t)p1 * C + j2] = make_uint2((uint32_t)wi, shoup(wi, q));
+                // inverse twiddle stored transposed ([j2][p1]): the inverse step-1 epilogue holds
+                // one p1 per lane and walks j2, so lanes read consecutive entries
+                hTi[(size_t)l * N + (size_t)j2 * R + p1] = make_uint2((uint32_t)wi, shoup(wi, q));
             }
         }
         for (uint32_t p2 = 0; p2 < C; ++p2) {
@@ -485,7 +513,30 @@ cudaError_t launch_gemm(const CUtensorMap& amap, const CUtensorMap& bmap, const 
     }
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
-    cfg.gridDim = dim3(g.L * g.batch * (g.DN / BM));
+    const uint32_t items = g.L * g.batch * (g.DN / BM) / g.cs;
+    uint32_t clusters = items;
+    {
+        // persistent: as many clusters as can be resident at once (cached per cluster size)
+        static int max_clusters[5] = {0, 0, 0, 0, 0};
+        if (!max_clusters[g.cs]) {
+            cudaLaunchConfig_t q = {};
+            cudaLaunchAttribute qa[1];
+            q.gridDim = dim3(g.cs * 64);
+            q.blockDim = dim3(THREADS);
+            q.dynamicSmemBytes = SMEM_BYTES;
+            qa[0].id = cudaLaunchAttributeClusterDimension;
+            qa[0].val.clusterDim.x = g.cs;
+            qa[0].val.clusterDim.y = 1;
+            qa[0].val.clusterDim.z = 1;
+            q.attrs = qa;
+            q.numAttrs = 1;
+            int n = 0;
+            if (cudaOccupancyMaxActiveClusters(&n, kern, &q) != cudaSuccess || n <= 0) n = 1;
+            max_clusters[g.cs] = n;
+        }
+        clusters = std::min<uint32_t>(items, (uint32_t)max_clusters[g.cs]);
+    }
+    cfg.gridDim = dim3(clusters * g.cs);
     cfg.blockDim = dim3(THREADS);
     cfg.dynamicSmemBytes = SMEM_BYTES;
     cfg.stream = s;
@@ -519,7 +570,8 @@ cudaError_t step(const hefx_params* p, int stp, int outk, int mul, const uint16_
     g.OUT = trans_data ? t->R : t->C;
     g.K = 4 * g.OUT;  // reduction length equals the output count (square matrices)
     const uint32_t blocks = g.batch * (g.DN / BM);
-    g.cs = blocks % 4 == 0 ? 4 : blocks % 2 == 0 ? 2 : 1;
+    // clusters of 2 (constant multicast to 2 CTAs): pairs fill the GPCs better than quads
+    g.cs = blocks % 2 == 0 ? 2 : 1;
     CUtensorMap amap;
     if (!encode_map_2d(&amap, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, const_cast<uint16_t*>(adig), g.K,
                        (uint64_t)batch * g.L * g.DN, 2ull * g.K, BK, BM, CU_TENSOR_MAP_SWIZZLE_128B))
