@@ -3,16 +3,22 @@
 // the printed algorithm are replaced by the textbook ones), with lazy Shoup butterflies.
 //
 // GB300 mapping
-//  - One CTA holds a whole limb (N <= 2^15) or half of one (N = 2^16) in shared memory,
-//    so each limb is read from and written to HBM once per transform (512 KiB per
-//    N = 2^16 limb-NTT).  A CTA with N < 2^13 holds 2^13 / N limbs.
-//  - N = 2^16 uses a 2-CTA cluster.  Forward: the first stage (pairs j, j + N/2) is
-//    computed while loading, each CTA producing its own half (both read the whole limb,
-//    the second read hits L2).  Inverse: the last stage is exchanged through distributed
-//    shared memory.
-//  - Stages run in register passes of up to 5 stages (radix-32 sub-transforms); each pass
-//    reads and writes shared memory once.  Shared memory is padded by one word per 32 so
-//    that both strided and contiguous sub-transform accesses are bank-conflict free.
+//  - A row (one limb of one polynomial) is held in shared memory by one CTA (N <= 2^15) or
+//    split over a cluster of P CTAs (P = 8 at N = 2^16: 32 KiB + padding and 128 threads
+//    per CTA, registers sized for five CTAs of different rows per SM, so that their load,
+//    compute and barrier phases overlap).  Each row is read from and written to HBM once
+//    per transform (512 KiB per N = 2^16 limb-NTT).  A CTA with N < 2^13 holds 2^13 / N
+//    rows.
+//  - With P > 1 the log2(P) stages whose butterflies pair elements of different CTAs run
+//    as one radix-P step through distributed shared memory: the forward transform computes
+//    them while loading (each position j' of the first N/P is owned by one thread of the
+//    cluster, which reads the P inputs j' + t N/P from global memory and stores output t
+//    into CTA t's shared memory); the inverse computes them last, reading the P CTAs'
+//    shared memory and writing global memory.
+//  - The other stages run in register passes of up to 5 stages (radix-32 sub-transforms);
+//    each pass reads and writes shared memory once.  Shared memory is padded by one word
+//    per 32 so that both strided and contiguous sub-transform accesses are bank-conflict
+//    free.
 //  - The forward output is in bit-reversed order with no shuffle (the twiddle table is
 //    stored in bit-reversed order, as MAT folds permutations into constants, Sec. IV-B).
 #pragma once
@@ -30,14 +36,34 @@ namespace cc {
 
 __device__ __forceinline__ int pad(int j) { return j + (j >> 5); }
 
+// Tuning knobs: log2 of the CTAs per row at N = 2^16 and 2^15, the threads of a CTA that
+// holds less than 2^15 elements of a split row, and the CTAs per SM its register budget
+// is sized for.
+#ifndef HEFX_CC_LOGP16
+#define HEFX_CC_LOGP16 3
+#endif
+#ifndef HEFX_CC_LOGP15
+#define HEFX_CC_LOGP15 0
+#endif
+#ifndef HEFX_CC_SPLIT_THREADS
+#define HEFX_CC_SPLIT_THREADS 128
+#endif
+#ifndef HEFX_CC_SPLIT_MINB
+#define HEFX_CC_SPLIT_MINB 5
+#endif
+
 template <int LOGN>
 struct Cfg {
-    static constexpr bool split = LOGN >= 16;
-    static constexpr int logm = split ? LOGN - 1 : LOGN;  // elements of one row segment
+    static constexpr int logP = LOGN >= 16 ? HEFX_CC_LOGP16 : (LOGN == 15 ? HEFX_CC_LOGP15 : 0);
+    static constexpr int P = 1 << logP;  // CTAs (one cluster) per row
+    static constexpr bool split = P > 1;
+    static constexpr int logm = LOGN - logP;  // elements of one row segment
     static constexpr int m = 1 << logm;
-    static constexpr int rows = logm >= 13 ? 1 : (1 << (13 - logm));  // row segments per CTA
+    static constexpr int rows = (split || logm >= 13) ? 1 : (1 << (13 - logm));  // row segments per CTA
     static constexpr int elems = m * rows;
-    static constexpr int threads = elems >= (1 << 14) ? 512 : 256;
+    static constexpr bool small_split = split && m < (1 << 15);
+    static constexpr int threads = small_split ? HEFX_CC_SPLIT_THREADS : (elems >= (1 << 14) ? 512 : 256);
+    static constexpr int minb = small_split ? HEFX_CC_SPLIT_MINB : 1;
     static constexpr int smem_bytes = (elems + elems / 32) * 4;
     static constexpr int S = logm;                  // stages run inside the CTA
     static constexpr int r_small = S < 5 ? S : 5;   // pass over the smallest strides
@@ -46,6 +72,9 @@ struct Cfg {
     __host__ __device__ static constexpr int big(int i) {
         return nrest == 0 ? 0 : rest / nrest + (i < rest % nrest ? 1 : 0);
     }
+    static_assert(!split || (m / P) % threads == 0, "cross-CTA positions divide among the threads");
+    static_assert(P <= 8, "portable cluster sizes only");
+    static_assert(threads >= 128, "at least four warps per CTA");
 };
 
 struct KArgs {
@@ -85,12 +114,13 @@ __device__ __forceinline__ uint32_t row_limb(const KArgs& a, uint32_t r) {
 }
 
 // Where a register pass takes its inputs and puts its outputs.
-enum : int { SRC_SMEM = 0, SRC_GLOBAL = 1, SRC_SPLIT0 = 2, SRC_GLOBAL_HAD = 3 };
+enum : int { SRC_SMEM = 0, SRC_GLOBAL = 1, SRC_GLOBAL_HAD = 3 };
 enum : int { DST_SMEM = 0, DST_GLOBAL = 1, DST_GLOBAL_REDUCE = 2 };
 
-// The CTA's share of the batch: rows [row0, row0 + nrows) (or one half of row row0).
+// The CTA's share of the batch: rows [row0, row0 + nrows), or segment `part` (elements
+// [gbase, gbase + m)) of row row0 when the row is split.
 struct Seg {
-    uint32_t row0, gbase, half;
+    uint32_t row0, gbase, part;
     int nrows;
 };
 
@@ -104,7 +134,7 @@ __device__ __forceinline__ uint32_t reduce_out(uint32_t x, uint32_t q) {
 // Loads the 2^R elements jb + k * 2^logs (k < 2^R) of local row `row` into x.
 template <int R, int LOGN, int logs, int SRC, int F>
 __device__ __forceinline__ void load_elems(uint32_t (&x)[1 << R], const uint32_t* sm, const KArgs& a, const Seg& sg,
-                                           int row, int jb, const LimbConst& lc, const uint2* tw) {
+                                           int row, int jb, const LimbConst& lc) {
     using C = Cfg<LOGN>;
     constexpr int N = 1 << LOGN;
     if constexpr (SRC == SRC_SMEM) {
@@ -115,19 +145,7 @@ __device__ __forceinline__ void load_elems(uint32_t (&x)[1 << R], const uint32_t
         const uint32_t grow_r = valid ? sg.row0 + row : sg.row0;
         const uint32_t* rin = row_in<N, F>(a, grow_r);
         const uint32_t* rhad = SRC == SRC_GLOBAL_HAD ? row_had<N, F>(a, grow_r) : nullptr;
-        if constexpr (SRC == SRC_SPLIT0) {
-            // first forward stage (pairs j, j + N/2) computed while loading: this CTA keeps
-            // X + w Y (half 0) or X - w Y (half 1), w = psi^brv(1)
-            const uint2 w = __ldg(&tw[1]);
-            const uint32_t q = lc.q;
-#pragma unroll
-            for (int k = 0; k < (1 << R); ++k) {
-                const size_t g = jb + (k << logs);
-                const uint32_t X = __ldg(rin + g), Y = __ldg(rin + g + N / 2);
-                const uint32_t t = mul_shoup_lazy(Y, w.x, w.y, q);
-                x[k] = sg.half ? X - t + 2 * q : X + t;
-            }
-        } else if constexpr (logs == 0 && R >= 2) {
+        if constexpr (logs == 0 && R >= 2) {
             const uint4* src = reinterpret_cast<const uint4*>(rin + sg.gbase + jb);
             const uint4* hs = reinterpret_cast<const uint4*>(rhad + sg.gbase + jb);
 #pragma unroll
@@ -190,7 +208,7 @@ __device__ __forceinline__ void store_elems(const uint32_t (&x)[1 << R], uint32_
 // Lazy-range schedule of the forward transform for moduli below 2^28 (flag F & 2): values
 // may grow to 16q < 2^32, so the conditional subtraction of the butterfly's first input is
 // only needed where the bound entering a stage (in units of q) would pass 16 after the stage.
-// s_first / b_first: first stage run by the kernel and the bound of its inputs.
+// s_first / b_first: first stage and the bound of its inputs (0 and 1: canonical input).
 __host__ __device__ constexpr int lazy_bound_in(int s_first, int b_first, int s) {
     int b = b_first;
     for (int t = s_first; t < s; ++t) b = (b + 2 > 16 ? 8 : b) + 2;
@@ -205,7 +223,7 @@ __device__ __forceinline__ void fwd_stages(uint32_t (&x)[1 << R], uint32_t g0, c
     // the smallest-stride pass reads the group-major part of the table
     constexpr bool PERM = (s0 + R == LOGN);
     constexpr bool LAZY = (F & 2) != 0;
-    constexpr int S_FIRST = LOGN >= 16 ? 1 : 0, B_FIRST = LOGN >= 16 ? 3 : 1;
+    constexpr int S_FIRST = 0, B_FIRST = 1;
     const uint32_t two_q = 2 * q, eight_q = 8 * q;
 #pragma unroll
     for (int v = 0; v < R; ++v) {
@@ -286,7 +304,7 @@ __device__ __forceinline__ void fwd_pass(uint32_t* sm, const Seg& sg, const KArg
         const LimbConst& lc = a.lc[limb];
         const uint2* tw = a.tw_f + (size_t)limb * N;
         uint32_t x[1 << R];
-        load_elems<R, LOGN, logtl, SRC, F>(x, sm, a, sg, row, jb, lc, tw);
+        load_elems<R, LOGN, logtl, SRC, F>(x, sm, a, sg, row, jb, lc);
         fwd_stages<R, LOGN, s0, F>(x, g0, tw, lc.q);
         store_elems<R, LOGN, logtl, DST, F>(x, sm, a, sg, row, jb, lc.q);
     }
@@ -309,7 +327,7 @@ __device__ __forceinline__ void inv_pass(uint32_t* sm, const Seg& sg, const KArg
         const LimbConst& lc = a.lc[limb];
         const uint2* tw = a.tw_i + (size_t)limb * N;
         uint32_t x[1 << R];
-        load_elems<R, LOGN, e0, SRC, F>(x, sm, a, sg, row, jb, lc, tw);
+        load_elems<R, LOGN, e0, SRC, F>(x, sm, a, sg, row, jb, lc);
         inv_stages<R, LOGN, SCALE, e0>(x, sg.gbase, j_hi, tw, lc);
         store_elems<R, LOGN, e0, DST, F>(x, sm, a, sg, row, jb, lc.q);
     }
@@ -333,7 +351,7 @@ __device__ __forceinline__ void fwd_had_inv_pass(uint32_t* sm, const Seg& sg, co
         const uint32_t limb = row_limb<F>(a, row < sg.nrows ? sg.row0 + row : sg.row0);
         const LimbConst& lc = a.lc[limb];
         uint32_t x[1 << R];
-        load_elems<R, LOGN, 0, SRC, F>(x, sm, a, sg, row, jb, lc, a.tw_f + (size_t)limb * N);
+        load_elems<R, LOGN, 0, SRC, F>(x, sm, a, sg, row, jb, lc);
         fwd_stages<R, LOGN, s0, F>(x, g0, a.tw_f + (size_t)limb * N, lc.q);
         const bool valid = row < sg.nrows;
         const uint4* hs = reinterpret_cast<const uint4*>(row_had<N, F>(a, valid ? sg.row0 + row : sg.row0) + sg.gbase + jb);
@@ -350,28 +368,44 @@ __device__ __forceinline__ void fwd_had_inv_pass(uint32_t* sm, const Seg& sg, co
     }
 }
 
+// 32-bit address of this CTA's shared-memory word `sm` in cluster rank t's shared memory
+// (shared::cluster window), and loads / stores through such addresses.
+__device__ __forceinline__ uint32_t cluster_addr(const uint32_t* sm, uint32_t t) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"((uint32_t)__cvta_generic_to_shared(sm)), "r"(t));
+    return r;
+}
+__device__ __forceinline__ void st_cluster(uint32_t addr, uint32_t v) {
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_cluster(uint32_t addr) {
+    uint32_t v;
+    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+    return v;
+}
+
 template <bool SPLIT>
 __device__ __forceinline__ void sync_all() {
     if constexpr (SPLIT) cg::this_cluster().sync();
     else __syncthreads();
 }
 
-// Forward passes I .. nrest-1 (big strides), SMEM -> SMEM except the first (from global).
+// Forward passes I .. nrest-1 (big strides), SMEM -> SMEM; the first reads global memory
+// unless the cross-CTA stages already filled shared memory.
 template <int LOGN, int I, int s, int F>
 __device__ __forceinline__ void fwd_big(uint32_t* sm, const Seg& sg, const KArgs& a) {
     using C = Cfg<LOGN>;
     if constexpr (I < C::nrest) {
         constexpr int r = C::big(I);
-        constexpr int SRC = I == 0 ? (C::split ? SRC_SPLIT0 : SRC_GLOBAL) : SRC_SMEM;
+        constexpr int SRC = (I == 0 && !C::split) ? SRC_GLOBAL : SRC_SMEM;
         fwd_pass<r, LOGN, s, SRC, DST_SMEM, F>(sm, sg, a);
-        if constexpr (I == 0) sync_all<C::split>();  // every global read done before any write
-        else __syncthreads();
+        __syncthreads();
         fwd_big<LOGN, I + 1, s + r, F>(sm, sg, a);
     }
 }
 
 // Inverse passes over big strides, from I down to 0; the last one writes global memory
-// unless the transform is split (then the cross-CTA stage follows).
+// unless the row is split (then the cross-CTA stages follow).
 template <int LOGN, int SCALE, int I, int e, int F>
 __device__ __forceinline__ void inv_big(uint32_t* sm, const Seg& sg, const KArgs& a) {
     using C = Cfg<LOGN>;
@@ -387,47 +421,77 @@ __device__ __forceinline__ void inv_big(uint32_t* sm, const Seg& sg, const KArgs
     }
 }
 
-// Last stage of a split inverse: pairs (j, j + N/2) live in the two CTAs of the cluster.
-template <int LOGN, int SCALE, int F>
-__device__ __forceinline__ void split_last_stage(uint32_t* sm, const Seg& sg, const KArgs& a) {
+// Forward stages 0 .. logP-1 of a split row, whose butterflies pair elements of different
+// CTAs: position j' < N/P is owned by one thread of the cluster, which reads the P inputs
+// j' + t N/P from global memory, runs the radix-P step and stores output t into CTA t's
+// shared memory.  Ends with a cluster barrier (outputs visible; every global read of the
+// row done before any CTA writes it, so in-place transforms are safe).
+template <int LOGN, int F>
+__device__ __forceinline__ void fwd_cross_pass(uint32_t* sm, const Seg& sg, const KArgs& a) {
     using C = Cfg<LOGN>;
-    constexpr int N = 1 << LOGN;
+    constexpr int N = 1 << LOGN, P = C::P, share = C::m / P;
+    cg::cluster_group cluster = cg::this_cluster();
+    uint32_t dst[P];
+#pragma unroll
+    for (int t = 0; t < P; ++t) dst[t] = cluster_addr(sm, t);
+    const uint32_t limb = row_limb<F>(a, sg.row0);
+    const LimbConst& lc = a.lc[limb];
+    const uint2* tw = a.tw_f + (size_t)limb * N;
+    const uint32_t* rin = row_in<N, F>(a, sg.row0);
+#pragma unroll 4
+    for (int it = 0; it < share / C::threads; ++it) {
+        const int j = (int)sg.part * share + it * C::threads + (int)threadIdx.x;
+        uint32_t x[P];
+#pragma unroll
+        for (int t = 0; t < P; ++t) x[t] = __ldg(rin + j + t * C::m);
+        fwd_stages<C::logP, LOGN, 0, F>(x, 0u, tw, lc.q);
+#pragma unroll
+        for (int t = 0; t < P; ++t) st_cluster(dst[t] + 4u * pad(j), x[t]);
+    }
+    cluster.sync();
+}
+
+// Inverse stages LOGN-logP .. LOGN-1 of a split row (the scale N^-1, or N^-1 2^32, folded
+// into the last): position j' < N/P is owned by one thread of the cluster, which reads it
+// from the P CTAs' shared memory and writes the P outputs j' + t N/P to global memory.
+// The closing barrier keeps this CTA's shared memory alive until its peers have read it.
+template <int LOGN, int SCALE, int F>
+__device__ __forceinline__ void inv_cross_pass(uint32_t* sm, const Seg& sg, const KArgs& a) {
+    using C = Cfg<LOGN>;
+    constexpr int N = 1 << LOGN, P = C::P, share = C::m / P;
     cg::cluster_group cluster = cg::this_cluster();
     cluster.sync();
-    const uint32_t* s0 = cluster.map_shared_rank(sm, 0);
-    const uint32_t* s1 = cluster.map_shared_rank(sm, 1);
-    const LimbConst& lc = a.lc[row_limb<F>(a, sg.row0)];
-    const uint32_t q = lc.q;
-    const uint32_t s = SCALE == 1 ? lc.ninv : lc.ninvR, ssh = SCALE == 1 ? lc.ninv_sh : lc.ninvR_sh;
-    const uint32_t w = SCALE == 1 ? lc.ninvw : lc.ninvRw, wsh = SCALE == 1 ? lc.ninvw_sh : lc.ninvRw_sh;
-    uint32_t* out = row_out<N, F>(a, sg.row0);
-    for (int i = threadIdx.x * 4; i < N / 4; i += C::threads * 4) {
-        const int j = sg.half * (N / 4) + i;
-        uint32_t r0[4], r1[4];
+    uint32_t src[P];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            const uint32_t X = s0[pad(j + t)], Y = s1[pad(j + t)];
-            const uint32_t u0 = mul_shoup_lazy(X + Y, s, ssh, q), u1 = mul_shoup_lazy(X - Y + 2 * q, w, wsh, q);
-            r0[t] = umin(u0, u0 - q);
-            r1[t] = umin(u1, u1 - q);
-        }
-        *reinterpret_cast<uint4*>(out + j) = make_uint4(r0[0], r0[1], r0[2], r0[3]);
-        *reinterpret_cast<uint4*>(out + j + N / 2) = make_uint4(r1[0], r1[1], r1[2], r1[3]);
+    for (int t = 0; t < P; ++t) src[t] = cluster_addr(sm, t);
+    const uint32_t limb = row_limb<F>(a, sg.row0);
+    const LimbConst& lc = a.lc[limb];
+    const uint2* tw = a.tw_i + (size_t)limb * N;
+    uint32_t* out = row_out<N, F>(a, sg.row0);
+#pragma unroll 4
+    for (int it = 0; it < share / C::threads; ++it) {
+        const int j = (int)sg.part * share + it * C::threads + (int)threadIdx.x;
+        uint32_t x[P];
+#pragma unroll
+        for (int t = 0; t < P; ++t) x[t] = ld_cluster(src[t] + 4u * pad(j));
+        inv_stages<C::logP, LOGN, SCALE, LOGN - C::logP>(x, 0u, 0, tw, lc);
+#pragma unroll
+        for (int t = 0; t < P; ++t) out[j + t * C::m] = x[t];
     }
-    cluster.sync();  // keep this CTA's shared memory alive until the peer has read it
+    cluster.sync();
 }
 
 template <int LOGN, int MODE, int F>
 __device__ __forceinline__ void run_task(uint32_t* sm, const Seg& sg, const KArgs& a) {
     using C = Cfg<LOGN>;
     constexpr int RS = C::r_small;
-    constexpr int S_FIRST = C::split ? 1 : 0;     // first global stage run by the CTA
+    constexpr int S_FIRST = C::logP;              // first stage run inside the CTA
     constexpr int S_SMALL = LOGN - RS;            // first stage of the smallest-stride pass
-    constexpr int SRC0 = C::split ? SRC_SPLIT0 : SRC_GLOBAL;
 
     if constexpr (MODE == MODE_FWD) {
+        if constexpr (C::split) fwd_cross_pass<LOGN, F>(sm, sg, a);
         if constexpr (C::nrest == 0) {
-            fwd_pass<RS, LOGN, S_FIRST, SRC0, DST_GLOBAL_REDUCE, F>(sm, sg, a);
+            fwd_pass<RS, LOGN, S_FIRST, C::split ? SRC_SMEM : SRC_GLOBAL, DST_GLOBAL_REDUCE, F>(sm, sg, a);
         } else {
             fwd_big<LOGN, 0, S_FIRST, F>(sm, sg, a);
             fwd_pass<RS, LOGN, S_SMALL, SRC_SMEM, DST_GLOBAL_REDUCE, F>(sm, sg, a);
@@ -441,44 +505,46 @@ __device__ __forceinline__ void run_task(uint32_t* sm, const Seg& sg, const KArg
             inv_pass<RS, LOGN, C::split ? 0 : SCALE, 0, SRC, DST_SMEM, F>(sm, sg, a);
             __syncthreads();
             inv_big<LOGN, SCALE, C::nrest - 1, RS, F>(sm, sg, a);
-            if constexpr (C::split) split_last_stage<LOGN, SCALE, F>(sm, sg, a);
+            if constexpr (C::split) inv_cross_pass<LOGN, SCALE, F>(sm, sg, a);
         }
     } else {  // MODE_FWD_HAD_INV
         if constexpr (C::nrest == 0 && !C::split) {
-            fwd_had_inv_pass<RS, LOGN, S_SMALL, SRC0, DST_GLOBAL, F>(sm, sg, a);
+            fwd_had_inv_pass<RS, LOGN, S_SMALL, SRC_GLOBAL, DST_GLOBAL, F>(sm, sg, a);
         } else {
+            if constexpr (C::split) fwd_cross_pass<LOGN, F>(sm, sg, a);
             fwd_big<LOGN, 0, S_FIRST, F>(sm, sg, a);
             fwd_had_inv_pass<RS, LOGN, S_SMALL, SRC_SMEM, DST_SMEM, F>(sm, sg, a);
             __syncthreads();
             inv_big<LOGN, 2, C::nrest - 1, RS, F>(sm, sg, a);
-            if constexpr (C::split) split_last_stage<LOGN, 2, F>(sm, sg, a);
+            if constexpr (C::split) inv_cross_pass<LOGN, 2, F>(sm, sg, a);
         }
     }
 }
 
 template <int LOGN, int MODE, int F>
-__global__ void __launch_bounds__(Cfg<LOGN>::threads) ntt_cc_kernel(KArgs a) {
+__global__ void __launch_bounds__(Cfg<LOGN>::threads, Cfg<LOGN>::minb) ntt_cc_kernel(KArgs a) {
     using C = Cfg<LOGN>;
     extern __shared__ __align__(16) uint32_t sm[];
-    // persistent: each CTA (or CTA pair) walks a strided sequence of tasks; a task is one
-    // row (split N) or C::rows rows
+    // persistent: each CTA (or cluster of P CTAs) walks a strided sequence of tasks; a task
+    // is one row (split N) or C::rows rows
     const uint32_t ntasks = C::split ? a.rows : (a.rows + C::rows - 1) / C::rows;
-    const uint32_t first = C::split ? blockIdx.x >> 1 : blockIdx.x;
-    const uint32_t stride = C::split ? gridDim.x >> 1 : gridDim.x;
+    const uint32_t first = blockIdx.x >> C::logP;
+    const uint32_t stride = gridDim.x >> C::logP;
     for (uint32_t task = first; task < ntasks; task += stride) {
         Seg sg;
         if constexpr (C::split) {
             sg.row0 = task;
-            sg.half = blockIdx.x & 1;
+            sg.part = blockIdx.x & (C::P - 1);  // == rank in the cluster
             sg.nrows = 1;
         } else {
             sg.row0 = task * C::rows;
-            sg.half = 0;
+            sg.part = 0;
             sg.nrows = (int)min((uint32_t)C::rows, a.rows - sg.row0);
         }
-        sg.gbase = sg.half * C::m;
+        sg.gbase = sg.part * C::m;
         run_task<LOGN, MODE, F>(sm, sg, a);
-        __syncthreads();  // shared memory is reused by the next task
+        // shared memory is reused by the next task; with a split row the peers write into it
+        if (task + stride < ntasks) sync_all<C::split>();
     }
 }
 
@@ -491,6 +557,7 @@ cudaError_t launch_one(const KArgs& a, size_t rows, cudaStream_t stream) {
     if (!attr_done) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::smem_bytes);
         if (e != cudaSuccess) return e;
+
         attr_done = true;
     }
     if (rows == 0) return cudaSuccess;
@@ -505,11 +572,11 @@ cudaError_t launch_one(const KArgs& a, size_t rows, cudaStream_t stream) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::threads, C::smem_bytes);
     // row lists run persistent (a grid of resident CTAs walking the list); the contiguous
     // layout launches one CTA (pair) per task
-    const size_t resident = F ? (size_t)sms * (size_t)(per_sm > 0 ? per_sm : 1) : (size_t)-1 / 4;
+    const size_t resident = (F & 1) ? (size_t)sms * (size_t)(per_sm > 0 ? per_sm : 1) : (size_t)-1 / 4;
     if (C::split) {
-        cfg.gridDim = dim3((unsigned)(2 * std::min(rows, resident / 2)));
+        cfg.gridDim = dim3((unsigned)(C::P * std::min(rows, resident / C::P)));
         attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.x = C::P;
         attr[0].val.clusterDim.y = 1;
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
