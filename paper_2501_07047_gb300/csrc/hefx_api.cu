@@ -183,6 +183,7 @@ hefx_status hefx_params_create(hefx_ctx* ctx, uint32_t log2n, const uint32_t* pr
         c.ninvRw = (uint32_t)vals[3];
         c.ninvRw_sh = shoup(vals[3], q);
         c.r2 = (uint32_t)mul_mod(r32, r32, q);
+        c.one_sh = shoup(1, q);
     }
     cudaError_t e = cudaMalloc(&p->d_lc, sizeof(LimbConst) * nlimbs);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_tw_fwd, sizeof(uint2) * twf.size());

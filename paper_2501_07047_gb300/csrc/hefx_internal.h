@@ -23,7 +23,8 @@ struct LimbConst {
     uint32_t ninvR, ninvR_sh;     // N^-1 * 2^32: undoes the 2^-32 of a Montgomery Hadamard product
     uint32_t ninvRw, ninvRw_sh;   // N^-1 * 2^32 * psi^-brv_N(1)
     uint32_t r2;                  // 2^64 mod q: two Montgomery products give a plain one
-    uint32_t pad[5];
+    uint32_t one_sh;              // floor(2^32 / q), Shoup companion of 1: any x < 2^32 -> [0, 2q)
+    uint32_t pad[4];
 };
 static_assert(sizeof(LimbConst) == 64, "LimbConst is one 64-byte line");
 

@@ -16,9 +16,8 @@
 //    into CTA t's shared memory); the inverse computes them last, reading the P CTAs'
 //    shared memory and writing global memory.
 //  - The other stages run in register passes of up to 5 stages (radix-32 sub-transforms);
-//    each pass reads and writes shared memory once.  Shared memory is padded by one word
-//    per 32 so that both strided and contiguous sub-transform accesses are bank-conflict
-//    free.
+//    each pass reads and writes shared memory once, in a swizzled layout (swz) where both
+//    strided and contiguous (uint4) sub-transform accesses are bank-conflict free.
 //  - The forward output is in bit-reversed order with no shuffle (the twiddle table is
 //    stored in bit-reversed order, as MAT folds permutations into constants, Sec. IV-B).
 #pragma once
@@ -34,7 +33,11 @@ namespace cg = cooperative_groups;
 namespace hefx {
 namespace cc {
 
-__device__ __forceinline__ int pad(int j) { return j + (j >> 5); }
+// Shared-memory word of element j: the 16-byte chunk index within each 32-word row is XORed
+// with the row's low three bits.  Consecutive elements (the strided passes' lanes) stay in
+// one row, and 16-byte groups of the contiguous sub-transforms (read and written as uint4)
+// of eight consecutive rows land on different banks: both patterns are conflict free.
+__device__ __forceinline__ int swz(int j) { return j ^ (((j >> 5) & 7) << 2); }
 
 // Tuning knobs: log2 of the CTAs per row at N = 2^16 and 2^15, the threads of a CTA that
 // holds less than 2^15 elements of a split row, and the CTAs per SM its register budget
@@ -64,7 +67,7 @@ struct Cfg {
     static constexpr bool small_split = split && m < (1 << 15);
     static constexpr int threads = small_split ? HEFX_CC_SPLIT_THREADS : (elems >= (1 << 14) ? 512 : 256);
     static constexpr int minb = small_split ? HEFX_CC_SPLIT_MINB : 1;
-    static constexpr int smem_bytes = (elems + elems / 32) * 4;
+    static constexpr int smem_bytes = elems * 4;
     static constexpr int S = logm;                  // stages run inside the CTA
     static constexpr int r_small = S < 5 ? S : 5;   // pass over the smallest strides
     static constexpr int rest = S - r_small;
@@ -124,11 +127,12 @@ struct Seg {
     int nrows;
 };
 
-// Canonical value of a forward output: from [0, 4q) (Harvey ranges) or [0, 16q) (lazy ranges).
+// Canonical value of a forward output: from [0, 4q) (Harvey ranges) or [0, 16q) (lazy
+// ranges, reduced to [0, 2q) by a Shoup product with 1 first).
 template <int F>
-__device__ __forceinline__ uint32_t reduce_out(uint32_t x, uint32_t q) {
-    if constexpr ((F & 2) != 0) x = csub(csub(x, 8 * q), 4 * q);
-    return csub(csub(x, 2 * q), q);
+__device__ __forceinline__ uint32_t reduce_out(uint32_t x, const LimbConst& lc) {
+    if constexpr ((F & 2) != 0) return csub(mul_shoup_lazy(x, 1u, lc.one_sh, lc.q), lc.q);
+    return csub(csub(x, 2 * lc.q), lc.q);
 }
 
 // Loads the 2^R elements jb + k * 2^logs (k < 2^R) of local row `row` into x.
@@ -138,8 +142,19 @@ __device__ __forceinline__ void load_elems(uint32_t (&x)[1 << R], const uint32_t
     using C = Cfg<LOGN>;
     constexpr int N = 1 << LOGN;
     if constexpr (SRC == SRC_SMEM) {
+        if constexpr (logs == 0 && R >= 2) {
 #pragma unroll
-        for (int k = 0; k < (1 << R); ++k) x[k] = sm[pad(row * C::m + jb + (k << logs))];
+            for (int k = 0; k < (1 << R); k += 4) {
+                const uint4 v = *reinterpret_cast<const uint4*>(&sm[swz(row * C::m + jb + k)]);
+                x[k] = v.x;
+                x[k + 1] = v.y;
+                x[k + 2] = v.z;
+                x[k + 3] = v.w;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < (1 << R); ++k) x[k] = sm[swz(row * C::m + jb + (k << logs))];
+        }
     } else {
         const bool valid = row < sg.nrows;
         const uint32_t grow_r = valid ? sg.row0 + row : sg.row0;
@@ -177,12 +192,18 @@ __device__ __forceinline__ void load_elems(uint32_t (&x)[1 << R], const uint32_t
 
 template <int R, int LOGN, int logs, int DST, int F>
 __device__ __forceinline__ void store_elems(const uint32_t (&x)[1 << R], uint32_t* sm, const KArgs& a, const Seg& sg,
-                                            int row, int jb, uint32_t q) {
+                                            int row, int jb, const LimbConst& lc) {
     using C = Cfg<LOGN>;
     constexpr int N = 1 << LOGN;
     if constexpr (DST == DST_SMEM) {
+        if constexpr (logs == 0 && R >= 2) {
 #pragma unroll
-        for (int k = 0; k < (1 << R); ++k) sm[pad(row * C::m + jb + (k << logs))] = x[k];
+            for (int k = 0; k < (1 << R); k += 4)
+                *reinterpret_cast<uint4*>(&sm[swz(row * C::m + jb + k)]) = make_uint4(x[k], x[k + 1], x[k + 2], x[k + 3]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < (1 << R); ++k) sm[swz(row * C::m + jb + (k << logs))] = x[k];
+        }
     } else {
         if (row >= sg.nrows) return;
         uint32_t* dst = row_out<N, F>(a, sg.row0 + row) + sg.gbase + jb;
@@ -191,27 +212,37 @@ __device__ __forceinline__ void store_elems(const uint32_t (&x)[1 << R], uint32_
             for (int k = 0; k < (1 << R); k += 4) {
                 uint4 v = make_uint4(x[k], x[k + 1], x[k + 2], x[k + 3]);
                 if constexpr (DST == DST_GLOBAL_REDUCE) {
-                    v.x = reduce_out<F>(v.x, q);
-                    v.y = reduce_out<F>(v.y, q);
-                    v.z = reduce_out<F>(v.z, q);
-                    v.w = reduce_out<F>(v.w, q);
+                    v.x = reduce_out<F>(v.x, lc);
+                    v.y = reduce_out<F>(v.y, lc);
+                    v.z = reduce_out<F>(v.z, lc);
+                    v.w = reduce_out<F>(v.w, lc);
                 }
                 reinterpret_cast<uint4*>(dst)[k / 4] = v;
             }
         } else {
 #pragma unroll
-            for (int k = 0; k < (1 << R); ++k) dst[k << logs] = DST == DST_GLOBAL_REDUCE ? reduce_out<F>(x[k], q) : x[k];
+            for (int k = 0; k < (1 << R); ++k) dst[k << logs] = DST == DST_GLOBAL_REDUCE ? reduce_out<F>(x[k], lc) : x[k];
         }
     }
 }
 
-// Lazy-range schedule of the forward transform for moduli below 2^28 (flag F & 2): values
-// may grow to 16q < 2^32, so the conditional subtraction of the butterfly's first input is
-// only needed where the bound entering a stage (in units of q) would pass 16 after the stage.
-// s_first / b_first: first stage and the bound of its inputs (0 and 1: canonical input).
-__host__ __device__ constexpr int lazy_bound_in(int s_first, int b_first, int s) {
-    int b = b_first;
-    for (int t = s_first; t < s; ++t) b = (b + 2 > 16 ? 8 : b) + 2;
+// Lazy-range schedules for moduli below 2^28 (flag F & 2), where values may grow to
+// 16q < 2^32.  A Shoup product with 1 (x - floor(x floor(2^32/q) / 2^32) q, two IMADs)
+// brings any 32-bit value into [0, 2q); it replaces the conditional subtractions of
+// Harvey's butterflies at the few stages where a bound (in units of q) would pass 16.
+//  - forward (Cooley-Tukey): the first input enters stage s below fwd_bound_in(s) q; it is
+//    reduced where fwd_bound_in(s) + 2 > 16, and the outputs are below (its bound + 2) q.
+//  - inverse (Gentleman-Sande): both inputs of stage e are below inv_bound_in(e) q (2 for a
+//    canonical or Montgomery-product input); the sum doubles the bound and is reduced where
+//    it would pass 8 (so the next stage's sum and difference stay below 16q).
+__host__ __device__ constexpr int fwd_bound_in(int s) {
+    int b = 1;
+    for (int t = 0; t < s; ++t) b = (b + 2 > 16 ? 2 : b) + 2;
+    return b;
+}
+__host__ __device__ constexpr int inv_bound_in(int e) {
+    int b = 2;
+    for (int t = 0; t < e; ++t) b = 2 * b > 8 ? 2 : 2 * b;
     return b;
 }
 
@@ -219,16 +250,15 @@ __host__ __device__ constexpr int lazy_bound_in(int s_first, int b_first, int s)
 // and uses twiddle psi^brv(2^s + G) for group G (one load per group, reused by its
 // butterflies).  Without F & 2 every butterfly keeps Harvey's [0, 4q) range (q < 2^30).
 template <int R, int LOGN, int s0, int F>
-__device__ __forceinline__ void fwd_stages(uint32_t (&x)[1 << R], uint32_t g0, const uint2* tw, uint32_t q) {
+__device__ __forceinline__ void fwd_stages(uint32_t (&x)[1 << R], uint32_t g0, const uint2* tw, const LimbConst& lc) {
     // the smallest-stride pass reads the group-major part of the table
     constexpr bool PERM = (s0 + R == LOGN);
     constexpr bool LAZY = (F & 2) != 0;
-    constexpr int S_FIRST = 0, B_FIRST = 1;
-    const uint32_t two_q = 2 * q, eight_q = 8 * q;
+    const uint32_t q = lc.q, two_q = 2 * q;
 #pragma unroll
     for (int v = 0; v < R; ++v) {
         const int half = 1 << (R - 1 - v);
-        const bool corr = !LAZY || lazy_bound_in(S_FIRST, B_FIRST, s0 + v) + 2 > 16;
+        const bool corr = !LAZY || fwd_bound_in(s0 + v) + 2 > 16;
         uint2 w = make_uint2(0, 0);
 #pragma unroll
         for (int b = 0; b < (1 << (R - 1)); ++b) {
@@ -236,7 +266,7 @@ __device__ __forceinline__ void fwd_stages(uint32_t (&x)[1 << R], uint32_t g0, c
             const int k = (g << (R - v)) + (b & (half - 1));
             if ((b & (half - 1)) == 0)
                 w = __ldg(&tw[PERM ? (1u << (s0 + v)) + ((uint32_t)g << s0) + g0 : (1u << (s0 + v)) + (g0 << v) + g]);
-            const uint32_t xa = !corr ? x[k] : (LAZY ? umin(x[k], x[k] - eight_q) : umin(x[k], x[k] - two_q));
+            const uint32_t xa = !corr ? x[k] : (LAZY ? mul_shoup_lazy(x[k], 1u, lc.one_sh, q) : csub(x[k], two_q));
             const uint32_t t = mul_shoup_lazy(x[k + half], w.x, w.y, q);
             x[k] = xa + t;
             x[k + half] = xa - t + two_q;
@@ -246,26 +276,32 @@ __device__ __forceinline__ void fwd_stages(uint32_t (&x)[1 << R], uint32_t g0, c
 
 // R inverse (Gentleman-Sande) stages e0 .. e0+R-1 on registers; stage e pairs j, j + 2^e with
 // twiddle psi^-brv(N/2^(e+1) + G).  SCALE folds N^-1 (1) or N^-1 2^32 (2) into stage LOGN-1.
-template <int R, int LOGN, int SCALE, int e0>
+// Inputs are below 2q (canonical, or a Montgomery Hadamard product); outputs of the scaled
+// stage are canonical.  Without F & 2 every butterfly keeps Harvey's [0, 2q) range.
+template <int R, int LOGN, int SCALE, int e0, int F>
 __device__ __forceinline__ void inv_stages(uint32_t (&x)[1 << R], uint32_t gbase, int j_hi, const uint2* tw,
                                            const LimbConst& lc) {
     constexpr int N = 1 << LOGN;
     constexpr bool PERM = (e0 == 0);  // the smallest-stride pass reads the group-major table part
+    constexpr bool LAZY = (F & 2) != 0;
     const uint32_t q = lc.q, two_q = 2 * q;
     const uint32_t J = (gbase >> R) + (uint32_t)j_hi;  // global index of the sub-transform (e0 == 0)
 #pragma unroll
     for (int v = 0; v < R; ++v) {
         const int e = e0 + v;
         const int h = 1 << v;
+        // X - Y + c q >= 0 for Y below c q; the sum is reduced where its bound passes 8q
+        const uint32_t cq = LAZY ? (uint32_t)inv_bound_in(e) * q : two_q;
+        const bool red = !LAZY || 2 * inv_bound_in(e) > 8;
         if (SCALE && e == LOGN - 1) {
             const uint32_t s = SCALE == 1 ? lc.ninv : lc.ninvR, ssh = SCALE == 1 ? lc.ninv_sh : lc.ninvR_sh;
             const uint32_t w = SCALE == 1 ? lc.ninvw : lc.ninvRw, wsh = SCALE == 1 ? lc.ninvw_sh : lc.ninvRw_sh;
 #pragma unroll
             for (int kk = 0; kk < (1 << (R - 1)); ++kk) {
                 const uint32_t X = x[kk], Y = x[kk + h];
-                const uint32_t s0v = mul_shoup_lazy(X + Y, s, ssh, q), s1v = mul_shoup_lazy(X - Y + two_q, w, wsh, q);
-                x[kk] = umin(s0v, s0v - q);
-                x[kk + h] = umin(s1v, s1v - q);
+                const uint32_t s0v = mul_shoup_lazy(X + Y, s, ssh, q), s1v = mul_shoup_lazy(X - Y + cq, w, wsh, q);
+                x[kk] = csub(s0v, q);
+                x[kk + h] = csub(s1v, q);
             }
             continue;
         }
@@ -279,8 +315,8 @@ __device__ __forceinline__ void inv_stages(uint32_t (&x)[1 << R], uint32_t gbase
                 w = __ldg(&tw[PERM ? (uint32_t)(N >> (e + 1)) + ((uint32_t)g << (LOGN - R)) + J : hbase + g]);
             const uint32_t X = x[k], Y = x[k + h];
             const uint32_t sum = X + Y;
-            x[k] = umin(sum, sum - two_q);
-            x[k + h] = mul_shoup_lazy(X - Y + two_q, w.x, w.y, q);
+            x[k] = !red ? sum : (LAZY ? mul_shoup_lazy(sum, 1u, lc.one_sh, q) : csub(sum, two_q));
+            x[k + h] = mul_shoup_lazy(X - Y + cq, w.x, w.y, q);
         }
     }
 }
@@ -294,7 +330,7 @@ __device__ __forceinline__ void fwd_pass(uint32_t* sm, const Seg& sg, const KArg
     constexpr int lognsub = C::logm - R;
     constexpr int nsub = 1 << lognsub;
     for (int u = threadIdx.x; u < C::rows * nsub; u += C::threads) {
-        const int row = u >> lognsub;
+        const int row = C::rows == 1 ? 0 : u >> lognsub;
         const int uu = u & (nsub - 1);
         const int j_lo = uu & ((1 << logtl) - 1);
         const int j_hi = uu >> logtl;
@@ -305,8 +341,8 @@ __device__ __forceinline__ void fwd_pass(uint32_t* sm, const Seg& sg, const KArg
         const uint2* tw = a.tw_f + (size_t)limb * N;
         uint32_t x[1 << R];
         load_elems<R, LOGN, logtl, SRC, F>(x, sm, a, sg, row, jb, lc);
-        fwd_stages<R, LOGN, s0, F>(x, g0, tw, lc.q);
-        store_elems<R, LOGN, logtl, DST, F>(x, sm, a, sg, row, jb, lc.q);
+        fwd_stages<R, LOGN, s0, F>(x, g0, tw, lc);
+        store_elems<R, LOGN, logtl, DST, F>(x, sm, a, sg, row, jb, lc);
     }
 }
 
@@ -318,7 +354,7 @@ __device__ __forceinline__ void inv_pass(uint32_t* sm, const Seg& sg, const KArg
     constexpr int lognsub = C::logm - R;
     constexpr int nsub = 1 << lognsub;
     for (int u = threadIdx.x; u < C::rows * nsub; u += C::threads) {
-        const int row = u >> lognsub;
+        const int row = C::rows == 1 ? 0 : u >> lognsub;
         const int uu = u & (nsub - 1);
         const int j_lo = uu & ((1 << e0) - 1);
         const int j_hi = uu >> e0;
@@ -328,8 +364,8 @@ __device__ __forceinline__ void inv_pass(uint32_t* sm, const Seg& sg, const KArg
         const uint2* tw = a.tw_i + (size_t)limb * N;
         uint32_t x[1 << R];
         load_elems<R, LOGN, e0, SRC, F>(x, sm, a, sg, row, jb, lc);
-        inv_stages<R, LOGN, SCALE, e0>(x, sg.gbase, j_hi, tw, lc);
-        store_elems<R, LOGN, e0, DST, F>(x, sm, a, sg, row, jb, lc.q);
+        inv_stages<R, LOGN, SCALE, e0, F>(x, sg.gbase, j_hi, tw, lc);
+        store_elems<R, LOGN, e0, DST, F>(x, sm, a, sg, row, jb, lc);
     }
 }
 
@@ -344,7 +380,7 @@ __device__ __forceinline__ void fwd_had_inv_pass(uint32_t* sm, const Seg& sg, co
     constexpr int nsub = 1 << lognsub;
     static_assert(LOGN - s0 - R == 0, "the fused pass covers the smallest strides");
     for (int u = threadIdx.x; u < C::rows * nsub; u += C::threads) {
-        const int row = u >> lognsub;
+        const int row = C::rows == 1 ? 0 : u >> lognsub;
         const int j_hi = u & (nsub - 1);
         const int jb = j_hi << R;
         const uint32_t g0 = (sg.gbase >> R) + (uint32_t)j_hi;
@@ -352,7 +388,7 @@ __device__ __forceinline__ void fwd_had_inv_pass(uint32_t* sm, const Seg& sg, co
         const LimbConst& lc = a.lc[limb];
         uint32_t x[1 << R];
         load_elems<R, LOGN, 0, SRC, F>(x, sm, a, sg, row, jb, lc);
-        fwd_stages<R, LOGN, s0, F>(x, g0, a.tw_f + (size_t)limb * N, lc.q);
+        fwd_stages<R, LOGN, s0, F>(x, g0, a.tw_f + (size_t)limb * N, lc);
         const bool valid = row < sg.nrows;
         const uint4* hs = reinterpret_cast<const uint4*>(row_had<N, F>(a, valid ? sg.row0 + row : sg.row0) + sg.gbase + jb);
 #pragma unroll
@@ -363,8 +399,8 @@ __device__ __forceinline__ void fwd_had_inv_pass(uint32_t* sm, const Seg& sg, co
             x[k + 2] = mul_mont_lazy(x[k + 2], h.z, lc.q, lc.qinv_neg);
             x[k + 3] = mul_mont_lazy(x[k + 3], h.w, lc.q, lc.qinv_neg);
         }
-        inv_stages<R, LOGN, 2, 0>(x, sg.gbase, j_hi, a.tw_i + (size_t)limb * N, lc);
-        store_elems<R, LOGN, 0, DST, F>(x, sm, a, sg, row, jb, lc.q);
+        inv_stages<R, LOGN, 2, 0, F>(x, sg.gbase, j_hi, a.tw_i + (size_t)limb * N, lc);
+        store_elems<R, LOGN, 0, DST, F>(x, sm, a, sg, row, jb, lc);
     }
 }
 
@@ -375,12 +411,17 @@ __device__ __forceinline__ uint32_t cluster_addr(const uint32_t* sm, uint32_t t)
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"((uint32_t)__cvta_generic_to_shared(sm)), "r"(t));
     return r;
 }
-__device__ __forceinline__ void st_cluster(uint32_t addr, uint32_t v) {
-    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+__device__ __forceinline__ void st_cluster4(uint32_t addr, uint4 v) {
+    asm volatile("st.shared::cluster.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z),
+                 "r"(v.w)
+                 : "memory");
 }
-__device__ __forceinline__ uint32_t ld_cluster(uint32_t addr) {
-    uint32_t v;
-    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+__device__ __forceinline__ uint4 ld_cluster4(uint32_t addr) {
+    uint4 v;
+    asm volatile("ld.shared::cluster.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "r"(addr)
+                 : "memory");
     return v;
 }
 
@@ -422,15 +463,16 @@ __device__ __forceinline__ void inv_big(uint32_t* sm, const Seg& sg, const KArgs
 }
 
 // Forward stages 0 .. logP-1 of a split row, whose butterflies pair elements of different
-// CTAs: position j' < N/P is owned by one thread of the cluster, which reads the P inputs
-// j' + t N/P from global memory, runs the radix-P step and stores output t into CTA t's
-// shared memory.  Ends with a cluster barrier (outputs visible; every global read of the
-// row done before any CTA writes it, so in-place transforms are safe).
+// CTAs: position j' < N/P is owned by one thread of the cluster (four consecutive positions
+// per thread, moved as uint4), which reads the P inputs j' + t N/P from global memory, runs
+// the radix-P step and stores output t into CTA t's shared memory.  Ends with a cluster
+// barrier (outputs visible; every global read of the row done before any CTA writes it,
+// so in-place transforms are safe).
 template <int LOGN, int F>
 __device__ __forceinline__ void fwd_cross_pass(uint32_t* sm, const Seg& sg, const KArgs& a) {
     using C = Cfg<LOGN>;
-    constexpr int N = 1 << LOGN, P = C::P, share = C::m / P;
-    cg::cluster_group cluster = cg::this_cluster();
+    constexpr int N = 1 << LOGN, P = C::P, share = C::m / P, ITERS = share / (4 * C::threads);
+    static_assert(share % (4 * C::threads) == 0, "whole uint4 groups per thread");
     uint32_t dst[P];
 #pragma unroll
     for (int t = 0; t < P; ++t) dst[t] = cluster_addr(sm, t);
@@ -438,27 +480,37 @@ __device__ __forceinline__ void fwd_cross_pass(uint32_t* sm, const Seg& sg, cons
     const LimbConst& lc = a.lc[limb];
     const uint2* tw = a.tw_f + (size_t)limb * N;
     const uint32_t* rin = row_in<N, F>(a, sg.row0);
-#pragma unroll 4
-    for (int it = 0; it < share / C::threads; ++it) {
-        const int j = (int)sg.part * share + it * C::threads + (int)threadIdx.x;
-        uint32_t x[P];
+    for (int it = 0; it < ITERS; ++it) {
+        const int j = (int)sg.part * share + (it * C::threads + (int)threadIdx.x) * 4;
+        uint4 v[P];
 #pragma unroll
-        for (int t = 0; t < P; ++t) x[t] = __ldg(rin + j + t * C::m);
-        fwd_stages<C::logP, LOGN, 0, F>(x, 0u, tw, lc.q);
+        for (int t = 0; t < P; ++t) v[t] = __ldg(reinterpret_cast<const uint4*>(rin + j + t * C::m));
+        uint32_t x[4][P];
 #pragma unroll
-        for (int t = 0; t < P; ++t) st_cluster(dst[t] + 4u * pad(j), x[t]);
+        for (int t = 0; t < P; ++t) {
+            x[0][t] = v[t].x;
+            x[1][t] = v[t].y;
+            x[2][t] = v[t].z;
+            x[3][t] = v[t].w;
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) fwd_stages<C::logP, LOGN, 0, F>(x[c], 0u, tw, lc);
+#pragma unroll
+        for (int t = 0; t < P; ++t) st_cluster4(dst[t] + 4u * swz(j), make_uint4(x[0][t], x[1][t], x[2][t], x[3][t]));
     }
-    cluster.sync();
+    cg::this_cluster().sync();
 }
 
 // Inverse stages LOGN-logP .. LOGN-1 of a split row (the scale N^-1, or N^-1 2^32, folded
-// into the last): position j' < N/P is owned by one thread of the cluster, which reads it
-// from the P CTAs' shared memory and writes the P outputs j' + t N/P to global memory.
-// The closing barrier keeps this CTA's shared memory alive until its peers have read it.
+// into the last): position j' < N/P is owned by one thread of the cluster (four consecutive
+// positions per thread), which reads it from the P CTAs' shared memory and writes the P
+// outputs j' + t N/P to global memory.  The closing barrier keeps this CTA's shared memory
+// alive until its peers have read it.
 template <int LOGN, int SCALE, int F>
 __device__ __forceinline__ void inv_cross_pass(uint32_t* sm, const Seg& sg, const KArgs& a) {
     using C = Cfg<LOGN>;
-    constexpr int N = 1 << LOGN, P = C::P, share = C::m / P;
+    constexpr int N = 1 << LOGN, P = C::P, share = C::m / P, ITERS = share / (4 * C::threads);
+    static_assert(share % (4 * C::threads) == 0, "whole uint4 groups per thread");
     cg::cluster_group cluster = cg::this_cluster();
     cluster.sync();
     uint32_t src[P];
@@ -468,15 +520,24 @@ __device__ __forceinline__ void inv_cross_pass(uint32_t* sm, const Seg& sg, cons
     const LimbConst& lc = a.lc[limb];
     const uint2* tw = a.tw_i + (size_t)limb * N;
     uint32_t* out = row_out<N, F>(a, sg.row0);
-#pragma unroll 4
-    for (int it = 0; it < share / C::threads; ++it) {
-        const int j = (int)sg.part * share + it * C::threads + (int)threadIdx.x;
-        uint32_t x[P];
+    for (int it = 0; it < ITERS; ++it) {
+        const int j = (int)sg.part * share + (it * C::threads + (int)threadIdx.x) * 4;
+        uint4 v[P];
 #pragma unroll
-        for (int t = 0; t < P; ++t) x[t] = ld_cluster(src[t] + 4u * pad(j));
-        inv_stages<C::logP, LOGN, SCALE, LOGN - C::logP>(x, 0u, 0, tw, lc);
+        for (int t = 0; t < P; ++t) v[t] = ld_cluster4(src[t] + 4u * swz(j));
+        uint32_t x[4][P];
 #pragma unroll
-        for (int t = 0; t < P; ++t) out[j + t * C::m] = x[t];
+        for (int t = 0; t < P; ++t) {
+            x[0][t] = v[t].x;
+            x[1][t] = v[t].y;
+            x[2][t] = v[t].z;
+            x[3][t] = v[t].w;
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) inv_stages<C::logP, LOGN, SCALE, LOGN - C::logP, F>(x[c], 0u, 0, tw, lc);
+#pragma unroll
+        for (int t = 0; t < P; ++t)
+            *reinterpret_cast<uint4*>(out + j + t * C::m) = make_uint4(x[0][t], x[1][t], x[2][t], x[3][t]);
     }
     cluster.sync();
 }
@@ -548,42 +609,54 @@ __global__ void __launch_bounds__(Cfg<LOGN>::threads, Cfg<LOGN>::minb) ntt_cc_ke
     }
 }
 
-// rows == 0: set the kernel's attributes only (done before a stream capture).
+// rows == 0: set the kernel's attributes and measure its occupancy only (done before a
+// stream capture, so that a captured launch makes no query).
 template <int LOGN, int MODE, int F>
 cudaError_t launch_one(const KArgs& a, size_t rows, cudaStream_t stream) {
     using C = Cfg<LOGN>;
     auto kern = ntt_cc_kernel<LOGN, MODE, F>;
-    static bool attr_done = false;  // per template instance; benign race (idempotent call)
-    if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::smem_bytes);
-        if (e != cudaSuccess) return e;
-
-        attr_done = true;
-    }
-    if (rows == 0) return cudaSuccess;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     cfg.blockDim = dim3(C::threads);
     cfg.dynamicSmemBytes = C::smem_bytes;
     cfg.stream = stream;
-    int dev = 0, sms = 148, per_sm = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::threads, C::smem_bytes);
-    // row lists run persistent (a grid of resident CTAs walking the list); the contiguous
-    // layout launches one CTA (pair) per task
-    const size_t resident = (F & 1) ? (size_t)sms * (size_t)(per_sm > 0 ? per_sm : 1) : (size_t)-1 / 4;
     if (C::split) {
-        cfg.gridDim = dim3((unsigned)(C::P * std::min(rows, resident / C::P)));
         attr[0].id = cudaLaunchAttributeClusterDimension;
         attr[0].val.clusterDim.x = C::P;
         attr[0].val.clusterDim.y = 1;
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-    } else {
-        cfg.gridDim = dim3((unsigned)std::min((rows + C::rows - 1) / C::rows, resident));
     }
+    // The contiguous layout launches one CTA (cluster) per task and lets the hardware
+    // schedule them (measured faster than a persistent grid with the same number of tasks
+    // per CTA, whose lower occupancy costs more than the partial last wave); row lists run
+    // persistent on the co-resident CTAs (clusters) the runtime reports for this kernel,
+    // measured once per device.
+    int dev = 0;
+    cudaGetDevice(&dev);
+    static int cap[64] = {};  // per template instance and device; benign race (idempotent)
+    int& g_cap = cap[dev & 63];
+    if (g_cap == 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::smem_bytes);
+        if (e != cudaSuccess) return e;
+        int n = 0;
+        if (C::split) {
+            cfg.gridDim = dim3(C::P);
+            e = cudaOccupancyMaxActiveClusters(&n, kern, &cfg);
+        } else {
+            int sms = 0, per_sm = 0;
+            e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::threads, C::smem_bytes);
+            n = sms * per_sm;
+        }
+        if (e != cudaSuccess) return e;
+        g_cap = n > 0 ? n : 1;
+    }
+    if (rows == 0) return cudaSuccess;
+    const size_t tasks = C::split ? rows : (rows + C::rows - 1) / C::rows;
+    const size_t groups = (F & 1) ? std::min(tasks, (size_t)g_cap) : tasks;
+    cfg.gridDim = dim3((unsigned)(C::P * groups));
     return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
@@ -591,9 +664,9 @@ template <int LOGN, int F>
 cudaError_t launch_mode_d(NttMode mode, const KArgs& a, size_t rows, cudaStream_t s) {
     switch (mode) {
         case MODE_FWD: return launch_one<LOGN, MODE_FWD, F>(a, rows, s);
-        case MODE_INV: return launch_one<LOGN, MODE_INV, F & 1>(a, rows, s);
+        case MODE_INV: return launch_one<LOGN, MODE_INV, F>(a, rows, s);
         case MODE_FWD_HAD_INV: return launch_one<LOGN, MODE_FWD_HAD_INV, F>(a, rows, s);
-        default: return launch_one<LOGN, MODE_HAD_INV, F & 1>(a, rows, s);
+        default: return launch_one<LOGN, MODE_HAD_INV, F>(a, rows, s);
     }
 }
 
