@@ -65,6 +65,9 @@ def _load():
         lib.or_polymul_rows.argtypes = [i32, sz, _u32p, _u32p, _u32p, _u32p]
         lib.or_bconv.argtypes = [sz, i32, _u32p, i32, _u32p, _u32p, _u32p]
         lib.or_modmatmul.argtypes = [sz, sz, sz, u64, _u32p, _u32p, _u32p]
+        lib.or_moddown.argtypes = [sz, i32, _u32p, i32, _u32p, _u32p, _u32p]
+        lib.or_rescale.argtypes = [sz, i32, _u32p, _u32p, _u32p]
+        lib.or_key_inner_product.argtypes = [sz, i32, _u32p, i32, _u32p, _u32p, _u32p]
         for fn in ("or_ntt_direct", "or_ntt_fwd", "or_ntt_inv", "or_ntt_rows", "or_polymul_schoolbook",
                    "or_polymul_ntt", "or_polymul_rows", "or_bconv", "or_modmatmul"):
             getattr(lib, fn).restype = None
@@ -204,3 +207,39 @@ def modmatmul(A, B, q: int) -> np.ndarray:
     Z = np.empty((H, W), dtype=np.uint32)
     _load().or_modmatmul(H, V, W, q, _p(A), _p(B), _p(Z))
     return Z
+
+
+def moddown(x: np.ndarray, qs, ps) -> np.ndarray:
+    """ModDown: x [L + K][n] (Q limbs, then P limbs), coefficient form -> [L][n]:
+    (x_Q - BConv_{P->Q}(x_P)) * P^-1 mod q_j.  Batched over a leading axis."""
+    x = _u32(x)
+    if x.ndim == 3:
+        return np.stack([moddown(v, qs, ps) for v in x])
+    qs_a, ps_a = _u32(qs), _u32(ps)
+    assert x.shape[0] == qs_a.size + ps_a.size
+    out = np.empty((qs_a.size, x.shape[1]), dtype=np.uint32)
+    _load().or_moddown(x.shape[1], qs_a.size, _p(qs_a), ps_a.size, _p(ps_a), _p(x), _p(out))
+    return out
+
+
+def rescale(x: np.ndarray, qs) -> np.ndarray:
+    """Rescale: x [L][n] coefficient form over qs -> [L-1][n]: (x_i - x_{L-1}) q_{L-1}^-1 mod q_i."""
+    x = _u32(x)
+    if x.ndim == 3:
+        return np.stack([rescale(v, qs) for v in x])
+    qs_a = _u32(qs)
+    assert x.shape[0] == qs_a.size >= 2
+    out = np.empty((qs_a.size - 1, x.shape[1]), dtype=np.uint32)
+    _load().or_rescale(x.shape[1], qs_a.size, _p(qs_a), _p(x), _p(out))
+    return out
+
+
+def key_inner_product(digits: np.ndarray, evk: np.ndarray, qs) -> np.ndarray:
+    """sum_j digits[j] o evk[j][k] mod q per limb: digits [dnum][nl][n], evk [dnum][2][nl][n]
+    -> [2][nl][n]."""
+    digits, evk, qs_a = _u32(digits), _u32(evk), _u32(qs)
+    dnum, nl, n = digits.shape
+    assert evk.shape == (dnum, 2, nl, n) and qs_a.size == nl
+    out = np.empty((2, nl, n), dtype=np.uint32)
+    _load().or_key_inner_product(n, nl, _p(qs_a), dnum, _p(digits), _p(evk), _p(out))
+    return out

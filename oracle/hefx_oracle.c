@@ -18,7 +18,11 @@
  *    i.e. ahat[p] = a(psi^(2 brv(p) + 1));
  *  - inverse NTT: a_j = N^-1 * sum_p ahat[p] * psi^(-j (2 brv(p) + 1)) mod q;
  *  - basis conversion exactly as written in App. B (BConv), without any correction of the
- *    multiple of Q that the fast conversion may add.
+ *    multiple of Q that the fast conversion may add;
+ *  - ModDown, Rescale and the key-switching inner product (the HE operators of Sec. V-A and
+ *    the hybrid key switching with dnum digits of Sec. V-C, whose formulas the paper does
+ *    not print) as in textbook RNS-CKKS: ModDown(x) = (x_Q - BConv_{P->Q}(x_P)) * P^-1,
+ *    Rescale(x)_i = (x_i - x_{L-1}) * q_{L-1}^-1, both on coefficient-form residues.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -246,4 +250,50 @@ void or_modmatmul(size_t H, size_t V, size_t W, uint64_t q, const uint32_t* A, c
             for (size_t v = 0; v < V; ++v) acc += (u128)A[h * V + v] * B[v * W + w];
             Z[h * W + w] = (uint32_t)(acc % q);
         }
+}
+
+/* ------------------------------------------------------------------ key switching pieces
+ * ModDown: x is [L + K][n] (Q limbs q_0..q_{L-1}, then P limbs p_0..p_{K-1}), coefficient
+ * form.  out_j = (x_j - BConv_{P->Q}(x_P)_j) * P^-1 mod q_j, P = prod p_k.  out: [L][n]. */
+void or_moddown(size_t n, int L, const uint32_t* qs, int K, const uint32_t* ps, const uint32_t* x, uint32_t* out) {
+    uint32_t* y = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)L * n);
+    or_bconv(n, K, ps, L, qs, x + (size_t)L * n, y);
+    for (int j = 0; j < L; ++j) {
+        uint64_t P = 1;
+        for (int k = 0; k < K; ++k) P = mulmod(P, ps[k], qs[j]);
+        const uint64_t pinv = or_inverse(P, qs[j]);
+        for (size_t c = 0; c < n; ++c) {
+            const uint64_t d = (x[(size_t)j * n + c] + (uint64_t)qs[j] - y[(size_t)j * n + c] % qs[j]) % qs[j];
+            out[(size_t)j * n + c] = (uint32_t)mulmod(d, pinv, qs[j]);
+        }
+    }
+    free(y);
+}
+
+/* Rescale: x is [L][n] coefficient form over q_0..q_{L-1}.
+ * out_i = (x_i - (x_{L-1} mod q_i)) * q_{L-1}^-1 mod q_i for i < L - 1.  out: [L-1][n]. */
+void or_rescale(size_t n, int L, const uint32_t* qs, const uint32_t* x, uint32_t* out) {
+    const uint64_t ql = qs[L - 1];
+    for (int i = 0; i < L - 1; ++i) {
+        const uint64_t inv = or_inverse(ql % qs[i], qs[i]);
+        for (size_t c = 0; c < n; ++c) {
+            const uint64_t last = x[(size_t)(L - 1) * n + c] % qs[i];
+            const uint64_t d = (x[(size_t)i * n + c] + (uint64_t)qs[i] - last) % qs[i];
+            out[(size_t)i * n + c] = (uint32_t)mulmod(d, inv, qs[i]);
+        }
+    }
+}
+
+/* Key-switching inner product: digits [dnum][nl][n], evk [dnum][2][nl][n] (limb l reduced
+ * by qs[l]); out[k][l][c] = sum_j digits[j][l][c] * evk[j][k][l][c] mod qs[l], k = 0, 1. */
+void or_key_inner_product(size_t n, int nl, const uint32_t* qs, int dnum, const uint32_t* digits, const uint32_t* evk,
+                          uint32_t* out) {
+    for (int k = 0; k < 2; ++k)
+        for (int l = 0; l < nl; ++l)
+            for (size_t c = 0; c < n; ++c) {
+                u128 acc = 0;
+                for (int j = 0; j < dnum; ++j)
+                    acc += (u128)digits[((size_t)j * nl + l) * n + c] * evk[(((size_t)j * 2 + k) * nl + l) * n + c];
+                out[((size_t)k * nl + l) * n + c] = (uint32_t)(acc % qs[l]);
+            }
 }
