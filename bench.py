@@ -298,7 +298,8 @@ def run_gpu(args):
     del data, data0, flush
     torch.cuda.empty_cache()
     if not args.no_extras and world == 1:
-        line["extra"] = {"bconv_config3": bench_bconv(ctx, args), "batch_config4": bench_batch(ctx, args)}
+        line["extra"] = {"bconv_config3": bench_bconv(ctx, args), "batch_config4": bench_batch(ctx, args),
+                         "he_mult": bench_he_mult(ctx, args)}
         if args.serve:
             line["extra"]["serving_config5"] = bench_serving(ctx, args)
     hefx.hefx_destroy(ctx)
@@ -353,6 +354,48 @@ def bench_bconv(ctx, args):
     out["peak"] = f"{hbm} GB/s ({src} hbm_gbs)"
     hefx.hefx_bconv_plan_destroy(plan)
     return out
+
+
+def bench_he_mult(ctx, args):
+    """HE-Mult (tensor product + dnum-digit hybrid key switching) and Rescale of one ciphertext
+    pair at N = 2^16, the shapes of the paper's HE-operator table (L, log q, dnum) = (48, 28, 3)
+    and (24, 28, 3); K = alpha = L / dnum special 30-bit primes.  Synthetic keys and inputs."""
+    import torch
+    from paper_2501_07047_gb300 import inputs
+    from paper_2501_07047_gb300.hemult import HeMult
+    logn, n = 16, 1 << 16
+    res = {"workload": "HE-Mult = tensor product + relinearisation (ModUp, key inner product, ModDown); "
+                       "Rescale = INTT, rescale, NTT; one ciphertext pair, N = 2^16",
+           "paper_context_us": "CROSS TPU v6e-8 (48, 28, 3): HE-Mult 487, Rescale 74 (Table of HE operators)"}
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    s = torch.cuda.current_stream()
+    for L, dnum in ((48, 3), (24, 3)):
+        alpha = -(-L // dnum)
+        qs, ps = inputs.source_primes(L), inputs.special_primes(alpha)
+        hm = HeMult(ctx, logn, qs, ps, alpha)
+        qp = list(qs) + list(ps)
+
+        def d(a):
+            return torch.from_numpy(np.ascontiguousarray(a).view(np.int32).copy()).cuda()
+
+        ins = [d(inputs.residue_tensor(inputs.derive_seed(6, L, c), 1, qs, n)[0]) for c in range(4)]
+        evk = d(np.stack([np.stack([inputs.residue_tensor(inputs.derive_seed(6, L, 10 + j, k), 1, qp, n)[0]
+                                    for k in range(2)]) for j in range(hm.dnum)]))
+        cq = torch.empty((2, L, n), dtype=torch.int32, device="cuda")
+        out = torch.empty((2, L - 1, n), dtype=torch.int32, device="cuda")
+        for _ in range(3):
+            hm.run(*ins, evk, cq, s, rescale=False)
+            hm.rescale(cq.clone(), out, s)
+        steps = max(5, args.steps // 2)
+        mult_ms = _events_time(lambda: hm.run(*ins, evk, cq, s, rescale=False), steps, flush, s)
+        cw = cq.clone()
+        resc_ms = _events_time(lambda: hm.rescale(cw, out, s), steps, flush, s)
+        res[f"L{L}_dnum{dnum}"] = {"he_mult_us": round(mult_ms * 1e3, 1), "rescale_us": round(resc_ms * 1e3, 1),
+                                   "K": alpha, "launches_he_mult": hm.launches(rescale=False),
+                                   "launches_rescale": 3}
+        hm.close()
+        del ins, evk, cq, out, cw
+    return res
 
 
 def bench_batch(ctx, args):

@@ -166,6 +166,54 @@ hefx_status hefx_vec_mod_mul(hefx_ctx* ctx, const hefx_params* params, const uin
                              uint32_t* d_z, size_t batch, void* stream);
 
 /*
+ * z = x + y mod q per limb (VecModAdd, App. A), elementwise over [batch][nlimbs][N]; any of
+ * the buffers may alias.  Errors as for hefx_ntt_fwd.
+ */
+hefx_status hefx_vec_mod_add(hefx_ctx* ctx, const hefx_params* params, const uint32_t* d_x, const uint32_t* d_y,
+                             uint32_t* d_z, size_t batch, void* stream);
+
+/*
+ * Key-switching inner product of hybrid key switching with dnum digits (the HE-Mult /
+ * Relin. measured in Sec. V-A and V-C, "Effects of Security Parameters"; App. A builds it
+ * from VecModMul and VecModAdd): for each of `batch` inputs,
+ *   d_out[b][k][l] = sum_{j < dnum} d_digits[b][j][l] o d_evk[j][k][l]  mod q_l,  k = 0, 1,
+ * elementwise over the params' nlimbs limbs (the key-switching basis Q u P) in evaluation
+ * form.  Layouts: d_digits [batch][dnum][nlimbs][N], d_evk [dnum][2][nlimbs][N] (shared by
+ * the batch), d_out [batch][2][nlimbs][N]; inputs canonical.  d_out must not overlap an
+ * input.  Errors: as for hefx_ntt_fwd, and EINVAL for dnum outside [1, 64] or overlap.
+ * The paper keeps evaluation keys out of BAT (App. "Applying BAT to Preknown Parameters":
+ * the dnum-long reduction is too short for a matrix engine); this runs on the CUDA cores.
+ */
+hefx_status hefx_key_inner_product(hefx_ctx* ctx, const hefx_params* params, const uint32_t* d_digits,
+                                   const uint32_t* d_evk, uint32_t* d_out, uint32_t dnum, size_t batch, void* stream);
+
+/*
+ * ModDown of hybrid key switching (Sec. V-C; the formula is textbook RNS-CKKS, which the
+ * paper cites but does not print): with `plan` a basis conversion from the special primes
+ * P = p_0..p_{K-1} (its sources) to the ciphertext primes q_0..q_{L-1} (its targets),
+ *   d_out[b][j] = (x[b][j] - BConv_{P->Q}(x[b][L..L+K-1])_j) * P^-1  mod q_j,   j < L,
+ * where d_x is [batch][L + K][N] in coefficient form (the L ciphertext limbs, then the K
+ * special limbs) and d_out is [batch][L][N].  The conversion is the fast one of
+ * hefx_basis_convert, so the result represents floor(X / P) - u, 0 <= u < K, for the
+ * integer X that d_x represents.  d_out must not overlap d_x.  Runs on the CUDA cores.
+ * Errors: EINVAL for a null, foreign or misaligned argument or overlap.
+ */
+hefx_status hefx_mod_down(hefx_ctx* ctx, const hefx_bconv_plan* plan, const uint32_t* d_x, uint32_t* d_out,
+                          size_t batch, void* stream);
+
+/*
+ * Rescale by the last prime of the parameter set (the HE operator Rescale of Sec. V-A;
+ * textbook RNS-CKKS): for params over q_0..q_{L-1} (L >= 2), d_x [batch][L][N] and d_out
+ * [batch][L-1][N], both in coefficient form,
+ *   d_out[b][i] = (x[b][i] - (x[b][L-1] mod q_i)) * q_{L-1}^-1  mod q_i,   i < L - 1,
+ * i.e. floor(X / q_{L-1}) for the integer X that d_x represents.  d_out may equal d_x when
+ * batch == 1 (the result then occupies the first L - 1 rows); otherwise it must not overlap.
+ * Errors: as for hefx_ntt_fwd, and EINVAL for L < 2 or overlap.
+ */
+hefx_status hefx_rescale(hefx_ctx* ctx, const hefx_params* params, const uint32_t* d_x, uint32_t* d_out,
+                         size_t batch, void* stream);
+
+/*
  * Tensor product of two ciphertexts (a0, a1), (b0, b1) in evaluation (NTT) form, the first
  * step of HE-Mult (Sec. III; App. A: HE-Mult is built from NTT, INTT, BConv, VecModMul and
  * VecModAdd): d0 = a0 o b0, d1 = a0 o b1 + a1 o b0, d2 = a1 o b1 mod q, elementwise over

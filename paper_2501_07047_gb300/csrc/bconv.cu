@@ -2,6 +2,10 @@
 //
 //   out_{n,j} = sum_i [a_{n,i} * qhat_i^-1]_{q_i} * [qhat_i]_{p_j}  mod p_j
 //
+// The same kernel with a ModDown epilogue finishes hybrid key switching (the HE-Mult of
+// Sec. V-A): with the plan's sources the special primes P and its targets the ciphertext
+// primes, out_{n,j} = (x_{n,j} - BConv(x_P)_{n,j}) * P^-1 mod q_j.
+//
 // Step 1 is L independent VecModMuls by the constant qhat_i^-1 (Shoup products); step 2
 // is an (N, L, L') MatModMul whose right operand is the constant matrix [qhat_i]_{p_j}.
 // This file runs step 2 as 64-bit multiply-accumulates (each product < 2^58, L <= 64
@@ -38,6 +42,11 @@ cudaError_t bconv_plan_upload(hefx_bconv_plan* plan) {
     for (uint32_t j = 0; j < Lp; ++j) {
         h.p[j] = plan->dst[j];
         h.p_mu[j] = (uint64_t)(((u128)1 << 64) / plan->dst[j]);  // floor(2^64 / p_j)
+        uint64_t prod = 1;
+        for (uint32_t i = 0; i < L; ++i) prod = mul_mod(prod, plan->src[i], plan->dst[j]);
+        const uint64_t pinv = inv_mod(prod, plan->dst[j]);
+        h.pinv[j] = (uint32_t)pinv;
+        h.pinv_sh[j] = shoup(pinv, plan->dst[j]);
     }
     cudaError_t e = cudaMalloc(&plan->d_const, sizeof(BConvConst));
     if (e != cudaSuccess) return e;
@@ -63,9 +72,13 @@ __device__ __forceinline__ uint32_t barrett64(uint64_t x, uint32_t p, uint64_t m
 }
 
 // kCoef coefficients per thread: each constant load serves kCoef products (1 for n < 4).
-template <int kCoef>
+// Polynomial b's source limbs start at in + b * in_stride, its outputs at out + b * out_stride.
+// MODDOWN: the epilogue returns (x_j - conv_j) * P^-1 mod p_j, x_j at xq + b * in_stride + j n.
+template <int kCoef, bool MODDOWN>
 __global__ void __launch_bounds__(256) bconv_cc_kernel(const BConvConst* __restrict__ gc, const uint32_t* __restrict__ in,
-                                                       uint32_t* __restrict__ out, uint32_t n, uint32_t batch) {
+                                                       uint32_t* __restrict__ out, const uint32_t* __restrict__ xq,
+                                                       uint32_t n, uint32_t batch, size_t in_stride,
+                                                       size_t out_stride) {
     __shared__ BConvConst c;
     for (int i = threadIdx.x; i < (int)(sizeof(BConvConst) / 4); i += blockDim.x)
         reinterpret_cast<uint32_t*>(&c)[i] = reinterpret_cast<const uint32_t*>(gc)[i];
@@ -76,8 +89,8 @@ __global__ void __launch_bounds__(256) bconv_cc_kernel(const BConvConst* __restr
         // kCoef coefficients x, x + stride, ... of one polynomial (stride keeps warps coalesced)
         const size_t per_poly = n / kCoef;
         const size_t b = t / per_poly, x0 = t % per_poly;
-        const uint32_t* src = in + b * L * n + x0;
-        uint32_t* dst = out + b * Lp * n + x0;
+        const uint32_t* src = in + b * in_stride + x0;
+        uint32_t* dst = out + b * out_stride + x0;
         for (uint32_t j0 = 0; j0 < Lp; j0 += kJChunk) {
             uint64_t acc[kCoef][kJChunk];
 #pragma unroll
@@ -104,12 +117,25 @@ __global__ void __launch_bounds__(256) bconv_cc_kernel(const BConvConst* __restr
                 const uint32_t j = j0 + jj;
                 if (j < Lp) {
 #pragma unroll
-                    for (int u = 0; u < kCoef; ++u)
-                        dst[(size_t)j * n + u * per_poly] = barrett64(acc[u][jj], c.p[j], c.p_mu[j]);
+                    for (int u = 0; u < kCoef; ++u) {
+                        uint32_t r = barrett64(acc[u][jj], c.p[j], c.p_mu[j]);
+                        if constexpr (MODDOWN) {
+                            const uint32_t pj = c.p[j];
+                            const uint32_t x = __ldg(xq + b * in_stride + (size_t)j * n + x0 + u * per_poly);
+                            r = csub(mul_shoup_lazy(x + pj - r, c.pinv[j], c.pinv_sh[j], pj), pj);
+                        }
+                        dst[(size_t)j * n + u * per_poly] = r;
+                    }
                 }
             }
         }
     }
+}
+
+unsigned bconv_blocks(size_t total) {
+    size_t blocks = (total + 255) / 256;  // one coefficient per thread, many short blocks
+    const size_t cap = (size_t)1 << 20;
+    return (unsigned)(blocks > cap ? cap : blocks);
 }
 
 }  // namespace
@@ -119,20 +145,23 @@ cudaError_t launch_bconv_cc(const hefx_bconv_plan* plan, const uint32_t* in, uin
     const uint32_t n = 1u << plan->log2n;
     const size_t total = (size_t)n * batch;
     if (total == 0) return cudaSuccess;
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int kc = 1;  // measured: 4 coefficients per thread (95 registers) is slower than 1
-    // kc coefficients per thread, many short blocks: no ragged persistent tail
-    size_t blocks = (total / kc + 255) / 256;
-    const size_t cap = (size_t)1 << 20;
-    if (blocks > cap) blocks = cap;
-    (void)sms;
-    const BConvConst* gc = static_cast<const BConvConst*>(plan->d_const);
-    if (kc == 4)
-        bconv_cc_kernel<4><<<(unsigned)blocks, 256, 0, stream>>>(gc, in, out, n, (uint32_t)batch);
-    else
-        bconv_cc_kernel<1><<<(unsigned)blocks, 256, 0, stream>>>(gc, in, out, n, (uint32_t)batch);
+    // measured: 4 coefficients per thread (95 registers) is slower than 1
+    bconv_cc_kernel<1, false><<<bconv_blocks(total), 256, 0, stream>>>(
+        static_cast<const BConvConst*>(plan->d_const), in, out, nullptr, n, (uint32_t)batch, (size_t)plan->L * n,
+        (size_t)plan->Lp * n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mod_down(const hefx_bconv_plan* plan, const uint32_t* x, uint32_t* out, size_t batch,
+                            cudaStream_t stream) {
+    // x: [batch][Lp + L][n] (target-basis limbs first, then the plan's source limbs)
+    const uint32_t n = 1u << plan->log2n;
+    const size_t total = (size_t)n * batch;
+    if (total == 0) return cudaSuccess;
+    const size_t stride = (size_t)(plan->L + plan->Lp) * n;
+    bconv_cc_kernel<1, true><<<bconv_blocks(total), 256, 0, stream>>>(
+        static_cast<const BConvConst*>(plan->d_const), x + (size_t)plan->Lp * n, out, x, n, (uint32_t)batch, stride,
+        (size_t)plan->Lp * n);
     return cudaGetLastError();
 }
 

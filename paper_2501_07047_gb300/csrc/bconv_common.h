@@ -16,6 +16,8 @@ struct BConvConst {
     uint32_t qhat_inv_sh[kBConvMaxLimbs];  // its Shoup companion
     uint32_t p[kBConvMaxLimbs];            // target primes p_j
     uint64_t p_mu[kBConvMaxLimbs];         // floor(2^64 / p_j) (Barrett)
+    uint32_t pinv[kBConvMaxLimbs];         // (prod_i q_i)^-1 mod p_j (ModDown scale)
+    uint32_t pinv_sh[kBConvMaxLimbs];      // its Shoup companion
     uint32_t qhat_p[kBConvMaxLimbs * kBConvMaxLimbs];  // [i][j] = qhat_i mod p_j (step 2 matrix)
 };
 

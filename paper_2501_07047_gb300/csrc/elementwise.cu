@@ -1,9 +1,9 @@
-// Elementwise modular products of the HE-Mult request: VecModMul and the ciphertext tensor
-// product (Sec. III: HE-Mult = tensor product, then key switching built from INTT, BConv,
-// NTT and VecModMul).  Both operands are runtime residues, so BAT (which needs one known
-// factor) does not apply; the product is two Montgomery REDCs: mont(mont(x, y), 2^64 mod q)
-// = x y mod q.  HBM-bound: 12 bytes (VecModMul) or 28 bytes (tensor product) per
-// coefficient, vectorized 16-byte accesses, grid sized to the SM count.
+// Elementwise kernels of HE-Mult (App. A: HE operators are built from NTT, INTT, BConv,
+// VecModMul and VecModAdd): VecModMul, VecModAdd, the ciphertext tensor product, the
+// key-switching inner product and Rescale.  Both operands of a product are runtime
+// residues, so BAT (which needs one known factor) does not apply; the product is two
+// Montgomery REDCs: mont(mont(x, y), 2^64 mod q) = x y mod q.  All are HBM-bound
+// (vectorized 16-byte accesses, grid sized to the SM count).
 #include <algorithm>
 
 #include "hefx_internal.h"
@@ -46,6 +46,70 @@ __global__ void __launch_bounds__(256) tensor_product_kernel(const LimbConst* __
     }
 }
 
+__global__ void __launch_bounds__(256) vec_mod_add_kernel(const LimbConst* __restrict__ lc, uint32_t L, uint32_t n,
+                                                          size_t total4, const uint4* x, const uint4* y, uint4* z) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total4; i += (size_t)gridDim.x * blockDim.x) {
+        const uint32_t q = lc[((i * 4) / n) % L].q;
+        const uint4 a = x[i], b = y[i];
+        z[i] = make_uint4(csub(a.x + b.x, q), csub(a.y + b.y, q), csub(a.z + b.z, q), csub(a.w + b.w, q));
+    }
+}
+
+// Key-switching inner product: out[b][k][l] = sum_j dig[b][j][l] o evk[j][k][l] mod q_l over
+// the nl limbs of Q u P.  Each term is one REDC (x y 2^-32 in [0, 2q)); the running sum is kept
+// in [0, 2q) and one REDC by 2^64 mod q at the end removes the 2^-32.
+__device__ __forceinline__ uint32_t kip_term(uint32_t acc, uint32_t x, uint32_t y, const LimbConst& c) {
+    return csub(acc + mul_mont_lazy(x, y, c.q, c.qinv_neg), 2 * c.q);
+}
+__device__ __forceinline__ uint32_t kip_final(uint32_t acc, const LimbConst& c) {
+    return csub(mul_mont_lazy(acc, c.r2, c.q, c.qinv_neg), c.q);
+}
+
+__global__ void __launch_bounds__(256) key_inner_product_kernel(const LimbConst* __restrict__ lc, uint32_t nl,
+                                                                uint32_t n, uint32_t dnum, size_t batch,
+                                                                const uint4* dig, const uint4* evk, uint4* out) {
+    const size_t per_poly4 = (size_t)nl * n / 4;  // uint4 groups of one polynomial over Q u P
+    const size_t total4 = batch * per_poly4;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total4; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t b = i / per_poly4, e = i % per_poly4;
+        const LimbConst c = lc[(e * 4) / n];
+        uint4 a0 = make_uint4(0, 0, 0, 0), a1 = make_uint4(0, 0, 0, 0);
+        for (uint32_t j = 0; j < dnum; ++j) {
+            const uint4 d = dig[(b * dnum + j) * per_poly4 + e];
+            const uint4 k0 = evk[(size_t)(2 * j) * per_poly4 + e], k1 = evk[(size_t)(2 * j + 1) * per_poly4 + e];
+            a0 = make_uint4(kip_term(a0.x, d.x, k0.x, c), kip_term(a0.y, d.y, k0.y, c), kip_term(a0.z, d.z, k0.z, c),
+                            kip_term(a0.w, d.w, k0.w, c));
+            a1 = make_uint4(kip_term(a1.x, d.x, k1.x, c), kip_term(a1.y, d.y, k1.y, c), kip_term(a1.z, d.z, k1.z, c),
+                            kip_term(a1.w, d.w, k1.w, c));
+        }
+        out[(2 * b) * per_poly4 + e] = make_uint4(kip_final(a0.x, c), kip_final(a0.y, c), kip_final(a0.z, c),
+                                                  kip_final(a0.w, c));
+        out[(2 * b + 1) * per_poly4 + e] = make_uint4(kip_final(a1.x, c), kip_final(a1.y, c), kip_final(a1.z, c),
+                                                      kip_final(a1.w, c));
+    }
+}
+
+// Rescale by the parameter set's last prime: out[b][i] = (x[b][i] - [x[b][L-1]]_{q_i}) * q_{L-1}^-1
+// mod q_i for i < L - 1 (coefficient form).  x_{L-1} < q_{L-1} < 2^30 is brought into [0, q_i)
+// by a Shoup product with 1 and one subtraction.
+__global__ void __launch_bounds__(256) rescale_kernel(const LimbConst* __restrict__ lc, uint32_t L, uint32_t n,
+                                                      size_t batch, const uint4* x, uint4* out) {
+    const size_t row4 = n / 4;
+    const size_t per_out4 = (size_t)(L - 1) * row4;
+    const size_t total4 = batch * per_out4;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total4; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t b = i / per_out4, e = i % per_out4;
+        const size_t limb = e / row4, col = e % row4;
+        const LimbConst c = lc[limb];
+        const uint4 v = x[(b * L + limb) * row4 + col], t = x[(b * L + L - 1) * row4 + col];
+        auto one = [&](uint32_t xv, uint32_t tv) {
+            const uint32_t last = csub(mul_shoup_lazy(tv, 1u, c.one_sh, c.q), c.q);
+            return csub(mul_shoup_lazy(xv + c.q - last, c.rs_inv, c.rs_inv_sh, c.q), c.q);
+        };
+        out[i] = make_uint4(one(v.x, t.x), one(v.y, t.y), one(v.z, t.z), one(v.w, t.w));
+    }
+}
+
 unsigned grid_for(size_t total4) {
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
@@ -72,6 +136,31 @@ cudaError_t launch_tensor_product(const hefx_params* p, const uint32_t* a0, cons
     tensor_product_kernel<<<grid_for(total4), 256, 0, s>>>(p->d_lc, p->nlimbs, p->n, total4, (const uint4*)a0,
                                                            (const uint4*)a1, (const uint4*)b0, (const uint4*)b1,
                                                            (uint4*)d0, (uint4*)d1, (uint4*)d2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vec_mod_add(const hefx_params* p, const uint32_t* x, const uint32_t* y, uint32_t* z, size_t rows,
+                               cudaStream_t s) {
+    const size_t total4 = rows * p->n / 4;
+    if (!total4) return cudaSuccess;
+    vec_mod_add_kernel<<<grid_for(total4), 256, 0, s>>>(p->d_lc, p->nlimbs, p->n, total4, (const uint4*)x,
+                                                        (const uint4*)y, (uint4*)z);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_key_inner_product(const hefx_params* p, const uint32_t* dig, const uint32_t* evk, uint32_t* out,
+                                     uint32_t dnum, size_t batch, cudaStream_t s) {
+    const size_t total4 = batch * p->nlimbs * p->n / 4;
+    if (!total4) return cudaSuccess;
+    key_inner_product_kernel<<<grid_for(total4), 256, 0, s>>>(p->d_lc, p->nlimbs, p->n, dnum, batch,
+                                                              (const uint4*)dig, (const uint4*)evk, (uint4*)out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rescale(const hefx_params* p, const uint32_t* x, uint32_t* out, size_t batch, cudaStream_t s) {
+    const size_t total4 = batch * (p->nlimbs - 1) * p->n / 4;
+    if (!total4) return cudaSuccess;
+    rescale_kernel<<<grid_for(total4), 256, 0, s>>>(p->d_lc, p->nlimbs, p->n, batch, (const uint4*)x, (uint4*)out);
     return cudaGetLastError();
 }
 

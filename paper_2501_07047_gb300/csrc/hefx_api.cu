@@ -184,6 +184,11 @@ hefx_status hefx_params_create(hefx_ctx* ctx, uint32_t log2n, const uint32_t* pr
         c.ninvRw_sh = shoup(vals[3], q);
         c.r2 = (uint32_t)mul_mod(r32, r32, q);
         c.one_sh = shoup(1, q);
+        if (l + 1 < nlimbs) {
+            const uint64_t ri = inv_mod(primes[nlimbs - 1] % q, q);
+            c.rs_inv = (uint32_t)ri;
+            c.rs_inv_sh = shoup(ri, q);
+        }
     }
     cudaError_t e = cudaMalloc(&p->d_lc, sizeof(LimbConst) * nlimbs);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_tw_fwd, sizeof(uint2) * twf.size());
@@ -356,6 +361,76 @@ hefx_status hefx_vec_mod_mul(hefx_ctx* ctx, const hefx_params* p, const uint32_t
     if ((st = use_device(ctx)) != HEFX_OK) return st;
     cudaError_t e = launch_vec_mod_mul(p, x, y, z, batch * p->nlimbs, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "hefx_vec_mod_mul launch");
+    return HEFX_OK;
+}
+
+// True when [a, a + an) and [b, b + bn) (bytes) overlap.
+bool overlaps(const void* a, size_t an, const void* b, size_t bn) {
+    const char *x = (const char*)a, *y = (const char*)b;
+    return an && bn && x < y + bn && y < x + an;
+}
+
+hefx_status hefx_vec_mod_add(hefx_ctx* ctx, const hefx_params* p, const uint32_t* x, const uint32_t* y, uint32_t* z,
+                             size_t batch, void* stream) {
+    hefx_status st;
+    if ((st = check_ntt_args(ctx, p, x, "d_x")) != HEFX_OK) return st;
+    if ((st = check_ntt_args(ctx, p, y, "d_y")) != HEFX_OK) return st;
+    if ((st = check_ntt_args(ctx, p, z, "d_z")) != HEFX_OK) return st;
+    if (batch == 0) return HEFX_OK;
+    if ((st = use_device(ctx)) != HEFX_OK) return st;
+    cudaError_t e = launch_vec_mod_add(p, x, y, z, batch * p->nlimbs, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "hefx_vec_mod_add launch");
+    return HEFX_OK;
+}
+
+hefx_status hefx_key_inner_product(hefx_ctx* ctx, const hefx_params* p, const uint32_t* digits, const uint32_t* evk,
+                                   uint32_t* out, uint32_t dnum, size_t batch, void* stream) {
+    hefx_status st;
+    if ((st = check_ntt_args(ctx, p, digits, "d_digits")) != HEFX_OK) return st;
+    if ((st = check_ntt_args(ctx, p, evk, "d_evk")) != HEFX_OK) return st;
+    if ((st = check_ntt_args(ctx, p, out, "d_out")) != HEFX_OK) return st;
+    if (dnum == 0 || dnum > 64) return fail(ctx, HEFX_EINVAL, "dnum = %u outside [1, 64]", dnum);
+    const size_t poly = (size_t)p->nlimbs * p->n * 4;
+    if (overlaps(out, batch * 2 * poly, digits, batch * dnum * poly) || overlaps(out, batch * 2 * poly, evk, dnum * 2 * poly))
+        return fail(ctx, HEFX_EINVAL, "d_out overlaps an input");
+    if (batch == 0) return HEFX_OK;
+    if ((st = use_device(ctx)) != HEFX_OK) return st;
+    cudaError_t e = launch_key_inner_product(p, digits, evk, out, dnum, batch, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "hefx_key_inner_product launch");
+    return HEFX_OK;
+}
+
+hefx_status hefx_rescale(hefx_ctx* ctx, const hefx_params* p, const uint32_t* x, uint32_t* out, size_t batch,
+                         void* stream) {
+    hefx_status st;
+    if ((st = check_ntt_args(ctx, p, x, "d_x")) != HEFX_OK) return st;
+    if ((st = check_ntt_args(ctx, p, out, "d_out")) != HEFX_OK) return st;
+    if (p->nlimbs < 2) return fail(ctx, HEFX_EINVAL, "rescale needs at least 2 limbs");
+    const size_t row = (size_t)p->n * 4;
+    if (!(batch == 1 && (const void*)out == (const void*)x) &&
+        overlaps(out, batch * (p->nlimbs - 1) * row, x, batch * p->nlimbs * row))
+        return fail(ctx, HEFX_EINVAL, "d_out overlaps d_x (in place only with batch == 1)");
+    if (batch == 0) return HEFX_OK;
+    if ((st = use_device(ctx)) != HEFX_OK) return st;
+    cudaError_t e = launch_rescale(p, x, out, batch, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "hefx_rescale launch");
+    return HEFX_OK;
+}
+
+hefx_status hefx_mod_down(hefx_ctx* ctx, const hefx_bconv_plan* plan, const uint32_t* x, uint32_t* out, size_t batch,
+                          void* stream) {
+    if (!ctx) return HEFX_EINVAL;
+    if (!plan || plan->ctx != ctx) return fail(ctx, HEFX_EINVAL, "plan is null or belongs to another context");
+    if (!x || !out) return fail(ctx, HEFX_EINVAL, "null buffer");
+    if (!aligned16(x) || !aligned16(out)) return fail(ctx, HEFX_EINVAL, "buffers must be 16-byte aligned");
+    const size_t row = ((size_t)1 << plan->log2n) * 4;
+    if (overlaps(out, batch * plan->Lp * row, x, batch * (plan->L + plan->Lp) * row))
+        return fail(ctx, HEFX_EINVAL, "d_out overlaps d_x");
+    hefx_status st = use_device(ctx);
+    if (st != HEFX_OK) return st;
+    if (batch == 0) return HEFX_OK;
+    cudaError_t e = launch_mod_down(plan, x, out, batch, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "hefx_mod_down launch");
     return HEFX_OK;
 }
 

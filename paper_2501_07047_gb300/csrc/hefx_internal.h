@@ -24,7 +24,8 @@ struct LimbConst {
     uint32_t ninvRw, ninvRw_sh;   // N^-1 * 2^32 * psi^-brv_N(1)
     uint32_t r2;                  // 2^64 mod q: two Montgomery products give a plain one
     uint32_t one_sh;              // floor(2^32 / q), Shoup companion of 1: any x < 2^32 -> [0, 2q)
-    uint32_t pad[4];
+    uint32_t rs_inv, rs_inv_sh;   // q_{L-1}^-1 mod q (Rescale by the set's last prime) and companion
+    uint32_t pad[2];
 };
 static_assert(sizeof(LimbConst) == 64, "LimbConst is one 64-byte line");
 
@@ -121,6 +122,13 @@ cudaError_t prepare_ntt_cc(const hefx_params* p, NttMode mode);
 cudaError_t launch_ntt_cc_rows(const hefx_params* p, NttMode mode, const RowDesc* d_rows, size_t nrows,
                                cudaStream_t stream);
 
+cudaError_t launch_vec_mod_add(const hefx_params* p, const uint32_t* x, const uint32_t* y, uint32_t* z, size_t rows,
+                               cudaStream_t s);
+cudaError_t launch_key_inner_product(const hefx_params* p, const uint32_t* dig, const uint32_t* evk, uint32_t* out,
+                                     uint32_t dnum, size_t batch, cudaStream_t s);
+cudaError_t launch_rescale(const hefx_params* p, const uint32_t* x, uint32_t* out, size_t batch, cudaStream_t s);
+cudaError_t launch_mod_down(const hefx_bconv_plan* plan, const uint32_t* x, uint32_t* out, size_t batch,
+                            cudaStream_t stream);
 cudaError_t launch_bconv_cc(const hefx_bconv_plan* plan, const uint32_t* in, uint32_t* out, size_t batch,
                             cudaStream_t stream);
 cudaError_t bconv_plan_upload(hefx_bconv_plan* plan);

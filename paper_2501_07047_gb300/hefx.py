@@ -40,6 +40,10 @@ SIGNATURES = {
     "hefx_stream_check": (_i32, [_vp, _vp, _vp]),
     "hefx_vec_mod_mul": (_i32, [_vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "hefx_tensor_product": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "hefx_vec_mod_add": (_i32, [_vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "hefx_key_inner_product": (_i32, [_vp, _vp, _vp, _vp, _vp, _u32, _sz, _vp]),
+    "hefx_mod_down": (_i32, [_vp, _vp, _vp, _vp, _sz, _vp]),
+    "hefx_rescale": (_i32, [_vp, _vp, _vp, _vp, _sz, _vp]),
     "hefx_batch_plan_create": (_i32, [_vp, _vp, _sz, _i32, ctypes.POINTER(_vp)]),
     "hefx_batch_plan_destroy": (None, [_vp]),
     "hefx_batch_polymul": (_i32, [_vp, _vp, _vp]),
@@ -186,6 +190,23 @@ def hefx_vec_mod_mul(ctx, params, x, y, z, batch, stream=None) -> None:
 def hefx_tensor_product(ctx, params, a0, a1, b0, b1, d0, d1, d2, batch, stream=None) -> None:
     _check(ctx, load().hefx_tensor_product(ctx, params, _ptr(a0), _ptr(a1), _ptr(b0), _ptr(b1), _ptr(d0), _ptr(d1),
                                            _ptr(d2), batch, _stream(stream)))
+
+
+def hefx_vec_mod_add(ctx, params, x, y, z, batch, stream=None) -> None:
+    _check(ctx, load().hefx_vec_mod_add(ctx, params, _ptr(x), _ptr(y), _ptr(z), batch, _stream(stream)))
+
+
+def hefx_key_inner_product(ctx, params, digits, evk, out, dnum, batch, stream=None) -> None:
+    _check(ctx, load().hefx_key_inner_product(ctx, params, _ptr(digits), _ptr(evk), _ptr(out), dnum, batch,
+                                              _stream(stream)))
+
+
+def hefx_mod_down(ctx, plan, x, out, batch, stream=None) -> None:
+    _check(ctx, load().hefx_mod_down(ctx, plan, _ptr(x), _ptr(out), batch, _stream(stream)))
+
+
+def hefx_rescale(ctx, params, x, out, batch, stream=None) -> None:
+    _check(ctx, load().hefx_rescale(ctx, params, _ptr(x), _ptr(out), batch, _stream(stream)))
 
 
 def hefx_batch_plan_create(ctx, jobs, path="auto") -> int:

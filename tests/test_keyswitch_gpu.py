@@ -1,0 +1,142 @@
+"""GPU parity of the key-switching pieces (VecModAdd, key inner product, ModDown, Rescale) and
+of the composed HE-Mult against the oracle, bit for bit, plus the decryption relation of a
+genuine switching key on the GPU's result."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import keyswitch as oks
+from paper_2501_07047_gb300 import hefx, inputs
+
+from hefx_testutil import to_dev as dev, to_host as host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hx():
+    ctx = hefx.hefx_create(0)
+    yield hefx, ctx
+    hefx.hefx_destroy(ctx)
+
+
+def _res(seed, rows, primes, n):
+    return inputs.residue_tensor(inputs.derive_seed(*seed), rows, primes, n)
+
+
+@pytest.mark.parametrize("logn,L,K", [(8, 3, 2), (12, 6, 4), (16, 24, 8)])
+def test_mod_down(hx, logn, L, K):
+    hefx, ctx = hx
+    n, batch = 1 << logn, 2
+    qs, ps = inputs.source_primes(L), inputs.special_primes(K)
+    x = np.stack([_res((60, logn, b), 1, list(qs) + list(ps), n)[0] for b in range(batch)])
+    plan = hefx.hefx_bconv_plan_create(ctx, logn, ps, qs)
+    dx, dout = dev(x), dev(np.zeros((batch, L, n), dtype=np.uint32))
+    hefx.hefx_mod_down(ctx, plan, dx, dout, batch)
+    got = host(dout)
+    if logn <= 12:
+        assert np.array_equal(got, oracle.moddown(x, qs, ps))
+    else:  # full size: every limb of sampled coefficients
+        cols = np.random.default_rng(1).choice(n, 256, replace=False)
+        want = oracle.moddown(x[:, :, cols], qs, ps)
+        assert np.array_equal(got[:, :, cols], want)
+    hefx.hefx_bconv_plan_destroy(plan)
+
+
+@pytest.mark.parametrize("logn,L", [(6, 2), (10, 5), (16, 24)])
+def test_rescale(hx, logn, L):
+    hefx, ctx = hx
+    n = 1 << logn
+    qs = inputs.source_primes(L)
+    p = hefx.hefx_params_create(ctx, logn, qs)
+    x = np.stack([_res((61, logn, b), 1, qs, n)[0] for b in range(2)])
+    dx, dout = dev(x), dev(np.zeros((2, L - 1, n), dtype=np.uint32))
+    hefx.hefx_rescale(ctx, p, dx, dout, 2)
+    assert np.array_equal(host(dout), oracle.rescale(x, qs))
+    # in place with batch 1: the result occupies the first L - 1 rows
+    d1 = dev(x[0])
+    hefx.hefx_rescale(ctx, p, d1, d1, 1)
+    assert np.array_equal(host(d1)[:L - 1], oracle.rescale(x[0], qs))
+    hefx.hefx_params_destroy(p)
+
+
+@pytest.mark.parametrize("logn,nl,dnum,batch", [(8, 5, 3, 1), (12, 10, 1, 2), (16, 32, 3, 1)])
+def test_key_inner_product_and_add(hx, logn, nl, dnum, batch):
+    hefx, ctx = hx
+    n = 1 << logn
+    qs = list(inputs.source_primes(nl - nl // 3)) + list(inputs.special_primes(nl // 3))
+    p = hefx.hefx_params_create(ctx, logn, qs)
+    dig = np.stack([np.stack([_res((62, logn, b, j), 1, qs, n)[0] for j in range(dnum)]) for b in range(batch)])
+    evk = np.stack([np.stack([_res((63, logn, j, k), 1, qs, n)[0] for k in range(2)]) for j in range(dnum)])
+    dd, de, do = dev(dig), dev(evk), dev(np.zeros((batch, 2, nl, n), dtype=np.uint32))
+    hefx.hefx_key_inner_product(ctx, p, dd, de, do, dnum, batch)
+    got = host(do)
+    for b in range(batch):
+        assert np.array_equal(got[b], oracle.key_inner_product(dig[b], evk, qs))
+    # VecModAdd on the two halves, in place into the first
+    hefx.hefx_vec_mod_add(ctx, p, do[0, 0], do[0, 1], do[0, 0], 1)
+    q = np.asarray(qs, dtype=np.uint64)[:, None]
+    want = ((got[0, 0].astype(np.uint64) + got[0, 1]) % q).astype(np.uint32)
+    assert np.array_equal(host(do)[0, 0], want)
+    hefx.hefx_params_destroy(p)
+
+
+def test_keyswitch_errors(hx):
+    hefx, ctx = hx
+    q1 = inputs.source_primes(1)
+    p1 = hefx.hefx_params_create(ctx, 8, q1)
+    buf = dev(np.zeros((4, 256), dtype=np.uint32))
+    assert hefx.raw_status("hefx_rescale", ctx, p1, buf.data_ptr(), buf.data_ptr(), 1, 0) == hefx.HEFX_EINVAL
+    p3 = hefx.hefx_params_create(ctx, 8, inputs.source_primes(3))
+    assert hefx.raw_status("hefx_key_inner_product", ctx, p3, buf.data_ptr(), buf.data_ptr(), buf.data_ptr(), 0, 1,
+                           0) == hefx.HEFX_EINVAL
+    plan = hefx.hefx_bconv_plan_create(ctx, 8, inputs.special_primes(1), inputs.source_primes(2))
+    # ModDown output overlapping its input
+    assert hefx.raw_status("hefx_mod_down", ctx, plan, buf.data_ptr(), buf.data_ptr() + 1024, 1, 0) \
+        == hefx.HEFX_EINVAL
+    hefx.hefx_bconv_plan_destroy(plan)
+    hefx.hefx_params_destroy(p1)
+    hefx.hefx_params_destroy(p3)
+
+
+def _he_mult_case(logn, L, K, alpha, seed, genuine_key):
+    n = 1 << logn
+    qs, ps = inputs.source_primes(L), inputs.special_primes(K)
+    qp = list(qs) + list(ps)
+    dn = len(oks.digit_ranges(L, alpha))
+    s = None
+    if genuine_key:
+        s = np.random.default_rng(seed).integers(-1, 2, n)
+        a_r = np.stack([_res((seed, 1, j), 1, qp, n)[0] for j in range(dn)])
+        evk = oks.keygen(s, qs, ps, alpha, a_r)
+    else:
+        evk = np.stack([np.stack([_res((seed, 3, j, k), 1, qp, n)[0] for k in range(2)]) for j in range(dn)])
+    ins = [_res((seed, 2, c), 1, qs, n)[0] for c in range(4)]
+    return qs, ps, s, evk, ins
+
+
+@pytest.mark.parametrize("logn,L,K,alpha,genuine", [(6, 5, 2, 2, True), (10, 6, 3, 3, True), (8, 4, 4, 4, True),
+                                                    (16, 24, 8, 8, False)])
+def test_he_mult_matches_oracle(hx, logn, L, K, alpha, genuine):
+    hefx, ctx = hx
+    from paper_2501_07047_gb300.hemult import HeMult
+    qs, ps, s, evk, ins = _he_mult_case(logn, L, K, alpha, 64 + logn, genuine)
+    hm = HeMult(ctx, logn, qs, ps, alpha)
+    n = 1 << logn
+    out = dev(np.zeros((2, L - 1, n), dtype=np.uint32))
+    dins = [dev(a) for a in ins]
+    devk = dev(evk)
+    hm.run(*dins, devk, out)
+    want = oks.he_mult(*ins, evk, qs, ps, alpha)
+    got = host(out)
+    assert np.array_equal(got[0], want["c0r"]) and np.array_equal(got[1], want["c1r"])
+    st = {k: host(v) for k, v in hm.stages().items()}
+    qp = list(qs) + list(ps)
+    assert np.array_equal(st["d2"], want["d2"])
+    assert np.array_equal(st["modup_eval"], oracle.ntt_batch(want["modup"], qp))
+    assert np.array_equal(st["acc_coeff"], oracle.ntt_batch(want["acc"], qp, inverse=True))
+    assert np.array_equal(st["ks_eval"], oracle.ntt_batch(want["ks"], qs))
+    if genuine:
+        res = dict(want, c0r=got[0], c1r=got[1])
+        assert oks.phase_error(res, s, qs) <= 2 * n + 2 * K + 8
+    hm.close()
