@@ -309,3 +309,33 @@ def test_iterative_bat_congruent(seed):
         assert all(0 <= M[i][j] < 256 for i in range(4))
         col = sum(M[i][j] << (8 * i) for i in range(4))
         assert col % q == (a << (8 * j)) % q == bat.chunk_merge([D[i][j] for i in range(4)], 8)
+
+
+# ------------------------------------------------------------------ exact (u-corrected) BConv
+def test_bconv_exact_small_signed_values():
+    from math import prod
+    qs, ps = inputs.source_primes(4), inputs.special_primes(3)
+    Q = prod(qs)
+    zs = [0, 1, -1, 2, -2, 12345, -98765, 2 ** 40 + 3, -(2 ** 50), (Q - 1) // 2, -(Q - 1) // 2]
+    a = [[z % q for z in zs] for q in qs]
+    out = crt.bconv_exact(a, qs, ps)
+    for j, p in enumerate(ps):
+        assert out[j] == [z % p for z in zs]
+
+
+@pytest.mark.parametrize("L,Lp", [(1, 2), (3, 4), (24, 8)])
+def test_bconv_exact_vs_fast_conversion(L, Lp):
+    from math import prod
+    qs, ps = inputs.source_primes(L), inputs.special_primes(Lp)
+    Q = prod(qs)
+    a = inputs.residue_tensor(inputs.derive_seed(47, L, Lp), 1, qs, 32)[0]
+    exact = crt.bconv_exact(a, qs, ps)
+    fast = oracle.bconv(a, qs, ps)
+    for c in range(32):
+        col = [int(a[i, c]) for i in range(L)]
+        y = crt.fast_conversion_integer(col, qs)
+        xb = crt.centered(crt.crt(col, qs), Q)
+        k = (y - xb) // Q
+        assert (y - xb) % Q == 0 and 0 <= k <= L
+        for j, p in enumerate(ps):
+            assert (int(fast[j, c]) - exact[j][c] - k * Q) % p == 0
