@@ -143,7 +143,8 @@ hefx_status hefx_poly_mul_noalloc(hefx_ctx* ctx, const hefx_params* params, cons
  * by u*Q with 0 <= u < L; no correction is applied.  The plan holds the step-1 constants
  * qhat_i^-1 mod q_i and the BAT-compiled digit matrix of step 2 (Sec. IV-A3).
  * Errors: EINVAL for non-prime, repeated (within or across bases) or >= 2^30 moduli,
- * L or Lp outside [1, 64]; EUNSUPPORTED for log2n outside [0, 24].
+ * L or Lp outside [1, 64]; EUNSUPPORTED for log2n outside [0, 24] or when
+ * L * max(q) * max(p) >= 2^64 (the CUDA-core kernel sums L products in 64 bits).
  */
 hefx_status hefx_bconv_plan_create(hefx_ctx* ctx, uint32_t log2n, const uint32_t* src, uint32_t L,
                                    const uint32_t* dst, uint32_t Lp, hefx_bconv_plan** out);
@@ -157,6 +158,19 @@ void hefx_bconv_plan_destroy(hefx_bconv_plan* plan);
  */
 hefx_status hefx_basis_convert(hefx_ctx* ctx, const hefx_bconv_plan* plan, const uint32_t* d_in, uint32_t* d_out,
                                size_t batch, hefx_path path, void* stream);
+
+/*
+ * Exact basis conversion (the u-corrected variant of App. B's fast conversion; the paper
+ * prints only the fast one): d_out[b][j] = xbar mod p_j, where xbar is the centered CRT value
+ * of d_in[b][.][c] in (-Q/2, Q/2), Q = prod q_i.  The multiple of Q that the fast conversion
+ * adds is removed with v = round(sum_i [a_i qhat_i^-1]_{q_i} / q_i), estimated as a 128-bit
+ * fixed-point sum with weights round(2^k / q_i), k = 63 + floor(log2 min q_i), so its error
+ * is below eps = L max(q_i) 2^-(k+1) of Q (2^-57 for up to 64 sources of 28 bits): the result
+ * is exact unless |xbar| lies within eps Q of Q/2 (then it may be the other representative's
+ * residue).  Same layouts, plan and overlap rule as hefx_basis_convert; CUDA cores.
+ */
+hefx_status hefx_basis_convert_exact(hefx_ctx* ctx, const hefx_bconv_plan* plan, const uint32_t* d_in,
+                                     uint32_t* d_out, size_t batch, void* stream);
 
 /*
  * z = x o y mod q per limb (VecModMul of Table "HE operator -> AI operator"), elementwise over

@@ -18,6 +18,10 @@ struct BConvConst {
     uint64_t p_mu[kBConvMaxLimbs];         // floor(2^64 / p_j) (Barrett)
     uint32_t pinv[kBConvMaxLimbs];         // (prod_i q_i)^-1 mod p_j (ModDown scale)
     uint32_t pinv_sh[kBConvMaxLimbs];      // its Shoup companion
+    uint32_t qmod_p[kBConvMaxLimbs];       // Q mod p_j (exact conversion's correction)
+    uint64_t w[kBConvMaxLimbs];            // round(2^k / q_i) (exact conversion's estimate of u)
+    uint64_t half_lo, half_hi;             // 2^(k-1) as a 128-bit value
+    uint32_t kshift, pad2;                 // k - 64
     uint32_t qhat_p[kBConvMaxLimbs * kBConvMaxLimbs];  // [i][j] = qhat_i mod p_j (step 2 matrix)
 };
 

@@ -35,6 +35,12 @@ hefx_status cuda_fail(hefx_ctx* ctx, cudaError_t e, const char* what) {
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+// True when [a, a + an) and [b, b + bn) (bytes) overlap.
+bool overlaps(const void* a, size_t an, const void* b, size_t bn) {
+    const char *x = (const char*)a, *y = (const char*)b;
+    return an && bn && x < y + bn && y < x + an;
+}
+
 hefx_status use_device(hefx_ctx* ctx) {
     int cur = -1;
     cudaError_t e = cudaGetDevice(&cur);
@@ -298,6 +304,13 @@ hefx_status hefx_bconv_plan_create(hefx_ctx* ctx, uint32_t log2n, const uint32_t
             return fail(ctx, HEFX_EINVAL, "modulus %u is not a prime in [3, 2^30)", q);
         if (!seen.insert(q).second) return fail(ctx, HEFX_EINVAL, "modulus %u repeats", q);
     }
+    {  // the CUDA-core kernel accumulates L products b_i [qhat_i]_{p_j} < q_i p_j in 64 bits
+        uint64_t mq = 0, mp = 0;
+        for (uint32_t i = 0; i < L; ++i) mq = std::max<uint64_t>(mq, src[i]);
+        for (uint32_t j = 0; j < Lp; ++j) mp = std::max<uint64_t>(mp, dst[j]);
+        if ((unsigned __int128)L * (mq - 1) * (mp - 1) >= ((unsigned __int128)1 << 64))
+            return fail(ctx, HEFX_EUNSUPPORTED, "L * max(q) * max(p) reaches 2^64 (64-bit accumulation)");
+    }
     hefx_status st = use_device(ctx);
     if (st != HEFX_OK) return st;
     hefx_bconv_plan* p = new hefx_bconv_plan();
@@ -351,6 +364,23 @@ hefx_status hefx_basis_convert(hefx_ctx* ctx, const hefx_bconv_plan* plan, const
     return HEFX_OK;
 }
 
+hefx_status hefx_basis_convert_exact(hefx_ctx* ctx, const hefx_bconv_plan* plan, const uint32_t* in, uint32_t* out,
+                                     size_t batch, void* stream) {
+    if (!ctx) return HEFX_EINVAL;
+    if (!plan || plan->ctx != ctx) return fail(ctx, HEFX_EINVAL, "plan is null or belongs to another context");
+    if (!in || !out) return fail(ctx, HEFX_EINVAL, "null buffer");
+    if (!aligned16(in) || !aligned16(out)) return fail(ctx, HEFX_EINVAL, "buffers must be 16-byte aligned");
+    const size_t row = ((size_t)1 << plan->log2n) * 4;
+    if (overlaps(out, batch * plan->Lp * row, in, batch * plan->L * row))
+        return fail(ctx, HEFX_EINVAL, "d_out overlaps d_in");
+    hefx_status st = use_device(ctx);
+    if (st != HEFX_OK) return st;
+    if (batch == 0) return HEFX_OK;
+    cudaError_t e = launch_bconv_exact(plan, in, out, batch, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "hefx_basis_convert_exact launch");
+    return HEFX_OK;
+}
+
 hefx_status hefx_vec_mod_mul(hefx_ctx* ctx, const hefx_params* p, const uint32_t* x, const uint32_t* y, uint32_t* z,
                              size_t batch, void* stream) {
     hefx_status st;
@@ -362,12 +392,6 @@ hefx_status hefx_vec_mod_mul(hefx_ctx* ctx, const hefx_params* p, const uint32_t
     cudaError_t e = launch_vec_mod_mul(p, x, y, z, batch * p->nlimbs, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "hefx_vec_mod_mul launch");
     return HEFX_OK;
-}
-
-// True when [a, a + an) and [b, b + bn) (bytes) overlap.
-bool overlaps(const void* a, size_t an, const void* b, size_t bn) {
-    const char *x = (const char*)a, *y = (const char*)b;
-    return an && bn && x < y + bn && y < x + an;
 }
 
 hefx_status hefx_vec_mod_add(hefx_ctx* ctx, const hefx_params* p, const uint32_t* x, const uint32_t* y, uint32_t* z,

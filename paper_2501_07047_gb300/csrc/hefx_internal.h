@@ -127,6 +127,8 @@ cudaError_t launch_vec_mod_add(const hefx_params* p, const uint32_t* x, const ui
 cudaError_t launch_key_inner_product(const hefx_params* p, const uint32_t* dig, const uint32_t* evk, uint32_t* out,
                                      uint32_t dnum, size_t batch, cudaStream_t s);
 cudaError_t launch_rescale(const hefx_params* p, const uint32_t* x, uint32_t* out, size_t batch, cudaStream_t s);
+cudaError_t launch_bconv_exact(const hefx_bconv_plan* plan, const uint32_t* in, uint32_t* out, size_t batch,
+                               cudaStream_t stream);
 cudaError_t launch_mod_down(const hefx_bconv_plan* plan, const uint32_t* x, uint32_t* out, size_t batch,
                             cudaStream_t stream);
 cudaError_t launch_bconv_cc(const hefx_bconv_plan* plan, const uint32_t* in, uint32_t* out, size_t batch,

@@ -41,6 +41,7 @@ SIGNATURES = {
     "hefx_vec_mod_mul": (_i32, [_vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "hefx_tensor_product": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "hefx_vec_mod_add": (_i32, [_vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "hefx_basis_convert_exact": (_i32, [_vp, _vp, _vp, _vp, _sz, _vp]),
     "hefx_key_inner_product": (_i32, [_vp, _vp, _vp, _vp, _vp, _u32, _sz, _vp]),
     "hefx_mod_down": (_i32, [_vp, _vp, _vp, _vp, _sz, _vp]),
     "hefx_rescale": (_i32, [_vp, _vp, _vp, _vp, _sz, _vp]),
@@ -199,6 +200,10 @@ def hefx_vec_mod_add(ctx, params, x, y, z, batch, stream=None) -> None:
 def hefx_key_inner_product(ctx, params, digits, evk, out, dnum, batch, stream=None) -> None:
     _check(ctx, load().hefx_key_inner_product(ctx, params, _ptr(digits), _ptr(evk), _ptr(out), dnum, batch,
                                               _stream(stream)))
+
+
+def hefx_basis_convert_exact(ctx, plan, x, out, batch, stream=None) -> None:
+    _check(ctx, load().hefx_basis_convert_exact(ctx, plan, _ptr(x), _ptr(out), batch, _stream(stream)))
 
 
 def hefx_mod_down(ctx, plan, x, out, batch, stream=None) -> None:

@@ -108,3 +108,39 @@ def test_bconv_validation(ctx):
         assert e.value.status == hefx.HEFX_EINVAL
     finally:
         hefx.hefx_bconv_plan_destroy(plan)
+
+
+@pytest.mark.parametrize("logn,L,Lp,batch", [(4, 1, 2, 2), (8, 3, 4, 2), (10, 24, 8, 1), (16, 24, 8, 2)])
+def test_bconv_exact_matches_oracle(ctx, logn, L, Lp, batch):
+    qs, ps = inputs.source_primes(L), inputs.special_primes(Lp)
+    plan = hefx.hefx_bconv_plan_create(ctx, logn, qs, ps)
+    try:
+        n = 1 << logn
+        a = inputs.residue_tensor(inputs.derive_seed(48, logn, L, Lp), batch, qs, n)
+        # the first coefficients hold small signed values, zero, +-Q/4 and values 2^-40 Q away
+        # from +-Q/2 (outside the documented misrounding band of 2^-57 Q around Q/2)
+        from math import prod
+        Q = prod(qs)
+        near = Q // 2 - (Q >> 40) if L > 1 else (Q - 1) // 2
+        special = [0, 1, -1, 7, -7, 2 ** 45, -(2 ** 45), Q // 4, -(Q // 4), near, -near]
+        for c, z in enumerate(special[:n]):
+            for i, q in enumerate(qs):
+                a[0, i, c] = z % q
+        din, dout = to_dev(a), empty_dev((batch, Lp, n))
+        hefx.hefx_basis_convert_exact(ctx, plan, din, dout, batch)
+        got = to_host(dout).reshape(batch, Lp, n)
+        cols = np.arange(n) if n <= 1024 else np.concatenate(
+            [np.arange(len(special)), np.random.default_rng(2).choice(n, 200, replace=False)])
+        for b in range(batch):
+            want = np.array(crt.bconv_exact(a[b][:, cols].tolist(), qs, ps), dtype=np.uint32)
+            bad = np.nonzero((got[b][:, cols] != want).any(axis=0))[0]
+            assert bad.size == 0, f"batch {b}: columns {cols[bad][:8].tolist()} differ"
+    finally:
+        hefx.hefx_bconv_plan_destroy(plan)
+
+
+def test_bconv_plan_rejects_accumulator_overflow(ctx):
+    big = inputs.special_primes(40)
+    st = hefx.raw_status("hefx_bconv_plan_create", ctx, 10, hefx._u32_array(big[:20]), 20,
+                         hefx._u32_array(big[20:]), 20, hefx.ctypes.byref(hefx._vp()))
+    assert st == hefx.HEFX_EUNSUPPORTED
