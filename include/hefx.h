@@ -21,7 +21,8 @@
  *    the context, parameter sets and plans it creates (and the device tables inside them),
  *    and releases them in the matching *_destroy call.
  *  - Moduli: primes q with q = 1 (mod 2N) and 2^3 < q < 2^30 (the lazy butterflies keep
- *    values below 4q < 2^32).  N = 2^log2n with 3 <= log2n <= 16.
+ *    values below 4q < 2^32).  N = 2^log2n with 3 <= log2n <= 17 (the tensor path covers
+ *    14 <= log2n <= 16; N = 2^17 needs q = 1 mod 2^18 and runs on the CUDA cores).
  *  - Paths: HEFX_PATH_CUDACORE is the radix-2 Cooley-Tukey / Gentleman-Sande transform on
  *    the CUDA cores (App. A, "Radix-2 Cooley-Tukey NTT").  HEFX_PATH_TENSOR is the
  *    layout-invariant matrix NTT of Sec. IV-B with its modular matrix products split into
@@ -72,7 +73,7 @@ const char* hefx_version(void);
  * "Notations": q_i coprime, L limbs).  Precomputes on the host and uploads the twiddle
  * tables of both paths (the offline "compile time" step of Sec. IV-A/IV-B).
  * Errors: EINVAL for a non-prime, repeated prime, q != 1 mod 2N or q >= 2^30;
- * EUNSUPPORTED for log2n outside [3, 16]; ENOMEM when the tables do not fit.
+ * EUNSUPPORTED for log2n outside [3, 17]; ENOMEM when the tables do not fit.
  */
 hefx_status hefx_params_create(hefx_ctx* ctx, uint32_t log2n, const uint32_t* primes, uint32_t nlimbs,
                                hefx_params** out);

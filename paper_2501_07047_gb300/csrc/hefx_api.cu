@@ -109,7 +109,7 @@ hefx_status hefx_params_create(hefx_ctx* ctx, uint32_t log2n, const uint32_t* pr
                                hefx_params** out) {
     if (!ctx || !out) return HEFX_EINVAL;
     *out = nullptr;
-    if (log2n < 3 || log2n > 16) return fail(ctx, HEFX_EUNSUPPORTED, "log2n = %u outside [3, 16]", log2n);
+    if (log2n < 3 || log2n > 17) return fail(ctx, HEFX_EUNSUPPORTED, "log2n = %u outside [3, 17]", log2n);
     if (!primes || nlimbs == 0 || nlimbs > 4096) return fail(ctx, HEFX_EINVAL, "need 1..4096 primes");
     const uint64_t n = 1ull << log2n;
     std::set<uint32_t> seen;

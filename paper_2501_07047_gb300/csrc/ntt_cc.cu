@@ -52,6 +52,7 @@ cudaError_t launch_dispatch(const hefx_params* p, NttMode mode, const cc::KArgs&
     if (L >= 12 && L <= 14) return cc::launch_range_b(L, mode, a, rows, stream, lazy);
     if (L == 15) return cc::launch_range_c(L, mode, a, rows, stream, lazy);
     if (L == 16) return cc::launch_range_d(L, mode, a, rows, stream, lazy);
+    if (L == 17) return cc::launch_range_e(L, mode, a, rows, stream, lazy);
     return cudaErrorInvalidValue;
 }
 

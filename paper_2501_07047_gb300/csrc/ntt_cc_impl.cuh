@@ -39,9 +39,18 @@ namespace cc {
 // of eight consecutive rows land on different banks: both patterns are conflict free.
 __device__ __forceinline__ int swz(int j) { return j ^ (((j >> 5) & 7) << 2); }
 
-// Tuning knobs: log2 of the CTAs per row at N = 2^16 and 2^15, the threads of a CTA that
-// holds less than 2^15 elements of a split row, and the CTAs per SM its register budget
-// is sized for.
+// Tuning knobs: log2 of the CTAs per row at N = 2^17, 2^16 and 2^15, the threads of a CTA
+// that holds less than 2^15 elements of a split row, and the CTAs per SM its register budget
+// is sized for (N = 2^17: 2^14 elements and 64 KiB per CTA).
+#ifndef HEFX_CC_LOGP17
+#define HEFX_CC_LOGP17 3
+#endif
+#ifndef HEFX_CC_THREADS17
+#define HEFX_CC_THREADS17 256
+#endif
+#ifndef HEFX_CC_MINB17
+#define HEFX_CC_MINB17 2
+#endif
 #ifndef HEFX_CC_LOGP16
 #define HEFX_CC_LOGP16 3
 #endif
@@ -57,7 +66,8 @@ __device__ __forceinline__ int swz(int j) { return j ^ (((j >> 5) & 7) << 2); }
 
 template <int LOGN>
 struct Cfg {
-    static constexpr int logP = LOGN >= 16 ? HEFX_CC_LOGP16 : (LOGN == 15 ? HEFX_CC_LOGP15 : 0);
+    static constexpr int logP =
+        LOGN >= 17 ? HEFX_CC_LOGP17 : (LOGN == 16 ? HEFX_CC_LOGP16 : (LOGN == 15 ? HEFX_CC_LOGP15 : 0));
     static constexpr int P = 1 << logP;  // CTAs (one cluster) per row
     static constexpr bool split = P > 1;
     static constexpr int logm = LOGN - logP;  // elements of one row segment
@@ -65,8 +75,9 @@ struct Cfg {
     static constexpr int rows = (split || logm >= 13) ? 1 : (1 << (13 - logm));  // row segments per CTA
     static constexpr int elems = m * rows;
     static constexpr bool small_split = split && m < (1 << 15);
-    static constexpr int threads = small_split ? HEFX_CC_SPLIT_THREADS : (elems >= (1 << 14) ? 512 : 256);
-    static constexpr int minb = small_split ? HEFX_CC_SPLIT_MINB : 1;
+    static constexpr int threads = LOGN >= 17 ? HEFX_CC_THREADS17
+                                   : small_split ? HEFX_CC_SPLIT_THREADS : (elems >= (1 << 14) ? 512 : 256);
+    static constexpr int minb = LOGN >= 17 ? HEFX_CC_MINB17 : small_split ? HEFX_CC_SPLIT_MINB : 1;
     static constexpr int smem_bytes = elems * 4;
     static constexpr int S = logm;                  // stages run inside the CTA
     static constexpr int r_small = S < 5 ? S : 5;   // pass over the smallest strides
@@ -682,6 +693,7 @@ cudaError_t launch_range_a(int logn, NttMode mode, const KArgs& a, size_t rows, 
 cudaError_t launch_range_b(int logn, NttMode mode, const KArgs& a, size_t rows, cudaStream_t s, bool lazy);
 cudaError_t launch_range_c(int logn, NttMode mode, const KArgs& a, size_t rows, cudaStream_t s, bool lazy);
 cudaError_t launch_range_d(int logn, NttMode mode, const KArgs& a, size_t rows, cudaStream_t s, bool lazy);
+cudaError_t launch_range_e(int logn, NttMode mode, const KArgs& a, size_t rows, cudaStream_t s, bool lazy);
 
 }  // namespace cc
 }  // namespace hefx

@@ -215,7 +215,7 @@ def test_host_validation(ctx):
         hefx.hefx_params_create(ctx, 12, [q, q])           # repeated
     assert e.value.status == hefx.HEFX_EINVAL
     with pytest.raises(hefx.HefxError) as e:
-        hefx.hefx_params_create(ctx, 17, [q])
+        hefx.hefx_params_create(ctx, 18, [q])
     assert e.value.status == hefx.HEFX_EUNSUPPORTED
     p = hefx.hefx_params_create(ctx, 12, [q])
     try:
@@ -241,5 +241,33 @@ def test_autotune_sets_auto_path(ctx, tmp_path, monkeypatch):
         assert (tmp_path / "tune.json").exists()
         data = inputs.residue_tensor(inputs.derive_seed(12, 16), 2, primes, 1 << 16)
         assert (run_fwd(ctx, p, data, "auto") == oracle.ntt_batch(data, primes)).all()
+    finally:
+        hefx.hefx_params_destroy(p)
+
+
+# ----------------------------------------------------------------------------- N = 2^17
+
+@pytest.mark.parametrize("bits", [28, 30])
+def test_n_2_17(ctx, bits):
+    """N = 2^17 (primes = 1 mod 2^18) on the CUDA cores: 28-bit moduli take the lazy
+    butterflies, 30-bit ones Harvey's; forward, inverse and product against the oracle."""
+    logn, L, batch = 17, 3, 2
+    n = 1 << logn
+    primes = inputs.ntt_primes(L, bits, two_n=1 << 18)
+    p = make_params(ctx, logn, primes)
+    try:
+        a = inputs.residue_tensor(inputs.derive_seed(32, bits, 0), batch, primes, n)
+        b = inputs.residue_tensor(inputs.derive_seed(32, bits, 1), batch, primes, n)
+        got = run_fwd(ctx, p, a, "cudacore")
+        assert (got == oracle.ntt_batch(a, primes)).all()
+        assert (run_inv(ctx, p, got, "cudacore") == a).all()
+        da, db, dc = to_dev(a), to_dev(b), empty_dev(a.shape)
+        hefx.hefx_poly_mul(ctx, p, da, db, dc, batch, "cudacore")
+        hefx.hefx_stream_check(ctx, p)
+        assert (to_host(dc).reshape(a.shape) == oracle.polymul_batch(a, b, primes)).all()
+        # the tensor path is not built for N = 2^17: it refuses instead of computing
+        d = empty_dev((1, L, n))
+        assert hefx.raw_status("hefx_ntt_fwd", ctx, p, d.data_ptr(), 1, hefx.PATHS["tensor"], 0) \
+            == hefx.HEFX_EUNSUPPORTED
     finally:
         hefx.hefx_params_destroy(p)

@@ -339,3 +339,15 @@ def test_bconv_exact_vs_fast_conversion(L, Lp):
         assert (y - xb) % Q == 0 and 0 <= k <= L
         for j, p in enumerate(ps):
             assert (int(fast[j, c]) - exact[j][c] - k * Q) % p == 0
+
+
+def test_ntt_n_2_17_pinned_by_direct_evaluation():
+    """The O(N log N) oracle at N = 2^17 (q = 1 mod 2^18) agrees with the per-output
+    definition a(psi^(2 brv(p) + 1)) at sampled positions, and INTT inverts it."""
+    q = inputs.ntt_primes(1, 30, two_n=1 << 18)[0]
+    n = 1 << 17
+    a = inputs.residue_tensor(inputs.derive_seed(49), 1, [q], n)[0, 0]
+    ahat = oracle.ntt(a, q)
+    for pos in [0, 1, 2, 12345, n // 2, n - 1]:
+        assert int(ahat[pos]) == oracle.ntt_at(a, q, pos)
+    assert (oracle.intt(ahat, q) == a).all()
