@@ -299,7 +299,8 @@ def run_gpu(args):
     torch.cuda.empty_cache()
     if not args.no_extras and world == 1:
         line["extra"] = {"bconv_config3": bench_bconv(ctx, args), "batch_config4": bench_batch(ctx, args),
-                         "he_mult": bench_he_mult(ctx, args)}
+                         "he_mult": bench_he_mult(ctx, args),
+                         "reduction_ablation": bench_reduction_ablation(ctx, args)}
         if args.serve:
             line["extra"]["serving_config5"] = bench_serving(ctx, args)
     hefx.hefx_destroy(ctx)
@@ -353,6 +354,56 @@ def bench_bconv(ctx, args):
                      "hbm_frac": round(gbs / hbm, 4)}
     out["peak"] = f"{hbm} GB/s ({src} hbm_gbs)"
     hefx.hefx_bconv_plan_destroy(plan)
+    return out
+
+
+def bench_reduction_ablation(ctx, args):
+    """The paper's modular-reduction ablation (Sec. V-F) on GB300: Shoup / Montgomery / Barrett
+    twiddle products in the CUDA-core NTT (N = 2^16, L = 24, batch 1 and 8, fwd + inv) and
+    Montgomery / Barrett VecModMul over the same data.  Results are identical across variants."""
+    import torch
+    from paper_2501_07047_gb300 import hefx, inputs
+    primes = inputs.source_primes(L)
+    params = hefx.hefx_params_create(ctx, LOGN, primes)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    s = torch.cuda.current_stream()
+    host = inputs.residue_tensor(inputs.derive_seed(2, 99), BATCH, primes, N)
+    d0 = torch.from_numpy(host.view(np.int32).copy()).cuda()
+    d = d0.clone()
+    out = {"workload": "N=2^16, L=24 28-bit limbs; NTT = fwd + inv per batch; VecModMul over batch 8",
+           "ntt_limb_ntt_per_s": {}, "vec_mod_mul_GB_s": {}}
+    ref = None
+    steps = max(5, args.steps // 2)
+    for red in ("shoup", "montgomery", "barrett"):
+        hefx.hefx_params_set_reduction(ctx, params, red, "montgomery")
+        d.copy_(d0)
+        hefx.hefx_ntt_fwd(ctx, params, d, BATCH, "cudacore", s)
+        torch.cuda.synchronize()
+        if ref is None:
+            ref = d.clone()
+        assert torch.equal(d, ref), f"{red}: forward NTT differs"
+        for b in (1, BATCH):
+            def step():
+                hefx.hefx_ntt_fwd(ctx, params, d, b, "cudacore", s)
+                hefx.hefx_ntt_inv(ctx, params, d, b, "cudacore", s)
+            for _ in range(3):
+                step()
+            ms = _events_time(step, steps, flush, s)
+            out["ntt_limb_ntt_per_s"][f"{red}_batch{b}"] = round(2 * b * L / (ms / 1e3), 1)
+    hefx.hefx_params_set_reduction(ctx, params, "shoup", "montgomery")
+    y = d0.clone()
+    z = torch.empty_like(d0)
+    zref = None
+    for red in ("montgomery", "barrett"):
+        hefx.hefx_params_set_reduction(ctx, params, "shoup", red)
+        hefx.hefx_vec_mod_mul(ctx, params, d0, y, z, BATCH, s)
+        torch.cuda.synchronize()
+        if zref is None:
+            zref = z.clone()
+        assert torch.equal(z, zref), f"{red}: VecModMul differs"
+        ms = _events_time(lambda: hefx.hefx_vec_mod_mul(ctx, params, d0, y, z, BATCH, s), steps, flush, s)
+        out["vec_mod_mul_GB_s"][red] = round(3 * 4 * BATCH * L * N / (ms / 1e3) / 1e9, 1)
+    hefx.hefx_params_destroy(params)
     return out
 
 

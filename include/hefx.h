@@ -90,6 +90,25 @@ void hefx_params_destroy(hefx_params* params);
 hefx_status hefx_params_set_auto_path(hefx_params* params, hefx_path path);
 
 /*
+ * Modular reductions of the paper's ablation (Sec. V-F, "Impact of Modular Reduction
+ * Algorithm": Barrett, Montgomery, Shoup).
+ */
+typedef enum { HEFX_RED_SHOUP = 0, HEFX_RED_MONTGOMERY = 1, HEFX_RED_BARRETT = 2 } hefx_reduction;
+
+/*
+ * Selects the reduction of the CUDA-core NTT's twiddle products (ntt_red; default Shoup) and
+ * of hefx_vec_mod_mul (vec_red; default Montgomery) for this parameter set.  Montgomery
+ * twiddles keep w 2^32 mod q (a second table, built here on first use); Barrett takes the
+ * quotient of the 64-bit product from floor(2^64 / q).  Every choice returns the same
+ * (canonical) results.  Non-default ntt_red covers hefx_ntt_fwd / hefx_ntt_inv at
+ * N = 2^16 only: other sizes, hefx_poly_mul and the tensor path then return EUNSUPPORTED;
+ * batch plans always use Shoup.  vec_red = HEFX_RED_SHOUP is EINVAL (Shoup needs a
+ * precomputed companion of one operand; VecModMul's operands are both runtime values).
+ * Synchronous; not thread-safe with concurrent calls that use the same params.
+ */
+hefx_status hefx_params_set_reduction(hefx_params* params, hefx_reduction ntt_red, hefx_reduction vec_red);
+
+/*
  * In-place forward NTT of d_data[batch][nlimbs][N] (natural order in, bit-reversed out).
  * The definition is Sec. II-A's ring with the bit-reversed output of Sec. IV-B2; the
  * CUDA-core path follows App. A (radix-2 Cooley-Tukey), the tensor path Sec. IV-B

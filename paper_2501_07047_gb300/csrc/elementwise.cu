@@ -17,12 +17,25 @@ __device__ __forceinline__ uint32_t mulmod(uint32_t x, uint32_t y, const LimbCon
     return csub(mul_mont_lazy(t, c.r2, c.q, c.qinv_neg), c.q);
 }
 
+// Barrett variant of the same product (the paper's reduction ablation, Sec. V-F): quotient of
+// the 64-bit product from floor(2^64 / q), one conditional subtraction.
+__device__ __forceinline__ uint32_t mulmod_barrett(uint32_t x, uint32_t y, const LimbConst& c) {
+    const uint64_t z = (uint64_t)x * y;
+    const uint64_t mu = ((uint64_t)c.bar_hi << 32) | c.bar_lo;
+    return csub((uint32_t)(z - __umul64hi(z, mu) * c.q), c.q);
+}
+
+template <bool BARRETT>
 __global__ void __launch_bounds__(256) vec_mod_mul_kernel(const LimbConst* __restrict__ lc, uint32_t L, uint32_t n,
                                                           size_t total4, const uint4* x, const uint4* y, uint4* z) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total4; i += (size_t)gridDim.x * blockDim.x) {
         const LimbConst c = lc[((i * 4) / n) % L];
         const uint4 a = x[i], b = y[i];
-        z[i] = make_uint4(mulmod(a.x, b.x, c), mulmod(a.y, b.y, c), mulmod(a.z, b.z, c), mulmod(a.w, b.w, c));
+        if constexpr (BARRETT)
+            z[i] = make_uint4(mulmod_barrett(a.x, b.x, c), mulmod_barrett(a.y, b.y, c), mulmod_barrett(a.z, b.z, c),
+                              mulmod_barrett(a.w, b.w, c));
+        else
+            z[i] = make_uint4(mulmod(a.x, b.x, c), mulmod(a.y, b.y, c), mulmod(a.z, b.z, c), mulmod(a.w, b.w, c));
     }
 }
 
@@ -123,8 +136,12 @@ cudaError_t launch_vec_mod_mul(const hefx_params* p, const uint32_t* x, const ui
                                cudaStream_t s) {
     const size_t total4 = rows * p->n / 4;  // N >= 8, so rows of N words split into whole uint4
     if (!total4) return cudaSuccess;
-    vec_mod_mul_kernel<<<grid_for(total4), 256, 0, s>>>(p->d_lc, p->nlimbs, p->n, total4, (const uint4*)x,
-                                                        (const uint4*)y, (uint4*)z);
+    if (p->red_vec == HEFX_RED_BARRETT)
+        vec_mod_mul_kernel<true><<<grid_for(total4), 256, 0, s>>>(p->d_lc, p->nlimbs, p->n, total4, (const uint4*)x,
+                                                                  (const uint4*)y, (uint4*)z);
+    else
+        vec_mod_mul_kernel<false><<<grid_for(total4), 256, 0, s>>>(p->d_lc, p->nlimbs, p->n, total4, (const uint4*)x,
+                                                                   (const uint4*)y, (uint4*)z);
     return cudaGetLastError();
 }
 

@@ -190,6 +190,9 @@ hefx_status hefx_params_create(hefx_ctx* ctx, uint32_t log2n, const uint32_t* pr
         c.ninvRw_sh = shoup(vals[3], q);
         c.r2 = (uint32_t)mul_mod(r32, r32, q);
         c.one_sh = shoup(1, q);
+        const uint64_t mu = (uint64_t)((((unsigned __int128)1) << 64) / q);
+        c.bar_lo = (uint32_t)mu;
+        c.bar_hi = (uint32_t)(mu >> 32);
         if (l + 1 < nlimbs) {
             const uint64_t ri = inv_mod(primes[nlimbs - 1] % q, q);
             c.rs_inv = (uint32_t)ri;
@@ -220,6 +223,8 @@ void hefx_params_destroy(hefx_params* p) {
     if (p->d_lc) cudaFree(p->d_lc);
     if (p->d_tw_fwd) cudaFree(p->d_tw_fwd);
     if (p->d_tw_inv) cudaFree(p->d_tw_inv);
+    if (p->d_tw_fwd_mont) cudaFree(p->d_tw_fwd_mont);
+    if (p->d_tw_inv_mont) cudaFree(p->d_tw_inv_mont);
     delete p;
 }
 
@@ -229,6 +234,8 @@ static hefx_status run_ntt(hefx_ctx* ctx, const hefx_params* p, uint32_t* d, siz
     if (st != HEFX_OK) return st;
     if ((st = use_device(ctx)) != HEFX_OK) return st;
     const hefx_path pth = resolve(p, path);
+    if (pth == HEFX_PATH_TENSOR && p->red_ntt != HEFX_RED_SHOUP)
+        return fail(ctx, HEFX_EUNSUPPORTED, "the tensor path has no NTT reduction choice");
     if (pth == HEFX_PATH_TENSOR && (st = ensure_tc(ctx, p)) != HEFX_OK) return st;
     if (batch == 0) return HEFX_OK;
     cudaError_t e;
@@ -236,6 +243,10 @@ static hefx_status run_ntt(hefx_ctx* ctx, const hefx_params* p, uint32_t* d, siz
         hefx_params* pm = const_cast<hefx_params*>(p);
         e = mode == MODE_FWD ? tc2_forward(pm, d, d, 0, nullptr, batch, (cudaStream_t)stream)
                              : tc2_inverse(pm, d, d, batch, (cudaStream_t)stream);
+    } else if (pth == HEFX_PATH_CUDACORE && p->red_ntt != HEFX_RED_SHOUP) {
+        e = launch_ntt_cc_red(p, mode, d, batch * p->nlimbs, (cudaStream_t)stream);
+        if (e == cudaErrorNotSupported)
+            return fail(ctx, HEFX_EUNSUPPORTED, "non-default NTT reduction is built for N = 2^16 only");
     } else if (pth == HEFX_PATH_CUDACORE) {
         e = launch_ntt_cc(p, mode, d, nullptr, d, batch * p->nlimbs, (cudaStream_t)stream);
     } else {
@@ -264,6 +275,8 @@ hefx_status hefx_poly_mul(hefx_ctx* ctx, const hefx_params* p, const uint32_t* a
     if ((st = use_device(ctx)) != HEFX_OK) return st;
     const hefx_path pth = resolve(p, path);
     if (pth != HEFX_PATH_CUDACORE && pth != HEFX_PATH_TENSOR) return fail(ctx, HEFX_EINVAL, "unknown path");
+    if (p->red_ntt != HEFX_RED_SHOUP)
+        return fail(ctx, HEFX_EUNSUPPORTED, "hefx_poly_mul uses the default (Shoup) NTT reduction only");
     if (pth == HEFX_PATH_TENSOR && (st = ensure_tc(ctx, p)) != HEFX_OK) return st;
     if (batch == 0) return HEFX_OK;
     cudaStream_t s = (cudaStream_t)stream;
@@ -389,7 +402,7 @@ hefx_status hefx_vec_mod_mul(hefx_ctx* ctx, const hefx_params* p, const uint32_t
     if ((st = check_ntt_args(ctx, p, z, "d_z")) != HEFX_OK) return st;
     if (batch == 0) return HEFX_OK;
     if ((st = use_device(ctx)) != HEFX_OK) return st;
-    cudaError_t e = launch_vec_mod_mul(p, x, y, z, batch * p->nlimbs, (cudaStream_t)stream);
+    cudaError_t e = launch_vec_mod_mul(p, x, y, z, batch * p->nlimbs, (cudaStream_t)stream);  // p->red_vec
     if (e != cudaSuccess) return cuda_fail(ctx, e, "hefx_vec_mod_mul launch");
     return HEFX_OK;
 }
@@ -651,6 +664,32 @@ hefx_status hefx_stream_check(hefx_ctx* ctx, const hefx_params* p, void* stream)
 }
 
 /* Tuner hook: records the path AUTO resolves to. */
+hefx_status hefx_params_set_reduction(hefx_params* p, hefx_reduction ntt_red, hefx_reduction vec_red) {
+    if (!p) return HEFX_EINVAL;
+    if (ntt_red < HEFX_RED_SHOUP || ntt_red > HEFX_RED_BARRETT)
+        return fail(p->ctx, HEFX_EINVAL, "unknown NTT reduction %d", (int)ntt_red);
+    if (vec_red != HEFX_RED_MONTGOMERY && vec_red != HEFX_RED_BARRETT)
+        return fail(p->ctx, HEFX_EINVAL, "VecModMul reduction must be Montgomery or Barrett");
+    hefx_status st = use_device(p->ctx);
+    if (st != HEFX_OK) return st;
+    if (ntt_red == HEFX_RED_MONTGOMERY && !p->d_tw_fwd_mont) {
+        const size_t bytes = sizeof(uint2) * (size_t)p->nlimbs * p->n;
+        cudaError_t e = cudaMalloc(&p->d_tw_fwd_mont, bytes);
+        if (e == cudaSuccess) e = cudaMalloc(&p->d_tw_inv_mont, bytes);
+        if (e == cudaSuccess) e = make_mont_twiddles(p, p->d_tw_fwd, p->d_tw_fwd_mont);
+        if (e == cudaSuccess) e = make_mont_twiddles(p, p->d_tw_inv, p->d_tw_inv_mont);
+        if (e != cudaSuccess) {
+            cudaFree(p->d_tw_fwd_mont);
+            cudaFree(p->d_tw_inv_mont);
+            p->d_tw_fwd_mont = p->d_tw_inv_mont = nullptr;
+            return cuda_fail(p->ctx, e, "Montgomery twiddle tables");
+        }
+    }
+    p->red_ntt = ntt_red;
+    p->red_vec = vec_red;
+    return HEFX_OK;
+}
+
 hefx_status hefx_params_set_auto_path(hefx_params* p, hefx_path path) {
     if (!p || (path != HEFX_PATH_CUDACORE && path != HEFX_PATH_TENSOR && path != HEFX_PATH_AUTO)) return HEFX_EINVAL;
     p->tuned_path = path;

@@ -25,7 +25,7 @@ struct LimbConst {
     uint32_t r2;                  // 2^64 mod q: two Montgomery products give a plain one
     uint32_t one_sh;              // floor(2^32 / q), Shoup companion of 1: any x < 2^32 -> [0, 2q)
     uint32_t rs_inv, rs_inv_sh;   // q_{L-1}^-1 mod q (Rescale by the set's last prime) and companion
-    uint32_t pad[2];
+    uint32_t bar_lo, bar_hi;      // floor(2^64 / q) (Barrett reduction variant)
 };
 static_assert(sizeof(LimbConst) == 64, "LimbConst is one 64-byte line");
 
@@ -75,6 +75,10 @@ struct hefx_params {
     hefx::Tc2Tables* tc2 = nullptr;   // built on first tensor-path use
     std::mutex tc_mu;
     hefx_path tuned_path = HEFX_PATH_AUTO;
+    int red_ntt = 0;                  // hefx_reduction of the CUDA-core twiddle products
+    int red_vec = 1;                  // hefx_reduction of VecModMul
+    uint2* d_tw_fwd_mont = nullptr;   // Montgomery-form twiddles (w 2^32 mod q), built on demand
+    uint2* d_tw_inv_mont = nullptr;
 };
 
 struct hefx_batch_plan {
@@ -122,6 +126,8 @@ cudaError_t prepare_ntt_cc(const hefx_params* p, NttMode mode);
 cudaError_t launch_ntt_cc_rows(const hefx_params* p, NttMode mode, const RowDesc* d_rows, size_t nrows,
                                cudaStream_t stream);
 
+cudaError_t launch_ntt_cc_red(const hefx_params* p, NttMode mode, uint32_t* data, size_t rows, cudaStream_t stream);
+cudaError_t make_mont_twiddles(const hefx_params* p, const uint2* tw, uint2* out);
 cudaError_t launch_vec_mod_add(const hefx_params* p, const uint32_t* x, const uint32_t* y, uint32_t* z, size_t rows,
                                cudaStream_t s);
 cudaError_t launch_key_inner_product(const hefx_params* p, const uint32_t* dig, const uint32_t* evk, uint32_t* out,

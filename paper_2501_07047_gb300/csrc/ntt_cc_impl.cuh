@@ -257,6 +257,24 @@ __host__ __device__ constexpr int inv_bound_in(int e) {
     return b;
 }
 
+// Twiddle product x w mod q in [0, 2q) for any x < 2^32, by the reduction F selects (bits 2-3):
+// 0 Shoup (w.y = floor(w 2^32 / q)), 1 Montgomery (w.x holds w 2^32 mod q; one REDC), 2 Barrett
+// (64-bit product, quotient from floor(2^64 / q)).  The three are the variants of the paper's
+// modular-reduction ablation (Sec. V-F); Shoup is the default.
+template <int F>
+__device__ __forceinline__ uint32_t twmul(uint32_t x, uint2 w, const LimbConst& lc) {
+    constexpr int RED = (F >> 2) & 3;
+    if constexpr (RED == 1) {
+        return mul_mont_lazy(x, w.x, lc.q, lc.qinv_neg);
+    } else if constexpr (RED == 2) {
+        const uint64_t z = (uint64_t)x * w.x;
+        const uint64_t mu = ((uint64_t)lc.bar_hi << 32) | lc.bar_lo;
+        return (uint32_t)(z - __umul64hi(z, mu) * lc.q);
+    } else {
+        return mul_shoup_lazy(x, w.x, w.y, lc.q);
+    }
+}
+
 // R forward (Cooley-Tukey) stages s0 .. s0+R-1 on registers; stage s pairs j, j + N/2^(s+1)
 // and uses twiddle psi^brv(2^s + G) for group G (one load per group, reused by its
 // butterflies).  Without F & 2 every butterfly keeps Harvey's [0, 4q) range (q < 2^30).
@@ -278,7 +296,7 @@ __device__ __forceinline__ void fwd_stages(uint32_t (&x)[1 << R], uint32_t g0, c
             if ((b & (half - 1)) == 0)
                 w = __ldg(&tw[PERM ? (1u << (s0 + v)) + ((uint32_t)g << s0) + g0 : (1u << (s0 + v)) + (g0 << v) + g]);
             const uint32_t xa = !corr ? x[k] : (LAZY ? mul_shoup_lazy(x[k], 1u, lc.one_sh, q) : csub(x[k], two_q));
-            const uint32_t t = mul_shoup_lazy(x[k + half], w.x, w.y, q);
+            const uint32_t t = twmul<F>(x[k + half], w, lc);
             x[k] = xa + t;
             x[k + half] = xa - t + two_q;
         }
@@ -327,7 +345,7 @@ __device__ __forceinline__ void inv_stages(uint32_t (&x)[1 << R], uint32_t gbase
             const uint32_t X = x[k], Y = x[k + h];
             const uint32_t sum = X + Y;
             x[k] = !red ? sum : (LAZY ? mul_shoup_lazy(sum, 1u, lc.one_sh, q) : csub(sum, two_q));
-            x[k + h] = mul_shoup_lazy(X - Y + cq, w.x, w.y, q);
+            x[k + h] = twmul<F>(X - Y + cq, w, lc);
         }
     }
 }

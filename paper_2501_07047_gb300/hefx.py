@@ -18,6 +18,7 @@ STATUS_NAMES = ["HEFX_OK", "HEFX_EINVAL", "HEFX_EUNSUPPORTED", "HEFX_ENOMEM", "H
                 "HEFX_ETIMEOUT"]
 HEFX_PATH_AUTO, HEFX_PATH_CUDACORE, HEFX_PATH_TENSOR = 0, 1, 2
 PATHS = {"auto": HEFX_PATH_AUTO, "cudacore": HEFX_PATH_CUDACORE, "tensor": HEFX_PATH_TENSOR}
+REDUCTIONS = {"shoup": 0, "montgomery": 1, "barrett": 2}
 
 # Every symbol include/hefx.h declares, with its ctypes signature.
 _vp, _u32, _sz, _i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_size_t, ctypes.c_int
@@ -30,6 +31,7 @@ SIGNATURES = {
     "hefx_params_create": (_i32, [_vp, _u32, _u32p, _u32, ctypes.POINTER(_vp)]),
     "hefx_params_destroy": (None, [_vp]),
     "hefx_params_set_auto_path": (_i32, [_vp, _i32]),
+    "hefx_params_set_reduction": (_i32, [_vp, _i32, _i32]),
     "hefx_ntt_fwd": (_i32, [_vp, _vp, _vp, _sz, _i32, _vp]),
     "hefx_ntt_inv": (_i32, [_vp, _vp, _vp, _sz, _i32, _vp]),
     "hefx_poly_mul": (_i32, [_vp, _vp, _vp, _vp, _vp, _sz, _i32, _vp]),
@@ -145,6 +147,11 @@ def hefx_params_destroy(params: int) -> None:
 
 def hefx_params_set_auto_path(params: int, path) -> int:
     return load().hefx_params_set_auto_path(params, _path(path))
+
+
+def hefx_params_set_reduction(ctx, params: int, ntt_red="shoup", vec_red="montgomery") -> None:
+    """Reduction of the CUDA-core NTT twiddle products and of VecModMul (the paper's ablation)."""
+    _check(ctx, load().hefx_params_set_reduction(params, REDUCTIONS[ntt_red], REDUCTIONS[vec_red]))
 
 
 def hefx_ntt_fwd(ctx, params, data, batch, path="cudacore", stream=None) -> None:
