@@ -441,9 +441,17 @@ def bench_he_mult(ctx, args):
         mult_ms = _events_time(lambda: hm.run(*ins, evk, cq, s, rescale=False), steps, flush, s)
         cw = cq.clone()
         resc_ms = _events_time(lambda: hm.rescale(cw, out, s), steps, flush, s)
-        res[f"L{L}_dnum{dnum}"] = {"he_mult_us": round(mult_ms * 1e3, 1), "rescale_us": round(resc_ms * 1e3, 1),
-                                   "K": alpha, "launches_he_mult": hm.launches(rescale=False),
-                                   "launches_rescale": 3}
+        # the same sequence replayed as one CUDA graph (no per-call host submission)
+        g = hm.capture(*ins, evk, cq, rescale=False)
+        ref = cq.clone()
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(cq, ref), "graph replay differs from the eager run"
+        graph_ms = _events_time(g.replay, steps, flush, s)
+        res[f"L{L}_dnum{dnum}"] = {"he_mult_us": round(mult_ms * 1e3, 1), "he_mult_graph_us": round(graph_ms * 1e3, 1),
+                                   "rescale_us": round(resc_ms * 1e3, 1), "K": alpha,
+                                   "launches_he_mult": hm.launches(rescale=False), "launches_rescale": 3}
+        del g
         hm.close()
         del ins, evk, cq, out, cw
     return res

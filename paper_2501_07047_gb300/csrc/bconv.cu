@@ -109,7 +109,13 @@ __global__ void __launch_bounds__(256) bconv_cc_kernel(const BConvConst* __restr
     __syncthreads();
     const uint32_t L = c.L, Lp = c.Lp;
     const size_t groups = (size_t)n * batch / kCoef;  // n is a multiple of kCoef
-    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < groups; t += (size_t)gridDim.x * blockDim.x) {
+    // one thread per (group of kCoef coefficients, chunk of kJChunk target limbs): the chunk is
+    // the slow index, so the lanes of a warp read consecutive coefficients
+    const uint32_t nchunks = (Lp + kJChunk - 1) / kJChunk;
+    for (size_t tt = blockIdx.x * (size_t)blockDim.x + threadIdx.x; tt < groups * nchunks;
+         tt += (size_t)gridDim.x * blockDim.x) {
+        const size_t t = tt % groups;
+        const uint32_t j0 = (uint32_t)(tt / groups) * kJChunk;
         // kCoef coefficients x, x + stride, ... of one polynomial (stride keeps warps coalesced)
         const size_t per_poly = n / kCoef;
         const size_t b = t / per_poly, x0 = t % per_poly;
@@ -131,7 +137,7 @@ __global__ void __launch_bounds__(256) bconv_cc_kernel(const BConvConst* __restr
                 v[u] = (uint32_t)(hi >> c.kshift);
             }
         }
-        for (uint32_t j0 = 0; j0 < Lp; j0 += kJChunk) {
+        {
             uint64_t acc[kCoef][kJChunk];
 #pragma unroll
             for (int u = 0; u < kCoef; ++u)
@@ -176,8 +182,9 @@ __global__ void __launch_bounds__(256) bconv_cc_kernel(const BConvConst* __restr
     }
 }
 
-unsigned bconv_blocks(size_t total) {
-    size_t blocks = (total + 255) / 256;  // one coefficient per thread, many short blocks
+unsigned bconv_blocks(size_t total, uint32_t Lp) {
+    total *= (Lp + kJChunk - 1) / kJChunk;
+    size_t blocks = (total + 255) / 256;  // one (coefficient, target chunk) per thread, many short blocks
     const size_t cap = (size_t)1 << 20;
     return (unsigned)(blocks > cap ? cap : blocks);
 }
@@ -190,7 +197,7 @@ cudaError_t launch_bconv_cc(const hefx_bconv_plan* plan, const uint32_t* in, uin
     const size_t total = (size_t)n * batch;
     if (total == 0) return cudaSuccess;
     // measured: 4 coefficients per thread (95 registers) is slower than 1
-    bconv_cc_kernel<1, BC_FAST><<<bconv_blocks(total), 256, 0, stream>>>(
+    bconv_cc_kernel<1, BC_FAST><<<bconv_blocks(total, plan->Lp), 256, 0, stream>>>(
         static_cast<const BConvConst*>(plan->d_const), in, out, nullptr, n, (uint32_t)batch, (size_t)plan->L * n,
         (size_t)plan->Lp * n);
     return cudaGetLastError();
@@ -201,7 +208,7 @@ cudaError_t launch_bconv_exact(const hefx_bconv_plan* plan, const uint32_t* in, 
     const uint32_t n = 1u << plan->log2n;
     const size_t total = (size_t)n * batch;
     if (total == 0) return cudaSuccess;
-    bconv_cc_kernel<1, BC_EXACT><<<bconv_blocks(total), 256, 0, stream>>>(
+    bconv_cc_kernel<1, BC_EXACT><<<bconv_blocks(total, plan->Lp), 256, 0, stream>>>(
         static_cast<const BConvConst*>(plan->d_const), in, out, nullptr, n, (uint32_t)batch, (size_t)plan->L * n,
         (size_t)plan->Lp * n);
     return cudaGetLastError();
@@ -214,7 +221,7 @@ cudaError_t launch_mod_down(const hefx_bconv_plan* plan, const uint32_t* x, uint
     const size_t total = (size_t)n * batch;
     if (total == 0) return cudaSuccess;
     const size_t stride = (size_t)(plan->L + plan->Lp) * n;
-    bconv_cc_kernel<1, BC_MODDOWN><<<bconv_blocks(total), 256, 0, stream>>>(
+    bconv_cc_kernel<1, BC_MODDOWN><<<bconv_blocks(total, plan->Lp), 256, 0, stream>>>(
         static_cast<const BConvConst*>(plan->d_const), x + (size_t)plan->Lp * n, out, x, n, (uint32_t)batch, stride,
         (size_t)plan->Lp * n);
     return cudaGetLastError();

@@ -111,6 +111,23 @@ class HeMult:
             hefx.hefx_rescale(self.ctx, self.pQ, c, out, 2, st)
             hefx.hefx_ntt_fwd(self.ctx, self.pQr, out, 2, self.ntt_path, st)
 
+    def capture(self, a0, a1, b0, b1, evk, out, rescale: bool = True):
+        """Records one run on fixed buffers as a CUDA graph (one graph launch replays all the
+        kernel launches and copies, removing the host's per-call submission time).  A first
+        eager run sets every kernel's attributes and occupancy before the capture.  Returns
+        the torch.cuda.CUDAGraph; call .replay() to rerun on the same buffers."""
+        torch = self.torch
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            self.run(a0, a1, b0, b1, evk, out, side, rescale)
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.run(a0, a1, b0, b1, evk, out, torch.cuda.current_stream(), rescale)
+        return g
+
     def stages(self) -> dict:
         """The workspaces after a run (for stage-by-stage parity tests)."""
         return {"d0": self.d[0], "d1": self.d[1], "d2": self.d[2], "modup_eval": self.U, "acc_coeff": self.acc,

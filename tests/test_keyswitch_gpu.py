@@ -140,3 +140,25 @@ def test_he_mult_matches_oracle(hx, logn, L, K, alpha, genuine):
         res = dict(want, c0r=got[0], c1r=got[1])
         assert oks.phase_error(res, s, qs) <= 2 * n + 2 * K + 8
     hm.close()
+
+
+def test_he_mult_graph_replay(hx):
+    """The HE-Mult sequence captured as one CUDA graph replays to the oracle's result."""
+    import torch
+    hefx_, ctx = hx
+    from paper_2501_07047_gb300.hemult import HeMult
+    logn, L, K, alpha = 12, 6, 3, 3
+    qs, ps, s, evk, ins = _he_mult_case(logn, L, K, alpha, 90, True)
+    hm = HeMult(ctx, logn, qs, ps, alpha)
+    out = dev(np.zeros((2, L - 1, 1 << logn), dtype=np.uint32))
+    dins = [dev(a) for a in ins]
+    devk = dev(evk)
+    g = hm.capture(*dins, devk, out)
+    out.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    want = oks.he_mult(*ins, evk, qs, ps, alpha)
+    got = host(out)
+    assert np.array_equal(got[0], want["c0r"]) and np.array_equal(got[1], want["c1r"])
+    del g
+    hm.close()
