@@ -200,6 +200,8 @@ hefx_status hefx_params_create(hefx_ctx* ctx, uint32_t log2n, const uint32_t* pr
         }
     }
     cudaError_t e = cudaMalloc(&p->d_lc, sizeof(LimbConst) * nlimbs);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_err_cc, 4);
+    if (e == cudaSuccess) e = cudaMemset(p->d_err_cc, 0, 4);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_tw_fwd, sizeof(uint2) * twf.size());
     if (e == cudaSuccess) e = cudaMalloc(&p->d_tw_inv, sizeof(uint2) * twi.size());
     if (e == cudaSuccess) e = cudaMemcpy(p->d_lc, lc.data(), sizeof(LimbConst) * nlimbs, cudaMemcpyHostToDevice);
@@ -223,6 +225,7 @@ void hefx_params_destroy(hefx_params* p) {
     if (p->d_lc) cudaFree(p->d_lc);
     if (p->d_tw_fwd) cudaFree(p->d_tw_fwd);
     if (p->d_tw_inv) cudaFree(p->d_tw_inv);
+    if (p->d_err_cc) cudaFree(p->d_err_cc);
     if (p->d_tw_fwd_mont) cudaFree(p->d_tw_fwd_mont);
     if (p->d_tw_inv_mont) cudaFree(p->d_tw_inv_mont);
     delete p;
@@ -657,13 +660,19 @@ hefx_status hefx_stream_check(hefx_ctx* ctx, const hefx_params* p, void* stream)
         if (e == cudaSuccess && code2) e = cudaMemsetAsync(tc2_err(p), 0, 4, (cudaStream_t)stream);
         if (!code) code = code2;
     }
+    if (e == cudaSuccess && p->d_err_cc) {
+        uint32_t code3 = 0;
+        e = cudaMemcpyAsync(&code3, p->d_err_cc, 4, cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+        if (e == cudaSuccess && code3) e = cudaMemsetAsync(p->d_err_cc, 0, 4, (cudaStream_t)stream);
+        if (!code) code = code3;
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "hefx_stream_check");
     if (code) return fail(ctx, HEFX_ETIMEOUT, "a bounded device wait expired (code %u); results are invalid", code);
     return HEFX_OK;
 }
 
-/* Tuner hook: records the path AUTO resolves to. */
 hefx_status hefx_params_set_reduction(hefx_params* p, hefx_reduction ntt_red, hefx_reduction vec_red) {
     if (!p) return HEFX_EINVAL;
     if (ntt_red < HEFX_RED_SHOUP || ntt_red > HEFX_RED_BARRETT)
@@ -690,6 +699,7 @@ hefx_status hefx_params_set_reduction(hefx_params* p, hefx_reduction ntt_red, he
     return HEFX_OK;
 }
 
+/* Tuner hook: records the path AUTO resolves to. */
 hefx_status hefx_params_set_auto_path(hefx_params* p, hefx_path path) {
     if (!p || (path != HEFX_PATH_CUDACORE && path != HEFX_PATH_TENSOR && path != HEFX_PATH_AUTO)) return HEFX_EINVAL;
     p->tuned_path = path;

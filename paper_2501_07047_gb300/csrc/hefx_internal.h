@@ -1,6 +1,7 @@
 // Internal types shared by the hefx host API and its kernels (not part of the C ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -79,6 +80,7 @@ struct hefx_params {
     int red_vec = 1;                  // hefx_reduction of VecModMul
     uint2* d_tw_fwd_mont = nullptr;   // Montgomery-form twiddles (w 2^32 mod q), built on demand
     uint2* d_tw_inv_mont = nullptr;
+    uint32_t* d_err_cc = nullptr;     // CUDA-core kernels' bounded-wait error flag
 };
 
 struct hefx_batch_plan {
@@ -126,6 +128,7 @@ cudaError_t prepare_ntt_cc(const hefx_params* p, NttMode mode);
 cudaError_t launch_ntt_cc_rows(const hefx_params* p, NttMode mode, const RowDesc* d_rows, size_t nrows,
                                cudaStream_t stream);
 
+cudaError_t encode_input_map(const hefx_params* p, const uint32_t* in, size_t rows, CUtensorMap* map);
 cudaError_t launch_ntt_cc_red(const hefx_params* p, NttMode mode, uint32_t* data, size_t rows, cudaStream_t stream);
 cudaError_t make_mont_twiddles(const hefx_params* p, const uint2* tw, uint2* out);
 cudaError_t launch_vec_mod_add(const hefx_params* p, const uint32_t* x, const uint32_t* y, uint32_t* z, size_t rows,

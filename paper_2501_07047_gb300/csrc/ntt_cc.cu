@@ -1,14 +1,31 @@
 // CUDA-core NTT dispatcher and public launchers; the kernels are in ntt_cc_impl.cuh and are
 // instantiated per ring-degree range in ntt_cc_range_*.cu (parallel compilation).
+#include <cstring>
+
 #include "ntt_cc_impl.cuh"
 
 namespace hefx {
 
 cudaError_t launch_dispatch(const hefx_params* p, NttMode mode, const cc::KArgs& a, size_t rows, cudaStream_t stream);
 
+// Tensor map of a contiguous [rows][N] input for the inverse transforms' TMA loads.
+cudaError_t encode_input_map(const hefx_params* p, const uint32_t* in, size_t rows, CUtensorMap* map) {
+    const uint64_t lines = (uint64_t)rows * p->n / 32;  // 128-byte lines of 32 words
+    if (!encode_map_2d(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, const_cast<uint32_t*>(in), 32, lines, 128, 32, 256,
+                       CU_TENSOR_MAP_SWIZZLE_128B))
+        return cudaErrorNotSupported;
+    return cudaSuccess;
+}
+
 cudaError_t launch_ntt_cc(const hefx_params* p, NttMode mode, const uint32_t* in, const uint32_t* had, uint32_t* out,
                           size_t rows, cudaStream_t stream) {
     cc::KArgs a;
+    memset(&a.tmap_in, 0, sizeof a.tmap_in);
+    a.err = p->d_err_cc;
+    if (mode == MODE_INV && rows > 0 && p->log2n >= 13) {
+        cudaError_t e = encode_input_map(p, in, rows, &a.tmap_in);
+        if (e != cudaSuccess) return e;
+    }
     a.in = in;
     a.had = had;
     a.out = out;
@@ -25,6 +42,7 @@ cudaError_t launch_ntt_cc(const hefx_params* p, NttMode mode, const uint32_t* in
 cudaError_t prepare_ntt_cc(const hefx_params* p, NttMode mode) {
     static const RowDesc dummy = {};
     cc::KArgs a = {};
+    a.err = p->d_err_cc;
     a.desc = &dummy;  // selects the row-list kernels; rows == 0 sets attributes without launching
     return launch_dispatch(p, mode, a, 0, nullptr);
 }
@@ -32,6 +50,8 @@ cudaError_t prepare_ntt_cc(const hefx_params* p, NttMode mode) {
 cudaError_t launch_ntt_cc_rows(const hefx_params* p, NttMode mode, const RowDesc* d_rows, size_t nrows,
                                cudaStream_t stream) {
     cc::KArgs a;
+    memset(&a.tmap_in, 0, sizeof a.tmap_in);
+    a.err = p->d_err_cc;
     a.in = nullptr;
     a.had = nullptr;
     a.out = nullptr;

@@ -27,6 +27,7 @@
 
 #include "hefx_internal.h"
 #include "modarith.cuh"
+#include "tc_common.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -92,6 +93,10 @@ struct Cfg {
 };
 
 struct KArgs {
+    // the input viewed as [rows * N / 32][32] uint32, 128-byte swizzle, box 32 x 256: the
+    // inverse transforms of the contiguous layout load their part of a row with it (TMA)
+    alignas(64) CUtensorMap tmap_in;
+    uint32_t* err;      // bounded-wait error flag (a device word, 0 = no error)
     const uint32_t* in;
     const uint32_t* had;
     uint32_t* out;
@@ -571,8 +576,39 @@ __device__ __forceinline__ void inv_cross_pass(uint32_t* sm, const Seg& sg, cons
     cluster.sync();
 }
 
+// The inverse transforms of the contiguous layout take their input part by TMA (an async
+// bulk copy into the swizzled shared layout, which is the tensor map's 128-byte swizzle);
+// row lists (per-row pointers) and the Hadamard form keep the register loads.
 template <int LOGN, int MODE, int F>
-__device__ __forceinline__ void run_task(uint32_t* sm, const Seg& sg, const KArgs& a) {
+__host__ __device__ constexpr bool tma_input() {
+    return MODE == MODE_INV && (F & 1) == 0 && LOGN >= 13;  // whole 256-line boxes per CTA
+}
+
+constexpr uint32_t kErrCcTma = 16;  // error code: the input copy did not arrive in time
+
+// Copies the CTA's elems words (rows of 32 in 256-row boxes) into shared memory and waits
+// (bounded) for them.  On a timeout the error flag is set and the task runs on to its end on
+// whatever the buffer holds, so that every barrier is still reached.
+template <int LOGN>
+__device__ __forceinline__ void load_part_tma(uint32_t* sm, const Seg& sg, const KArgs& a, uint64_t* bar,
+                                              uint32_t& phase) {
+    using C = Cfg<LOGN>;
+    constexpr int N = 1 << LOGN;
+    constexpr int BOXES = C::elems / 8192;  // 256 rows of 32 words per box
+    if (threadIdx.x == 0) {
+        tc::fence_proxy_async_smem();  // earlier generic accesses of the buffer before the copy
+        tc::mbar_arrive_expect_tx(bar, (uint32_t)C::elems * 4u);
+        const int32_t y0 = (int32_t)(((size_t)sg.row0 * N + sg.gbase) / 32);
+#pragma unroll
+        for (int b = 0; b < BOXES; ++b) tc::tma_load_2d(sm + b * 8192, &a.tmap_in, 0, y0 + b * 256, bar);
+    }
+    tc::mbar_wait(bar, phase, a.err, kErrCcTma);
+    phase ^= 1u;
+}
+
+template <int LOGN, int MODE, int F>
+__device__ __forceinline__ void run_task(uint32_t* sm, const Seg& sg, const KArgs& a, uint64_t* tma_bar,
+                                         uint32_t& tma_phase) {
     using C = Cfg<LOGN>;
     constexpr int RS = C::r_small;
     constexpr int S_FIRST = C::logP;              // first stage run inside the CTA
@@ -588,7 +624,9 @@ __device__ __forceinline__ void run_task(uint32_t* sm, const Seg& sg, const KArg
         }
     } else if constexpr (MODE == MODE_INV || MODE == MODE_HAD_INV) {
         constexpr int SCALE = MODE == MODE_INV ? 1 : 2;
-        constexpr int SRC = MODE == MODE_INV ? SRC_GLOBAL : SRC_GLOBAL_HAD;
+        constexpr bool TMA = tma_input<LOGN, MODE, F>();
+        constexpr int SRC = TMA ? SRC_SMEM : (MODE == MODE_INV ? SRC_GLOBAL : SRC_GLOBAL_HAD);
+        if constexpr (TMA) load_part_tma<LOGN>(sm, sg, a, tma_bar, tma_phase);
         if constexpr (C::nrest == 0 && !C::split) {
             inv_pass<RS, LOGN, SCALE, 0, SRC, DST_GLOBAL, F>(sm, sg, a);
         } else {
@@ -612,9 +650,22 @@ __device__ __forceinline__ void run_task(uint32_t* sm, const Seg& sg, const KArg
 }
 
 template <int LOGN, int MODE, int F>
-__global__ void __launch_bounds__(Cfg<LOGN>::threads, Cfg<LOGN>::minb) ntt_cc_kernel(KArgs a) {
+__global__ void __launch_bounds__(Cfg<LOGN>::threads, Cfg<LOGN>::minb) ntt_cc_kernel(const __grid_constant__ KArgs a) {
     using C = Cfg<LOGN>;
-    extern __shared__ __align__(16) uint32_t sm[];
+    extern __shared__ __align__(16) uint32_t sm_raw[];
+    __shared__ uint64_t tma_bar;
+    uint32_t tma_phase = 0;
+    uint32_t* sm = sm_raw;
+    if constexpr (tma_input<LOGN, MODE, F>()) {
+        // the 128-byte swizzle repeats every 1024 bytes: align the buffer to it (1 KiB extra)
+        const uint32_t s0 = tc::smem_u32(sm_raw);
+        sm = sm_raw + ((((s0 + 1023u) & ~1023u) - s0) >> 2);
+        if (threadIdx.x == 0) {
+            tc::mbar_init(&tma_bar, 1);
+            tc::fence_mbar_init();
+        }
+        __syncthreads();
+    }
     // persistent: each CTA (or cluster of P CTAs) walks a strided sequence of tasks; a task
     // is one row (split N) or C::rows rows
     const uint32_t ntasks = C::split ? a.rows : (a.rows + C::rows - 1) / C::rows;
@@ -632,7 +683,7 @@ __global__ void __launch_bounds__(Cfg<LOGN>::threads, Cfg<LOGN>::minb) ntt_cc_ke
             sg.nrows = (int)min((uint32_t)C::rows, a.rows - sg.row0);
         }
         sg.gbase = sg.part * C::m;
-        run_task<LOGN, MODE, F>(sm, sg, a);
+        run_task<LOGN, MODE, F>(sm, sg, a, &tma_bar, tma_phase);
         // shared memory is reused by the next task; with a split row the peers write into it
         if (task + stride < ntasks) sync_all<C::split>();
     }
@@ -644,10 +695,11 @@ template <int LOGN, int MODE, int F>
 cudaError_t launch_one(const KArgs& a, size_t rows, cudaStream_t stream) {
     using C = Cfg<LOGN>;
     auto kern = ntt_cc_kernel<LOGN, MODE, F>;
+    constexpr int smem = C::smem_bytes + (tma_input<LOGN, MODE, F>() ? 1024 : 0);
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     cfg.blockDim = dim3(C::threads);
-    cfg.dynamicSmemBytes = C::smem_bytes;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = stream;
     if (C::split) {
         attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -667,7 +719,7 @@ cudaError_t launch_one(const KArgs& a, size_t rows, cudaStream_t stream) {
     static int cap[64] = {};  // per template instance and device; benign race (idempotent)
     int& g_cap = cap[dev & 63];
     if (g_cap == 0) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::smem_bytes);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         int n = 0;
         if (C::split) {
@@ -676,7 +728,7 @@ cudaError_t launch_one(const KArgs& a, size_t rows, cudaStream_t stream) {
         } else {
             int sms = 0, per_sm = 0;
             e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::threads, C::smem_bytes);
+            if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::threads, smem);
             n = sms * per_sm;
         }
         if (e != cudaSuccess) return e;

@@ -1,6 +1,8 @@
 // The N = 2^16 CUDA-core forward and inverse transforms with Montgomery and Barrett twiddle
 // products: the variants of the paper's modular-reduction ablation (Sec. V-F, "Impact of
 // Modular Reduction Algorithm").  Shoup products, the default, live in ntt_cc_range_d.cu.
+#include <cstring>
+
 #include "ntt_cc_impl.cuh"
 
 namespace hefx {
@@ -32,6 +34,12 @@ cudaError_t launch_ntt_cc_red(const hefx_params* p, NttMode mode, uint32_t* data
     if (p->log2n != 16 || (mode != MODE_FWD && mode != MODE_INV)) return cudaErrorNotSupported;
     if (rows == 0) return cudaSuccess;
     cc::KArgs a;
+    memset(&a.tmap_in, 0, sizeof a.tmap_in);
+    a.err = p->d_err_cc;
+    if (mode == MODE_INV) {
+        cudaError_t e = encode_input_map(p, data, rows, &a.tmap_in);
+        if (e != cudaSuccess) return e;
+    }
     a.in = data;
     a.had = nullptr;
     a.out = data;
