@@ -40,9 +40,9 @@ namespace cc {
 // of eight consecutive rows land on different banks: both patterns are conflict free.
 __device__ __forceinline__ int swz(int j) { return j ^ (((j >> 5) & 7) << 2); }
 
-// Tuning knobs: log2 of the CTAs per row at N = 2^17, 2^16 and 2^15, the threads of a CTA
-// that holds less than 2^15 elements of a split row, and the CTAs per SM its register budget
-// is sized for (N = 2^17: 2^14 elements and 64 KiB per CTA).
+// Tuning knobs: log2 of the CTAs per row at N = 2^17 .. 2^14 (2^13 elements per CTA below
+// N = 2^17), the threads of a CTA that holds less than 2^15 elements of a split row, and the
+// CTAs per SM its register budget is sized for (N = 2^17: 2^14 elements and 64 KiB per CTA).
 #ifndef HEFX_CC_LOGP17
 #define HEFX_CC_LOGP17 3
 #endif
@@ -56,7 +56,10 @@ __device__ __forceinline__ int swz(int j) { return j ^ (((j >> 5) & 7) << 2); }
 #define HEFX_CC_LOGP16 3
 #endif
 #ifndef HEFX_CC_LOGP15
-#define HEFX_CC_LOGP15 0
+#define HEFX_CC_LOGP15 2
+#endif
+#ifndef HEFX_CC_LOGP14
+#define HEFX_CC_LOGP14 1
 #endif
 #ifndef HEFX_CC_SPLIT_THREADS
 #define HEFX_CC_SPLIT_THREADS 128
@@ -68,7 +71,11 @@ __device__ __forceinline__ int swz(int j) { return j ^ (((j >> 5) & 7) << 2); }
 template <int LOGN>
 struct Cfg {
     static constexpr int logP =
-        LOGN >= 17 ? HEFX_CC_LOGP17 : (LOGN == 16 ? HEFX_CC_LOGP16 : (LOGN == 15 ? HEFX_CC_LOGP15 : 0));
+        LOGN >= 17   ? HEFX_CC_LOGP17
+        : LOGN == 16 ? HEFX_CC_LOGP16
+        : LOGN == 15 ? HEFX_CC_LOGP15
+        : LOGN == 14 ? HEFX_CC_LOGP14
+                     : 0;
     static constexpr int P = 1 << logP;  // CTAs (one cluster) per row
     static constexpr bool split = P > 1;
     static constexpr int logm = LOGN - logP;  // elements of one row segment
@@ -689,8 +696,7 @@ __global__ void __launch_bounds__(Cfg<LOGN>::threads, Cfg<LOGN>::minb) ntt_cc_ke
     }
 }
 
-// rows == 0: set the kernel's attributes and measure its occupancy only (done before a
-// stream capture, so that a captured launch makes no query).
+// rows == 0: set the kernel's attributes only (done before a stream capture).
 template <int LOGN, int MODE, int F>
 cudaError_t launch_one(const KArgs& a, size_t rows, cudaStream_t stream) {
     using C = Cfg<LOGN>;
@@ -709,34 +715,20 @@ cudaError_t launch_one(const KArgs& a, size_t rows, cudaStream_t stream) {
         cfg.attrs = attr;
         cfg.numAttrs = 1;
     }
-    // The contiguous layout launches one CTA (cluster) per task and lets the hardware
-    // schedule them (measured faster than a persistent grid with the same number of tasks
-    // per CTA, whose lower occupancy costs more than the partial last wave); row lists run
-    // persistent on the co-resident CTAs (clusters) the runtime reports for this kernel,
-    // measured once per device.
+    // One CTA (cluster) per task, scheduled by the hardware: measured faster than persistent
+    // grids, both with an equal number of tasks per CTA (whose lower occupancy costs more
+    // than a partial last wave) and walking row lists from the co-resident count (config-4
+    // batch 1.30 vs 1.35 ms).  The kernel still loops, so a smaller grid would stay correct.
     int dev = 0;
     cudaGetDevice(&dev);
-    static int cap[64] = {};  // per template instance and device; benign race (idempotent)
-    int& g_cap = cap[dev & 63];
-    if (g_cap == 0) {
+    static bool attr_set[64] = {};  // per template instance and device; benign race (idempotent)
+    if (!attr_set[dev & 63]) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
-        int n = 0;
-        if (C::split) {
-            cfg.gridDim = dim3(C::P);
-            e = cudaOccupancyMaxActiveClusters(&n, kern, &cfg);
-        } else {
-            int sms = 0, per_sm = 0;
-            e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::threads, smem);
-            n = sms * per_sm;
-        }
-        if (e != cudaSuccess) return e;
-        g_cap = n > 0 ? n : 1;
+        attr_set[dev & 63] = true;
     }
     if (rows == 0) return cudaSuccess;
-    const size_t tasks = C::split ? rows : (rows + C::rows - 1) / C::rows;
-    const size_t groups = (F & 1) ? std::min(tasks, (size_t)g_cap) : tasks;
+    const size_t groups = C::split ? rows : (rows + C::rows - 1) / C::rows;
     cfg.gridDim = dim3((unsigned)(C::P * groups));
     return cudaLaunchKernelEx(&cfg, kern, a);
 }
