@@ -487,12 +487,13 @@ def bench_serving(ctx, args):
     ex = GpuExecutor(ctx, nstreams=8)
     res = {"workload": "HE-Mult front half, N in {2^13..2^16}, L in [8, 36], 8 special primes", "budget_GB": 40}
     try:
-        for rate in (100, 400, 1600):
-            reqs = poisson_requests(inputs_seed(5, rate), 120, rate)
+        for rate in (100, 400, 1600, 6400, 25600):
+            count = int(min(2000, max(120, 0.15 * rate)))  # about 0.15 s of arrivals, at least 120
+            reqs = poisson_requests(inputs_seed(5, rate), count, rate)
             for r in reqs:
                 ex.warm(r.logn, r.L)
             serve(reqs[:8], ex)  # warm kernels on this request mix
-            reqs = poisson_requests(inputs_seed(5, rate), 120, rate)
+            reqs = poisson_requests(inputs_seed(5, rate), count, rate)
             st = serve(reqs, ex, budget_bytes=40 << 30)
             res[f"rate_{rate}"] = {k: (round(v, 3) if isinstance(v, float) else v) for k, v in st.items()}
     finally:

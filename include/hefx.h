@@ -258,6 +258,42 @@ hefx_status hefx_tensor_product(hefx_ctx* ctx, const hefx_params* params, const 
                                 uint32_t* d_d2, size_t batch, void* stream);
 
 /*
+ * The HE-Mult front half of one ciphertext pair as one call (Sec. III HE-Mult, built from
+ * NTT, INTT, BConv and VecModMul as in App. A): for ciphertexts (a0, a1), (b0, b1) over the
+ * L limbs of `pq` in evaluation form and keys (k0, k1) over Q u P,
+ *   d0 = a0 o b0, d1 = a0 o b1 + a1 o b0, d2 = a1 o b1,
+ *   p = NTT_P(BConv_{Q->P}(INTT_Q(d2))),  e_k = (d2 o kq_k | p o kp_k),  k = 0, 1.
+ * The plan records (does not own) the Q and P parameter sets, a conversion plan from Q's
+ * primes to P's, and the key buffers kq_k [L][N], kp_k [K][N] (device, evaluation form).
+ * Errors (create): EINVAL for null or foreign arguments, mismatched sizes, primes or N.
+ */
+typedef struct hefx_mult_plan hefx_mult_plan;
+hefx_status hefx_mult_plan_create(hefx_ctx* ctx, const hefx_params* pq, const hefx_params* pp,
+                                  const hefx_bconv_plan* bc, const uint32_t* d_kq0, const uint32_t* d_kq1,
+                                  const uint32_t* d_kp0, const uint32_t* d_kp1, hefx_mult_plan** out);
+void hefx_mult_plan_destroy(hefx_mult_plan* plan);
+
+/*
+ * Runs the front half on `stream`: d_in = [a0, a1, b0, b1], each [L][N]; d_out = [d0, d1,
+ * e0 (Q part), e1 (Q part), e0 (P part), e1 (P part)], [4L + 2K][N] contiguous (one copy reads
+ * every result); d_work [2L + K][N] holds d2, INTT(d2) and p.  The three must not overlap.
+ * CUDA-core transforms; the conversion takes the tensor path where the plan has one.
+ * Errors: EINVAL for null, foreign, misaligned or overlapping buffers; ECUDA.
+ */
+hefx_status hefx_mult_front(hefx_ctx* ctx, const hefx_mult_plan* plan, const uint32_t* d_in, uint32_t* d_out,
+                            uint32_t* d_work, void* stream);
+
+/*
+ * hefx_mult_front with host buffers: copies a0, a1, b0, b1 (host, [L][N] each; pinned memory
+ * lets the copies overlap other work) into d_buf, runs the front half and copies the outputs
+ * ([4L + 2K][N], layout of hefx_mult_front's d_out) back into h_out, all on `stream`.  d_buf
+ * is device memory of [10L + 3K][N] words (inputs, outputs, workspace).  Errors as above.
+ */
+hefx_status hefx_mult_front_host(hefx_ctx* ctx, const hefx_mult_plan* plan, const uint32_t* h_a0,
+                                 const uint32_t* h_a1, const uint32_t* h_b0, const uint32_t* h_b1, uint32_t* h_out,
+                                 uint32_t* d_buf, void* stream);
+
+/*
  * Batched polynomial products of uneven shape (the batching pattern of the build; the
  * paper's batching study is Sec. V-B3, "TPUs favor large batch").  Each job multiplies two
  * polynomials of ring degree N = 2^params->log2n over the first `nlimbs` primes of

@@ -85,6 +85,17 @@ hefx_status ensure_tc(hefx_ctx* ctx, const hefx_params* pc) {
 
 }  // namespace
 
+// Native form of the serving request (HE-Mult front half; see hefx_mult_front in hefx.h):
+// the parameter sets, conversion plan and key buffers belong to the caller.
+struct hefx_mult_plan {
+    hefx_ctx* ctx = nullptr;
+    const hefx_params* pq = nullptr;
+    const hefx_params* pp = nullptr;
+    const hefx_bconv_plan* bc = nullptr;
+    const uint32_t* kq[2] = {nullptr, nullptr};
+    const uint32_t* kp[2] = {nullptr, nullptr};
+};
+
 extern "C" {
 
 const char* hefx_version(void) { return "hefx 0.1 (sm_103a)"; }
@@ -703,6 +714,95 @@ hefx_status hefx_params_set_reduction(hefx_params* p, hefx_reduction ntt_red, he
 hefx_status hefx_params_set_auto_path(hefx_params* p, hefx_path path) {
     if (!p || (path != HEFX_PATH_CUDACORE && path != HEFX_PATH_TENSOR && path != HEFX_PATH_AUTO)) return HEFX_EINVAL;
     p->tuned_path = path;
+    return HEFX_OK;
+}
+
+hefx_status hefx_mult_plan_create(hefx_ctx* ctx, const hefx_params* pq, const hefx_params* pp,
+                                  const hefx_bconv_plan* bc, const uint32_t* d_kq0, const uint32_t* d_kq1,
+                                  const uint32_t* d_kp0, const uint32_t* d_kp1, hefx_mult_plan** out) {
+    if (!ctx || !out) return HEFX_EINVAL;
+    *out = nullptr;
+    if (!pq || !pp || !bc || pq->ctx != ctx || pp->ctx != ctx || bc->ctx != ctx)
+        return fail(ctx, HEFX_EINVAL, "params or plan is null or belongs to another context");
+    if (pq->log2n != pp->log2n || bc->log2n != pq->log2n || bc->L != pq->nlimbs || bc->Lp != pp->nlimbs)
+        return fail(ctx, HEFX_EINVAL, "the conversion plan must map the Q params' limbs to the P params' limbs");
+    for (uint32_t i = 0; i < pq->nlimbs; ++i)
+        if (bc->src[i] != pq->primes[i]) return fail(ctx, HEFX_EINVAL, "plan source %u is not params prime %u", i, i);
+    for (uint32_t j = 0; j < pp->nlimbs; ++j)
+        if (bc->dst[j] != pp->primes[j]) return fail(ctx, HEFX_EINVAL, "plan target %u is not P prime %u", j, j);
+    const void* keys[4] = {d_kq0, d_kq1, d_kp0, d_kp1};
+    for (const void* k : keys)
+        if (!k || !aligned16(k)) return fail(ctx, HEFX_EINVAL, "key pointers must be non-null and 16-byte aligned");
+    hefx_mult_plan* p = new hefx_mult_plan();
+    p->ctx = ctx;
+    p->pq = pq;
+    p->pp = pp;
+    p->bc = bc;
+    p->kq[0] = d_kq0;
+    p->kq[1] = d_kq1;
+    p->kp[0] = d_kp0;
+    p->kp[1] = d_kp1;
+    *out = p;
+    return HEFX_OK;
+}
+
+void hefx_mult_plan_destroy(hefx_mult_plan* plan) { delete plan; }
+
+hefx_status hefx_mult_front(hefx_ctx* ctx, const hefx_mult_plan* plan, const uint32_t* d_in, uint32_t* d_out,
+                            uint32_t* d_work, void* stream) {
+    if (!ctx) return HEFX_EINVAL;
+    if (!plan || plan->ctx != ctx) return fail(ctx, HEFX_EINVAL, "plan is null or belongs to another context");
+    if (!d_in || !d_out || !d_work || !aligned16(d_in) || !aligned16(d_out) || !aligned16(d_work))
+        return fail(ctx, HEFX_EINVAL, "buffers must be non-null and 16-byte aligned");
+    const size_t n = plan->pq->n, L = plan->pq->nlimbs, K = plan->pp->nlimbs;
+    const size_t row = n * 4;
+    const char *in = (const char*)d_in, *o = (const char*)d_out, *w = (const char*)d_work;
+    auto overl = [](const char* a, size_t an, const char* b, size_t bn) { return a < b + bn && b < a + an; };
+    if (overl(o, (4 * L + 2 * K) * row, in, 4 * L * row) || overl(w, (2 * L + K) * row, in, 4 * L * row) ||
+        overl(w, (2 * L + K) * row, o, (4 * L + 2 * K) * row))
+        return fail(ctx, HEFX_EINVAL, "d_in, d_out and d_work must not overlap");
+    hefx_status st = use_device(ctx);
+    if (st != HEFX_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint32_t *a0 = d_in, *a1 = d_in + L * n, *b0 = d_in + 2 * L * n, *b1 = d_in + 3 * L * n;
+    uint32_t *d0 = d_out, *d1 = d_out + L * n, *e0q = d_out + 2 * L * n, *e1q = d_out + 3 * L * n;
+    uint32_t *e0p = d_out + 4 * L * n, *e1p = d_out + (4 * L + K) * n;
+    uint32_t *d2 = d_work, *c = d_work + L * n, *p = d_work + 2 * L * n;
+    cudaError_t e = launch_tensor_product(plan->pq, a0, a1, b0, b1, d0, d1, d2, L, s);
+    if (e == cudaSuccess) e = launch_ntt_cc(plan->pq, MODE_INV, d2, nullptr, c, L, s);  // c = INTT(d2)
+    if (e == cudaSuccess)
+        e = bconv_tc_available(plan->bc) ? launch_bconv_tc(plan->bc, c, p, 1, s) : launch_bconv_cc(plan->bc, c, p, 1, s);
+    if (e == cudaSuccess) e = launch_ntt_cc(plan->pp, MODE_FWD, p, nullptr, p, K, s);
+    if (e == cudaSuccess) e = launch_vec_mod_mul(plan->pq, d2, plan->kq[0], e0q, L, s);
+    if (e == cudaSuccess) e = launch_vec_mod_mul(plan->pq, d2, plan->kq[1], e1q, L, s);
+    if (e == cudaSuccess) e = launch_vec_mod_mul(plan->pp, p, plan->kp[0], e0p, K, s);
+    if (e == cudaSuccess) e = launch_vec_mod_mul(plan->pp, p, plan->kp[1], e1p, K, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "hefx_mult_front launch");
+    return HEFX_OK;
+}
+
+hefx_status hefx_mult_front_host(hefx_ctx* ctx, const hefx_mult_plan* plan, const uint32_t* h_a0,
+                                 const uint32_t* h_a1, const uint32_t* h_b0, const uint32_t* h_b1, uint32_t* h_out,
+                                 uint32_t* d_buf, void* stream) {
+    if (!ctx) return HEFX_EINVAL;
+    if (!plan || plan->ctx != ctx) return fail(ctx, HEFX_EINVAL, "plan is null or belongs to another context");
+    if (!h_a0 || !h_a1 || !h_b0 || !h_b1 || !h_out || !d_buf || !aligned16(d_buf))
+        return fail(ctx, HEFX_EINVAL, "null host buffer or null / misaligned device buffer");
+    hefx_status st = use_device(ctx);
+    if (st != HEFX_OK) return st;
+    const size_t n = plan->pq->n, L = plan->pq->nlimbs, K = plan->pp->nlimbs;
+    const size_t in_bytes = L * n * 4;
+    cudaStream_t s = (cudaStream_t)stream;
+    uint32_t *d_in = d_buf, *d_out = d_buf + 4 * L * n, *d_work = d_buf + (8 * L + 2 * K) * n;
+    const uint32_t* h_in[4] = {h_a0, h_a1, h_b0, h_b1};
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i)
+        e = cudaMemcpyAsync(d_in + i * L * n, h_in[i], in_bytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "hefx_mult_front_host input copy");
+    st = hefx_mult_front(ctx, plan, d_in, d_out, d_work, stream);
+    if (st != HEFX_OK) return st;
+    e = cudaMemcpyAsync(h_out, d_out, (4 * L + 2 * K) * n * 4, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "hefx_mult_front_host output copy");
     return HEFX_OK;
 }
 

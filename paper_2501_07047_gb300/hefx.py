@@ -47,6 +47,10 @@ SIGNATURES = {
     "hefx_key_inner_product": (_i32, [_vp, _vp, _vp, _vp, _vp, _u32, _sz, _vp]),
     "hefx_mod_down": (_i32, [_vp, _vp, _vp, _vp, _sz, _vp]),
     "hefx_rescale": (_i32, [_vp, _vp, _vp, _vp, _sz, _vp]),
+    "hefx_mult_plan_create": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_vp)]),
+    "hefx_mult_plan_destroy": (None, [_vp]),
+    "hefx_mult_front": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "hefx_mult_front_host": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "hefx_batch_plan_create": (_i32, [_vp, _vp, _sz, _i32, ctypes.POINTER(_vp)]),
     "hefx_batch_plan_destroy": (None, [_vp]),
     "hefx_batch_polymul": (_i32, [_vp, _vp, _vp]),
@@ -219,6 +223,26 @@ def hefx_mod_down(ctx, plan, x, out, batch, stream=None) -> None:
 
 def hefx_rescale(ctx, params, x, out, batch, stream=None) -> None:
     _check(ctx, load().hefx_rescale(ctx, params, _ptr(x), _ptr(out), batch, _stream(stream)))
+
+
+def hefx_mult_plan_create(ctx, pq, pp, bc, kq0, kq1, kp0, kp1) -> int:
+    h = _vp()
+    _check(ctx, load().hefx_mult_plan_create(ctx, pq, pp, bc, _ptr(kq0), _ptr(kq1), _ptr(kp0), _ptr(kp1),
+                                             ctypes.byref(h)))
+    return h.value
+
+
+def hefx_mult_plan_destroy(plan) -> None:
+    load().hefx_mult_plan_destroy(plan)
+
+
+def hefx_mult_front(ctx, plan, d_in, d_out, d_work, stream=None) -> None:
+    _check(ctx, load().hefx_mult_front(ctx, plan, _ptr(d_in), _ptr(d_out), _ptr(d_work), _stream(stream)))
+
+
+def hefx_mult_front_host(ctx, plan, h_a0, h_a1, h_b0, h_b1, h_out, d_buf, stream=None) -> None:
+    _check(ctx, load().hefx_mult_front_host(ctx, plan, _ptr(h_a0), _ptr(h_a1), _ptr(h_b0), _ptr(h_b1), _ptr(h_out),
+                                            _ptr(d_buf), _stream(stream)))
 
 
 def hefx_batch_plan_create(ctx, jobs, path="auto") -> int:

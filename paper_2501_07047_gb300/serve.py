@@ -51,8 +51,9 @@ class Request:
 
 
 def request_bytes(logn: int, L: int) -> int:
-    """Device bytes of one request: 4 input, 2 + 2 output and 2 temporary limbs-sets over Q,
-    2 output and 1 temporary limb-sets over P (uint32 residues)."""
+    """Device bytes of one request: 4 input, 4 output and 2 temporary limb-sets over Q (the
+    inputs, d0, d1, the Q parts of e0, e1, then d2 and INTT(d2)), 2 output and 1 temporary
+    limb-sets over P (uint32 residues)."""
     n = 1 << logn
     return 4 * n * (10 * L + 3 * N_SPECIAL)
 
@@ -96,7 +97,7 @@ class Admission:
 class GpuExecutor:
     """Runs requests through the hefx C ABI on a pool of CUDA streams."""
 
-    def __init__(self, ctx: int, nstreams: int = 8, seed: int = 5, variants: int = 2):
+    def __init__(self, ctx: int, nstreams: int = 8, seed: int = 5, variants: int = 2, slots: int | None = None):
         import torch
 
         from . import hefx
@@ -110,6 +111,10 @@ class GpuExecutor:
         self.pools = {}
         self.pparams_cache = {}
         self.qprimes = inputs.source_primes(36)
+        self.free_slots = []
+        # the serving loop keeps at most 4 requests per stream in flight: allocate their slots
+        # now (pinned host memory is slow to allocate while requests are being served)
+        self.free_slots = [self._slot() for _ in range(4 * nstreams if slots is None else slots)]
         self.pprimes = inputs.special_primes(N_SPECIAL)
 
     # ---------------------------------------------------------------- per-shape resources
@@ -149,6 +154,9 @@ class GpuExecutor:
             "pP": self.pparams(logn),
             "bc": hefx.hefx_bconv_plan_create(self.ctx, logn, qs, self.pprimes),
         }
+        pl = self.pool(logn)
+        res["mp"] = hefx.hefx_mult_plan_create(self.ctx, res["pQ"], res["pP"], res["bc"], pl["kQ"][0][:L],
+                                               pl["kQ"][1][:L], pl["kP"][0], pl["kP"][1])
         self.shapes[key] = res
         return res
 
@@ -162,49 +170,40 @@ class GpuExecutor:
         self.shape(logn, L)
 
     # ---------------------------------------------------------------- request lifecycle
+    def _slot(self):
+        """A free (device buffer, pinned output buffer, event) slot, sized for the largest
+        request (N = 2^16, 36 limbs); slots are created on demand and reused."""
+        if self.free_slots:
+            return self.free_slots.pop()
+        torch = self.torch
+        n, L, K = 1 << 16, len(self.qprimes), N_SPECIAL
+        return {"d": torch.empty((10 * L + 3 * K) * n, dtype=torch.int32, device="cuda"),
+                "h": torch.empty((4 * L + 2 * K) * n, dtype=torch.int32, pin_memory=True),
+                "ev": torch.cuda.Event()}
+
     def launch(self, req: Request):
-        torch, hefx = self.torch, self.hefx
+        """Enqueues one request as one hefx_mult_front_host call (four input copies, every
+        stage, one read-back of the contiguous outputs) and a completion event."""
         res = self.shape(req.logn, req.L)
         pl = self.pool(req.logn)
-        n, L = 1 << req.logn, req.L
         s = self.streams[self.next_stream]
         self.next_stream = (self.next_stream + 1) % len(self.streams)
-        with torch.cuda.stream(s):
-            q = torch.empty((10 * L + 3 * N_SPECIAL, n), dtype=torch.int32, device="cuda")
-            a0, a1, b0, b1 = (q[i * L:(i + 1) * L] for i in range(4))
-            d0, d1, d2, c = (q[(4 + i) * L:(5 + i) * L] for i in range(4))
-            e0q, e1q = q[8 * L:9 * L], q[9 * L:10 * L]
-            base = 10 * L
-            p, e0p, e1p = (q[base + i * N_SPECIAL: base + (i + 1) * N_SPECIAL] for i in range(3))
-            for dst, src in zip((a0, a1, b0, b1), pl["host_in"][req.variant % self.variants]):
-                dst.copy_(src[:L], non_blocking=True)
-            st = s.cuda_stream
-            hefx.hefx_tensor_product(self.ctx, res["pQ"], a0, a1, b0, b1, d0, d1, d2, 1, st)
-            c.copy_(d2)
-            hefx.hefx_ntt_inv(self.ctx, res["pQ"], c, 1, "cudacore", st)
-            hefx.hefx_basis_convert(self.ctx, res["bc"], c, p, 1, "auto", st)
-            hefx.hefx_ntt_fwd(self.ctx, res["pP"], p, 1, "cudacore", st)
-            hefx.hefx_vec_mod_mul(self.ctx, res["pQ"], d2, pl["kQ"][0][:L], e0q, 1, st)
-            hefx.hefx_vec_mod_mul(self.ctx, res["pQ"], d2, pl["kQ"][1][:L], e1q, 1, st)
-            hefx.hefx_vec_mod_mul(self.ctx, res["pP"], p, pl["kP"][0], e0p, 1, st)
-            hefx.hefx_vec_mod_mul(self.ctx, res["pP"], p, pl["kP"][1], e1p, 1, st)
-            out = torch.empty((4 * L + 2 * N_SPECIAL, n), dtype=torch.int32, pin_memory=True)
-            out[0:L].copy_(d0, non_blocking=True)
-            out[L:2 * L].copy_(d1, non_blocking=True)
-            out[2 * L:3 * L].copy_(e0q, non_blocking=True)
-            out[3 * L:4 * L].copy_(e1q, non_blocking=True)
-            out[4 * L:4 * L + N_SPECIAL].copy_(e0p, non_blocking=True)
-            out[4 * L + N_SPECIAL:].copy_(e1p, non_blocking=True)
-            ev = torch.cuda.Event()
-            ev.record(s)
-        return {"ev": ev, "buf": q, "out": out, "stream": s}
+        slot = self._slot()
+        a0, a1, b0, b1 = pl["host_in"][req.variant % self.variants]
+        self.hefx.hefx_mult_front_host(self.ctx, res["mp"], a0, a1, b0, b1, slot["h"], slot["d"], s.cuda_stream)
+        slot["ev"].record(s)
+        return {"ev": slot["ev"], "slot": slot, "stream": s}
+
+    def retire(self, handle) -> None:
+        """Returns a completed request's slot to the pool."""
+        self.free_slots.append(handle["slot"])
 
     def done(self, handle) -> bool:
         return handle["ev"].query()
 
     def outputs(self, req: Request, handle):
-        L = req.L
-        o = handle["out"].numpy().view(np.uint32)
+        L, n = req.L, 1 << req.logn
+        o = handle["slot"]["h"][:(4 * L + 2 * N_SPECIAL) * n].numpy().view(np.uint32).reshape(-1, n)
         return (o[0:L].copy(), o[L:2 * L].copy(), np.concatenate([o[2 * L:3 * L], o[4 * L:4 * L + N_SPECIAL]]),
                 np.concatenate([o[3 * L:4 * L], o[4 * L + N_SPECIAL:]]))
 
@@ -218,6 +217,7 @@ class GpuExecutor:
 
     def close(self):
         for res in self.shapes.values():
+            self.hefx.hefx_mult_plan_destroy(res["mp"])
             self.hefx.hefx_bconv_plan_destroy(res["bc"])
             self.hefx.hefx_params_destroy(res["pQ"])
         for p in self.pparams_cache.values():
@@ -225,35 +225,44 @@ class GpuExecutor:
         self.shapes, self.pparams_cache, self.pools = {}, {}, {}
 
 
-def serve(requests, executor, budget_bytes: int = 40 << 30, max_slots: int = 512, keep_outputs: bool = False):
-    """Runs the requests (sorted by arrival) to completion in real time; returns stats."""
+def serve(requests, executor, budget_bytes: int = 40 << 30, max_slots: int | None = None,
+          keep_outputs: bool = False):
+    """Runs the requests (sorted by arrival) to completion in real time; returns stats.
+
+    At most max_slots requests (default: 4 per executor stream) are in flight; later ones wait
+    in the FIFO admission queue, so queueing shows up as latency instead of piling work onto
+    the streams.  A stream completes its requests in order, so only the oldest request of
+    each stream is polled."""
     requests = sorted(requests, key=lambda r: r.arrival)
-    adm = Admission(budget_bytes, max_slots)
-    running = []
+    nstreams = len(getattr(executor, "streams", [])) or 8
+    adm = Admission(budget_bytes, max_slots if max_slots is not None else 4 * nstreams)
+    fifo = collections.defaultdict(collections.deque)  # stream key -> in-flight (req, handle)
     t0 = time.perf_counter()
     i = 0
     max_active = 0
-    while i < len(requests) or adm.queue or running:
+    host_launch = 0.0
+    while i < len(requests) or adm.queue or adm.active:
         now = time.perf_counter() - t0
         while i < len(requests) and requests[i].arrival <= now:
             adm.submit(requests[i])
             i += 1
         for req in adm.admit():
             req.admitted = time.perf_counter() - t0
-            running.append((req, executor.launch(req)))
-        max_active = max(max_active, len(running))
-        still = []
-        for req, h in running:
-            if executor.done(h):
+            h = executor.launch(req)
+            host_launch += time.perf_counter() - t0 - req.admitted
+            fifo[id(h.get("stream")) if isinstance(h, dict) else 0].append((req, h))
+        max_active = max(max_active, adm.active)
+        for q in fifo.values():
+            while q and executor.done(q[0][1]):
+                req, h = q.popleft()
                 req.completed = time.perf_counter() - t0
                 req.status = "done"
                 if keep_outputs:
                     req.outputs = executor.outputs(req, h)
+                if hasattr(executor, "retire"):
+                    executor.retire(h)
                 adm.release(req)
-            else:
-                still.append((req, h))
-        running = still
-        if not running and not adm.queue and i < len(requests):
+        if not adm.active and not adm.queue and i < len(requests):
             wait = requests[i].arrival - (time.perf_counter() - t0)
             if wait > 0:
                 time.sleep(min(wait, 0.01))
@@ -266,6 +275,7 @@ def serve(requests, executor, budget_bytes: int = 40 << 30, max_slots: int = 512
         "throughput_rps": len(done) / span if span > 0 else 0.0,
         "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
         "max_active": max_active, "memory_high_water_bytes": adm.high_water,
+        "host_launch_us_per_request": 1e6 * host_launch / max(1, sum(r.admitted >= 0 for r in requests)),
     }
 
 

@@ -81,3 +81,30 @@ def test_budget_limits_concurrency(ctx):
         assert big.status == "rejected" and st2["rejected"] == 1
     finally:
         ex.close()
+
+
+def test_mult_plan_validation(ctx):
+    """hefx_mult_plan_create refuses a conversion plan that does not map Q's primes to P's."""
+    import torch
+    logn, L = 10, 4
+    qs, ps = inputs.source_primes(L), inputs.special_primes(N_SPECIAL)
+    pq = hefx.hefx_params_create(ctx, logn, qs)
+    pp = hefx.hefx_params_create(ctx, logn, ps)
+    good = hefx.hefx_bconv_plan_create(ctx, logn, qs, ps)
+    bad = hefx.hefx_bconv_plan_create(ctx, logn, inputs.source_primes(L + 1), ps)
+    k = torch.zeros((L + N_SPECIAL, 1 << logn), dtype=torch.int32, device="cuda")
+    try:
+        with pytest.raises(hefx.HefxError) as e:
+            hefx.hefx_mult_plan_create(ctx, pq, pp, bad, k, k, k, k)
+        assert e.value.status == hefx.HEFX_EINVAL
+        mp = hefx.hefx_mult_plan_create(ctx, pq, pp, good, k, k, k, k)
+        buf = torch.zeros((4 * L, 1 << logn), dtype=torch.int32, device="cuda")
+        # overlapping input and output buffers are refused before any launch
+        assert hefx.raw_status("hefx_mult_front", ctx, mp, buf.data_ptr(), buf.data_ptr(), buf.data_ptr(), 0) \
+            == hefx.HEFX_EINVAL
+        hefx.hefx_mult_plan_destroy(mp)
+    finally:
+        for pl in (good, bad):
+            hefx.hefx_bconv_plan_destroy(pl)
+        hefx.hefx_params_destroy(pq)
+        hefx.hefx_params_destroy(pp)
