@@ -315,35 +315,51 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
 }
 
-// Digits of the first step's A operand: TRANS (forward step 1) reads the data matrix by
-// columns (rows of the A operand are the data's columns, K over its rows), otherwise rows.
-template <bool TRANS>
+// Digits of the first step's A operand where its rows are the data's rows (inverse step 1):
+// 4 elements per thread, coalesced 16-byte loads and 32-byte stores.
 __global__ void __launch_bounds__(256) digitize_kernel(const uint32_t* __restrict__ in, uint16_t* __restrict__ dig,
                                                        uint32_t R, uint32_t C, size_t mats) {
     const size_t per = (size_t)R * C / 4;  // 4 elements per thread
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < mats * per; t += (size_t)gridDim.x * blockDim.x) {
         const size_t m = t / per, w = t % per;
-        const uint32_t* src = in + m * R * C;
-        uint16_t* dst = dig + m * R * C * 4;
-        uint32_t x[4];
-        size_t doff;
-        if constexpr (TRANS) {
-            // thread: column c, rows r0..r0+3 -> A row c, K = 4 r0 .. 4 r0 + 15
-            const uint32_t c = (uint32_t)(w % C), r0 = (uint32_t)(w / C) * 4;
-#pragma unroll
-            for (int u = 0; u < 4; ++u) x[u] = __ldg(src + (size_t)(r0 + u) * C + c);
-            doff = (size_t)c * (4 * R) + 4 * r0;
-        } else {
-            const uint4 v = __ldg(reinterpret_cast<const uint4*>(src) + w);
-            x[0] = v.x, x[1] = v.y, x[2] = v.z, x[3] = v.w;
-            const uint32_t r = (uint32_t)((w * 4) / C), c0 = (uint32_t)((w * 4) % C);
-            doff = (size_t)r * (4 * C) + 4 * c0;
-        }
-        const uint2 d0 = tc::split_digits4(x[0]), d1 = tc::split_digits4(x[1]);
-        const uint2 d2 = tc::split_digits4(x[2]), d3 = tc::split_digits4(x[3]);
-        uint4* o = reinterpret_cast<uint4*>(dst + doff);
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(in + m * R * C) + w);
+        const uint32_t r = (uint32_t)((w * 4) / C), c0 = (uint32_t)((w * 4) % C);
+        const uint2 d0 = tc::split_digits4(v.x), d1 = tc::split_digits4(v.y);
+        const uint2 d2 = tc::split_digits4(v.z), d3 = tc::split_digits4(v.w);
+        uint4* o = reinterpret_cast<uint4*>(dig + m * R * C * 4 + (size_t)r * (4 * C) + 4 * c0);
         o[0] = make_uint4(d0.x, d0.y, d1.x, d1.y);
         o[1] = make_uint4(d2.x, d2.y, d3.x, d3.y);
+    }
+}
+
+// Digits of forward step 1's A operand, whose rows are the data's columns (K over its rows):
+// a 32 x 32 tile of the data matrix is read by rows (coalesced 128-byte rows) and written by
+// columns, where the 32 rows of one column are 128 consecutive digits (256 bytes) of one
+// A-operand row.
+__global__ void __launch_bounds__(256) digitize_t_kernel(const uint32_t* __restrict__ in, uint16_t* __restrict__ dig,
+                                                         uint32_t R, uint32_t C, size_t mats) {
+    __shared__ uint32_t tile[32][33];
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const size_t tiles_per = (size_t)(R / 32) * (C / 32);
+    for (size_t t = blockIdx.x; t < mats * tiles_per; t += gridDim.x) {
+        const size_t m = t / tiles_per, w = t % tiles_per;
+        const uint32_t r0 = (uint32_t)(w / (C / 32)) * 32, c0 = (uint32_t)(w % (C / 32)) * 32;
+        const uint32_t* src = in + m * R * C;
+        uint16_t* dst = dig + m * R * C * 4;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t r = warp + 8 * k;
+            tile[r][lane] = __ldg(src + (size_t)(r0 + r) * C + c0 + lane);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t c = warp + 8 * k;  // this warp's column of the tile
+            const uint2 d = tc::split_digits4(tile[lane][c]);
+            // A row c0 + c, K = 4 (r0 + lane) .. + 3
+            *reinterpret_cast<uint2*>(dst + (size_t)(c0 + c) * (4 * R) + 4 * (r0 + lane)) = d;
+        }
+        __syncthreads();
     }
 }
 
@@ -595,10 +611,12 @@ cudaError_t digitize(const hefx_params* p, const uint32_t* in, uint16_t* dig, bo
     const size_t mats = batch * p->nlimbs;
     const size_t work = mats * p->n / 4;
     const unsigned grid = (unsigned)std::min<size_t>((work + 255) / 256, (size_t)1 << 20);
-    if (trans)
-        tc2::digitize_kernel<true><<<grid, 256, 0, s>>>(in, dig, t->R, t->C, mats);
-    else
-        tc2::digitize_kernel<false><<<grid, 256, 0, s>>>(in, dig, t->R, t->C, mats);
+    if (trans) {
+        const size_t tiles = mats * (t->R / 32) * (t->C / 32);
+        tc2::digitize_t_kernel<<<(unsigned)std::min<size_t>(tiles, (size_t)1 << 20), 256, 0, s>>>(in, dig, t->R, t->C,
+                                                                                                mats);
+    } else
+        tc2::digitize_kernel<<<grid, 256, 0, s>>>(in, dig, t->R, t->C, mats);
     return cudaGetLastError();
 }
 
