@@ -21,9 +21,14 @@ cudaError_t launch_ntt_cc(const hefx_params* p, NttMode mode, const uint32_t* in
                           size_t rows, cudaStream_t stream) {
     cc::KArgs a;
     memset(&a.tmap_in, 0, sizeof a.tmap_in);
+    memset(&a.tmap_out, 0, sizeof a.tmap_out);
     a.err = p->d_err_cc;
     if (mode == MODE_INV && rows > 0 && p->log2n >= 13) {
         cudaError_t e = encode_input_map(p, in, rows, &a.tmap_in);
+        if (e != cudaSuccess) return e;
+    }
+    if (mode == MODE_FWD && rows > 0 && p->log2n >= 13) {
+        cudaError_t e = encode_input_map(p, out, rows, &a.tmap_out);
         if (e != cudaSuccess) return e;
     }
     a.in = in;
@@ -51,6 +56,7 @@ cudaError_t launch_ntt_cc_rows(const hefx_params* p, NttMode mode, const RowDesc
                                cudaStream_t stream) {
     cc::KArgs a;
     memset(&a.tmap_in, 0, sizeof a.tmap_in);
+    memset(&a.tmap_out, 0, sizeof a.tmap_out);
     a.err = p->d_err_cc;
     a.in = nullptr;
     a.had = nullptr;

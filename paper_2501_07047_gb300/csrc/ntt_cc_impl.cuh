@@ -103,6 +103,7 @@ struct KArgs {
     // the input viewed as [rows * N / 32][32] uint32, 128-byte swizzle, box 32 x 256: the
     // inverse transforms of the contiguous layout load their part of a row with it (TMA)
     alignas(64) CUtensorMap tmap_in;
+    CUtensorMap tmap_out;  // the output, same view: forward transforms store their part with it
     uint32_t* err;      // bounded-wait error flag (a device word, 0 = no error)
     const uint32_t* in;
     const uint32_t* had;
@@ -141,7 +142,7 @@ __device__ __forceinline__ uint32_t row_limb(const KArgs& a, uint32_t r) {
 
 // Where a register pass takes its inputs and puts its outputs.
 enum : int { SRC_SMEM = 0, SRC_GLOBAL = 1, SRC_GLOBAL_HAD = 3 };
-enum : int { DST_SMEM = 0, DST_GLOBAL = 1, DST_GLOBAL_REDUCE = 2 };
+enum : int { DST_SMEM = 0, DST_GLOBAL = 1, DST_GLOBAL_REDUCE = 2, DST_SMEM_REDUCE = 3 };
 
 // The CTA's share of the batch: rows [row0, row0 + nrows), or segment `part` (elements
 // [gbase, gbase + m)) of row row0 when the row is split.
@@ -218,7 +219,14 @@ __device__ __forceinline__ void store_elems(const uint32_t (&x)[1 << R], uint32_
                                             int row, int jb, const LimbConst& lc) {
     using C = Cfg<LOGN>;
     constexpr int N = 1 << LOGN;
-    if constexpr (DST == DST_SMEM) {
+    if constexpr (DST == DST_SMEM_REDUCE) {  // canonical values into the swizzled buffer (TMA store)
+        static_assert(logs == 0 && R >= 2, "the smallest-stride pass");
+#pragma unroll
+        for (int k = 0; k < (1 << R); k += 4)
+            *reinterpret_cast<uint4*>(&sm[swz(row * C::m + jb + k)]) =
+                make_uint4(reduce_out<F>(x[k], lc), reduce_out<F>(x[k + 1], lc), reduce_out<F>(x[k + 2], lc),
+                           reduce_out<F>(x[k + 3], lc));
+    } else if constexpr (DST == DST_SMEM) {
         if constexpr (logs == 0 && R >= 2) {
 #pragma unroll
             for (int k = 0; k < (1 << R); k += 4)
@@ -590,6 +598,35 @@ template <int LOGN, int MODE, int F>
 __host__ __device__ constexpr bool tma_input() {
     return MODE == MODE_INV && (F & 1) == 0 && LOGN >= 13;  // whole 256-line boxes per CTA
 }
+// The forward transforms of the contiguous layout write their part by TMA (the last pass
+// reduces into the swizzled buffer, one thread stores it as 256-line boxes).
+template <int LOGN, int MODE, int F>
+__host__ __device__ constexpr bool tma_output() {
+    return MODE == MODE_FWD && (F & 1) == 0 && LOGN >= 13;
+}
+template <int LOGN, int MODE, int F>
+__host__ __device__ constexpr bool uses_tma() {
+    return tma_input<LOGN, MODE, F>() || tma_output<LOGN, MODE, F>();
+}
+
+// Stores the CTA's elems words (the buffer, swizzled) to the output by TMA and waits until
+// the copy has read shared memory, so that the buffer may be reused or released.
+template <int LOGN>
+__device__ __forceinline__ void store_part_tma(uint32_t* sm, const Seg& sg, const KArgs& a) {
+    using C = Cfg<LOGN>;
+    constexpr int N = 1 << LOGN;
+    constexpr int BOXES = C::elems / 8192;
+    tc::fence_proxy_async_smem();  // this thread's buffer writes before the async-proxy read
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int32_t y0 = (int32_t)(((size_t)sg.row0 * N + sg.gbase) / 32);
+#pragma unroll
+        for (int b = 0; b < BOXES; ++b) tc::tma_store_2d(&a.tmap_out, 0, y0 + b * 256, sm + b * 8192);
+        tc::bulk_commit();
+        tc::bulk_wait_read0();
+    }
+    __syncthreads();
+}
 
 constexpr uint32_t kErrCcTma = 16;  // error code: the input copy did not arrive in time
 
@@ -622,12 +659,15 @@ __device__ __forceinline__ void run_task(uint32_t* sm, const Seg& sg, const KArg
     constexpr int S_SMALL = LOGN - RS;            // first stage of the smallest-stride pass
 
     if constexpr (MODE == MODE_FWD) {
+        constexpr bool TMA = tma_output<LOGN, MODE, F>();
         if constexpr (C::split) fwd_cross_pass<LOGN, F>(sm, sg, a);
         if constexpr (C::nrest == 0) {
+            static_assert(!TMA, "TMA output needs the smallest-stride pass to follow a shared-memory pass");
             fwd_pass<RS, LOGN, S_FIRST, C::split ? SRC_SMEM : SRC_GLOBAL, DST_GLOBAL_REDUCE, F>(sm, sg, a);
         } else {
             fwd_big<LOGN, 0, S_FIRST, F>(sm, sg, a);
-            fwd_pass<RS, LOGN, S_SMALL, SRC_SMEM, DST_GLOBAL_REDUCE, F>(sm, sg, a);
+            fwd_pass<RS, LOGN, S_SMALL, SRC_SMEM, TMA ? DST_SMEM_REDUCE : DST_GLOBAL_REDUCE, F>(sm, sg, a);
+            if constexpr (TMA) store_part_tma<LOGN>(sm, sg, a);
         }
     } else if constexpr (MODE == MODE_INV || MODE == MODE_HAD_INV) {
         constexpr int SCALE = MODE == MODE_INV ? 1 : 2;
@@ -663,7 +703,7 @@ __global__ void __launch_bounds__(Cfg<LOGN>::threads, Cfg<LOGN>::minb) ntt_cc_ke
     __shared__ uint64_t tma_bar;
     uint32_t tma_phase = 0;
     uint32_t* sm = sm_raw;
-    if constexpr (tma_input<LOGN, MODE, F>()) {
+    if constexpr (uses_tma<LOGN, MODE, F>()) {
         // the 128-byte swizzle repeats every 1024 bytes: align the buffer to it (1 KiB extra)
         const uint32_t s0 = tc::smem_u32(sm_raw);
         sm = sm_raw + ((((s0 + 1023u) & ~1023u) - s0) >> 2);
@@ -701,7 +741,7 @@ template <int LOGN, int MODE, int F>
 cudaError_t launch_one(const KArgs& a, size_t rows, cudaStream_t stream) {
     using C = Cfg<LOGN>;
     auto kern = ntt_cc_kernel<LOGN, MODE, F>;
-    constexpr int smem = C::smem_bytes + (tma_input<LOGN, MODE, F>() ? 1024 : 0);
+    constexpr int smem = C::smem_bytes + (uses_tma<LOGN, MODE, F>() ? 1024 : 0);
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     cfg.blockDim = dim3(C::threads);

@@ -35,11 +35,10 @@ cudaError_t launch_ntt_cc_red(const hefx_params* p, NttMode mode, uint32_t* data
     if (rows == 0) return cudaSuccess;
     cc::KArgs a;
     memset(&a.tmap_in, 0, sizeof a.tmap_in);
+    memset(&a.tmap_out, 0, sizeof a.tmap_out);
     a.err = p->d_err_cc;
-    if (mode == MODE_INV) {
-        cudaError_t e = encode_input_map(p, data, rows, &a.tmap_in);
-        if (e != cudaSuccess) return e;
-    }
+    cudaError_t em = encode_input_map(p, data, rows, mode == MODE_INV ? &a.tmap_in : &a.tmap_out);
+    if (em != cudaSuccess) return em;
     a.in = data;
     a.had = nullptr;
     a.out = data;
