@@ -609,6 +609,39 @@ __host__ __device__ constexpr bool uses_tma() {
     return tma_input<LOGN, MODE, F>() || tma_output<LOGN, MODE, F>();
 }
 
+// Where TMA does not apply (row lists, N < 2^13) the first inverse pass and the last forward
+// pass still move whole lines: the CTA copies its rows between global and shared memory with
+// lane-consecutive 16-byte accesses (the Hadamard product, if any, applied on the way in).
+template <int LOGN, int F, bool HAD>
+__device__ __forceinline__ void copy_in(uint32_t* sm, const Seg& sg, const KArgs& a) {
+    using C = Cfg<LOGN>;
+    constexpr int N = 1 << LOGN;
+    for (int idx = threadIdx.x * 4; idx < sg.nrows * C::m; idx += C::threads * 4) {
+        const int row = idx >> C::logm, i = idx & (C::m - 1);
+        uint4 v = __ldg(reinterpret_cast<const uint4*>(row_in<N, F>(a, sg.row0 + row) + sg.gbase + i));
+        if constexpr (HAD) {
+            const uint4 h = __ldg(reinterpret_cast<const uint4*>(row_had<N, F>(a, sg.row0 + row) + sg.gbase + i));
+            const LimbConst& lc = a.lc[row_limb<F>(a, sg.row0 + row)];
+            v = make_uint4(mul_mont_lazy(v.x, h.x, lc.q, lc.qinv_neg), mul_mont_lazy(v.y, h.y, lc.q, lc.qinv_neg),
+                           mul_mont_lazy(v.z, h.z, lc.q, lc.qinv_neg), mul_mont_lazy(v.w, h.w, lc.q, lc.qinv_neg));
+        }
+        *reinterpret_cast<uint4*>(&sm[swz(row * C::m + i)]) = v;
+    }
+    __syncthreads();
+}
+
+template <int LOGN, int F>
+__device__ __forceinline__ void copy_out(const uint32_t* sm, const Seg& sg, const KArgs& a) {
+    using C = Cfg<LOGN>;
+    constexpr int N = 1 << LOGN;
+    __syncthreads();
+    for (int idx = threadIdx.x * 4; idx < sg.nrows * C::m; idx += C::threads * 4) {
+        const int row = idx >> C::logm, i = idx & (C::m - 1);
+        *reinterpret_cast<uint4*>(row_out<N, F>(a, sg.row0 + row) + sg.gbase + i) =
+            *reinterpret_cast<const uint4*>(&sm[swz(row * C::m + i)]);
+    }
+}
+
 // Stores the CTA's elems words (the buffer, swizzled) to the output by TMA and waits until
 // the copy has read shared memory, so that the buffer may be reused or released.
 template <int LOGN>
@@ -666,17 +699,19 @@ __device__ __forceinline__ void run_task(uint32_t* sm, const Seg& sg, const KArg
             fwd_pass<RS, LOGN, S_FIRST, C::split ? SRC_SMEM : SRC_GLOBAL, DST_GLOBAL_REDUCE, F>(sm, sg, a);
         } else {
             fwd_big<LOGN, 0, S_FIRST, F>(sm, sg, a);
-            fwd_pass<RS, LOGN, S_SMALL, SRC_SMEM, TMA ? DST_SMEM_REDUCE : DST_GLOBAL_REDUCE, F>(sm, sg, a);
+            fwd_pass<RS, LOGN, S_SMALL, SRC_SMEM, DST_SMEM_REDUCE, F>(sm, sg, a);
             if constexpr (TMA) store_part_tma<LOGN>(sm, sg, a);
+            else copy_out<LOGN, F>(sm, sg, a);
         }
     } else if constexpr (MODE == MODE_INV || MODE == MODE_HAD_INV) {
         constexpr int SCALE = MODE == MODE_INV ? 1 : 2;
         constexpr bool TMA = tma_input<LOGN, MODE, F>();
-        constexpr int SRC = TMA ? SRC_SMEM : (MODE == MODE_INV ? SRC_GLOBAL : SRC_GLOBAL_HAD);
-        if constexpr (TMA) load_part_tma<LOGN>(sm, sg, a, tma_bar, tma_phase);
         if constexpr (C::nrest == 0 && !C::split) {
-            inv_pass<RS, LOGN, SCALE, 0, SRC, DST_GLOBAL, F>(sm, sg, a);
+            inv_pass<RS, LOGN, SCALE, 0, MODE == MODE_INV ? SRC_GLOBAL : SRC_GLOBAL_HAD, DST_GLOBAL, F>(sm, sg, a);
         } else {
+            constexpr int SRC = SRC_SMEM;
+            if constexpr (TMA) load_part_tma<LOGN>(sm, sg, a, tma_bar, tma_phase);
+            else copy_in<LOGN, F, MODE == MODE_HAD_INV>(sm, sg, a);
             inv_pass<RS, LOGN, C::split ? 0 : SCALE, 0, SRC, DST_SMEM, F>(sm, sg, a);
             __syncthreads();
             inv_big<LOGN, SCALE, C::nrest - 1, RS, F>(sm, sg, a);
