@@ -144,6 +144,21 @@ def time_oracle(budget_s: float, cores: int | None = None):
 
 # ----------------------------------------------------------------------------- GPU arm
 
+def max_over_ranks(ms: float, dist=None, device: str = "cpu") -> float:
+    """The slowest rank's time (every rank gets it); the time itself without a process group."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world: int, units_per_step: int, steps: int, total_ms: float) -> float:
+    """Whole-job throughput: the units every rank processed over the slowest rank's time."""
+    return world * units_per_step * steps / (total_ms / 1e3)
+
+
 def run_gpu(args):
     import torch
     from paper_2501_07047_gb300 import build, hefx, inputs
@@ -210,13 +225,10 @@ def run_gpu(args):
         inv_ms = [ev[k][1].elapsed_time(ev[k][2]) for k in range(args.steps)]
         step_ms = sum(fwd_ms) / args.steps + sum(inv_ms) / args.steps
         total_ms = step_ms * args.steps
-        if dist:
-            t = torch.tensor([total_ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, dist, "cuda")
         results[path] = {
             "ms_per_step": total_ms / args.steps,
-            "value": world * UNITS_PER_STEP * args.steps / (total_ms / 1e3),
+            "value": job_value(world, UNITS_PER_STEP, args.steps, total_ms),
             "fwd_ms": statistics.mean(fwd_ms), "inv_ms": statistics.mean(inv_ms),
             "wall_s": t_wall, "clocks": clk.summary(),
             "launches_per_step": 2 if path == "cudacore" else 6,
@@ -243,7 +255,7 @@ def run_gpu(args):
         pinned_out.copy_(data, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
     assert torch.equal(pinned_out, host_t)
 
     hbm, bf16, bf16_s, src = peaks()
@@ -288,7 +300,7 @@ def run_gpu(args):
         "roofline": roof,
         "roofline_tensor_path": roof_other,
         "clocks": r["clocks"],
-        "e2e": {"value": round(world * UNITS_PER_STEP * args.steps / (e2e_ms / 1e3), 1), "unit": "limb-NTT/s",
+        "e2e": {"value": round(job_value(world, UNITS_PER_STEP, args.steps, e2e_ms), 1), "unit": "limb-NTT/s",
                 "h2d_bytes_per_step": int(host.nbytes), "d2h_bytes_per_step": int(host.nbytes)},
         "gpu_launches": r["launches_per_step"] * args.steps,
     }
