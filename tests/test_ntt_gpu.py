@@ -271,3 +271,28 @@ def test_n_2_17(ctx, bits):
             == hefx.HEFX_EUNSUPPORTED
     finally:
         hefx.hefx_params_destroy(p)
+
+
+def test_large_batch_sampled(ctx):
+    """A large launch (2048 rows of N = 2^16, 512 MiB: 16k CTAs in 2048 clusters) on the
+    CUDA-core path: sampled rows against the oracle, every row through the round trip."""
+    import torch
+    logn, L, batch = 16, 32, 64
+    n = 1 << logn
+    primes = inputs.source_primes(L)
+    p = make_params(ctx, logn, primes)
+    try:
+        small = inputs.residue_tensor(inputs.derive_seed(33, 0), 2, primes, n)
+        d = torch.from_numpy(np.tile(small, (batch // 2, 1, 1)).view(np.int32)).cuda()
+        d0 = d.clone()
+        hefx.hefx_ntt_fwd(ctx, p, d, batch, "cudacore")
+        hefx.hefx_stream_check(ctx, p)
+        got = to_host(d).reshape(batch, L, n)
+        want = oracle.ntt_batch(small, primes)
+        for b in (0, 1, batch // 2, batch - 1):  # identical inputs in every pair of polynomials
+            assert (got[b] == want[b % 2]).all()
+        hefx.hefx_ntt_inv(ctx, p, d, batch, "cudacore")
+        hefx.hefx_stream_check(ctx, p)
+        assert torch.equal(d, d0)
+    finally:
+        hefx.hefx_params_destroy(p)
