@@ -37,6 +37,9 @@ cudaError_t bconv_plan_upload(hefx_bconv_plan* plan) {
         h.q[i] = (uint32_t)q;
         h.qhat_inv[i] = (uint32_t)qi;
         h.qhat_inv_sh[i] = shoup(qi, q);
+        h.qpack[i][0] = h.q[i];
+        h.qpack[i][1] = h.qhat_inv[i];
+        h.qpack[i][2] = h.qhat_inv_sh[i];
         for (uint32_t j = 0; j < Lp; ++j) {
             uint64_t c = 1;
             for (uint32_t k = 0; k < L; ++k)
@@ -85,6 +88,7 @@ void bconv_plan_free(hefx_bconv_plan* plan) {
 namespace {
 
 constexpr int kJChunk = 8;  // target limbs accumulated per pass over the source limbs
+constexpr int kIGroup = 8;  // source limbs whose loads are in flight together
 
 __device__ __forceinline__ uint32_t barrett64(uint64_t x, uint32_t p, uint64_t mu) {
     const uint64_t qt = __umul64hi(x, mu);  // floor(x / p) or one less
@@ -92,71 +96,123 @@ __device__ __forceinline__ uint32_t barrett64(uint64_t x, uint32_t p, uint64_t m
     return (uint32_t)(r >= p ? r - p : r);
 }
 
-// kCoef coefficients per thread: each constant load serves kCoef products (1 for n < 4).
+// kCoef coefficients per thread: each constant load serves kCoef products.
 // Polynomial b's source limbs start at in + b * in_stride, its outputs at out + b * out_stride.
 // MODE 1 (ModDown): the epilogue returns (x_j - conv_j) * P^-1 mod p_j, x_j at
 // xq + b * in_stride + j n.  MODE 2 (exact): conv_j - v [Q]_{p_j}, v = round(sum_i b_i / q_i).
+// A persistent grid (the resident blocks of every SM) strides over (target chunk, coefficient
+// group), so each block copies the plan constants to shared memory once.
 enum : int { BC_FAST = 0, BC_MODDOWN = 1, BC_EXACT = 2 };
 
-template <int kCoef, int MODE>
-__global__ void __launch_bounds__(256) bconv_cc_kernel(const BConvConst* __restrict__ gc, const uint32_t* __restrict__ in,
-                                                       uint32_t* __restrict__ out, const uint32_t* __restrict__ xq,
-                                                       uint32_t n, uint32_t batch, size_t in_stride,
-                                                       size_t out_stride) {
-    __shared__ BConvConst c;
-    for (int i = threadIdx.x; i < (int)(sizeof(BConvConst) / 4); i += blockDim.x)
-        reinterpret_cast<uint32_t*>(&c)[i] = reinterpret_cast<const uint32_t*>(gc)[i];
-    __syncthreads();
-    const uint32_t L = c.L, Lp = c.Lp;
-    const size_t groups = (size_t)n * batch / kCoef;  // n is a multiple of kCoef
-    // one thread per (group of kCoef coefficients, chunk of kJChunk target limbs): the chunk is
-    // the slow index, so the lanes of a warp read consecutive coefficients
-    const uint32_t nchunks = (Lp + kJChunk - 1) / kJChunk;
-    for (size_t tt = blockIdx.x * (size_t)blockDim.x + threadIdx.x; tt < groups * nchunks;
-         tt += (size_t)gridDim.x * blockDim.x) {
-        const size_t t = tt % groups;
-        const uint32_t j0 = (uint32_t)(tt / groups) * kJChunk;
-        // kCoef coefficients x, x + stride, ... of one polynomial (stride keeps warps coalesced)
-        const size_t per_poly = n / kCoef;
-        const size_t b = t / per_poly, x0 = t % per_poly;
-        const uint32_t* src = in + b * in_stride + x0;
-        uint32_t* dst = out + b * out_stride + x0;
-        uint32_t v[kCoef];  // exact conversion: the multiple of Q to remove
-        if constexpr (MODE == BC_EXACT) {
+template <int kCoef>
+__host__ __device__ constexpr int log2_const() {
+    return kCoef == 1 ? 0 : 1 + log2_const<kCoef / 2>();
+}
+
+// Step 1 and step 2 of one source limb i for kCoef coefficients.
+template <int kCoef>
+__device__ __forceinline__ void bconv_limb(const BConvConst& c, uint32_t i, uint32_t j0, const uint32_t (&x)[kCoef],
+                                           uint64_t (&acc)[kCoef][kJChunk]) {
+    const uint4 qc = *reinterpret_cast<const uint4*>(c.qpack[i]);  // q_i, qhat_i^-1, Shoup companion
+    // kJChunk = 8 consecutive words of row i: two 16-byte shared loads
+    const uint4* row = reinterpret_cast<const uint4*>(&c.qhat_p[i * kBConvMaxLimbs + j0]);
+    const uint4 r0 = row[0], r1 = row[1];
+    const uint32_t cst[kJChunk] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
 #pragma unroll
-            for (int u = 0; u < kCoef; ++u) {
-                uint64_t lo = c.half_lo, hi = c.half_hi;
-                for (uint32_t i = 0; i < L; ++i) {
-                    const uint32_t qi = c.q[i];
-                    const uint32_t bi = csub(mul_shoup_lazy(__ldg(src + (size_t)i * n + u * per_poly), c.qhat_inv[i],
-                                                            c.qhat_inv_sh[i], qi), qi);
-                    const uint64_t plo = (uint64_t)bi * c.w[i], phi = __umul64hi((uint64_t)bi, c.w[i]);
-                    lo += plo;
-                    hi += phi + (lo < plo ? 1u : 0u);
+    for (int u = 0; u < kCoef; ++u) {
+        const uint32_t bi = csub(mul_shoup_lazy(x[u], qc.y, qc.z, qc.x), qc.x);  // step 1
+#pragma unroll
+        for (int jj = 0; jj < kJChunk; ++jj) acc[u][jj] += (uint64_t)bi * cst[jj];  // step 2
+    }
+}
+
+// Exact conversion: accumulate b_i round(2^k / q_i) into a 128-bit (hi, lo) sum.
+__device__ __forceinline__ void exact_limb(const BConvConst& c, uint32_t i, uint32_t x, uint64_t& lo, uint64_t& hi) {
+    const uint4 qc = *reinterpret_cast<const uint4*>(c.qpack[i]);
+    const uint32_t bi = csub(mul_shoup_lazy(x, qc.y, qc.z, qc.x), qc.x);
+    const uint64_t plo = (uint64_t)bi * c.w[i], phi = __umul64hi((uint64_t)bi, c.w[i]);
+    lo += plo;
+    hi += phi + (lo < plo ? 1u : 0u);
+}
+
+// LOGN > 0 fixes the ring degree at compile time (the loads of a group then sit at constant
+// offsets from one pointer); LOGN = 0 takes it from log2n.
+template <int kCoef, int MODE, int LOGN>
+__global__ void __launch_bounds__(256, 5)
+    bconv_cc_kernel(const BConvConst* __restrict__ gc, const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
+                    const uint32_t* __restrict__ xq, uint32_t log2n, uint32_t batch, size_t in_stride,
+                    size_t out_stride) {
+    static_assert((kCoef & (kCoef - 1)) == 0, "kCoef is a power of two");
+    __shared__ __align__(16) BConvConst c;
+    {
+        // the vectors, then the L used rows of the step 2 matrix
+        const uint32_t L = __ldg(&gc->L);
+        const uint32_t words = (uint32_t)(offsetof(BConvConst, qhat_p) / 4) + L * kBConvMaxLimbs;
+        const uint4* s4 = reinterpret_cast<const uint4*>(gc);
+        uint4* d4 = reinterpret_cast<uint4*>(&c);
+        for (uint32_t k = threadIdx.x; k < words / 4; k += blockDim.x) d4[k] = __ldg(s4 + k);
+    }
+    __syncthreads();
+    if (LOGN > 0) log2n = LOGN;
+    const uint32_t L = c.L, Lp = c.Lp;
+    const uint32_t lpp = log2n - log2_const<kCoef>();  // n is a multiple of kCoef
+    const size_t per_poly = (size_t)1 << lpp, n = (size_t)1 << log2n;
+    const size_t groups = (size_t)batch << lpp;
+    const uint32_t Lfull = L - L % kIGroup;  // limbs in full groups
+    // one thread per (chunk of kJChunk target limbs, group of kCoef coefficients): the group is
+    // the fast index, so the lanes of a warp read consecutive coefficients
+    for (uint32_t j0 = 0; j0 < Lp; j0 += kJChunk) {
+        for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < groups; t += (size_t)gridDim.x * blockDim.x) {
+            // kCoef coefficients x, x + stride, ... of one polynomial (stride keeps warps coalesced)
+            const size_t b = t >> lpp, x0 = t & (per_poly - 1);
+            const uint32_t* src = in + b * in_stride + x0;
+            uint32_t* dst = out + b * out_stride + x0;
+            uint32_t v[kCoef];  // exact conversion: the multiple of Q to remove
+            if constexpr (MODE == BC_EXACT) {
+#pragma unroll
+                for (int u = 0; u < kCoef; ++u) {
+                    uint64_t lo = c.half_lo, hi = c.half_hi;
+                    const uint32_t* p = src + u * per_poly;
+                    uint32_t i0 = 0;
+                    for (; i0 < Lfull; i0 += kIGroup, p += kIGroup * n) {
+                        uint32_t xg[kIGroup];
+#pragma unroll
+                        for (int g = 0; g < kIGroup; ++g) xg[g] = __ldg(p + g * n);
+#pragma unroll
+                        for (int g = 0; g < kIGroup; ++g) exact_limb(c, i0 + g, xg[g], lo, hi);
+                    }
+                    for (; i0 < L; ++i0, p += n) exact_limb(c, i0, __ldg(p), lo, hi);
+                    v[u] = (uint32_t)(hi >> c.kshift);
                 }
-                v[u] = (uint32_t)(hi >> c.kshift);
             }
-        }
-        {
             uint64_t acc[kCoef][kJChunk];
 #pragma unroll
             for (int u = 0; u < kCoef; ++u)
 #pragma unroll
                 for (int jj = 0; jj < kJChunk; ++jj) acc[u][jj] = 0;
-            for (uint32_t i = 0; i < L; ++i) {
-                uint32_t v[kCoef];
+            // groups of kIGroup source limbs: the group's loads are all in flight before its
+            // arithmetic, so a thread waits for one DRAM round trip per group, not per limb;
+            // full groups need no bounds checks
+            const uint32_t* p = src;
+            uint32_t i0 = 0;
+            for (; i0 < Lfull; i0 += kIGroup, p += kIGroup * n) {
+                uint32_t x[kIGroup][kCoef];
 #pragma unroll
-                for (int u = 0; u < kCoef; ++u) v[u] = __ldg(src + (size_t)i * n + u * per_poly);
-                const uint32_t qi = c.q[i], w = c.qhat_inv[i], wsh = c.qhat_inv_sh[i];
-                uint32_t cst[kJChunk];
+                for (int g = 0; g < kIGroup; ++g)
 #pragma unroll
-                for (int jj = 0; jj < kJChunk; ++jj) cst[jj] = c.qhat_p[i * kBConvMaxLimbs + j0 + jj];
+                    for (int u = 0; u < kCoef; ++u) x[g][u] = __ldg(p + g * n + u * per_poly);
 #pragma unroll
-                for (int u = 0; u < kCoef; ++u) {
-                    const uint32_t bi = csub(mul_shoup_lazy(v[u], w, wsh, qi), qi);  // step 1
+                for (int g = 0; g < kIGroup; ++g) bconv_limb<kCoef>(c, i0 + g, j0, x[g], acc);
+            }
+            if (i0 < L) {  // the ragged last group
+                uint32_t x[kIGroup][kCoef];
 #pragma unroll
-                    for (int jj = 0; jj < kJChunk; ++jj) acc[u][jj] += (uint64_t)bi * cst[jj];  // step 2
-                }
+                for (int g = 0; g < kIGroup; ++g)
+#pragma unroll
+                    for (int u = 0; u < kCoef; ++u) x[g][u] = i0 + g < L ? __ldg(p + g * n + u * per_poly) : 0u;
+#pragma unroll
+                for (int g = 0; g < kIGroup; ++g)
+                    if (i0 + g < L) bconv_limb<kCoef>(c, i0 + g, j0, x[g], acc);
             }
 #pragma unroll
             for (int jj = 0; jj < kJChunk; ++jj) {
@@ -171,8 +227,8 @@ __global__ void __launch_bounds__(256) bconv_cc_kernel(const BConvConst* __restr
                         }
                         if constexpr (MODE == BC_MODDOWN) {
                             const uint32_t pj = c.p[j];
-                            const uint32_t x = __ldg(xq + b * in_stride + (size_t)j * n + x0 + u * per_poly);
-                            r = csub(mul_shoup_lazy(x + pj - r, c.pinv[j], c.pinv_sh[j], pj), pj);
+                            const uint32_t xj = __ldg(xq + b * in_stride + (size_t)j * n + x0 + u * per_poly);
+                            r = csub(mul_shoup_lazy(xj + pj - r, c.pinv[j], c.pinv_sh[j], pj), pj);
                         }
                         dst[(size_t)j * n + u * per_poly] = r;
                     }
@@ -182,49 +238,68 @@ __global__ void __launch_bounds__(256) bconv_cc_kernel(const BConvConst* __restr
     }
 }
 
-unsigned bconv_blocks(size_t total, uint32_t Lp) {
-    total *= (Lp + kJChunk - 1) / kJChunk;
-    size_t blocks = (total + 255) / 256;  // one (coefficient, target chunk) per thread, many short blocks
-    const size_t cap = (size_t)1 << 20;
-    return (unsigned)(blocks > cap ? cap : blocks);
+// Persistent grid: at most the resident blocks of every SM (occupancy cached per instance).
+template <int kCoef, int MODE, int LOGN>
+unsigned bconv_blocks(size_t total) {
+    static int resident[64];  // blocks per SM x SMs, per device ordinal; 0 = not yet known
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+    if (resident[dev] == 0) {
+        int per_sm = 0, sms = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bconv_cc_kernel<kCoef, MODE, LOGN>, 256, 0) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || per_sm <= 0 || sms <= 0)
+            per_sm = 1, sms = 148;
+        resident[dev] = per_sm * sms;
+    }
+    const size_t blocks = (total / kCoef + 255) / 256;
+    return (unsigned)std::min(blocks, (size_t)resident[dev]);
+}
+
+}  // namespace
+
+namespace {
+
+// The N = 2^16 instance has the ring degree compiled in; every other degree takes the generic one.
+// One coefficient per thread and 5 resident blocks per SM (48 registers) measured best on
+// the conversions of HE-Mult (ModUp 16 -> 48 limbs, ModDown 16 -> 48 limbs of two
+// polynomials); 2 coefficients per thread gained 4% on 24 -> 8 limbs but lost on ModUp.
+template <int MODE>
+cudaError_t launch_cc(const hefx_bconv_plan* plan, const uint32_t* in, uint32_t* out, const uint32_t* xq, size_t batch,
+                      size_t in_stride, cudaStream_t stream) {
+    const size_t total = ((size_t)1 << plan->log2n) * batch;
+    const size_t out_stride = (size_t)plan->Lp << plan->log2n;
+    if (plan->log2n == 16)
+        bconv_cc_kernel<1, MODE, 16><<<bconv_blocks<1, MODE, 16>(total), 256, 0, stream>>>(
+            static_cast<const BConvConst*>(plan->d_const), in, out, xq, plan->log2n, (uint32_t)batch, in_stride,
+            out_stride);
+    else
+        bconv_cc_kernel<1, MODE, 0><<<bconv_blocks<1, MODE, 0>(total), 256, 0, stream>>>(
+            static_cast<const BConvConst*>(plan->d_const), in, out, xq, plan->log2n, (uint32_t)batch, in_stride,
+            out_stride);
+    return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_bconv_cc(const hefx_bconv_plan* plan, const uint32_t* in, uint32_t* out, size_t batch,
                             cudaStream_t stream) {
-    const uint32_t n = 1u << plan->log2n;
-    const size_t total = (size_t)n * batch;
-    if (total == 0) return cudaSuccess;
-    // measured: 4 coefficients per thread (95 registers) is slower than 1
-    bconv_cc_kernel<1, BC_FAST><<<bconv_blocks(total, plan->Lp), 256, 0, stream>>>(
-        static_cast<const BConvConst*>(plan->d_const), in, out, nullptr, n, (uint32_t)batch, (size_t)plan->L * n,
-        (size_t)plan->Lp * n);
-    return cudaGetLastError();
+    if (batch == 0) return cudaSuccess;
+    return launch_cc<BC_FAST>(plan, in, out, nullptr, batch, (size_t)plan->L << plan->log2n, stream);
 }
 
 cudaError_t launch_bconv_exact(const hefx_bconv_plan* plan, const uint32_t* in, uint32_t* out, size_t batch,
                                cudaStream_t stream) {
-    const uint32_t n = 1u << plan->log2n;
-    const size_t total = (size_t)n * batch;
-    if (total == 0) return cudaSuccess;
-    bconv_cc_kernel<1, BC_EXACT><<<bconv_blocks(total, plan->Lp), 256, 0, stream>>>(
-        static_cast<const BConvConst*>(plan->d_const), in, out, nullptr, n, (uint32_t)batch, (size_t)plan->L * n,
-        (size_t)plan->Lp * n);
-    return cudaGetLastError();
+    if (batch == 0) return cudaSuccess;
+    return launch_cc<BC_EXACT>(plan, in, out, nullptr, batch, (size_t)plan->L << plan->log2n, stream);
 }
 
 cudaError_t launch_mod_down(const hefx_bconv_plan* plan, const uint32_t* x, uint32_t* out, size_t batch,
                             cudaStream_t stream) {
     // x: [batch][Lp + L][n] (target-basis limbs first, then the plan's source limbs)
-    const uint32_t n = 1u << plan->log2n;
-    const size_t total = (size_t)n * batch;
-    if (total == 0) return cudaSuccess;
-    const size_t stride = (size_t)(plan->L + plan->Lp) * n;
-    bconv_cc_kernel<1, BC_MODDOWN><<<bconv_blocks(total, plan->Lp), 256, 0, stream>>>(
-        static_cast<const BConvConst*>(plan->d_const), x + (size_t)plan->Lp * n, out, x, n, (uint32_t)batch, stride,
-        (size_t)plan->Lp * n);
-    return cudaGetLastError();
+    if (batch == 0) return cudaSuccess;
+    const size_t n = (size_t)1 << plan->log2n;
+    return launch_cc<BC_MODDOWN>(plan, x + (size_t)plan->Lp * n, out, x, batch, (size_t)(plan->L + plan->Lp) * n,
+                                 stream);
 }
 
 }  // namespace hefx

@@ -1,6 +1,7 @@
 // Basis-conversion plan constants shared by the CUDA-core and tensor-core BConv kernels.
 #pragma once
 
+#include <cstddef>
 #include <cstring>
 
 #include "hefx_internal.h"
@@ -21,12 +22,18 @@ struct BConvConst {
     uint32_t qmod_p[kBConvMaxLimbs];       // Q mod p_j (exact conversion's correction)
     uint64_t w[kBConvMaxLimbs];            // round(2^k / q_i) (exact conversion's estimate of u)
     uint64_t half_lo, half_hi;             // 2^(k-1) as a 128-bit value
-    uint32_t kshift, pad2;                 // k - 64
+    uint32_t kshift, pad2, pad3[2];        // k - 64
+    uint32_t qpack[kBConvMaxLimbs][4];     // (q_i, qhat_i^-1, its Shoup companion, 0): one 16-byte load
     uint32_t qhat_p[kBConvMaxLimbs * kBConvMaxLimbs];  // [i][j] = qhat_i mod p_j (step 2 matrix)
 };
+// 16-byte aligned rows: the kernels read the matrix and copy the struct as uint4
+static_assert(offsetof(BConvConst, qhat_p) % 16 == 0 && sizeof(BConvConst) % 16 == 0, "BConvConst layout");
 
 cudaError_t bconv_tc_upload(hefx_bconv_plan* plan, const BConvConst& h);
 void bconv_tc_free(hefx_bconv_plan* plan);
 bool bconv_tc_available(const hefx_bconv_plan* plan);
+// The path HEFX_PATH_AUTO takes for a call of `batch` polynomials (measured rule: the tensor
+// path wins only with more than 8 targets on throughput-sized calls).
+bool bconv_prefer_tc(const hefx_bconv_plan* plan, size_t batch);
 
 }  // namespace hefx

@@ -230,6 +230,10 @@ bool bconv_tc_available(const hefx_bconv_plan* plan) {
     return plan->d_bat != nullptr && plan->log2n >= 7;
 }
 
+bool bconv_prefer_tc(const hefx_bconv_plan* plan, size_t batch) {
+    return bconv_tc_available(plan) && plan->Lp > 8 && ((batch * plan->L) << plan->log2n) >= ((size_t)96 << 16);
+}
+
 // Offline compile of the step-2 constant (OfflineCompileLeft of Alg. 2 for the right-hand
 // constant matrix): row (j, o), column (i, d) holds chunk_o([qhat_i]_{p_j} 2^32 2^(7d) mod p_j),
 // laid out exactly as the kernel's shared-memory B tile (K-major, 128B swizzle).

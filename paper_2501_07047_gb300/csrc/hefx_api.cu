@@ -374,7 +374,7 @@ hefx_status hefx_basis_convert(hefx_ctx* ctx, const hefx_bconv_plan* plan, const
         return fail(ctx, HEFX_EINVAL, "d_out overlaps d_in");
     hefx_status st = use_device(ctx);
     if (st != HEFX_OK) return st;
-    if (path == HEFX_PATH_AUTO) path = bconv_tc_available(plan) ? HEFX_PATH_TENSOR : HEFX_PATH_CUDACORE;
+    if (path == HEFX_PATH_AUTO) path = bconv_prefer_tc(plan, batch) ? HEFX_PATH_TENSOR : HEFX_PATH_CUDACORE;
     if (path == HEFX_PATH_TENSOR && !bconv_tc_available(plan))
         return fail(ctx, HEFX_EUNSUPPORTED, "tensor basis conversion not available for this plan");
     if (batch == 0) return HEFX_OK;
@@ -771,7 +771,7 @@ hefx_status hefx_mult_front(hefx_ctx* ctx, const hefx_mult_plan* plan, const uin
     cudaError_t e = launch_tensor_product(plan->pq, a0, a1, b0, b1, d0, d1, d2, L, s);
     if (e == cudaSuccess) e = launch_ntt_cc(plan->pq, MODE_INV, d2, nullptr, c, L, s);  // c = INTT(d2)
     if (e == cudaSuccess)
-        e = bconv_tc_available(plan->bc) ? launch_bconv_tc(plan->bc, c, p, 1, s) : launch_bconv_cc(plan->bc, c, p, 1, s);
+        e = bconv_prefer_tc(plan->bc, 1) ? launch_bconv_tc(plan->bc, c, p, 1, s) : launch_bconv_cc(plan->bc, c, p, 1, s);
     if (e == cudaSuccess) e = launch_ntt_cc(plan->pp, MODE_FWD, p, nullptr, p, K, s);
     if (e == cudaSuccess) e = launch_vec_mod_mul(plan->pq, d2, plan->kq[0], e0q, L, s);
     if (e == cudaSuccess) e = launch_vec_mod_mul(plan->pq, d2, plan->kq[1], e1q, L, s);
