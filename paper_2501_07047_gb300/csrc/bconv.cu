@@ -100,8 +100,9 @@ __device__ __forceinline__ uint32_t barrett64(uint64_t x, uint32_t p, uint64_t m
 // Polynomial b's source limbs start at in + b * in_stride, its outputs at out + b * out_stride.
 // MODE 1 (ModDown): the epilogue returns (x_j - conv_j) * P^-1 mod p_j, x_j at
 // xq + b * in_stride + j n.  MODE 2 (exact): conv_j - v [Q]_{p_j}, v = round(sum_i b_i / q_i).
-// A persistent grid (the resident blocks of every SM) strides over (target chunk, coefficient
-// group), so each block copies the plan constants to shared memory once.
+// A persistent grid (at most the resident blocks of every SM) strides over (target chunk,
+// coefficient group) pairs, so each block copies the plan constants to shared memory once
+// and a conversion of one polynomial to many targets still fills the GPU.
 enum : int { BC_FAST = 0, BC_MODDOWN = 1, BC_EXACT = 2 };
 
 template <int kCoef>
@@ -161,8 +162,18 @@ __global__ void __launch_bounds__(256, 5)
     const uint32_t Lfull = L - L % kIGroup;  // limbs in full groups
     // one thread per (chunk of kJChunk target limbs, group of kCoef coefficients): the group is
     // the fast index, so the lanes of a warp read consecutive coefficients
-    for (uint32_t j0 = 0; j0 < Lp; j0 += kJChunk) {
-        for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < groups; t += (size_t)gridDim.x * blockDim.x) {
+    const uint32_t nchunks = (Lp + kJChunk - 1) / kJChunk;
+    // grid-stride over (chunk, group) pairs, chunk-major; the pair advances by a fixed
+    // (chunk, group) step, so there is no division per task
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    const size_t first = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    const uint32_t cstep = (uint32_t)(stride / groups);
+    const size_t tstep = stride - (size_t)cstep * groups;
+    uint32_t chunk = (uint32_t)(first / groups);
+    size_t t = first - (size_t)chunk * groups;
+    while (chunk < nchunks) {
+        const uint32_t j0 = chunk * kJChunk;
+        {
             // kCoef coefficients x, x + stride, ... of one polynomial (stride keeps warps coalesced)
             const size_t b = t >> lpp, x0 = t & (per_poly - 1);
             const uint32_t* src = in + b * in_stride + x0;
@@ -235,12 +246,18 @@ __global__ void __launch_bounds__(256, 5)
                 }
             }
         }
+        t += tstep;  // t + tstep < 2 groups
+        chunk += cstep;
+        if (t >= groups) {
+            t -= groups;
+            ++chunk;
+        }
     }
 }
 
 // Persistent grid: at most the resident blocks of every SM (occupancy cached per instance).
 template <int kCoef, int MODE, int LOGN>
-unsigned bconv_blocks(size_t total) {
+unsigned bconv_blocks(size_t total, uint32_t Lp) {
     static int resident[64];  // blocks per SM x SMs, per device ordinal; 0 = not yet known
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
@@ -251,7 +268,7 @@ unsigned bconv_blocks(size_t total) {
             per_sm = 1, sms = 148;
         resident[dev] = per_sm * sms;
     }
-    const size_t blocks = (total / kCoef + 255) / 256;
+    const size_t blocks = (total / kCoef * ((Lp + kJChunk - 1) / kJChunk) + 255) / 256;
     return (unsigned)std::min(blocks, (size_t)resident[dev]);
 }
 
@@ -269,11 +286,11 @@ cudaError_t launch_cc(const hefx_bconv_plan* plan, const uint32_t* in, uint32_t*
     const size_t total = ((size_t)1 << plan->log2n) * batch;
     const size_t out_stride = (size_t)plan->Lp << plan->log2n;
     if (plan->log2n == 16)
-        bconv_cc_kernel<1, MODE, 16><<<bconv_blocks<1, MODE, 16>(total), 256, 0, stream>>>(
+        bconv_cc_kernel<1, MODE, 16><<<bconv_blocks<1, MODE, 16>(total, plan->Lp), 256, 0, stream>>>(
             static_cast<const BConvConst*>(plan->d_const), in, out, xq, plan->log2n, (uint32_t)batch, in_stride,
             out_stride);
     else
-        bconv_cc_kernel<1, MODE, 0><<<bconv_blocks<1, MODE, 0>(total), 256, 0, stream>>>(
+        bconv_cc_kernel<1, MODE, 0><<<bconv_blocks<1, MODE, 0>(total, plan->Lp), 256, 0, stream>>>(
             static_cast<const BConvConst*>(plan->d_const), in, out, xq, plan->log2n, (uint32_t)batch, in_stride,
             out_stride);
     return cudaGetLastError();
