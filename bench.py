@@ -264,9 +264,10 @@ def run_gpu(args):
     def roof_cudacore(rr):
         dom = max(rr["fwd_ms"], rr["inv_ms"])
         achieved = units_per_launch * BYTES_PER_UNIT / (dom / 1e3) / 1e9
+        which = "fwd" if rr["fwd_ms"] >= rr["inv_ms"] else "inv"
         return {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                "frac": round(achieved / hbm, 4), "traffic": profile_traffic("ntt_cc"),
-                "kernel": "ntt_cc_kernel<16, " + ("FWD" if rr["fwd_ms"] >= rr["inv_ms"] else "INV") + ">",
+                "frac": round(achieved / hbm, 4), "traffic": profile_traffic("ntt_cc", which),
+                "kernel": "ntt_cc_kernel<16, " + which.upper() + ">",
                 "algorithmic_bytes_per_launch": units_per_launch * BYTES_PER_UNIT,
                 "peak_source": f"{src} hbm_gbs"}
 
@@ -524,8 +525,9 @@ def tensor_flops_per_limb_ntt() -> float:
     return tensor_plan.flops_per_limb_ntt(LOGN)
 
 
-def profile_traffic(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if it matches the current source."""
+def profile_traffic(kernel: str, which: str):
+    """DRAM bytes per launch of the `which` ("fwd" / "inv") kernel from the committed ncu
+    summary, if it matches the current source."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.txt")
     try:
         kv = dict(ln.split("=", 1) for ln in open(path).read().split("\n") if "=" in ln)
@@ -533,7 +535,7 @@ def profile_traffic(kernel: str):
         src = os.path.join(ROOT, "paper_2501_07047_gb300", "csrc", kv["source"].strip())
         if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != kv["source_sha"].strip():
             return None
-        return int(float(kv["dram_bytes_per_launch"]))
+        return int(float(kv["dram_bytes_per_launch_" + which]))
     except Exception:
         return None
 

@@ -59,6 +59,7 @@ typedef enum {
 typedef struct hefx_ctx hefx_ctx;
 typedef struct hefx_params hefx_params;
 typedef struct hefx_bconv_plan hefx_bconv_plan;
+typedef struct hefx_modup_plan hefx_modup_plan;
 
 /* Creates a context bound to CUDA device `device` (made current by every hefx call). */
 hefx_status hefx_create(hefx_ctx** out, int device);
@@ -181,6 +182,28 @@ void hefx_bconv_plan_destroy(hefx_bconv_plan* plan);
  */
 hefx_status hefx_basis_convert(hefx_ctx* ctx, const hefx_bconv_plan* plan, const uint32_t* d_in, uint32_t* d_out,
                                size_t batch, hefx_path path, void* stream);
+
+/*
+ * ModUp of hybrid key switching (the HE-Mult / Relin. of Sec. V-A and V-C, "Effects of
+ * Security Parameters", built from BConv per App. A; the formulas are textbook RNS-CKKS):
+ * the ciphertext basis Q = q[0..L) is cut into dnum = ceil(L / alpha) digits D_j = limbs
+ * [j alpha, min(L, (j + 1) alpha)), and digit j's polynomial is extended to Q u P (P =
+ * p[0..K), appended after Q):
+ *   U[b][j][l] = c[b][l]                       for l in D_j,
+ *   U[b][j][l] = BConv_{D_j -> {l}}(c[b][D_j])  otherwise (the fast conversion of
+ *                hefx_basis_convert, sources D_j, target limb l of Q u P).
+ * hefx_modup_plan_create takes the primes (distinct primes in [3, 2^30), L + K <= 64,
+ * alpha in [1, L]) and uploads every digit's constants; EUNSUPPORTED for log2n > 24 or when
+ * alpha * max(q) * max(q, p) >= 2^64.  hefx_mod_up converts all digits in one launch on the
+ * CUDA cores.  Layouts: d_c [batch][L][N] and d_U [batch][dnum][L + K][N], coefficient form,
+ * canonical, 16-byte aligned; d_U must not overlap d_c (EINVAL).
+ */
+hefx_status hefx_modup_plan_create(hefx_ctx* ctx, uint32_t log2n, const uint32_t* q, uint32_t L, const uint32_t* p,
+                                   uint32_t K, uint32_t alpha, hefx_modup_plan** out);
+void hefx_modup_plan_destroy(hefx_modup_plan* plan);
+uint32_t hefx_modup_plan_dnum(const hefx_modup_plan* plan); /* 0 for a null plan */
+hefx_status hefx_mod_up(hefx_ctx* ctx, const hefx_modup_plan* plan, const uint32_t* d_c, uint32_t* d_U, size_t batch,
+                        void* stream);
 
 /*
  * Exact basis conversion (the u-corrected variant of App. B's fast conversion; the paper

@@ -15,6 +15,7 @@
 // products fit in 64 bits) with one Barrett reduction per output; bconv_tc.cu runs it on
 // the tensor cores as a digit-split (BAT) matrix product.
 #include <algorithm>
+#include <vector>
 
 #include "bconv_common.h"
 #include "host_nt.h"
@@ -22,17 +23,15 @@
 
 namespace hefx {
 
-cudaError_t bconv_plan_upload(hefx_bconv_plan* plan) {
-    const uint32_t L = plan->L, Lp = plan->Lp;
-    BConvConst h;
+void fill_bconv_const(const uint32_t* src, uint32_t L, const uint32_t* dst, uint32_t Lp, BConvConst& h) {
     memset(&h, 0, sizeof(h));
     h.L = L;
     h.Lp = Lp;
     for (uint32_t i = 0; i < L; ++i) {
-        const uint64_t q = plan->src[i];
+        const uint64_t q = src[i];
         uint64_t qhat = 1;
         for (uint32_t k = 0; k < L; ++k)
-            if (k != i) qhat = mul_mod(qhat, plan->src[k], q);
+            if (k != i) qhat = mul_mod(qhat, src[k], q);
         const uint64_t qi = inv_mod(qhat, q);
         h.q[i] = (uint32_t)q;
         h.qhat_inv[i] = (uint32_t)qi;
@@ -43,40 +42,65 @@ cudaError_t bconv_plan_upload(hefx_bconv_plan* plan) {
         for (uint32_t j = 0; j < Lp; ++j) {
             uint64_t c = 1;
             for (uint32_t k = 0; k < L; ++k)
-                if (k != i) c = mul_mod(c, plan->src[k], plan->dst[j]);
+                if (k != i) c = mul_mod(c, src[k], dst[j]);
             h.qhat_p[i * kBConvMaxLimbs + j] = (uint32_t)c;
         }
     }
     for (uint32_t j = 0; j < Lp; ++j) {
-        h.p[j] = plan->dst[j];
-        h.p_mu[j] = (uint64_t)(((u128)1 << 64) / plan->dst[j]);  // floor(2^64 / p_j)
+        h.p[j] = dst[j];
+        h.p_mu[j] = (uint64_t)(((u128)1 << 64) / dst[j]);  // floor(2^64 / p_j)
         uint64_t prod = 1;
-        for (uint32_t i = 0; i < L; ++i) prod = mul_mod(prod, plan->src[i], plan->dst[j]);
-        const uint64_t pinv = inv_mod(prod, plan->dst[j]);
+        for (uint32_t i = 0; i < L; ++i) prod = mul_mod(prod, src[i], dst[j]);
+        const uint64_t pinv = inv_mod(prod, dst[j]);
         h.pinv[j] = (uint32_t)pinv;
-        h.pinv_sh[j] = shoup(pinv, plan->dst[j]);
+        h.pinv_sh[j] = shoup(pinv, dst[j]);
         h.qmod_p[j] = (uint32_t)prod;
     }
     // exact conversion: k = 63 + floor(log2(min q_i)) keeps every w_i = round(2^k / q_i) below 2^64
-    uint32_t minq = plan->src[0];
-    for (uint32_t i = 1; i < L; ++i) minq = std::min(minq, plan->src[i]);
+    uint32_t minq = src[0];
+    for (uint32_t i = 1; i < L; ++i) minq = std::min(minq, src[i]);
     int lg = 0;
     while ((2u << lg) <= minq) ++lg;
     const int k = 63 + lg;
     for (uint32_t i = 0; i < L; ++i) {
         const u128 num = (u128)1 << k;
-        const u128 qi = plan->src[i];
+        const u128 qi = src[i];
         h.w[i] = (uint64_t)((num + qi / 2) / qi);
     }
     const u128 half = (u128)1 << (k - 1);
     h.half_lo = (uint64_t)half;
     h.half_hi = (uint64_t)(half >> 64);
     h.kshift = (uint32_t)(k - 64);
+}
+
+cudaError_t bconv_plan_upload(hefx_bconv_plan* plan) {
+    BConvConst h;
+    fill_bconv_const(plan->src.data(), plan->L, plan->dst.data(), plan->Lp, h);
     cudaError_t e = cudaMalloc(&plan->d_const, sizeof(BConvConst));
     if (e != cudaSuccess) return e;
     e = cudaMemcpy(plan->d_const, &h, sizeof(BConvConst), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return e;
     return bconv_tc_upload(plan, h);
+}
+
+// ModUp of hybrid key switching: digit j (limbs [lo, hi) of Q, alpha per digit) converts to
+// every other limb of Q u P, in Q u P order; its own limbs are the skipped rows.
+cudaError_t modup_plan_upload(hefx_modup_plan* mp) {
+    const uint32_t L = mp->L;
+    std::vector<BConvConst> h(mp->dnum);
+    std::vector<uint32_t> qp(mp->q);
+    qp.insert(qp.end(), mp->p.begin(), mp->p.end());
+    for (uint32_t j = 0; j < mp->dnum; ++j) {
+        const uint32_t lo = j * mp->alpha, hi = std::min(L, lo + mp->alpha);
+        std::vector<uint32_t> dst(qp.begin(), qp.begin() + lo);
+        dst.insert(dst.end(), qp.begin() + hi, qp.end());
+        fill_bconv_const(mp->q.data() + lo, hi - lo, dst.data(), (uint32_t)dst.size(), h[j]);
+        h[j].skip_lo = lo;
+        h[j].skip_len = hi - lo;
+    }
+    cudaError_t e = cudaMalloc(&mp->d_const, sizeof(BConvConst) * mp->dnum);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(mp->d_const, h.data(), sizeof(BConvConst) * mp->dnum, cudaMemcpyHostToDevice);
 }
 
 void bconv_plan_free(hefx_bconv_plan* plan) {
@@ -103,7 +127,10 @@ __device__ __forceinline__ uint32_t barrett64(uint64_t x, uint32_t p, uint64_t m
 // A persistent grid (at most the resident blocks of every SM) strides over (target chunk,
 // coefficient group) pairs, so each block copies the plan constants to shared memory once
 // and a conversion of one polynomial to many targets still fills the GPU.
-enum : int { BC_FAST = 0, BC_MODDOWN = 1, BC_EXACT = 2 };
+// MODE 3 (ModUp): block row y converts digit y of a ModUp plan (constants gc[y], sources the
+// input rows from skip_lo, outputs at out + y * out_digit_stride with the digit's own rows
+// skipped); the threads of target chunk 0 also copy the digit's own limbs into those rows.
+enum : int { BC_FAST = 0, BC_MODDOWN = 1, BC_EXACT = 2, BC_MODUP = 3 };
 
 template <int kCoef>
 __host__ __device__ constexpr int log2_const() {
@@ -142,9 +169,10 @@ template <int kCoef, int MODE, int LOGN>
 __global__ void __launch_bounds__(256, 5)
     bconv_cc_kernel(const BConvConst* __restrict__ gc, const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
                     const uint32_t* __restrict__ xq, uint32_t log2n, uint32_t batch, size_t in_stride,
-                    size_t out_stride) {
+                    size_t out_stride, size_t out_digit_stride) {
     static_assert((kCoef & (kCoef - 1)) == 0, "kCoef is a power of two");
     __shared__ __align__(16) BConvConst c;
+    if constexpr (MODE == BC_MODUP) gc += blockIdx.y;
     {
         // the vectors, then the L used rows of the step 2 matrix
         const uint32_t L = __ldg(&gc->L);
@@ -156,6 +184,10 @@ __global__ void __launch_bounds__(256, 5)
     __syncthreads();
     if (LOGN > 0) log2n = LOGN;
     const uint32_t L = c.L, Lp = c.Lp;
+    if constexpr (MODE == BC_MODUP) {
+        in += (size_t)c.skip_lo << log2n;
+        out += blockIdx.y * out_digit_stride;
+    }
     const uint32_t lpp = log2n - log2_const<kCoef>();  // n is a multiple of kCoef
     const size_t per_poly = (size_t)1 << lpp, n = (size_t)1 << log2n;
     const size_t groups = (size_t)batch << lpp;
@@ -214,6 +246,11 @@ __global__ void __launch_bounds__(256, 5)
                     for (int u = 0; u < kCoef; ++u) x[g][u] = __ldg(p + g * n + u * per_poly);
 #pragma unroll
                 for (int g = 0; g < kIGroup; ++g) bconv_limb<kCoef>(c, i0 + g, j0, x[g], acc);
+                if (MODE == BC_MODUP && j0 == 0)
+#pragma unroll
+                    for (int g = 0; g < kIGroup; ++g)
+#pragma unroll
+                        for (int u = 0; u < kCoef; ++u) dst[(size_t)(c.skip_lo + i0 + g) * n + u * per_poly] = x[g][u];
             }
             if (i0 < L) {  // the ragged last group
                 uint32_t x[kIGroup][kCoef];
@@ -224,6 +261,13 @@ __global__ void __launch_bounds__(256, 5)
 #pragma unroll
                 for (int g = 0; g < kIGroup; ++g)
                     if (i0 + g < L) bconv_limb<kCoef>(c, i0 + g, j0, x[g], acc);
+                if (MODE == BC_MODUP && j0 == 0)
+#pragma unroll
+                    for (int g = 0; g < kIGroup; ++g)
+                        if (i0 + g < L)
+#pragma unroll
+                            for (int u = 0; u < kCoef; ++u)
+                                dst[(size_t)(c.skip_lo + i0 + g) * n + u * per_poly] = x[g][u];
             }
 #pragma unroll
             for (int jj = 0; jj < kJChunk; ++jj) {
@@ -241,7 +285,8 @@ __global__ void __launch_bounds__(256, 5)
                             const uint32_t xj = __ldg(xq + b * in_stride + (size_t)j * n + x0 + u * per_poly);
                             r = csub(mul_shoup_lazy(xj + pj - r, c.pinv[j], c.pinv_sh[j], pj), pj);
                         }
-                        dst[(size_t)j * n + u * per_poly] = r;
+                        const uint32_t jr = MODE == BC_MODUP && j >= c.skip_lo ? j + c.skip_len : j;
+                        dst[(size_t)jr * n + u * per_poly] = r;
                     }
                 }
             }
@@ -288,15 +333,39 @@ cudaError_t launch_cc(const hefx_bconv_plan* plan, const uint32_t* in, uint32_t*
     if (plan->log2n == 16)
         bconv_cc_kernel<1, MODE, 16><<<bconv_blocks<1, MODE, 16>(total, plan->Lp), 256, 0, stream>>>(
             static_cast<const BConvConst*>(plan->d_const), in, out, xq, plan->log2n, (uint32_t)batch, in_stride,
-            out_stride);
+            out_stride, 0);
     else
         bconv_cc_kernel<1, MODE, 0><<<bconv_blocks<1, MODE, 0>(total, plan->Lp), 256, 0, stream>>>(
             static_cast<const BConvConst*>(plan->d_const), in, out, xq, plan->log2n, (uint32_t)batch, in_stride,
-            out_stride);
+            out_stride, 0);
     return cudaGetLastError();
 }
 
 }  // namespace
+
+cudaError_t launch_mod_up(const hefx_modup_plan* mp, const uint32_t* c, uint32_t* U, size_t batch,
+                          cudaStream_t stream) {
+    if (batch == 0) return cudaSuccess;
+    const size_t n = (size_t)1 << mp->log2n;
+    const uint32_t rows = mp->L + mp->K;                       // rows of one digit's output
+    const uint32_t lp_max = rows - std::min(mp->alpha, mp->L);  // targets of a full digit (the most)
+    const size_t in_stride = (size_t)mp->L * n, digit_stride = (size_t)rows * n;
+    const size_t out_stride = digit_stride * mp->dnum;
+    const size_t total = n * batch;
+    // the resident blocks of the GPU shared between the digits (block row y = digit y)
+    const unsigned all = mp->log2n == 16 ? bconv_blocks<1, BC_MODUP, 16>(total * mp->dnum, lp_max)
+                                         : bconv_blocks<1, BC_MODUP, 0>(total * mp->dnum, lp_max);
+    const dim3 grid(std::max(1u, all / mp->dnum), mp->dnum);
+    if (mp->log2n == 16)
+        bconv_cc_kernel<1, BC_MODUP, 16><<<grid, 256, 0, stream>>>(static_cast<const BConvConst*>(mp->d_const), c, U,
+                                                                   nullptr, mp->log2n, (uint32_t)batch, in_stride,
+                                                                   out_stride, digit_stride);
+    else
+        bconv_cc_kernel<1, BC_MODUP, 0><<<grid, 256, 0, stream>>>(static_cast<const BConvConst*>(mp->d_const), c, U,
+                                                                  nullptr, mp->log2n, (uint32_t)batch, in_stride,
+                                                                  out_stride, digit_stride);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_bconv_cc(const hefx_bconv_plan* plan, const uint32_t* in, uint32_t* out, size_t batch,
                             cudaStream_t stream) {

@@ -11,7 +11,8 @@ namespace hefx {
 constexpr int kBConvMaxLimbs = 64;
 
 struct BConvConst {
-    uint32_t L, Lp, pad0, pad1;
+    uint32_t L, Lp;
+    uint32_t skip_lo, skip_len;            // ModUp: target j is written at row j + (j >= skip_lo ? skip_len : 0)
     uint32_t q[kBConvMaxLimbs];            // source primes q_i
     uint32_t qhat_inv[kBConvMaxLimbs];     // qhat_i^-1 mod q_i (step 1 constant)
     uint32_t qhat_inv_sh[kBConvMaxLimbs];  // its Shoup companion
@@ -28,6 +29,9 @@ struct BConvConst {
 };
 // 16-byte aligned rows: the kernels read the matrix and copy the struct as uint4
 static_assert(offsetof(BConvConst, qhat_p) % 16 == 0 && sizeof(BConvConst) % 16 == 0, "BConvConst layout");
+
+// Host: the plan constants of a conversion from src[0..L) to dst[0..Lp) (skip fields 0).
+void fill_bconv_const(const uint32_t* src, uint32_t L, const uint32_t* dst, uint32_t Lp, BConvConst& h);
 
 cudaError_t bconv_tc_upload(hefx_bconv_plan* plan, const BConvConst& h);
 void bconv_tc_free(hefx_bconv_plan* plan);

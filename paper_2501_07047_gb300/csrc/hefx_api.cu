@@ -362,6 +362,72 @@ void hefx_bconv_plan_destroy(hefx_bconv_plan* p) {
     delete p;
 }
 
+hefx_status hefx_modup_plan_create(hefx_ctx* ctx, uint32_t log2n, const uint32_t* q, uint32_t L, const uint32_t* p,
+                                   uint32_t K, uint32_t alpha, hefx_modup_plan** out) {
+    if (!ctx || !out) return HEFX_EINVAL;
+    *out = nullptr;
+    if (log2n > 24) return fail(ctx, HEFX_EUNSUPPORTED, "log2n = %u outside [0, 24]", log2n);
+    if (!q || !p || L == 0 || K == 0 || L + K > (uint32_t)kBConvMaxLimbs)
+        return fail(ctx, HEFX_EINVAL, "need L >= 1, K >= 1 and L + K <= %d primes", kBConvMaxLimbs);
+    if (alpha == 0 || alpha > L) return fail(ctx, HEFX_EINVAL, "alpha = %u outside [1, L]", alpha);
+    std::set<uint32_t> seen;
+    uint64_t mq = 0, mqp = 0;
+    for (uint32_t i = 0; i < L + K; ++i) {
+        const uint32_t v = i < L ? q[i] : p[i - L];
+        if (v < 3 || v >= (1u << 30) || !is_prime(v))
+            return fail(ctx, HEFX_EINVAL, "modulus %u is not a prime in [3, 2^30)", v);
+        if (!seen.insert(v).second) return fail(ctx, HEFX_EINVAL, "modulus %u repeats", v);
+        if (i < L) mq = std::max<uint64_t>(mq, v);
+        mqp = std::max<uint64_t>(mqp, v);
+    }
+    // each digit's conversion accumulates alpha products b_i [qhat_i]_{t} < q_i t in 64 bits
+    if ((unsigned __int128)alpha * (mq - 1) * (mqp - 1) >= ((unsigned __int128)1 << 64))
+        return fail(ctx, HEFX_EUNSUPPORTED, "alpha * max(q) * max(q, p) reaches 2^64 (64-bit accumulation)");
+    hefx_status st = use_device(ctx);
+    if (st != HEFX_OK) return st;
+    hefx_modup_plan* mp = new hefx_modup_plan();
+    mp->ctx = ctx;
+    mp->log2n = log2n;
+    mp->L = L;
+    mp->K = K;
+    mp->alpha = alpha;
+    mp->dnum = (L + alpha - 1) / alpha;
+    mp->q.assign(q, q + L);
+    mp->p.assign(p, p + K);
+    cudaError_t e = modup_plan_upload(mp);
+    if (e != cudaSuccess) {
+        hefx_modup_plan_destroy(mp);
+        return cuda_fail(ctx, e, "ModUp constants");
+    }
+    *out = mp;
+    return HEFX_OK;
+}
+
+void hefx_modup_plan_destroy(hefx_modup_plan* mp) {
+    if (!mp) return;
+    if (mp->d_const) cudaFree(mp->d_const);
+    delete mp;
+}
+
+uint32_t hefx_modup_plan_dnum(const hefx_modup_plan* mp) { return mp ? mp->dnum : 0; }
+
+hefx_status hefx_mod_up(hefx_ctx* ctx, const hefx_modup_plan* plan, const uint32_t* c, uint32_t* U, size_t batch,
+                        void* stream) {
+    if (!ctx) return HEFX_EINVAL;
+    if (!plan || plan->ctx != ctx) return fail(ctx, HEFX_EINVAL, "plan is null or belongs to another context");
+    if (!c || !U) return fail(ctx, HEFX_EINVAL, "null buffer");
+    if (!aligned16(c) || !aligned16(U)) return fail(ctx, HEFX_EINVAL, "buffers must be 16-byte aligned");
+    const size_t row = ((size_t)1 << plan->log2n) * 4;
+    if (overlaps(U, batch * plan->dnum * (plan->L + plan->K) * row, c, batch * plan->L * row))
+        return fail(ctx, HEFX_EINVAL, "d_U overlaps d_c");
+    hefx_status st = use_device(ctx);
+    if (st != HEFX_OK) return st;
+    if (batch == 0) return HEFX_OK;
+    cudaError_t e = launch_mod_up(plan, c, U, batch, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "hefx_mod_up launch");
+    return HEFX_OK;
+}
+
 hefx_status hefx_basis_convert(hefx_ctx* ctx, const hefx_bconv_plan* plan, const uint32_t* in, uint32_t* out,
                                size_t batch, hefx_path path, void* stream) {
     if (!ctx) return HEFX_EINVAL;

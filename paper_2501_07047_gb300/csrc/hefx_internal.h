@@ -108,6 +108,15 @@ struct hefx_bconv_plan {
     void* d_bat = nullptr;            // BAT digit matrix of step 2 (fp16), see bconv.cu
 };
 
+// ModUp of hybrid key switching (bconv.cu): one plan for every digit of (Q, P, alpha).
+struct hefx_modup_plan {
+    hefx_ctx* ctx = nullptr;
+    uint32_t log2n = 0;
+    uint32_t L = 0, K = 0, alpha = 0, dnum = 0;
+    std::vector<uint32_t> q, p;
+    void* d_const = nullptr;  // dnum BConvConst
+};
+
 namespace hefx {
 
 // Kernel launchers (return a CUDA error code; the host API maps it to hefx_status).
@@ -143,6 +152,10 @@ cudaError_t launch_mod_down(const hefx_bconv_plan* plan, const uint32_t* x, uint
 cudaError_t launch_bconv_cc(const hefx_bconv_plan* plan, const uint32_t* in, uint32_t* out, size_t batch,
                             cudaStream_t stream);
 cudaError_t bconv_plan_upload(hefx_bconv_plan* plan);
+cudaError_t modup_plan_upload(hefx_modup_plan* plan);
+// U[b][j] = ModUp digit j of c[b] ([batch][L][N] -> [batch][dnum][L + K][N], coefficient form)
+cudaError_t launch_mod_up(const hefx_modup_plan* plan, const uint32_t* c, uint32_t* U, size_t batch,
+                          cudaStream_t stream);
 void bconv_plan_free(hefx_bconv_plan* plan);
 
 // Tensor-core path (ntt_tc.cu / bconv_tc.cu).

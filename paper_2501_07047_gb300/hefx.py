@@ -46,6 +46,10 @@ SIGNATURES = {
     "hefx_basis_convert_exact": (_i32, [_vp, _vp, _vp, _vp, _sz, _vp]),
     "hefx_key_inner_product": (_i32, [_vp, _vp, _vp, _vp, _vp, _u32, _sz, _vp]),
     "hefx_mod_down": (_i32, [_vp, _vp, _vp, _vp, _sz, _vp]),
+    "hefx_modup_plan_create": (_i32, [_vp, _u32, _u32p, _u32, _u32p, _u32, _u32, ctypes.POINTER(_vp)]),
+    "hefx_modup_plan_destroy": (None, [_vp]),
+    "hefx_modup_plan_dnum": (_u32, [_vp]),
+    "hefx_mod_up": (_i32, [_vp, _vp, _vp, _vp, _sz, _vp]),
     "hefx_rescale": (_i32, [_vp, _vp, _vp, _vp, _sz, _vp]),
     "hefx_mult_plan_create": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_vp)]),
     "hefx_mult_plan_destroy": (None, [_vp]),
@@ -219,6 +223,25 @@ def hefx_basis_convert_exact(ctx, plan, x, out, batch, stream=None) -> None:
 
 def hefx_mod_down(ctx, plan, x, out, batch, stream=None) -> None:
     _check(ctx, load().hefx_mod_down(ctx, plan, _ptr(x), _ptr(out), batch, _stream(stream)))
+
+
+def hefx_modup_plan_create(ctx: int, log2n: int, q, p, alpha: int) -> int:
+    h = _vp()
+    _check(ctx, load().hefx_modup_plan_create(ctx, log2n, _u32_array(q), len(q), _u32_array(p), len(p), alpha,
+                                             ctypes.byref(h)))
+    return h.value
+
+
+def hefx_modup_plan_destroy(plan: int) -> None:
+    load().hefx_modup_plan_destroy(plan)
+
+
+def hefx_modup_plan_dnum(plan: int) -> int:
+    return int(load().hefx_modup_plan_dnum(plan))
+
+
+def hefx_mod_up(ctx, plan, c, U, batch, stream=None) -> None:
+    _check(ctx, load().hefx_mod_up(ctx, plan, _ptr(c), _ptr(U), batch, _stream(stream)))
 
 
 def hefx_rescale(ctx, params, x, out, batch, stream=None) -> None:

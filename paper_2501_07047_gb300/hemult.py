@@ -43,8 +43,12 @@ class HeMult:
         self.pQr = hefx.hefx_params_create(ctx, logn, self.qs[:-1])
         self.pQP = hefx.hefx_params_create(ctx, logn, self.qs + self.ps)
         qp = self.qs + self.ps
+        # ModUp: one launch for every digit on the CUDA cores ("auto", "cudacore"), or two
+        # conversions per digit through hefx_basis_convert on the requested path
+        self.modup = hefx.hefx_modup_plan_create(ctx, logn, self.qs, self.ps, alpha) \
+            if bconv_path in ("auto", "cudacore") else None
         self.plans = []
-        for lo, hi in self.digits:
+        for lo, hi in ([] if self.modup else self.digits):
             src = self.qs[lo:hi]
             lo_plan = hefx.hefx_bconv_plan_create(ctx, logn, src, self.qs[:lo]) if lo > 0 else None
             hi_plan = hefx.hefx_bconv_plan_create(ctx, logn, src, qp[hi:])
@@ -60,6 +64,8 @@ class HeMult:
         self.cc = torch.empty((2, L, n), dtype=torch.int32, device=dev)
 
     def close(self) -> None:
+        if self.modup:
+            hefx.hefx_modup_plan_destroy(self.modup)
         for lo_plan, hi_plan in self.plans:
             if lo_plan:
                 hefx.hefx_bconv_plan_destroy(lo_plan)
@@ -70,14 +76,14 @@ class HeMult:
 
     def launches(self, rescale: bool = True) -> int:
         """Kernel launches of one run (CUDA-core NTT path)."""
-        bconv = sum(2 if lo else 1 for lo, _ in self.digits)
-        return 1 + 1 + bconv + 1 + 1 + 1 + 1 + 1 + 2 + (3 if rescale else 0)
+        modup = 1 if self.modup else sum(2 if lo else 1 for lo, _ in self.digits)
+        return 1 + 1 + modup + 1 + 1 + 1 + 1 + 1 + 2 + (3 if rescale else 0)
 
     def run(self, a0, a1, b0, b1, evk, out, stream=None, rescale: bool = True) -> None:
         """a*, b*: [L][N] evaluation form over Q; evk: [dnum][2][L+K][N] evaluation form over
         Q u P.  With rescale, out [2][L-1][N] receives (c'_0, c'_1); without, out [2][L][N]
-        receives the relinearised (c_0, c_1) over Q.  Copies (c <- d2, U_j <- c on D_j) are
-        device-to-device on the same stream."""
+        receives the relinearised (c_0, c_1) over Q.  Copies (c <- d2, and U_j <- c on D_j
+        when ModUp runs as per-digit conversions) are device-to-device on the same stream."""
         torch = self.torch
         ctx, s = self.ctx, stream
         d0, d1, d2 = self.d[0], self.d[1], self.d[2]
@@ -86,6 +92,8 @@ class HeMult:
             hefx.hefx_tensor_product(ctx, self.pQ, a0, a1, b0, b1, d0, d1, d2, 1, st)
             self.c.copy_(d2)
             hefx.hefx_ntt_inv(ctx, self.pQ, self.c, 1, self.ntt_path, st)
+            if self.modup:
+                hefx.hefx_mod_up(ctx, self.modup, self.c, self.U, 1, st)
             for j, ((lo, hi), (lo_plan, hi_plan)) in enumerate(zip(self.digits, self.plans)):
                 self.U[j, lo:hi].copy_(self.c[lo:hi])
                 if lo_plan:

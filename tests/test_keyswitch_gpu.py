@@ -43,6 +43,48 @@ def test_mod_down(hx, logn, L, K):
     hefx.hefx_bconv_plan_destroy(plan)
 
 
+@pytest.mark.parametrize("logn,L,K,alpha,batch", [(8, 5, 2, 2, 1), (12, 6, 3, 3, 2), (10, 7, 1, 7, 1),
+                                                    (16, 48, 16, 16, 1), (16, 24, 8, 8, 2)])
+def test_mod_up(hx, logn, L, K, alpha, batch):
+    """One-launch ModUp of every digit (ragged last digit, single digit, batch 2) equals the
+    oracle's per-digit conversions and copies."""
+    hefx, ctx = hx
+    n = 1 << logn
+    qs, ps = inputs.source_primes(L), inputs.special_primes(K)
+    c = np.stack([_res((67, logn, b), 1, qs, n)[0] for b in range(batch)])
+    c[:, :, 0] = np.asarray(qs, dtype=np.uint32)[None, :] - 1  # extremes
+    c[:, :, 1] = 0
+    plan = hefx.hefx_modup_plan_create(ctx, logn, qs, ps, alpha)
+    dnum = hefx.hefx_modup_plan_dnum(plan)
+    assert dnum == len(oks.digit_ranges(L, alpha))
+    dc = dev(c)
+    dU = dev(np.full((batch, dnum, L + K, n), 0xFFFFFFFF, dtype=np.uint32))
+    hefx.hefx_mod_up(ctx, plan, dc, dU, batch)
+    got = host(dU)
+    cols = np.arange(n) if logn <= 12 else np.sort(np.random.default_rng(2).choice(n, 512, replace=False))
+    for b in range(batch):
+        want = oks.modup(c[b][:, cols], qs, ps, alpha)
+        assert np.array_equal(got[b][:, :, cols], want)
+    hefx.hefx_modup_plan_destroy(plan)
+
+
+def test_mod_up_errors(hx):
+    hefx, ctx = hx
+    qs, ps = inputs.source_primes(4), inputs.special_primes(2)
+    with pytest.raises(hefx.HefxError):
+        hefx.hefx_modup_plan_create(ctx, 8, qs, ps, 0)  # alpha outside [1, L]
+    with pytest.raises(hefx.HefxError):
+        hefx.hefx_modup_plan_create(ctx, 8, qs, ps, 5)
+    with pytest.raises(hefx.HefxError):
+        hefx.hefx_modup_plan_create(ctx, 8, qs, list(ps[:1]) + [qs[0]], 2)  # repeated prime
+    plan = hefx.hefx_modup_plan_create(ctx, 8, qs, ps, 2)
+    buf = dev(np.zeros((2 * 6 + 4, 256), dtype=np.uint32))
+    # d_U overlapping d_c
+    assert hefx.raw_status("hefx_mod_up", ctx, plan, buf.data_ptr(), buf.data_ptr() + 1024, 1, 0) == hefx.HEFX_EINVAL
+    assert hefx.raw_status("hefx_mod_up", ctx, 0, buf.data_ptr(), buf.data_ptr(), 1, 0) == hefx.HEFX_EINVAL
+    hefx.hefx_modup_plan_destroy(plan)
+
+
 @pytest.mark.parametrize("logn,L", [(6, 2), (10, 5), (16, 24)])
 def test_rescale(hx, logn, L):
     hefx, ctx = hx
@@ -115,13 +157,15 @@ def _he_mult_case(logn, L, K, alpha, seed, genuine_key):
     return qs, ps, s, evk, ins
 
 
-@pytest.mark.parametrize("logn,L,K,alpha,genuine", [(6, 5, 2, 2, True), (10, 6, 3, 3, True), (8, 4, 4, 4, True),
-                                                    (16, 24, 8, 8, False)])
-def test_he_mult_matches_oracle(hx, logn, L, K, alpha, genuine):
+@pytest.mark.parametrize("logn,L,K,alpha,genuine,bconv", [(6, 5, 2, 2, True, "auto"), (10, 6, 3, 3, True, "auto"),
+                                                           (8, 4, 4, 4, True, "auto"), (16, 24, 8, 8, False, "auto"),
+                                                           (10, 6, 3, 3, True, "tensor")])
+def test_he_mult_matches_oracle(hx, logn, L, K, alpha, genuine, bconv):
+    """bconv "auto": one-launch ModUp; "tensor": per-digit conversions on the tensor path."""
     hefx, ctx = hx
     from paper_2501_07047_gb300.hemult import HeMult
     qs, ps, s, evk, ins = _he_mult_case(logn, L, K, alpha, 64 + logn, genuine)
-    hm = HeMult(ctx, logn, qs, ps, alpha)
+    hm = HeMult(ctx, logn, qs, ps, alpha, bconv_path=bconv)
     n = 1 << logn
     out = dev(np.zeros((2, L - 1, n), dtype=np.uint32))
     dins = [dev(a) for a in ins]
