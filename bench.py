@@ -47,6 +47,65 @@ def peaks():
 
 # ----------------------------------------------------------------------------- clocks
 
+class NvmlSampler:
+    """Samples SM clocks and throttle reasons every 2 ms through NVML (ctypes, read-only
+    queries) while the timed region runs; the GPU is found by its PCI bus id."""
+
+    # clock-event reason bits (nvml.h)
+    REASONS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40}
+
+    def __init__(self, device: int):
+        import ctypes
+        self.ct = ctypes
+        self.nvml = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.nvml.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        import torch
+        pr = torch.cuda.get_device_properties(device)
+        bus = f"{getattr(pr, 'pci_domain_id', 0):08X}:{pr.pci_bus_id:02X}:{pr.pci_device_id:02X}.0".encode()
+        if self.nvml.nvmlDeviceGetHandleByPciBusId_v2(ctypes.c_char_p(bus), ctypes.byref(self.h)) != 0:
+            raise RuntimeError("GPU not found by PCI bus id")
+        self.reason_fn = getattr(self.nvml, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.nvml.nvmlDeviceGetCurrentClocksThrottleReasons
+        mx = ctypes.c_uint()
+        self.max_mhz = float(mx.value) if self.nvml.nvmlDeviceGetMaxClockInfo(self.h, 1, ctypes.byref(mx)) == 0 else None
+        self.samples, self.reasons, self.stop = [], set(), threading.Event()
+
+    def _poll(self):
+        ct = self.ct
+        clk, rs = ct.c_uint(), ct.c_ulonglong()
+        while not self.stop.is_set():
+            if self.nvml.nvmlDeviceGetClockInfo(self.h, 1, ct.byref(clk)) == 0:  # NVML_CLOCK_SM
+                self.samples.append(float(clk.value))
+            if self.reason_fn(self.h, ct.byref(rs)) == 0:
+                self.reasons.update(k for k, bit in self.REASONS.items() if rs.value & bit)
+            time.sleep(0.002)
+
+    def __enter__(self):
+        self.thread = threading.Thread(target=self._poll, daemon=True)
+        self.thread.start()
+        return self
+
+    def __exit__(self, *exc):
+        self.stop.set()
+        self.thread.join(timeout=5)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(self.samples), "sm_max_mhz": self.max_mhz,
+                "reasons": sorted(self.reasons), "samples": len(self.samples), "source": "nvml"}
+
+
+def clock_sampler(device: int):
+    """NVML sampler where the driver's library loads, else nvidia-smi polling."""
+    try:
+        return NvmlSampler(device)
+    except Exception:
+        return ClockSampler(device)
+
+
 class ClockSampler:
     """Samples SM clocks and throttle reasons with nvidia-smi while the timed region runs."""
 
@@ -208,7 +267,7 @@ def run_gpu(args):
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
-        with ClockSampler(local) as clk:
+        with clock_sampler(local) as clk:
             t_wall = time.perf_counter()
             for k in range(args.steps):
                 flush.fill_(k)  # write 256 MiB > L2 between timed steps (outside the events)

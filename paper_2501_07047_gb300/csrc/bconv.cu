@@ -165,8 +165,10 @@ __device__ __forceinline__ void exact_limb(const BConvConst& c, uint32_t i, uint
 
 // LOGN > 0 fixes the ring degree at compile time (the loads of a group then sit at constant
 // offsets from one pointer); LOGN = 0 takes it from log2n.
+// ModUp: 4 resident blocks per SM (its digit-copy stores spill at 48 registers; measured
+// 49.8 vs 51.8 us for three 16 -> 48 digits at N = 2^16); every other mode 5.
 template <int kCoef, int MODE, int LOGN>
-__global__ void __launch_bounds__(256, 5)
+__global__ void __launch_bounds__(256, MODE == BC_MODUP ? 4 : 5)
     bconv_cc_kernel(const BConvConst* __restrict__ gc, const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
                     const uint32_t* __restrict__ xq, uint32_t log2n, uint32_t batch, size_t in_stride,
                     size_t out_stride, size_t out_digit_stride) {
