@@ -466,7 +466,7 @@ def bench_reduction_ablation(ctx, args):
     y = d0.clone()
     z = torch.empty_like(d0)
     zref = None
-    for red in ("montgomery", "barrett"):
+    for red in ("montgomery", "barrett", "bat_lazy"):  # bat_lazy: tensor-core MMA of the high bytes
         hefx.hefx_params_set_reduction(ctx, params, "shoup", red)
         hefx.hefx_vec_mod_mul(ctx, params, d0, y, z, BATCH, s)
         torch.cuda.synchronize()

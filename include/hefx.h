@@ -94,7 +94,12 @@ hefx_status hefx_params_set_auto_path(hefx_params* params, hefx_path path);
  * Modular reductions of the paper's ablation (Sec. V-F, "Impact of Modular Reduction
  * Algorithm": Barrett, Montgomery, Shoup).
  */
-typedef enum { HEFX_RED_SHOUP = 0, HEFX_RED_MONTGOMERY = 1, HEFX_RED_BARRETT = 2 } hefx_reduction;
+typedef enum {
+    HEFX_RED_SHOUP = 0,
+    HEFX_RED_MONTGOMERY = 1,
+    HEFX_RED_BARRETT = 2,
+    HEFX_RED_BAT_LAZY = 3 /* VecModMul only: BAT lazy reduction on the tensor cores */
+} hefx_reduction;
 
 /*
  * Selects the reduction of the CUDA-core NTT's twiddle products (ntt_red; default Shoup) and
@@ -105,6 +110,10 @@ typedef enum { HEFX_RED_SHOUP = 0, HEFX_RED_MONTGOMERY = 1, HEFX_RED_BARRETT = 2
  * N = 2^16 only: other sizes, hefx_poly_mul and the tensor path then return EUNSUPPORTED;
  * batch plans always use Shoup.  vec_red = HEFX_RED_SHOUP is EINVAL (Shoup needs a
  * precomputed companion of one operand; VecModMul's operands are both runtime values).
+ * vec_red = HEFX_RED_BAT_LAZY (the paper's appendix "BAT for Modular Reduction", part of the
+ * Sec. V-F ablation) reduces the 64-bit product's high four bytes with a byte-matrix product
+ * on the tensor cores (one tcgen05 MMA per 128 elements) and finishes with one Barrett
+ * reduction; it needs log2n >= 9 (EUNSUPPORTED otherwise) and is used by hefx_vec_mod_mul.
  * Synchronous; not thread-safe with concurrent calls that use the same params.
  */
 hefx_status hefx_params_set_reduction(hefx_params* params, hefx_reduction ntt_red, hefx_reduction vec_red);

@@ -136,6 +136,7 @@ cudaError_t launch_vec_mod_mul(const hefx_params* p, const uint32_t* x, const ui
                                cudaStream_t s) {
     const size_t total4 = rows * p->n / 4;  // N >= 8, so rows of N words split into whole uint4
     if (!total4) return cudaSuccess;
+    if (p->red_vec == HEFX_RED_BAT_LAZY) return launch_vec_mod_mul_bat(p, x, y, z, rows, s);
     if (p->red_vec == HEFX_RED_BARRETT)
         vec_mod_mul_kernel<true><<<grid_for(total4), 256, 0, s>>>(p->d_lc, p->nlimbs, p->n, total4, (const uint4*)x,
                                                                   (const uint4*)y, (uint4*)z);

@@ -754,8 +754,10 @@ hefx_status hefx_params_set_reduction(hefx_params* p, hefx_reduction ntt_red, he
     if (!p) return HEFX_EINVAL;
     if (ntt_red < HEFX_RED_SHOUP || ntt_red > HEFX_RED_BARRETT)
         return fail(p->ctx, HEFX_EINVAL, "unknown NTT reduction %d", (int)ntt_red);
-    if (vec_red != HEFX_RED_MONTGOMERY && vec_red != HEFX_RED_BARRETT)
-        return fail(p->ctx, HEFX_EINVAL, "VecModMul reduction must be Montgomery or Barrett");
+    if (vec_red != HEFX_RED_MONTGOMERY && vec_red != HEFX_RED_BARRETT && vec_red != HEFX_RED_BAT_LAZY)
+        return fail(p->ctx, HEFX_EINVAL, "VecModMul reduction must be Montgomery, Barrett or BAT lazy");
+    if (vec_red == HEFX_RED_BAT_LAZY && p->log2n < 9)
+        return fail(p->ctx, HEFX_EUNSUPPORTED, "BAT lazy reduction needs log2n >= 9");
     hefx_status st = use_device(p->ctx);
     if (st != HEFX_OK) return st;
     if (ntt_red == HEFX_RED_MONTGOMERY && !p->d_tw_fwd_mont) {

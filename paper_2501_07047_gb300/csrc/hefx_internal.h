@@ -127,6 +127,9 @@ cudaError_t launch_ntt_cc(const hefx_params* p, NttMode mode, const uint32_t* in
 // Elementwise products of the HE-Mult request (elementwise.cu).
 cudaError_t launch_vec_mod_mul(const hefx_params* p, const uint32_t* x, const uint32_t* y, uint32_t* z, size_t rows,
                                cudaStream_t s);
+// VecModMul with the BAT lazy reduction on the tensor cores (bat_lazy.cu); log2n >= 9.
+cudaError_t launch_vec_mod_mul_bat(const hefx_params* p, const uint32_t* x, const uint32_t* y, uint32_t* z,
+                                   size_t rows, cudaStream_t s);
 cudaError_t launch_tensor_product(const hefx_params* p, const uint32_t* a0, const uint32_t* a1, const uint32_t* b0,
                                   const uint32_t* b1, uint32_t* d0, uint32_t* d1, uint32_t* d2, size_t rows,
                                   cudaStream_t s);

@@ -18,7 +18,7 @@ STATUS_NAMES = ["HEFX_OK", "HEFX_EINVAL", "HEFX_EUNSUPPORTED", "HEFX_ENOMEM", "H
                 "HEFX_ETIMEOUT"]
 HEFX_PATH_AUTO, HEFX_PATH_CUDACORE, HEFX_PATH_TENSOR = 0, 1, 2
 PATHS = {"auto": HEFX_PATH_AUTO, "cudacore": HEFX_PATH_CUDACORE, "tensor": HEFX_PATH_TENSOR}
-REDUCTIONS = {"shoup": 0, "montgomery": 1, "barrett": 2}
+REDUCTIONS = {"shoup": 0, "montgomery": 1, "barrett": 2, "bat_lazy": 3}
 
 # Every symbol include/hefx.h declares, with its ctypes signature.
 _vp, _u32, _sz, _i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_size_t, ctypes.c_int
