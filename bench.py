@@ -375,9 +375,10 @@ def run_gpu(args):
     del data, data0, flush
     torch.cuda.empty_cache()
     if not args.no_extras and world == 1:
-        line["extra"] = {"bconv_config3": bench_bconv(ctx, args), "batch_config4": bench_batch(ctx, args),
-                         "he_mult": bench_he_mult(ctx, args),
-                         "reduction_ablation": bench_reduction_ablation(ctx, args)}
+        runs = {"bconv_config3": bench_bconv, "batch_config4": bench_batch, "he_mult": bench_he_mult,
+                "reduction_ablation": bench_reduction_ablation}
+        chosen = [k for k in runs if args.extras is None or k in args.extras.split(",")]
+        line["extra"] = {k: runs[k](ctx, args) for k in chosen}
         if args.serve:
             line["extra"]["serving_config5"] = bench_serving(ctx, args)
     hefx.hefx_destroy(ctx)
@@ -640,6 +641,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the BConv and batch measurements")
+    ap.add_argument("--extras", default=None,
+                    help="comma-separated subset of bconv_config3,batch_config4,he_mult,reduction_ablation")
     ap.add_argument("--serve", action="store_true", help="also run the serving arrival-rate sweep")
     args = ap.parse_args()
     if args.impl == "reference":
