@@ -528,7 +528,8 @@ def bench_he_mult(ctx, args):
         graph_ms = _events_time(g.replay, steps, flush, s)
         res[f"L{L}_dnum{dnum}"] = {"he_mult_us": round(mult_ms * 1e3, 1), "he_mult_graph_us": round(graph_ms * 1e3, 1),
                                    "rescale_us": round(resc_ms * 1e3, 1), "K": alpha,
-                                   "launches_he_mult": hm.launches(rescale=False), "launches_rescale": 3}
+                                   "launches_he_mult": hm.launches(rescale=False),
+                                   "launches_rescale": hm.launches(rescale=True) - hm.launches(rescale=False)}
         del g
         hm.close()
         del ins, evk, cq, out, cw

@@ -283,6 +283,20 @@ hefx_status hefx_rescale(hefx_ctx* ctx, const hefx_params* params, const uint32_
                          size_t batch, void* stream);
 
 /*
+ * NTT(Rescale(x)): the rescaled polynomial in evaluation form over q_0 .. q_{L-2}, from x in
+ * coefficient form over the params' L limbs -- hefx_rescale followed by the forward NTT of
+ * its L - 1 limbs, with identical results.  For N >= 2^14 one launch: the transform's first
+ * (cross-CTA) pass reads limb i and the last limb of the same polynomial and rescales on the
+ * way in, so the rescaled polynomial never goes to memory; the limb tables of q_0 .. q_{L-2}
+ * are the params' own.  Smaller N run the two steps (d_out is the workspace).  Layouts: d_x
+ * [batch][L][N], d_out [batch][L - 1][N]; d_out must not overlap d_x.  Errors: as for
+ * hefx_ntt_fwd; EINVAL for L < 2 or overlap; EUNSUPPORTED when the params' NTT reduction is
+ * not the default (Shoup).
+ */
+hefx_status hefx_rescale_ntt(hefx_ctx* ctx, const hefx_params* params, const uint32_t* d_x, uint32_t* d_out,
+                             size_t batch, void* stream);
+
+/*
  * Tensor product of two ciphertexts (a0, a1), (b0, b1) in evaluation (NTT) form, the first
  * step of HE-Mult (Sec. III; App. A: HE-Mult is built from NTT, INTT, BConv, VecModMul and
  * VecModAdd): d0 = a0 o b0, d1 = a0 o b1 + a1 o b0, d2 = a1 o b1 mod q, elementwise over

@@ -534,6 +534,24 @@ hefx_status hefx_rescale(hefx_ctx* ctx, const hefx_params* p, const uint32_t* x,
     return HEFX_OK;
 }
 
+hefx_status hefx_rescale_ntt(hefx_ctx* ctx, const hefx_params* p, const uint32_t* x, uint32_t* out, size_t batch,
+                             void* stream) {
+    hefx_status st;
+    if ((st = check_ntt_args(ctx, p, x, "d_x")) != HEFX_OK) return st;
+    if ((st = check_ntt_args(ctx, p, out, "d_out")) != HEFX_OK) return st;
+    if (p->nlimbs < 2) return fail(ctx, HEFX_EINVAL, "rescale needs at least 2 limbs");
+    if (p->red_ntt != HEFX_RED_SHOUP)
+        return fail(ctx, HEFX_EUNSUPPORTED, "hefx_rescale_ntt uses the default (Shoup) NTT reduction only");
+    const size_t row = (size_t)p->n * 4;
+    if (overlaps(out, batch * (p->nlimbs - 1) * row, x, batch * p->nlimbs * row))
+        return fail(ctx, HEFX_EINVAL, "d_out overlaps d_x");
+    if (batch == 0) return HEFX_OK;
+    if ((st = use_device(ctx)) != HEFX_OK) return st;
+    cudaError_t e = launch_ntt_cc_rescale(p, x, out, batch, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "hefx_rescale_ntt launch");
+    return HEFX_OK;
+}
+
 hefx_status hefx_mod_down(hefx_ctx* ctx, const hefx_bconv_plan* plan, const uint32_t* x, uint32_t* out, size_t batch,
                           void* stream) {
     if (!ctx) return HEFX_EINVAL;

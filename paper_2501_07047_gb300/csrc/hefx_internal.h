@@ -120,7 +120,9 @@ struct hefx_modup_plan {
 namespace hefx {
 
 // Kernel launchers (return a CUDA error code; the host API maps it to hefx_status).
-enum NttMode { MODE_FWD = 0, MODE_INV = 1, MODE_FWD_HAD_INV = 2, MODE_HAD_INV = 3 };
+// MODE_RS_FWD: NTT(Rescale(x)): the forward transform of q_0..q_{L-2} whose first pass reads
+// limb i and the last limb of the same coefficient-form polynomial and rescales on the way in.
+enum NttMode { MODE_FWD = 0, MODE_INV = 1, MODE_FWD_HAD_INV = 2, MODE_HAD_INV = 3, MODE_RS_FWD = 4 };
 
 cudaError_t launch_ntt_cc(const hefx_params* p, NttMode mode, const uint32_t* in, const uint32_t* had, uint32_t* out,
                           size_t rows, cudaStream_t stream);
@@ -137,6 +139,11 @@ cudaError_t launch_tensor_product(const hefx_params* p, const uint32_t* a0, cons
 // Sets the kernel attributes of (N, mode) ahead of time (no launch), e.g. before a capture.
 cudaError_t prepare_ntt_cc(const hefx_params* p, NttMode mode);
 // Same kernels over an explicit list of rows (device array of RowDesc), persistent grid.
+// out[b] (evaluation form over q_0..q_{L-2}) = NTT(Rescale(in[b])), in [batch][L][N] coefficient
+// form over the params' L limbs: one fused launch where built (N >= 2^14, contiguous),
+// else the rescale kernel then the forward transform.
+cudaError_t launch_ntt_cc_rescale(const hefx_params* p, const uint32_t* in, uint32_t* out, size_t batch,
+                                  cudaStream_t stream);
 cudaError_t launch_ntt_cc_rows(const hefx_params* p, NttMode mode, const RowDesc* d_rows, size_t nrows,
                                cudaStream_t stream);
 

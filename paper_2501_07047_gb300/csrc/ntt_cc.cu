@@ -40,8 +40,42 @@ cudaError_t launch_ntt_cc(const hefx_params* p, NttMode mode, const uint32_t* in
     a.desc = nullptr;
     a.rows = (uint32_t)rows;
     a.L = p->nlimbs;
+    a.in_rows = 0;
     if (rows == 0) return cudaSuccess;
     return launch_dispatch(p, mode, a, rows, stream);
+}
+
+cudaError_t launch_ntt_cc_rescale(const hefx_params* p, const uint32_t* in, uint32_t* out, size_t batch,
+                                  cudaStream_t stream) {
+    const uint32_t L = p->nlimbs;
+    const size_t rows = batch * (L - 1);
+    if (rows == 0) return cudaSuccess;
+    cc::KArgs a;
+    memset(&a.tmap_in, 0, sizeof a.tmap_in);
+    memset(&a.tmap_out, 0, sizeof a.tmap_out);
+    a.err = p->d_err_cc;
+    if (p->log2n >= 13) {
+        cudaError_t e = encode_input_map(p, out, rows, &a.tmap_out);
+        if (e != cudaSuccess) return e;
+    }
+    a.in = in;
+    a.had = nullptr;
+    a.out = out;
+    a.tw_f = p->d_tw_fwd;  // limbs 0 .. L-2 of the full set: the tables of q_0 .. q_{L-2}
+    a.tw_i = p->d_tw_inv;
+    a.lc = p->d_lc;        // rs_inv: q_{L-1}^-1 mod q_i
+    a.desc = nullptr;
+    a.rows = (uint32_t)rows;
+    a.L = L - 1;
+    a.in_rows = L;
+    cudaError_t e = launch_dispatch(p, MODE_RS_FWD, a, rows, stream);
+    if (e != cudaErrorNotSupported) return e;
+    // not fused at this N: rescale into out, then the forward transform of its L - 1 limbs
+    e = launch_rescale(p, in, out, batch, stream);
+    if (e != cudaSuccess) return e;
+    a.in = out;
+    a.in_rows = 0;
+    return launch_dispatch(p, MODE_FWD, a, rows, stream);
 }
 
 cudaError_t prepare_ntt_cc(const hefx_params* p, NttMode mode) {
@@ -67,6 +101,7 @@ cudaError_t launch_ntt_cc_rows(const hefx_params* p, NttMode mode, const RowDesc
     a.desc = d_rows;
     a.rows = (uint32_t)nrows;
     a.L = p->nlimbs;
+    a.in_rows = 0;
     if (nrows == 0) return cudaSuccess;
     return launch_dispatch(p, mode, a, nrows, stream);
 }

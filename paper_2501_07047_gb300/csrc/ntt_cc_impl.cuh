@@ -114,6 +114,7 @@ struct KArgs {
     const RowDesc* desc;  // per-row pointers and limb (batched jobs), or null: [rows][N] layout
     uint32_t rows;
     uint32_t L;
+    uint32_t in_rows;  // MODE_RS_FWD: input rows per polynomial (the output has L = in_rows - 1)
 };
 
 // Row r's input / Hadamard operand / output and limb, from the descriptor list when there
@@ -517,7 +518,13 @@ __device__ __forceinline__ void inv_big(uint32_t* sm, const Seg& sg, const KArgs
 // the radix-P step and stores output t into CTA t's shared memory.  Ends with a cluster
 // barrier (outputs visible; every global read of the row done before any CTA writes it,
 // so in-place transforms are safe).
-template <int LOGN, int F>
+// x_i -> (x_i - [x_{L-1}]_{q_i}) q_{L-1}^-1 mod q_i (Rescale by the set's last prime; canonical).
+__device__ __forceinline__ uint32_t rescale_one(uint32_t x, uint32_t last_raw, const LimbConst& c) {
+    const uint32_t last = csub(mul_shoup_lazy(last_raw, 1u, c.one_sh, c.q), c.q);
+    return csub(mul_shoup_lazy(x + c.q - last, c.rs_inv, c.rs_inv_sh, c.q), c.q);
+}
+
+template <int LOGN, int F, bool RS = false>
 __device__ __forceinline__ void fwd_cross_pass(uint32_t* sm, const Seg& sg, const KArgs& a) {
     using C = Cfg<LOGN>;
     constexpr int N = 1 << LOGN, P = C::P, share = C::m / P, ITERS = share / (4 * C::threads);
@@ -529,11 +536,25 @@ __device__ __forceinline__ void fwd_cross_pass(uint32_t* sm, const Seg& sg, cons
     const LimbConst& lc = a.lc[limb];
     const uint2* tw = a.tw_f + (size_t)limb * N;
     const uint32_t* rin = row_in<N, F>(a, sg.row0);
+    const uint32_t* rlast = nullptr;
+    if constexpr (RS) {  // output row (b, limb) of [B][L]: input rows (b, limb) and (b, in_rows - 1)
+        const size_t b = sg.row0 / a.L;
+        rin = a.in + (b * a.in_rows + limb) * (size_t)N;
+        rlast = a.in + (b * a.in_rows + a.in_rows - 1) * (size_t)N;
+    }
     for (int it = 0; it < ITERS; ++it) {
         const int j = (int)sg.part * share + (it * C::threads + (int)threadIdx.x) * 4;
         uint4 v[P];
 #pragma unroll
         for (int t = 0; t < P; ++t) v[t] = __ldg(reinterpret_cast<const uint4*>(rin + j + t * C::m));
+        if constexpr (RS) {
+#pragma unroll
+            for (int t = 0; t < P; ++t) {
+                const uint4 w = __ldg(reinterpret_cast<const uint4*>(rlast + j + t * C::m));
+                v[t] = make_uint4(rescale_one(v[t].x, w.x, lc), rescale_one(v[t].y, w.y, lc),
+                                  rescale_one(v[t].z, w.z, lc), rescale_one(v[t].w, w.w, lc));
+            }
+        }
         uint32_t x[4][P];
 #pragma unroll
         for (int t = 0; t < P; ++t) {
@@ -602,7 +623,7 @@ __host__ __device__ constexpr bool tma_input() {
 // reduces into the swizzled buffer, one thread stores it as 256-line boxes).
 template <int LOGN, int MODE, int F>
 __host__ __device__ constexpr bool tma_output() {
-    return MODE == MODE_FWD && (F & 1) == 0 && LOGN >= 13;
+    return (MODE == MODE_FWD || MODE == MODE_RS_FWD) && (F & 1) == 0 && LOGN >= 13;
 }
 template <int LOGN, int MODE, int F>
 __host__ __device__ constexpr bool uses_tma() {
@@ -691,9 +712,10 @@ __device__ __forceinline__ void run_task(uint32_t* sm, const Seg& sg, const KArg
     constexpr int S_FIRST = C::logP;              // first stage run inside the CTA
     constexpr int S_SMALL = LOGN - RS;            // first stage of the smallest-stride pass
 
-    if constexpr (MODE == MODE_FWD) {
+    if constexpr (MODE == MODE_FWD || MODE == MODE_RS_FWD) {
         constexpr bool TMA = tma_output<LOGN, MODE, F>();
-        if constexpr (C::split) fwd_cross_pass<LOGN, F>(sm, sg, a);
+        static_assert(MODE == MODE_FWD || C::split, "the rescaling load is the cross-CTA pass");
+        if constexpr (C::split) fwd_cross_pass<LOGN, F, MODE == MODE_RS_FWD>(sm, sg, a);
         if constexpr (C::nrest == 0) {
             static_assert(!TMA, "TMA output needs the smallest-stride pass to follow a shared-memory pass");
             fwd_pass<RS, LOGN, S_FIRST, C::split ? SRC_SMEM : SRC_GLOBAL, DST_GLOBAL_REDUCE, F>(sm, sg, a);
@@ -814,6 +836,9 @@ cudaError_t launch_mode_d(NttMode mode, const KArgs& a, size_t rows, cudaStream_
         case MODE_FWD: return launch_one<LOGN, MODE_FWD, F>(a, rows, s);
         case MODE_INV: return launch_one<LOGN, MODE_INV, F>(a, rows, s);
         case MODE_FWD_HAD_INV: return launch_one<LOGN, MODE_FWD_HAD_INV, F>(a, rows, s);
+        case MODE_RS_FWD:
+            if constexpr ((F & 1) == 0 && Cfg<LOGN>::split) return launch_one<LOGN, MODE_RS_FWD, F>(a, rows, s);
+            else return cudaErrorNotSupported;
         default: return launch_one<LOGN, MODE_HAD_INV, F>(a, rows, s);
     }
 }

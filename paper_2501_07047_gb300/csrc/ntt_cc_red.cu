@@ -47,6 +47,7 @@ cudaError_t launch_ntt_cc_red(const hefx_params* p, NttMode mode, uint32_t* data
     if (!a.tw_f || !a.tw_i) return cudaErrorNotSupported;
     a.lc = p->d_lc;
     a.desc = nullptr;
+    a.in_rows = 0;
     a.rows = (uint32_t)rows;
     a.L = p->nlimbs;
     const bool lazy = p->max_prime < (1u << 28);

@@ -51,6 +51,7 @@ SIGNATURES = {
     "hefx_modup_plan_dnum": (_u32, [_vp]),
     "hefx_mod_up": (_i32, [_vp, _vp, _vp, _vp, _sz, _vp]),
     "hefx_rescale": (_i32, [_vp, _vp, _vp, _vp, _sz, _vp]),
+    "hefx_rescale_ntt": (_i32, [_vp, _vp, _vp, _vp, _sz, _vp]),
     "hefx_mult_plan_create": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_vp)]),
     "hefx_mult_plan_destroy": (None, [_vp]),
     "hefx_mult_front": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
@@ -247,6 +248,10 @@ def hefx_mod_up(ctx, plan, c, U, batch, stream=None) -> None:
 def hefx_rescale(ctx, params, x, out, batch, stream=None) -> None:
     _check(ctx, load().hefx_rescale(ctx, params, _ptr(x), _ptr(out), batch, _stream(stream)))
 
+
+
+def hefx_rescale_ntt(ctx, params, x, out, batch, stream=None) -> None:
+    _check(ctx, load().hefx_rescale_ntt(ctx, params, _ptr(x), _ptr(out), batch, _stream(stream)))
 
 def hefx_mult_plan_create(ctx, pq, pp, bc, kq0, kq1, kp0, kp1) -> int:
     h = _vp()

@@ -77,7 +77,7 @@ class HeMult:
     def launches(self, rescale: bool = True) -> int:
         """Kernel launches of one run (CUDA-core NTT path)."""
         modup = 1 if self.modup else sum(2 if lo else 1 for lo, _ in self.digits)
-        return 1 + 1 + modup + 1 + 1 + 1 + 1 + 1 + 2 + (3 if rescale else 0)
+        return 1 + 1 + modup + 1 + 1 + 1 + 1 + 1 + 1 + (2 if rescale else 0)
 
     def run(self, a0, a1, b0, b1, evk, out, stream=None, rescale: bool = True) -> None:
         """a*, b*: [L][N] evaluation form over Q; evk: [dnum][2][L+K][N] evaluation form over
@@ -105,19 +105,23 @@ class HeMult:
             hefx.hefx_mod_down(ctx, self.plan_pq, self.acc, self.ks, 2, st)
             hefx.hefx_ntt_fwd(ctx, self.pQ, self.ks, 2, self.ntt_path, st)
             dst = self.cc if rescale else out
-            hefx.hefx_vec_mod_add(ctx, self.pQ, d0, self.ks[0], dst[0], 1, st)
-            hefx.hefx_vec_mod_add(ctx, self.pQ, d1, self.ks[1], dst[1], 1, st)
+            # (c_0, c_1) = (d_0, d_1) + (ks_0, ks_1): both halves are contiguous, one launch
+            hefx.hefx_vec_mod_add(ctx, self.pQ, self.d[0:2], self.ks, dst, 2, st)
             if rescale:
                 self.rescale(self.cc, out, st)
 
     def rescale(self, c, out, stream=None) -> None:
         """c: [2][L][N] evaluation form over Q (overwritten) -> out [2][L-1][N] evaluation form
-        over q_0 .. q_{L-2}: NTT(Rescale(INTT(c)))."""
+        over q_0 .. q_{L-2}: NTT(Rescale(INTT(c))); on the CUDA-core path the rescale runs on
+        the forward transform's input load (two launches)."""
         st = self.torch.cuda.current_stream() if stream is None else stream
         with self.torch.cuda.stream(st):
             hefx.hefx_ntt_inv(self.ctx, self.pQ, c, 2, self.ntt_path, st)
-            hefx.hefx_rescale(self.ctx, self.pQ, c, out, 2, st)
-            hefx.hefx_ntt_fwd(self.ctx, self.pQr, out, 2, self.ntt_path, st)
+            if self.ntt_path == "cudacore":
+                hefx.hefx_rescale_ntt(self.ctx, self.pQ, c, out, 2, st)
+            else:
+                hefx.hefx_rescale(self.ctx, self.pQ, c, out, 2, st)
+                hefx.hefx_ntt_fwd(self.ctx, self.pQr, out, 2, self.ntt_path, st)
 
     def capture(self, a0, a1, b0, b1, evk, out, rescale: bool = True):
         """Records one run on fixed buffers as a CUDA graph (one graph launch replays all the

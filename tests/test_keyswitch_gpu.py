@@ -102,6 +102,25 @@ def test_rescale(hx, logn, L):
     hefx.hefx_params_destroy(p)
 
 
+@pytest.mark.parametrize("logn,L,batch", [(10, 5, 2), (14, 6, 2), (15, 9, 1), (16, 24, 2), (16, 48, 2), (17, 4, 1)])
+def test_rescale_ntt(hx, logn, L, batch):
+    """NTT(Rescale(x)) over q_0..q_{L-2}: fused on the forward transform's load for N >= 2^14,
+    two steps below; equal to the oracle's rescale followed by its forward NTT."""
+    hefx, ctx = hx
+    n = 1 << logn
+    qs = inputs.source_primes(L) if logn <= 16 else inputs.ntt_primes(L, 28, 2 << logn)
+    p = hefx.hefx_params_create(ctx, logn, qs)
+    x = np.stack([_res((68, logn, b), 1, qs, n)[0] for b in range(batch)])
+    x[:, :, 0] = np.asarray(qs, dtype=np.uint32)[None, :] - 1  # extremes, last limb included
+    x[:, :, 1] = 0
+    dx, dout = dev(x), dev(np.zeros((batch, L - 1, n), dtype=np.uint32))
+    hefx.hefx_rescale_ntt(ctx, p, dx, dout, batch)
+    want = oracle.ntt_batch(oracle.rescale(x, qs), list(qs[:-1]))
+    assert np.array_equal(host(dout), want)
+    assert np.array_equal(host(dx), x)  # input untouched
+    hefx.hefx_params_destroy(p)
+
+
 @pytest.mark.parametrize("logn,nl,dnum,batch", [(8, 5, 3, 1), (12, 10, 1, 2), (16, 32, 3, 1)])
 def test_key_inner_product_and_add(hx, logn, nl, dnum, batch):
     hefx, ctx = hx
