@@ -146,9 +146,18 @@ def test_keyswitch_errors(hx):
     hefx, ctx = hx
     q1 = inputs.source_primes(1)
     p1 = hefx.hefx_params_create(ctx, 8, q1)
-    buf = dev(np.zeros((4, 256), dtype=np.uint32))
+    buf = dev(np.zeros((8, 256), dtype=np.uint32))  # every range named below lies inside it
     assert hefx.raw_status("hefx_rescale", ctx, p1, buf.data_ptr(), buf.data_ptr(), 1, 0) == hefx.HEFX_EINVAL
+    assert hefx.raw_status("hefx_rescale_ntt", ctx, p1, buf.data_ptr(), buf.data_ptr() + 2048, 1, 0) \
+        == hefx.HEFX_EINVAL  # one limb: nothing to rescale
     p3 = hefx.hefx_params_create(ctx, 8, inputs.source_primes(3))
+    # rescaled output overlapping the input
+    assert hefx.raw_status("hefx_rescale_ntt", ctx, p3, buf.data_ptr(), buf.data_ptr() + 1024, 1, 0) \
+        == hefx.HEFX_EINVAL
+    hefx.hefx_params_set_reduction(ctx, p3, "barrett", "montgomery")
+    assert hefx.raw_status("hefx_rescale_ntt", ctx, p3, buf.data_ptr(), buf.data_ptr() + 3072, 1, 0) \
+        == hefx.HEFX_EUNSUPPORTED
+    hefx.hefx_params_set_reduction(ctx, p3, "shoup", "montgomery")
     assert hefx.raw_status("hefx_key_inner_product", ctx, p3, buf.data_ptr(), buf.data_ptr(), buf.data_ptr(), 0, 1,
                            0) == hefx.HEFX_EINVAL
     plan = hefx.hefx_bconv_plan_create(ctx, 8, inputs.special_primes(1), inputs.source_primes(2))
