@@ -35,6 +35,10 @@
 #include "modarith.cuh"
 #include "tc_common.cuh"
 
+#ifndef HEFX_TC2_PDL
+#define HEFX_TC2_PDL 1  // programmatic dependent launch of the digit GEMMs
+#endif
+
 namespace hefx {
 namespace tc2 {
 
@@ -159,6 +163,10 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (cs > 1) cluster_sync_all();  // peers' barriers are initialised before any multicast
     tc::tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    // Programmatic dependent launch: the set-up above touches only shared memory, TMEM and
+    // the kernel's parameters; every global access below waits for the preceding kernel of the
+    // stream to finish (a no-op when the launch did not allow the overlap).
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 
     if (warp == 0) {
         if (lane == 0) {  // ---- TMA producer
@@ -363,6 +371,57 @@ __global__ void __launch_bounds__(256) digitize_t_kernel(const uint32_t* __restr
     }
 }
 
+// The same transposed digit split on 64 x 64 tiles (R, C multiples of 64): each thread moves
+// four 16-byte row pieces (16 KiB of loads per block), and the next tile's loads are issued
+// before this tile's stores (persistent blocks).  Column c of the tile is 64 consecutive
+// A-operand positions: one warp writes it as one 512-byte store, each lane the digits of two
+// adjacent rows.  The odd row stride (65 words) limits the column reads to two-way conflicts.
+__device__ __forceinline__ void load_tile64(const uint32_t* __restrict__ in, uint32_t R, uint32_t C, size_t tiles_per,
+                                            size_t t, uint4 (&v)[4]) {
+    const size_t m = t / tiles_per, w = t % tiles_per;
+    const uint32_t r0 = (uint32_t)(w / (C / 64)) * 64, c0 = (uint32_t)(w % (C / 64)) * 64;
+    const uint32_t* src = in + m * R * C;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {  // piece p = threadIdx + 256 k: row p / 16, columns 4 (p % 16) ..
+        const uint32_t pc = threadIdx.x + 256u * k, r = pc >> 4, c = (pc & 15u) * 4;
+        v[k] = __ldg(reinterpret_cast<const uint4*>(src + (size_t)(r0 + r) * C + c0 + c));
+    }
+}
+
+__global__ void __launch_bounds__(256) digitize_t64_kernel(const uint32_t* __restrict__ in, uint16_t* __restrict__ dig,
+                                                           uint32_t R, uint32_t C, size_t mats) {
+    __shared__ uint32_t tile[64][65];
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const size_t tiles_per = (size_t)(R / 64) * (C / 64), total = mats * tiles_per;
+    size_t t = blockIdx.x;
+    uint4 v[4];
+    if (t < total) load_tile64(in, R, C, tiles_per, t, v);
+    for (; t < total; t += gridDim.x) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t pc = threadIdx.x + 256u * k, r = pc >> 4, c = (pc & 15u) * 4;
+            tile[r][c] = v[k].x;
+            tile[r][c + 1] = v[k].y;
+            tile[r][c + 2] = v[k].z;
+            tile[r][c + 3] = v[k].w;
+        }
+        __syncthreads();
+        if (t + gridDim.x < total) load_tile64(in, R, C, tiles_per, t + gridDim.x, v);  // in flight during the stores
+        const size_t m = t / tiles_per, w = t % tiles_per;
+        const uint32_t r0 = (uint32_t)(w / (C / 64)) * 64, c0 = (uint32_t)(w % (C / 64)) * 64;
+        uint16_t* dst = dig + m * R * C * 4;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const uint32_t c = warp + 8 * k;  // this warp's column of the tile
+            const uint2 lo = tc::split_digits4(tile[2 * lane][c]), hi = tc::split_digits4(tile[2 * lane + 1][c]);
+            // A row c0 + c, K = 4 (r0 + 2 lane) .. + 7
+            *reinterpret_cast<uint4*>(dst + (size_t)(c0 + c) * (4 * R) + 4 * (r0 + 2 * lane)) =
+                make_uint4(lo.x, lo.y, hi.x, hi.y);
+        }
+        __syncthreads();
+    }
+}
+
 uint16_t half_bits_small(uint32_t d) {
     if (d == 0) return 0;
     int e = 31 - __builtin_clz(d);
@@ -528,7 +587,7 @@ cudaError_t launch_gemm(const CUtensorMap& amap, const CUtensorMap& bmap, const 
         attr = true;
     }
     cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute at[1];
+    cudaLaunchAttribute at[2];
     const uint32_t items = g.L * g.batch * (g.DN / BM) / g.cs;
     uint32_t clusters = items;
     {
@@ -560,8 +619,11 @@ cudaError_t launch_gemm(const CUtensorMap& amap, const CUtensorMap& bmap, const 
     at[0].val.clusterDim.x = g.cs;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
+    // the set-up of this GEMM may overlap the tail of the stream's preceding kernel
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[1].val.programmaticStreamSerializationAllowed = HEFX_TC2_PDL;
     cfg.attrs = at;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     return cudaLaunchKernelEx(&cfg, kern, amap, bmap, g);
 }
 
@@ -611,7 +673,15 @@ cudaError_t digitize(const hefx_params* p, const uint32_t* in, uint16_t* dig, bo
     const size_t mats = batch * p->nlimbs;
     const size_t work = mats * p->n / 4;
     const unsigned grid = (unsigned)std::min<size_t>((work + 255) / 256, (size_t)1 << 20);
-    if (trans) {
+    if (trans && t->R % 64 == 0 && t->C % 64 == 0) {
+        const size_t tiles = mats * (t->R / 64) * (t->C / 64);
+        int dev = 0, sms = 148;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        // persistent: 8 blocks of 256 threads per SM (16.6 KiB of shared memory each)
+        tc2::digitize_t64_kernel<<<(unsigned)std::min<size_t>(tiles, (size_t)sms * 8), 256, 0, s>>>(in, dig, t->R,
+                                                                                                   t->C, mats);
+    } else if (trans) {
         const size_t tiles = mats * (t->R / 32) * (t->C / 32);
         tc2::digitize_t_kernel<<<(unsigned)std::min<size_t>(tiles, (size_t)1 << 20), 256, 0, s>>>(in, dig, t->R, t->C,
                                                                                                 mats);
