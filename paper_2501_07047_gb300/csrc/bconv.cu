@@ -184,6 +184,9 @@ __global__ void __launch_bounds__(256, MODE == BC_MODUP ? 4 : 5)
         for (uint32_t k = threadIdx.x; k < words / 4; k += blockDim.x) d4[k] = __ldg(s4 + k);
     }
     __syncthreads();
+    // the plan constants are written once at plan creation; everything below waits for the
+    // stream's preceding kernel (programmatic dependent launch)
+    griddep_wait();
     if (LOGN > 0) log2n = LOGN;
     const uint32_t L = c.L, Lp = c.Lp;
     if constexpr (MODE == BC_MODUP) {
@@ -332,15 +335,12 @@ cudaError_t launch_cc(const hefx_bconv_plan* plan, const uint32_t* in, uint32_t*
                       size_t in_stride, cudaStream_t stream) {
     const size_t total = ((size_t)1 << plan->log2n) * batch;
     const size_t out_stride = (size_t)plan->Lp << plan->log2n;
+    const BConvConst* gc = static_cast<const BConvConst*>(plan->d_const);
     if (plan->log2n == 16)
-        bconv_cc_kernel<1, MODE, 16><<<bconv_blocks<1, MODE, 16>(total, plan->Lp), 256, 0, stream>>>(
-            static_cast<const BConvConst*>(plan->d_const), in, out, xq, plan->log2n, (uint32_t)batch, in_stride,
-            out_stride, 0);
-    else
-        bconv_cc_kernel<1, MODE, 0><<<bconv_blocks<1, MODE, 0>(total, plan->Lp), 256, 0, stream>>>(
-            static_cast<const BConvConst*>(plan->d_const), in, out, xq, plan->log2n, (uint32_t)batch, in_stride,
-            out_stride, 0);
-    return cudaGetLastError();
+        return launch_pdl(bconv_cc_kernel<1, MODE, 16>, dim3(bconv_blocks<1, MODE, 16>(total, plan->Lp)), dim3(256), 0,
+                          stream, gc, in, out, xq, plan->log2n, (uint32_t)batch, in_stride, out_stride, (size_t)0);
+    return launch_pdl(bconv_cc_kernel<1, MODE, 0>, dim3(bconv_blocks<1, MODE, 0>(total, plan->Lp)), dim3(256), 0,
+                      stream, gc, in, out, xq, plan->log2n, (uint32_t)batch, in_stride, out_stride, (size_t)0);
 }
 
 }  // namespace
@@ -358,15 +358,13 @@ cudaError_t launch_mod_up(const hefx_modup_plan* mp, const uint32_t* c, uint32_t
     const unsigned all = mp->log2n == 16 ? bconv_blocks<1, BC_MODUP, 16>(total * mp->dnum, lp_max)
                                          : bconv_blocks<1, BC_MODUP, 0>(total * mp->dnum, lp_max);
     const dim3 grid(std::max(1u, all / mp->dnum), mp->dnum);
+    const BConvConst* gc = static_cast<const BConvConst*>(mp->d_const);
+    const uint32_t* none = nullptr;
     if (mp->log2n == 16)
-        bconv_cc_kernel<1, BC_MODUP, 16><<<grid, 256, 0, stream>>>(static_cast<const BConvConst*>(mp->d_const), c, U,
-                                                                   nullptr, mp->log2n, (uint32_t)batch, in_stride,
-                                                                   out_stride, digit_stride);
-    else
-        bconv_cc_kernel<1, BC_MODUP, 0><<<grid, 256, 0, stream>>>(static_cast<const BConvConst*>(mp->d_const), c, U,
-                                                                  nullptr, mp->log2n, (uint32_t)batch, in_stride,
-                                                                  out_stride, digit_stride);
-    return cudaGetLastError();
+        return launch_pdl(bconv_cc_kernel<1, BC_MODUP, 16>, grid, dim3(256), 0, stream, gc, c, U, none, mp->log2n,
+                          (uint32_t)batch, in_stride, out_stride, digit_stride);
+    return launch_pdl(bconv_cc_kernel<1, BC_MODUP, 0>, grid, dim3(256), 0, stream, gc, c, U, none, mp->log2n,
+                      (uint32_t)batch, in_stride, out_stride, digit_stride);
 }
 
 cudaError_t launch_bconv_cc(const hefx_bconv_plan* plan, const uint32_t* in, uint32_t* out, size_t batch,

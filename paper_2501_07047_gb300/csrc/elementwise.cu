@@ -28,6 +28,7 @@ __device__ __forceinline__ uint32_t mulmod_barrett(uint32_t x, uint32_t y, const
 template <bool BARRETT>
 __global__ void __launch_bounds__(256) vec_mod_mul_kernel(const LimbConst* __restrict__ lc, uint32_t L, uint32_t n,
                                                           size_t total4, const uint4* x, const uint4* y, uint4* z) {
+    griddep_wait();
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total4; i += (size_t)gridDim.x * blockDim.x) {
         const LimbConst c = lc[((i * 4) / n) % L];
         const uint4 a = x[i], b = y[i];
@@ -49,6 +50,7 @@ __global__ void __launch_bounds__(256) tensor_product_kernel(const LimbConst* __
                                                              size_t total4, const uint4* a0, const uint4* a1,
                                                              const uint4* b0, const uint4* b1, uint4* d0, uint4* d1,
                                                              uint4* d2) {
+    griddep_wait();
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total4; i += (size_t)gridDim.x * blockDim.x) {
         const LimbConst c = lc[((i * 4) / n) % L];
         const uint4 x0 = a0[i], x1 = a1[i], y0 = b0[i], y1 = b1[i];
@@ -61,6 +63,7 @@ __global__ void __launch_bounds__(256) tensor_product_kernel(const LimbConst* __
 
 __global__ void __launch_bounds__(256) vec_mod_add_kernel(const LimbConst* __restrict__ lc, uint32_t L, uint32_t n,
                                                           size_t total4, const uint4* x, const uint4* y, uint4* z) {
+    griddep_wait();
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total4; i += (size_t)gridDim.x * blockDim.x) {
         const uint32_t q = lc[((i * 4) / n) % L].q;
         const uint4 a = x[i], b = y[i];
@@ -81,6 +84,7 @@ __device__ __forceinline__ uint32_t kip_final(uint32_t acc, const LimbConst& c) 
 __global__ void __launch_bounds__(256) key_inner_product_kernel(const LimbConst* __restrict__ lc, uint32_t nl,
                                                                 uint32_t n, uint32_t dnum, size_t batch,
                                                                 const uint4* dig, const uint4* evk, uint4* out) {
+    griddep_wait();
     const size_t per_poly4 = (size_t)nl * n / 4;  // uint4 groups of one polynomial over Q u P
     const size_t total4 = batch * per_poly4;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total4; i += (size_t)gridDim.x * blockDim.x) {
@@ -107,6 +111,7 @@ __global__ void __launch_bounds__(256) key_inner_product_kernel(const LimbConst*
 // by a Shoup product with 1 and one subtraction.
 __global__ void __launch_bounds__(256) rescale_kernel(const LimbConst* __restrict__ lc, uint32_t L, uint32_t n,
                                                       size_t batch, const uint4* x, uint4* out) {
+    griddep_wait();
     const size_t row4 = n / 4;
     const size_t per_out4 = (size_t)(L - 1) * row4;
     const size_t total4 = batch * per_out4;
@@ -138,12 +143,11 @@ cudaError_t launch_vec_mod_mul(const hefx_params* p, const uint32_t* x, const ui
     if (!total4) return cudaSuccess;
     if (p->red_vec == HEFX_RED_BAT_LAZY) return launch_vec_mod_mul_bat(p, x, y, z, rows, s);
     if (p->red_vec == HEFX_RED_BARRETT)
-        vec_mod_mul_kernel<true><<<grid_for(total4), 256, 0, s>>>(p->d_lc, p->nlimbs, p->n, total4, (const uint4*)x,
-                                                                  (const uint4*)y, (uint4*)z);
+        return launch_pdl(vec_mod_mul_kernel<true>, grid_for(total4), 256, 0, s, (const LimbConst*)p->d_lc, p->nlimbs,
+                          p->n, total4, (const uint4*)x, (const uint4*)y, (uint4*)z);
     else
-        vec_mod_mul_kernel<false><<<grid_for(total4), 256, 0, s>>>(p->d_lc, p->nlimbs, p->n, total4, (const uint4*)x,
-                                                                   (const uint4*)y, (uint4*)z);
-    return cudaGetLastError();
+        return launch_pdl(vec_mod_mul_kernel<false>, grid_for(total4), 256, 0, s, (const LimbConst*)p->d_lc, p->nlimbs,
+                          p->n, total4, (const uint4*)x, (const uint4*)y, (uint4*)z);
 }
 
 cudaError_t launch_tensor_product(const hefx_params* p, const uint32_t* a0, const uint32_t* a1, const uint32_t* b0,
@@ -151,35 +155,32 @@ cudaError_t launch_tensor_product(const hefx_params* p, const uint32_t* a0, cons
                                   cudaStream_t s) {
     const size_t total4 = rows * p->n / 4;
     if (!total4) return cudaSuccess;
-    tensor_product_kernel<<<grid_for(total4), 256, 0, s>>>(p->d_lc, p->nlimbs, p->n, total4, (const uint4*)a0,
-                                                           (const uint4*)a1, (const uint4*)b0, (const uint4*)b1,
-                                                           (uint4*)d0, (uint4*)d1, (uint4*)d2);
-    return cudaGetLastError();
+    return launch_pdl(tensor_product_kernel, grid_for(total4), 256, 0, s, (const LimbConst*)p->d_lc, p->nlimbs, p->n,
+                      total4, (const uint4*)a0, (const uint4*)a1, (const uint4*)b0, (const uint4*)b1, (uint4*)d0,
+                      (uint4*)d1, (uint4*)d2);
 }
 
 cudaError_t launch_vec_mod_add(const hefx_params* p, const uint32_t* x, const uint32_t* y, uint32_t* z, size_t rows,
                                cudaStream_t s) {
     const size_t total4 = rows * p->n / 4;
     if (!total4) return cudaSuccess;
-    vec_mod_add_kernel<<<grid_for(total4), 256, 0, s>>>(p->d_lc, p->nlimbs, p->n, total4, (const uint4*)x,
-                                                        (const uint4*)y, (uint4*)z);
-    return cudaGetLastError();
+    return launch_pdl(vec_mod_add_kernel, grid_for(total4), 256, 0, s, (const LimbConst*)p->d_lc, p->nlimbs, p->n,
+                      total4, (const uint4*)x, (const uint4*)y, (uint4*)z);
 }
 
 cudaError_t launch_key_inner_product(const hefx_params* p, const uint32_t* dig, const uint32_t* evk, uint32_t* out,
                                      uint32_t dnum, size_t batch, cudaStream_t s) {
     const size_t total4 = batch * p->nlimbs * p->n / 4;
     if (!total4) return cudaSuccess;
-    key_inner_product_kernel<<<grid_for(total4), 256, 0, s>>>(p->d_lc, p->nlimbs, p->n, dnum, batch,
-                                                              (const uint4*)dig, (const uint4*)evk, (uint4*)out);
-    return cudaGetLastError();
+    return launch_pdl(key_inner_product_kernel, grid_for(total4), 256, 0, s, (const LimbConst*)p->d_lc, p->nlimbs, p->n,
+                      dnum, batch, (const uint4*)dig, (const uint4*)evk, (uint4*)out);
 }
 
 cudaError_t launch_rescale(const hefx_params* p, const uint32_t* x, uint32_t* out, size_t batch, cudaStream_t s) {
     const size_t total4 = batch * (p->nlimbs - 1) * p->n / 4;
     if (!total4) return cudaSuccess;
-    rescale_kernel<<<grid_for(total4), 256, 0, s>>>(p->d_lc, p->nlimbs, p->n, batch, (const uint4*)x, (uint4*)out);
-    return cudaGetLastError();
+    return launch_pdl(rescale_kernel, grid_for(total4), 256, 0, s, (const LimbConst*)p->d_lc, p->nlimbs, p->n, batch,
+                      (const uint4*)x, (uint4*)out);
 }
 
 }  // namespace hefx

@@ -119,6 +119,30 @@ struct hefx_modup_plan {
 
 namespace hefx {
 
+// Programmatic dependent launch: a kernel launched this way may start (set-up only) while the
+// stream's preceding kernel drains; it runs griddep_wait() before its first access to memory
+// that a preceding kernel writes or reads, which then waits for that kernel to complete.  No
+// early trigger is issued anywhere, so a dependent launch starts only after every block of
+// the preceding kernel has exited.  griddep_wait() is a no-op for a plain launch.
+#ifdef __CUDACC__
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... Params, typename... Args>
+cudaError_t launch_pdl(void (*kern)(Params...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+#endif
+
 // Kernel launchers (return a CUDA error code; the host API maps it to hefx_status).
 // MODE_RS_FWD: NTT(Rescale(x)): the forward transform of q_0..q_{L-2} whose first pass reads
 // limb i and the last limb of the same coefficient-form polynomial and rescales on the way in.

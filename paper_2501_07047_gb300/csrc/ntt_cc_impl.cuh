@@ -770,6 +770,8 @@ __global__ void __launch_bounds__(Cfg<LOGN>::threads, Cfg<LOGN>::minb) ntt_cc_ke
         }
         __syncthreads();
     }
+    // programmatic dependent launch: every global access (and every cluster access) is below
+    griddep_wait();
     // persistent: each CTA (or cluster of P CTAs) walks a strided sequence of tasks; a task
     // is one row (split N) or C::rows rows
     const uint32_t ntasks = C::split ? a.rows : (a.rows + C::rows - 1) / C::rows;
@@ -800,17 +802,22 @@ cudaError_t launch_one(const KArgs& a, size_t rows, cudaStream_t stream) {
     auto kern = ntt_cc_kernel<LOGN, MODE, F>;
     constexpr int smem = C::smem_bytes + (uses_tma<LOGN, MODE, F>() ? 1024 : 0);
     cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     cfg.blockDim = dim3(C::threads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = stream;
+    // the set-up may overlap the stream's preceding kernel; the kernel waits (griddep_wait)
+    // before its first memory access
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     if (C::split) {
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = C::P;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
+        attr[1].id = cudaLaunchAttributeClusterDimension;
+        attr[1].val.clusterDim.x = C::P;
+        attr[1].val.clusterDim.y = 1;
+        attr[1].val.clusterDim.z = 1;
+        cfg.numAttrs = 2;
     }
     // One CTA (cluster) per task, scheduled by the hardware: measured faster than persistent
     // grids, both with an equal number of tasks per CTA (whose lower occupancy costs more
