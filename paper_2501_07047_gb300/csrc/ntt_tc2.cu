@@ -340,38 +340,8 @@ __global__ void __launch_bounds__(256) digitize_kernel(const uint32_t* __restric
     }
 }
 
-// Digits of forward step 1's A operand, whose rows are the data's columns (K over its rows):
-// a 32 x 32 tile of the data matrix is read by rows (coalesced 128-byte rows) and written by
-// columns, where the 32 rows of one column are 128 consecutive digits (256 bytes) of one
-// A-operand row.
-__global__ void __launch_bounds__(256) digitize_t_kernel(const uint32_t* __restrict__ in, uint16_t* __restrict__ dig,
-                                                         uint32_t R, uint32_t C, size_t mats) {
-    __shared__ uint32_t tile[32][33];
-    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const size_t tiles_per = (size_t)(R / 32) * (C / 32);
-    for (size_t t = blockIdx.x; t < mats * tiles_per; t += gridDim.x) {
-        const size_t m = t / tiles_per, w = t % tiles_per;
-        const uint32_t r0 = (uint32_t)(w / (C / 32)) * 32, c0 = (uint32_t)(w % (C / 32)) * 32;
-        const uint32_t* src = in + m * R * C;
-        uint16_t* dst = dig + m * R * C * 4;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const uint32_t r = warp + 8 * k;
-            tile[r][lane] = __ldg(src + (size_t)(r0 + r) * C + c0 + lane);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const uint32_t c = warp + 8 * k;  // this warp's column of the tile
-            const uint2 d = tc::split_digits4(tile[lane][c]);
-            // A row c0 + c, K = 4 (r0 + lane) .. + 3
-            *reinterpret_cast<uint2*>(dst + (size_t)(c0 + c) * (4 * R) + 4 * (r0 + lane)) = d;
-        }
-        __syncthreads();
-    }
-}
-
-// The same transposed digit split on 64 x 64 tiles (R, C multiples of 64): each thread moves
+// Digits of forward step 1's A operand, whose rows are the data's columns (K over its rows),
+// on 64 x 64 tiles of the data matrix (R, C multiples of 64): each thread moves
 // four 16-byte row pieces (16 KiB of loads per block), and the next tile's loads are issued
 // before this tile's stores (persistent blocks).  Column c of the tile is 64 consecutive
 // A-operand positions: one warp writes it as one 512-byte store, each lane the digits of two
@@ -673,7 +643,7 @@ cudaError_t digitize(const hefx_params* p, const uint32_t* in, uint16_t* dig, bo
     const size_t mats = batch * p->nlimbs;
     const size_t work = mats * p->n / 4;
     const unsigned grid = (unsigned)std::min<size_t>((work + 255) / 256, (size_t)1 << 20);
-    if (trans && t->R % 64 == 0 && t->C % 64 == 0) {
+    if (trans) {  // R, C >= 128 (14 <= log2 N <= 16): multiples of 64
         const size_t tiles = mats * (t->R / 64) * (t->C / 64);
         int dev = 0, sms = 148;
         cudaGetDevice(&dev);
@@ -681,10 +651,6 @@ cudaError_t digitize(const hefx_params* p, const uint32_t* in, uint16_t* dig, bo
         // persistent: 8 blocks of 256 threads per SM (16.6 KiB of shared memory each)
         tc2::digitize_t64_kernel<<<(unsigned)std::min<size_t>(tiles, (size_t)sms * 8), 256, 0, s>>>(in, dig, t->R,
                                                                                                    t->C, mats);
-    } else if (trans) {
-        const size_t tiles = mats * (t->R / 32) * (t->C / 32);
-        tc2::digitize_t_kernel<<<(unsigned)std::min<size_t>(tiles, (size_t)1 << 20), 256, 0, s>>>(in, dig, t->R, t->C,
-                                                                                                mats);
     } else
         tc2::digitize_kernel<<<grid, 256, 0, s>>>(in, dig, t->R, t->C, mats);
     return cudaGetLastError();
