@@ -326,7 +326,8 @@ void hefx_mult_plan_destroy(hefx_mult_plan* plan);
  * Runs the front half on `stream`: d_in = [a0, a1, b0, b1], each [L][N]; d_out = [d0, d1,
  * e0 (Q part), e1 (Q part), e0 (P part), e1 (P part)], [4L + 2K][N] contiguous (one copy reads
  * every result); d_work [2L + K][N] holds d2, INTT(d2) and p.  The three must not overlap.
- * CUDA-core transforms; the conversion takes the tensor path where the plan has one.
+ * CUDA-core transforms; the conversion takes the path HEFX_PATH_AUTO picks for one polynomial
+ * (see hefx_basis_convert); each pair of key products is one launch.
  * Errors: EINVAL for null, foreign, misaligned or overlapping buffers; ECUDA.
  */
 hefx_status hefx_mult_front(hefx_ctx* ctx, const hefx_mult_plan* plan, const uint32_t* d_in, uint32_t* d_out,
@@ -335,8 +336,10 @@ hefx_status hefx_mult_front(hefx_ctx* ctx, const hefx_mult_plan* plan, const uin
 /*
  * hefx_mult_front with host buffers: copies a0, a1, b0, b1 (host, [L][N] each; pinned memory
  * lets the copies overlap other work) into d_buf, runs the front half and copies the outputs
- * ([4L + 2K][N], layout of hefx_mult_front's d_out) back into h_out, all on `stream`.  d_buf
- * is device memory of [10L + 3K][N] words (inputs, outputs, workspace).  Errors as above.
+ * ([4L + 2K][N], layout of hefx_mult_front's d_out) back into h_out, all on `stream`.  When the
+ * four inputs are equally spaced in host memory (h_a1 - h_a0 == h_b0 - h_a1 == h_b1 - h_b0 >=
+ * L N words) they are uploaded as one pitched copy, else as four.  d_buf is device memory of
+ * [10L + 3K][N] words (inputs, outputs, workspace).  Errors as above.
  */
 hefx_status hefx_mult_front_host(hefx_ctx* ctx, const hefx_mult_plan* plan, const uint32_t* h_a0,
                                  const uint32_t* h_a1, const uint32_t* h_b0, const uint32_t* h_b1, uint32_t* h_out,

@@ -40,6 +40,19 @@ __global__ void __launch_bounds__(256) vec_mod_mul_kernel(const LimbConst* __res
     }
 }
 
+// z0 = x o y0, z1 = x o y1 (one key-switching operand times both key halves: x read once).
+__global__ void __launch_bounds__(256) vec_mod_mul2_kernel(const LimbConst* __restrict__ lc, uint32_t L, uint32_t n,
+                                                           size_t total4, const uint4* x, const uint4* y0,
+                                                           const uint4* y1, uint4* z0, uint4* z1) {
+    griddep_wait();
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total4; i += (size_t)gridDim.x * blockDim.x) {
+        const LimbConst c = lc[((i * 4) / n) % L];
+        const uint4 a = x[i], b0 = y0[i], b1 = y1[i];
+        z0[i] = make_uint4(mulmod(a.x, b0.x, c), mulmod(a.y, b0.y, c), mulmod(a.z, b0.z, c), mulmod(a.w, b0.w, c));
+        z1[i] = make_uint4(mulmod(a.x, b1.x, c), mulmod(a.y, b1.y, c), mulmod(a.z, b1.z, c), mulmod(a.w, b1.w, c));
+    }
+}
+
 __device__ __forceinline__ uint32_t mac2(uint32_t a, uint32_t b, uint32_t c, uint32_t d, const LimbConst& k) {
     // (a b + c d) mod q with one final pair of reductions
     const uint32_t t = mul_mont_lazy(a, b, k.q, k.qinv_neg) + mul_mont_lazy(c, d, k.q, k.qinv_neg);  // < 4q
@@ -148,6 +161,18 @@ cudaError_t launch_vec_mod_mul(const hefx_params* p, const uint32_t* x, const ui
     else
         return launch_pdl(vec_mod_mul_kernel<false>, grid_for(total4), 256, 0, s, (const LimbConst*)p->d_lc, p->nlimbs,
                           p->n, total4, (const uint4*)x, (const uint4*)y, (uint4*)z);
+}
+
+cudaError_t launch_vec_mod_mul2(const hefx_params* p, const uint32_t* x, const uint32_t* y0, const uint32_t* y1,
+                                uint32_t* z0, uint32_t* z1, size_t rows, cudaStream_t s) {
+    const size_t total4 = rows * p->n / 4;
+    if (!total4) return cudaSuccess;
+    if (p->red_vec != HEFX_RED_MONTGOMERY) {  // the other reductions: two single products
+        cudaError_t e = launch_vec_mod_mul(p, x, y0, z0, rows, s);
+        return e == cudaSuccess ? launch_vec_mod_mul(p, x, y1, z1, rows, s) : e;
+    }
+    return launch_pdl(vec_mod_mul2_kernel, grid_for(total4), 256, 0, s, (const LimbConst*)p->d_lc, p->nlimbs, p->n,
+                      total4, (const uint4*)x, (const uint4*)y0, (const uint4*)y1, (uint4*)z0, (uint4*)z1);
 }
 
 cudaError_t launch_tensor_product(const hefx_params* p, const uint32_t* a0, const uint32_t* a1, const uint32_t* b0,

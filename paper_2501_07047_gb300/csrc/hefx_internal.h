@@ -153,6 +153,9 @@ cudaError_t launch_ntt_cc(const hefx_params* p, NttMode mode, const uint32_t* in
 // Elementwise products of the HE-Mult request (elementwise.cu).
 cudaError_t launch_vec_mod_mul(const hefx_params* p, const uint32_t* x, const uint32_t* y, uint32_t* z, size_t rows,
                                cudaStream_t s);
+// z0 = x o y0 and z1 = x o y1 in one pass (the default Montgomery reduction; else two launches).
+cudaError_t launch_vec_mod_mul2(const hefx_params* p, const uint32_t* x, const uint32_t* y0, const uint32_t* y1,
+                                uint32_t* z0, uint32_t* z1, size_t rows, cudaStream_t s);
 // VecModMul with the BAT lazy reduction on the tensor cores (bat_lazy.cu); log2n >= 9.
 cudaError_t launch_vec_mod_mul_bat(const hefx_params* p, const uint32_t* x, const uint32_t* y, uint32_t* z,
                                    size_t rows, cudaStream_t s);

@@ -138,7 +138,10 @@ class GpuExecutor:
         for v in range(self.variants):
             sv = inputs.derive_seed(self.seed, 2000, logn, v)
             arrs = [inputs.residue_tensor(inputs.derive_seed(sv, c), 1, self.qprimes, n)[0] for c in range(4)]
-            pl["host_in"].append([torch.from_numpy(a.view(np.int32).copy()).pin_memory() for a in arrs])
+            # one pinned block [4][36][N]: a request's four inputs are equally spaced, which the
+            # native call uploads as one pitched copy
+            block = torch.from_numpy(np.stack(arrs).view(np.int32).copy()).pin_memory()
+            pl["host_in"].append([block[c] for c in range(4)])
         assert all(a.shape[0] == LQ for a in pl["host_in"][0])
         self.pools[logn] = pl
         return pl
@@ -182,8 +185,8 @@ class GpuExecutor:
                 "ev": torch.cuda.Event()}
 
     def launch(self, req: Request):
-        """Enqueues one request as one hefx_mult_front_host call (four input copies, every
-        stage, one read-back of the contiguous outputs) and a completion event."""
+        """Enqueues one request as one hefx_mult_front_host call (one pitched upload of the four
+        inputs, every stage, one read-back of the contiguous outputs) and a completion event."""
         res = self.shape(req.logn, req.L)
         pl = self.pool(req.logn)
         s = self.streams[self.next_stream]
