@@ -1,0 +1,81 @@
+"""Host-side logic that needs no GPU: key-switching digit ranges, the bench's traffic-file
+reader and its source-hash check, the path tuner's cache, and the seeded input generators."""
+import hashlib
+import importlib.util
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import keyswitch as oks
+from paper_2501_07047_gb300 import inputs
+from paper_2501_07047_gb300.hemult import digit_ranges
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _bench():
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+@pytest.mark.parametrize("L,alpha", [(1, 1), (5, 2), (6, 3), (7, 7), (48, 16), (24, 8), (10, 4)])
+def test_digit_ranges_partition(L, alpha):
+    """HE-Mult's digits equal the oracle's and partition [0, L) into ceil(L / alpha) ranges."""
+    d = digit_ranges(L, alpha)
+    assert d == oks.digit_ranges(L, alpha)
+    assert len(d) == -(-L // alpha)
+    assert d[0][0] == 0 and d[-1][1] == L
+    assert all(a < b <= a + alpha for a, b in d)
+    assert all(d[i][1] == d[i + 1][0] for i in range(len(d) - 1))
+
+
+def test_profile_traffic_reader(tmp_path):
+    """The committed traffic figures are read only while the kernel source still matches."""
+    b = _bench()
+    fwd, inv = b.profile_traffic("ntt_cc", "fwd"), b.profile_traffic("ntt_cc", "inv")
+    assert fwd is not None and inv is not None and 48 << 20 < fwd < 80 << 20 and 48 << 20 < inv < 80 << 20
+    # a copy of the tree whose kernel source differs: no traffic figure
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "paper_2501_07047_gb300" / "csrc").mkdir(parents=True)
+    text = open(os.path.join(ROOT, "profiles", "ntt_cc_traffic.txt")).read()
+    (tmp_path / "profiles" / "ntt_cc_traffic.txt").write_text(text)
+    src = tmp_path / "paper_2501_07047_gb300" / "csrc" / "ntt_cc_impl.cuh"
+    src.write_text("// changed\n")
+    b.ROOT = str(tmp_path)
+    assert b.profile_traffic("ntt_cc", "fwd") is None
+    # and with a matching hash the figure comes back
+    sha = hashlib.sha256(src.read_bytes()).hexdigest()[:16]
+    lines = [("source_sha=" + sha) if ln.startswith("source_sha=") else ln for ln in text.split("\n")]
+    (tmp_path / "profiles" / "ntt_cc_traffic.txt").write_text("\n".join(lines))
+    assert b.profile_traffic("ntt_cc", "fwd") == fwd
+    assert b.profile_traffic("ntt_cc", "nope") is None
+
+
+def test_tuner_cache_round_trip(tmp_path, monkeypatch):
+    from paper_2501_07047_gb300 import autotune
+    monkeypatch.setattr(autotune, "CACHE", str(tmp_path / "sub" / "tune.json"))
+    assert autotune._load_cache() == {}
+    autotune._save_cache({"GB300|16|24": "cudacore"})
+    assert autotune._load_cache() == {"GB300|16|24": "cudacore"}
+    assert json.load(open(tmp_path / "sub" / "tune.json")) == {"GB300|16|24": "cudacore"}
+
+
+def test_input_generators():
+    """Seeded and reproducible; residues below their prime; primes prime and NTT-friendly."""
+    assert inputs.derive_seed(2, 0) == inputs.derive_seed(2, 0) != inputs.derive_seed(2, 1)
+    qs = inputs.source_primes(6)
+    a = inputs.residue_tensor(inputs.derive_seed(7, 1), 2, qs, 1 << 10)
+    assert a.shape == (2, 6, 1 << 10) and a.dtype == np.uint32
+    assert np.array_equal(a, inputs.residue_tensor(inputs.derive_seed(7, 1), 2, qs, 1 << 10))
+    assert (a < np.asarray(qs, dtype=np.uint32)[None, :, None]).all()
+    for q in qs + inputs.special_primes(4) + inputs.ntt_primes(3, 28, 1 << 18):
+        assert q % 2 and all(q % d for d in range(3, int(q ** 0.5) + 1, 2))  # trial division (q < 2^30)
+    assert all(q % (1 << 17) == 1 and q < (1 << 28) for q in qs)
+    assert all(p % (1 << 17) == 1 and (1 << 29) < p < (1 << 30) for p in inputs.special_primes(4))
+    assert all(q % (1 << 18) == 1 for q in inputs.ntt_primes(3, 28, 1 << 18))
+    t = inputs.poisson_arrivals(inputs.derive_seed(5, 1), 500, 1000.0)
+    assert np.all(np.diff(t) >= 0) and 0.2 < t[-1] < 1.0  # about 0.5 s of arrivals at 1000/s
