@@ -300,11 +300,24 @@ hefx_status hefx_rescale_ntt(hefx_ctx* ctx, const hefx_params* params, const uin
  * Tensor product of two ciphertexts (a0, a1), (b0, b1) in evaluation (NTT) form, the first
  * step of HE-Mult (Sec. III; App. A: HE-Mult is built from NTT, INTT, BConv, VecModMul and
  * VecModAdd): d0 = a0 o b0, d1 = a0 o b1 + a1 o b0, d2 = a1 o b1 mod q, elementwise over
- * [batch][nlimbs][N].  Outputs must not alias inputs.  Errors as for hefx_ntt_fwd.
+ * [batch][nlimbs][N].  d_d2 may be null: d2 is then not written (a caller that only needs
+ * INTT(d2) takes it from hefx_ntt_inv_hadamard(a1, b1)).  Outputs must not alias inputs.
+ * Errors as for hefx_ntt_fwd.
  */
 hefx_status hefx_tensor_product(hefx_ctx* ctx, const hefx_params* params, const uint32_t* d_a0, const uint32_t* d_a1,
                                 const uint32_t* d_b0, const uint32_t* d_b1, uint32_t* d_d0, uint32_t* d_d1,
                                 uint32_t* d_d2, size_t batch, void* stream);
+
+/*
+ * d_out = INTT(d_x o d_y) over the params' limbs (the inverse NTT of a Hadamard product, as in
+ * the last step of hefx_poly_mul): the CUDA-core inverse transform multiplies the two inputs
+ * (lazy Montgomery products, 2^32 folded into the final scale) as it loads them, with the same
+ * results as hefx_vec_mod_mul then hefx_ntt_inv.  Layouts [batch][nlimbs][N] evaluation form
+ * in, coefficient form out; d_out must not overlap an input (EINVAL).  Errors as for
+ * hefx_ntt_fwd; EUNSUPPORTED when the params' NTT reduction is not the default (Shoup).
+ */
+hefx_status hefx_ntt_inv_hadamard(hefx_ctx* ctx, const hefx_params* params, const uint32_t* d_x, const uint32_t* d_y,
+                                  uint32_t* d_out, size_t batch, void* stream);
 
 /*
  * The HE-Mult front half of one ciphertext pair as one call (Sec. III HE-Mult, built from

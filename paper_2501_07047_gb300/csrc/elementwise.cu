@@ -70,7 +70,9 @@ __global__ void __launch_bounds__(256) tensor_product_kernel(const LimbConst* __
         d0[i] = make_uint4(mulmod(x0.x, y0.x, c), mulmod(x0.y, y0.y, c), mulmod(x0.z, y0.z, c), mulmod(x0.w, y0.w, c));
         d1[i] = make_uint4(mac2(x0.x, y1.x, x1.x, y0.x, c), mac2(x0.y, y1.y, x1.y, y0.y, c),
                            mac2(x0.z, y1.z, x1.z, y0.z, c), mac2(x0.w, y1.w, x1.w, y0.w, c));
-        d2[i] = make_uint4(mulmod(x1.x, y1.x, c), mulmod(x1.y, y1.y, c), mulmod(x1.z, y1.z, c), mulmod(x1.w, y1.w, c));
+        if (d2)  // null: d2 not wanted (HE-Mult takes INTT(a1 o b1) straight from the inputs)
+            d2[i] =
+                make_uint4(mulmod(x1.x, y1.x, c), mulmod(x1.y, y1.y, c), mulmod(x1.z, y1.z, c), mulmod(x1.w, y1.w, c));
     }
 }
 

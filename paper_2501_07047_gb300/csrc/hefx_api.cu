@@ -575,6 +575,7 @@ hefx_status hefx_tensor_product(hefx_ctx* ctx, const hefx_params* p, const uint3
     const void* ptrs[7] = {a0, a1, b0, b1, d0, d1, d2};
     const char* names[7] = {"d_a0", "d_a1", "d_b0", "d_b1", "d_d0", "d_d1", "d_d2"};
     for (int i = 0; i < 7; ++i) {
+        if (i == 6 && !d2) break;  // d2 not wanted
         hefx_status st = check_ntt_args(ctx, p, ptrs[i], names[i]);
         if (st != HEFX_OK) return st;
     }
@@ -583,6 +584,24 @@ hefx_status hefx_tensor_product(hefx_ctx* ctx, const hefx_params* p, const uint3
     if (st != HEFX_OK) return st;
     cudaError_t e = launch_tensor_product(p, a0, a1, b0, b1, d0, d1, d2, batch * p->nlimbs, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "hefx_tensor_product launch");
+    return HEFX_OK;
+}
+
+hefx_status hefx_ntt_inv_hadamard(hefx_ctx* ctx, const hefx_params* p, const uint32_t* x, const uint32_t* y,
+                                  uint32_t* out, size_t batch, void* stream) {
+    hefx_status st;
+    if ((st = check_ntt_args(ctx, p, x, "d_x")) != HEFX_OK) return st;
+    if ((st = check_ntt_args(ctx, p, y, "d_y")) != HEFX_OK) return st;
+    if ((st = check_ntt_args(ctx, p, out, "d_out")) != HEFX_OK) return st;
+    if (p->red_ntt != HEFX_RED_SHOUP)
+        return fail(ctx, HEFX_EUNSUPPORTED, "hefx_ntt_inv_hadamard uses the default (Shoup) NTT reduction only");
+    const size_t bytes = batch * p->nlimbs * (size_t)p->n * 4;
+    if (overlaps(out, bytes, x, bytes) || overlaps(out, bytes, y, bytes))
+        return fail(ctx, HEFX_EINVAL, "d_out overlaps an input");
+    if (batch == 0) return HEFX_OK;
+    if ((st = use_device(ctx)) != HEFX_OK) return st;
+    cudaError_t e = launch_ntt_cc(p, MODE_HAD_INV, x, y, out, batch * p->nlimbs, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "hefx_ntt_inv_hadamard launch");
     return HEFX_OK;
 }
 

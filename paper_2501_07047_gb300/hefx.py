@@ -52,6 +52,7 @@ SIGNATURES = {
     "hefx_mod_up": (_i32, [_vp, _vp, _vp, _vp, _sz, _vp]),
     "hefx_rescale": (_i32, [_vp, _vp, _vp, _vp, _sz, _vp]),
     "hefx_rescale_ntt": (_i32, [_vp, _vp, _vp, _vp, _sz, _vp]),
+    "hefx_ntt_inv_hadamard": (_i32, [_vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "hefx_mult_plan_create": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_vp)]),
     "hefx_mult_plan_destroy": (None, [_vp]),
     "hefx_mult_front": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
@@ -248,6 +249,10 @@ def hefx_mod_up(ctx, plan, c, U, batch, stream=None) -> None:
 def hefx_rescale(ctx, params, x, out, batch, stream=None) -> None:
     _check(ctx, load().hefx_rescale(ctx, params, _ptr(x), _ptr(out), batch, _stream(stream)))
 
+
+
+def hefx_ntt_inv_hadamard(ctx, params, x, y, out, batch, stream=None) -> None:
+    _check(ctx, load().hefx_ntt_inv_hadamard(ctx, params, _ptr(x), _ptr(y), _ptr(out), batch, _stream(stream)))
 
 
 def hefx_rescale_ntt(ctx, params, x, out, batch, stream=None) -> None:

@@ -5,7 +5,8 @@ Sec. V-C "Effects of Security Parameters") and builds them from NTT, INTT, BConv
 and VecModAdd (App. A); it does not print their formulas, which here are textbook RNS-CKKS:
 
   d0 = a0 b0, d1 = a0 b1 + a1 b0, d2 = a1 b1            tensor product (evaluation form, Q)
-  c = INTT(d2); per digit j (limbs D_j, alpha per digit):  ModUp
+  c = INTT(d2) (= INTT(a1 o b1), taken from a1, b1 directly)
+  per digit j (limbs D_j, alpha per digit):              ModUp
       U_j = c on D_j, BConv_{D_j -> rest of Q u P}(c) elsewhere, NTT over Q u P
   acc_k = sum_j U_j o evk_{j,k}                           key inner product
   ks_k = ModDown(INTT(acc_k)), c_k = d_k + NTT(ks_k)
@@ -89,9 +90,15 @@ class HeMult:
         d0, d1, d2 = self.d[0], self.d[1], self.d[2]
         st = torch.cuda.current_stream() if s is None else s
         with torch.cuda.stream(st):
-            hefx.hefx_tensor_product(ctx, self.pQ, a0, a1, b0, b1, d0, d1, d2, 1, st)
-            self.c.copy_(d2)
-            hefx.hefx_ntt_inv(ctx, self.pQ, self.c, 1, self.ntt_path, st)
+            if self.ntt_path == "cudacore":
+                # d2 = a1 o b1 only feeds c = INTT(d2): the inverse transform multiplies a1 and
+                # b1 as it loads them, and the tensor product writes d0 and d1 only
+                hefx.hefx_tensor_product(ctx, self.pQ, a0, a1, b0, b1, d0, d1, None, 1, st)
+                hefx.hefx_ntt_inv_hadamard(ctx, self.pQ, a1, b1, self.c, 1, st)
+            else:
+                hefx.hefx_tensor_product(ctx, self.pQ, a0, a1, b0, b1, d0, d1, d2, 1, st)
+                self.c.copy_(d2)
+                hefx.hefx_ntt_inv(ctx, self.pQ, self.c, 1, self.ntt_path, st)
             if self.modup:
                 hefx.hefx_mod_up(ctx, self.modup, self.c, self.U, 1, st)
             for j, ((lo, hi), (lo_plan, hi_plan)) in enumerate(zip(self.digits, self.plans)):
@@ -142,5 +149,5 @@ class HeMult:
 
     def stages(self) -> dict:
         """The workspaces after a run (for stage-by-stage parity tests)."""
-        return {"d0": self.d[0], "d1": self.d[1], "d2": self.d[2], "modup_eval": self.U, "acc_coeff": self.acc,
+        return {"d0": self.d[0], "d1": self.d[1], "d2_coeff": self.c, "modup_eval": self.U, "acc_coeff": self.acc,
                 "ks_eval": self.ks, "c_coeff": self.cc}
