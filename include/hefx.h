@@ -16,7 +16,10 @@
  *    bit-reversed evaluations back to natural-order coefficients and includes N^-1.
  *  - Every call is asynchronous on `stream` (a cudaStream_t passed as void*, NULL = the
  *    legacy default stream).  Errors that the host can detect are returned synchronously
- *    and nothing is launched; hefx_last_error() then holds a one-line message.
+ *    and nothing is launched; hefx_last_error() then holds a one-line message.  Most
+ *    kernels launch with programmatic stream serialization: their set-up may overlap the
+ *    drain of the stream's preceding kernel, and each waits for that kernel to complete
+ *    before touching memory, so the ordering against earlier stream work is unchanged.
  *  - The caller owns every data buffer (device pointers from any allocator).  hefx owns
  *    the context, parameter sets and plans it creates (and the device tables inside them),
  *    and releases them in the matching *_destroy call.
