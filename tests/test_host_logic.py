@@ -79,3 +79,17 @@ def test_input_generators():
     assert all(q % (1 << 18) == 1 for q in inputs.ntt_primes(3, 28, 1 << 18))
     t = inputs.poisson_arrivals(inputs.derive_seed(5, 1), 500, 1000.0)
     assert np.all(np.diff(t) >= 0) and 0.2 < t[-1] < 1.0  # about 0.5 s of arrivals at 1000/s
+
+
+def test_tensor_work_model():
+    """The tensor path's roofline numerator: 2 flops per digit MAC, 4 x 4 digit products per
+    modular product, N (R + C) modular MACs per limb-NTT for the square split (1.074 GFLOP at
+    N = 2^16), and the 7-bit digits' worst-case partial sum stays exact in fp32."""
+    from paper_2501_07047_gb300 import tensor_plan as tp
+    assert tp.split(16) == (256, 256) and tp.split(15) == (128, 256) and tp.split(14) == (128, 128)
+    assert tp.flops_per_limb_ntt(16) == 2 * 4 * 4 * 65536 * 512 == 1073741824
+    assert tp.flops_per_step_launch(16, 192) * 2 == tp.flops_per_limb_ntt(16) * 192
+    R, _ = tp.split(16)
+    worst = tp.K_IN * R * ((1 << tp.W_IN) - 1) * ((1 << tp.W_OUT) - 1)  # one output's digit sum
+    assert worst < (1 << 24)  # every partial sum is an exact fp32 integer
+    assert tp.K_IN * tp.W_IN >= 28  # four 7-bit digits hold a 28-bit residue
