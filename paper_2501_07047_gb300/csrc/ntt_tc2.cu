@@ -10,17 +10,17 @@
 //
 // GB300 mapping
 //  - A (data digits, K-major) and B (constant, K-major) both arrive by TMA with the 128-byte
-//    swizzle, 4 stages of 16 KiB + 32 KiB.  The CTAs of a cluster (2 by default) work on
-//    128-row data blocks of the same limb; each loads its share of every constant stage and
-//    multicasts it to the others, so the constant is read from L2 once per cluster.
+//    swizzle, 4 stages of 16 KiB + 32 KiB.  Each CTA loads its own constant stages: the
+//    constant matrices of a limb (2 MiB per step at N = 2^16) stay resident in L2 while the
+//    limb's data blocks stream past them.
 //  - Two 256-column TMEM accumulators: the epilogue of one 64-output tile overlaps the MMAs
 //    of the next.  The epilogue merges the 4 chunk sums (sum_o p_o 2^(7o) < 2^46), reduces
 //    with one Montgomery REDC (2^32 folded into the constants), applies the twiddle or
 //    Hadamard product and writes either the final residues or -- after a first step -- the
 //    7-bit digits of the next step's A operand, already transposed where that step needs it.
-//  - Persistent clusters (as many as fit at once) walk the work items (limb, group of data
-//    blocks); the two accumulators carry across items, so an item's last epilogue overlaps
-//    the next item's MMAs.
+//  - Persistent CTAs (as many as fit at once) walk the work items (limb, data block); the
+//    two accumulators carry across items, so an item's last epilogue overlaps the next
+//    item's MMAs.
 //  - Warp roles: warp 0 TMA producer, warp 1 MMA issuer and TMEM owner, warps 2-9 epilogue
 //    (two per TMEM lane quadrant, splitting the columns).  Every mbarrier wait is bounded.
 #include <cuda.h>
@@ -77,37 +77,7 @@ struct Args {
     uint32_t DN;            // data rows per polynomial limb (A operand rows)
     uint32_t OUT;           // outputs per data row
     uint32_t K;             // 4 * reduction length
-    uint32_t cs;            // CTAs per cluster (1, 2 or 4)
 };
-
-__device__ __forceinline__ uint32_t cluster_rank() {
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-
-__device__ __forceinline__ void cluster_sync_all() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
-// TMA 2D load multicast to the CTAs in `mask` (same shared offset and mbarrier offset in each).
-__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* map, int32_t x, int32_t y, uint64_t* bar,
-                                              uint16_t mask) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-        " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(tc::smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(tc::smem_u32(bar)), "h"(mask)
-        : "memory");
-}
-
-// Arrives on `bar` in every CTA of `mask` when this thread's tcgen05 operations complete.
-__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-            tc::smem_u32(bar)),
-        "h"(mask)
-        : "memory");
-}
 
 template <int OUTK, int MUL>
 __global__ void __launch_bounds__(THREADS, 1)
@@ -122,20 +92,16 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 1);
 
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t cs = a.cs;
-    const uint32_t rank = cs > 1 ? cluster_rank() : 0;
-    // work items: (limb, group of cs consecutive data blocks of that limb); a data block is a
-    // (poly, 128-row block) pair.  Clusters walk the items with a stride.
+    // work items: (limb, data block of that limb); a data block is a (poly, 128-row block)
+    // pair.  Consecutive items share the limb (and so the L2-resident constant); CTAs walk the
+    // items with a stride.
     const uint32_t blocks_per_limb = a.batch * (a.DN / BM);
-    const uint32_t groups_per_limb = blocks_per_limb / cs;
-    const uint32_t items = a.L * groups_per_limb;
-    const uint32_t cid = blockIdx.x / cs, nclusters = gridDim.x / cs;
+    const uint32_t items = a.L * blocks_per_limb;
+    const uint32_t cid = blockIdx.x, nctas = gridDim.x;
     const uint32_t ntiles = a.OUT / OUTS, kstages = a.K / BK;
-    const uint32_t slice = BN / cs;                     // constant rows loaded by this CTA
-    const uint16_t mask = (uint16_t)((1u << cs) - 1u);
     auto item_rows = [&](uint32_t item, uint32_t& limb, uint32_t& pl, uint32_t& drow0) {
-        limb = item / groups_per_limb;
-        const uint32_t blk = (item % groups_per_limb) * cs + rank;
+        limb = item / blocks_per_limb;
+        const uint32_t blk = item % blocks_per_limb;
         const uint32_t poly = blk / (a.DN / BM);
         drow0 = (blk % (a.DN / BM)) * BM;
         pl = poly * a.L + limb;
@@ -144,7 +110,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             tc::mbar_init(&full[s], 1);
-            tc::mbar_init(&empty[s], cs);  // one MMA commit from every CTA of the cluster
+            tc::mbar_init(&empty[s], 1);  // the MMA commit that frees the stage
         }
         for (int b = 0; b < 2; ++b) {
             tc::mbar_init(&acc_full[b], 1);
@@ -160,7 +126,6 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     tc::tc_fence_before();
     __syncthreads();
-    if (cs > 1) cluster_sync_all();  // peers' barriers are initialised before any multicast
     tc::tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     // Programmatic dependent launch: the set-up above touches only shared memory, TMEM and
@@ -172,7 +137,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (lane == 0) {  // ---- TMA producer
             uint32_t stage = 0, phase = 0;
             bool ok = true;
-            for (uint32_t item = cid; item < items && ok; item += nclusters) {
+            for (uint32_t item = cid; item < items && ok; item += nctas) {
                 uint32_t limb, pl, drow0;
                 item_rows(item, limb, pl, drow0);
                 const uint32_t a_row0 = pl * a.DN + drow0;   // A rows: [poly][limb][DN]
@@ -186,12 +151,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                         uint8_t* st = smem + stage * STAGE_BYTES;
                         tc::mbar_arrive_expect_tx(&full[stage], STAGE_BYTES);
                         tc::tma_load_2d(st, &amap, (int32_t)(kc * BK), (int32_t)a_row0, &full[stage]);
-                        uint8_t* bdst = st + A_BYTES + rank * slice * 128;
-                        const int32_t by = (int32_t)(b_row0 + nt * BN + rank * slice);
-                        if (cs > 1)
-                            tma_load_2d_mc(bdst, &bmap, (int32_t)(kc * BK), by, &full[stage], mask);
-                        else
-                            tc::tma_load_2d(bdst, &bmap, (int32_t)(kc * BK), by, &full[stage]);
+                        tc::tma_load_2d(st + A_BYTES, &bmap, (int32_t)(kc * BK), (int32_t)(b_row0 + nt * BN),
+                                        &full[stage]);
                         if (++stage == STAGES) {
                             stage = 0;
                             phase ^= 1u;
@@ -204,7 +165,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             const uint32_t idesc = tc::idesc_f16_f32(BM, BN);
             uint32_t stage = 0, phase = 0, t = 0;  // t: tiles issued by this CTA so far
             bool ok = true;
-            for (uint32_t item = cid; item < items && ok; item += nclusters)
+            for (uint32_t item = cid; item < items && ok; item += nctas)
                 for (uint32_t nt = 0; nt < ntiles && ok; ++nt, ++t) {
                     const uint32_t acc = t & 1;
                     if (t >= 2 && !tc::mbar_wait(&acc_empty[acc], ((t - 2) >> 1) & 1u, a.err, tc::ERR_TIMEOUT_ACC))
@@ -222,10 +183,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                         for (int ks = 0; ks < BK / 16; ++ks)
                             tc::mma_f16(tmem + acc * BN, tc::sw128_desc(ab + ks * 32), tc::sw128_desc(bb + ks * 32),
                                         idesc, (kc | ks) != 0);
-                        if (cs > 1)
-                            mma_commit_mc(&empty[stage], mask);
-                        else
-                            tc::mma_commit(&empty[stage]);
+                        tc::mma_commit(&empty[stage]);
                         if (++stage == STAGES) {
                             stage = 0;
                             phase ^= 1u;
@@ -239,7 +197,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     } else {  // ---- epilogue: warps 2..9; warp % 4 is the TMEM lane quadrant, (warp - 2) / 4 the column half
         const uint32_t quad = warp & 3, half = (warp - 2) >> 2;
         uint32_t t = 0;
-        for (uint32_t item = cid; item < items; item += nclusters) {
+        for (uint32_t item = cid; item < items; item += nctas) {
             uint32_t limb, pl, drow0;
             item_rows(item, limb, pl, drow0);
             const uint32_t drow = drow0 + quad * 32 + lane;  // data row held by this thread
@@ -316,7 +274,6 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     tc::tc_fence_before();
     __syncthreads();
-    if (cs > 1) cluster_sync_all();  // no CTA leaves while a peer may still multicast into it
     if (warp == 1) {
         tc::tc_fence_after();
         tc::tmem_dealloc(tmem, TMEM_COLS);
@@ -405,7 +362,7 @@ uint16_t half_bits_small(uint32_t d) {
 struct Tc2Tables {
     uint32_t R = 0, C = 0;
     uint16_t* cst[4] = {nullptr, nullptr, nullptr, nullptr};  // fp16 [L][OUT x 4][4V]
-    CUtensorMap bmaps[4][3];                                   // per step, per cluster size 4/2/1
+    CUtensorMap bmaps[4];                                      // per step
     uint2* T = nullptr;
     uint2* Tinv = nullptr;  // transposed: [L][C][R]
     tc2::Limb* limbs = nullptr;
@@ -415,12 +372,6 @@ struct Tc2Tables {
     uint32_t* scratch = nullptr;
     size_t dig_elems = 0, scratch_words = 0;
 };
-
-namespace {
-
-int cs_index(uint32_t cs) { return cs == 4 ? 0 : cs == 2 ? 1 : 2; }
-
-}  // namespace
 
 // Offline precompute: BAT digit matrices with 7-bit input digits and 7-bit output chunks,
 // constants times 2^32 (Montgomery), rows (out, chunk) interleaved so that one output's four
@@ -492,12 +443,10 @@ cudaError_t tc2_prepare(hefx_params* p) {
     for (int s = 0; s < 4 && e == cudaSuccess; ++s) {
         e = cudaMalloc(&t->cst[s], hc[s].size() * 2);
         if (e == cudaSuccess) e = cudaMemcpy(t->cst[s], hc[s].data(), hc[s].size() * 2, cudaMemcpyHostToDevice);
-        const uint32_t cs_list[3] = {4, 2, 1};
-        for (int c = 0; c < 3 && e == cudaSuccess; ++c)
-            if (!encode_map_2d(&t->bmaps[s][c], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, t->cst[s], 4ull * Vs[s],
-                               (uint64_t)L * outs[s] * KO, 8ull * Vs[s], BK, BN / cs_list[c],
-                               CU_TENSOR_MAP_SWIZZLE_128B))
-                e = cudaErrorInvalidValue;
+        if (e == cudaSuccess &&
+            !encode_map_2d(&t->bmaps[s], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, t->cst[s], 4ull * Vs[s],
+                           (uint64_t)L * outs[s] * KO, 8ull * Vs[s], BK, BN, CU_TENSOR_MAP_SWIZZLE_128B))
+            e = cudaErrorInvalidValue;
     }
     if (e == cudaSuccess) e = cudaMalloc(&t->T, hT.size() * sizeof(uint2));
     if (e == cudaSuccess) e = cudaMemcpy(t->T, hT.data(), hT.size() * sizeof(uint2), cudaMemcpyHostToDevice);
@@ -557,43 +506,30 @@ cudaError_t launch_gemm(const CUtensorMap& amap, const CUtensorMap& bmap, const 
         attr = true;
     }
     cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute at[2];
-    const uint32_t items = g.L * g.batch * (g.DN / BM) / g.cs;
-    uint32_t clusters = items;
-    {
-        // persistent: as many clusters as can be resident at once (cached per cluster size)
-        static int max_clusters[5] = {0, 0, 0, 0, 0};
-        if (!max_clusters[g.cs]) {
-            cudaLaunchConfig_t q = {};
-            cudaLaunchAttribute qa[1];
-            q.gridDim = dim3(g.cs * 64);
-            q.blockDim = dim3(THREADS);
-            q.dynamicSmemBytes = SMEM_BYTES;
-            qa[0].id = cudaLaunchAttributeClusterDimension;
-            qa[0].val.clusterDim.x = g.cs;
-            qa[0].val.clusterDim.y = 1;
-            qa[0].val.clusterDim.z = 1;
-            q.attrs = qa;
-            q.numAttrs = 1;
-            int n = 0;
-            if (cudaOccupancyMaxActiveClusters(&n, kern, &q) != cudaSuccess || n <= 0) n = 1;
-            max_clusters[g.cs] = n;
-        }
-        clusters = std::min<uint32_t>(items, (uint32_t)max_clusters[g.cs]);
+    cudaLaunchAttribute at[1];
+    const uint32_t items = g.L * g.batch * (g.DN / BM);
+    // persistent: as many CTAs as can be resident at once (one per SM: the pipeline's shared
+    // memory), cached per device
+    static int max_ctas[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (!max_ctas[dev & 63]) {
+        int per_sm = 0, sms = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, SMEM_BYTES) != cudaSuccess ||
+            per_sm <= 0)
+            per_sm = 1;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 1;
+        max_ctas[dev & 63] = per_sm * sms;
     }
-    cfg.gridDim = dim3(clusters * g.cs);
+    cfg.gridDim = dim3(std::min<uint32_t>(items, (uint32_t)max_ctas[dev & 63]));
     cfg.blockDim = dim3(THREADS);
     cfg.dynamicSmemBytes = SMEM_BYTES;
     cfg.stream = s;
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = g.cs;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
     // the set-up of this GEMM may overlap the tail of the stream's preceding kernel
-    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[1].val.programmaticStreamSerializationAllowed = HEFX_TC2_PDL;
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = HEFX_TC2_PDL;
     cfg.attrs = at;
-    cfg.numAttrs = 2;
+    cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kern, amap, bmap, g);
 }
 
@@ -617,14 +553,11 @@ cudaError_t step(const hefx_params* p, int stp, int outk, int mul, const uint16_
     g.DN = trans_data ? t->C : t->R;
     g.OUT = trans_data ? t->R : t->C;
     g.K = 4 * g.OUT;  // reduction length equals the output count (square matrices)
-    const uint32_t blocks = g.batch * (g.DN / BM);
-    // clusters of 2 (constant multicast to 2 CTAs): pairs fill the GPCs better than quads
-    g.cs = blocks % 2 == 0 ? 2 : 1;
     CUtensorMap amap;
     if (!encode_map_2d(&amap, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, const_cast<uint16_t*>(adig), g.K,
                        (uint64_t)batch * g.L * g.DN, 2ull * g.K, BK, BM, CU_TENSOR_MAP_SWIZZLE_128B))
         return cudaErrorInvalidValue;
-    const CUtensorMap& bmap = t->bmaps[stp][cs_index(g.cs)];
+    const CUtensorMap& bmap = t->bmaps[stp];
     if (outk == OUT_DIGITS_T) {
         if (mul == MUL_TW_OUT_ROW) return launch_gemm<OUT_DIGITS_T, MUL_TW_OUT_ROW>(amap, bmap, g, s);
         return launch_gemm<OUT_DIGITS_T, MUL_TW_DATA_ROW>(amap, bmap, g, s);
