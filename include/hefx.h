@@ -150,9 +150,11 @@ hefx_status hefx_poly_mul(hefx_ctx* ctx, const hefx_params* params, const uint32
  * device memory once they are running: code whose memory is planned up front (a fixed arena
  * handed out by a host framework), or a latency-critical loop where a cudaMalloc could
  * block on device-wide synchronization or fail under memory pressure.  hefx_poly_mul's
- * tensor path allocates (and may grow) a workspace for the second factor's forward
- * transform; this variant uses instead a fixed 8 MiB array compiled into the library
- * (2^21 residues), which every GPU that loads the library keeps until the process exits.
+ * tensor path keeps its digit workspace in the parameter set and allocates it lazily: on
+ * its first call, and again (after a device synchronization) whenever a larger batch
+ * arrives.  This variant never allocates, not even lazily: its workspace is a fixed 8 MiB
+ * array compiled into the library (2^21 residues), which every GPU that loads the library
+ * keeps until the process exits.
  * There is no counterpart in the paper: this is a deployment variant of the same math.
  *  - Calls no cudaMalloc, cudaFree or allocating library routine.  The parameter set's
  *    tensor tables must exist already: make one tensor-path call with `params` first
@@ -163,7 +165,10 @@ hefx_status hefx_poly_mul(hefx_ctx* ctx, const hefx_params* params, const uint32
  *  - All calls share the one array and it keeps the last call's contents (each call writes
  *    it fully before reading it, so nothing needs clearing).  Calls whose work overlaps on
  *    the GPU (different streams, or different host threads) race on it: serialize them.
- *  - Layout, aliasing and errors otherwise as for hefx_poly_mul.
+ *  - Like hefx_poly_mul, it takes the default (Shoup) NTT reduction only: a parameter set
+ *    switched to another reduction gets HEFX_EUNSUPPORTED.
+ *  - Layout, aliasing (d_c may alias d_a and/or d_b) and errors otherwise as for
+ *    hefx_poly_mul.
  */
 hefx_status hefx_poly_mul_noalloc(hefx_ctx* ctx, const hefx_params* params, const uint32_t* d_a,
                                   const uint32_t* d_b, uint32_t* d_c, size_t batch, void* stream);
@@ -407,6 +412,23 @@ hefx_status hefx_batch_polymul(hefx_ctx* ctx, hefx_batch_plan* plan, void* strea
  * recorded code rather than a hung device.  Errors: EINVAL, ECUDA, ETIMEOUT.
  */
 hefx_status hefx_stream_check(hefx_ctx* ctx, const hefx_params* params, void* stream);
+
+/*
+ * Check of the failure-detection path (no counterpart in the paper: a property of this
+ * library's kernels).  Every wait of the tensor-core and TMA pipelines is bounded: when a
+ * copy or an MMA it waits for does not arrive within the limit, the waiting thread records
+ * an error code in a device flag, the kernel releases what it holds (TMEM) and returns, and
+ * hefx_stream_check reports HEFX_ETIMEOUT instead of the device hanging.  This call runs that
+ * same bounded wait in a one-warp kernel that holds TMEM while it waits on an mbarrier:
+ *  - arrive != 0: the kernel arrives on the barrier first; the wait succeeds and the next
+ *    hefx_stream_check(ctx, params, stream) returns HEFX_OK;
+ *  - arrive == 0: nothing ever arrives; the wait gives up after limit_ns nanoseconds, the
+ *    code is recorded in params' error flag and the next hefx_stream_check returns
+ *    HEFX_ETIMEOUT (and clears the flag).  The context stays usable.
+ * limit_ns at most 2e9 (the pipelines' own limit), else HEFX_EINVAL.  Asynchronous on stream.
+ * Errors: EINVAL, ECUDA.
+ */
+hefx_status hefx_wait_check(hefx_ctx* ctx, const hefx_params* params, uint64_t limit_ns, int arrive, void* stream);
 
 #ifdef __cplusplus
 }

@@ -745,10 +745,18 @@ hefx_status hefx_poly_mul_noalloc(hefx_ctx* ctx, const hefx_params* p, const uin
     if ((st = use_device(ctx)) != HEFX_OK) return st;
     if (!tc_supported(p))
         return fail(ctx, HEFX_EUNSUPPORTED, "tensor path not available for N = 2^%u with these moduli", p->log2n);
-    if (!p->tc)
-        return fail(ctx, HEFX_EUNSUPPORTED,
-                    "tensor tables of these params are not built yet; make one tensor-path call "
-                    "(for example hefx_poly_mul with HEFX_PATH_TENSOR) before using the no-allocation variant");
+    if (p->red_ntt != HEFX_RED_SHOUP)
+        return fail(ctx, HEFX_EUNSUPPORTED, "hefx_poly_mul_noalloc uses the default (Shoup) NTT reduction only");
+    {
+        // the tables are built under tc_mu by the first tensor-path call (ensure_tc); once
+        // built they stay until hefx_params_destroy, so reading the pointer under the lock is
+        // enough
+        std::lock_guard<std::mutex> g(const_cast<hefx_params*>(p)->tc_mu);
+        if (!p->tc)
+            return fail(ctx, HEFX_EUNSUPPORTED,
+                        "tensor tables of these params are not built yet; make one tensor-path call "
+                        "(for example hefx_poly_mul with HEFX_PATH_TENSOR) before using the no-allocation variant");
+    }
     const size_t words = batch * p->nlimbs * (size_t)p->n;
     if (words > noalloc_scratch_words())
         return fail(ctx, HEFX_EINVAL,
@@ -784,6 +792,17 @@ hefx_status hefx_stream_check(hefx_ctx* ctx, const hefx_params* p, void* stream)
     if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "hefx_stream_check");
     if (code) return fail(ctx, HEFX_ETIMEOUT, "a bounded device wait expired (code %u); results are invalid", code);
+    return HEFX_OK;
+}
+
+hefx_status hefx_wait_check(hefx_ctx* ctx, const hefx_params* p, uint64_t limit_ns, int arrive, void* stream) {
+    if (!ctx) return HEFX_EINVAL;
+    if (!p || p->ctx != ctx) return fail(ctx, HEFX_EINVAL, "params is null or belongs to another context");
+    if (limit_ns > 2000000000ull) return fail(ctx, HEFX_EINVAL, "limit_ns above the 2 s wait limit of the kernels");
+    hefx_status st = use_device(ctx);
+    if (st != HEFX_OK) return st;
+    cudaError_t e = launch_wait_check(p->d_err_cc, limit_ns, arrive, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "hefx_wait_check launch");
     return HEFX_OK;
 }
 

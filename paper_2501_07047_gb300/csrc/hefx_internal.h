@@ -199,12 +199,9 @@ void bconv_plan_free(hefx_bconv_plan* plan);
 bool tc_supported(const hefx_params* p);
 cudaError_t tc_prepare(hefx_params* p);
 void tc_free(hefx_params* p);
-cudaError_t launch_ntt_tc(const hefx_params* p, NttMode mode, const uint32_t* in, const uint32_t* had, uint32_t* out,
-                          size_t batch, cudaStream_t stream);
-cudaError_t launch_polymul_tc(hefx_params* p, const uint32_t* a, const uint32_t* b, uint32_t* c, size_t batch,
-                              cudaStream_t stream);
 cudaError_t tc_check(const hefx_params* p, cudaStream_t stream, uint32_t* code);
 size_t noalloc_scratch_words();
+cudaError_t launch_wait_check(uint32_t* err, uint64_t limit_ns, int arrive, cudaStream_t stream);
 cudaError_t tc2_prepare(hefx_params* p);
 void tc2_free(hefx_params* p);
 uint32_t* tc2_err(const hefx_params* p);

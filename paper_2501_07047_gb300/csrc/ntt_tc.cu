@@ -1,6 +1,8 @@
-// Tensor-core NTT (path b): the layout-invariant 3-step negacyclic NTT of Sec. IV-B with
-// each modular matrix product recast by BAT (Sec. IV-A, Alg. 2) as a low-precision matrix
-// product on the tcgen05 tensor cores.
+// Tensor-core NTT (path b), single-pass form: the layout-invariant 3-step negacyclic NTT of
+// Sec. IV-B with each modular matrix product recast by BAT (Sec. IV-A, Alg. 2) as a
+// low-precision matrix product on the tcgen05 tensor cores.  The NTT entry points run the
+// pipelined form (ntt_tc2.cu); this one is kept for hefx_poly_mul_noalloc, whose steps
+// write their results in place and need no digit workspace.
 //
 // Math (N = R x C, data viewed as an R x C row-major matrix; Sec. IV-B2 formula with the
 // negacyclic pre-twist folded into the constants):
@@ -56,8 +58,6 @@ struct TensorTables {
     TcLimb* limbs = nullptr;                                   // [L]
     CUtensorMap maps[4];
     uint32_t* err = nullptr;                                   // device error flag
-    uint32_t* scratch = nullptr;                               // polynomial-product workspace
-    size_t scratch_words = 0;
 };
 
 namespace {
@@ -355,7 +355,6 @@ void tc_free(hefx_params* p) {
     if (t->Tinv) cudaFree(t->Tinv);
     if (t->limbs) cudaFree(t->limbs);
     if (t->err) cudaFree(t->err);
-    if (t->scratch) cudaFree(t->scratch);
     delete t;
     p->tc = nullptr;
 }
@@ -513,58 +512,6 @@ cudaError_t run_step(const hefx_params* p, TcStep step, int op, const uint32_t* 
 }
 
 }  // namespace
-
-cudaError_t launch_ntt_tc(const hefx_params* p, NttMode mode, const uint32_t* in, const uint32_t* had, uint32_t* out,
-                          size_t batch, cudaStream_t s) {
-    (void)had;
-    if (batch == 0) return cudaSuccess;
-    cudaError_t e;
-    if (mode == MODE_FWD) {
-        e = run_step(p, FWD1, OP_TW, in, nullptr, out, batch, s);
-        if (e == cudaSuccess) e = run_step(p, FWD3, OP_PLAIN, out, nullptr, out, batch, s);
-        return e;
-    }
-    if (mode == MODE_INV) {
-        e = run_step(p, INV1, OP_TW, in, nullptr, out, batch, s);
-        if (e == cudaSuccess) e = run_step(p, INV3, OP_PLAIN, out, nullptr, out, batch, s);
-        return e;
-    }
-    return cudaErrorNotSupported;
-}
-
-// c = INTT(NTT(a) o NTT(b)) on the tensor path.  The forward transform of the second factor
-// goes through a workspace held by the parameter set (grown on demand).
-cudaError_t launch_polymul_tc(hefx_params* p, const uint32_t* a, const uint32_t* b, uint32_t* c, size_t batch,
-                              cudaStream_t s) {
-    if (batch == 0) return cudaSuccess;
-    TensorTables* t = p->tc;
-    const size_t words = batch * p->nlimbs * (size_t)p->n;
-    if (t->scratch_words < words) {
-        cudaError_t e = cudaDeviceSynchronize();  // the old workspace may still be in use
-        if (e != cudaSuccess) return e;
-        if (t->scratch) cudaFree(t->scratch);
-        t->scratch = nullptr;
-        t->scratch_words = 0;
-        e = cudaMalloc(&t->scratch, words * 4);
-        if (e != cudaSuccess) return e;
-        t->scratch_words = words;
-    }
-    uint32_t* S = t->scratch;
-    cudaError_t e;
-    if (a == b) {
-        e = run_step(p, FWD1, OP_TW, a, nullptr, S, batch, s);
-        if (e == cudaSuccess) e = run_step(p, FWD3, OP_SQUARE, S, nullptr, c, batch, s);
-    } else {
-        if (c == b) std::swap(a, b);
-        e = run_step(p, FWD1, OP_TW, a, nullptr, c, batch, s);
-        if (e == cudaSuccess) e = run_step(p, FWD3, OP_PLAIN, c, nullptr, c, batch, s);  // c = NTT(a)
-        if (e == cudaSuccess) e = run_step(p, FWD1, OP_TW, b, nullptr, S, batch, s);
-        if (e == cudaSuccess) e = run_step(p, FWD3, OP_HAD, S, c, c, batch, s);          // c = NTT(b) o c
-    }
-    if (e == cudaSuccess) e = run_step(p, INV1, OP_TW, c, nullptr, c, batch, s);
-    if (e == cudaSuccess) e = run_step(p, INV3, OP_PLAIN, c, nullptr, c, batch, s);
-    return e;
-}
 
 // ------------------------------------------------------------------ no-allocation product
 // Workspace of hefx_poly_mul_noalloc: a fixed device array in the library image, so that

@@ -40,6 +40,7 @@ SIGNATURES = {
     "hefx_bconv_plan_destroy": (None, [_vp]),
     "hefx_basis_convert": (_i32, [_vp, _vp, _vp, _vp, _sz, _i32, _vp]),
     "hefx_stream_check": (_i32, [_vp, _vp, _vp]),
+    "hefx_wait_check": (_i32, [_vp, _vp, ctypes.c_uint64, _i32, _vp]),
     "hefx_vec_mod_mul": (_i32, [_vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "hefx_tensor_product": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "hefx_vec_mod_add": (_i32, [_vp, _vp, _vp, _vp, _vp, _sz, _vp]),
@@ -199,6 +200,10 @@ def hefx_basis_convert(ctx, plan, d_in, d_out, batch, path="auto", stream=None) 
 
 def hefx_stream_check(ctx, params, stream=None) -> None:
     _check(ctx, load().hefx_stream_check(ctx, params, _stream(stream)))
+
+
+def hefx_wait_check(ctx, params, limit_ns: int, arrive: bool, stream=None) -> None:
+    _check(ctx, load().hefx_wait_check(ctx, params, int(limit_ns), int(bool(arrive)), _stream(stream)))
 
 
 def hefx_vec_mod_mul(ctx, params, x, y, z, batch, stream=None) -> None:

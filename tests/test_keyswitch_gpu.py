@@ -210,9 +210,11 @@ def _he_mult_case(logn, L, K, alpha, seed, genuine_key):
 
 @pytest.mark.parametrize("logn,L,K,alpha,genuine,bconv", [(6, 5, 2, 2, True, "auto"), (10, 6, 3, 3, True, "auto"),
                                                            (8, 4, 4, 4, True, "auto"), (16, 24, 8, 8, False, "auto"),
+                                                           (16, 48, 16, 16, False, "auto"),
                                                            (10, 6, 3, 3, True, "tensor")])
 def test_he_mult_matches_oracle(hx, logn, L, K, alpha, genuine, bconv):
-    """bconv "auto": one-launch ModUp; "tensor": per-digit conversions on the tensor path."""
+    """bconv "auto": one-launch ModUp; "tensor": per-digit conversions on the tensor path.
+    (16, 48, 16, 16) is the shape bench.py times: (L, log q, dnum) = (48, 28, 3), K = 16."""
     hefx, ctx = hx
     from paper_2501_07047_gb300.hemult import HeMult
     qs, ps, s, evk, ins = _he_mult_case(logn, L, K, alpha, 64 + logn, genuine)

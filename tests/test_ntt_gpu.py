@@ -136,10 +136,21 @@ def test_edge_values(ctx, path):
 
 # ----------------------------------------------------------------------------- config 2 (full size)
 
+def oracle_rows(data, primes, inverse=False):
+    """oracle.ntt_batch over the polynomials of `data`, one thread per polynomial (the oracle's
+    C calls release the GIL)."""
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max_workers=8) as ex:
+        parts = list(ex.map(lambda b: oracle.ntt_batch(data[b:b + 1], primes, inverse=inverse), range(len(data))))
+    return np.concatenate(parts)
+
+
 @pytest.mark.parametrize("path", PATHS)
-def test_config2_full_size_sampled(ctx, path):
-    """N = 2^16, L = 24, batch 8: every output of three limbs in full, 256 sampled outputs by
-    the O(N) definition elsewhere, and INTT(NTT(x)) = x over the whole batch."""
+def test_config2_full_size(ctx, path):
+    """N = 2^16, L = 24, batch 8 (192 limb-NTTs, the bench launch): every output of the forward
+    transform and of the inverse of an arbitrary input against the oracle, 256 sampled forward
+    outputs against the O(N) definition (pinning the oracle itself at full size), and
+    INTT(NTT(x)) = x over the whole batch."""
     primes = inputs.source_primes(24)
     n = 1 << 16
     p = make_params(ctx, 16, primes)
@@ -151,14 +162,22 @@ def test_config2_full_size_sampled(ctx, path):
         hefx.hefx_ntt_fwd(ctx, p, d, 8, path)
         hefx.hefx_stream_check(ctx, p)
         got = to_host(d).reshape(data.shape)
-        for (b, l) in [(0, 0), (3, 11), (7, 23)]:
-            assert (got[b, l] == oracle.ntt(data[b, l], primes[l])).all()
+        want = oracle_rows(data, primes)
+        bad = np.argwhere(got != want)
+        assert bad.size == 0, f"{len(bad)} forward outputs differ, first at {bad[0]}"
         rng = np.random.default_rng(5)
         for _ in range(256):
             b, l, k = int(rng.integers(8)), int(rng.integers(24)), int(rng.integers(n))
-            assert got[b, l, k] == oracle.ntt_at(data[b, l], primes[l], k)
+            assert want[b, l, k] == oracle.ntt_at(data[b, l], primes[l], k)
         hefx.hefx_ntt_inv(ctx, p, d, 8, path)
         assert (to_host(d).reshape(data.shape) == data).all()
+        rnd = inputs.residue_tensor(inputs.derive_seed(2, 1), 8, primes, n)
+        d = to_dev(rnd)
+        hefx.hefx_ntt_inv(ctx, p, d, 8, path)
+        hefx.hefx_stream_check(ctx, p)
+        got = to_host(d).reshape(rnd.shape)
+        bad = np.argwhere(got != oracle_rows(rnd, primes, inverse=True))
+        assert bad.size == 0, f"{len(bad)} inverse outputs differ, first at {bad[0]}"
     finally:
         hefx.hefx_params_destroy(p)
 

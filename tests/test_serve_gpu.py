@@ -36,10 +36,13 @@ def oracle_request(ex, req):
     return [x.astype(np.uint32) for x in (d0, d1, e0, e1)]
 
 
-def test_request_matches_oracle(ctx):
+@pytest.mark.parametrize("logn,L,variant", [(13, 8, 1), (16, 36, 0)])
+def test_request_matches_oracle(ctx, logn, L, variant):
+    """The smallest request shape and the largest one of the serving sweep (N = 2^16, L = 36),
+    every output against the oracle composition."""
     ex = GpuExecutor(ctx, nstreams=2, seed=9)
     try:
-        req = Request(0, 13, 8, 0.0, variant=1)
+        req = Request(0, logn, L, 0.0, variant=variant)
         st = serve([req], ex, keep_outputs=True)
         assert st["completed"] == 1
         for got, exp in zip(req.outputs, oracle_request(ex, req)):
