@@ -40,6 +40,25 @@ namespace cc {
 // of eight consecutive rows land on different banks: both patterns are conflict free.
 __device__ __forceinline__ int swz(int j) { return j ^ (((j >> 5) & 7) << 2); }
 
+// Word of element j0 + (k << logs) (k < 2^R) of a register pass's sub-transform in the
+// swizzled buffer, j0 = row * m + jb the sub-transform's first element.  Equal to
+// swz(j0 + (k << logs)) under each branch's condition, but written so that the per-element
+// part is a compile-time offset (logs >= 8), one XOR with a constant (logs == 5: bits 5-7 of
+// j0 are zero for one-row CTAs and R >= 3), or one XOR per 16-byte chunk (logs == 0: the
+// sub-transform is 2^R-aligned inside one 32-word row).
+template <int R, int logs, int ROWS>
+__device__ __forceinline__ int swz_elem(int j0, int k) {
+    if constexpr (logs >= 8) {
+        return swz(j0) + (k << logs);
+    } else if constexpr (logs == 5 && R >= 3 && ROWS == 1) {
+        return (j0 ^ ((k & 7) << 2)) + (k << 5);
+    } else if constexpr (logs == 0 && R >= 2 && R <= 5) {
+        return (j0 & ~31) + (k ^ ((j0 & 31) ^ (((j0 >> 5) & 7) << 2)));
+    } else {
+        return swz(j0 + (k << logs));
+    }
+}
+
 // Tuning knobs: log2 of the CTAs per row at N = 2^17 .. 2^14 (2^13 elements per CTA below
 // N = 2^17), the threads of a CTA that holds less than 2^15 elements of a split row, and the
 // CTAs per SM its register budget is sized for (N = 2^17: 2^14 elements and 64 KiB per CTA).
@@ -167,10 +186,11 @@ __device__ __forceinline__ void load_elems(uint32_t (&x)[1 << R], const uint32_t
     using C = Cfg<LOGN>;
     constexpr int N = 1 << LOGN;
     if constexpr (SRC == SRC_SMEM) {
+        const int j0 = row * C::m + jb;
         if constexpr (logs == 0 && R >= 2) {
 #pragma unroll
             for (int k = 0; k < (1 << R); k += 4) {
-                const uint4 v = *reinterpret_cast<const uint4*>(&sm[swz(row * C::m + jb + k)]);
+                const uint4 v = *reinterpret_cast<const uint4*>(&sm[swz_elem<R, logs, C::rows>(j0, k)]);
                 x[k] = v.x;
                 x[k + 1] = v.y;
                 x[k + 2] = v.z;
@@ -178,7 +198,7 @@ __device__ __forceinline__ void load_elems(uint32_t (&x)[1 << R], const uint32_t
             }
         } else {
 #pragma unroll
-            for (int k = 0; k < (1 << R); ++k) x[k] = sm[swz(row * C::m + jb + (k << logs))];
+            for (int k = 0; k < (1 << R); ++k) x[k] = sm[swz_elem<R, logs, C::rows>(j0, k)];
         }
     } else {
         const bool valid = row < sg.nrows;
@@ -222,19 +242,22 @@ __device__ __forceinline__ void store_elems(const uint32_t (&x)[1 << R], uint32_
     constexpr int N = 1 << LOGN;
     if constexpr (DST == DST_SMEM_REDUCE) {  // canonical values into the swizzled buffer (TMA store)
         static_assert(logs == 0 && R >= 2, "the smallest-stride pass");
+        const int j0 = row * C::m + jb;
 #pragma unroll
         for (int k = 0; k < (1 << R); k += 4)
-            *reinterpret_cast<uint4*>(&sm[swz(row * C::m + jb + k)]) =
+            *reinterpret_cast<uint4*>(&sm[swz_elem<R, logs, C::rows>(j0, k)]) =
                 make_uint4(reduce_out<F>(x[k], lc), reduce_out<F>(x[k + 1], lc), reduce_out<F>(x[k + 2], lc),
                            reduce_out<F>(x[k + 3], lc));
     } else if constexpr (DST == DST_SMEM) {
+        const int j0 = row * C::m + jb;
         if constexpr (logs == 0 && R >= 2) {
 #pragma unroll
             for (int k = 0; k < (1 << R); k += 4)
-                *reinterpret_cast<uint4*>(&sm[swz(row * C::m + jb + k)]) = make_uint4(x[k], x[k + 1], x[k + 2], x[k + 3]);
+                *reinterpret_cast<uint4*>(&sm[swz_elem<R, logs, C::rows>(j0, k)]) =
+                    make_uint4(x[k], x[k + 1], x[k + 2], x[k + 3]);
         } else {
 #pragma unroll
-            for (int k = 0; k < (1 << R); ++k) sm[swz(row * C::m + jb + (k << logs))] = x[k];
+            for (int k = 0; k < (1 << R); ++k) sm[swz_elem<R, logs, C::rows>(j0, k)] = x[k];
         }
     } else {
         if (row >= sg.nrows) return;
@@ -310,12 +333,13 @@ __device__ __forceinline__ void fwd_stages(uint32_t (&x)[1 << R], uint32_t g0, c
         const int half = 1 << (R - 1 - v);
         const bool corr = !LAZY || fwd_bound_in(s0 + v) + 2 > 16;
         uint2 w = make_uint2(0, 0);
+        // one base pointer per stage: the loads below have compile-time offsets
+        const uint2* base = PERM ? tw + g0 + (1u << (s0 + v)) : tw + (1u << (s0 + v)) + ((size_t)g0 << v);
 #pragma unroll
         for (int b = 0; b < (1 << (R - 1)); ++b) {
             const int g = b >> (R - 1 - v);
             const int k = (g << (R - v)) + (b & (half - 1));
-            if ((b & (half - 1)) == 0)
-                w = __ldg(&tw[PERM ? (1u << (s0 + v)) + ((uint32_t)g << s0) + g0 : (1u << (s0 + v)) + (g0 << v) + g]);
+            if ((b & (half - 1)) == 0) w = __ldg(base + (PERM ? (g << s0) : g));
             const uint32_t xa = !corr ? x[k] : (LAZY ? mul_shoup_lazy(x[k], 1u, lc.one_sh, q) : csub(x[k], two_q));
             const uint32_t t = twmul<F>(x[k + half], w, lc);
             x[k] = xa + t;
@@ -355,18 +379,113 @@ __device__ __forceinline__ void inv_stages(uint32_t (&x)[1 << R], uint32_t gbase
             }
             continue;
         }
-        const uint32_t hbase = (uint32_t)(N >> (e + 1)) + (gbase >> (e + 1)) + ((uint32_t)j_hi << (R - v - 1));
+        const uint2* base = PERM ? tw + (uint32_t)(N >> (e + 1)) + J
+                                 : tw + (uint32_t)(N >> (e + 1)) + (gbase >> (e + 1)) + ((uint32_t)j_hi << (R - v - 1));
         uint2 w = make_uint2(0, 0);
 #pragma unroll
         for (int b = 0; b < (1 << (R - 1)); ++b) {
             const int g = b >> v;
             const int k = (g << (v + 1)) + (b & (h - 1));
-            if ((b & (h - 1)) == 0)
-                w = __ldg(&tw[PERM ? (uint32_t)(N >> (e + 1)) + ((uint32_t)g << (LOGN - R)) + J : hbase + g]);
+            if ((b & (h - 1)) == 0) w = __ldg(base + (PERM ? (g << (LOGN - R)) : g));
             const uint32_t X = x[k], Y = x[k + h];
             const uint32_t sum = X + Y;
             x[k] = !red ? sum : (LAZY ? mul_shoup_lazy(sum, 1u, lc.one_sh, q) : csub(sum, two_q));
             x[k + h] = twmul<F>(X - Y + cq, w, lc);
+        }
+    }
+}
+
+// Twiddles of R forward stages s0 .. s0+R-1 for one sub-transform, loaded up front:
+// w[2^v - 1 + g] is stage s0+v's twiddle for group g (the ones fwd_stages loads one by one).
+// The table is read through one base pointer per stage so that every load of a stage has a
+// compile-time offset.
+template <int R, int LOGN, int s0>
+__device__ __forceinline__ void load_tw_fwd(uint2 (&w)[(1 << R) - 1], uint32_t g0, const uint2* tw) {
+    constexpr bool PERM = (s0 + R == LOGN);
+#pragma unroll
+    for (int v = 0; v < R; ++v) {
+        const uint2* base = PERM ? tw + g0 + (1u << (s0 + v)) : tw + (1u << (s0 + v)) + ((size_t)g0 << v);
+#pragma unroll
+        for (int g = 0; g < (1 << v); ++g) w[(1 << v) - 1 + g] = __ldg(base + (PERM ? (g << s0) : g));
+    }
+}
+
+// fwd_stages on preloaded twiddles.
+template <int R, int LOGN, int s0, int F>
+__device__ __forceinline__ void fwd_stages_w(uint32_t (&x)[1 << R], const uint2 (&w)[(1 << R) - 1],
+                                             const LimbConst& lc) {
+    constexpr bool LAZY = (F & 2) != 0;
+    const uint32_t q = lc.q, two_q = 2 * q;
+#pragma unroll
+    for (int v = 0; v < R; ++v) {
+        const int half = 1 << (R - 1 - v);
+        const bool corr = !LAZY || fwd_bound_in(s0 + v) + 2 > 16;
+#pragma unroll
+        for (int b = 0; b < (1 << (R - 1)); ++b) {
+            const int g = b >> (R - 1 - v);
+            const int k = (g << (R - v)) + (b & (half - 1));
+            const uint32_t xa = !corr ? x[k] : (LAZY ? mul_shoup_lazy(x[k], 1u, lc.one_sh, q) : csub(x[k], two_q));
+            const uint32_t t = twmul<F>(x[k + half], w[(1 << v) - 1 + g], lc);
+            x[k] = xa + t;
+            x[k + half] = xa - t + two_q;
+        }
+    }
+}
+
+// Offset of inverse stage v's twiddles in the preloaded array (stage v has 2^(R-1-v) groups).
+__host__ __device__ constexpr int inv_tw_off(int R, int v) { return (1 << R) - (1 << (R - v)); }
+
+// Twiddles of R inverse stages e0 .. e0+R-1 for one sub-transform (those inv_stages loads one
+// by one; the scaled last stage takes its constants from LimbConst and has no entry).
+template <int R, int LOGN, int SCALE, int e0>
+__device__ __forceinline__ void load_tw_inv(uint2 (&w)[(1 << R) - 1], uint32_t gbase, int j_hi, const uint2* tw) {
+    constexpr int N = 1 << LOGN;
+    constexpr bool PERM = (e0 == 0);
+    const uint32_t J = (gbase >> R) + (uint32_t)j_hi;
+#pragma unroll
+    for (int v = 0; v < R; ++v) {
+        const int e = e0 + v;
+        if (SCALE && e == LOGN - 1) continue;
+        const uint2* base = PERM ? tw + (uint32_t)(N >> (e + 1)) + J
+                                 : tw + (uint32_t)(N >> (e + 1)) + (gbase >> (e + 1)) + ((uint32_t)j_hi << (R - v - 1));
+#pragma unroll
+        for (int g = 0; g < (1 << (R - 1 - v)); ++g)
+            w[inv_tw_off(R, v) + g] = __ldg(base + (PERM ? (g << (LOGN - R)) : g));
+    }
+}
+
+// inv_stages on preloaded twiddles.
+template <int R, int LOGN, int SCALE, int e0, int F>
+__device__ __forceinline__ void inv_stages_w(uint32_t (&x)[1 << R], const uint2 (&w)[(1 << R) - 1],
+                                             const LimbConst& lc) {
+    constexpr bool LAZY = (F & 2) != 0;
+    const uint32_t q = lc.q, two_q = 2 * q;
+#pragma unroll
+    for (int v = 0; v < R; ++v) {
+        const int e = e0 + v;
+        const int h = 1 << v;
+        const uint32_t cq = LAZY ? (uint32_t)inv_bound_in(e) * q : two_q;
+        const bool red = !LAZY || 2 * inv_bound_in(e) > 8;
+        if (SCALE && e == LOGN - 1) {
+            const uint32_t s = SCALE == 1 ? lc.ninv : lc.ninvR, ssh = SCALE == 1 ? lc.ninv_sh : lc.ninvR_sh;
+            const uint32_t wv = SCALE == 1 ? lc.ninvw : lc.ninvRw, wsh = SCALE == 1 ? lc.ninvw_sh : lc.ninvRw_sh;
+#pragma unroll
+            for (int kk = 0; kk < (1 << (R - 1)); ++kk) {
+                const uint32_t X = x[kk], Y = x[kk + h];
+                const uint32_t s0v = mul_shoup_lazy(X + Y, s, ssh, q), s1v = mul_shoup_lazy(X - Y + cq, wv, wsh, q);
+                x[kk] = csub(s0v, q);
+                x[kk + h] = csub(s1v, q);
+            }
+            continue;
+        }
+#pragma unroll
+        for (int b = 0; b < (1 << (R - 1)); ++b) {
+            const int g = b >> v;
+            const int k = (g << (v + 1)) + (b & (h - 1));
+            const uint32_t X = x[k], Y = x[k + h];
+            const uint32_t sum = X + Y;
+            x[k] = !red ? sum : (LAZY ? mul_shoup_lazy(sum, 1u, lc.one_sh, q) : csub(sum, two_q));
+            x[k + h] = twmul<F>(X - Y + cq, w[inv_tw_off(R, v) + g], lc);
         }
     }
 }
@@ -379,20 +498,41 @@ __device__ __forceinline__ void fwd_pass(uint32_t* sm, const Seg& sg, const KArg
     constexpr int logtl = LOGN - s0 - R;  // log2 of the smallest stride of the pass
     constexpr int lognsub = C::logm - R;
     constexpr int nsub = 1 << lognsub;
-    for (int u = threadIdx.x; u < C::rows * nsub; u += C::threads) {
-        const int row = C::rows == 1 ? 0 : u >> lognsub;
-        const int uu = u & (nsub - 1);
-        const int j_lo = uu & ((1 << logtl) - 1);
-        const int j_hi = uu >> logtl;
-        const int jb = (j_hi << (logtl + R)) + j_lo;
-        const uint32_t g0 = (sg.gbase >> (logtl + R)) + (uint32_t)j_hi;
-        const uint32_t limb = row_limb<F>(a, row < sg.nrows ? sg.row0 + row : sg.row0);
+    if constexpr (R <= 4 && C::rows == 1) {
+        // one row: every sub-transform shares the limb; each sub-transform's twiddles are all
+        // requested before its data is read, so their latency is paid once per sub-transform
+        // rather than once per stage
+        const uint32_t limb = row_limb<F>(a, sg.row0);
         const LimbConst& lc = a.lc[limb];
         const uint2* tw = a.tw_f + (size_t)limb * N;
-        uint32_t x[1 << R];
-        load_elems<R, LOGN, logtl, SRC, F>(x, sm, a, sg, row, jb, lc);
-        fwd_stages<R, LOGN, s0, F>(x, g0, tw, lc);
-        store_elems<R, LOGN, logtl, DST, F>(x, sm, a, sg, row, jb, lc);
+#pragma unroll 1
+        for (int u = threadIdx.x; u < nsub; u += C::threads) {
+            uint2 w[(1 << R) - 1];
+            load_tw_fwd<R, LOGN, s0>(w, (sg.gbase >> (logtl + R)) + (uint32_t)(u >> logtl), tw);
+            const int j_lo = u & ((1 << logtl) - 1);
+            const int j_hi = u >> logtl;
+            const int jb = (j_hi << (logtl + R)) + j_lo;
+            uint32_t x[1 << R];
+            load_elems<R, LOGN, logtl, SRC, F>(x, sm, a, sg, 0, jb, lc);
+            fwd_stages_w<R, LOGN, s0, F>(x, w, lc);
+            store_elems<R, LOGN, logtl, DST, F>(x, sm, a, sg, 0, jb, lc);
+        }
+    } else {
+        for (int u = threadIdx.x; u < C::rows * nsub; u += C::threads) {
+            const int row = C::rows == 1 ? 0 : u >> lognsub;
+            const int uu = u & (nsub - 1);
+            const int j_lo = uu & ((1 << logtl) - 1);
+            const int j_hi = uu >> logtl;
+            const int jb = (j_hi << (logtl + R)) + j_lo;
+            const uint32_t g0 = (sg.gbase >> (logtl + R)) + (uint32_t)j_hi;
+            const uint32_t limb = row_limb<F>(a, row < sg.nrows ? sg.row0 + row : sg.row0);
+            const LimbConst& lc = a.lc[limb];
+            const uint2* tw = a.tw_f + (size_t)limb * N;
+            uint32_t x[1 << R];
+            load_elems<R, LOGN, logtl, SRC, F>(x, sm, a, sg, row, jb, lc);
+            fwd_stages<R, LOGN, s0, F>(x, g0, tw, lc);
+            store_elems<R, LOGN, logtl, DST, F>(x, sm, a, sg, row, jb, lc);
+        }
     }
 }
 
@@ -403,19 +543,38 @@ __device__ __forceinline__ void inv_pass(uint32_t* sm, const Seg& sg, const KArg
     constexpr int N = 1 << LOGN;
     constexpr int lognsub = C::logm - R;
     constexpr int nsub = 1 << lognsub;
-    for (int u = threadIdx.x; u < C::rows * nsub; u += C::threads) {
-        const int row = C::rows == 1 ? 0 : u >> lognsub;
-        const int uu = u & (nsub - 1);
-        const int j_lo = uu & ((1 << e0) - 1);
-        const int j_hi = uu >> e0;
-        const int jb = (j_hi << (e0 + R)) + j_lo;
-        const uint32_t limb = row_limb<F>(a, row < sg.nrows ? sg.row0 + row : sg.row0);
+    if constexpr (R <= 4 && C::rows == 1) {
+        // as fwd_pass: a sub-transform's twiddles are all requested before its data is read
+        const uint32_t limb = row_limb<F>(a, sg.row0);
         const LimbConst& lc = a.lc[limb];
         const uint2* tw = a.tw_i + (size_t)limb * N;
-        uint32_t x[1 << R];
-        load_elems<R, LOGN, e0, SRC, F>(x, sm, a, sg, row, jb, lc);
-        inv_stages<R, LOGN, SCALE, e0, F>(x, sg.gbase, j_hi, tw, lc);
-        store_elems<R, LOGN, e0, DST, F>(x, sm, a, sg, row, jb, lc);
+#pragma unroll 1
+        for (int u = threadIdx.x; u < nsub; u += C::threads) {
+            uint2 w[(1 << R) - 1];
+            load_tw_inv<R, LOGN, SCALE, e0>(w, sg.gbase, u >> e0, tw);
+            const int j_lo = u & ((1 << e0) - 1);
+            const int j_hi = u >> e0;
+            const int jb = (j_hi << (e0 + R)) + j_lo;
+            uint32_t x[1 << R];
+            load_elems<R, LOGN, e0, SRC, F>(x, sm, a, sg, 0, jb, lc);
+            inv_stages_w<R, LOGN, SCALE, e0, F>(x, w, lc);
+            store_elems<R, LOGN, e0, DST, F>(x, sm, a, sg, 0, jb, lc);
+        }
+    } else {
+        for (int u = threadIdx.x; u < C::rows * nsub; u += C::threads) {
+            const int row = C::rows == 1 ? 0 : u >> lognsub;
+            const int uu = u & (nsub - 1);
+            const int j_lo = uu & ((1 << e0) - 1);
+            const int j_hi = uu >> e0;
+            const int jb = (j_hi << (e0 + R)) + j_lo;
+            const uint32_t limb = row_limb<F>(a, row < sg.nrows ? sg.row0 + row : sg.row0);
+            const LimbConst& lc = a.lc[limb];
+            const uint2* tw = a.tw_i + (size_t)limb * N;
+            uint32_t x[1 << R];
+            load_elems<R, LOGN, e0, SRC, F>(x, sm, a, sg, row, jb, lc);
+            inv_stages<R, LOGN, SCALE, e0, F>(x, sg.gbase, j_hi, tw, lc);
+            store_elems<R, LOGN, e0, DST, F>(x, sm, a, sg, row, jb, lc);
+        }
     }
 }
 
@@ -542,18 +701,40 @@ __device__ __forceinline__ void fwd_cross_pass(uint32_t* sm, const Seg& sg, cons
         rin = a.in + (b * a.in_rows + limb) * (size_t)N;
         rlast = a.in + (b * a.in_rows + a.in_rows - 1) * (size_t)N;
     }
+    // the stages' twiddles are the same for every position: loaded once
+    uint2 w[P - 1];
+    load_tw_fwd<C::logP, LOGN, 0>(w, 0u, tw);
+    // every input of every iteration is requested before the first is used (one DRAM round
+    // trip; the cluster stores below are ordered memory operations the loads cannot pass)
+    constexpr int PRE = RS ? 1 : ITERS;
+    uint4 vin[PRE][P];
+    if constexpr (PRE > 1) {
+#pragma unroll
+        for (int it = 0; it < ITERS; ++it) {
+            const int j = (int)sg.part * share + (it * C::threads + (int)threadIdx.x) * 4;
+#pragma unroll
+            for (int t = 0; t < P; ++t) vin[it][t] = __ldg(reinterpret_cast<const uint4*>(rin + j + t * C::m));
+        }
+    }
+#pragma unroll
     for (int it = 0; it < ITERS; ++it) {
         const int j = (int)sg.part * share + (it * C::threads + (int)threadIdx.x) * 4;
         uint4 v[P];
+        if constexpr (PRE == 1) {
 #pragma unroll
-        for (int t = 0; t < P; ++t) v[t] = __ldg(reinterpret_cast<const uint4*>(rin + j + t * C::m));
+            for (int t = 0; t < P; ++t) v[t] = __ldg(reinterpret_cast<const uint4*>(rin + j + t * C::m));
+        }
         if constexpr (RS) {
 #pragma unroll
             for (int t = 0; t < P; ++t) {
-                const uint4 w = __ldg(reinterpret_cast<const uint4*>(rlast + j + t * C::m));
-                v[t] = make_uint4(rescale_one(v[t].x, w.x, lc), rescale_one(v[t].y, w.y, lc),
-                                  rescale_one(v[t].z, w.z, lc), rescale_one(v[t].w, w.w, lc));
+                const uint4 wl = __ldg(reinterpret_cast<const uint4*>(rlast + j + t * C::m));
+                v[t] = make_uint4(rescale_one(v[t].x, wl.x, lc), rescale_one(v[t].y, wl.y, lc),
+                                  rescale_one(v[t].z, wl.z, lc), rescale_one(v[t].w, wl.w, lc));
             }
+        }
+        if constexpr (PRE > 1) {
+#pragma unroll
+            for (int t = 0; t < P; ++t) v[t] = vin[it][t];
         }
         uint32_t x[4][P];
 #pragma unroll
@@ -564,7 +745,7 @@ __device__ __forceinline__ void fwd_cross_pass(uint32_t* sm, const Seg& sg, cons
             x[3][t] = v[t].w;
         }
 #pragma unroll
-        for (int c = 0; c < 4; ++c) fwd_stages<C::logP, LOGN, 0, F>(x[c], 0u, tw, lc);
+        for (int c = 0; c < 4; ++c) fwd_stages_w<C::logP, LOGN, 0, F>(x[c], w, lc);
 #pragma unroll
         for (int t = 0; t < P; ++t) st_cluster4(dst[t] + 4u * swz(j), make_uint4(x[0][t], x[1][t], x[2][t], x[3][t]));
     }
@@ -590,21 +771,29 @@ __device__ __forceinline__ void inv_cross_pass(uint32_t* sm, const Seg& sg, cons
     const LimbConst& lc = a.lc[limb];
     const uint2* tw = a.tw_i + (size_t)limb * N;
     uint32_t* out = row_out<N, F>(a, sg.row0);
+    // twiddles shared by every position, and every peer read of every iteration, first
+    uint2 w[P - 1];
+    load_tw_inv<C::logP, LOGN, SCALE, LOGN - C::logP>(w, 0u, 0, tw);
+    uint4 vin[ITERS][P];
+#pragma unroll
     for (int it = 0; it < ITERS; ++it) {
         const int j = (int)sg.part * share + (it * C::threads + (int)threadIdx.x) * 4;
-        uint4 v[P];
 #pragma unroll
-        for (int t = 0; t < P; ++t) v[t] = ld_cluster4(src[t] + 4u * swz(j));
+        for (int t = 0; t < P; ++t) vin[it][t] = ld_cluster4(src[t] + 4u * swz(j));
+    }
+#pragma unroll
+    for (int it = 0; it < ITERS; ++it) {
+        const int j = (int)sg.part * share + (it * C::threads + (int)threadIdx.x) * 4;
         uint32_t x[4][P];
 #pragma unroll
         for (int t = 0; t < P; ++t) {
-            x[0][t] = v[t].x;
-            x[1][t] = v[t].y;
-            x[2][t] = v[t].z;
-            x[3][t] = v[t].w;
+            x[0][t] = vin[it][t].x;
+            x[1][t] = vin[it][t].y;
+            x[2][t] = vin[it][t].z;
+            x[3][t] = vin[it][t].w;
         }
 #pragma unroll
-        for (int c = 0; c < 4; ++c) inv_stages<C::logP, LOGN, SCALE, LOGN - C::logP, F>(x[c], 0u, 0, tw, lc);
+        for (int c = 0; c < 4; ++c) inv_stages_w<C::logP, LOGN, SCALE, LOGN - C::logP, F>(x[c], w, lc);
 #pragma unroll
         for (int t = 0; t < P; ++t)
             *reinterpret_cast<uint4*>(out + j + t * C::m) = make_uint4(x[0][t], x[1][t], x[2][t], x[3][t]);
