@@ -165,25 +165,38 @@ class ClockSampler:
 # ----------------------------------------------------------------------------- CPU oracle
 
 def _oracle_worker(args):
-    seed, budget_s, primes = args
+    kind, seed, budget_s, primes = args
     import oracle as orc
     from paper_2501_07047_gb300 import inputs
     done = 0
     t0 = time.perf_counter()
     i = 0
     while time.perf_counter() - t0 < budget_s:
-        q = primes[i % len(primes)]
-        a = inputs.uniform_residues(inputs.derive_seed(seed, i), N, q)
-        ahat = orc.ntt(a, q)
-        orc.intt(ahat, q)
-        done += 2
+        if kind == "ntt":  # forward + inverse limb-NTT pair
+            q = primes[i % len(primes)]
+            a = inputs.uniform_residues(inputs.derive_seed(seed, i), N, q)
+            orc.intt(orc.ntt(a, q), q)
+            done += 2
+        elif kind == "polymul":  # one N = 2^16 limb product (NTT, Hadamard, INTT)
+            q = primes[i % len(primes)]
+            a = inputs.uniform_residues(inputs.derive_seed(seed, i, 0), N, q)
+            b = inputs.uniform_residues(inputs.derive_seed(seed, i, 1), N, q)
+            orc.polymul(a, b, q)
+            done += 1
+        else:  # basis conversion of 2^12 coefficients, 24 -> 8 limbs (config 3's shape)
+            qs, ps = primes[:24], inputs.special_primes(8)
+            x = inputs.residue_tensor(inputs.derive_seed(seed, i), 1, qs, 4096)[0]
+            orc.bconv(x, qs, ps)
+            done += 4096
         i += 1
     return done, time.perf_counter() - t0
 
 
-def time_oracle(budget_s: float, cores: int | None = None):
-    """Runs the oracle's forward + inverse N = 2^16 limb-NTTs on every host core (spawned
-    processes) for a bounded time and returns limb-NTTs/s over all cores."""
+def time_oracle(budget_s: float, cores: int | None = None, kind: str = "ntt"):
+    """Runs the oracle on every host core (spawned processes, one per core) for a bounded time
+    and returns the throughput over all cores: forward + inverse N = 2^16 limb-NTTs (kind
+    "ntt", the headline unit), N = 2^16 limb products ("polymul") or 24 -> 8 basis-conversion
+    coefficients ("bconv")."""
     import oracle as orc
     orc.build()
     from paper_2501_07047_gb300 import inputs
@@ -192,13 +205,23 @@ def time_oracle(budget_s: float, cores: int | None = None):
     ctx = mp.get_context("spawn")
     t0 = time.perf_counter()
     with ctx.Pool(cores) as pool:
-        res = pool.map(_oracle_worker, [(1000 + w, budget_s, primes) for w in range(cores)])
+        res = pool.map(_oracle_worker, [(kind, 1000 + w, budget_s, primes) for w in range(cores)])
     wall = time.perf_counter() - t0
     units = sum(r[0] for r in res)
     longest = max(r[1] for r in res)
-    return {"value": units / longest, "unit": "limb-NTT/s", "cores": cores, "kind": "oracle",
-            "sample": f"{units} N=2^16 limb-NTTs (forward+inverse pairs over the 24 limb primes) in "
-                      f"{longest:.1f} s per core, {cores} processes, wall {wall:.1f} s"}
+    unit, what = {"ntt": ("limb-NTT/s", "N=2^16 limb-NTTs (forward+inverse pairs over the 24 limb primes)"),
+                  "polymul": ("limb-products/s", "N=2^16 limb products (NTT, Hadamard, INTT)"),
+                  "bconv": ("coeffs/s", "basis-conversion coefficients (24 -> 8 limbs)")}[kind]
+    return {"value": units / longest, "unit": unit, "cores": cores, "kind": "oracle",
+            "sample": f"{units} {what} in {longest:.1f} s per core, {cores} processes, wall {wall:.1f} s"}
+
+
+def cpu_baseline_extra(budget_s: float):
+    """The oracle's other units (SURVEY 8(d) CPU plan): one-thread limb-NTT/s, and limb
+    products and basis-conversion coefficients per second on every core."""
+    return {"ntt_1_thread": time_oracle(budget_s, cores=1, kind="ntt"),
+            "polymul_all_cores": time_oracle(budget_s, kind="polymul"),
+            "bconv_all_cores": time_oracle(budget_s, kind="bconv")}
 
 
 # ----------------------------------------------------------------------------- GPU arm
@@ -226,9 +249,10 @@ def run_gpu(args):
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     # start the CPU-baseline pool (spawn) before the first CUDA call
-    cpu_baseline = None
+    cpu_baseline = cpu_extra = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu_baseline = time_oracle(args.cpu_seconds)
+        cpu_extra = cpu_baseline_extra(max(1.0, args.cpu_seconds / 4))
 
     build.build()
     torch.cuda.set_device(local)
@@ -371,6 +395,7 @@ def run_gpu(args):
     }
     if cpu_baseline:
         line["cpu_baseline"] = cpu_baseline
+        line["cpu_baseline_other_units"] = cpu_extra
     hefx.hefx_params_destroy(params)
     del data, data0, flush
     torch.cuda.empty_cache()
@@ -379,7 +404,7 @@ def run_gpu(args):
                 "reduction_ablation": bench_reduction_ablation}
         chosen = [k for k in runs if args.extras is None or k in args.extras.split(",")]
         line["extra"] = {k: runs[k](ctx, args) for k in chosen}
-        if args.serve:
+        if not args.no_serve and (args.extras is None or "serving_config5" in args.extras.split(",")):
             line["extra"]["serving_config5"] = bench_serving(ctx, args)
     hefx.hefx_destroy(ctx)
     if rank == 0:
@@ -614,10 +639,12 @@ def run_reference(args):
     if rank != 0:
         return
     per = []
+    # each step is a bounded sample; the whole --steps K --warmup W run stays near two minutes
+    step_s = min(args.cpu_seconds, max(1.0, 120.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
-        time_oracle(min(2.0, args.cpu_seconds / 4))
+        time_oracle(min(1.0, step_s))
     for _ in range(args.steps):
-        per.append(time_oracle(args.cpu_seconds))
+        per.append(time_oracle(step_s))
     value = statistics.median(p["value"] for p in per)
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "limb-NTT/s", "n_gpus": world, "steps": args.steps,
@@ -644,7 +671,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the BConv and batch measurements")
     ap.add_argument("--extras", default=None,
                     help="comma-separated subset of bconv_config3,batch_config4,he_mult,reduction_ablation")
-    ap.add_argument("--serve", action="store_true", help="also run the serving arrival-rate sweep")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving arrival-rate sweep")
     args = ap.parse_args()
     if args.impl == "reference":
         if args.steps > 5:
