@@ -457,6 +457,38 @@ def bench_bconv(ctx, args):
                      "hbm_frac": round(gbs / hbm, 4)}
     out["peak"] = f"{hbm} GB/s ({src} hbm_gbs)"
     hefx.hefx_bconv_plan_destroy(plan)
+    del dx, dy
+    # the paper's skewed conversion shapes (N = 2^16, one polynomial and a batch of 8), both paths
+    shapes = {}
+    for Lq2, Lp2 in ((12, 28), (12, 36), (16, 40), (24, 56)):
+        qs2, ps2 = inputs.source_primes(Lq2), inputs.special_primes(Lp2)
+        plan2 = hefx.hefx_bconv_plan_create(ctx, logn, qs2, ps2)
+        row = {}
+        for B2 in (1, 8):
+            x2 = inputs.residue_tensor(inputs.derive_seed(3, Lq2, Lp2), B2, qs2, n)
+            dx2 = torch.from_numpy(x2.view(np.int32).copy()).cuda()
+            dy2 = torch.empty((B2, Lp2, n), dtype=torch.int32, device="cuda")
+            ref2 = None
+            for path in ("cudacore", "tensor"):
+                st = hefx.raw_status("hefx_basis_convert", ctx, plan2, dx2.data_ptr(), dy2.data_ptr(), 0,
+                                     hefx.PATHS[path], s.cuda_stream)
+                if st != hefx.HEFX_OK:
+                    row[f"{path}_b{B2}_us"] = None
+                    continue
+                hefx.hefx_basis_convert(ctx, plan2, dx2, dy2, B2, path, s)
+                torch.cuda.synchronize()
+                if ref2 is None:
+                    ref2 = dy2.clone()
+                assert torch.equal(dy2, ref2), "paths disagree"
+                for _ in range(3):
+                    hefx.hefx_basis_convert(ctx, plan2, dx2, dy2, B2, path, s)
+                ms = _events_time(lambda: hefx.hefx_basis_convert(ctx, plan2, dx2, dy2, B2, path, s),
+                                  max(5, args.steps // 2), flush, s)
+                row[f"{path}_b{B2}_us"] = round(ms * 1e3, 2)
+        shapes[f"{Lq2}->{Lp2}"] = row
+        hefx.hefx_bconv_plan_destroy(plan2)
+    out["paper_shapes_n65536"] = shapes
+    out["paper_context_us"] = "TPU v6e one tensor core, BAT: 12->28 135.91, 12->36 147.28, 16->40 65.77, 24->56 94.67"
     return out
 
 

@@ -192,10 +192,13 @@ void hefx_bconv_plan_destroy(hefx_bconv_plan* plan);
  * d_out[batch][Lp][n] = BConv(d_in[batch][L][n]).  d_out must not overlap d_in.
  * HEFX_PATH_TENSOR runs step 2 as a digit-split matrix product on the tensor cores
  * (Sec. IV-A3, "High-Precision MatModMul in BConv"); HEFX_PATH_CUDACORE as 64-bit
- * multiply-accumulates.  Results are identical.  HEFX_PATH_AUTO takes the tensor path only
- * when the plan has it, Lp > 8 (the CUDA-core kernel makes one pass over the sources per 8
- * targets) and batch * L * n >= 96 * 2^16 (smaller calls are latency-bound, where the
- * CUDA-core kernel measured faster); otherwise the CUDA-core path.
+ * multiply-accumulates.  Results are identical.  The plan has the tensor path when every
+ * source prime is below 2^28, L <= 48, Lp <= 64 (one 256-column MMA: four 8-bit chunk
+ * columns per target) and the kernel's tiles fit one CTA's shared memory; otherwise
+ * HEFX_PATH_TENSOR returns HEFX_EUNSUPPORTED.  HEFX_PATH_AUTO takes the tensor path only when
+ * the plan has it, Lp >= 48 and batch * L * n >= 96 * 2^16 (where it measured faster: the
+ * CUDA-core kernel makes one pass over the sources per 8 targets, so many targets favour the
+ * matrix form); otherwise the CUDA-core path.
  */
 hefx_status hefx_basis_convert(hefx_ctx* ctx, const hefx_bconv_plan* plan, const uint32_t* d_in, uint32_t* d_out,
                                size_t batch, hefx_path path, void* stream);

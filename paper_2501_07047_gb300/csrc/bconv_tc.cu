@@ -2,11 +2,13 @@
 // into a BAT digit-split matrix product (Sec. IV-A3, "High-Precision MatModMul in BConv").
 //
 //   D[n][(j, o)] = sum_{(i, d)} digit_d(b_{n,i}) * chunk_o([qhat_i]_{p_j} 2^32 2^(7d) mod p_j)
-//   out_{n,j}    = REDC_{p_j}( sum_o D[n][(j, o)] 2^(6o) )
+//   out_{n,j}    = REDC_{p_j}( sum_o D[n][(j, o)] 2^(8o) )
 //
 // b_{n,i} = [a_{n,i} qhat_i^-1]_{q_i} is step 1 (a Shoup product in the prologue); digits are
-// 7 bits (b < q_i < 2^28), chunks 6 bits (constants < p_j < 2^30), and every partial sum is
-// below 4 * 64 * 127 * 63 < 2^23, so fp16 operands with fp32 accumulation are exact.
+// 7 bits (b < q_i < 2^28), chunks 8 bits (four per constant < p_j < 2^32; integers up to 2048
+// are exact in fp16), and every partial sum is below 4 * 64 * 127 * 255 < 2^23, so fp16
+// operands with fp32 accumulation are exact.  Four chunk columns per target limb put up to
+// 64 targets in one 256-column MMA (N = 256), two accumulators in 512 TMEM columns.
 //
 // GB300 mapping: a persistent kernel streams 128-coefficient tiles.  One thread keeps four
 // raw residue tiles (L rows x 128 coefficients) in flight with TMA; four producer warps apply
@@ -28,12 +30,12 @@ namespace hefx {
 
 namespace {
 
-constexpr int KO = 5;
+constexpr int KO = 4;
 constexpr int THREADS = 448;  // warps 0-3 and 8-11 producer, 4-7 epilogue, 12 MMA, 13 TMA
-constexpr int MAX_L = 48, MAX_LP = 32;  // MAX_L: 4 staged raw tiles fit in shared memory
+constexpr int MAX_L = 48, MAX_LP = 64;  // MAX_L: 4 staged raw tiles fit in shared memory; MAX_LP: MMA N <= 256
 
 struct BcTcConst {
-    uint32_t L, Lp, kpad, npad;      // K = 4L padded to 64, N = 8 columns per target limb, padded to 16
+    uint32_t L, Lp, kpad, npad;      // K = 4L padded to 64, N = 4 columns per target limb, padded to 16
     uint32_t q[MAX_L], qhat_inv[MAX_L], qhat_inv_sh[MAX_L];
     uint32_t p[MAX_LP], pinv_neg[MAX_LP];
 };
@@ -171,20 +173,19 @@ __global__ void __launch_bounds__(THREADS, 1)
             tc::tc_fence_after();
             const uint32_t b = t / tiles_per_poly, x = (t % tiles_per_poly) * 128 + lq + lane;
             uint32_t* dst = out + (size_t)b * Lp * n + x;
-            // columns: output j's five chunk sums sit at 8j .. 8j+4, two outputs per 16 columns
+            // columns: output j's four chunk sums sit at 4j .. 4j+3, four outputs per 16 columns
             for (uint32_t cb = 0; cb < npad; cb += 16) {
                 uint32_t r[16];
                 tc::tmem_ld16(tmem + (lq << 16) + s * npad + cb, r);
                 tc::tmem_ld_wait();
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const uint32_t j = cb / 8 + h;
+                for (int h = 0; h < 4; ++h) {
+                    const uint32_t j = cb / 4 + h;
                     if (j < Lp) {
-                        const uint64_t z = (uint64_t)tc::acc_to_u32(r[8 * h]) +
-                                           ((uint64_t)tc::acc_to_u32(r[8 * h + 1]) << 6) +
-                                           ((uint64_t)tc::acc_to_u32(r[8 * h + 2]) << 12) +
-                                           ((uint64_t)tc::acc_to_u32(r[8 * h + 3]) << 18) +
-                                           ((uint64_t)tc::acc_to_u32(r[8 * h + 4]) << 24);
+                        const uint64_t z = (uint64_t)tc::acc_to_u32(r[4 * h]) +
+                                           ((uint64_t)tc::acc_to_u32(r[4 * h + 1]) << 8) +
+                                           ((uint64_t)tc::acc_to_u32(r[4 * h + 2]) << 16) +
+                                           ((uint64_t)tc::acc_to_u32(r[4 * h + 3]) << 24);
                         const uint32_t pj = c.p[j];
                         const uint32_t zl = (uint32_t)z, zh = (uint32_t)(z >> 32);
                         const uint32_t rr = zh + __umulhi(zl * c.pinv_neg[j], pj) + (zl != 0u);
@@ -231,7 +232,10 @@ bool bconv_tc_available(const hefx_bconv_plan* plan) {
 }
 
 bool bconv_prefer_tc(const hefx_bconv_plan* plan, size_t batch) {
-    return bconv_tc_available(plan) && plan->Lp > 8 && ((batch * plan->L) << plan->log2n) >= ((size_t)96 << 16);
+    // measured at N = 2^16: the tensor kernel wins only where many targets share each source
+    // digit (24 -> 56 at batch 8: 130 vs 175 us); 8 to 40 targets and small calls favour the
+    // CUDA-core kernel (24 -> 8: 72 vs 58 us, 16 -> 40 at batch 8: 97 vs 93 us)
+    return bconv_tc_available(plan) && plan->Lp >= 48 && ((batch * plan->L) << plan->log2n) >= ((size_t)96 << 16);
 }
 
 // Offline compile of the step-2 constant (OfflineCompileLeft of Alg. 2 for the right-hand
@@ -244,7 +248,7 @@ cudaError_t bconv_tc_upload(hefx_bconv_plan* plan, const BConvConst& h) {
     if (L > (uint32_t)MAX_L || Lp > (uint32_t)MAX_LP) return cudaSuccess;  // CUDA-core path only
     BcTcPlan* tp = new BcTcPlan();
     tp->kpad = ((4 * L + 63) / 64) * 64;
-    tp->npad = ((8 * Lp + 15) / 16) * 16;
+    tp->npad = ((KO * Lp + 15) / 16) * 16;
     uint32_t cols = 32;
     while (cols < 2 * tp->npad) cols *= 2;
     tp->tmem_cols = cols;
@@ -262,8 +266,8 @@ cudaError_t bconv_tc_upload(hefx_bconv_plan* plan, const BConvConst& h) {
             for (uint32_t d = 0; d < 4; ++d) {
                 const uint32_t k = 4 * i + d;
                 for (int o = 0; o < KO; ++o) {
-                    const uint32_t row = 8 * j + o;
-                    const uint16_t hb = half_bits_small((uint32_t)((cst >> (6 * o)) & 63u));
+                    const uint32_t row = KO * j + o;
+                    const uint16_t hb = half_bits_small((uint32_t)((cst >> (8 * o)) & 255u));
                     const size_t off = (size_t)(k / 64) * (tp->npad * 128) + sw128_offset_host(row, k % 64);
                     memcpy(&img[off], &hb, 2);
                 }

@@ -149,3 +149,20 @@ def test_bconv_plan_rejects_accumulator_overflow(ctx):
     st = hefx.raw_status("hefx_bconv_plan_create", ctx, 10, hefx._u32_array(big[:20]), 20,
                          hefx._u32_array(big[20:]), 20, hefx.ctypes.byref(hefx._vp()))
     assert st == hefx.HEFX_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("Lq,Lp", [(12, 28), (12, 36), (16, 40), (24, 56)])
+def test_bconv_paper_shapes_tensor_path(ctx, Lq, Lp):
+    """The paper's skewed conversion shapes at N = 2^16 run on the tensor path (up to 64 targets
+    in one 256-column MMA) and match the oracle on every output; AUTO agrees."""
+    qs, ps = inputs.source_primes(Lq), inputs.special_primes(Lp)
+    n, B = 1 << 16, 2
+    plan = hefx.hefx_bconv_plan_create(ctx, 16, qs, ps)
+    try:
+        assert available(ctx, plan, "tensor", Lq, Lp, n), "tensor path must be built for this shape"
+        a = inputs.residue_tensor(inputs.derive_seed(41, Lq, Lp), B, qs, n)
+        want = oracle.bconv(a, qs, ps)
+        assert (convert(ctx, plan, a, Lp, "tensor") == want).all()
+        assert (convert(ctx, plan, a, Lp, "auto") == want).all()
+    finally:
+        hefx.hefx_bconv_plan_destroy(plan)
