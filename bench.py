@@ -275,9 +275,15 @@ def run_gpu(args):
         st = hefx.raw_status("hefx_ntt_fwd", ctx, params, data.data_ptr(), 0, hefx.PATHS[path], stream.cuda_stream)
         return st == hefx.HEFX_OK
 
-    paths = [p for p in ("cudacore", "tensor") if available(p)]
+    # timed configurations: the CUDA-core path and the tensor path with each GEMM tile width
+    # (the tensor split at N = 2^16 has one valid choice, 256 x 256)
+    configs = [("cudacore", "cudacore", 0)]
+    if available("tensor"):
+        configs += [("tensor", "tensor", 64), ("tensor_t32", "tensor", 32)]
     results = {}
-    for path in paths:
+    for name, path, tile in configs:
+        if tile:
+            hefx.hefx_params_set_tensor_config(ctx, params, 0, tile)
         # correctness gate: INTT(NTT(x)) == x on the bench data before timing
         data.copy_(data0)
         hefx.hefx_ntt_fwd(ctx, params, data, BATCH, path, stream)
@@ -309,7 +315,8 @@ def run_gpu(args):
         step_ms = sum(fwd_ms) / args.steps + sum(inv_ms) / args.steps
         total_ms = step_ms * args.steps
         total_ms = max_over_ranks(total_ms, dist, "cuda")
-        results[path] = {
+        results[name] = {
+            "path": path, "tile": tile,
             "ms_per_step": total_ms / args.steps,
             "value": job_value(world, UNITS_PER_STEP, args.steps, total_ms),
             "fwd_ms": statistics.mean(fwd_ms), "inv_ms": statistics.mean(inv_ms),
@@ -317,8 +324,13 @@ def run_gpu(args):
             "launches_per_step": 2 if path == "cudacore" else 6,
         }
 
-    best = max(results, key=lambda p: results[p]["value"])
-    r = results[best]
+    if available("tensor"):
+        hefx.hefx_params_set_tensor_config(ctx, params, 0, 64)
+    best_name = max(results, key=lambda p: results[p]["value"])
+    r = results[best_name]
+    best = r["path"]
+    if best == "tensor":
+        hefx.hefx_params_set_tensor_config(ctx, params, 0, r["tile"])
 
     # end to end through the public calls with host buffers: per step the pinned H2D of the
     # batch, fwd, inv and the D2H of the result, over three streams and three device buffers
@@ -372,8 +384,12 @@ def run_gpu(args):
 
     roof = roof_cudacore(r) if best == "cudacore" else roof_tensor(r)
     roof_other = None
-    if "tensor" in results and best != "tensor":
-        roof_other = roof_tensor(results["tensor"])
+    tensor_names = [k for k in results if results[k]["path"] == "tensor"]
+    if tensor_names and best != "tensor":
+        roof_other = roof_tensor(results[max(tensor_names, key=lambda k: results[k]["value"])])
+    roof_tensor_configs = {k: {"tile_outputs": results[k]["tile"], "split": "256x256",
+                               "frac": roof_tensor(results[k])["frac"],
+                               "achieved_TFLOP_s": roof_tensor(results[k])["achieved"]} for k in tensor_names}
 
     line = {
         "metric": METRIC, "value": round(r["value"], 1), "unit": "limb-NTT/s", "n_gpus": world,
@@ -385,8 +401,10 @@ def run_gpu(args):
                    "parallelism": f"replicas x{world}"},
         "paths": {p: {"value": round(v["value"], 1), "ms_per_step": round(v["ms_per_step"], 5),
                       "fwd_ms": round(v["fwd_ms"], 5), "inv_ms": round(v["inv_ms"], 5)} for p, v in results.items()},
+        "config_choice": best_name,
         "roofline": roof,
         "roofline_tensor_path": roof_other,
+        "roofline_tensor_configs": roof_tensor_configs,
         "clocks": r["clocks"],
         "e2e": {"value": round(job_value(world, UNITS_PER_STEP, args.steps, e2e_ms), 1), "unit": "limb-NTT/s",
                 "h2d_bytes_per_step": int(host.nbytes), "d2h_bytes_per_step": int(host.nbytes),

@@ -1,10 +1,14 @@
-"""Path tuner: times the CUDA-core and tensor-core paths of a parameter set on the device and
-records the faster one as the target of HEFX_PATH_AUTO (`hefx_params_set_auto_path`).
+"""Autotuner of the NTT configuration of a parameter set: times every candidate on the device
+and records the fastest as what HEFX_PATH_AUTO runs.
 
-The paper picks the best of three (R, C) splits per HE operator by measurement (Sec. V-A,
-"we sweep three (R, C) configurations and report the best-performing one"); hefx generalises
-that choice to the path itself.  Results are cached per GPU name and shape in a JSON file
-(`$HEFX_TUNE_CACHE`, default ~/.cache/hefx/tune.json).
+Candidates (all bit-exact; checked by INTT(NTT(x)) = x before timing):
+  - the CUDA-core radix-2 path;
+  - the tensor-core matrix NTT for every valid split N = R x C (`tensor_plan.splits`: the
+    paper sweeps its (R, C) configurations per operator and keeps the best, Sec. V-A) and
+    both GEMM tile widths (64 or 32 outputs per tile).
+The winner is applied with `hefx_params_set_auto_path` and, for the tensor path,
+`hefx_params_set_tensor_config`.  Results are cached per GPU name, shape and batch in a JSON
+file (`$HEFX_TUNE_CACHE`, default ~/.cache/hefx/tune.json).
 """
 from __future__ import annotations
 
@@ -13,9 +17,10 @@ import os
 
 import numpy as np
 
-from . import hefx, inputs
+from . import hefx, inputs, tensor_plan
 
 CACHE = os.environ.get("HEFX_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "hefx", "tune.json"))
+TILES = (64, 32)
 
 
 def _load_cache() -> dict:
@@ -37,8 +42,26 @@ def _save_cache(c: dict) -> None:
         pass
 
 
-def time_paths(ctx: int, params: int, logn: int, primes, batch: int = 4, reps: int = 5) -> dict:
-    """Median ms of one forward + inverse NTT of [batch][L][N] per available path."""
+def candidates(logn: int) -> list:
+    """Every configuration the tuner tries at N = 2^logn: ("cudacore", 0, 0) and
+    ("tensor", log2 R, tile) for each valid split and tile width."""
+    out = [("cudacore", 0, 0)]
+    for log2r in tensor_plan.splits(logn):
+        for tile in TILES:
+            out.append(("tensor", log2r, tile))
+    return out
+
+
+def apply(ctx: int, params: int, cand) -> None:
+    path, log2r, tile = cand
+    if path == "tensor":
+        hefx.hefx_params_set_tensor_config(ctx, params, log2r, tile)
+    hefx.hefx_params_set_auto_path(params, path)
+
+
+def time_candidates(ctx: int, params: int, logn: int, primes, batch: int = 4, reps: int = 5) -> dict:
+    """Median ms of one forward + inverse NTT of [batch][L][N] per available candidate, keyed
+    "path/log2r/tile"."""
     import torch
     n = 1 << logn
     data = inputs.residue_tensor(inputs.derive_seed(90, logn, len(primes)), batch, primes, n)
@@ -46,15 +69,18 @@ def time_paths(ctx: int, params: int, logn: int, primes, batch: int = 4, reps: i
     d = d0.clone()
     s = torch.cuda.current_stream()
     out = {}
-    for path in ("cudacore", "tensor"):
+    for cand in candidates(logn):
+        path = cand[0]
         if hefx.raw_status("hefx_ntt_fwd", ctx, params, d.data_ptr(), 0, hefx.PATHS[path], s.cuda_stream) != 0:
             continue
+        if path == "tensor":
+            hefx.hefx_params_set_tensor_config(ctx, params, cand[1], cand[2])
         d.copy_(d0)
         hefx.hefx_ntt_fwd(ctx, params, d, batch, path, s)
         hefx.hefx_ntt_inv(ctx, params, d, batch, path, s)
         torch.cuda.synchronize()
         if not torch.equal(d, d0):
-            raise RuntimeError(f"{path}: INTT(NTT(x)) != x while tuning")
+            raise RuntimeError(f"{cand}: INTT(NTT(x)) != x while tuning")
         ms = []
         for _ in range(reps):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -64,22 +90,29 @@ def time_paths(ctx: int, params: int, logn: int, primes, batch: int = 4, reps: i
             e1.record(s)
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
-        out[path] = float(np.median(ms))
+        out[f"{cand[0]}/{cand[1]}/{cand[2]}"] = float(np.median(ms))
     return out
 
 
-def tune(ctx: int, params: int, logn: int, primes, use_cache: bool = True) -> str:
-    """Chooses the AUTO path of `params` by measurement; returns the chosen path name."""
+def parse(key: str):
+    path, log2r, tile = key.split("/")
+    return path, int(log2r), int(tile)
+
+
+def tune(ctx: int, params: int, logn: int, primes, batch: int = 4, use_cache: bool = True) -> str:
+    """Chooses what HEFX_PATH_AUTO runs for `params` by measurement (or from the cache) and
+    applies it; returns the chosen path name."""
     import torch
-    key = f"{torch.cuda.get_device_name()}|logn={logn}|L={len(primes)}|maxq={max(primes)}"
+    key = f"{torch.cuda.get_device_name()}|logn={logn}|L={len(primes)}|maxq={max(primes)}|batch={batch}"
     cache = _load_cache() if use_cache else {}
-    if key in cache:
-        best = cache[key]["best"]
+    if key in cache and "config" in cache[key]:
+        best = cache[key]["config"]
     else:
-        times = time_paths(ctx, params, logn, primes)
+        times = time_candidates(ctx, params, logn, primes, batch)
         best = min(times, key=times.get)
-        cache[key] = {"best": best, "ms": times}
+        cache[key] = {"config": best, "ms": times}
         if use_cache:
             _save_cache(cache)
-    hefx.hefx_params_set_auto_path(params, best)
-    return best
+    cand = parse(best)
+    apply(ctx, params, cand)
+    return cand[0]

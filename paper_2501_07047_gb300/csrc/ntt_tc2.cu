@@ -43,7 +43,7 @@ namespace hefx {
 namespace tc2 {
 
 constexpr int BM = 128;                // data rows per CTA (MMA M)
-constexpr int OUTS = 64;               // outputs per tile
+constexpr int OUTS = 64;               // outputs per tile (the default tile; 32 is the other choice)
 constexpr int KO = 4;                  // 7-bit constant chunks
 constexpr int BN = OUTS * KO;          // 256 (MMA N)
 constexpr int BK = 64;                 // K elements per stage (128 bytes of fp16)
@@ -54,6 +54,16 @@ constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int THREADS = 320;  // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue (two per TMEM lane quadrant)
 constexpr uint32_t TMEM_COLS = 512;
 constexpr size_t SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + 256;
+
+// Tile of TO outputs (TO * 4 accumulator columns; two accumulators in TMEM).
+template <int TO>
+struct Tile {
+    static constexpr int BN = TO * KO;
+    static constexpr uint32_t B_BYTES = BN * BK * 2;
+    static constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
+    static constexpr uint32_t TMEM_COLS = 2 * BN < 32 ? 32 : 2 * BN;
+    static constexpr size_t SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + 256;
+};
 
 enum Step { FWD1 = 0, FWD3 = 1, INV1 = 2, INV3 = 3 };
 // epilogue output
@@ -79,9 +89,11 @@ struct Args {
     uint32_t K;             // 4 * reduction length
 };
 
-template <int OUTK, int MUL>
+template <int OUTK, int MUL, int TO>
 __global__ void __launch_bounds__(THREADS, 1)
     gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bmap, Args a) {
+    constexpr int BN = Tile<TO>::BN, OUTS = TO;
+    constexpr uint32_t STAGE_BYTES = Tile<TO>::STAGE_BYTES, TMEM_COLS = Tile<TO>::TMEM_COLS;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
@@ -362,7 +374,7 @@ uint16_t half_bits_small(uint32_t d) {
 struct Tc2Tables {
     uint32_t R = 0, C = 0;
     uint16_t* cst[4] = {nullptr, nullptr, nullptr, nullptr};  // fp16 [L][OUT x 4][4V]
-    CUtensorMap bmaps[4];                                      // per step
+    CUtensorMap bmaps[4][2];                                   // per step, per tile width (64, 32 outputs)
     uint2* T = nullptr;
     uint2* Tinv = nullptr;  // transposed: [L][C][R]
     tc2::Limb* limbs = nullptr;
@@ -379,7 +391,7 @@ struct Tc2Tables {
 cudaError_t tc2_prepare(hefx_params* p) {
     using namespace tc2;
     const uint32_t logn = p->log2n, N = p->n, L = p->nlimbs;
-    const uint32_t logR = logn / 2, R = 1u << logR, C = N / R, logC = logn - logR;
+    const uint32_t logR = p->tc_log2r ? p->tc_log2r : logn / 2, R = 1u << logR, C = N / R, logC = logn - logR;
     Tc2Tables* t = new Tc2Tables();
     t->R = R;
     t->C = C;
@@ -443,10 +455,11 @@ cudaError_t tc2_prepare(hefx_params* p) {
     for (int s = 0; s < 4 && e == cudaSuccess; ++s) {
         e = cudaMalloc(&t->cst[s], hc[s].size() * 2);
         if (e == cudaSuccess) e = cudaMemcpy(t->cst[s], hc[s].data(), hc[s].size() * 2, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess &&
-            !encode_map_2d(&t->bmaps[s], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, t->cst[s], 4ull * Vs[s],
-                           (uint64_t)L * outs[s] * KO, 8ull * Vs[s], BK, BN, CU_TENSOR_MAP_SWIZZLE_128B))
-            e = cudaErrorInvalidValue;
+        for (int w = 0; w < 2 && e == cudaSuccess; ++w)
+            if (!encode_map_2d(&t->bmaps[s][w], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, t->cst[s], 4ull * Vs[s],
+                               (uint64_t)L * outs[s] * KO, 8ull * Vs[s], BK, w == 0 ? BN : BN / 2,
+                               CU_TENSOR_MAP_SWIZZLE_128B))
+                e = cudaErrorInvalidValue;
     }
     if (e == cudaSuccess) e = cudaMalloc(&t->T, hT.size() * sizeof(uint2));
     if (e == cudaSuccess) e = cudaMemcpy(t->T, hT.data(), hT.size() * sizeof(uint2), cudaMemcpyHostToDevice);
@@ -495,10 +508,11 @@ cudaError_t ensure_workspace(Tc2Tables* t, size_t elems) {
     return e;
 }
 
-template <int OUTK, int MUL>
-cudaError_t launch_gemm(const CUtensorMap& amap, const CUtensorMap& bmap, const tc2::Args& g, cudaStream_t s) {
+template <int OUTK, int MUL, int TO>
+cudaError_t launch_gemm_t(const CUtensorMap& amap, const CUtensorMap& bmap, const tc2::Args& g, cudaStream_t s) {
     using namespace tc2;
-    auto kern = gemm_kernel<OUTK, MUL>;
+    auto kern = gemm_kernel<OUTK, MUL, TO>;
+    constexpr size_t SMEM_BYTES = Tile<TO>::SMEM_BYTES;
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
@@ -533,6 +547,13 @@ cudaError_t launch_gemm(const CUtensorMap& amap, const CUtensorMap& bmap, const 
     return cudaLaunchKernelEx(&cfg, kern, amap, bmap, g);
 }
 
+template <int OUTK, int MUL>
+cudaError_t launch_gemm(const CUtensorMap* bmaps, int tile, const CUtensorMap& amap, const tc2::Args& g,
+                        cudaStream_t s) {
+    if (tile == 32) return launch_gemm_t<OUTK, MUL, 32>(amap, bmaps[1], g, s);
+    return launch_gemm_t<OUTK, MUL, 64>(amap, bmaps[0], g, s);
+}
+
 // one GEMM step: A digits from `adig` ([poly][limb][DN][K]); output per OUTK
 cudaError_t step(const hefx_params* p, int stp, int outk, int mul, const uint16_t* adig, uint16_t* odig, uint32_t* out,
                  const uint32_t* had, size_t batch, cudaStream_t s) {
@@ -557,16 +578,17 @@ cudaError_t step(const hefx_params* p, int stp, int outk, int mul, const uint16_
     if (!encode_map_2d(&amap, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, const_cast<uint16_t*>(adig), g.K,
                        (uint64_t)batch * g.L * g.DN, 2ull * g.K, BK, BM, CU_TENSOR_MAP_SWIZZLE_128B))
         return cudaErrorInvalidValue;
-    const CUtensorMap& bmap = t->bmaps[stp];
+    const CUtensorMap* bm = t->bmaps[stp];
+    const int tile = p->tc_tile == 32 ? 32 : 64;
     if (outk == OUT_DIGITS_T) {
-        if (mul == MUL_TW_OUT_ROW) return launch_gemm<OUT_DIGITS_T, MUL_TW_OUT_ROW>(amap, bmap, g, s);
-        return launch_gemm<OUT_DIGITS_T, MUL_TW_DATA_ROW>(amap, bmap, g, s);
+        if (mul == MUL_TW_OUT_ROW) return launch_gemm<OUT_DIGITS_T, MUL_TW_OUT_ROW>(bm, tile, amap, g, s);
+        return launch_gemm<OUT_DIGITS_T, MUL_TW_DATA_ROW>(bm, tile, amap, g, s);
     }
-    if (outk == OUT_U32_ROW_OUT) return launch_gemm<OUT_U32_ROW_OUT, MUL_NONE>(amap, bmap, g, s);
+    if (outk == OUT_U32_ROW_OUT) return launch_gemm<OUT_U32_ROW_OUT, MUL_NONE>(bm, tile, amap, g, s);
     switch (mul) {
-        case MUL_HAD: return launch_gemm<OUT_U32_ROW_DATA, MUL_HAD>(amap, bmap, g, s);
-        case MUL_SQUARE: return launch_gemm<OUT_U32_ROW_DATA, MUL_SQUARE>(amap, bmap, g, s);
-        default: return launch_gemm<OUT_U32_ROW_DATA, MUL_NONE>(amap, bmap, g, s);
+        case MUL_HAD: return launch_gemm<OUT_U32_ROW_DATA, MUL_HAD>(bm, tile, amap, g, s);
+        case MUL_SQUARE: return launch_gemm<OUT_U32_ROW_DATA, MUL_SQUARE>(bm, tile, amap, g, s);
+        default: return launch_gemm<OUT_U32_ROW_DATA, MUL_NONE>(bm, tile, amap, g, s);
     }
 }
 

@@ -93,3 +93,31 @@ def test_tensor_work_model():
     worst = tp.K_IN * R * ((1 << tp.W_IN) - 1) * ((1 << tp.W_OUT) - 1)  # one output's digit sum
     assert worst < (1 << 24)  # every partial sum is an exact fp32 integer
     assert tp.K_IN * tp.W_IN >= 28  # four 7-bit digits hold a 28-bit residue
+
+
+def test_tuner_candidates_and_cached_choice(tmp_path, monkeypatch):
+    """The tuner's search space (path x valid split x tile) and its cache: a measured winner is
+    stored per shape and batch and reapplied without timing again."""
+    import torch
+    from paper_2501_07047_gb300 import autotune, tensor_plan
+    assert tensor_plan.splits(15) == [7, 8] and tensor_plan.splits(16) == [8] and tensor_plan.splits(14) == [7]
+    assert tensor_plan.splits(13) == [] and tensor_plan.splits(17) == []
+    assert autotune.candidates(13) == [("cudacore", 0, 0)]
+    assert len(autotune.candidates(15)) == 1 + 2 * len(autotune.TILES)
+    for logn in (14, 15, 16):  # every tensor candidate multiplies out to N with factors 128 or 256
+        for path, log2r, tile in autotune.candidates(logn)[1:]:
+            R, C = tensor_plan.split(logn, log2r)
+            assert R * C == 1 << logn and R in (128, 256) and C in (128, 256) and tile in (32, 64)
+    assert autotune.parse("tensor/7/32") == ("tensor", 7, 32)
+    monkeypatch.setattr(autotune, "CACHE", str(tmp_path / "tune.json"))
+    monkeypatch.setattr(torch.cuda, "get_device_name", lambda *a: "FAKE-GPU")
+    timed, applied = [], []
+    monkeypatch.setattr(autotune, "time_candidates",
+                        lambda *a, **k: timed.append(1) or {"cudacore/0/0": 2.0, "tensor/7/32": 1.5, "tensor/8/64": 1.7})
+    monkeypatch.setattr(autotune, "apply", lambda ctx, p, cand: applied.append(cand))
+    assert autotune.tune(None, None, 15, [268042241, 265420801]) == "tensor"
+    assert applied[-1] == ("tensor", 7, 32) and len(timed) == 1
+    assert autotune.tune(None, None, 15, [268042241, 265420801]) == "tensor"  # from the cache
+    assert applied[-1] == ("tensor", 7, 32) and len(timed) == 1
+    assert autotune.tune(None, None, 15, [268042241, 265420801], batch=8) == "tensor"  # another batch: timed
+    assert len(timed) == 2

@@ -249,17 +249,52 @@ def test_host_validation(ctx):
         hefx.hefx_params_destroy(p)
 
 
-def test_autotune_sets_auto_path(ctx, tmp_path, monkeypatch):
+@pytest.mark.parametrize("logn", [15, 16])
+def test_autotune_sets_auto_path(ctx, tmp_path, monkeypatch, logn):
+    """The tuner measures every candidate (path, split, tile), caches the winner and applies
+    it; AUTO then runs it bit-exactly."""
+    import json
     from paper_2501_07047_gb300 import autotune
     monkeypatch.setattr(autotune, "CACHE", str(tmp_path / "tune.json"))
     primes = inputs.source_primes(4)
-    p = make_params(ctx, 16, primes)
+    p = make_params(ctx, logn, primes)
     try:
-        best = autotune.tune(ctx, p, 16, primes)
+        best = autotune.tune(ctx, p, logn, primes)
         assert best in ("cudacore", "tensor")
-        assert (tmp_path / "tune.json").exists()
-        data = inputs.residue_tensor(inputs.derive_seed(12, 16), 2, primes, 1 << 16)
+        entry = next(iter(json.load(open(tmp_path / "tune.json")).values()))
+        assert set(entry["ms"]) == {f"{c[0]}/{c[1]}/{c[2]}" for c in autotune.candidates(logn)}
+        data = inputs.residue_tensor(inputs.derive_seed(12, logn), 2, primes, 1 << logn)
         assert (run_fwd(ctx, p, data, "auto") == oracle.ntt_batch(data, primes)).all()
+    finally:
+        hefx.hefx_params_destroy(p)
+
+
+@pytest.mark.parametrize("logn", [14, 15, 16])
+def test_tensor_configs_bit_exact(ctx, logn):
+    """Every tensor-path split and tile width gives the oracle's transforms and products;
+    invalid splits and tiles are refused."""
+    from paper_2501_07047_gb300 import autotune
+    primes = inputs.source_primes(3)
+    n = 1 << logn
+    p = make_params(ctx, logn, primes)
+    try:
+        a = inputs.residue_tensor(inputs.derive_seed(13, logn, 0), 2, primes, n)
+        b = inputs.residue_tensor(inputs.derive_seed(13, logn, 1), 2, primes, n)
+        want_f = oracle.ntt_batch(a, primes)
+        want_m = oracle.polymul_batch(a, b, primes)
+        for _, log2r, tile in autotune.candidates(logn)[1:]:
+            hefx.hefx_params_set_tensor_config(ctx, p, log2r, tile)
+            got = run_fwd(ctx, p, a, "tensor")
+            assert (got == want_f).all(), (log2r, tile)
+            assert (run_inv(ctx, p, got, "tensor") == a).all(), (log2r, tile)
+            da, db, dc = to_dev(a), to_dev(b), empty_dev(a.shape)
+            hefx.hefx_poly_mul(ctx, p, da, db, dc, 2, "tensor")
+            hefx.hefx_stream_check(ctx, p)
+            assert (to_host(dc).reshape(a.shape) == want_m).all(), (log2r, tile)
+        for bad in ((logn // 2 - 2, 64), (0, 48)):
+            with pytest.raises(hefx.HefxError) as e:
+                hefx.hefx_params_set_tensor_config(ctx, p, *bad)
+            assert e.value.status == hefx.HEFX_EINVAL
     finally:
         hefx.hefx_params_destroy(p)
 
