@@ -614,7 +614,7 @@ def bench_he_mult(ctx, args):
 def bench_batch(ctx, args):
     """256 uneven polynomial-product jobs, one graph launch per batch."""
     import torch
-    from paper_2501_07047_gb300 import inputs
+    from paper_2501_07047_gb300 import hefx, inputs
     from paper_2501_07047_gb300.batch import UnevenBatch
     shapes = inputs.uneven_jobs(inputs.derive_seed(4), 256)
     batch = UnevenBatch(ctx, shapes, seed=4, fill=False)
@@ -630,7 +630,7 @@ def bench_batch(ctx, args):
                 "ms_per_batch": round(ms, 4), "jobs_per_s": round(256 / (ms / 1e3), 1),
                 "coeff_limbs_per_s": round(cl / (ms / 1e3), 1), "coeff_limbs": cl,
                 "hbm_bytes_per_batch": 20 * cl, "GB_s": round(20 * cl / (ms / 1e3) / 1e9, 1),
-                "launches_per_batch": 2 * len({l for l, _ in shapes}), "graph": True}
+                "launches_per_batch": hefx.hefx_batch_plan_launches(batch.plan), "graph": True}
     finally:
         batch.close()
 

@@ -401,10 +401,14 @@ typedef struct {
 typedef struct hefx_batch_plan hefx_batch_plan;
 
 /*
- * Builds the device work lists of a batch once: jobs are grouped by parameter set (one size
- * class per ring degree) and every limb of every job becomes one row descriptor.  The
- * buffers named by the jobs must stay valid for the plan's lifetime.  path: AUTO or
- * CUDACORE (the persistent row-list kernels); TENSOR gives EUNSUPPORTED.
+ * Builds the device work lists of a batch once: every limb of every job becomes one row
+ * descriptor (carrying its parameter set's tables).  When every job's ring degree is in
+ * [2^10, 2^16] and every modulus is below 2^28, the rows are cut into cluster tasks of 2^16
+ * elements of one ring degree (one row of 2^16, two of 2^15, four of 2^14, or 8 CTA-sized
+ * groups of smaller rows; largest ring degree first) and the whole batch runs as ONE launch
+ * of the fused batch kernel; otherwise jobs are grouped by parameter set and each size class
+ * takes two row-list launches.  The buffers named by the jobs must stay valid for the plan's
+ * lifetime.  path: AUTO or CUDACORE (the CUDA-core kernels); TENSOR gives EUNSUPPORTED.
  * Errors: EINVAL (null/misaligned pointer, nlimbs out of range, params of another context),
  * EUNSUPPORTED, ENOMEM.
  */
@@ -413,8 +417,15 @@ hefx_status hefx_batch_plan_create(hefx_ctx* ctx, const hefx_job* jobs, size_t n
 void hefx_batch_plan_destroy(hefx_batch_plan* plan);
 
 /*
- * Runs every job of the plan: per size class, one persistent launch computes NTT(a) into c
- * and one computes INTT(NTT(b) o c) into c.  On a non-default stream that is not already
+ * Kernel launches one hefx_batch_polymul of the plan makes (1 for the fused form).
+ */
+uint32_t hefx_batch_plan_launches(const hefx_batch_plan* plan);
+
+/*
+ * Runs every job of the plan: c = INTT(NTT(a) o NTT(b)) per limb (INTT(NTT(a) o NTT(a)) when
+ * a == b); in the fused form one launch in which each cluster computes NTT(a) into c and then
+ * INTT(NTT(b) o c) into c for its task's rows, otherwise per size class one launch of each
+ * half.  On a non-default stream that is not already
  * being captured, the first call captures these launches into a CUDA graph and every call
  * replays it (one graph launch per batch); on the legacy default stream, or inside a
  * caller's own capture, the kernels are launched directly.  Errors: EINVAL, ECUDA.

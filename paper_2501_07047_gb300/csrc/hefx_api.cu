@@ -83,6 +83,98 @@ hefx_status ensure_tc(hefx_ctx* ctx, const hefx_params* pc) {
     return HEFX_OK;
 }
 
+RowDesc row_desc(const hefx_params* p, uint32_t l, const uint32_t* in, const uint32_t* had, uint32_t* out) {
+    RowDesc r;
+    memset(&r, 0, sizeof r);
+    r.in = in;
+    r.had = had;
+    r.out = out;
+    r.lc = p->d_lc + l;
+    r.twf = p->d_tw_fwd + (size_t)l * p->n;
+    r.twi = p->d_tw_inv + (size_t)l * p->n;
+    r.limb = l;
+    return r;
+}
+
+// Fused batch plan: rows grouped by (ring degree, second-half kind), cut into cluster tasks of
+// 2^16 elements (ntt_cc_batch_rows_per_task rows), largest ring degree first.  The last task
+// of a split ring degree (2^14 .. 2^16, whose CTAs exchange data inside the cluster) is filled
+// with scratch rows so that every CTA of the cluster runs the same barriers.
+typedef std::vector<std::pair<RowDesc, RowDesc>> RowPairs;  // (first half, second half) per row
+
+hefx_status batch_plan_fused(hefx_ctx* ctx, const std::vector<const hefx_params*>& order,
+                             const std::vector<RowPairs>& pfhi, const std::vector<RowPairs>& psq, hefx_batch_plan** out) {
+    hefx_batch_plan* plan = new hefx_batch_plan();
+    plan->ctx = ctx;
+    plan->fused = true;
+    plan->err = order[0]->d_err_cc;
+    std::vector<size_t> idx(order.size());
+    for (size_t g = 0; g < idx.size(); ++g) idx[g] = g;
+    std::sort(idx.begin(), idx.end(), [&](size_t x, size_t y) { return order[x]->log2n > order[y]->log2n; });
+    // scratch for fill rows: a, b, c of the largest ring degree
+    uint32_t nmax = 0;
+    for (const hefx_params* pr : order) nmax = std::max(nmax, pr->n);
+    cudaError_t e = cudaMalloc(&plan->d_pad, 3ull * nmax * 4);
+    if (e == cudaSuccess) e = cudaMemset(plan->d_pad, 0, 3ull * nmax * 4);
+    if (e != cudaSuccess) {
+        hefx_batch_plan_destroy(plan);
+        return cuda_fail(ctx, e, "batch plan scratch");
+    }
+    std::vector<RowDesc> first, second;
+    std::vector<BatchTask> tasks;
+    for (size_t g : idx) {
+        const hefx_params* pr = order[g];
+        const uint32_t per = ntt_cc_batch_rows_per_task(pr->log2n);
+        const bool split = pr->log2n >= 14;
+        for (int kind = 0; kind < 2; ++kind) {
+            const RowPairs& pairs = kind == 0 ? pfhi[g] : psq[g];
+            size_t nrows = pairs.size();
+            if (nrows == 0) continue;
+            std::vector<RowDesc> one, t2;
+            for (const auto& pr2 : pairs) {
+                one.push_back(pr2.first);
+                t2.push_back(pr2.second);
+            }
+            if (split && nrows % per) {
+                uint32_t* pa = plan->d_pad;
+                uint32_t* pb = plan->d_pad + nmax;
+                uint32_t* pc = plan->d_pad + 2ull * nmax;
+                while (nrows % per) {
+                    one.push_back(row_desc(pr, 0, pa, nullptr, pc));
+                    t2.push_back(kind == 0 ? row_desc(pr, 0, pb, pc, pc) : row_desc(pr, 0, pc, pc, pc));
+                    ++nrows;
+                }
+            }
+            for (size_t r = 0; r < nrows; r += per) {
+                BatchTask t;
+                t.logn = pr->log2n;
+                t.mode = kind == 0 ? MODE_FWD_HAD_INV : MODE_HAD_INV;
+                t.row0 = (uint32_t)(first.size() + r);
+                t.nrows = (uint32_t)std::min<size_t>(per, nrows - r);
+                tasks.push_back(t);
+            }
+            first.insert(first.end(), one.begin(), one.end());
+            second.insert(second.end(), t2.begin(), t2.end());
+        }
+    }
+    plan->off2 = (uint32_t)first.size();
+    plan->ntasks = (uint32_t)tasks.size();
+    plan->total_rows = first.size();
+    std::vector<RowDesc> all = first;
+    all.insert(all.end(), second.begin(), second.end());
+    e = cudaMalloc(&plan->d_rows, all.size() * sizeof(RowDesc));
+    if (e == cudaSuccess) e = cudaMemcpy(plan->d_rows, all.data(), all.size() * sizeof(RowDesc), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&plan->d_tasks, tasks.size() * sizeof(BatchTask));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(plan->d_tasks, tasks.data(), tasks.size() * sizeof(BatchTask), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        hefx_batch_plan_destroy(plan);
+        return cuda_fail(ctx, e, "batch plan upload");
+    }
+    *out = plan;
+    return HEFX_OK;
+}
+
 }  // namespace
 
 // Native form of the serving request (HE-Mult front half; see hefx_mult_front in hefx.h):
@@ -616,6 +708,7 @@ hefx_status hefx_batch_plan_create(hefx_ctx* ctx, const hefx_job* jobs, size_t n
     // group rows by (parameter set, launch kind): NTT(a) -> c; INTT(NTT(b) o c); INTT(c o c)
     std::vector<const hefx_params*> order;
     std::vector<std::vector<RowDesc>> fwd, fhi, sq;
+    std::vector<RowPairs> pfhi, psq;
     for (size_t j = 0; j < njobs; ++j) {
         const hefx_job& jb = jobs[j];
         if (!jb.params || jb.params->ctx != ctx)
@@ -631,24 +724,33 @@ hefx_status hefx_batch_plan_create(hefx_ctx* ctx, const hefx_job* jobs, size_t n
             fwd.emplace_back();
             fhi.emplace_back();
             sq.emplace_back();
+            pfhi.emplace_back();
+            psq.emplace_back();
         }
         const size_t n = jb.params->n;
         const uint32_t *a = jb.d_a, *b = jb.d_b;
         if (a != b && jb.d_c == b) std::swap(a, b);  // keep b intact while c is written
         for (uint32_t l = 0; l < jb.nlimbs; ++l) {
-            RowDesc r0 = {a + l * n, nullptr, jb.d_c + l * n, l, 0};
-            fwd[g].push_back(r0);
+            const RowDesc r1 = row_desc(jb.params, l, a + l * n, nullptr, jb.d_c + l * n);
+            fwd[g].push_back(r1);
             if (a == b) {
-                RowDesc r1 = {jb.d_c + l * n, jb.d_c + l * n, jb.d_c + l * n, l, 0};
-                sq[g].push_back(r1);
+                const RowDesc r2 = row_desc(jb.params, l, jb.d_c + l * n, jb.d_c + l * n, jb.d_c + l * n);
+                sq[g].push_back(r2);
+                psq[g].push_back({r1, r2});
             } else {
-                RowDesc r1 = {b + l * n, jb.d_c + l * n, jb.d_c + l * n, l, 0};
-                fhi[g].push_back(r1);
+                const RowDesc r2 = row_desc(jb.params, l, b + l * n, jb.d_c + l * n, jb.d_c + l * n);
+                fhi[g].push_back(r2);
+                pfhi[g].push_back({r1, r2});
             }
         }
     }
+    // fused form when every job's ring degree and moduli suit the one-launch kernel
+    bool fused = !order.empty();
+    for (const hefx_params* pr : order)
+        fused = fused && ntt_cc_batch_supported(pr->log2n, pr->max_prime < (1u << 28));
     hefx_status st = use_device(ctx);
     if (st != HEFX_OK) return st;
+    if (fused) return batch_plan_fused(ctx, order, pfhi, psq, out);
     hefx_batch_plan* plan = new hefx_batch_plan();
     plan->ctx = ctx;
     std::vector<RowDesc> all;
@@ -685,14 +787,25 @@ hefx_status hefx_batch_plan_create(hefx_ctx* ctx, const hefx_job* jobs, size_t n
 
 void hefx_batch_plan_destroy(hefx_batch_plan* plan) {
     if (!plan) return;
+    if (plan->d_tasks) cudaFree(plan->d_tasks);
+    if (plan->d_pad) cudaFree(plan->d_pad);
     if (plan->exec) cudaGraphExecDestroy(plan->exec);
     if (plan->graph) cudaGraphDestroy(plan->graph);
     if (plan->d_rows) cudaFree(plan->d_rows);
     delete plan;
 }
 
+uint32_t hefx_batch_plan_launches(const hefx_batch_plan* plan) {
+    if (!plan) return 0;
+    if (plan->fused) return plan->ntasks ? 1u : 0u;
+    return (uint32_t)plan->launches.size();
+}
+
 static cudaError_t batch_launch_all(hefx_batch_plan* plan, cudaStream_t s) {
     const RowDesc* rows = static_cast<const RowDesc*>(plan->d_rows);
+    if (plan->fused)
+        return launch_ntt_cc_batch(rows, static_cast<const BatchTask*>(plan->d_tasks), plan->ntasks, plan->off2,
+                                   plan->err, s);
     for (const auto& l : plan->launches) {
         cudaError_t e = launch_ntt_cc_rows(l.params, (NttMode)l.mode, rows + l.offset, l.nrows, s);
         if (e != cudaSuccess) return e;
@@ -706,7 +819,7 @@ hefx_status hefx_batch_polymul(hefx_ctx* ctx, hefx_batch_plan* plan, void* strea
     hefx_status st = use_device(ctx);
     if (st != HEFX_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    if (plan->launches.empty()) return HEFX_OK;
+    if (plan->launches.empty() && !(plan->fused && plan->ntasks)) return HEFX_OK;
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     cudaError_t e = s ? cudaStreamIsCapturing(s, &cap) : cudaSuccess;
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamIsCapturing");

@@ -43,8 +43,21 @@ struct RowDesc {
     const uint32_t* in;
     const uint32_t* had;
     uint32_t* out;
+    const LimbConst* lc;  // the row's limb constants (its parameter set's table, limb resolved)
+    const uint2* twf;     // the row's forward twiddles (N entries)
+    const uint2* twi;     // the row's inverse twiddles (N entries)
     uint32_t limb;
-    uint32_t pad;
+    uint32_t pad[3];
+};
+static_assert(sizeof(RowDesc) == 64, "RowDesc is one 64-byte line");
+
+// One cluster task of the fused batch kernel (ntt_cc_batch.cu): nrows rows of ring degree
+// 2^logn whose first-half descriptors start at row0 (second halves at row0 + the plan's offset).
+struct BatchTask {
+    uint32_t logn;
+    uint32_t mode;  // second half: MODE_FWD_HAD_INV, or MODE_HAD_INV for squares
+    uint32_t row0;
+    uint32_t nrows;
 };
 
 // Device tables of the tensor-core (matrix) NTT for one parameter set: the single-pass GEMMs
@@ -94,6 +107,13 @@ struct hefx_batch_plan {
         size_t nrows;
     };
     std::vector<Launch> launches;
+    // fused form (every job's ring degree in [2^10, 2^16], 28-bit moduli): one launch of
+    // ntasks cluster tasks over d_rows (first halves, then second halves at row off2)
+    bool fused = false;
+    void* d_tasks = nullptr;  // BatchTask array
+    uint32_t ntasks = 0, off2 = 0;
+    uint32_t* d_pad = nullptr;  // scratch rows that fill the last task of a split ring degree
+    uint32_t* err = nullptr;
     void* d_rows = nullptr;  // RowDesc array
     size_t total_rows = 0;
     cudaGraph_t graph = nullptr;
@@ -204,6 +224,11 @@ void tc_free(hefx_params* p);
 cudaError_t tc_check(const hefx_params* p, cudaStream_t stream, uint32_t* code);
 size_t noalloc_scratch_words();
 cudaError_t launch_wait_check(uint32_t* err, uint64_t limit_ns, int arrive, cudaStream_t stream);
+// Fused batch kernel (ntt_cc_batch.cu).
+bool ntt_cc_batch_supported(uint32_t log2n, bool lazy);
+uint32_t ntt_cc_batch_rows_per_task(uint32_t log2n);
+cudaError_t launch_ntt_cc_batch(const RowDesc* d_rows, const BatchTask* d_tasks, uint32_t ntasks, uint32_t off2,
+                                uint32_t* err, cudaStream_t stream);
 cudaError_t tc2_prepare(hefx_params* p);
 void tc2_free(hefx_params* p);
 uint32_t* tc2_err(const hefx_params* p);

@@ -87,7 +87,10 @@ __device__ __forceinline__ int swz_elem(int j0, int k) {
 #define HEFX_CC_SPLIT_MINB 5
 #endif
 
-template <int LOGN>
+// F & 16 selects the configuration of the fused batch kernel (every ring degree in CTAs of
+// 128 threads and 2^13 elements, clusters of 8: one row of 2^16, two of 2^15, four of 2^14, or
+// eight CTA-sized groups of smaller rows per cluster).
+template <int LOGN, int F = 0>
 struct Cfg {
     static constexpr int logP =
         LOGN >= 17   ? HEFX_CC_LOGP17
@@ -102,9 +105,11 @@ struct Cfg {
     static constexpr int rows = (split || logm >= 13) ? 1 : (1 << (13 - logm));  // row segments per CTA
     static constexpr int elems = m * rows;
     static constexpr bool small_split = split && m < (1 << 15);
-    static constexpr int threads = LOGN >= 17 ? HEFX_CC_THREADS17
+    static constexpr bool unified = (F & 16) != 0;
+    static constexpr int threads = unified        ? 128
+                                   : LOGN >= 17   ? HEFX_CC_THREADS17
                                    : small_split ? HEFX_CC_SPLIT_THREADS : (elems >= (1 << 14) ? 512 : 256);
-    static constexpr int minb = LOGN >= 17 ? HEFX_CC_MINB17 : small_split ? HEFX_CC_SPLIT_MINB : 1;
+    static constexpr int minb = unified ? 5 : LOGN >= 17 ? HEFX_CC_MINB17 : small_split ? HEFX_CC_SPLIT_MINB : 1;
     static constexpr int smem_bytes = elems * 4;
     static constexpr int S = logm;                  // stages run inside the CTA
     static constexpr int r_small = S < 5 ? S : 5;   // pass over the smallest strides
@@ -159,6 +164,31 @@ __device__ __forceinline__ uint32_t row_limb(const KArgs& a, uint32_t r) {
     if constexpr ((F & 1) != 0) return a.desc[r].limb;
     else return r % a.L;
 }
+// Row r's limb constants and twiddle tables: from its descriptor (which carries its own
+// parameter set's tables, so rows of different ring degrees can share a launch), else from the
+// launch's parameter set.
+template <int F>
+__device__ __forceinline__ const LimbConst& row_lc(const KArgs& a, uint32_t r) {
+    if constexpr ((F & 1) != 0) return *a.desc[r].lc;
+    else return a.lc[r % a.L];
+}
+template <int N, int F>
+__device__ __forceinline__ const uint2* row_twf(const KArgs& a, uint32_t r) {
+    if constexpr ((F & 1) != 0) return a.desc[r].twf;
+    else return a.tw_f + (size_t)(r % a.L) * N;
+}
+template <int N, int F>
+__device__ __forceinline__ const uint2* row_twi(const KArgs& a, uint32_t r) {
+    if constexpr ((F & 1) != 0) return a.desc[r].twi;
+    else return a.tw_i + (size_t)(r % a.L) * N;
+}
+// A Hadamard operand load: the fused batch kernel (F & 16) reads operands written earlier in the
+// same launch, so it takes the coherent path (L2) instead of the read-only one.
+template <int F, typename T>
+__device__ __forceinline__ T ld_had(const T* p) {
+    if constexpr ((F & 16) != 0) return __ldcg(p);
+    else return __ldg(p);
+}
 
 // Where a register pass takes its inputs and puts its outputs.
 enum : int { SRC_SMEM = 0, SRC_GLOBAL = 1, SRC_GLOBAL_HAD = 3 };
@@ -169,6 +199,7 @@ enum : int { DST_SMEM = 0, DST_GLOBAL = 1, DST_GLOBAL_REDUCE = 2, DST_SMEM_REDUC
 struct Seg {
     uint32_t row0, gbase, part;
     int nrows;
+    uint32_t rbase;  // cluster rank of the row's first CTA (the fused batch kernel runs several rows per cluster)
 };
 
 // Canonical value of a forward output: from [0, 4q) (Harvey ranges) or [0, 16q) (lazy
@@ -183,7 +214,7 @@ __device__ __forceinline__ uint32_t reduce_out(uint32_t x, const LimbConst& lc) 
 template <int R, int LOGN, int logs, int SRC, int F>
 __device__ __forceinline__ void load_elems(uint32_t (&x)[1 << R], const uint32_t* sm, const KArgs& a, const Seg& sg,
                                            int row, int jb, const LimbConst& lc) {
-    using C = Cfg<LOGN>;
+    using C = Cfg<LOGN, F>;
     constexpr int N = 1 << LOGN;
     if constexpr (SRC == SRC_SMEM) {
         const int j0 = row * C::m + jb;
@@ -210,9 +241,9 @@ __device__ __forceinline__ void load_elems(uint32_t (&x)[1 << R], const uint32_t
             const uint4* hs = reinterpret_cast<const uint4*>(rhad + sg.gbase + jb);
 #pragma unroll
             for (int k = 0; k < (1 << R); k += 4) {
-                uint4 v = valid ? __ldg(src + k / 4) : make_uint4(0, 0, 0, 0);
+                uint4 v = valid ? ld_had<F>(src + k / 4) : make_uint4(0, 0, 0, 0);
                 if constexpr (SRC == SRC_GLOBAL_HAD) {
-                    const uint4 h = valid ? __ldg(hs + k / 4) : make_uint4(0, 0, 0, 0);
+                    const uint4 h = valid ? ld_had<F>(hs + k / 4) : make_uint4(0, 0, 0, 0);
                     v.x = mul_mont_lazy(v.x, h.x, lc.q, lc.qinv_neg);
                     v.y = mul_mont_lazy(v.y, h.y, lc.q, lc.qinv_neg);
                     v.z = mul_mont_lazy(v.z, h.z, lc.q, lc.qinv_neg);
@@ -227,8 +258,8 @@ __device__ __forceinline__ void load_elems(uint32_t (&x)[1 << R], const uint32_t
 #pragma unroll
             for (int k = 0; k < (1 << R); ++k) {
                 const size_t g = sg.gbase + jb + (k << logs);
-                uint32_t v = valid ? __ldg(rin + g) : 0u;
-                if constexpr (SRC == SRC_GLOBAL_HAD) v = mul_mont_lazy(v, valid ? __ldg(rhad + g) : 0u, lc.q, lc.qinv_neg);
+                uint32_t v = valid ? ld_had<F>(rin + g) : 0u;
+                if constexpr (SRC == SRC_GLOBAL_HAD) v = mul_mont_lazy(v, valid ? ld_had<F>(rhad + g) : 0u, lc.q, lc.qinv_neg);
                 x[k] = v;
             }
         }
@@ -238,7 +269,7 @@ __device__ __forceinline__ void load_elems(uint32_t (&x)[1 << R], const uint32_t
 template <int R, int LOGN, int logs, int DST, int F>
 __device__ __forceinline__ void store_elems(const uint32_t (&x)[1 << R], uint32_t* sm, const KArgs& a, const Seg& sg,
                                             int row, int jb, const LimbConst& lc) {
-    using C = Cfg<LOGN>;
+    using C = Cfg<LOGN, F>;
     constexpr int N = 1 << LOGN;
     if constexpr (DST == DST_SMEM_REDUCE) {  // canonical values into the swizzled buffer (TMA store)
         static_assert(logs == 0 && R >= 2, "the smallest-stride pass");
@@ -493,7 +524,7 @@ __device__ __forceinline__ void inv_stages_w(uint32_t (&x)[1 << R], const uint2 
 // Forward register pass over stages s0 .. s0+R-1 of every sub-transform of the CTA.
 template <int R, int LOGN, int s0, int SRC, int DST, int F>
 __device__ __forceinline__ void fwd_pass(uint32_t* sm, const Seg& sg, const KArgs& a) {
-    using C = Cfg<LOGN>;
+    using C = Cfg<LOGN, F>;
     constexpr int N = 1 << LOGN;
     constexpr int logtl = LOGN - s0 - R;  // log2 of the smallest stride of the pass
     constexpr int lognsub = C::logm - R;
@@ -502,9 +533,8 @@ __device__ __forceinline__ void fwd_pass(uint32_t* sm, const Seg& sg, const KArg
         // one row: every sub-transform shares the limb; each sub-transform's twiddles are all
         // requested before its data is read, so their latency is paid once per sub-transform
         // rather than once per stage
-        const uint32_t limb = row_limb<F>(a, sg.row0);
-        const LimbConst& lc = a.lc[limb];
-        const uint2* tw = a.tw_f + (size_t)limb * N;
+        const LimbConst& lc = row_lc<F>(a, sg.row0);
+        const uint2* tw = row_twf<N, F>(a, sg.row0);
 #pragma unroll 1
         for (int u = threadIdx.x; u < nsub; u += C::threads) {
             uint2 w[(1 << R) - 1];
@@ -525,9 +555,9 @@ __device__ __forceinline__ void fwd_pass(uint32_t* sm, const Seg& sg, const KArg
             const int j_hi = uu >> logtl;
             const int jb = (j_hi << (logtl + R)) + j_lo;
             const uint32_t g0 = (sg.gbase >> (logtl + R)) + (uint32_t)j_hi;
-            const uint32_t limb = row_limb<F>(a, row < sg.nrows ? sg.row0 + row : sg.row0);
-            const LimbConst& lc = a.lc[limb];
-            const uint2* tw = a.tw_f + (size_t)limb * N;
+            const uint32_t rr = row < sg.nrows ? sg.row0 + row : sg.row0;
+            const LimbConst& lc = row_lc<F>(a, rr);
+            const uint2* tw = row_twf<N, F>(a, rr);
             uint32_t x[1 << R];
             load_elems<R, LOGN, logtl, SRC, F>(x, sm, a, sg, row, jb, lc);
             fwd_stages<R, LOGN, s0, F>(x, g0, tw, lc);
@@ -539,15 +569,14 @@ __device__ __forceinline__ void fwd_pass(uint32_t* sm, const Seg& sg, const KArg
 // Inverse register pass over stages e0 .. e0+R-1.
 template <int R, int LOGN, int SCALE, int e0, int SRC, int DST, int F>
 __device__ __forceinline__ void inv_pass(uint32_t* sm, const Seg& sg, const KArgs& a) {
-    using C = Cfg<LOGN>;
+    using C = Cfg<LOGN, F>;
     constexpr int N = 1 << LOGN;
     constexpr int lognsub = C::logm - R;
     constexpr int nsub = 1 << lognsub;
     if constexpr (R <= 4 && C::rows == 1) {
         // as fwd_pass: a sub-transform's twiddles are all requested before its data is read
-        const uint32_t limb = row_limb<F>(a, sg.row0);
-        const LimbConst& lc = a.lc[limb];
-        const uint2* tw = a.tw_i + (size_t)limb * N;
+        const LimbConst& lc = row_lc<F>(a, sg.row0);
+        const uint2* tw = row_twi<N, F>(a, sg.row0);
 #pragma unroll 1
         for (int u = threadIdx.x; u < nsub; u += C::threads) {
             uint2 w[(1 << R) - 1];
@@ -567,9 +596,9 @@ __device__ __forceinline__ void inv_pass(uint32_t* sm, const Seg& sg, const KArg
             const int j_lo = uu & ((1 << e0) - 1);
             const int j_hi = uu >> e0;
             const int jb = (j_hi << (e0 + R)) + j_lo;
-            const uint32_t limb = row_limb<F>(a, row < sg.nrows ? sg.row0 + row : sg.row0);
-            const LimbConst& lc = a.lc[limb];
-            const uint2* tw = a.tw_i + (size_t)limb * N;
+            const uint32_t rr = row < sg.nrows ? sg.row0 + row : sg.row0;
+            const LimbConst& lc = row_lc<F>(a, rr);
+            const uint2* tw = row_twi<N, F>(a, rr);
             uint32_t x[1 << R];
             load_elems<R, LOGN, e0, SRC, F>(x, sm, a, sg, row, jb, lc);
             inv_stages<R, LOGN, SCALE, e0, F>(x, sg.gbase, j_hi, tw, lc);
@@ -583,7 +612,7 @@ __device__ __forceinline__ void inv_pass(uint32_t* sm, const Seg& sg, const KArg
 // over the same strides, on the same registers.
 template <int R, int LOGN, int s0, int SRC, int DST, int F>
 __device__ __forceinline__ void fwd_had_inv_pass(uint32_t* sm, const Seg& sg, const KArgs& a) {
-    using C = Cfg<LOGN>;
+    using C = Cfg<LOGN, F>;
     constexpr int N = 1 << LOGN;
     constexpr int lognsub = C::logm - R;
     constexpr int nsub = 1 << lognsub;
@@ -593,22 +622,22 @@ __device__ __forceinline__ void fwd_had_inv_pass(uint32_t* sm, const Seg& sg, co
         const int j_hi = u & (nsub - 1);
         const int jb = j_hi << R;
         const uint32_t g0 = (sg.gbase >> R) + (uint32_t)j_hi;
-        const uint32_t limb = row_limb<F>(a, row < sg.nrows ? sg.row0 + row : sg.row0);
-        const LimbConst& lc = a.lc[limb];
+        const uint32_t rr = row < sg.nrows ? sg.row0 + row : sg.row0;
+        const LimbConst& lc = row_lc<F>(a, rr);
         uint32_t x[1 << R];
         load_elems<R, LOGN, 0, SRC, F>(x, sm, a, sg, row, jb, lc);
-        fwd_stages<R, LOGN, s0, F>(x, g0, a.tw_f + (size_t)limb * N, lc);
+        fwd_stages<R, LOGN, s0, F>(x, g0, row_twf<N, F>(a, rr), lc);
         const bool valid = row < sg.nrows;
         const uint4* hs = reinterpret_cast<const uint4*>(row_had<N, F>(a, valid ? sg.row0 + row : sg.row0) + sg.gbase + jb);
 #pragma unroll
         for (int k = 0; k < (1 << R); k += 4) {
-            const uint4 h = valid ? __ldg(hs + k / 4) : make_uint4(0, 0, 0, 0);
+            const uint4 h = valid ? ld_had<F>(hs + k / 4) : make_uint4(0, 0, 0, 0);
             x[k] = mul_mont_lazy(x[k], h.x, lc.q, lc.qinv_neg);
             x[k + 1] = mul_mont_lazy(x[k + 1], h.y, lc.q, lc.qinv_neg);
             x[k + 2] = mul_mont_lazy(x[k + 2], h.z, lc.q, lc.qinv_neg);
             x[k + 3] = mul_mont_lazy(x[k + 3], h.w, lc.q, lc.qinv_neg);
         }
-        inv_stages<R, LOGN, 2, 0, F>(x, sg.gbase, j_hi, a.tw_i + (size_t)limb * N, lc);
+        inv_stages<R, LOGN, 2, 0, F>(x, sg.gbase, j_hi, row_twi<N, F>(a, rr), lc);
         store_elems<R, LOGN, 0, DST, F>(x, sm, a, sg, row, jb, lc);
     }
 }
@@ -644,7 +673,7 @@ __device__ __forceinline__ void sync_all() {
 // unless the cross-CTA stages already filled shared memory.
 template <int LOGN, int I, int s, int F>
 __device__ __forceinline__ void fwd_big(uint32_t* sm, const Seg& sg, const KArgs& a) {
-    using C = Cfg<LOGN>;
+    using C = Cfg<LOGN, F>;
     if constexpr (I < C::nrest) {
         constexpr int r = C::big(I);
         constexpr int SRC = (I == 0 && !C::split) ? SRC_GLOBAL : SRC_SMEM;
@@ -658,7 +687,7 @@ __device__ __forceinline__ void fwd_big(uint32_t* sm, const Seg& sg, const KArgs
 // unless the row is split (then the cross-CTA stages follow).
 template <int LOGN, int SCALE, int I, int e, int F>
 __device__ __forceinline__ void inv_big(uint32_t* sm, const Seg& sg, const KArgs& a) {
-    using C = Cfg<LOGN>;
+    using C = Cfg<LOGN, F>;
     if constexpr (I >= 0) {
         constexpr int r = C::big(I);
         if constexpr (I == 0 && !C::split) {
@@ -685,15 +714,15 @@ __device__ __forceinline__ uint32_t rescale_one(uint32_t x, uint32_t last_raw, c
 
 template <int LOGN, int F, bool RS = false>
 __device__ __forceinline__ void fwd_cross_pass(uint32_t* sm, const Seg& sg, const KArgs& a) {
-    using C = Cfg<LOGN>;
+    using C = Cfg<LOGN, F>;
     constexpr int N = 1 << LOGN, P = C::P, share = C::m / P, ITERS = share / (4 * C::threads);
     static_assert(share % (4 * C::threads) == 0, "whole uint4 groups per thread");
     uint32_t dst[P];
 #pragma unroll
-    for (int t = 0; t < P; ++t) dst[t] = cluster_addr(sm, t);
+    for (int t = 0; t < P; ++t) dst[t] = cluster_addr(sm, sg.rbase + t);
     const uint32_t limb = row_limb<F>(a, sg.row0);
-    const LimbConst& lc = a.lc[limb];
-    const uint2* tw = a.tw_f + (size_t)limb * N;
+    const LimbConst& lc = row_lc<F>(a, sg.row0);
+    const uint2* tw = row_twf<N, F>(a, sg.row0);
     const uint32_t* rin = row_in<N, F>(a, sg.row0);
     const uint32_t* rlast = nullptr;
     if constexpr (RS) {  // output row (b, limb) of [B][L]: input rows (b, limb) and (b, in_rows - 1)
@@ -713,7 +742,7 @@ __device__ __forceinline__ void fwd_cross_pass(uint32_t* sm, const Seg& sg, cons
         for (int it = 0; it < ITERS; ++it) {
             const int j = (int)sg.part * share + (it * C::threads + (int)threadIdx.x) * 4;
 #pragma unroll
-            for (int t = 0; t < P; ++t) vin[it][t] = __ldg(reinterpret_cast<const uint4*>(rin + j + t * C::m));
+            for (int t = 0; t < P; ++t) vin[it][t] = ld_had<F>(reinterpret_cast<const uint4*>(rin + j + t * C::m));
         }
     }
 #pragma unroll
@@ -759,17 +788,16 @@ __device__ __forceinline__ void fwd_cross_pass(uint32_t* sm, const Seg& sg, cons
 // alive until its peers have read it.
 template <int LOGN, int SCALE, int F>
 __device__ __forceinline__ void inv_cross_pass(uint32_t* sm, const Seg& sg, const KArgs& a) {
-    using C = Cfg<LOGN>;
+    using C = Cfg<LOGN, F>;
     constexpr int N = 1 << LOGN, P = C::P, share = C::m / P, ITERS = share / (4 * C::threads);
     static_assert(share % (4 * C::threads) == 0, "whole uint4 groups per thread");
     cg::cluster_group cluster = cg::this_cluster();
     cluster.sync();
     uint32_t src[P];
 #pragma unroll
-    for (int t = 0; t < P; ++t) src[t] = cluster_addr(sm, t);
-    const uint32_t limb = row_limb<F>(a, sg.row0);
-    const LimbConst& lc = a.lc[limb];
-    const uint2* tw = a.tw_i + (size_t)limb * N;
+    for (int t = 0; t < P; ++t) src[t] = cluster_addr(sm, sg.rbase + t);
+    const LimbConst& lc = row_lc<F>(a, sg.row0);
+    const uint2* tw = row_twi<N, F>(a, sg.row0);
     uint32_t* out = row_out<N, F>(a, sg.row0);
     // twiddles shared by every position, and every peer read of every iteration, first
     uint2 w[P - 1];
@@ -824,14 +852,14 @@ __host__ __device__ constexpr bool uses_tma() {
 // lane-consecutive 16-byte accesses (the Hadamard product, if any, applied on the way in).
 template <int LOGN, int F, bool HAD>
 __device__ __forceinline__ void copy_in(uint32_t* sm, const Seg& sg, const KArgs& a) {
-    using C = Cfg<LOGN>;
+    using C = Cfg<LOGN, F>;
     constexpr int N = 1 << LOGN;
     for (int idx = threadIdx.x * 4; idx < sg.nrows * C::m; idx += C::threads * 4) {
         const int row = idx >> C::logm, i = idx & (C::m - 1);
-        uint4 v = __ldg(reinterpret_cast<const uint4*>(row_in<N, F>(a, sg.row0 + row) + sg.gbase + i));
+        uint4 v = ld_had<F>(reinterpret_cast<const uint4*>(row_in<N, F>(a, sg.row0 + row) + sg.gbase + i));
         if constexpr (HAD) {
-            const uint4 h = __ldg(reinterpret_cast<const uint4*>(row_had<N, F>(a, sg.row0 + row) + sg.gbase + i));
-            const LimbConst& lc = a.lc[row_limb<F>(a, sg.row0 + row)];
+            const uint4 h = ld_had<F>(reinterpret_cast<const uint4*>(row_had<N, F>(a, sg.row0 + row) + sg.gbase + i));
+            const LimbConst& lc = row_lc<F>(a, sg.row0 + row);
             v = make_uint4(mul_mont_lazy(v.x, h.x, lc.q, lc.qinv_neg), mul_mont_lazy(v.y, h.y, lc.q, lc.qinv_neg),
                            mul_mont_lazy(v.z, h.z, lc.q, lc.qinv_neg), mul_mont_lazy(v.w, h.w, lc.q, lc.qinv_neg));
         }
@@ -842,7 +870,7 @@ __device__ __forceinline__ void copy_in(uint32_t* sm, const Seg& sg, const KArgs
 
 template <int LOGN, int F>
 __device__ __forceinline__ void copy_out(const uint32_t* sm, const Seg& sg, const KArgs& a) {
-    using C = Cfg<LOGN>;
+    using C = Cfg<LOGN, F>;
     constexpr int N = 1 << LOGN;
     __syncthreads();
     for (int idx = threadIdx.x * 4; idx < sg.nrows * C::m; idx += C::threads * 4) {
@@ -896,7 +924,7 @@ __device__ __forceinline__ void load_part_tma(uint32_t* sm, const Seg& sg, const
 template <int LOGN, int MODE, int F>
 __device__ __forceinline__ void run_task(uint32_t* sm, const Seg& sg, const KArgs& a, uint64_t* tma_bar,
                                          uint32_t& tma_phase) {
-    using C = Cfg<LOGN>;
+    using C = Cfg<LOGN, F>;
     constexpr int RS = C::r_small;
     constexpr int S_FIRST = C::logP;              // first stage run inside the CTA
     constexpr int S_SMALL = LOGN - RS;            // first stage of the smallest-stride pass
@@ -943,8 +971,8 @@ __device__ __forceinline__ void run_task(uint32_t* sm, const Seg& sg, const KArg
 }
 
 template <int LOGN, int MODE, int F>
-__global__ void __launch_bounds__(Cfg<LOGN>::threads, Cfg<LOGN>::minb) ntt_cc_kernel(const __grid_constant__ KArgs a) {
-    using C = Cfg<LOGN>;
+__global__ void __launch_bounds__(Cfg<LOGN, F>::threads, Cfg<LOGN, F>::minb) ntt_cc_kernel(const __grid_constant__ KArgs a) {
+    using C = Cfg<LOGN, F>;
     extern __shared__ __align__(16) uint32_t sm_raw[];
     __shared__ uint64_t tma_bar;
     uint32_t tma_phase = 0;
@@ -978,6 +1006,7 @@ __global__ void __launch_bounds__(Cfg<LOGN>::threads, Cfg<LOGN>::minb) ntt_cc_ke
             sg.nrows = (int)min((uint32_t)C::rows, a.rows - sg.row0);
         }
         sg.gbase = sg.part * C::m;
+        sg.rbase = 0;
         run_task<LOGN, MODE, F>(sm, sg, a, &tma_bar, tma_phase);
         // shared memory is reused by the next task; with a split row the peers write into it
         if (task + stride < ntasks) sync_all<C::split>();
@@ -987,7 +1016,7 @@ __global__ void __launch_bounds__(Cfg<LOGN>::threads, Cfg<LOGN>::minb) ntt_cc_ke
 // rows == 0: set the kernel's attributes only (done before a stream capture).
 template <int LOGN, int MODE, int F>
 cudaError_t launch_one(const KArgs& a, size_t rows, cudaStream_t stream) {
-    using C = Cfg<LOGN>;
+    using C = Cfg<LOGN, F>;
     auto kern = ntt_cc_kernel<LOGN, MODE, F>;
     constexpr int smem = C::smem_bytes + (uses_tma<LOGN, MODE, F>() ? 1024 : 0);
     cudaLaunchConfig_t cfg = {};

@@ -62,6 +62,7 @@ SIGNATURES = {
     "hefx_batch_plan_create": (_i32, [_vp, _vp, _sz, _i32, ctypes.POINTER(_vp)]),
     "hefx_batch_plan_destroy": (None, [_vp]),
     "hefx_batch_polymul": (_i32, [_vp, _vp, _vp]),
+    "hefx_batch_plan_launches": (_u32, [_vp]),
 }
 
 
@@ -311,3 +312,8 @@ def hefx_batch_polymul(ctx, plan, stream=None) -> None:
 def raw_status(fn_name: str, *args) -> int:
     """Calls a C entry point and returns its status code without raising (for error tests)."""
     return getattr(load(), fn_name)(*args)
+
+
+def hefx_batch_plan_launches(plan) -> int:
+    """Kernel launches one hefx_batch_polymul of the plan makes (1 for the fused form)."""
+    return int(load().hefx_batch_plan_launches(plan))
