@@ -636,22 +636,27 @@ def bench_batch(ctx, args):
 
 
 def bench_serving(ctx, args):
-    """Poisson arrival-rate sweep of ciphertext-multiply requests, 40 GB admission budget."""
+    """Poisson arrival-rate sweep of ciphertext-multiply requests, 40 GB admission budget:
+    continuous batching (requests admitted together run as groups of one ring degree in shared
+    launches) and, for comparison at the top rates, one native call per request."""
     from paper_2501_07047_gb300.serve import GpuExecutor, poisson_requests, serve
-    ex = GpuExecutor(ctx, nstreams=8)
     res = {"workload": "HE-Mult front half, N in {2^13..2^16}, L in [8, 36], 8 special primes", "budget_GB": 40}
-    try:
-        for rate in (100, 400, 1600, 6400, 25600):
-            count = int(min(2000, max(120, 0.15 * rate)))  # about 0.15 s of arrivals, at least 120
-            reqs = poisson_requests(inputs_seed(5, rate), count, rate)
-            for r in reqs:
-                ex.warm(r.logn, r.L)
-            serve(reqs[:8], ex)  # warm kernels on this request mix
-            reqs = poisson_requests(inputs_seed(5, rate), count, rate)
-            st = serve(reqs, ex, budget_bytes=40 << 30)
-            res[f"rate_{rate}"] = {k: (round(v, 3) if isinstance(v, float) else v) for k, v in st.items()}
-    finally:
-        ex.close()
+    for mode, rates in (("grouped", (100, 400, 1600, 6400, 25600, 51200)), ("per_request", (6400, 25600))):
+        ex = GpuExecutor(ctx, nstreams=8, grouped=(mode == "grouped"))
+        try:
+            out = {}
+            for rate in rates:
+                count = int(min(2000, max(120, 0.15 * rate)))  # about 0.15 s of arrivals, at least 120
+                reqs = poisson_requests(inputs_seed(5, rate), count, rate)
+                for r in reqs:
+                    ex.warm(r.logn, r.L)
+                serve(reqs[:8], ex)  # warm kernels on this request mix
+                reqs = poisson_requests(inputs_seed(5, rate), count, rate)
+                st = serve(reqs, ex, budget_bytes=40 << 30)
+                out[f"rate_{rate}"] = {k: (round(v, 3) if isinstance(v, float) else v) for k, v in st.items()}
+            res[mode] = out
+        finally:
+            ex.close()
     return res
 
 

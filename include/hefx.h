@@ -384,6 +384,30 @@ hefx_status hefx_mult_front_host(hefx_ctx* ctx, const hefx_mult_plan* plan, cons
                                  uint32_t* d_buf, void* stream);
 
 /*
+ * Several serving requests of one ring degree in shared launches (the batching of the
+ * serving loop; the paper's batching study is Sec. V-B3).  Each request r is a front half as
+ * in hefx_mult_front_host: plan plans[r] (requests may differ in limb count L_r, i.e. in Q
+ * parameter set, conversion plan and keys, but share N and the P parameter set), host inputs
+ * h_a0[r] .. h_b1[r], host output h_out[r], device buffer d_buf[r] of [10 L_r + 3K][N] words.
+ * Per request the inputs are uploaded and the outputs read back; every stage runs ONCE over
+ * all requests' rows: the tensor product and the key products as row-list elementwise
+ * launches, INTT(d2) and NTT over P as row-list transforms, BConv_{Q->P} as one launch with a
+ * block row per request (CUDA-core conversion).  Results equal hefx_mult_front_host's, bit
+ * for bit.  The batch object owns a ring of descriptor slots (pinned host + device): create
+ * it once with the largest count and limb count to serve; a call reuses a slot only after the
+ * launches that read it have completed.  All on `stream`.
+ * Errors: EINVAL (null or foreign arguments, count or limbs above the object's, mixed N or P,
+ * misaligned buffers), EUNSUPPORTED (more than 64 special limbs), ENOMEM (create), ECUDA.
+ */
+typedef struct hefx_mult_batch hefx_mult_batch;
+hefx_status hefx_mult_batch_create(hefx_ctx* ctx, uint32_t max_requests, uint32_t max_limbs, hefx_mult_batch** out);
+void hefx_mult_batch_destroy(hefx_mult_batch* batch);
+hefx_status hefx_mult_front_batch_host(hefx_ctx* ctx, hefx_mult_batch* batch, const hefx_mult_plan* const* plans,
+                                       uint32_t count, const uint32_t* const* h_a0, const uint32_t* const* h_a1,
+                                       const uint32_t* const* h_b0, const uint32_t* const* h_b1,
+                                       uint32_t* const* h_out, uint32_t* const* d_buf, void* stream);
+
+/*
  * Batched polynomial products of uneven shape (the batching pattern of the build; the
  * paper's batching study is Sec. V-B3, "TPUs favor large batch").  Each job multiplies two
  * polynomials of ring degree N = 2^params->log2n over the first `nlimbs` primes of

@@ -130,7 +130,10 @@ __device__ __forceinline__ uint32_t barrett64(uint64_t x, uint32_t p, uint64_t m
 // MODE 3 (ModUp): block row y converts digit y of a ModUp plan (constants gc[y], sources the
 // input rows from skip_lo, outputs at out + y * out_digit_stride with the digit's own rows
 // skipped); the threads of target chunk 0 also copy the digit's own limbs into those rows.
-enum : int { BC_FAST = 0, BC_MODDOWN = 1, BC_EXACT = 2, BC_MODUP = 3 };
+// MODE 4 (list): block row y converts one polynomial of an independent conversion of its own
+// (BcListEntry y: plan constants, source and output pointers; serving batches requests whose
+// source bases differ).
+enum : int { BC_FAST = 0, BC_MODDOWN = 1, BC_EXACT = 2, BC_MODUP = 3, BC_LIST = 4 };
 
 template <int kCoef>
 __host__ __device__ constexpr int log2_const() {
@@ -175,6 +178,12 @@ __global__ void __launch_bounds__(256, MODE == BC_MODUP ? 4 : 5)
     static_assert((kCoef & (kCoef - 1)) == 0, "kCoef is a power of two");
     __shared__ __align__(16) BConvConst c;
     if constexpr (MODE == BC_MODUP) gc += blockIdx.y;
+    if constexpr (MODE == BC_LIST) {
+        const BcListEntry e = reinterpret_cast<const BcListEntry*>(gc)[blockIdx.y];
+        gc = static_cast<const BConvConst*>(e.c);
+        in = e.in;
+        out = e.out;
+    }
     {
         // the vectors, then the L used rows of the step 2 matrix
         const uint32_t L = __ldg(&gc->L);
@@ -365,6 +374,23 @@ cudaError_t launch_mod_up(const hefx_modup_plan* mp, const uint32_t* c, uint32_t
                           (uint32_t)batch, in_stride, out_stride, digit_stride);
     return launch_pdl(bconv_cc_kernel<1, BC_MODUP, 0>, grid, dim3(256), 0, stream, gc, c, U, none, mp->log2n,
                       (uint32_t)batch, in_stride, out_stride, digit_stride);
+}
+
+cudaError_t launch_bconv_cc_list(const BcListEntry* d_list, uint32_t count, uint32_t log2n, uint32_t lp_max,
+                                 cudaStream_t stream) {
+    if (count == 0) return cudaSuccess;
+    const size_t n = (size_t)1 << log2n;
+    const unsigned all = log2n == 16 ? bconv_blocks<1, BC_LIST, 16>(n * count, lp_max)
+                                     : bconv_blocks<1, BC_LIST, 0>(n * count, lp_max);
+    const dim3 grid(std::max(1u, all / count), count);
+    const BConvConst* gc = reinterpret_cast<const BConvConst*>(d_list);
+    const uint32_t* none = nullptr;
+    uint32_t* nout = nullptr;
+    if (log2n == 16)
+        return launch_pdl(bconv_cc_kernel<1, BC_LIST, 16>, grid, dim3(256), 0, stream, gc, none, nout, none, log2n,
+                          1u, (size_t)0, (size_t)0, (size_t)0);
+    return launch_pdl(bconv_cc_kernel<1, BC_LIST, 0>, grid, dim3(256), 0, stream, gc, none, nout, none, log2n, 1u,
+                      (size_t)0, (size_t)0, (size_t)0);
 }
 
 cudaError_t launch_bconv_cc(const hefx_bconv_plan* plan, const uint32_t* in, uint32_t* out, size_t batch,

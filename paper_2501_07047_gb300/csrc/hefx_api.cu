@@ -188,6 +188,21 @@ struct hefx_mult_plan {
     const uint32_t* kp[2] = {nullptr, nullptr};
 };
 
+namespace hefx {
+bool mult_plan_view(const hefx_mult_plan* plan, MultPlanView* out) {
+    if (!plan) return false;
+    out->ctx = plan->ctx;
+    out->pq = plan->pq;
+    out->pp = plan->pp;
+    out->bc = plan->bc;
+    for (int k = 0; k < 2; ++k) {
+        out->kq[k] = plan->kq[k];
+        out->kp[k] = plan->kp[k];
+    }
+    return true;
+}
+}  // namespace hefx
+
 extern "C" {
 
 const char* hefx_version(void) { return "hefx 0.1 (sm_103a)"; }

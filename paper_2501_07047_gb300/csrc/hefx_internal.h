@@ -51,6 +51,14 @@ struct RowDesc {
 };
 static_assert(sizeof(RowDesc) == 64, "RowDesc is one 64-byte line");
 
+// One conversion of a list launch (bconv.cu, serving batches): plan constants (a plan's
+// d_const), one polynomial's source limbs and its output limbs.
+struct BcListEntry {
+    const void* c;
+    const uint32_t* in;
+    uint32_t* out;
+};
+
 // One cluster task of the fused batch kernel (ntt_cc_batch.cu): nrows rows of ring degree
 // 2^logn whose first-half descriptors start at row0 (second halves at row0 + the plan's offset).
 struct BatchTask {
@@ -224,6 +232,18 @@ void tc_free(hefx_params* p);
 cudaError_t tc_check(const hefx_params* p, cudaStream_t stream, uint32_t* code);
 size_t noalloc_scratch_words();
 cudaError_t launch_wait_check(uint32_t* err, uint64_t limit_ns, int arrive, cudaStream_t stream);
+// Read access to a serving plan's fields (hefx_api.cu) for the batched request (mult_batch.cu).
+struct MultPlanView {
+    hefx_ctx* ctx;
+    const hefx_params* pq;
+    const hefx_params* pp;
+    const hefx_bconv_plan* bc;
+    const uint32_t* kq[2];
+    const uint32_t* kp[2];
+};
+bool mult_plan_view(const hefx_mult_plan* plan, MultPlanView* out);
+cudaError_t launch_bconv_cc_list(const BcListEntry* d_list, uint32_t count, uint32_t log2n, uint32_t lp_max,
+                                 cudaStream_t stream);
 // Fused batch kernel (ntt_cc_batch.cu).
 bool ntt_cc_batch_supported(uint32_t log2n, bool lazy);
 uint32_t ntt_cc_batch_rows_per_task(uint32_t log2n);

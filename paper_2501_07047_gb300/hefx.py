@@ -59,6 +59,9 @@ SIGNATURES = {
     "hefx_mult_plan_destroy": (None, [_vp]),
     "hefx_mult_front": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "hefx_mult_front_host": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "hefx_mult_batch_create": (_i32, [_vp, _u32, _u32, ctypes.POINTER(_vp)]),
+    "hefx_mult_batch_destroy": (None, [_vp]),
+    "hefx_mult_front_batch_host": (_i32, [_vp, _vp, _vp, _u32, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "hefx_batch_plan_create": (_i32, [_vp, _vp, _sz, _i32, ctypes.POINTER(_vp)]),
     "hefx_batch_plan_destroy": (None, [_vp]),
     "hefx_batch_polymul": (_i32, [_vp, _vp, _vp]),
@@ -317,3 +320,28 @@ def raw_status(fn_name: str, *args) -> int:
 def hefx_batch_plan_launches(plan) -> int:
     """Kernel launches one hefx_batch_polymul of the plan makes (1 for the fused form)."""
     return int(load().hefx_batch_plan_launches(plan))
+
+
+def hefx_mult_batch_create(ctx, max_requests: int, max_limbs: int) -> int:
+    """Descriptor slots for batched serving requests (hefx_mult_front_batch_host)."""
+    out = _vp()
+    _check(ctx, load().hefx_mult_batch_create(ctx, int(max_requests), int(max_limbs), ctypes.byref(out)))
+    return out.value
+
+
+def hefx_mult_batch_destroy(batch) -> None:
+    load().hefx_mult_batch_destroy(batch)
+
+
+def _ptr_array(items):
+    return (_vp * len(items))(*[_ptr(x) for x in items])
+
+
+def hefx_mult_front_batch_host(ctx, batch, plans, h_a0, h_a1, h_b0, h_b1, h_out, d_buf, stream=None) -> None:
+    """Several serving requests of one ring degree in shared launches (lists of per-request
+    plans and buffers, as in hefx_mult_front_host)."""
+    n = len(plans)
+    assert all(len(x) == n for x in (h_a0, h_a1, h_b0, h_b1, h_out, d_buf))
+    arrs = [_ptr_array(x) for x in (plans, h_a0, h_a1, h_b0, h_b1, h_out, d_buf)]
+    _check(ctx, load().hefx_mult_front_batch_host(ctx, batch, arrs[0], n, arrs[1], arrs[2], arrs[3], arrs[4],
+                                                  arrs[5], arrs[6], _stream(stream)))

@@ -95,9 +95,15 @@ class Admission:
 
 
 class GpuExecutor:
-    """Runs requests through the hefx C ABI on a pool of CUDA streams."""
+    """Runs requests through the hefx C ABI on a pool of CUDA streams.
 
-    def __init__(self, ctx: int, nstreams: int = 8, seed: int = 5, variants: int = 2, slots: int | None = None):
+    grouped=False: one native call per request (`hefx_mult_front_host`, six launches each).
+    grouped=True: the requests admitted together are grouped by ring degree and each group
+    (at most `max_group` requests) is one `hefx_mult_front_batch_host` call whose five
+    launches cover every request of the group (continuous batching across requests)."""
+
+    def __init__(self, ctx: int, nstreams: int = 8, seed: int = 5, variants: int = 2, slots: int | None = None,
+                 grouped: bool = False, max_group: int = 32):
         import torch
 
         from . import hefx
@@ -116,6 +122,9 @@ class GpuExecutor:
         # now (pinned host memory is slow to allocate while requests are being served)
         self.free_slots = [self._slot() for _ in range(4 * nstreams if slots is None else slots)]
         self.pprimes = inputs.special_primes(N_SPECIAL)
+        self.grouped = grouped
+        self.max_group = max_group
+        self.batch = hefx.hefx_mult_batch_create(ctx, max_group, len(self.qprimes)) if grouped else None
 
     # ---------------------------------------------------------------- per-shape resources
     def pool(self, logn: int):
@@ -197,6 +206,27 @@ class GpuExecutor:
         slot["ev"].record(s)
         return {"ev": slot["ev"], "slot": slot, "stream": s}
 
+    def launch_group(self, reqs):
+        """Enqueues requests of one ring degree as one batched native call and a completion
+        event; returns one handle per request (sharing the event)."""
+        s = self.streams[self.next_stream]
+        self.next_stream = (self.next_stream + 1) % len(self.streams)
+        plans, ins, outs, bufs, slots = [], [[], [], [], []], [], [], []
+        for req in reqs:
+            res = self.shape(req.logn, req.L)
+            pl = self.pool(req.logn)
+            slot = self._slot()
+            plans.append(res["mp"])
+            for c, t in enumerate(pl["host_in"][req.variant % self.variants]):
+                ins[c].append(t)
+            outs.append(slot["h"])
+            bufs.append(slot["d"])
+            slots.append(slot)
+        self.hefx.hefx_mult_front_batch_host(self.ctx, self.batch, plans, *ins, outs, bufs, s.cuda_stream)
+        ev = slots[0]["ev"]
+        ev.record(s)
+        return [{"ev": ev, "slot": sl, "stream": s} for sl in slots]
+
     def retire(self, handle) -> None:
         """Returns a completed request's slot to the pool."""
         self.free_slots.append(handle["slot"])
@@ -225,6 +255,9 @@ class GpuExecutor:
             self.hefx.hefx_params_destroy(res["pQ"])
         for p in self.pparams_cache.values():
             self.hefx.hefx_params_destroy(p)
+        if self.batch:
+            self.hefx.hefx_mult_batch_destroy(self.batch)
+            self.batch = None
         self.shapes, self.pparams_cache, self.pools = {}, {}, {}
 
 
@@ -249,11 +282,28 @@ def serve(requests, executor, budget_bytes: int = 40 << 30, max_slots: int | Non
         while i < len(requests) and requests[i].arrival <= now:
             adm.submit(requests[i])
             i += 1
-        for req in adm.admit():
-            req.admitted = time.perf_counter() - t0
-            h = executor.launch(req)
-            host_launch += time.perf_counter() - t0 - req.admitted
-            fifo[id(h.get("stream")) if isinstance(h, dict) else 0].append((req, h))
+        admitted = list(adm.admit())
+        if admitted and getattr(executor, "grouped", False):
+            # continuous batching: requests admitted together run as groups of one ring degree
+            by_n = collections.defaultdict(list)
+            for req in admitted:
+                by_n[req.logn].append(req)
+            for group in by_n.values():
+                for k in range(0, len(group), executor.max_group):
+                    chunk = group[k:k + executor.max_group]
+                    ta = time.perf_counter() - t0
+                    for req in chunk:
+                        req.admitted = ta
+                    hs = executor.launch_group(chunk)
+                    host_launch += time.perf_counter() - t0 - ta
+                    for req, h in zip(chunk, hs):
+                        fifo[id(h["stream"])].append((req, h))
+        else:
+            for req in admitted:
+                req.admitted = time.perf_counter() - t0
+                h = executor.launch(req)
+                host_launch += time.perf_counter() - t0 - req.admitted
+                fifo[id(h.get("stream")) if isinstance(h, dict) else 0].append((req, h))
         max_active = max(max_active, adm.active)
         for q in fifo.values():
             while q and executor.done(q[0][1]):

@@ -111,3 +111,31 @@ def test_mult_plan_validation(ctx):
             hefx.hefx_bconv_plan_destroy(pl)
         hefx.hefx_params_destroy(pq)
         hefx.hefx_params_destroy(pp)
+
+
+def test_grouped_equals_alone_and_oracle(ctx):
+    """Continuous batching across requests: requests admitted together run as groups of one
+    ring degree in shared launches (hefx_mult_front_batch_host); every output equals the
+    request served alone (bit for bit), and the small ones equal the oracle composition."""
+    shapes = [(13, 8), (13, 30), (13, 12), (14, 20), (14, 9), (16, 36), (16, 8), (13, 36)]
+    alone_ex = GpuExecutor(ctx, nstreams=2, seed=12)
+    grouped_ex = GpuExecutor(ctx, nstreams=2, seed=12, grouped=True, max_group=4)
+    try:
+        alone = []
+        for k, (logn, L) in enumerate(shapes):
+            r = Request(k, logn, L, 0.0, variant=k % 2)
+            serve([r], alone_ex, keep_outputs=True)
+            alone.append(r.outputs)
+        mix = [Request(k, logn, L, 0.0, variant=k % 2) for k, (logn, L) in enumerate(shapes)]
+        st = serve(mix, grouped_ex, keep_outputs=True, max_slots=16)
+        assert st["completed"] == len(shapes)
+        for r, ref in zip(mix, alone):
+            for got, exp in zip(r.outputs, ref):
+                assert (got == exp).all(), (r.rid, r.logn, r.L)
+        for r in mix:
+            if r.logn == 13:
+                for got, exp in zip(r.outputs, oracle_request(grouped_ex, r)):
+                    assert (got == exp).all(), (r.rid, r.L)
+    finally:
+        alone_ex.close()
+        grouped_ex.close()
