@@ -277,13 +277,15 @@ def run_gpu(args):
 
     # timed configurations: the CUDA-core path and the tensor path with each GEMM tile width
     # (the tensor split at N = 2^16 has one valid choice, 256 x 256)
-    configs = [("cudacore", "cudacore", 0)]
+    configs = [("cudacore", "cudacore", 0, (0, 0))]
     if available("tensor"):
-        configs += [("tensor", "tensor", 64), ("tensor_t32", "tensor", 32)]
+        # two-factor 256 x 256 and the three-factor 64 x 32 x 32 split, each with both tiles
+        configs += [("tensor", "tensor", 64, (0, 0)), ("tensor_t32", "tensor", 32, (0, 0)),
+                    ("tensor_3f", "tensor", 64, (6, 5)), ("tensor_3f_t32", "tensor", 32, (6, 5))]
     results = {}
-    for name, path, tile in configs:
+    for name, path, tile, split in configs:
         if tile:
-            hefx.hefx_params_set_tensor_config(ctx, params, 0, tile)
+            hefx.hefx_params_set_tensor_config(ctx, params, split[0], tile, split[1])
         # correctness gate: INTT(NTT(x)) == x on the bench data before timing
         data.copy_(data0)
         hefx.hefx_ntt_fwd(ctx, params, data, BATCH, path, stream)
@@ -316,21 +318,21 @@ def run_gpu(args):
         total_ms = step_ms * args.steps
         total_ms = max_over_ranks(total_ms, dist, "cuda")
         results[name] = {
-            "path": path, "tile": tile,
+            "path": path, "tile": tile, "split": split,
             "ms_per_step": total_ms / args.steps,
             "value": job_value(world, UNITS_PER_STEP, args.steps, total_ms),
             "fwd_ms": statistics.mean(fwd_ms), "inv_ms": statistics.mean(inv_ms),
             "wall_s": t_wall, "clocks": clk.summary(),
-            "launches_per_step": 2 if path == "cudacore" else 6,
+            "launches_per_step": 2 if path == "cudacore" else (6 if not split[1] else 8),
         }
 
     if available("tensor"):
-        hefx.hefx_params_set_tensor_config(ctx, params, 0, 64)
+        hefx.hefx_params_set_tensor_config(ctx, params, 0, 64, 0)
     best_name = max(results, key=lambda p: results[p]["value"])
     r = results[best_name]
     best = r["path"]
     if best == "tensor":
-        hefx.hefx_params_set_tensor_config(ctx, params, 0, r["tile"])
+        hefx.hefx_params_set_tensor_config(ctx, params, r["split"][0], r["tile"], r["split"][1])
 
     # end to end through the public calls with host buffers: per step the pinned H2D of the
     # batch, fwd, inv and the D2H of the result, over three streams and three device buffers
@@ -371,9 +373,9 @@ def run_gpu(args):
                 "peak_source": f"{src} hbm_gbs"}
 
     def roof_tensor(rr):
-        # one transform = digitize + two digit-GEMM launches; flops are the GEMMs' digit MACs
+        # one transform = digitize + two (three) digit-GEMM launches; flops are the GEMMs' digit MACs
         dom = max(rr["fwd_ms"], rr["inv_ms"])
-        flops = tensor_flops_per_limb_ntt() * units_per_launch
+        flops = tensor_flops_per_limb_ntt(*rr["split"]) * units_per_launch
         achieved = flops / (dom / 1e3) / 1e12
         return {"bound": "tensor", "achieved": round(achieved, 1), "peak": bf16, "unit": "TFLOP/s",
                 "frac": round(achieved / bf16, 4), "traffic": None,
@@ -387,7 +389,8 @@ def run_gpu(args):
     tensor_names = [k for k in results if results[k]["path"] == "tensor"]
     if tensor_names and best != "tensor":
         roof_other = roof_tensor(results[max(tensor_names, key=lambda k: results[k]["value"])])
-    roof_tensor_configs = {k: {"tile_outputs": results[k]["tile"], "split": "256x256",
+    roof_tensor_configs = {k: {"tile_outputs": results[k]["tile"],
+                               "split": "x".join(str(f) for f in tensor_split(*results[k]["split"])),
                                "frac": roof_tensor(results[k])["frac"],
                                "achieved_TFLOP_s": roof_tensor(results[k])["achieved"]} for k in tensor_names}
 
@@ -665,10 +668,15 @@ def inputs_seed(*parts):
     return inputs.derive_seed(*parts)
 
 
-def tensor_flops_per_limb_ntt() -> float:
-    """Algorithmic tensor work of one tensor-path limb-NTT (2 flops per digit MAC)."""
+def tensor_flops_per_limb_ntt(log2r: int = 0, log2r2: int = 0) -> float:
+    """Algorithmic tensor work of one tensor-path limb-NTT (2 flops per digit MAC) for a split."""
     from paper_2501_07047_gb300 import tensor_plan
-    return tensor_plan.flops_per_limb_ntt(LOGN)
+    return tensor_plan.flops_per_limb_ntt(LOGN, log2r, log2r2)
+
+
+def tensor_split(log2r: int = 0, log2r2: int = 0):
+    from paper_2501_07047_gb300 import tensor_plan
+    return tensor_plan.split(LOGN, log2r, log2r2)
 
 
 def profile_traffic(kernel: str, which: str):

@@ -95,17 +95,24 @@ hefx_status hefx_params_set_auto_path(hefx_params* params, hefx_path path);
 
 /*
  * Tensor-path configuration of a parameter set, for the autotuner (Sec. V-A sweeps the
- * (R, C) split of each operator; the GEMM tile is this library's own choice):
- *  - log2r: the matrix NTT's split N = R x C with R = 2^log2r (0: R = 2^floor(log2n / 2)).
- *    Both R and C must be 128 or 256: the GEMMs take 128-row data blocks, and the fp32
+ * (R, C) split of each operator; deeper splits and the GEMM tile are this library's own):
+ *  - log2r2 == 0: the matrix NTT's split N = R x C with R = 2^log2r (0: R = 2^floor(log2n /
+ *    2)); both R and C must be 128 or 256: the GEMMs take 128-row data blocks, and the fp32
  *    accumulation of 7-bit digit products stays exact only for reduction lengths up to 256.
- *    So N = 2^15 has two splits (128 x 256, 256 x 128), 2^14 and 2^16 one each.
- *  - tile_outputs: outputs per GEMM tile, 64 (256 accumulator columns) or 32 (128).
- * Results do not depend on either choice.  Changing the split drops the parameter set's
+ *    So N = 2^15 has two such splits, 2^14 and 2^16 one each.
+ *  - log2r2 > 0: three factors N = R1 x R2 x R3, R1 = 2^log2r (64 .. 256: the transposing
+ *    digit split works on 64-wide tiles), R2 = 2^log2r2 and R3 = N / (R1 R2) (16 .. 256): step
+ *    1 over R1 as before, then the remaining cyclic transform of each row as two digit GEMMs
+ *    (R2, then R3) with a twiddle between them.  Fewer digit MACs (16 N (R1 + R2 + R3) instead of
+ *    16 N (R + C)), one more epilogue.
+ *  - tile_outputs: outputs per GEMM tile, 64 (256 accumulator columns) or 32 (128); steps with
+ *    fewer outputs take a tile of their output count (16 or 32).
+ * Results do not depend on any of these choices.  Changing the split drops the parameter set's
  * pipelined tensor tables (after a device synchronization); the next tensor-path call builds
  * them for the new split.  Errors: EINVAL (no such split or tile), ECUDA.
  */
-hefx_status hefx_params_set_tensor_config(hefx_params* params, uint32_t log2r, uint32_t tile_outputs);
+hefx_status hefx_params_set_tensor_config(hefx_params* params, uint32_t log2r, uint32_t log2r2,
+                                          uint32_t tile_outputs);
 
 /*
  * Modular reductions of the paper's ablation (Sec. V-F, "Impact of Modular Reduction

@@ -3,9 +3,10 @@ and records the fastest as what HEFX_PATH_AUTO runs.
 
 Candidates (all bit-exact; checked by INTT(NTT(x)) = x before timing):
   - the CUDA-core radix-2 path;
-  - the tensor-core matrix NTT for every valid split N = R x C (`tensor_plan.splits`: the
-    paper sweeps its (R, C) configurations per operator and keeps the best, Sec. V-A) and
-    both GEMM tile widths (64 or 32 outputs per tile).
+  - the tensor-core matrix NTT for every valid two-factor split N = R x C and the three-factor
+    splits R1 x R2 x R3 with the fewest digit MACs (`tensor_plan.tuned_splits`: the paper sweeps
+    its (R, C) configurations per operator and keeps the best, Sec. V-A), each with both GEMM
+    tile widths (64 or 32 outputs per tile).
 The winner is applied with `hefx_params_set_auto_path` and, for the tensor path,
 `hefx_params_set_tensor_config`.  Results are cached per GPU name, shape and batch in a JSON
 file (`$HEFX_TUNE_CACHE`, default ~/.cache/hefx/tune.json).
@@ -43,25 +44,26 @@ def _save_cache(c: dict) -> None:
 
 
 def candidates(logn: int) -> list:
-    """Every configuration the tuner tries at N = 2^logn: ("cudacore", 0, 0) and
-    ("tensor", log2 R, tile) for each valid split and tile width."""
-    out = [("cudacore", 0, 0)]
-    for log2r in tensor_plan.splits(logn):
+    """Every configuration the tuner tries at N = 2^logn: ("cudacore", 0, 0, 0) and
+    ("tensor", log2 R1, log2 R2, tile) for each tuned split (two factors: log2 R2 = 0) and tile
+    width."""
+    out = [("cudacore", 0, 0, 0)]
+    for log2r, log2r2 in tensor_plan.tuned_splits(logn):
         for tile in TILES:
-            out.append(("tensor", log2r, tile))
+            out.append(("tensor", log2r, log2r2, tile))
     return out
 
 
 def apply(ctx: int, params: int, cand) -> None:
-    path, log2r, tile = cand
+    path, log2r, log2r2, tile = cand
     if path == "tensor":
-        hefx.hefx_params_set_tensor_config(ctx, params, log2r, tile)
+        hefx.hefx_params_set_tensor_config(ctx, params, log2r, tile, log2r2)
     hefx.hefx_params_set_auto_path(params, path)
 
 
 def time_candidates(ctx: int, params: int, logn: int, primes, batch: int = 4, reps: int = 5) -> dict:
     """Median ms of one forward + inverse NTT of [batch][L][N] per available candidate, keyed
-    "path/log2r/tile"."""
+    "path/log2r/log2r2/tile"."""
     import torch
     n = 1 << logn
     data = inputs.residue_tensor(inputs.derive_seed(90, logn, len(primes)), batch, primes, n)
@@ -74,7 +76,7 @@ def time_candidates(ctx: int, params: int, logn: int, primes, batch: int = 4, re
         if hefx.raw_status("hefx_ntt_fwd", ctx, params, d.data_ptr(), 0, hefx.PATHS[path], s.cuda_stream) != 0:
             continue
         if path == "tensor":
-            hefx.hefx_params_set_tensor_config(ctx, params, cand[1], cand[2])
+            hefx.hefx_params_set_tensor_config(ctx, params, cand[1], cand[3], cand[2])
         d.copy_(d0)
         hefx.hefx_ntt_fwd(ctx, params, d, batch, path, s)
         hefx.hefx_ntt_inv(ctx, params, d, batch, path, s)
@@ -90,13 +92,17 @@ def time_candidates(ctx: int, params: int, logn: int, primes, batch: int = 4, re
             e1.record(s)
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
-        out[f"{cand[0]}/{cand[1]}/{cand[2]}"] = float(np.median(ms))
+        out[key_of(cand)] = float(np.median(ms))
     return out
 
 
+def key_of(cand) -> str:
+    return "/".join(str(x) for x in cand)
+
+
 def parse(key: str):
-    path, log2r, tile = key.split("/")
-    return path, int(log2r), int(tile)
+    path, log2r, log2r2, tile = key.split("/")
+    return path, int(log2r), int(log2r2), int(tile)
 
 
 def tune(ctx: int, params: int, logn: int, primes, batch: int = 4, use_cache: bool = True) -> str:

@@ -31,7 +31,12 @@ namespace hefx {
 namespace {
 
 constexpr int KO = 4;
-constexpr int THREADS = 448;  // warps 0-3 and 8-11 producer, 4-7 epilogue, 12 MMA, 13 TMA
+#ifndef HEFX_BC_NPG
+#define HEFX_BC_NPG 2
+#endif
+constexpr int NPG = HEFX_BC_NPG;  // producer groups of 4 warps (each takes every NPG-th source limb)
+// warps 0-3 and 8-11 producer groups 0 and 1, 4-7 epilogue, 12 MMA, 13 TMA, 14.. further producer groups
+constexpr int THREADS = (14 + 4 * (NPG - 2)) * 32;
 constexpr int MAX_L = 48, MAX_LP = 64;  // MAX_L: 4 staged raw tiles fit in shared memory; MAX_LP: MMA N <= 256
 
 struct BcTcConst {
@@ -102,14 +107,14 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (uint32_t i = tid; i < 2 * abytes / 16; i += THREADS) reinterpret_cast<uint4*>(smem)[i] = make_uint4(0, 0, 0, 0);
     if (tid == 0) {
         for (int s = 0; s < 2; ++s) {
-            tc::mbar_init(&a_full[s], 256);
+            tc::mbar_init(&a_full[s], 128 * NPG);
             tc::mbar_init(&a_empty[s], 1);
             tc::mbar_init(&acc_full[s], 1);
             tc::mbar_init(&acc_empty[s], 128);
         }
         for (int s = 0; s < RAW_STAGES; ++s) {
             tc::mbar_init(&raw_full[s], 1);
-            tc::mbar_init(&raw_empty[s], 256);
+            tc::mbar_init(&raw_empty[s], 128 * NPG);
         }
         tc::mbar_init(mma_done, 1);
         tc::fence_mbar_init();
@@ -143,8 +148,9 @@ __global__ void __launch_bounds__(THREADS, 1)
             for (int s = 0; s < RAW_STAGES; ++s)
                 if (issued[s]) tc::mbar_wait(&raw_full[s], par[s], err, tc::ERR_TIMEOUT_FULL);
         }
-    } else if (warp < 4 || (warp >= 8 && warp < 12)) {  // ---- producers: step 1 and digit split
-        const uint32_t row = tid & 127, grp = warp >= 8 ? 1u : 0u;  // coefficient row, limb parity
+    } else if (warp < 4 || (warp >= 8 && warp < 12) || warp >= 14) {  // ---- producers: step 1 and digit split
+        // coefficient row, and the group (source limbs i = grp mod NPG)
+        const uint32_t row = tid & 127, grp = warp < 4 ? 0u : warp < 12 ? 1u : 2u + (warp - 14) / 4;
         uint32_t it = 0;
         for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
             const uint32_t s = it & 1, ph = (it >> 1) & 1;
@@ -153,7 +159,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             if (!tc::mbar_wait(&a_empty[s], ph ^ 1u, err, tc::ERR_TIMEOUT_EMPTY)) break;
             const uint32_t* raw = reinterpret_cast<const uint32_t*>(raw_s + rs * rbytes) + row;
             uint8_t* A = a_s[s];
-            for (uint32_t i = grp; i < L; i += 2) {
+            for (uint32_t i = grp; i < L; i += NPG) {
                 const uint32_t qi = c.q[i];
                 const uint32_t bi = csub(mul_shoup_lazy(raw[i * 128], c.qhat_inv[i], c.qhat_inv_sh[i], qi), qi);
                 const uint2 d = tc::split_digits4(bi);

@@ -923,23 +923,33 @@ hefx_status hefx_stream_check(hefx_ctx* ctx, const hefx_params* p, void* stream)
     return HEFX_OK;
 }
 
-hefx_status hefx_params_set_tensor_config(hefx_params* p, uint32_t log2r, uint32_t tile_outputs) {
+hefx_status hefx_params_set_tensor_config(hefx_params* p, uint32_t log2r, uint32_t log2r2, uint32_t tile_outputs) {
     if (!p) return HEFX_EINVAL;
     const uint32_t logn = p->log2n;
     if (log2r == 0) log2r = logn / 2;
-    const uint32_t logc = logn >= log2r ? logn - log2r : 0;
-    if (log2r < 7 || log2r > 8 || logc < 7 || logc > 8)
-        return fail(p->ctx, HEFX_EINVAL,
-                    "tensor split 2^%u x 2^%u of N = 2^%u: both factors must be 128 or 256 (128-row data "
-                    "blocks; exact fp32 sums need reduction lengths <= 256)",
-                    log2r, logc, logn);
+    if (log2r2 == 0) {
+        const uint32_t logc = logn >= log2r ? logn - log2r : 0;
+        if (log2r < 7 || log2r > 8 || logc < 7 || logc > 8)
+            return fail(p->ctx, HEFX_EINVAL,
+                        "tensor split 2^%u x 2^%u of N = 2^%u: both factors must be 128 or 256 (128-row data "
+                        "blocks; exact fp32 sums need reduction lengths <= 256)",
+                        log2r, logc, logn);
+    } else {
+        const int log3 = (int)logn - (int)log2r - (int)log2r2;
+        if (log2r < 6 || log2r > 8 || log2r2 < 4 || log2r2 > 8 || log3 < 4 || log3 > 8)
+            return fail(p->ctx, HEFX_EINVAL,
+                        "tensor split 2^%u x 2^%u x 2^%d of N = 2^%u: the first factor must be 64 .. 256 (the "
+                        "transposing digit split takes 64-wide tiles), the others 16 .. 256 (one 64-digit "
+                        "K stage at least; exact fp32 sums need reduction lengths <= 256)",
+                        log2r, log2r2, log3, logn);
+    }
     if (tile_outputs != 32 && tile_outputs != 64)
         return fail(p->ctx, HEFX_EINVAL, "tile_outputs must be 32 or 64, not %u", tile_outputs);
     hefx_status st = use_device(p->ctx);
     if (st != HEFX_OK) return st;
     std::lock_guard<std::mutex> g(p->tc_mu);
     const uint32_t cur = p->tc_log2r ? p->tc_log2r : logn / 2;
-    if (p->tc2 && cur != log2r) {
+    if (p->tc2 && (cur != log2r || p->tc_log2r2 != log2r2)) {
         // the pipelined tables are built for one split: drop them (after the device is idle)
         // so that the next tensor-path call builds the new ones
         cudaError_t e = cudaDeviceSynchronize();
@@ -947,6 +957,7 @@ hefx_status hefx_params_set_tensor_config(hefx_params* p, uint32_t log2r, uint32
         tc2_free(p);
     }
     p->tc_log2r = log2r;
+    p->tc_log2r2 = log2r2;
     p->tc_tile = (int)tile_outputs;
     return HEFX_OK;
 }

@@ -97,7 +97,8 @@ struct hefx_params {
     hefx::Tc2Tables* tc2 = nullptr;   // built on first tensor-path use
     std::mutex tc_mu;
     hefx_path tuned_path = HEFX_PATH_AUTO;
-    uint32_t tc_log2r = 0;            // tensor-path split N = R x C, log2 R (0: R = 2^floor(log2n / 2))
+    uint32_t tc_log2r = 0;            // tensor-path split: log2 of the first factor (0: 2^floor(log2n / 2))
+    uint32_t tc_log2r2 = 0;           // log2 of the second factor of a three-factor split (0: two factors)
     int tc_tile = 64;                 // tensor-path GEMM tile: outputs per tile (64 or 32)
     int red_ntt = 0;                  // hefx_reduction of the CUDA-core twiddle products
     int red_vec = 1;                  // hefx_reduction of VecModMul

@@ -65,28 +65,34 @@ struct Tile {
     static constexpr size_t SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + 256;
 };
 
-enum Step { FWD1 = 0, FWD3 = 1, INV1 = 2, INV3 = 3 };
-// epilogue output
-enum : int { OUT_DIGITS_T = 0, OUT_U32_ROW_DATA = 1, OUT_U32_ROW_OUT = 2 };
+// epilogue output: the next step's digits, or final residues [data row][output] or [output][data row]
+enum : int { OUT_DIGITS = 0, OUT_U32_ROW_DATA = 1, OUT_U32_ROW_OUT = 2 };
 // epilogue multiplier
-enum : int { MUL_NONE = 0, MUL_TW_OUT_ROW = 1, MUL_TW_DATA_ROW = 2, MUL_HAD = 3, MUL_SQUARE = 4 };
+enum : int { MUL_NONE = 0, MUL_TW = 1, MUL_HAD = 3, MUL_SQUARE = 4 };
 
 struct Limb {
     uint32_t q, qinv_neg, r2, pad;
 };
 
+// One GEMM step of a matrix NTT: data row d (of DN per polynomial limb) times the constant gives
+// OUT outputs o.  Index maps of the epilogue, with d split as (d mod D, d div D):
+//  - twiddle (MUL_TW): tw[limb * twL + o twA + (d mod Dt) twB + (d div Dt) twC]
+//  - next step's digits (OUT_DIGITS): row o rA + (d mod Dd) rB + (d div Dd) rC of orows rows per
+//    polynomial limb, digit position 4 ((d mod Dd) kB + (d div Dd) kC) of 4 klen
+//  - residues: out[d OUT + o] (OUT_U32_ROW_DATA) or out[o DN + d] (OUT_U32_ROW_OUT).
 struct Args {
-    uint32_t* out;          // u32 results [poly][limb][R][C]
-    uint16_t* out_digits;   // digits of the next step [poly][limb][OUT][4 DN] (fp16 bits)
+    uint32_t* out;          // u32 results [poly][limb][DN * OUT]
+    uint16_t* out_digits;   // digits of the next step [poly][limb][orows][4 klen] (fp16 bits)
     const uint32_t* had;    // Hadamard operand, same layout as out
-    const uint2* tw;        // [L][R][C] Shoup twiddles
+    const uint2* tw;        // Shoup twiddles, twL per limb
     const Limb* limbs;
     uint32_t* err;
     uint32_t L, batch;
-    uint32_t R, C;          // data matrix shape
     uint32_t DN;            // data rows per polynomial limb (A operand rows)
     uint32_t OUT;           // outputs per data row
     uint32_t K;             // 4 * reduction length
+    uint32_t logDt, twA, twB, twC, twL;
+    uint32_t logDd, rA, rB, rC, kB, kC, klen, orows;
 };
 
 template <int OUTK, int MUL, int TO>
@@ -214,7 +220,18 @@ __global__ void __launch_bounds__(THREADS, 1)
             item_rows(item, limb, pl, drow0);
             const uint32_t drow = drow0 + quad * 32 + lane;  // data row held by this thread
             const Limb lc = a.limbs[limb];
-            const size_t mat = (size_t)pl * a.R * a.C;      // start of this polynomial limb
+            const size_t mat = (size_t)pl * a.DN * a.OUT;   // start of this polynomial limb
+            // the data row's parts of the twiddle and digit index maps
+            const uint32_t dt_lo = drow & ((1u << a.logDt) - 1u), dt_hi = drow >> a.logDt;
+            const uint32_t dd_lo = drow & ((1u << a.logDd) - 1u), dd_hi = drow >> a.logDd;
+            const uint2* twb = nullptr;
+            if constexpr (MUL == MUL_TW)
+                twb = a.tw + (size_t)limb * a.twL + (size_t)dt_lo * a.twB + (size_t)dt_hi * a.twC;
+            uint16_t* dgb = nullptr;
+            if constexpr (OUTK == OUT_DIGITS)
+                dgb = a.out_digits +
+                      ((size_t)pl * a.orows + (size_t)dd_lo * a.rB + (size_t)dd_hi * a.rC) * (4ull * a.klen) +
+                      4ull * ((size_t)dd_lo * a.kB + (size_t)dd_hi * a.kC);
             bool ok = true;
             for (uint32_t nt = 0; nt < ntiles; ++nt, ++t) {
                 const uint32_t acc = t & 1;
@@ -230,14 +247,9 @@ __global__ void __launch_bounds__(THREADS, 1)
                     tc::tmem_ld_wait();
                     const uint32_t out0 = nt * OUTS + cb / 4;
                     uint2 tw[4];
-                    if constexpr (MUL == MUL_TW_OUT_ROW || MUL == MUL_TW_DATA_ROW) {
+                    if constexpr (MUL == MUL_TW) {
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            // forward step 1: T[out][drow]; inverse step 1: the transposed table Tinv^T[out][drow]
-                            const size_t ti = MUL == MUL_TW_OUT_ROW ? (size_t)(out0 + u) * a.C + drow
-                                                                    : (size_t)(out0 + u) * a.R + drow;
-                            tw[u] = __ldg(a.tw + (size_t)limb * a.R * a.C + ti);
-                        }
+                        for (int u = 0; u < 4; ++u) tw[u] = __ldg(twb + (size_t)(out0 + u) * a.twA);
                     }
                     uint32_t res[4];
 #pragma unroll
@@ -251,10 +263,10 @@ __global__ void __launch_bounds__(THREADS, 1)
                         const uint32_t zl = (uint32_t)z, zh = (uint32_t)(z >> 32);
                         uint32_t v = zh + __umulhi(zl * lc.qinv_neg, lc.q) + (zl != 0u);  // z 2^-32 mod q, [0, 2q)
                         const uint32_t out = out0 + u;
-                        if constexpr (MUL == MUL_TW_OUT_ROW || MUL == MUL_TW_DATA_ROW) {
+                        if constexpr (MUL == MUL_TW) {
                             v = mul_shoup_lazy(v, tw[u].x, tw[u].y, lc.q);
                         } else if constexpr (MUL == MUL_HAD) {
-                            const uint32_t h = __ldg(a.had + mat + (size_t)drow * a.C + out);
+                            const uint32_t h = __ldg(a.had + mat + (size_t)drow * a.OUT + out);
                             v = mul_mont_lazy(mul_mont_lazy(v, h, lc.q, lc.qinv_neg), lc.r2, lc.q, lc.qinv_neg);
                         } else if constexpr (MUL == MUL_SQUARE) {
                             const uint32_t vc = csub(v, lc.q);
@@ -262,20 +274,18 @@ __global__ void __launch_bounds__(THREADS, 1)
                         }
                         res[u] = csub(v, lc.q);
                     }
-                    if constexpr (OUTK == OUT_DIGITS_T) {
-                        // next step's A operand: row = output index, digits of this data row at 4 drow
-                        uint16_t* base = a.out_digits + ((size_t)pl * a.OUT) * (4 * a.DN) + (size_t)drow * 4;
+                    if constexpr (OUTK == OUT_DIGITS) {
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
                             const uint2 d = tc::split_digits4(res[u]);
-                            *reinterpret_cast<uint2*>(base + (size_t)(out0 + u) * (4 * a.DN)) = d;
+                            *reinterpret_cast<uint2*>(dgb + (size_t)(out0 + u) * a.rA * (4ull * a.klen)) = d;
                         }
                     } else if constexpr (OUTK == OUT_U32_ROW_DATA) {
-                        *reinterpret_cast<uint4*>(a.out + mat + (size_t)drow * a.C + out0) =
+                        *reinterpret_cast<uint4*>(a.out + mat + (size_t)drow * a.OUT + out0) =
                             make_uint4(res[0], res[1], res[2], res[3]);
                     } else {
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) a.out[mat + (size_t)(out0 + u) * a.C + drow] = res[u];
+                        for (int u = 0; u < 4; ++u) a.out[mat + (size_t)(out0 + u) * a.DN + drow] = res[u];
                     }
                 }
                 tc::tc_fence_before();
@@ -371,34 +381,81 @@ uint16_t half_bits_small(uint32_t d) {
 
 // ------------------------------------------------------------------ host side
 
+// Tables of one split of the matrix NTT (Sec. IV-B's layout-invariant form):
+//  - two factors N = R x C: step 1 reduces over R (W1, twiddle T), step 2 over C (W3);
+//  - three factors N = R1 x R2 x R3: step 1 as before with C = R2 R3, then the C-point cyclic
+//    transform of each row (root w = psi^(2 R1)) as two steps: W2[p2][j2] = w^(R3 j2 brv(p2)),
+//    twiddle T2[p2][j3] = w^(j3 brv(p2)), W3[p3][j3] = w^(R2 j3 brv(p3)); every output lands
+//    at its bit-reversed position p1 R2 R3 + p2 R3 + p3 (the exponent j (2k + 1) mod 2N splits
+//    over (j1, j2, j3) and (k1, k2, k3) with k = k1 + R1 k2 + R1 R2 k3).
+// The inverse runs the mirror with the negated exponents and N^-1 folded into its last step.
 struct Tc2Tables {
-    uint32_t R = 0, C = 0;
-    uint16_t* cst[4] = {nullptr, nullptr, nullptr, nullptr};  // fp16 [L][OUT x 4][4V]
-    CUtensorMap bmaps[4][2];                                   // per step, per tile width (64, 32 outputs)
-    uint2* T = nullptr;
-    uint2* Tinv = nullptr;  // transposed: [L][C][R]
+    uint32_t nsteps = 0;
+    uint32_t f[3] = {0, 0, 0};
+    uint16_t* cst[6] = {};            // fp16 BAT digit matrices: forward steps, then inverse steps
+    uint32_t cst_out[6] = {}, cst_v[6] = {};
+    CUtensorMap bmaps[6][3];          // per matrix, per tile width 64 / 32 / 16 outputs
+    uint2* twf[2] = {nullptr, nullptr};  // forward twiddles after steps 1 and 2
+    uint2* twi[2] = {nullptr, nullptr};  // inverse twiddles after inverse steps 1 and 2
     tc2::Limb* limbs = nullptr;
     uint32_t* err = nullptr;
-    uint16_t* dig1 = nullptr;  // first-step digits
-    uint16_t* dig3 = nullptr;  // second-step digits
-    uint32_t* scratch = nullptr;
-    size_t dig_elems = 0, scratch_words = 0;
+    uint16_t* dig1 = nullptr;
+    uint16_t* dig3 = nullptr;
+    size_t dig_elems = 0;
 };
+
+namespace {
+
+int tile_index(uint32_t tile) { return tile >= 64 ? 0 : tile == 32 ? 1 : 2; }
+
+}  // namespace
+
+// The split a parameter set uses: log2 of its factors, from (tc_log2r, tc_log2r2).
+void tc2_split(const hefx_params* p, uint32_t f[3], uint32_t* nsteps) {
+    const uint32_t logn = p->log2n;
+    const uint32_t l1 = p->tc_log2r ? p->tc_log2r : logn / 2;
+    if (p->tc_log2r2) {
+        f[0] = 1u << l1;
+        f[1] = 1u << p->tc_log2r2;
+        f[2] = 1u << (logn - l1 - p->tc_log2r2);
+        *nsteps = 3;
+    } else {
+        f[0] = 1u << l1;
+        f[1] = 1u << (logn - l1);
+        f[2] = 0;
+        *nsteps = 2;
+    }
+}
 
 // Offline precompute: BAT digit matrices with 7-bit input digits and 7-bit output chunks,
 // constants times 2^32 (Montgomery), rows (out, chunk) interleaved so that one output's four
-// chunk sums land in four consecutive accumulator columns.
+// chunk sums land in four consecutive accumulator columns; Shoup twiddles.
 cudaError_t tc2_prepare(hefx_params* p) {
     using namespace tc2;
-    const uint32_t logn = p->log2n, N = p->n, L = p->nlimbs;
-    const uint32_t logR = p->tc_log2r ? p->tc_log2r : logn / 2, R = 1u << logR, C = N / R, logC = logn - logR;
+    const uint32_t N = p->n, L = p->nlimbs;
     Tc2Tables* t = new Tc2Tables();
-    t->R = R;
-    t->C = C;
-    const uint32_t outs[4] = {R, C, C, R}, Vs[4] = {R, C, C, R};
-    std::vector<std::vector<uint16_t>> hc(4);
-    for (int s = 0; s < 4; ++s) hc[s].assign((size_t)L * outs[s] * KO * 4 * Vs[s], 0);
-    std::vector<uint2> hT((size_t)L * N), hTi((size_t)L * N);
+    tc2_split(p, t->f, &t->nsteps);
+    const uint32_t ns = t->nsteps;
+    const uint32_t R = t->f[0], C = N / R;  // step 1 and the rest (C = R2 R3 with three factors)
+    const uint32_t R2 = t->f[1], R3 = ns == 3 ? t->f[2] : 1;
+    // matrices: forward steps 0..ns-1, inverse steps ns..2ns-1 (outputs = reduction length)
+    const uint32_t fw[3] = {R, ns == 3 ? R2 : C, R3};
+    for (uint32_t k = 0; k < ns; ++k) {
+        t->cst_out[k] = t->cst_v[k] = fw[k];
+        t->cst_out[ns + k] = t->cst_v[ns + k] = fw[ns - 1 - k];  // inverse steps mirror the order
+    }
+    std::vector<std::vector<uint16_t>> hc(2 * ns);
+    for (uint32_t m = 0; m < 2 * ns; ++m) hc[m].assign((size_t)L * t->cst_out[m] * KO * 4 * t->cst_v[m], 0);
+    // twiddles per limb: forward T (N), then T2 (R2 R3); inverse T2inv (R2 R3), then Tinv (N)
+    std::vector<uint2> hTf[2], hTi[2];
+    hTf[0].resize((size_t)L * N);
+    if (ns == 2) {
+        hTi[0].resize((size_t)L * N);
+    } else {
+        hTf[1].resize((size_t)L * R2 * R3);
+        hTi[0].resize((size_t)L * R2 * R3);
+        hTi[1].resize((size_t)L * N);
+    }
     std::vector<Limb> hl(L);
     auto work = [&](uint32_t l) {
         const uint64_t q = p->primes[l], psi = p->psi[l], twoN = 2ull * N;
@@ -409,36 +466,63 @@ cudaError_t tc2_prepare(hefx_params* p) {
         auto Pn = [&](uint64_t e) { return pw[(twoN - e % twoN) % twoN]; };
         const uint64_t r32 = ((uint64_t)1 << 32) % q, ninv = inv_mod(N % q, q);
         hl[l] = {(uint32_t)q, neg_inv_pow2_32((uint32_t)q), (uint32_t)mul_mod(r32, r32, q), 0};
-        auto put = [&](int s, uint32_t out, uint32_t v, uint64_t w) {
-            const uint32_t K = 4 * Vs[s];
+        auto put = [&](uint32_t m, uint32_t out, uint32_t v, uint64_t w) {
+            const uint32_t K = 4 * t->cst_v[m];
             uint64_t c = mul_mod(w, r32, q);
             for (uint32_t i = 0; i < 4; ++i) {
                 for (int o = 0; o < KO; ++o) {
                     const uint32_t chunk = (uint32_t)((c >> (7 * o)) & 127u);
-                    hc[s][(((size_t)l * outs[s] + out) * KO + o) * K + v * 4 + i] = half_bits_small(chunk);
+                    hc[m][(((size_t)l * t->cst_out[m] + out) * KO + o) * K + v * 4 + i] = half_bits_small(chunk);
                 }
                 c = (c << 7) % q;
             }
         };
+        auto shoup2 = [&](uint64_t w) { return make_uint2((uint32_t)w, shoup(w, q)); };
+        const int logR = 31 - __builtin_clz(R);
+        // step 1 over R (both forms): W1[p1][j1] = psi^(C j1 (2 brv(p1) + 1)); its inverse
+        // (the last inverse step) with N^-1; twiddle T[p1][j] = psi^(j (2 brv(p1) + 1)), the
+        // inverse one stored transposed [j][p1]
         for (uint32_t p1 = 0; p1 < R; ++p1) {
-            const uint64_t kodd = 2ull * bit_reverse(p1, (int)logR) + 1;
+            const uint64_t kodd = 2ull * bit_reverse(p1, logR) + 1;
             for (uint32_t j1 = 0; j1 < R; ++j1) {
-                put(FWD1, p1, j1, P((uint64_t)C * j1 * kodd));
-                put(INV3, j1, p1, mul_mod(ninv, Pn((uint64_t)C * j1 * kodd), q));
+                put(0, p1, j1, P((uint64_t)C * j1 * kodd));
+                put(2 * ns - 1, j1, p1, mul_mod(ninv, Pn((uint64_t)C * j1 * kodd), q));
             }
-            for (uint32_t j2 = 0; j2 < C; ++j2) {
-                const uint64_t w = P((uint64_t)j2 * kodd), wi = Pn((uint64_t)j2 * kodd);
-                hT[(size_t)l * N + (size_t)p1 * C + j2] = make_uint2((uint32_t)w, shoup(w, q));
-                // inverse twiddle stored transposed ([j2][p1]): the inverse step-1 epilogue holds
-                // one p1 per lane and walks j2, so lanes read consecutive entries
-                hTi[(size_t)l * N + (size_t)j2 * R + p1] = make_uint2((uint32_t)wi, shoup(wi, q));
+            for (uint32_t j = 0; j < C; ++j) {
+                hTf[0][(size_t)l * N + (size_t)p1 * C + j] = shoup2(P((uint64_t)j * kodd));
+                hTi[ns - 2][(size_t)l * N + (size_t)j * R + p1] = shoup2(Pn((uint64_t)j * kodd));
             }
         }
-        for (uint32_t p2 = 0; p2 < C; ++p2) {
-            const uint64_t kb = bit_reverse(p2, (int)logC);
-            for (uint32_t j2 = 0; j2 < C; ++j2) {
-                put(FWD3, p2, j2, P(2ull * R * j2 * kb));
-                put(INV1, j2, p2, Pn(2ull * R * j2 * kb));
+        if (ns == 2) {
+            // C-point cyclic step: W3[p2][j2] = psi^(2R j2 brv(p2)); inverse first step mirror
+            const int logC = 31 - __builtin_clz(C);
+            for (uint32_t p2 = 0; p2 < C; ++p2) {
+                const uint64_t kb = bit_reverse(p2, logC);
+                for (uint32_t j2 = 0; j2 < C; ++j2) {
+                    put(1, p2, j2, P(2ull * R * j2 * kb));
+                    put(2, j2, p2, Pn(2ull * R * j2 * kb));
+                }
+            }
+        } else {
+            // the C-point cyclic transform (w = psi^(2R)) as R2 x R3
+            const int log2 = 31 - __builtin_clz(R2), log3 = 31 - __builtin_clz(R3);
+            for (uint32_t p2 = 0; p2 < R2; ++p2) {
+                const uint64_t b2 = bit_reverse(p2, log2);
+                for (uint32_t j2 = 0; j2 < R2; ++j2) {
+                    put(1, p2, j2, P(2ull * R * R3 * j2 * b2));   // W2
+                    put(4, j2, p2, Pn(2ull * R * R3 * j2 * b2));  // inverse step 2: V2[j2][p2]
+                }
+                for (uint32_t j3 = 0; j3 < R3; ++j3) {
+                    hTf[1][(size_t)l * R2 * R3 + (size_t)p2 * R3 + j3] = shoup2(P(2ull * R * j3 * b2));
+                    hTi[0][(size_t)l * R2 * R3 + (size_t)p2 * R3 + j3] = shoup2(Pn(2ull * R * j3 * b2));
+                }
+            }
+            for (uint32_t p3 = 0; p3 < R3; ++p3) {
+                const uint64_t b3 = bit_reverse(p3, log3);
+                for (uint32_t j3 = 0; j3 < R3; ++j3) {
+                    put(2, p3, j3, P(2ull * R * R2 * j3 * b3));   // W3
+                    put(3, j3, p3, Pn(2ull * R * R2 * j3 * b3));  // inverse step 1: V3[j3][p3]
+                }
             }
         }
     };
@@ -452,19 +536,27 @@ cudaError_t tc2_prepare(hefx_params* p) {
         for (auto& x : th) x.join();
     }
     cudaError_t e = cudaSuccess;
-    for (int s = 0; s < 4 && e == cudaSuccess; ++s) {
-        e = cudaMalloc(&t->cst[s], hc[s].size() * 2);
-        if (e == cudaSuccess) e = cudaMemcpy(t->cst[s], hc[s].data(), hc[s].size() * 2, cudaMemcpyHostToDevice);
-        for (int w = 0; w < 2 && e == cudaSuccess; ++w)
-            if (!encode_map_2d(&t->bmaps[s][w], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, t->cst[s], 4ull * Vs[s],
-                               (uint64_t)L * outs[s] * KO, 8ull * Vs[s], BK, w == 0 ? BN : BN / 2,
+    for (uint32_t m = 0; m < 2 * ns && e == cudaSuccess; ++m) {
+        e = cudaMalloc(&t->cst[m], hc[m].size() * 2);
+        if (e == cudaSuccess) e = cudaMemcpy(t->cst[m], hc[m].data(), hc[m].size() * 2, cudaMemcpyHostToDevice);
+        for (int w = 0; w < 3 && e == cudaSuccess; ++w) {
+            const uint32_t tile = 64u >> w;
+            if (tile > t->cst_out[m]) continue;
+            if (!encode_map_2d(&t->bmaps[m][w], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, t->cst[m], 4ull * t->cst_v[m],
+                               (uint64_t)L * t->cst_out[m] * KO, 8ull * t->cst_v[m], BK, tile * KO,
                                CU_TENSOR_MAP_SWIZZLE_128B))
                 e = cudaErrorInvalidValue;
+        }
     }
-    if (e == cudaSuccess) e = cudaMalloc(&t->T, hT.size() * sizeof(uint2));
-    if (e == cudaSuccess) e = cudaMemcpy(t->T, hT.data(), hT.size() * sizeof(uint2), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMalloc(&t->Tinv, hTi.size() * sizeof(uint2));
-    if (e == cudaSuccess) e = cudaMemcpy(t->Tinv, hTi.data(), hTi.size() * sizeof(uint2), cudaMemcpyHostToDevice);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        if (hTf[k].empty()) continue;
+        e = cudaMalloc(&t->twf[k], hTf[k].size() * sizeof(uint2));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(t->twf[k], hTf[k].data(), hTf[k].size() * sizeof(uint2), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMalloc(&t->twi[k], hTi[k].size() * sizeof(uint2));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(t->twi[k], hTi[k].data(), hTi[k].size() * sizeof(uint2), cudaMemcpyHostToDevice);
+    }
     if (e == cudaSuccess) e = cudaMalloc(&t->limbs, L * sizeof(Limb));
     if (e == cudaSuccess) e = cudaMemcpy(t->limbs, hl.data(), L * sizeof(Limb), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&t->err, 4);
@@ -477,15 +569,16 @@ cudaError_t tc2_prepare(hefx_params* p) {
 void tc2_free(hefx_params* p) {
     Tc2Tables* t = p->tc2;
     if (!t) return;
-    for (int s = 0; s < 4; ++s)
-        if (t->cst[s]) cudaFree(t->cst[s]);
-    if (t->T) cudaFree(t->T);
-    if (t->Tinv) cudaFree(t->Tinv);
+    for (int m = 0; m < 6; ++m)
+        if (t->cst[m]) cudaFree(t->cst[m]);
+    for (int k = 0; k < 2; ++k) {
+        if (t->twf[k]) cudaFree(t->twf[k]);
+        if (t->twi[k]) cudaFree(t->twi[k]);
+    }
     if (t->limbs) cudaFree(t->limbs);
     if (t->err) cudaFree(t->err);
     if (t->dig1) cudaFree(t->dig1);
     if (t->dig3) cudaFree(t->dig3);
-    if (t->scratch) cudaFree(t->scratch);
     delete t;
     p->tc2 = nullptr;
 }
@@ -548,93 +641,145 @@ cudaError_t launch_gemm_t(const CUtensorMap& amap, const CUtensorMap& bmap, cons
 }
 
 template <int OUTK, int MUL>
-cudaError_t launch_gemm(const CUtensorMap* bmaps, int tile, const CUtensorMap& amap, const tc2::Args& g,
+cudaError_t launch_gemm(const CUtensorMap* bmaps, uint32_t tile, const CUtensorMap& amap, const tc2::Args& g,
                         cudaStream_t s) {
+    if (tile >= 64) return launch_gemm_t<OUTK, MUL, 64>(amap, bmaps[0], g, s);
     if (tile == 32) return launch_gemm_t<OUTK, MUL, 32>(amap, bmaps[1], g, s);
-    return launch_gemm_t<OUTK, MUL, 64>(amap, bmaps[0], g, s);
+    return launch_gemm_t<OUTK, MUL, 16>(amap, bmaps[2], g, s);
 }
 
-// one GEMM step: A digits from `adig` ([poly][limb][DN][K]); output per OUTK
-cudaError_t step(const hefx_params* p, int stp, int outk, int mul, const uint16_t* adig, uint16_t* odig, uint32_t* out,
-                 const uint32_t* had, size_t batch, cudaStream_t s) {
+int ilog2(uint32_t x) { return 31 - __builtin_clz(x); }
+
+// One GEMM step: constant matrix m, A digits `adig` ([poly][limb][DN][4 V]); output per outk.
+struct StepSpec {
+    uint32_t m, DN;
+    int outk, mul;
+    const uint2* tw;
+    uint32_t Dt, twA, twB, twC, twL;
+    uint32_t Dd, rA, rB, rC, kB, kC, klen, orows;
+};
+
+cudaError_t run_step(const hefx_params* p, const StepSpec& st, const uint16_t* adig, uint16_t* odig, uint32_t* out,
+                     const uint32_t* had, size_t batch, cudaStream_t s) {
     using namespace tc2;
     const Tc2Tables* t = p->tc2;
-    const bool trans_data = (stp == FWD1 || stp == INV3);  // A rows are the data's columns
     Args g;
+    memset(&g, 0, sizeof g);
     g.out = out;
     g.out_digits = odig;
     g.had = had;
-    g.tw = (stp == FWD1) ? t->T : t->Tinv;
+    g.tw = st.tw;
     g.limbs = t->limbs;
     g.err = t->err;
     g.L = p->nlimbs;
     g.batch = (uint32_t)batch;
-    g.R = t->R;
-    g.C = t->C;
-    g.DN = trans_data ? t->C : t->R;
-    g.OUT = trans_data ? t->R : t->C;
-    g.K = 4 * g.OUT;  // reduction length equals the output count (square matrices)
+    g.DN = st.DN;
+    g.OUT = t->cst_out[st.m];
+    g.K = 4 * t->cst_v[st.m];
+    g.logDt = ilog2(st.Dt ? st.Dt : 1);
+    g.twA = st.twA;
+    g.twB = st.twB;
+    g.twC = st.twC;
+    g.twL = st.twL;
+    g.logDd = ilog2(st.Dd ? st.Dd : 1);
+    g.rA = st.rA;
+    g.rB = st.rB;
+    g.rC = st.rC;
+    g.kB = st.kB;
+    g.kC = st.kC;
+    g.klen = st.klen;
+    g.orows = st.orows;
     CUtensorMap amap;
     if (!encode_map_2d(&amap, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, const_cast<uint16_t*>(adig), g.K,
                        (uint64_t)batch * g.L * g.DN, 2ull * g.K, BK, BM, CU_TENSOR_MAP_SWIZZLE_128B))
         return cudaErrorInvalidValue;
-    const CUtensorMap* bm = t->bmaps[stp];
-    const int tile = p->tc_tile == 32 ? 32 : 64;
-    if (outk == OUT_DIGITS_T) {
-        if (mul == MUL_TW_OUT_ROW) return launch_gemm<OUT_DIGITS_T, MUL_TW_OUT_ROW>(bm, tile, amap, g, s);
-        return launch_gemm<OUT_DIGITS_T, MUL_TW_DATA_ROW>(bm, tile, amap, g, s);
-    }
-    if (outk == OUT_U32_ROW_OUT) return launch_gemm<OUT_U32_ROW_OUT, MUL_NONE>(bm, tile, amap, g, s);
-    switch (mul) {
-        case MUL_HAD: return launch_gemm<OUT_U32_ROW_DATA, MUL_HAD>(bm, tile, amap, g, s);
-        case MUL_SQUARE: return launch_gemm<OUT_U32_ROW_DATA, MUL_SQUARE>(bm, tile, amap, g, s);
-        default: return launch_gemm<OUT_U32_ROW_DATA, MUL_NONE>(bm, tile, amap, g, s);
+    const uint32_t tile = std::min<uint32_t>(p->tc_tile == 32 ? 32u : 64u, g.OUT);
+    const CUtensorMap* b3 = t->bmaps[st.m];
+    if (st.outk == OUT_DIGITS) return launch_gemm<OUT_DIGITS, MUL_TW>(b3, tile, amap, g, s);
+    if (st.outk == OUT_U32_ROW_OUT) return launch_gemm<OUT_U32_ROW_OUT, MUL_NONE>(b3, tile, amap, g, s);
+    switch (st.mul) {
+        case MUL_HAD: return launch_gemm<OUT_U32_ROW_DATA, MUL_HAD>(b3, tile, amap, g, s);
+        case MUL_SQUARE: return launch_gemm<OUT_U32_ROW_DATA, MUL_SQUARE>(b3, tile, amap, g, s);
+        default: return launch_gemm<OUT_U32_ROW_DATA, MUL_NONE>(b3, tile, amap, g, s);
     }
 }
 
-cudaError_t digitize(const hefx_params* p, const uint32_t* in, uint16_t* dig, bool trans, size_t batch,
-                     cudaStream_t s) {
-    const Tc2Tables* t = p->tc2;
+cudaError_t digitize(const hefx_params* p, const uint32_t* in, uint16_t* dig, bool trans, uint32_t R, uint32_t C,
+                     size_t batch, cudaStream_t s) {
     const size_t mats = batch * p->nlimbs;
     const size_t work = mats * p->n / 4;
     const unsigned grid = (unsigned)std::min<size_t>((work + 255) / 256, (size_t)1 << 20);
-    if (trans) {  // R, C >= 128 (14 <= log2 N <= 16): multiples of 64
-        const size_t tiles = mats * (t->R / 64) * (t->C / 64);
+    if (trans) {  // R, C multiples of 64
+        const size_t tiles = mats * (R / 64) * (C / 64);
         int dev = 0, sms = 148;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         // persistent: 8 blocks of 256 threads per SM (16.6 KiB of shared memory each)
-        tc2::digitize_t64_kernel<<<(unsigned)std::min<size_t>(tiles, (size_t)sms * 8), 256, 0, s>>>(in, dig, t->R,
-                                                                                                   t->C, mats);
+        tc2::digitize_t64_kernel<<<(unsigned)std::min<size_t>(tiles, (size_t)sms * 8), 256, 0, s>>>(in, dig, R, C,
+                                                                                                   mats);
     } else
-        tc2::digitize_kernel<<<grid, 256, 0, s>>>(in, dig, t->R, t->C, mats);
+        tc2::digitize_kernel<<<grid, 256, 0, s>>>(in, dig, R, C, mats);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-// forward: digits(A^T) -> [W1 step, x T] -> digits -> [W3 step] -> out
+// forward: digits of the columns -> [step 1 over R, x T] -> digits -> ... -> residues in
+// bit-reversed order (two or three steps; see Tc2Tables)
 cudaError_t tc2_forward(hefx_params* p, const uint32_t* in, uint32_t* out, int mul, const uint32_t* had, size_t batch,
                         cudaStream_t s) {
     using namespace tc2;
     Tc2Tables* t = p->tc2;
-    const size_t elems = batch * p->nlimbs * (size_t)p->n;
-    cudaError_t e = ensure_workspace(t, elems);
-    if (e == cudaSuccess) e = digitize(p, in, t->dig1, true, batch, s);
-    if (e == cudaSuccess) e = step(p, FWD1, OUT_DIGITS_T, MUL_TW_OUT_ROW, t->dig1, t->dig3, nullptr, nullptr, batch, s);
-    if (e == cudaSuccess) e = step(p, FWD3, OUT_U32_ROW_DATA, mul, t->dig3, nullptr, out, had, batch, s);
+    const uint32_t N = p->n, R = t->f[0], C = N / R;
+    cudaError_t e = ensure_workspace(t, batch * p->nlimbs * (size_t)N);
+    if (e == cudaSuccess) e = digitize(p, in, t->dig1, true, R, C, batch, s);
+    if (t->nsteps == 2) {
+        const StepSpec s1 = {0, C, OUT_DIGITS, MUL_TW, t->twf[0], C, C, 1, 0, N, C, 1, 0, 0, 1, 0, C, R};
+        const StepSpec s2 = {1, R, OUT_U32_ROW_DATA, mul, nullptr, 1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 0, 0, 0};
+        if (e == cudaSuccess) e = run_step(p, s1, t->dig1, t->dig3, nullptr, nullptr, batch, s);
+        if (e == cudaSuccess) e = run_step(p, s2, t->dig3, nullptr, out, had, batch, s);
+        return e;
+    }
+    const uint32_t R2 = t->f[1], R3 = t->f[2];
+    // step 1: data row j = j2 R3 + j3 -> digits of row (p1, j3), position j2
+    const StepSpec s1 = {0, C, OUT_DIGITS, MUL_TW, t->twf[0], C, C, 1, 0, N, R3, R3, 1, 0, 0, 1, R2, R * R3};
+    // step 2: data row (p1, j3), output p2 -> digits of row (p1, p2), position j3
+    const StepSpec s2 = {1, R * R3, OUT_DIGITS, MUL_TW, t->twf[1], R3, R3, 1, 0, R2 * R3, R3, 1, 0, R2, 1, 0, R3, R * R2};
+    // step 3: data row (p1, p2), outputs p3 -> residue at p1 R2 R3 + p2 R3 + p3
+    const StepSpec s3 = {2, R * R2, OUT_U32_ROW_DATA, mul, nullptr, 1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 0, 0, 0};
+    if (e == cudaSuccess) e = run_step(p, s1, t->dig1, t->dig3, nullptr, nullptr, batch, s);
+    if (e == cudaSuccess) e = run_step(p, s2, t->dig3, t->dig1, nullptr, nullptr, batch, s);
+    if (e == cudaSuccess) e = run_step(p, s3, t->dig1, nullptr, out, had, batch, s);
     return e;
 }
 
-// inverse: digits(Ahat) -> [V3 step, x Tinv] -> digits (transposed) -> [V1 step, N^-1] -> out
+// inverse: digits of the rows -> the mirror steps (twiddles inverted, N^-1 in the last) ->
+// residues in natural order
 cudaError_t tc2_inverse(hefx_params* p, const uint32_t* in, uint32_t* out, size_t batch, cudaStream_t s) {
     using namespace tc2;
     Tc2Tables* t = p->tc2;
-    const size_t elems = batch * p->nlimbs * (size_t)p->n;
-    cudaError_t e = ensure_workspace(t, elems);
-    if (e == cudaSuccess) e = digitize(p, in, t->dig1, false, batch, s);
-    if (e == cudaSuccess) e = step(p, INV1, OUT_DIGITS_T, MUL_TW_DATA_ROW, t->dig1, t->dig3, nullptr, nullptr, batch, s);
-    if (e == cudaSuccess) e = step(p, INV3, OUT_U32_ROW_OUT, MUL_NONE, t->dig3, nullptr, out, nullptr, batch, s);
+    const uint32_t N = p->n, R = t->f[0], C = N / R;
+    cudaError_t e = ensure_workspace(t, batch * p->nlimbs * (size_t)N);
+    if (t->nsteps == 2) {
+        if (e == cudaSuccess) e = digitize(p, in, t->dig1, false, R, C, batch, s);
+        // data row p1, output j2; twiddle stored [j2][p1]; digits of row j2, position p1
+        const StepSpec s1 = {2, R, OUT_DIGITS, MUL_TW, t->twi[0], R, R, 1, 0, N, R, 1, 0, 0, 1, 0, R, C};
+        const StepSpec s2 = {3, C, OUT_U32_ROW_OUT, MUL_NONE, nullptr, 1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 0, 0, 0};
+        if (e == cudaSuccess) e = run_step(p, s1, t->dig1, t->dig3, nullptr, nullptr, batch, s);
+        if (e == cudaSuccess) e = run_step(p, s2, t->dig3, nullptr, out, nullptr, batch, s);
+        return e;
+    }
+    const uint32_t R2 = t->f[1], R3 = t->f[2];
+    if (e == cudaSuccess) e = digitize(p, in, t->dig1, false, R * R2, R3, batch, s);
+    // inverse step 1: data row (p1, p2), output j3; twiddle T2inv[p2][j3]; digits of row (p1, j3), position p2
+    const StepSpec s1 = {3, R * R2, OUT_DIGITS, MUL_TW, t->twi[0], R2, 1, R3, 0, R2 * R3, R2, 1, 0, R3, 1, 0, R2, R * R3};
+    // inverse step 2: data row (p1, j3), output j2; twiddle Tinv[j2 R3 + j3][p1]; digits of row j, position p1
+    const StepSpec s2 = {4, R * R3, OUT_DIGITS, MUL_TW, t->twi[1], R3, R3 * R, R, 1, N, R3, R3, 1, 0, 0, 1, R, C};
+    // inverse step 3: data row j, output j1 (N^-1 folded) -> residue j1 C + j
+    const StepSpec s3 = {5, C, OUT_U32_ROW_OUT, MUL_NONE, nullptr, 1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 0, 0, 0};
+    if (e == cudaSuccess) e = run_step(p, s1, t->dig1, t->dig3, nullptr, nullptr, batch, s);
+    if (e == cudaSuccess) e = run_step(p, s2, t->dig3, t->dig1, nullptr, nullptr, batch, s);
+    if (e == cudaSuccess) e = run_step(p, s3, t->dig1, nullptr, out, nullptr, batch, s);
     return e;
 }
 

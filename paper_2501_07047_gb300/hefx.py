@@ -32,7 +32,7 @@ SIGNATURES = {
     "hefx_params_destroy": (None, [_vp]),
     "hefx_params_set_auto_path": (_i32, [_vp, _i32]),
     "hefx_params_set_reduction": (_i32, [_vp, _i32, _i32]),
-    "hefx_params_set_tensor_config": (_i32, [_vp, _u32, _u32]),
+    "hefx_params_set_tensor_config": (_i32, [_vp, _u32, _u32, _u32]),
     "hefx_ntt_fwd": (_i32, [_vp, _vp, _vp, _sz, _i32, _vp]),
     "hefx_ntt_inv": (_i32, [_vp, _vp, _vp, _sz, _i32, _vp]),
     "hefx_poly_mul": (_i32, [_vp, _vp, _vp, _vp, _vp, _sz, _i32, _vp]),
@@ -170,9 +170,10 @@ def hefx_params_set_reduction(ctx, params: int, ntt_red="shoup", vec_red="montgo
     _check(ctx, load().hefx_params_set_reduction(params, REDUCTIONS[ntt_red], REDUCTIONS[vec_red]))
 
 
-def hefx_params_set_tensor_config(ctx, params: int, log2r: int = 0, tile_outputs: int = 64) -> None:
-    """Tensor-path split N = 2^log2r x N / 2^log2r (0: the square one) and GEMM tile width."""
-    _check(ctx, load().hefx_params_set_tensor_config(params, int(log2r), int(tile_outputs)))
+def hefx_params_set_tensor_config(ctx, params: int, log2r: int = 0, tile_outputs: int = 64, log2r2: int = 0) -> None:
+    """Tensor-path split (N = 2^log2r x rest, or with log2r2 > 0 the three factors 2^log2r x
+    2^log2r2 x rest; log2r = 0: the square two-factor split) and GEMM tile width."""
+    _check(ctx, load().hefx_params_set_tensor_config(params, int(log2r), int(log2r2), int(tile_outputs)))
 
 
 def hefx_ntt_fwd(ctx, params, data, batch, path="cudacore", stream=None) -> None:

@@ -6,25 +6,39 @@
 K_IN, W_IN, K_OUT, W_OUT = 4, 7, 4, 7
 
 
-def split(logn: int, log2r: int = 0):
-    """R x C split of N = 2^logn used by the tensor path (log2r = 0: the default, R =
-    2^floor(logn / 2))."""
+def split(logn: int, log2r: int = 0, log2r2: int = 0):
+    """Factors of N = 2^logn used by the tensor path: (R, C) for two factors (log2r = 0: R =
+    2^floor(logn / 2)), (R1, R2, R3) when log2r2 > 0."""
     r = log2r or logn // 2
+    if log2r2:
+        return 1 << r, 1 << log2r2, 1 << (logn - r - log2r2)
     return 1 << r, 1 << (logn - r)
 
 
 def splits(logn: int) -> list:
-    """log2 R of every split the tensor path accepts at N = 2^logn: both factors 128 or 256
-    (128-row data blocks; exact fp32 sums of 7-bit digit products need reduction lengths of at
-    most 256: 4 * 256 * 127 * 127 < 2^24)."""
-    return [r for r in (7, 8) if 7 <= logn - r <= 8]
+    """(log2r, log2r2) of every split the tensor path accepts at N = 2^logn.
+    Two factors: both 128 or 256 (128-row data blocks; exact fp32 sums of 7-bit digit products
+    need reduction lengths of at most 256: 4 * 256 * 127 * 127 < 2^24).  Three factors: the
+    first 64 .. 256 (64-wide transposing digit split), the others 16 .. 256."""
+    two = [(r, 0) for r in (7, 8) if 7 <= logn - r <= 8]
+    three = [(a, b) for a in (6, 7, 8) for b in (4, 5, 6, 7, 8) if 4 <= logn - a - b <= 8]
+    return two + three
 
 
-def flops_per_limb_ntt(logn: int, log2r: int = 0) -> float:
-    """2 flops per digit multiply-accumulate over both matrix steps:
-    step 1 (R data columns of K_IN R digits) by (K_OUT R) constant rows, step 3 likewise with C."""
-    R, C = split(logn, log2r)
-    return 2.0 * K_IN * K_OUT * R * C * (R + C)
+def tuned_splits(logn: int) -> list:
+    """The splits the autotuner times: every two-factor split, and the three-factor splits with
+    the fewest digit MACs (smallest R1 + R2 + R3)."""
+    all_ = splits(logn)
+    three = [s for s in all_ if s[1]]
+    best = min((sum(split(logn, *s)) for s in three), default=None)
+    return [s for s in all_ if not s[1]] + [s for s in three if sum(split(logn, *s)) == best]
+
+
+def flops_per_limb_ntt(logn: int, log2r: int = 0, log2r2: int = 0) -> float:
+    """2 flops per digit multiply-accumulate over the matrix steps: a step over a factor f
+    takes N / f data rows of K_IN f digits against K_OUT f constant rows, so each step costs
+    K_IN K_OUT N f and the transform K_IN K_OUT N (sum of the factors)."""
+    return 2.0 * K_IN * K_OUT * (1 << logn) * sum(split(logn, log2r, log2r2))
 
 
 def flops_per_step_launch(logn: int, limbs: int) -> float:

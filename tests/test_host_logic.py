@@ -96,28 +96,39 @@ def test_tensor_work_model():
 
 
 def test_tuner_candidates_and_cached_choice(tmp_path, monkeypatch):
-    """The tuner's search space (path x valid split x tile) and its cache: a measured winner is
+    """The tuner's search space (path x split x tile) and its cache: a measured winner is
     stored per shape and batch and reapplied without timing again."""
     import torch
     from paper_2501_07047_gb300 import autotune, tensor_plan
-    assert tensor_plan.splits(15) == [7, 8] and tensor_plan.splits(16) == [8] and tensor_plan.splits(14) == [7]
-    assert tensor_plan.splits(13) == [] and tensor_plan.splits(17) == []
-    assert autotune.candidates(13) == [("cudacore", 0, 0)]
-    assert len(autotune.candidates(15)) == 1 + 2 * len(autotune.TILES)
-    for logn in (14, 15, 16):  # every tensor candidate multiplies out to N with factors 128 or 256
-        for path, log2r, tile in autotune.candidates(logn)[1:]:
-            R, C = tensor_plan.split(logn, log2r)
-            assert R * C == 1 << logn and R in (128, 256) and C in (128, 256) and tile in (32, 64)
-    assert autotune.parse("tensor/7/32") == ("tensor", 7, 32)
+    assert [s for s in tensor_plan.splits(15) if not s[1]] == [(7, 0), (8, 0)]
+    assert [s for s in tensor_plan.splits(16) if not s[1]] == [(8, 0)]
+    assert tensor_plan.tuned_splits(16) == [(8, 0), (6, 5)]            # 256 x 256 and 64 x 32 x 32
+    assert tensor_plan.tuned_splits(14) == [(7, 0), (6, 4)]            # 128 x 128 and 64 x 16 x 16
+    assert tensor_plan.splits(13) == [] and tensor_plan.splits(12) == []
+    assert autotune.candidates(13) == [("cudacore", 0, 0, 0)]
+    for logn in (14, 15, 16):
+        for log2r, log2r2 in tensor_plan.splits(logn):  # every split multiplies out to N within bounds
+            f = tensor_plan.split(logn, log2r, log2r2)
+            assert int(np.prod(f)) == 1 << logn
+            if log2r2:
+                assert 64 <= f[0] <= 256 and all(16 <= x <= 256 for x in f[1:])
+            else:
+                assert all(x in (128, 256) for x in f)
+        for cand in autotune.candidates(logn)[1:]:
+            assert cand[0] == "tensor" and cand[3] in autotune.TILES
+            assert autotune.parse(autotune.key_of(cand)) == cand
+    # digit MACs: the three-factor split costs (R1 + R2 + R3) / (R + C) of the two-factor one
+    assert tensor_plan.flops_per_limb_ntt(16, 6, 5) * 4 == tensor_plan.flops_per_limb_ntt(16)
     monkeypatch.setattr(autotune, "CACHE", str(tmp_path / "tune.json"))
     monkeypatch.setattr(torch.cuda, "get_device_name", lambda *a: "FAKE-GPU")
     timed, applied = [], []
     monkeypatch.setattr(autotune, "time_candidates",
-                        lambda *a, **k: timed.append(1) or {"cudacore/0/0": 2.0, "tensor/7/32": 1.5, "tensor/8/64": 1.7})
+                        lambda *a, **k: timed.append(1) or {"cudacore/0/0/0": 2.0, "tensor/6/5/32": 1.5,
+                                                            "tensor/8/0/64": 1.7})
     monkeypatch.setattr(autotune, "apply", lambda ctx, p, cand: applied.append(cand))
-    assert autotune.tune(None, None, 15, [268042241, 265420801]) == "tensor"
-    assert applied[-1] == ("tensor", 7, 32) and len(timed) == 1
-    assert autotune.tune(None, None, 15, [268042241, 265420801]) == "tensor"  # from the cache
-    assert applied[-1] == ("tensor", 7, 32) and len(timed) == 1
-    assert autotune.tune(None, None, 15, [268042241, 265420801], batch=8) == "tensor"  # another batch: timed
+    assert autotune.tune(None, None, 16, [268042241, 265420801]) == "tensor"
+    assert applied[-1] == ("tensor", 6, 5, 32) and len(timed) == 1
+    assert autotune.tune(None, None, 16, [268042241, 265420801]) == "tensor"  # from the cache
+    assert applied[-1] == ("tensor", 6, 5, 32) and len(timed) == 1
+    assert autotune.tune(None, None, 16, [268042241, 265420801], batch=8) == "tensor"  # another batch: timed
     assert len(timed) == 2

@@ -262,7 +262,7 @@ def test_autotune_sets_auto_path(ctx, tmp_path, monkeypatch, logn):
         best = autotune.tune(ctx, p, logn, primes)
         assert best in ("cudacore", "tensor")
         entry = next(iter(json.load(open(tmp_path / "tune.json")).values()))
-        assert set(entry["ms"]) == {f"{c[0]}/{c[1]}/{c[2]}" for c in autotune.candidates(logn)}
+        assert set(entry["ms"]) == {autotune.key_of(c) for c in autotune.candidates(logn)}
         data = inputs.residue_tensor(inputs.derive_seed(12, logn), 2, primes, 1 << logn)
         assert (run_fwd(ctx, p, data, "auto") == oracle.ntt_batch(data, primes)).all()
     finally:
@@ -271,9 +271,9 @@ def test_autotune_sets_auto_path(ctx, tmp_path, monkeypatch, logn):
 
 @pytest.mark.parametrize("logn", [14, 15, 16])
 def test_tensor_configs_bit_exact(ctx, logn):
-    """Every tensor-path split and tile width gives the oracle's transforms and products;
-    invalid splits and tiles are refused."""
-    from paper_2501_07047_gb300 import autotune
+    """Every tensor-path split (two factors, and every three-factor split) with both tile widths
+    gives the oracle's transforms and products; invalid splits and tiles are refused."""
+    from paper_2501_07047_gb300 import tensor_plan
     primes = inputs.source_primes(3)
     n = 1 << logn
     p = make_params(ctx, logn, primes)
@@ -282,22 +282,24 @@ def test_tensor_configs_bit_exact(ctx, logn):
         b = inputs.residue_tensor(inputs.derive_seed(13, logn, 1), 2, primes, n)
         want_f = oracle.ntt_batch(a, primes)
         want_m = oracle.polymul_batch(a, b, primes)
-        for _, log2r, tile in autotune.candidates(logn)[1:]:
-            hefx.hefx_params_set_tensor_config(ctx, p, log2r, tile)
-            got = run_fwd(ctx, p, a, "tensor")
-            assert (got == want_f).all(), (log2r, tile)
-            assert (run_inv(ctx, p, got, "tensor") == a).all(), (log2r, tile)
-            da, db, dc = to_dev(a), to_dev(b), empty_dev(a.shape)
-            hefx.hefx_poly_mul(ctx, p, da, db, dc, 2, "tensor")
-            hefx.hefx_stream_check(ctx, p)
-            assert (to_host(dc).reshape(a.shape) == want_m).all(), (log2r, tile)
-        for bad in ((logn // 2 - 2, 64), (0, 48)):
+        for log2r, log2r2 in tensor_plan.splits(logn):
+            for tile in (64, 32):
+                hefx.hefx_params_set_tensor_config(ctx, p, log2r, tile, log2r2)
+                got = run_fwd(ctx, p, a, "tensor")
+                assert (got == want_f).all(), (log2r, log2r2, tile)
+                assert (run_inv(ctx, p, got, "tensor") == a).all(), (log2r, log2r2, tile)
+                rnd = inputs.residue_tensor(inputs.derive_seed(14, logn), 1, primes, n)
+                assert (run_inv(ctx, p, rnd, "tensor") == oracle.ntt_batch(rnd, primes, inverse=True)).all()
+                da, db, dc = to_dev(a), to_dev(b), empty_dev(a.shape)
+                hefx.hefx_poly_mul(ctx, p, da, db, dc, 2, "tensor")
+                hefx.hefx_stream_check(ctx, p)
+                assert (to_host(dc).reshape(a.shape) == want_m).all(), (log2r, log2r2, tile)
+        for bad in ((logn // 2 - 2, 64, 0), (0, 48, 0), (5, 64, 5), (6, 64, 3)):
             with pytest.raises(hefx.HefxError) as e:
-                hefx.hefx_params_set_tensor_config(ctx, p, *bad)
+                hefx.hefx_params_set_tensor_config(ctx, p, bad[0], bad[1], bad[2])
             assert e.value.status == hefx.HEFX_EINVAL
     finally:
         hefx.hefx_params_destroy(p)
-
 
 # ----------------------------------------------------------------------------- N = 2^17
 
