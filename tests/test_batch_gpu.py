@@ -102,3 +102,68 @@ def test_config4_full_size(ctx):
             assert (got == want).all(), (j, shapes[j])
     finally:
         batch.close()
+
+
+def test_fused_batch_edges(ctx):
+    """The one-launch batch with every ring degree it takes (2^10 .. 2^16), squares, c aliasing
+    a or b, and counts of split rows (2^14 .. 2^16) that leave the last cluster task partly
+    filled (scratch rows fill it); one launch, every limb against the oracle, replayed."""
+    primes = inputs.source_primes(5)
+    params = {logn: hefx.hefx_params_create(ctx, logn, primes) for logn in range(10, 17)}
+    try:
+        jobs, expect_list, keep = [], [], []
+        spec = [(10, 3, "ab"), (11, 2, "sq"), (12, 5, "ca"), (13, 1, "cb"), (14, 3, "ab"), (14, 1, "sq"),
+                (15, 1, "ab"), (15, 2, "sq"), (16, 3, "cb"), (16, 2, "ab"), (13, 4, "sq"), (12, 1, "ab")]
+        for k, (logn, L, kind) in enumerate(spec):
+            n = 1 << logn
+            ha = inputs.residue_tensor(inputs.derive_seed(120, k, 0), 1, primes[:L], n)[0]
+            hb = inputs.residue_tensor(inputs.derive_seed(120, k, 1), 1, primes[:L], n)[0]
+            a, b = to_dev(ha), to_dev(hb)
+            if kind == "sq":
+                c = torch.empty((L, n), dtype=torch.int32, device="cuda")
+                jobs.append((params[logn], L, a, a, c))
+                want = oracle.polymul_batch(ha[None], ha[None], primes[:L])[0]
+            elif kind == "ca":
+                c = a
+                jobs.append((params[logn], L, a, b, c))
+                want = oracle.polymul_batch(ha[None], hb[None], primes[:L])[0]
+            elif kind == "cb":
+                c = b
+                jobs.append((params[logn], L, a, b, c))
+                want = oracle.polymul_batch(ha[None], hb[None], primes[:L])[0]
+            else:
+                c = torch.empty((L, n), dtype=torch.int32, device="cuda")
+                jobs.append((params[logn], L, a, b, c))
+                want = oracle.polymul_batch(ha[None], hb[None], primes[:L])[0]
+            keep.append((a, b, c))
+            expect_list.append((c, want))
+        plan = hefx.hefx_batch_plan_create(ctx, jobs)
+        try:
+            assert hefx.hefx_batch_plan_launches(plan) == 1
+            s = torch.cuda.Stream()
+            with torch.cuda.stream(s):
+                hefx.hefx_batch_polymul(ctx, plan, s)
+            s.synchronize()
+            for k, (c, want) in enumerate(expect_list):
+                assert (to_host(c).reshape(want.shape) == want).all(), spec[k]
+        finally:
+            hefx.hefx_batch_plan_destroy(plan)
+        # a ring degree below 2^10 keeps the per-size-class launches
+        p8 = hefx.hefx_params_create(ctx, 8, primes)
+        try:
+            ha = inputs.residue_tensor(inputs.derive_seed(121, 0), 1, primes[:2], 256)[0]
+            a, c = to_dev(ha), torch.empty((2, 256), dtype=torch.int32, device="cuda")
+            plan = hefx.hefx_batch_plan_create(ctx, [(p8, 2, a, a, c), (params[12], 1, keep[0][0], keep[0][0],
+                                                                          torch.empty((1, 4096), dtype=torch.int32,
+                                                                                      device="cuda"))])
+            try:
+                assert hefx.hefx_batch_plan_launches(plan) > 1
+                hefx.hefx_batch_polymul(ctx, plan, None)
+                assert (to_host(c).reshape(2, 256) == oracle.polymul_batch(ha[None], ha[None], primes[:2])[0]).all()
+            finally:
+                hefx.hefx_batch_plan_destroy(plan)
+        finally:
+            hefx.hefx_params_destroy(p8)
+    finally:
+        for p in params.values():
+            hefx.hefx_params_destroy(p)

@@ -139,3 +139,34 @@ def test_grouped_equals_alone_and_oracle(ctx):
     finally:
         alone_ex.close()
         grouped_ex.close()
+
+
+def test_mult_batch_validation(ctx):
+    """Batched requests must share the ring degree and P; the batch object bounds count and limbs."""
+    import torch
+    ex = GpuExecutor(ctx, nstreams=1, seed=13, slots=2)
+    try:
+        r13, r14 = ex.shape(13, 8), ex.shape(14, 8)
+        mb = hefx.hefx_mult_batch_create(ctx, 2, 8)
+        try:
+            pl = ex.pool(13)["host_in"][0]
+            slot = ex._slot()
+            args = [pl[c] for c in range(4)]
+            with pytest.raises(hefx.HefxError) as e:  # mixed ring degrees
+                hefx.hefx_mult_front_batch_host(ctx, mb, [r13["mp"], r14["mp"]], *[[a, a] for a in args],
+                                                [slot["h"], slot["h"]], [slot["d"], slot["d"]])
+            assert e.value.status == hefx.HEFX_EINVAL
+            with pytest.raises(hefx.HefxError) as e:  # more requests than the object holds
+                hefx.hefx_mult_front_batch_host(ctx, mb, [r13["mp"]] * 3, *[[a] * 3 for a in args],
+                                                [slot["h"]] * 3, [slot["d"]] * 3)
+            assert e.value.status == hefx.HEFX_EINVAL
+            big = ex.shape(13, 9)
+            with pytest.raises(hefx.HefxError) as e:  # more limbs than the object holds
+                hefx.hefx_mult_front_batch_host(ctx, mb, [big["mp"]], *[[a] for a in args], [slot["h"]], [slot["d"]])
+            assert e.value.status == hefx.HEFX_EINVAL
+            hefx.hefx_mult_front_batch_host(ctx, mb, [], [], [], [], [], [], [])  # nothing to do
+            torch.cuda.synchronize()
+        finally:
+            hefx.hefx_mult_batch_destroy(mb)
+    finally:
+        ex.close()
