@@ -337,8 +337,12 @@ __device__ __forceinline__ void load_tile64(const uint32_t* __restrict__ in, uin
     }
 }
 
+// Column c of the data matrix becomes A row (c mod pr3) pr2 + c div pr3 (pr3 = 1: row c): the
+// three-factor split orders its first step's rows (j2, j3) as (j3, j2) so that the step's
+// epilogue writes its digits lane-contiguously.
 __global__ void __launch_bounds__(256) digitize_t64_kernel(const uint32_t* __restrict__ in, uint16_t* __restrict__ dig,
-                                                           uint32_t R, uint32_t C, size_t mats) {
+                                                           uint32_t R, uint32_t C, size_t mats, uint32_t pr2,
+                                                           uint32_t pr3) {
     __shared__ uint32_t tile[64][65];
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const size_t tiles_per = (size_t)(R / 64) * (C / 64), total = mats * tiles_per;
@@ -363,8 +367,9 @@ __global__ void __launch_bounds__(256) digitize_t64_kernel(const uint32_t* __res
         for (int k = 0; k < 8; ++k) {
             const uint32_t c = warp + 8 * k;  // this warp's column of the tile
             const uint2 lo = tc::split_digits4(tile[2 * lane][c]), hi = tc::split_digits4(tile[2 * lane + 1][c]);
-            // A row c0 + c, K = 4 (r0 + 2 lane) .. + 7
-            *reinterpret_cast<uint4*>(dst + (size_t)(c0 + c) * (4 * R) + 4 * (r0 + 2 * lane)) =
+            // A row of column c0 + c, K = 4 (r0 + 2 lane) .. + 7
+            const uint32_t col = c0 + c, arow = (col % pr3) * pr2 + col / pr3;
+            *reinterpret_cast<uint4*>(dst + (size_t)arow * (4 * R) + 4 * (r0 + 2 * lane)) =
                 make_uint4(lo.x, lo.y, hi.x, hi.y);
         }
         __syncthreads();
@@ -489,7 +494,9 @@ cudaError_t tc2_prepare(hefx_params* p) {
                 put(2 * ns - 1, j1, p1, mul_mod(ninv, Pn((uint64_t)C * j1 * kodd), q));
             }
             for (uint32_t j = 0; j < C; ++j) {
-                hTf[0][(size_t)l * N + (size_t)p1 * C + j] = shoup2(P((uint64_t)j * kodd));
+                // three factors: the first step's data rows come in the order (j3, j2)
+                const uint32_t jr = ns == 3 ? (j % R3) * R2 + j / R3 : j;
+                hTf[0][(size_t)l * N + (size_t)p1 * C + jr] = shoup2(P((uint64_t)j * kodd));
                 hTi[ns - 2][(size_t)l * N + (size_t)j * R + p1] = shoup2(Pn((uint64_t)j * kodd));
             }
         }
@@ -514,7 +521,7 @@ cudaError_t tc2_prepare(hefx_params* p) {
                 }
                 for (uint32_t j3 = 0; j3 < R3; ++j3) {
                     hTf[1][(size_t)l * R2 * R3 + (size_t)p2 * R3 + j3] = shoup2(P(2ull * R * j3 * b2));
-                    hTi[0][(size_t)l * R2 * R3 + (size_t)p2 * R3 + j3] = shoup2(Pn(2ull * R * j3 * b2));
+                    hTi[0][(size_t)l * R2 * R3 + (size_t)j3 * R2 + p2] = shoup2(Pn(2ull * R * j3 * b2));
                 }
             }
             for (uint32_t p3 = 0; p3 < R3; ++p3) {
@@ -705,7 +712,7 @@ cudaError_t run_step(const hefx_params* p, const StepSpec& st, const uint16_t* a
 }
 
 cudaError_t digitize(const hefx_params* p, const uint32_t* in, uint16_t* dig, bool trans, uint32_t R, uint32_t C,
-                     size_t batch, cudaStream_t s) {
+                     size_t batch, cudaStream_t s, uint32_t pr2 = 1, uint32_t pr3 = 1) {
     const size_t mats = batch * p->nlimbs;
     const size_t work = mats * p->n / 4;
     const unsigned grid = (unsigned)std::min<size_t>((work + 255) / 256, (size_t)1 << 20);
@@ -716,7 +723,7 @@ cudaError_t digitize(const hefx_params* p, const uint32_t* in, uint16_t* dig, bo
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         // persistent: 8 blocks of 256 threads per SM (16.6 KiB of shared memory each)
         tc2::digitize_t64_kernel<<<(unsigned)std::min<size_t>(tiles, (size_t)sms * 8), 256, 0, s>>>(in, dig, R, C,
-                                                                                                   mats);
+                                                                                                   mats, pr2, pr3);
     } else
         tc2::digitize_kernel<<<grid, 256, 0, s>>>(in, dig, R, C, mats);
     return cudaGetLastError();
@@ -732,8 +739,8 @@ cudaError_t tc2_forward(hefx_params* p, const uint32_t* in, uint32_t* out, int m
     Tc2Tables* t = p->tc2;
     const uint32_t N = p->n, R = t->f[0], C = N / R;
     cudaError_t e = ensure_workspace(t, batch * p->nlimbs * (size_t)N);
-    if (e == cudaSuccess) e = digitize(p, in, t->dig1, true, R, C, batch, s);
     if (t->nsteps == 2) {
+        if (e == cudaSuccess) e = digitize(p, in, t->dig1, true, R, C, batch, s);
         const StepSpec s1 = {0, C, OUT_DIGITS, MUL_TW, t->twf[0], C, C, 1, 0, N, C, 1, 0, 0, 1, 0, C, R};
         const StepSpec s2 = {1, R, OUT_U32_ROW_DATA, mul, nullptr, 1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 0, 0, 0};
         if (e == cudaSuccess) e = run_step(p, s1, t->dig1, t->dig3, nullptr, nullptr, batch, s);
@@ -741,8 +748,10 @@ cudaError_t tc2_forward(hefx_params* p, const uint32_t* in, uint32_t* out, int m
         return e;
     }
     const uint32_t R2 = t->f[1], R3 = t->f[2];
-    // step 1: data row j = j2 R3 + j3 -> digits of row (p1, j3), position j2
-    const StepSpec s1 = {0, C, OUT_DIGITS, MUL_TW, t->twf[0], C, C, 1, 0, N, R3, R3, 1, 0, 0, 1, R2, R * R3};
+    if (e == cudaSuccess) e = digitize(p, in, t->dig1, true, R, C, batch, s, R2, R3);
+    // step 1: data row j3 R2 + j2 (column j = j2 R3 + j3, reordered by the digit split; T stored
+    // in that order) -> digits of row (p1, j3), position j2 (lanes write consecutive positions)
+    const StepSpec s1 = {0, C, OUT_DIGITS, MUL_TW, t->twf[0], C, C, 1, 0, N, R2, R3, 0, 1, 1, 0, R2, R * R3};
     // step 2: data row (p1, j3), output p2 -> digits of row (p1, p2), position j3
     const StepSpec s2 = {1, R * R3, OUT_DIGITS, MUL_TW, t->twf[1], R3, R3, 1, 0, R2 * R3, R3, 1, 0, R2, 1, 0, R3, R * R2};
     // step 3: data row (p1, p2), outputs p3 -> residue at p1 R2 R3 + p2 R3 + p3
@@ -771,10 +780,12 @@ cudaError_t tc2_inverse(hefx_params* p, const uint32_t* in, uint32_t* out, size_
     }
     const uint32_t R2 = t->f[1], R3 = t->f[2];
     if (e == cudaSuccess) e = digitize(p, in, t->dig1, false, R * R2, R3, batch, s);
-    // inverse step 1: data row (p1, p2), output j3; twiddle T2inv[p2][j3]; digits of row (p1, j3), position p2
-    const StepSpec s1 = {3, R * R2, OUT_DIGITS, MUL_TW, t->twi[0], R2, 1, R3, 0, R2 * R3, R2, 1, 0, R3, 1, 0, R2, R * R3};
-    // inverse step 2: data row (p1, j3), output j2; twiddle Tinv[j2 R3 + j3][p1]; digits of row j, position p1
-    const StepSpec s2 = {4, R * R3, OUT_DIGITS, MUL_TW, t->twi[1], R3, R3 * R, R, 1, N, R3, R3, 1, 0, 0, 1, R, C};
+    // inverse step 1: data row (p1, p2), output j3; twiddle T2inv stored [j3][p2]; digits of
+    // row (j3, p1), position p2
+    const StepSpec s1 = {3, R * R2, OUT_DIGITS, MUL_TW, t->twi[0], R2, R2, 1, 0, R2 * R3, R2, R, 0, 1, 1, 0, R2, R3 * R};
+    // inverse step 2: data row (j3, p1), output j2; twiddle Tinv[j2 R3 + j3][p1]; digits of row
+    // j = j2 R3 + j3, position p1 (lanes: consecutive p1 in both)
+    const StepSpec s2 = {4, R3 * R, OUT_DIGITS, MUL_TW, t->twi[1], R3 * R, R3 * R, 1, 0, N, R, R3, 0, 1, 1, 0, R, C};
     // inverse step 3: data row j, output j1 (N^-1 folded) -> residue j1 C + j
     const StepSpec s3 = {5, C, OUT_U32_ROW_OUT, MUL_NONE, nullptr, 1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 0, 0, 0};
     if (e == cudaSuccess) e = run_step(p, s1, t->dig1, t->dig3, nullptr, nullptr, batch, s);
