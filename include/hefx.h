@@ -143,6 +143,26 @@ typedef enum {
 hefx_status hefx_params_set_reduction(hefx_params* params, hefx_reduction ntt_red, hefx_reduction vec_red);
 
 /*
+ * Schedules of the CUDA-core NTT / INTT of contiguous rows (hefx_ntt_fwd, hefx_ntt_inv and the
+ * plain transforms inside other calls).  Both run the same radix-2 butterflies (App. A) and
+ * return identical results.
+ *  - HEFX_CC_CLUSTER: one launch; a row of N = 2^16 is split over a cluster of 8 CTAs and
+ *    its three cross-CTA stages go through distributed shared memory.
+ *  - HEFX_CC_TWO_PASS (N = 2^16 only): two launches through L2, the row / column
+ *    factorisation of the matrix NTT (Sec. IV-B) with the twiddle step folded into the
+ *    butterflies: 8 stages within columns j mod 256, then 8 within 256-element blocks
+ *    (reversed for the inverse); the intermediate goes through the output buffer.
+ *  - HEFX_CC_AUTO (default): HEFX_CC_TWO_PASS for at most 32 rows at N = 2^16 (a launch of
+ *    so few rows leaves most of the GPU idle under the cluster schedule; measured 20 % faster
+ *    for one polynomial of 24 limbs), else HEFX_CC_CLUSTER.
+ * Hadamard-fused forms (hefx_poly_mul), Rescale, row lists and batch plans use the cluster
+ * schedule.  Errors: EINVAL (unknown schedule), EUNSUPPORTED (HEFX_CC_TWO_PASS at
+ * N != 2^16).  Not thread-safe with concurrent calls that use the same params.
+ */
+typedef enum { HEFX_CC_AUTO = 0, HEFX_CC_CLUSTER = 1, HEFX_CC_TWO_PASS = 2 } hefx_cc_schedule;
+hefx_status hefx_params_set_cc_schedule(hefx_params* params, hefx_cc_schedule schedule);
+
+/*
  * In-place forward NTT of d_data[batch][nlimbs][N] (natural order in, bit-reversed out).
  * The definition is Sec. II-A's ring with the bit-reversed output of Sec. IV-B2; the
  * CUDA-core path follows App. A (radix-2 Cooley-Tukey), the tensor path Sec. IV-B

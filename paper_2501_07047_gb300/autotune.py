@@ -2,13 +2,14 @@
 and records the fastest as what HEFX_PATH_AUTO runs.
 
 Candidates (all bit-exact; checked by INTT(NTT(x)) = x before timing):
-  - the CUDA-core radix-2 path;
+  - the CUDA-core radix-2 path, under each of its schedules at N = 2^16 (one launch of 8-CTA
+    clusters, or the two-pass column / block schedule; `hefx_params_set_cc_schedule`);
   - the tensor-core matrix NTT for every valid two-factor split N = R x C and the three-factor
     splits R1 x R2 x R3 with the fewest digit MACs (`tensor_plan.tuned_splits`: the paper sweeps
     its (R, C) configurations per operator and keeps the best, Sec. V-A), each with both GEMM
     tile widths (64 or 32 outputs per tile).
 The winner is applied with `hefx_params_set_auto_path` and, for the tensor path,
-`hefx_params_set_tensor_config`.  Results are cached per GPU name, shape and batch in a JSON
+`hefx_params_set_tensor_config` (for the CUDA-core path, `hefx_params_set_cc_schedule`).  Results are cached per GPU name, shape and batch in a JSON
 file (`$HEFX_TUNE_CACHE`, default ~/.cache/hefx/tune.json).
 """
 from __future__ import annotations
@@ -43,11 +44,15 @@ def _save_cache(c: dict) -> None:
         pass
 
 
+CC_SCHEDULES = {0: "auto", 1: "cluster", 2: "two_pass"}
+
+
 def candidates(logn: int) -> list:
-    """Every configuration the tuner tries at N = 2^logn: ("cudacore", 0, 0, 0) and
-    ("tensor", log2 R1, log2 R2, tile) for each tuned split (two factors: log2 R2 = 0) and tile
-    width."""
-    out = [("cudacore", 0, 0, 0)]
+    """Every configuration the tuner tries at N = 2^logn: ("cudacore", schedule, 0, 0) for each
+    CUDA-core schedule built at this size (1 cluster, 2 two-pass; 0 the library's own choice
+    where there is no alternative) and ("tensor", log2 R1, log2 R2, tile) for each tuned split
+    (two factors: log2 R2 = 0) and tile width."""
+    out = [("cudacore", 1, 0, 0), ("cudacore", 2, 0, 0)] if logn == 16 else [("cudacore", 0, 0, 0)]
     for log2r, log2r2 in tensor_plan.tuned_splits(logn):
         for tile in TILES:
             out.append(("tensor", log2r, log2r2, tile))
@@ -58,6 +63,8 @@ def apply(ctx: int, params: int, cand) -> None:
     path, log2r, log2r2, tile = cand
     if path == "tensor":
         hefx.hefx_params_set_tensor_config(ctx, params, log2r, tile, log2r2)
+    else:
+        hefx.hefx_params_set_cc_schedule(ctx, params, CC_SCHEDULES[log2r])
     hefx.hefx_params_set_auto_path(params, path)
 
 
@@ -77,6 +84,8 @@ def time_candidates(ctx: int, params: int, logn: int, primes, batch: int = 4, re
             continue
         if path == "tensor":
             hefx.hefx_params_set_tensor_config(ctx, params, cand[1], cand[3], cand[2])
+        else:
+            hefx.hefx_params_set_cc_schedule(ctx, params, CC_SCHEDULES[cand[1]])
         d.copy_(d0)
         hefx.hefx_ntt_fwd(ctx, params, d, batch, path, s)
         hefx.hefx_ntt_inv(ctx, params, d, batch, path, s)

@@ -250,6 +250,8 @@ hefx_status hefx_params_create(hefx_ctx* ctx, uint32_t log2n, const uint32_t* pr
     for (uint32_t i = 0; i < nlimbs; ++i) p->max_prime = std::max(p->max_prime, primes[i]);
     std::vector<LimbConst> lc(nlimbs);
     std::vector<uint2> twf((size_t)nlimbs * n), twi((size_t)nlimbs * n);
+    const bool two_pass = log2n == 16;
+    std::vector<uint2> twf2(two_pass ? twf.size() : 0), twi2(two_pass ? twi.size() : 0);
     std::vector<uint64_t> pw(n), pwi(n);
     for (uint32_t l = 0; l < nlimbs; ++l) {
         const uint64_t q = primes[l];
@@ -265,29 +267,36 @@ hefx_status hefx_params_create(hefx_ctx* ctx, uint32_t log2n, const uint32_t* pr
         // G = J 2^v + g of sub-transform J sits at stage_base + g * (N / 2^RS) + J, so the
         // lanes of a warp (consecutive J) read consecutive entries (MAT's offline
         // reordering of constants, Sec. IV-B, applied to the table layout).
-        const int RS = ntt_cc_small_radix((int)log2n);
-        const uint64_t nsub = n >> RS;
-        auto fwd_pos = [&](uint64_t k) -> uint64_t {
+        // The two-pass transform at N = 2^16 (ntt_cc_2p.cu) reads a second copy whose
+        // group-major part covers its 4-stage smallest-stride pass.
+        auto fwd_pos = [&](uint64_t k, int RS) -> uint64_t {
             if (k == 0) return 0;
             int s = 63 - __builtin_clzll(k);  // stage of entry k: k in [2^s, 2^(s+1))
             if (s < (int)log2n - RS) return k;
             const int v = s - ((int)log2n - RS);
             const uint64_t G = k - (1ull << s), J = G >> v, g = G & ((1ull << v) - 1);
-            return (1ull << s) + g * nsub + J;
+            return (1ull << s) + g * (n >> RS) + J;
         };
-        auto inv_pos = [&](uint64_t k) -> uint64_t {
+        auto inv_pos = [&](uint64_t k, int RS) -> uint64_t {
             if (k == 0) return 0;
             int hb = 63 - __builtin_clzll(k);  // entry k belongs to stage e = log2n - 1 - hb
             const int e = (int)log2n - 1 - hb;
             if (e >= RS) return k;
             const int w = RS - 1 - e;
             const uint64_t G = k - (1ull << hb), J = G >> w, g = G & ((1ull << w) - 1);
-            return (1ull << hb) + g * nsub + J;
+            return (1ull << hb) + g * (n >> RS) + J;
         };
+        const int RS = ntt_cc_small_radix((int)log2n);
         for (uint64_t k = 0; k < n; ++k) {
             const uint32_t r = bit_reverse((uint32_t)k, (int)log2n);
-            twf[l * n + fwd_pos(k)] = make_uint2((uint32_t)pw[r], shoup(pw[r], q));
-            twi[l * n + inv_pos(k)] = make_uint2((uint32_t)pwi[r], shoup(pwi[r], q));
+            const uint2 wf = make_uint2((uint32_t)pw[r], shoup(pw[r], q));
+            const uint2 wi = make_uint2((uint32_t)pwi[r], shoup(pwi[r], q));
+            twf[l * n + fwd_pos(k, RS)] = wf;
+            twi[l * n + inv_pos(k, RS)] = wi;
+            if (two_pass) {
+                twf2[l * n + fwd_pos(k, 4)] = wf;
+                twi2[l * n + inv_pos(k, 4)] = wi;
+            }
         }
         LimbConst& c = lc[l];
         memset(&c, 0, sizeof c);
@@ -325,6 +334,14 @@ hefx_status hefx_params_create(hefx_ctx* ctx, uint32_t log2n, const uint32_t* pr
     if (e == cudaSuccess) e = cudaMemcpy(p->d_lc, lc.data(), sizeof(LimbConst) * nlimbs, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(p->d_tw_fwd, twf.data(), sizeof(uint2) * twf.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(p->d_tw_inv, twi.data(), sizeof(uint2) * twi.size(), cudaMemcpyHostToDevice);
+    if (two_pass) {
+        if (e == cudaSuccess) e = cudaMalloc(&p->d_tw2_fwd, sizeof(uint2) * twf2.size());
+        if (e == cudaSuccess) e = cudaMalloc(&p->d_tw2_inv, sizeof(uint2) * twi2.size());
+        if (e == cudaSuccess)
+            e = cudaMemcpy(p->d_tw2_fwd, twf2.data(), sizeof(uint2) * twf2.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(p->d_tw2_inv, twi2.data(), sizeof(uint2) * twi2.size(), cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
         hefx_params_destroy(p);
         return cuda_fail(ctx, e, "parameter tables");
@@ -343,6 +360,8 @@ void hefx_params_destroy(hefx_params* p) {
     if (p->d_lc) cudaFree(p->d_lc);
     if (p->d_tw_fwd) cudaFree(p->d_tw_fwd);
     if (p->d_tw_inv) cudaFree(p->d_tw_inv);
+    if (p->d_tw2_fwd) cudaFree(p->d_tw2_fwd);
+    if (p->d_tw2_inv) cudaFree(p->d_tw2_inv);
     if (p->d_err_cc) cudaFree(p->d_err_cc);
     if (p->d_tw_fwd_mont) cudaFree(p->d_tw_fwd_mont);
     if (p->d_tw_inv_mont) cudaFree(p->d_tw_inv_mont);
@@ -998,6 +1017,16 @@ hefx_status hefx_params_set_reduction(hefx_params* p, hefx_reduction ntt_red, he
     }
     p->red_ntt = ntt_red;
     p->red_vec = vec_red;
+    return HEFX_OK;
+}
+
+hefx_status hefx_params_set_cc_schedule(hefx_params* p, hefx_cc_schedule schedule) {
+    if (!p) return HEFX_EINVAL;
+    if (schedule != HEFX_CC_AUTO && schedule != HEFX_CC_CLUSTER && schedule != HEFX_CC_TWO_PASS)
+        return fail(p->ctx, HEFX_EINVAL, "unknown CUDA-core schedule %d", (int)schedule);
+    if (schedule == HEFX_CC_TWO_PASS && !p->d_tw2_fwd)
+        return fail(p->ctx, HEFX_EUNSUPPORTED, "the two-pass schedule is built for N = 2^16 only");
+    p->cc_schedule = (int)schedule;
     return HEFX_OK;
 }
 

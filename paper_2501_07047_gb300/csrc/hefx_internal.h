@@ -93,6 +93,11 @@ struct hefx_params {
     hefx::LimbConst* d_lc = nullptr;  // [nlimbs]
     uint2* d_tw_fwd = nullptr;        // [nlimbs][N]: (psi^brv_N(k), Shoup companion), k >= 1
     uint2* d_tw_inv = nullptr;        // [nlimbs][N]: (psi^-brv_N(k), Shoup companion)
+    // N = 2^16 only: the same tables with the smallest-stride group-major part over 4 stages
+    // (the two-pass CUDA-core transform, ntt_cc_2p.cu); null for other ring degrees
+    uint2* d_tw2_fwd = nullptr;
+    uint2* d_tw2_inv = nullptr;
+    int cc_schedule = 0;              // hefx_cc_schedule of the contiguous CUDA-core transforms
     hefx::TensorTables* tc = nullptr; // built on first tensor-path use
     hefx::Tc2Tables* tc2 = nullptr;   // built on first tensor-path use
     std::mutex tc_mu;
@@ -158,6 +163,7 @@ namespace hefx {
 #ifdef __CUDACC__
 __device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+
 template <typename... Params, typename... Args>
 cudaError_t launch_pdl(void (*kern)(Params...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
     cudaLaunchConfig_t cfg = {};
@@ -179,6 +185,11 @@ cudaError_t launch_pdl(void (*kern)(Params...), dim3 grid, dim3 block, size_t sm
 // limb i and the last limb of the same coefficient-form polynomial and rescales on the way in.
 enum NttMode { MODE_FWD = 0, MODE_INV = 1, MODE_FWD_HAD_INV = 2, MODE_HAD_INV = 3, MODE_RS_FWD = 4 };
 
+// Two-pass CUDA-core transform of contiguous N = 2^16 rows (forward or inverse; in may equal
+// out).  cudaErrorNotSupported where ntt_cc_2p_supported is false.
+bool ntt_cc_2p_supported(const hefx_params* p, NttMode mode);
+cudaError_t launch_ntt_cc_2p(const hefx_params* p, NttMode mode, const uint32_t* in, uint32_t* out, size_t rows,
+                             cudaStream_t stream);
 cudaError_t launch_ntt_cc(const hefx_params* p, NttMode mode, const uint32_t* in, const uint32_t* had, uint32_t* out,
                           size_t rows, cudaStream_t stream);
 // Elementwise products of the HE-Mult request (elementwise.cu).

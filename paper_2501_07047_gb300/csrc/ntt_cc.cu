@@ -19,6 +19,13 @@ cudaError_t encode_input_map(const hefx_params* p, const uint32_t* in, size_t ro
 
 cudaError_t launch_ntt_cc(const hefx_params* p, NttMode mode, const uint32_t* in, const uint32_t* had, uint32_t* out,
                           size_t rows, cudaStream_t stream) {
+    // AUTO takes the two-pass schedule where it measured faster: up to 32 rows (one
+    // polynomial of 24 limbs: 16.7 / 16.4 us against 20.7 / 20.5 us); from about 48 rows the
+    // cluster kernel fills the GPU and the two are within a few percent of each other
+    constexpr size_t kTwoPassAutoRows = 32;
+    const bool two_pass = p->cc_schedule == HEFX_CC_TWO_PASS ||
+                          (p->cc_schedule == HEFX_CC_AUTO && rows <= kTwoPassAutoRows);
+    if (two_pass && ntt_cc_2p_supported(p, mode)) return launch_ntt_cc_2p(p, mode, in, out, rows, stream);
     cc::KArgs a;
     memset(&a.tmap_in, 0, sizeof a.tmap_in);
     memset(&a.tmap_out, 0, sizeof a.tmap_out);

@@ -19,6 +19,7 @@ STATUS_NAMES = ["HEFX_OK", "HEFX_EINVAL", "HEFX_EUNSUPPORTED", "HEFX_ENOMEM", "H
 HEFX_PATH_AUTO, HEFX_PATH_CUDACORE, HEFX_PATH_TENSOR = 0, 1, 2
 PATHS = {"auto": HEFX_PATH_AUTO, "cudacore": HEFX_PATH_CUDACORE, "tensor": HEFX_PATH_TENSOR}
 REDUCTIONS = {"shoup": 0, "montgomery": 1, "barrett": 2, "bat_lazy": 3}
+CC_SCHEDULES = {"auto": 0, "cluster": 1, "two_pass": 2}
 
 # Every symbol include/hefx.h declares, with its ctypes signature.
 _vp, _u32, _sz, _i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_size_t, ctypes.c_int
@@ -33,6 +34,7 @@ SIGNATURES = {
     "hefx_params_set_auto_path": (_i32, [_vp, _i32]),
     "hefx_params_set_reduction": (_i32, [_vp, _i32, _i32]),
     "hefx_params_set_tensor_config": (_i32, [_vp, _u32, _u32, _u32]),
+    "hefx_params_set_cc_schedule": (_i32, [_vp, _i32]),
     "hefx_ntt_fwd": (_i32, [_vp, _vp, _vp, _sz, _i32, _vp]),
     "hefx_ntt_inv": (_i32, [_vp, _vp, _vp, _sz, _i32, _vp]),
     "hefx_poly_mul": (_i32, [_vp, _vp, _vp, _vp, _vp, _sz, _i32, _vp]),
@@ -168,6 +170,12 @@ def hefx_params_set_auto_path(params: int, path) -> int:
 def hefx_params_set_reduction(ctx, params: int, ntt_red="shoup", vec_red="montgomery") -> None:
     """Reduction of the CUDA-core NTT twiddle products and of VecModMul (the paper's ablation)."""
     _check(ctx, load().hefx_params_set_reduction(params, REDUCTIONS[ntt_red], REDUCTIONS[vec_red]))
+
+
+def hefx_params_set_cc_schedule(ctx, params: int, schedule="auto") -> None:
+    """Schedule of the contiguous CUDA-core transforms: "cluster" (one launch, 8-CTA clusters),
+    "two_pass" (N = 2^16: column pass + block pass through L2) or "auto"."""
+    _check(ctx, load().hefx_params_set_cc_schedule(params, CC_SCHEDULES[schedule]))
 
 
 def hefx_params_set_tensor_config(ctx, params: int, log2r: int = 0, tile_outputs: int = 64, log2r2: int = 0) -> None:

@@ -106,6 +106,8 @@ def test_tuner_candidates_and_cached_choice(tmp_path, monkeypatch):
     assert tensor_plan.tuned_splits(14) == [(7, 0), (6, 4)]            # 128 x 128 and 64 x 16 x 16
     assert tensor_plan.splits(13) == [] and tensor_plan.splits(12) == []
     assert autotune.candidates(13) == [("cudacore", 0, 0, 0)]
+    assert autotune.candidates(16)[:2] == [("cudacore", 1, 0, 0), ("cudacore", 2, 0, 0)]  # both schedules
+    assert autotune.candidates(15)[0] == ("cudacore", 0, 0, 0) and autotune.candidates(15)[1][0] == "tensor"
     for logn in (14, 15, 16):
         for log2r, log2r2 in tensor_plan.splits(logn):  # every split multiplies out to N within bounds
             f = tensor_plan.split(logn, log2r, log2r2)
@@ -114,7 +116,7 @@ def test_tuner_candidates_and_cached_choice(tmp_path, monkeypatch):
                 assert 64 <= f[0] <= 256 and all(16 <= x <= 256 for x in f[1:])
             else:
                 assert all(x in (128, 256) for x in f)
-        for cand in autotune.candidates(logn)[1:]:
+        for cand in autotune.candidates(logn)[2 if logn == 16 else 1:]:
             assert cand[0] == "tensor" and cand[3] in autotune.TILES
             assert autotune.parse(autotune.key_of(cand)) == cand
     # digit MACs: the three-factor split costs (R1 + R2 + R3) / (R + C) of the two-factor one
@@ -123,7 +125,7 @@ def test_tuner_candidates_and_cached_choice(tmp_path, monkeypatch):
     monkeypatch.setattr(torch.cuda, "get_device_name", lambda *a: "FAKE-GPU")
     timed, applied = [], []
     monkeypatch.setattr(autotune, "time_candidates",
-                        lambda *a, **k: timed.append(1) or {"cudacore/0/0/0": 2.0, "tensor/6/5/32": 1.5,
+                        lambda *a, **k: timed.append(1) or {"cudacore/1/0/0": 2.0, "cudacore/2/0/0": 2.1, "tensor/6/5/32": 1.5,
                                                             "tensor/8/0/64": 1.7})
     monkeypatch.setattr(autotune, "apply", lambda ctx, p, cand: applied.append(cand))
     assert autotune.tune(None, None, 16, [268042241, 265420801]) == "tensor"

@@ -145,18 +145,19 @@ def oracle_rows(data, primes, inverse=False):
     return np.concatenate(parts)
 
 
-@pytest.mark.parametrize("path", PATHS)
-def test_config2_full_size(ctx, path):
-    """N = 2^16, L = 24, batch 8 (192 limb-NTTs, the bench launch): every output of the forward
-    transform and of the inverse of an arbitrary input against the oracle, 256 sampled forward
-    outputs against the O(N) definition (pinning the oracle itself at full size), and
-    INTT(NTT(x)) = x over the whole batch."""
+@pytest.mark.parametrize("path,schedule", [("cudacore", "cluster"), ("cudacore", "two_pass"), ("tensor", "auto")])
+def test_config2_full_size(ctx, path, schedule):
+    """N = 2^16, L = 24, batch 8 (192 limb-NTTs, the bench launch), on both CUDA-core schedules
+    and the tensor path: every output of the forward transform and of the inverse of an
+    arbitrary input against the oracle, 256 sampled forward outputs against the O(N) definition
+    (pinning the oracle itself at full size), and INTT(NTT(x)) = x over the whole batch."""
     primes = inputs.source_primes(24)
     n = 1 << 16
     p = make_params(ctx, 16, primes)
     try:
         if not supported(ctx, p, path, 8, 24, n):
             pytest.skip("path not built")
+        hefx.hefx_params_set_cc_schedule(ctx, p, schedule)
         data = inputs.residue_tensor(inputs.derive_seed(2, 0), 8, primes, n)
         d = to_dev(data)
         hefx.hefx_ntt_fwd(ctx, p, d, 8, path)
@@ -178,6 +179,44 @@ def test_config2_full_size(ctx, path):
         got = to_host(d).reshape(rnd.shape)
         bad = np.argwhere(got != oracle_rows(rnd, primes, inverse=True))
         assert bad.size == 0, f"{len(bad)} inverse outputs differ, first at {bad[0]}"
+    finally:
+        hefx.hefx_params_destroy(p)
+
+
+@pytest.mark.parametrize("bits,L,batch", [(28, 1, 1), (28, 5, 3), (30, 3, 1), (30, 2, 20)])
+def test_cc_schedules_agree_with_oracle(ctx, bits, L, batch):
+    """The two CUDA-core schedules at N = 2^16 (cluster, two-pass) and AUTO (two-pass up to 32
+    rows, cluster above): every output of the forward and inverse transforms against the
+    oracle, for 28-bit moduli (lazy ranges) and 30-bit ones (Harvey ranges), from one row to
+    past the AUTO switch."""
+    primes = inputs.source_primes(L) if bits == 28 else inputs.special_primes(L)
+    n = 1 << 16
+    p = make_params(ctx, 16, primes)
+    try:
+        data = inputs.residue_tensor(inputs.derive_seed(15, bits, L, batch), batch, primes, n)
+        want_f = oracle_rows(data, primes)
+        want_i = oracle_rows(data, primes, inverse=True)
+        for schedule in ("cluster", "two_pass", "auto"):
+            hefx.hefx_params_set_cc_schedule(ctx, p, schedule)
+            got = run_fwd(ctx, p, data, "cudacore")
+            bad = np.argwhere(got != want_f)
+            assert bad.size == 0, f"{schedule}: {len(bad)} forward outputs differ, first at {bad[0]}"
+            got = run_inv(ctx, p, data, "cudacore")
+            bad = np.argwhere(got != want_i)
+            assert bad.size == 0, f"{schedule}: {len(bad)} inverse outputs differ, first at {bad[0]}"
+    finally:
+        hefx.hefx_params_destroy(p)
+
+
+def test_cc_schedule_validation(ctx):
+    p = make_params(ctx, 15, inputs.source_primes(2))
+    try:
+        with pytest.raises(hefx.HefxError) as e:
+            hefx.hefx_params_set_cc_schedule(ctx, p, "two_pass")  # built for N = 2^16 only
+        assert e.value.status == hefx.HEFX_EUNSUPPORTED
+        hefx.hefx_params_set_cc_schedule(ctx, p, "cluster")
+        hefx.hefx_params_set_cc_schedule(ctx, p, "auto")
+        assert hefx.raw_status("hefx_params_set_cc_schedule", p, 7) == hefx.HEFX_EINVAL
     finally:
         hefx.hefx_params_destroy(p)
 
