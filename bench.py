@@ -2,8 +2,9 @@
 
 Workload (one "step"): forward + inverse negacyclic NTT of a batch of 8 polynomials with
 L = 24 RNS limbs of 28-bit primes, N = 2^16 (384 limb-NTTs), uniform synthetic residues.
-Both hefx paths are timed (CUDA-core radix-2 and the tensor-core matrix NTT, when built);
-`value` is the faster bit-exact path, `paths` lists both.  Inputs (48 MiB) are smaller than
+Both hefx paths are timed (CUDA-core radix-2 under its two schedules, and the tensor-core
+matrix NTT for each split and tile, when built); `value` is the fastest bit-exact
+configuration, `paths` lists them all.  Inputs (48 MiB) are smaller than
 L2, so a 256 MiB buffer is written between timed steps to flush it.
 
 Contract: one JSON line on rank 0.  `python bench.py --impl reference` times the CPU oracle
@@ -275,15 +276,17 @@ def run_gpu(args):
         st = hefx.raw_status("hefx_ntt_fwd", ctx, params, data.data_ptr(), 0, hefx.PATHS[path], stream.cuda_stream)
         return st == hefx.HEFX_OK
 
-    # timed configurations: the CUDA-core path and the tensor path with each GEMM tile width
-    # (the tensor split at N = 2^16 has one valid choice, 256 x 256)
-    configs = [("cudacore", "cudacore", 0, (0, 0))]
+    # timed configurations: the CUDA-core path under both of its schedules (one launch of 8-CTA
+    # clusters; two launches, column pass then block pass) and the tensor path with each split
+    # and GEMM tile width
+    configs = [("cudacore", "cudacore", 0, (0, 0), "cluster"), ("cudacore_2p", "cudacore", 0, (0, 0), "two_pass")]
     if available("tensor"):
         # two-factor 256 x 256 and the three-factor 64 x 32 x 32 split, each with both tiles
-        configs += [("tensor", "tensor", 64, (0, 0)), ("tensor_t32", "tensor", 32, (0, 0)),
-                    ("tensor_3f", "tensor", 64, (6, 5)), ("tensor_3f_t32", "tensor", 32, (6, 5))]
+        configs += [("tensor", "tensor", 64, (0, 0), "auto"), ("tensor_t32", "tensor", 32, (0, 0), "auto"),
+                    ("tensor_3f", "tensor", 64, (6, 5), "auto"), ("tensor_3f_t32", "tensor", 32, (6, 5), "auto")]
     results = {}
-    for name, path, tile, split in configs:
+    for name, path, tile, split, sched in configs:
+        hefx.hefx_params_set_cc_schedule(ctx, params, sched)
         if tile:
             hefx.hefx_params_set_tensor_config(ctx, params, split[0], tile, split[1])
         # correctness gate: INTT(NTT(x)) == x on the bench data before timing
@@ -318,12 +321,12 @@ def run_gpu(args):
         total_ms = step_ms * args.steps
         total_ms = max_over_ranks(total_ms, dist, "cuda")
         results[name] = {
-            "path": path, "tile": tile, "split": split,
+            "path": path, "tile": tile, "split": split, "schedule": sched,
             "ms_per_step": total_ms / args.steps,
             "value": job_value(world, UNITS_PER_STEP, args.steps, total_ms),
             "fwd_ms": statistics.mean(fwd_ms), "inv_ms": statistics.mean(inv_ms),
             "wall_s": t_wall, "clocks": clk.summary(),
-            "launches_per_step": 2 if path == "cudacore" else (6 if not split[1] else 8),
+            "launches_per_step": (2 if sched == "cluster" else 4) if path == "cudacore" else (6 if not split[1] else 8),
         }
 
     if available("tensor"):
@@ -331,6 +334,7 @@ def run_gpu(args):
     best_name = max(results, key=lambda p: results[p]["value"])
     r = results[best_name]
     best = r["path"]
+    hefx.hefx_params_set_cc_schedule(ctx, params, r["schedule"])
     if best == "tensor":
         hefx.hefx_params_set_tensor_config(ctx, params, r["split"][0], r["tile"], r["split"][1])
 
@@ -366,9 +370,11 @@ def run_gpu(args):
         dom = max(rr["fwd_ms"], rr["inv_ms"])
         achieved = units_per_launch * BYTES_PER_UNIT / (dom / 1e3) / 1e9
         which = "fwd" if rr["fwd_ms"] >= rr["inv_ms"] else "inv"
+        cluster = rr["schedule"] == "cluster"
         return {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                "frac": round(achieved / hbm, 4), "traffic": profile_traffic("ntt_cc", which),
-                "kernel": "ntt_cc_kernel<16, " + which.upper() + ">",
+                "frac": round(achieved / hbm, 4), "traffic": profile_traffic("ntt_cc", which) if cluster else None,
+                "kernel": ("ntt_cc_kernel<16, " + which.upper() + ">") if cluster else
+                          ("two-pass " + which + " transform (column and block kernels, timed together)"),
                 "algorithmic_bytes_per_launch": units_per_launch * BYTES_PER_UNIT,
                 "peak_source": f"{src} hbm_gbs"}
 
