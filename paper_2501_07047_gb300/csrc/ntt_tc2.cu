@@ -51,7 +51,13 @@ constexpr int STAGES = 4;
 constexpr uint32_t A_BYTES = BM * BK * 2;  // 16 KiB
 constexpr uint32_t B_BYTES = BN * BK * 2;  // 32 KiB
 constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int THREADS = 320;  // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue (two per TMEM lane quadrant)
+// warp 0 TMA, warp 1 MMA, warps 2-17 epilogue: four per TMEM lane quadrant, each on a quarter
+// of the accumulator's columns (measured against two per quadrant: config 2 with 64 x 32 x 32,
+// 147 / 147 us instead of 176 / 169 us per transform; the epilogue's dependent chain of TMEM
+// read, conversions, REDC, twiddle load and digit stores needs the extra warps to hide latency)
+constexpr int EPI_WARPS = 16;
+constexpr int EPI_PARTS = EPI_WARPS / 4;
+constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr size_t SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + 256;
 
@@ -132,7 +138,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         for (int b = 0; b < 2; ++b) {
             tc::mbar_init(&acc_full[b], 1);
-            tc::mbar_init(&acc_empty[b], 256);
+            tc::mbar_init(&acc_empty[b], 32 * EPI_WARPS);
         }
         tc::mbar_init(mma_done, 1);
         tc::fence_mbar_init();
@@ -212,8 +218,10 @@ __global__ void __launch_bounds__(THREADS, 1)
             tc::mma_commit(mma_done);
             tc::mbar_wait(mma_done, 0, a.err, tc::ERR_TIMEOUT_ACC);
         }
-    } else {  // ---- epilogue: warps 2..9; warp % 4 is the TMEM lane quadrant, (warp - 2) / 4 the column half
-        const uint32_t quad = warp & 3, half = (warp - 2) >> 2;
+    } else {  // ---- epilogue: warp % 4 is the TMEM lane quadrant, (warp - 2) / 4 the column slice
+        const uint32_t quad = warp & 3, part = (warp - 2) >> 2;
+        constexpr int SLICE = BN / EPI_PARTS;  // accumulator columns per epilogue warp
+        static_assert(SLICE % 16 == 0, "whole 16-column TMEM reads per warp");
         uint32_t t = 0;
         for (uint32_t item = cid; item < items; item += nctas) {
             uint32_t limb, pl, drow0;
@@ -241,7 +249,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 }
                 tc::tc_fence_after();
 #pragma unroll 1
-                for (int cb = half * (BN / 2); cb < (int)(half + 1) * (BN / 2); cb += 16) {
+                for (int cb = (int)part * SLICE; cb < (int)(part + 1) * SLICE; cb += 16) {
                     uint32_t r[16];
                     tc::tmem_ld16(tmem + ((quad * 32) << 16) + acc * BN + cb, r);
                     tc::tmem_ld_wait();
