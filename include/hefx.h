@@ -152,9 +152,11 @@ hefx_status hefx_params_set_reduction(hefx_params* params, hefx_reduction ntt_re
  *    factorisation of the matrix NTT (Sec. IV-B) with the twiddle step folded into the
  *    butterflies: 8 stages within columns j mod 256, then 8 within 256-element blocks
  *    (reversed for the inverse); the intermediate goes through the output buffer.
- *  - HEFX_CC_AUTO (default): HEFX_CC_TWO_PASS for at most 32 rows at N = 2^16 (a launch of
- *    so few rows leaves most of the GPU idle under the cluster schedule; measured 20 % faster
- *    for one polynomial of 24 limbs), else HEFX_CC_CLUSTER.
+ *  - HEFX_CC_AUTO (default): at N = 2^16, HEFX_CC_TWO_PASS for at most 32 rows (so few
+ *    clusters leave most of the GPU idle; measured 20 % faster for one polynomial of 24
+ *    limbs) and for one to one and a half waves of co-resident clusters (the cluster
+ *    kernel's second wave mostly empty; 4-14 % faster at 96 and 120 rows), else
+ *    HEFX_CC_CLUSTER.
  * Hadamard-fused forms (hefx_poly_mul), Rescale, row lists and batch plans use the cluster
  * schedule.  Errors: EINVAL (unknown schedule), EUNSUPPORTED (HEFX_CC_TWO_PASS at
  * N != 2^16).  Not thread-safe with concurrent calls that use the same params.

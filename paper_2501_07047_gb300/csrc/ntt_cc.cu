@@ -8,6 +8,18 @@ namespace hefx {
 
 cudaError_t launch_dispatch(const hefx_params* p, NttMode mode, const cc::KArgs& a, size_t rows, cudaStream_t stream);
 
+namespace {
+
+// Co-resident clusters of the N = 2^16 forward / inverse kernel, queried once per context.
+int clusters16(hefx_ctx* c, NttMode mode, bool lazy) {
+    std::lock_guard<std::mutex> g(c->mu);
+    int& v = c->cc16_clusters[mode == MODE_INV ? 1 : 0][lazy ? 1 : 0];
+    if (v < 0) v = cc::max_clusters_16(mode, lazy);
+    return v;
+}
+
+}  // namespace
+
 // Tensor map of a contiguous [rows][N] input for the inverse transforms' TMA loads.
 cudaError_t encode_input_map(const hefx_params* p, const uint32_t* in, size_t rows, CUtensorMap* map) {
     const uint64_t lines = (uint64_t)rows * p->n / 32;  // 128-byte lines of 32 words
@@ -19,12 +31,22 @@ cudaError_t encode_input_map(const hefx_params* p, const uint32_t* in, size_t ro
 
 cudaError_t launch_ntt_cc(const hefx_params* p, NttMode mode, const uint32_t* in, const uint32_t* had, uint32_t* out,
                           size_t rows, cudaStream_t stream) {
-    // AUTO takes the two-pass schedule where it measured faster: up to 32 rows (one
-    // polynomial of 24 limbs: 16.7 / 16.4 us against 20.7 / 20.5 us); from about 48 rows the
-    // cluster kernel fills the GPU and the two are within a few percent of each other
-    constexpr size_t kTwoPassAutoRows = 32;
-    const bool two_pass = p->cc_schedule == HEFX_CC_TWO_PASS ||
-                          (p->cc_schedule == HEFX_CC_AUTO && rows <= kTwoPassAutoRows);
+    // AUTO takes the two-pass schedule where it measured faster than the clusters: up to 32
+    // rows (one polynomial of 24 limbs: 16.7 / 16.4 us against 20.7 / 20.5 us), and from one
+    // to one and a half waves of co-resident clusters, where the cluster kernel's second wave
+    // is mostly empty (96 rows: 34.1 / 31.7 us against 35.6 / 34.8 us; 120 rows: 43.3 / 39.9
+    // against 45.6 / 45.1 us); elsewhere the two are within a few percent and the single
+    // launch stays
+    bool two_pass = p->cc_schedule == HEFX_CC_TWO_PASS;
+    if (p->cc_schedule == HEFX_CC_AUTO && ntt_cc_2p_supported(p, mode)) {
+        constexpr size_t kTwoPassAutoRows = 32;
+        if (rows <= kTwoPassAutoRows) {
+            two_pass = true;
+        } else {
+            const size_t slots = (size_t)clusters16(p->ctx, mode, p->max_prime < (1u << 28));
+            two_pass = slots > 0 && rows > slots && 2 * rows <= 3 * slots;
+        }
+    }
     if (two_pass && ntt_cc_2p_supported(p, mode)) return launch_ntt_cc_2p(p, mode, in, out, rows, stream);
     cc::KArgs a;
     memset(&a.tmap_in, 0, sizeof a.tmap_in);

@@ -1055,6 +1055,33 @@ cudaError_t launch_one(const KArgs& a, size_t rows, cudaStream_t stream) {
     return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
+// Clusters of this kernel configuration that fit on the device at once (the occupancy the
+// runtime reports), 0 for unsplit rows or where it cannot be queried.
+template <int LOGN, int MODE, int F>
+int max_active_clusters() {
+    using C = Cfg<LOGN, F>;
+    if constexpr (!C::split) {
+        return 0;
+    } else {
+        KArgs dummy = {};
+        if (launch_one<LOGN, MODE, F>(dummy, 0, nullptr) != cudaSuccess) return 0;  // sets the smem attribute
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        cfg.gridDim = dim3((unsigned)(C::P * 1024));
+        cfg.blockDim = dim3(C::threads);
+        cfg.dynamicSmemBytes = C::smem_bytes + (uses_tma<LOGN, MODE, F>() ? 1024 : 0);
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = C::P;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, ntt_cc_kernel<LOGN, MODE, F>, &cfg) != cudaSuccess) return 0;
+        return n;
+    }
+}
+
 template <int LOGN, int F>
 cudaError_t launch_mode_d(NttMode mode, const KArgs& a, size_t rows, cudaStream_t s) {
     switch (mode) {
@@ -1074,6 +1101,10 @@ cudaError_t launch_mode(NttMode mode, const KArgs& a, size_t rows, cudaStream_t 
     if (a.desc) return lazy ? launch_mode_d<LOGN, 3>(mode, a, rows, s) : launch_mode_d<LOGN, 1>(mode, a, rows, s);
     return lazy ? launch_mode_d<LOGN, 2>(mode, a, rows, s) : launch_mode_d<LOGN, 0>(mode, a, rows, s);
 }
+
+// Co-resident clusters of the contiguous-layout forward or inverse kernel at N = 2^16
+// (ntt_cc_range_d.cu), 0 where it cannot be queried.
+int max_clusters_16(NttMode mode, bool lazy);
 
 // One LOGN range of the dispatcher, compiled in its own translation unit (build time).
 cudaError_t launch_range_a(int logn, NttMode mode, const KArgs& a, size_t rows, cudaStream_t s, bool lazy);

@@ -183,12 +183,13 @@ def test_config2_full_size(ctx, path, schedule):
         hefx.hefx_params_destroy(p)
 
 
-@pytest.mark.parametrize("bits,L,batch", [(28, 1, 1), (28, 5, 3), (30, 3, 1), (30, 2, 20)])
+@pytest.mark.parametrize("bits,L,batch", [(28, 1, 1), (28, 5, 3), (30, 3, 1), (30, 2, 20), (28, 24, 5)])
 def test_cc_schedules_agree_with_oracle(ctx, bits, L, batch):
     """The two CUDA-core schedules at N = 2^16 (cluster, two-pass) and AUTO (two-pass up to 32
-    rows, cluster above): every output of the forward and inverse transforms against the
-    oracle, for 28-bit moduli (lazy ranges) and 30-bit ones (Harvey ranges), from one row to
-    past the AUTO switch."""
+    rows and between one and one and a half waves of clusters, cluster elsewhere): every output
+    of the forward and inverse transforms against the oracle, for 28-bit moduli (lazy ranges)
+    and 30-bit ones (Harvey ranges), from one row to 120 rows (inside the second AUTO band on
+    GB300's 89 co-resident clusters)."""
     primes = inputs.source_primes(L) if bits == 28 else inputs.special_primes(L)
     n = 1 << 16
     p = make_params(ctx, 16, primes)
