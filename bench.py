@@ -279,7 +279,7 @@ def run_gpu(args):
     # timed configurations: the CUDA-core path under both of its schedules (one launch of 8-CTA
     # clusters; two launches, column pass then block pass) and the tensor path with each split
     # and GEMM tile width
-    configs = [("cudacore", "cudacore", 0, (0, 0), "cluster"), ("cudacore_2p", "cudacore", 0, (0, 0), "two_pass")]
+    configs = [("cudacore", "cudacore", 0, (0, 0), "auto"), ("cudacore_2p", "cudacore", 0, (0, 0), "two_pass")]
     if available("tensor"):
         # two-factor 256 x 256 and the three-factor 64 x 32 x 32 split, each with both tiles
         configs += [("tensor", "tensor", 64, (0, 0), "auto"), ("tensor_t32", "tensor", 32, (0, 0), "auto"),
@@ -326,12 +326,14 @@ def run_gpu(args):
             "value": job_value(world, UNITS_PER_STEP, args.steps, total_ms),
             "fwd_ms": statistics.mean(fwd_ms), "inv_ms": statistics.mean(inv_ms),
             "wall_s": t_wall, "clocks": clk.summary(),
-            "launches_per_step": (2 if sched == "cluster" else 4) if path == "cudacore" else (6 if not split[1] else 8),
+            "launches_per_step": (4 if sched == "two_pass" else 2) if path == "cudacore" else (6 if not split[1] else 8),
         }
 
     if available("tensor"):
         hefx.hefx_params_set_tensor_config(ctx, params, 0, 64, 0)
-    best_name = max(results, key=lambda p: results[p]["value"])
+    # the headline is the library's own choice for this shape (AUTO: the cluster schedule at 192
+    # rows) or a tensor configuration; the explicit two-pass schedule is listed for comparison
+    best_name = max((k for k in results if k != "cudacore_2p"), key=lambda p: results[p]["value"])
     r = results[best_name]
     best = r["path"]
     hefx.hefx_params_set_cc_schedule(ctx, params, r["schedule"])
@@ -370,7 +372,7 @@ def run_gpu(args):
         dom = max(rr["fwd_ms"], rr["inv_ms"])
         achieved = units_per_launch * BYTES_PER_UNIT / (dom / 1e3) / 1e9
         which = "fwd" if rr["fwd_ms"] >= rr["inv_ms"] else "inv"
-        cluster = rr["schedule"] == "cluster"
+        cluster = rr["schedule"] != "two_pass"  # AUTO runs the cluster kernel at 192 rows
         return {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(achieved / hbm, 4), "traffic": profile_traffic("ntt_cc", which) if cluster else None,
                 "kernel": ("ntt_cc_kernel<16, " + which.upper() + ">") if cluster else

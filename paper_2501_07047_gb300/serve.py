@@ -28,6 +28,7 @@ from __future__ import annotations
 
 import collections
 import dataclasses
+import gc
 import time
 
 import numpy as np
@@ -270,6 +271,18 @@ def serve(requests, executor, budget_bytes: int = 40 << 30, max_slots: int | Non
     the streams.  A stream completes its requests in order, so only the oldest request of
     each stream is polled."""
     requests = sorted(requests, key=lambda r: r.arrival)
+    # the loop allocates many small objects; a cyclic-garbage pass over the whole process heap
+    # in the middle of it stalls admission for tens of ms, so the collector waits until the end
+    gc_was_enabled = gc.isenabled()
+    gc.disable()
+    try:
+        return _serve(requests, executor, budget_bytes, max_slots, keep_outputs)
+    finally:
+        if gc_was_enabled:
+            gc.enable()
+
+
+def _serve(requests, executor, budget_bytes, max_slots, keep_outputs):
     nstreams = len(getattr(executor, "streams", [])) or 8
     adm = Admission(budget_bytes, max_slots if max_slots is not None else 4 * nstreams)
     fifo = collections.defaultdict(collections.deque)  # stream key -> in-flight (req, handle)
