@@ -650,8 +650,33 @@ def bench_serving(ctx, args):
     """Poisson arrival-rate sweep of ciphertext-multiply requests, 40 GB admission budget:
     continuous batching (requests admitted together run as groups of one ring degree in shared
     launches) and, for comparison at the top rates, one native call per request."""
-    from paper_2501_07047_gb300.serve import GpuExecutor, poisson_requests, serve
+    import torch
+    from paper_2501_07047_gb300.serve import N_SPECIAL, GpuExecutor, poisson_requests, serve
     res = {"workload": "HE-Mult front half, N in {2^13..2^16}, L in [8, 36], 8 special primes", "budget_GB": 40}
+    # the ceiling the host link sets: every request uploads 4 L N words and reads back
+    # (4 L + 2 K) N words; the link rate is measured here with both directions at once
+    mix = poisson_requests(inputs_seed(5, 0), 2000, 1.0)
+    bytes_req = statistics.mean(4 * ((4 * r.L) + (4 * r.L + 2 * N_SPECIAL)) * (1 << r.logn) for r in mix)
+    nb = 256 << 20
+    h_up = torch.empty(nb // 4, dtype=torch.int32).pin_memory()
+    h_dn = torch.empty(nb // 4, dtype=torch.int32).pin_memory()
+    d_up = torch.empty(nb // 4, dtype=torch.int32, device="cuda")
+    d_dn = torch.empty(nb // 4, dtype=torch.int32, device="cuda")
+    s_up, s_dn = torch.cuda.Stream(), torch.cuda.Stream()
+    ms = []
+    for _ in range(4):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(s_up):
+            d_up.copy_(h_up, non_blocking=True)
+        with torch.cuda.stream(s_dn):
+            h_dn.copy_(d_dn, non_blocking=True)
+        torch.cuda.synchronize()
+        ms.append(time.perf_counter() - t0)
+    link = 2 * nb / min(ms[1:]) / 1e9
+    del h_up, h_dn, d_up, d_dn
+    res["host_link"] = {"GB_s_both_ways": round(link, 1), "bytes_per_request_mean": int(bytes_req),
+                        "bound_rps": round(link * 1e9 / bytes_req, 1)}
     for mode, rates in (("grouped", (100, 400, 1600, 6400, 25600, 51200)), ("per_request", (6400, 25600))):
         ex = GpuExecutor(ctx, nstreams=8, grouped=(mode == "grouped"))
         try:
