@@ -437,6 +437,20 @@ hefx_status hefx_mult_front_batch_host(hefx_ctx* ctx, hefx_mult_batch* batch, co
                                        uint32_t* const* h_out, uint32_t* const* d_buf, void* stream);
 
 /*
+ * The same batched front half on device-resident operands (the serving loop's resident mode:
+ * ciphertexts and keys stay in HBM between operations, nothing crosses the host link): request
+ * r reads d_a0[r] .. d_b1[r] ([L_r][N] each, device) and writes d_out[r] ([4 L_r + 2K][N], the
+ * layout of hefx_mult_front's d_out) using d_work[r] ([2 L_r + K][N]) as workspace.  A
+ * request's output and workspace must not overlap any of its buffers; distinct requests must
+ * not share outputs or workspaces.  Results equal hefx_mult_front's, bit for bit.  All on
+ * `stream`.  Errors as for hefx_mult_front_batch_host.
+ */
+hefx_status hefx_mult_front_batch(hefx_ctx* ctx, hefx_mult_batch* batch, const hefx_mult_plan* const* plans,
+                                  uint32_t count, const uint32_t* const* d_a0, const uint32_t* const* d_a1,
+                                  const uint32_t* const* d_b0, const uint32_t* const* d_b1, uint32_t* const* d_out,
+                                  uint32_t* const* d_work, void* stream);
+
+/*
  * Batched polynomial products of uneven shape (the batching pattern of the build; the
  * paper's batching study is Sec. V-B3, "TPUs favor large batch").  Each job multiplies two
  * polynomials of ring degree N = 2^params->log2n over the first `nlimbs` primes of

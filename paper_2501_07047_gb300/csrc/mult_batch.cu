@@ -5,6 +5,8 @@
 // row-list transforms, the conversion to P as a list launch with one block row per request.
 // Per request only the input upload and the output read-back remain.
 #include <algorithm>
+#include <cstdarg>
+#include <cstdio>
 #include <cstring>
 #include <vector>
 
@@ -126,8 +128,16 @@ RowDesc rowdesc(const hefx_params* p, uint32_t l, const uint32_t* in, uint32_t* 
     return r;
 }
 
-hefx_status fail_mb(hefx_ctx* ctx, hefx_status st, const char* msg) {
-    if (ctx) ctx->last_error = msg;
+hefx_status fail_mb(hefx_ctx* ctx, hefx_status st, const char* fmt, ...) {
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        std::lock_guard<std::mutex> g(ctx->mu);
+        ctx->last_error = buf;
+    }
     return st;
 }
 
@@ -176,44 +186,71 @@ void hefx_mult_batch_destroy(hefx_mult_batch* mb) {
     delete mb;
 }
 
-hefx_status hefx_mult_front_batch_host(hefx_ctx* ctx, hefx_mult_batch* mb, const hefx_mult_plan* const* plans,
-                                       uint32_t count, const uint32_t* const* h_a0, const uint32_t* const* h_a1,
-                                       const uint32_t* const* h_b0, const uint32_t* const* h_b1,
-                                       uint32_t* const* h_out, uint32_t* const* d_buf, void* stream) {
+}  // extern "C"
+
+namespace {
+
+bool overlap_bytes(const void* a, size_t an, const void* b, size_t bn) {
+    const char *x = (const char*)a, *y = (const char*)b;
+    return x < y + bn && y < x + an;
+}
+
+// Body of both batched calls: validation, the descriptors and the five shared launches.
+// inputs[i][r] is request r's input i (a0, a1, b0, b1; [L_r][N] on the device), d_out[r] its
+// [4 L_r + 2K][N] outputs, d_work[r] its [2 L_r + K][N] workspace.  With host copies, each
+// request's inputs are first uploaded from hin[i][r] into inputs[i][r], and its outputs are
+// read back into h_out[r] after the launches.
+hefx_status front_batch(hefx_ctx* ctx, hefx_mult_batch* mb, const hefx_mult_plan* const* plans, uint32_t count,
+                        const uint32_t* const* const inputs[4], uint32_t* const* d_out, uint32_t* const* d_work,
+                        const uint32_t* const* const hin[4], uint32_t* const* h_out, cudaStream_t s,
+                        const char* name) {
     if (!ctx) return HEFX_EINVAL;
     if (!mb || mb->ctx != ctx) return fail_mb(ctx, HEFX_EINVAL, "batch object is null or of another context");
     if (count == 0) return HEFX_OK;
-    if (count > mb->max_requests || !plans || !h_a0 || !h_a1 || !h_b0 || !h_b1 || !h_out || !d_buf)
-        return fail_mb(ctx, HEFX_EINVAL, "hefx_mult_front_batch_host: count above the batch object's or null arrays");
+    const bool host = hin != nullptr;
+    if (count > mb->max_requests || !plans || !inputs[0] || !inputs[1] || !inputs[2] || !inputs[3] || !d_out ||
+        !d_work || (host && (!hin[0] || !hin[1] || !hin[2] || !hin[3] || !h_out)))
+        return fail_mb(ctx, HEFX_EINVAL, "%s: count above the batch object's or null arrays", name);
     MultPlanView v0;
     if (!mult_plan_view(plans[0], &v0) || v0.ctx != ctx)
-        return fail_mb(ctx, HEFX_EINVAL, "hefx_mult_front_batch_host: plan 0 is null or of another context");
+        return fail_mb(ctx, HEFX_EINVAL, "%s: plan 0 is null or of another context", name);
+    const uint32_t K = v0.pp->nlimbs, logn = v0.pp->log2n;
+    const size_t n = (size_t)1 << logn;
     size_t r1 = 0;
     for (uint32_t r = 0; r < count; ++r) {
         MultPlanView v;
         if (!mult_plan_view(plans[r], &v) || v.ctx != ctx)
-            return fail_mb(ctx, HEFX_EINVAL, "hefx_mult_front_batch_host: a plan is null or of another context");
+            return fail_mb(ctx, HEFX_EINVAL, "%s: a plan is null or of another context", name);
         if (v.pq->log2n != v0.pq->log2n || v.pp != v0.pp)
-            return fail_mb(ctx, HEFX_EINVAL,
-                           "hefx_mult_front_batch_host: every request of a batch shares the ring degree and P");
+            return fail_mb(ctx, HEFX_EINVAL, "%s: every request of a batch shares the ring degree and P", name);
         if (v.pq->nlimbs > mb->max_rows)
-            return fail_mb(ctx, HEFX_EINVAL, "hefx_mult_front_batch_host: more limbs than the batch object holds");
-        if (!h_a0[r] || !h_a1[r] || !h_b0[r] || !h_b1[r] || !h_out[r] || !d_buf[r] || ((uintptr_t)d_buf[r] & 15))
-            return fail_mb(ctx, HEFX_EINVAL, "hefx_mult_front_batch_host: null host or null / misaligned device buffer");
-        r1 += v.pq->nlimbs;
+            return fail_mb(ctx, HEFX_EINVAL, "%s: more limbs than the batch object holds", name);
+        const size_t L = v.pq->nlimbs;
+        const void* bufs[6] = {inputs[0][r], inputs[1][r], inputs[2][r], inputs[3][r], d_out[r], d_work[r]};
+        const size_t sizes[6] = {L * n * 4, L * n * 4, L * n * 4, L * n * 4, (4 * L + 2 * K) * n * 4,
+                                 (2 * L + K) * n * 4};
+        for (int i = 0; i < 6; ++i)
+            if (!bufs[i] || ((uintptr_t)bufs[i] & 15))
+                return fail_mb(ctx, HEFX_EINVAL, "%s: null or misaligned device buffer", name);
+        // the outputs and the workspace are written: neither may overlap any buffer of the request
+        for (int w = 4; w < 6; ++w)
+            for (int i = 0; i < 6; ++i)
+                if (i != w && overlap_bytes(bufs[w], sizes[w], bufs[i], sizes[i]))
+                    return fail_mb(ctx, HEFX_EINVAL, "%s: a request's output or workspace overlaps its other buffers",
+                                   name);
+        if (host && (!hin[0][r] || !hin[1][r] || !hin[2][r] || !hin[3][r] || !h_out[r]))
+            return fail_mb(ctx, HEFX_EINVAL, "%s: null host buffer", name);
+        r1 += L;
     }
     const hefx_params* pp = v0.pp;
-    const uint32_t K = pp->nlimbs, logn = pp->log2n;
-    const size_t n = (size_t)1 << logn;
-    if (K > 64) return fail_mb(ctx, HEFX_EUNSUPPORTED, "hefx_mult_front_batch_host: at most 64 special limbs");
+    if (K > 64) return fail_mb(ctx, HEFX_EUNSUPPORTED, "%s: at most 64 special limbs", name);
     const Layout lay = layout(r1, count, K);
-    if (lay.total > mb->slot_bytes) return fail_mb(ctx, HEFX_EINVAL, "hefx_mult_front_batch_host: batch too large");
+    if (lay.total > mb->slot_bytes) return fail_mb(ctx, HEFX_EINVAL, "%s: batch too large", name);
     if (cudaSetDevice(ctx->device) != cudaSuccess) return fail_mb(ctx, HEFX_ECUDA, "cudaSetDevice failed");
-    cudaStream_t s = (cudaStream_t)stream;
     const int slot = mb->next;
     mb->next = (mb->next + 1) % hefx_mult_batch::kSlots;
     if (mb->used[slot] && cudaEventSynchronize(mb->ev[slot]) != cudaSuccess)
-        return fail_mb(ctx, HEFX_ECUDA, "hefx_mult_front_batch_host: waiting for a descriptor slot failed");
+        return fail_mb(ctx, HEFX_ECUDA, "%s: waiting for a descriptor slot failed", name);
     uint8_t* hb = mb->host[slot];
     uint8_t* db = mb->dev[slot];
     MultRow* tp = reinterpret_cast<MultRow*>(hb + lay.tp);
@@ -228,26 +265,29 @@ hefx_status hefx_mult_front_batch_host(hefx_ctx* ctx, hefx_mult_batch* mb, const
         MultPlanView v;
         mult_plan_view(plans[r], &v);
         const size_t L = v.pq->nlimbs;
-        // request buffer: inputs (4L rows) | outputs (4L + 2K rows) | d2 (L) | c (L) | p (K)
-        uint32_t* d_in = d_buf[r];
-        uint32_t* d_out = d_in + 4 * L * n;
-        uint32_t* d2 = d_out + (4 * L + 2 * K) * n;
+        // workspace: d2 (L rows) | c = INTT(d2) (L) | p (K)
+        uint32_t* out = d_out[r];
+        uint32_t* d2 = d_work[r];
         uint32_t* c = d2 + L * n;
         uint32_t* pr = c + L * n;
-        const size_t in_bytes = L * n * 4;
-        const ptrdiff_t gap = h_a1[r] - h_a0[r];
-        if (gap >= (ptrdiff_t)(L * n) && h_b0[r] - h_a1[r] == gap && h_b1[r] - h_b0[r] == gap)
-            e = cudaMemcpy2DAsync(d_in, in_bytes, h_a0[r], (size_t)gap * 4, in_bytes, 4, cudaMemcpyHostToDevice, s);
-        else {
-            const uint32_t* hs[4] = {h_a0[r], h_a1[r], h_b0[r], h_b1[r]};
-            for (int i = 0; i < 4 && e == cudaSuccess; ++i)
-                e = cudaMemcpyAsync(d_in + i * L * n, hs[i], in_bytes, cudaMemcpyHostToDevice, s);
+        if (host) {
+            const size_t in_bytes = L * n * 4;
+            const bool packed = inputs[1][r] == inputs[0][r] + L * n && inputs[2][r] == inputs[1][r] + L * n &&
+                                inputs[3][r] == inputs[2][r] + L * n;
+            const ptrdiff_t gap = hin[1][r] - hin[0][r];
+            if (packed && gap >= (ptrdiff_t)(L * n) && hin[2][r] - hin[1][r] == gap && hin[3][r] - hin[2][r] == gap)
+                e = cudaMemcpy2DAsync(const_cast<uint32_t*>(inputs[0][r]), in_bytes, hin[0][r], (size_t)gap * 4,
+                                      in_bytes, 4, cudaMemcpyHostToDevice, s);
+            else
+                for (int i = 0; i < 4 && e == cudaSuccess; ++i)
+                    e = cudaMemcpyAsync(const_cast<uint32_t*>(inputs[i][r]), hin[i][r], in_bytes,
+                                        cudaMemcpyHostToDevice, s);
         }
         for (uint32_t l = 0; l < L; ++l, ++q) {
             MultRow& t = tp[q];
-            for (int i = 0; i < 4; ++i) t.x[i] = d_in + (i * L + l) * n;
-            t.y[0] = d_out + l * n;
-            t.y[1] = d_out + (L + l) * n;
+            for (int i = 0; i < 4; ++i) t.x[i] = inputs[i][r] + l * n;
+            t.y[0] = out + l * n;
+            t.y[1] = out + (L + l) * n;
             t.y[2] = d2 + l * n;
             t.lc = v.pq->d_lc + l;
             intt[q] = rowdesc(v.pq, l, d2 + l * n, c + l * n);
@@ -256,8 +296,8 @@ hefx_status hefx_mult_front_batch_host(hefx_ctx* ctx, hefx_mult_batch* mb, const
             k.x[0] = d2 + l * n;
             k.x[1] = v.kq[0] + l * n;
             k.x[2] = v.kq[1] + l * n;
-            k.y[0] = d_out + (2 * L + l) * n;
-            k.y[1] = d_out + (3 * L + l) * n;
+            k.y[0] = out + (2 * L + l) * n;
+            k.y[1] = out + (3 * L + l) * n;
             k.lc = v.pq->d_lc + l;
         }
         bc[r].c = v.bc->d_const;
@@ -271,8 +311,8 @@ hefx_status hefx_mult_front_batch_host(hefx_ctx* ctx, hefx_mult_batch* mb, const
             k.x[0] = pr + j * n;
             k.x[1] = v.kp[0] + j * n;
             k.x[2] = v.kp[1] + j * n;
-            k.y[0] = d_out + (4 * L + j) * n;
-            k.y[1] = d_out + (4 * L + K + j) * n;
+            k.y[0] = out + (4 * L + j) * n;
+            k.y[1] = out + (4 * L + K + j) * n;
             k.lc = pp->d_lc + j;
         }
     }
@@ -297,14 +337,56 @@ hefx_status hefx_mult_front_batch_host(hefx_ctx* ctx, hefx_mult_batch* mb, const
     }
     if (e == cudaSuccess) e = cudaEventRecord(mb->ev[slot], s);  // the slot's descriptors are free after this
     mb->used[slot] = true;
-    for (uint32_t r = 0; r < count && e == cudaSuccess; ++r) {
+    for (uint32_t r = 0; host && r < count && e == cudaSuccess; ++r) {
         MultPlanView v;
         mult_plan_view(plans[r], &v);
         const size_t L = v.pq->nlimbs;
-        e = cudaMemcpyAsync(h_out[r], d_buf[r] + 4 * L * n, (4 * L + 2 * K) * n * 4, cudaMemcpyDeviceToHost, s);
+        e = cudaMemcpyAsync(h_out[r], d_out[r], (4 * L + 2 * K) * n * 4, cudaMemcpyDeviceToHost, s);
     }
-    if (e != cudaSuccess) return fail_mb(ctx, HEFX_ECUDA, cudaGetErrorString(e));
+    if (e != cudaSuccess) return fail_mb(ctx, HEFX_ECUDA, "%s", cudaGetErrorString(e));
     return HEFX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+hefx_status hefx_mult_front_batch_host(hefx_ctx* ctx, hefx_mult_batch* mb, const hefx_mult_plan* const* plans,
+                                       uint32_t count, const uint32_t* const* h_a0, const uint32_t* const* h_a1,
+                                       const uint32_t* const* h_b0, const uint32_t* const* h_b1,
+                                       uint32_t* const* h_out, uint32_t* const* d_buf, void* stream) {
+    if (!ctx) return HEFX_EINVAL;
+    if (count == 0) return HEFX_OK;
+    if (!mb || mb->ctx != ctx) return fail_mb(ctx, HEFX_EINVAL, "batch object is null or of another context");
+    if (count > mb->max_requests || !plans || !d_buf)
+        return fail_mb(ctx, HEFX_EINVAL, "hefx_mult_front_batch_host: count above the batch object's or null arrays");
+    // each d_buf[r]: inputs (4L rows) | outputs (4L + 2K rows) | workspace (2L + K rows)
+    std::vector<const uint32_t*> in[4];
+    std::vector<uint32_t*> out(count), work(count);
+    for (uint32_t r = 0; r < count; ++r) {
+        MultPlanView v;
+        if (!mult_plan_view(plans[r], &v) || v.ctx != ctx || !d_buf[r])
+            return fail_mb(ctx, HEFX_EINVAL, "hefx_mult_front_batch_host: a plan or buffer is null or foreign");
+        const size_t L = v.pq->nlimbs, K = v.pp->nlimbs, n = (size_t)v.pq->n;
+        for (int i = 0; i < 4; ++i) in[i].push_back(d_buf[r] + i * L * n);
+        out[r] = d_buf[r] + 4 * L * n;
+        work[r] = out[r] + (4 * L + 2 * K) * n;
+    }
+    const uint32_t* const* const inputs[4] = {in[0].data(), in[1].data(), in[2].data(), in[3].data()};
+    const uint32_t* const* const hin[4] = {h_a0, h_a1, h_b0, h_b1};
+    if (!h_a0 || !h_a1 || !h_b0 || !h_b1 || !h_out)
+        return fail_mb(ctx, HEFX_EINVAL, "hefx_mult_front_batch_host: null host arrays");
+    return front_batch(ctx, mb, plans, count, inputs, out.data(), work.data(), hin, h_out, (cudaStream_t)stream,
+                       "hefx_mult_front_batch_host");
+}
+
+hefx_status hefx_mult_front_batch(hefx_ctx* ctx, hefx_mult_batch* mb, const hefx_mult_plan* const* plans,
+                                  uint32_t count, const uint32_t* const* d_a0, const uint32_t* const* d_a1,
+                                  const uint32_t* const* d_b0, const uint32_t* const* d_b1, uint32_t* const* d_out,
+                                  uint32_t* const* d_work, void* stream) {
+    const uint32_t* const* const inputs[4] = {d_a0, d_a1, d_b0, d_b1};
+    return front_batch(ctx, mb, plans, count, inputs, d_out, d_work, nullptr, nullptr, (cudaStream_t)stream,
+                       "hefx_mult_front_batch");
 }
 
 }  // extern "C"

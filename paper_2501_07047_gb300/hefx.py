@@ -64,6 +64,7 @@ SIGNATURES = {
     "hefx_mult_batch_create": (_i32, [_vp, _u32, _u32, ctypes.POINTER(_vp)]),
     "hefx_mult_batch_destroy": (None, [_vp]),
     "hefx_mult_front_batch_host": (_i32, [_vp, _vp, _vp, _u32, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "hefx_mult_front_batch": (_i32, [_vp, _vp, _vp, _u32, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "hefx_batch_plan_create": (_i32, [_vp, _vp, _sz, _i32, ctypes.POINTER(_vp)]),
     "hefx_batch_plan_destroy": (None, [_vp]),
     "hefx_batch_polymul": (_i32, [_vp, _vp, _vp]),
@@ -332,7 +333,7 @@ def hefx_batch_plan_launches(plan) -> int:
 
 
 def hefx_mult_batch_create(ctx, max_requests: int, max_limbs: int) -> int:
-    """Descriptor slots for batched serving requests (hefx_mult_front_batch_host)."""
+    """Descriptor slots for batched serving requests (hefx_mult_front_batch(_host))."""
     out = _vp()
     _check(ctx, load().hefx_mult_batch_create(ctx, int(max_requests), int(max_limbs), ctypes.byref(out)))
     return out.value
@@ -354,3 +355,13 @@ def hefx_mult_front_batch_host(ctx, batch, plans, h_a0, h_a1, h_b0, h_b1, h_out,
     arrs = [_ptr_array(x) for x in (plans, h_a0, h_a1, h_b0, h_b1, h_out, d_buf)]
     _check(ctx, load().hefx_mult_front_batch_host(ctx, batch, arrs[0], n, arrs[1], arrs[2], arrs[3], arrs[4],
                                                   arrs[5], arrs[6], _stream(stream)))
+
+
+def hefx_mult_front_batch(ctx, batch, plans, d_a0, d_a1, d_b0, d_b1, d_out, d_work, stream=None) -> None:
+    """The batched front half on device-resident operands (lists of per-request plans and device
+    buffers, as in hefx_mult_front)."""
+    n = len(plans)
+    assert all(len(x) == n for x in (d_a0, d_a1, d_b0, d_b1, d_out, d_work))
+    arrs = [_ptr_array(x) for x in (plans, d_a0, d_a1, d_b0, d_b1, d_out, d_work)]
+    _check(ctx, load().hefx_mult_front_batch(ctx, batch, arrs[0], n, arrs[1], arrs[2], arrs[3], arrs[4],
+                                             arrs[5], arrs[6], _stream(stream)))

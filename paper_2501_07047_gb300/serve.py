@@ -101,10 +101,13 @@ class GpuExecutor:
     grouped=False: one native call per request (`hefx_mult_front_host`, six launches each).
     grouped=True: the requests admitted together are grouped by ring degree and each group
     (at most `max_group` requests) is one `hefx_mult_front_batch_host` call whose five
-    launches cover every request of the group (continuous batching across requests)."""
+    launches cover every request of the group (continuous batching across requests).
+    resident=True: the requests' ciphertexts live in device memory (uploaded once, like the
+    keys) and their results stay there (`hefx_mult_front_batch`), so nothing crosses the host
+    link per request; `outputs` reads a result back only when asked."""
 
     def __init__(self, ctx: int, nstreams: int = 8, seed: int = 5, variants: int = 2, slots: int | None = None,
-                 grouped: bool = False, max_group: int = 32):
+                 grouped: bool = False, max_group: int = 32, resident: bool = False):
         import torch
 
         from . import hefx
@@ -124,8 +127,10 @@ class GpuExecutor:
         self.free_slots = [self._slot() for _ in range(4 * nstreams if slots is None else slots)]
         self.pprimes = inputs.special_primes(N_SPECIAL)
         self.grouped = grouped
+        self.resident = resident
         self.max_group = max_group
-        self.batch = hefx.hefx_mult_batch_create(ctx, max_group, len(self.qprimes)) if grouped else None
+        self.batch = hefx.hefx_mult_batch_create(ctx, max_group if grouped else 1, len(self.qprimes)) \
+            if grouped or resident else None
 
     # ---------------------------------------------------------------- per-shape resources
     def pool(self, logn: int):
@@ -152,6 +157,9 @@ class GpuExecutor:
             # native call uploads as one pitched copy
             block = torch.from_numpy(np.stack(arrs).view(np.int32).copy()).pin_memory()
             pl["host_in"].append([block[c] for c in range(4)])
+            if self.resident:  # the same ciphertexts, resident in device memory
+                dblock = block.cuda()
+                pl.setdefault("dev_in", []).append([dblock[c] for c in range(4)])
         assert all(a.shape[0] == LQ for a in pl["host_in"][0])
         self.pools[logn] = pl
         return pl
@@ -194,9 +202,32 @@ class GpuExecutor:
                 "h": torch.empty((4 * L + 2 * K) * n, dtype=torch.int32, pin_memory=True),
                 "ev": torch.cuda.Event()}
 
+    def _resident_call(self, reqs, slots, s):
+        """hefx_mult_front_batch over device-resident inputs; each slot's device buffer holds the
+        request's outputs ([4L + 2K][N]) then its workspace ([2L + K][N])."""
+        plans, ins, outs, works = [], [[], [], [], []], [], []
+        for req, slot in zip(reqs, slots):
+            res = self.shape(req.logn, req.L)
+            pl = self.pool(req.logn)
+            plans.append(res["mp"])
+            for c, t in enumerate(pl["dev_in"][req.variant % self.variants]):
+                ins[c].append(t)
+            n = 1 << req.logn
+            outs.append(slot["d"])
+            works.append(slot["d"][(4 * req.L + 2 * N_SPECIAL) * n:])
+        self.hefx.hefx_mult_front_batch(self.ctx, self.batch, plans, *ins, outs, works, s.cuda_stream)
+
     def launch(self, req: Request):
         """Enqueues one request as one hefx_mult_front_host call (one pitched upload of the four
-        inputs, every stage, one read-back of the contiguous outputs) and a completion event."""
+        inputs, every stage, one read-back of the contiguous outputs) and a completion event
+        (resident: one hefx_mult_front_batch call over its device-resident inputs)."""
+        if self.resident:
+            s = self.streams[self.next_stream]
+            self.next_stream = (self.next_stream + 1) % len(self.streams)
+            slot = self._slot()
+            self._resident_call([req], [slot], s)
+            slot["ev"].record(s)
+            return {"ev": slot["ev"], "slot": slot, "stream": s}
         res = self.shape(req.logn, req.L)
         pl = self.pool(req.logn)
         s = self.streams[self.next_stream]
@@ -212,6 +243,12 @@ class GpuExecutor:
         event; returns one handle per request (sharing the event)."""
         s = self.streams[self.next_stream]
         self.next_stream = (self.next_stream + 1) % len(self.streams)
+        if self.resident:
+            slots = [self._slot() for _ in reqs]
+            self._resident_call(reqs, slots, s)
+            ev = slots[0]["ev"]
+            ev.record(s)
+            return [{"ev": ev, "slot": sl, "stream": s} for sl in slots]
         plans, ins, outs, bufs, slots = [], [[], [], [], []], [], [], []
         for req in reqs:
             res = self.shape(req.logn, req.L)
@@ -237,7 +274,9 @@ class GpuExecutor:
 
     def outputs(self, req: Request, handle):
         L, n = req.L, 1 << req.logn
-        o = handle["slot"]["h"][:(4 * L + 2 * N_SPECIAL) * n].numpy().view(np.uint32).reshape(-1, n)
+        words = (4 * L + 2 * N_SPECIAL) * n
+        src = handle["slot"]["d"][:words].cpu() if self.resident else handle["slot"]["h"][:words]
+        o = src.numpy().view(np.uint32).reshape(-1, n)
         return (o[0:L].copy(), o[L:2 * L].copy(), np.concatenate([o[2 * L:3 * L], o[4 * L:4 * L + N_SPECIAL]]),
                 np.concatenate([o[3 * L:4 * L], o[4 * L + N_SPECIAL:]]))
 

@@ -170,3 +170,67 @@ def test_mult_batch_validation(ctx):
             hefx.hefx_mult_batch_destroy(mb)
     finally:
         ex.close()
+
+
+@pytest.mark.parametrize("grouped", [False, True])
+def test_resident_equals_host_and_oracle(ctx, grouped):
+    """Resident serving (ciphertexts and results stay in device memory; hefx_mult_front_batch):
+    every output equals the host-buffer path's (bit for bit), per request and in groups, and
+    the small requests equal the oracle composition."""
+    shapes = [(13, 8), (14, 20), (16, 36), (15, 11), (13, 30), (16, 9)]
+    host_ex = GpuExecutor(ctx, nstreams=2, seed=13)
+    res_ex = GpuExecutor(ctx, nstreams=2, seed=13, grouped=grouped, max_group=4, resident=True)
+    try:
+        ref = []
+        for k, (logn, L) in enumerate(shapes):
+            r = Request(k, logn, L, 0.0, variant=k % 2)
+            serve([r], host_ex, keep_outputs=True)
+            ref.append(r.outputs)
+        mix = [Request(k, logn, L, 0.0, variant=k % 2) for k, (logn, L) in enumerate(shapes)]
+        st = serve(mix, res_ex, keep_outputs=True, max_slots=8)
+        assert st["completed"] == len(shapes)
+        for r, exp_out in zip(mix, ref):
+            for got, exp in zip(r.outputs, exp_out):
+                assert (got == exp).all(), (r.rid, r.logn, r.L)
+            if r.logn == 13:
+                for got, exp in zip(r.outputs, oracle_request(res_ex, r)):
+                    assert (got == exp).all(), (r.rid, r.L)
+    finally:
+        host_ex.close()
+        res_ex.close()
+
+
+def test_front_batch_validation(ctx):
+    """hefx_mult_front_batch refuses an output that overlaps the request's inputs, before any
+    launch."""
+    import torch
+    logn, L = 10, 4
+    n = 1 << logn
+    qs, ps = inputs.source_primes(L), inputs.special_primes(N_SPECIAL)
+    pq = hefx.hefx_params_create(ctx, logn, qs)
+    pp = hefx.hefx_params_create(ctx, logn, ps)
+    bc = hefx.hefx_bconv_plan_create(ctx, logn, qs, ps)
+    kq = torch.zeros((L, n), dtype=torch.int32, device="cuda")
+    kp = torch.zeros((N_SPECIAL, n), dtype=torch.int32, device="cuda")
+    mp = hefx.hefx_mult_plan_create(ctx, pq, pp, bc, kq, kq, kp, kp)
+    mb = hefx.hefx_mult_batch_create(ctx, 2, L)
+    try:
+        ins = torch.zeros((4, L, n), dtype=torch.int32, device="cuda")
+        out = torch.zeros(((4 * L + 2 * N_SPECIAL), n), dtype=torch.int32, device="cuda")
+        work = torch.zeros(((2 * L + N_SPECIAL), n), dtype=torch.int32, device="cuda")
+        hefx.hefx_mult_front_batch(ctx, mb, [mp], [ins[0]], [ins[1]], [ins[2]], [ins[3]], [out], [work])
+        torch.cuda.synchronize()
+        with pytest.raises(hefx.HefxError) as e:  # output over the inputs
+            hefx.hefx_mult_front_batch(ctx, mb, [mp], [ins[0]], [ins[1]], [ins[2]], [ins[3]], [ins[0]], [work])
+        assert e.value.status == hefx.HEFX_EINVAL
+        with pytest.raises(hefx.HefxError) as e:  # more requests than the batch object holds
+            hefx.hefx_mult_front_batch(ctx, mb, [mp] * 3, [ins[0]] * 3, [ins[1]] * 3, [ins[2]] * 3, [ins[3]] * 3,
+                                       [out] * 3, [work] * 3)
+        assert e.value.status == hefx.HEFX_EINVAL
+    finally:
+        hefx.hefx_mult_batch_destroy(mb)
+        hefx.hefx_mult_plan_destroy(mp)
+        hefx.hefx_bconv_plan_destroy(bc)
+        hefx.hefx_params_destroy(pq)
+        hefx.hefx_params_destroy(pp)
+
