@@ -651,7 +651,7 @@ def bench_serving(ctx, args):
     continuous batching (requests admitted together run as groups of one ring degree in shared
     launches) and, for comparison at the top rates, one native call per request."""
     import torch
-    from paper_2501_07047_gb300.serve import N_SPECIAL, GpuExecutor, poisson_requests, serve
+    from paper_2501_07047_gb300.serve import N_SPECIAL, GpuExecutor, poisson_requests, serve, serve_native
     res = {"workload": "HE-Mult front half, N in {2^13..2^16}, L in [8, 36], 8 special primes", "budget_GB": 40}
     # the ceiling the host link sets: every request uploads 4 L N words and reads back
     # (4 L + 2 K) N words; the link rate is measured here with both directions at once
@@ -680,9 +680,12 @@ def bench_serving(ctx, args):
     # host: every request uploads its ciphertexts and reads its results back (link-bound);
     # resident: ciphertexts and results stay in device memory (the serving pattern's resident
     # residues), so the rate is the device's and the loop's
-    for mode, rates in (("grouped_resident", (1600, 6400, 25600, 51200, 102400, 204800)),
+    # native: the same resident groups with the request loop in native code (hefx_serve_run)
+    for mode, rates in (("native_resident", (6400, 25600, 51200, 102400, 204800, 409600)),
+                        ("grouped_resident", (1600, 6400, 25600, 51200, 102400, 204800)),
                         ("grouped", (100, 400, 1600, 6400, 25600, 51200)), ("per_request", (6400, 25600))):
-        ex = GpuExecutor(ctx, nstreams=8, grouped=mode.startswith("grouped"), resident=mode.endswith("resident"))
+        ex = GpuExecutor(ctx, nstreams=8, grouped=mode != "per_request", resident=mode.endswith("resident"))
+        run = serve_native if mode.startswith("native") else serve
         try:
             out = {}
             for rate in rates:
@@ -690,9 +693,9 @@ def bench_serving(ctx, args):
                 reqs = poisson_requests(inputs_seed(5, rate), count, rate)
                 for r in reqs:
                     ex.warm(r.logn, r.L)
-                serve(reqs[:8], ex)  # warm kernels on this request mix
+                run(reqs[:8], ex)  # warm kernels on this request mix
                 reqs = poisson_requests(inputs_seed(5, rate), count, rate)
-                st = serve(reqs, ex, budget_bytes=40 << 30)
+                st = run(reqs, ex, budget_bytes=40 << 30)
                 out[f"rate_{rate}"] = {k: (round(v, 3) if isinstance(v, float) else v) for k, v in st.items()}
             res[mode] = out
         finally:

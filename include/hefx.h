@@ -451,6 +451,59 @@ hefx_status hefx_mult_front_batch(hefx_ctx* ctx, hefx_mult_batch* batch, const h
                                   uint32_t* const* d_work, void* stream);
 
 /*
+ * Native serving loop (the request loop of the build's serving pattern; continuous batching of
+ * HE-Mult front-half requests on device-resident ciphertexts).  Runs in real time on the
+ * calling host thread until every request is done or rejected:
+ *  - request i arrives reqs[i].arrival_s seconds after the call starts (sorted by arrival);
+ *    one needing more than budget_bytes is rejected;
+ *  - admission is FIFO (head-of-line blocking) while the bytes of the admitted requests fit
+ *    budget_bytes and a result slot is free;
+ *  - the requests admitted in one pass are grouped by ring degree and P parameter set and
+ *    each group of at most max_group runs as one hefx_mult_front_batch on the next of the
+ *    streams (round-robin) with the request's result slot as output (slot_out[k]:
+ *    [4L + 2K][N] words, slot_work[k]: [2L + K][N], for the largest request served);
+ *  - a group completes with an event recorded after its launches; its requests' slots and
+ *    bytes are then released.
+ * out[i] receives the admission and completion times (seconds from the start), the status and
+ * the slot that holds the results (valid until the slot is reused by a later request).  The
+ * caller owns every buffer and stream.  Errors: EINVAL (null or foreign arguments, unsorted
+ * arrivals), ECUDA (the run stops after waiting for the launched groups).
+ */
+typedef enum { HEFX_SERVE_PENDING = 0, HEFX_SERVE_RUNNING = 1, HEFX_SERVE_DONE = 2, HEFX_SERVE_REJECTED = 3 } hefx_serve_status;
+typedef struct {
+    double arrival_s;
+    const hefx_mult_plan* plan;
+    const uint32_t* d_a0;
+    const uint32_t* d_a1;
+    const uint32_t* d_b0;
+    const uint32_t* d_b1;
+    uint64_t bytes;  /* device bytes charged against the budget while the request runs */
+} hefx_serve_request;
+typedef struct {
+    double admitted_s;
+    double completed_s;
+    int32_t status; /* hefx_serve_status */
+    uint32_t slot;
+} hefx_serve_result;
+typedef struct {
+    uint64_t max_active;
+    uint64_t memory_high_water_bytes;
+    uint64_t groups;
+} hefx_serve_stats;
+typedef struct {
+    uint32_t nstreams;
+    void* const* streams;
+    uint32_t nslots;
+    uint32_t* const* slot_out;
+    uint32_t* const* slot_work;
+    uint64_t budget_bytes;
+    uint32_t max_group;
+    hefx_serve_stats* stats; /* optional */
+} hefx_serve_config;
+hefx_status hefx_serve_run(hefx_ctx* ctx, hefx_mult_batch* batch, const hefx_serve_request* reqs, size_t n,
+                           const hefx_serve_config* cfg, hefx_serve_result* out);
+
+/*
  * Batched polynomial products of uneven shape (the batching pattern of the build; the
  * paper's batching study is Sec. V-B3, "TPUs favor large batch").  Each job multiplies two
  * polynomials of ring degree N = 2^params->log2n over the first `nlimbs` primes of

@@ -258,6 +258,11 @@ struct MultPlanView {
     const uint32_t* kp[2];
 };
 bool mult_plan_view(const hefx_mult_plan* plan, MultPlanView* out);
+// The batched front half on device pointers (mult_batch.cu; hefx_mult_front_batch's body):
+// inputs[i][r] request r's input i, d_out[r] its outputs, d_work[r] its workspace.
+hefx_status mult_front_batch_dev(hefx_ctx* ctx, hefx_mult_batch* mb, const hefx_mult_plan* const* plans,
+                                 uint32_t count, const uint32_t* const* const inputs[4], uint32_t* const* d_out,
+                                 uint32_t* const* d_work, cudaStream_t s);
 cudaError_t launch_bconv_cc_list(const BcListEntry* d_list, uint32_t count, uint32_t log2n, uint32_t lp_max,
                                  cudaStream_t stream);
 // Fused batch kernel (ntt_cc_batch.cu).

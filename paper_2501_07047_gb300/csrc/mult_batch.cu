@@ -349,6 +349,12 @@ hefx_status front_batch(hefx_ctx* ctx, hefx_mult_batch* mb, const hefx_mult_plan
 
 }  // namespace
 
+hefx_status hefx::mult_front_batch_dev(hefx_ctx* ctx, hefx_mult_batch* mb, const hefx_mult_plan* const* plans,
+                                       uint32_t count, const uint32_t* const* const inputs[4],
+                                       uint32_t* const* d_out, uint32_t* const* d_work, cudaStream_t s) {
+    return front_batch(ctx, mb, plans, count, inputs, d_out, d_work, nullptr, nullptr, s, "hefx_serve_run");
+}
+
 extern "C" {
 
 hefx_status hefx_mult_front_batch_host(hefx_ctx* ctx, hefx_mult_batch* mb, const hefx_mult_plan* const* plans,

@@ -65,6 +65,7 @@ SIGNATURES = {
     "hefx_mult_batch_destroy": (None, [_vp]),
     "hefx_mult_front_batch_host": (_i32, [_vp, _vp, _vp, _u32, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "hefx_mult_front_batch": (_i32, [_vp, _vp, _vp, _u32, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "hefx_serve_run": (_i32, [_vp, _vp, _vp, _sz, _vp, _vp]),
     "hefx_batch_plan_create": (_i32, [_vp, _vp, _sz, _i32, ctypes.POINTER(_vp)]),
     "hefx_batch_plan_destroy": (None, [_vp]),
     "hefx_batch_polymul": (_i32, [_vp, _vp, _vp]),
@@ -365,3 +366,49 @@ def hefx_mult_front_batch(ctx, batch, plans, d_a0, d_a1, d_b0, d_b1, d_out, d_wo
     arrs = [_ptr_array(x) for x in (plans, d_a0, d_a1, d_b0, d_b1, d_out, d_work)]
     _check(ctx, load().hefx_mult_front_batch(ctx, batch, arrs[0], n, arrs[1], arrs[2], arrs[3], arrs[4],
                                              arrs[5], arrs[6], _stream(stream)))
+
+
+class ServeRequest(ctypes.Structure):
+    _fields_ = [("arrival_s", ctypes.c_double), ("plan", _vp), ("d_a0", _vp), ("d_a1", _vp), ("d_b0", _vp),
+                ("d_b1", _vp), ("bytes", ctypes.c_uint64)]
+
+
+class ServeResult(ctypes.Structure):
+    _fields_ = [("admitted_s", ctypes.c_double), ("completed_s", ctypes.c_double), ("status", ctypes.c_int32),
+                ("slot", ctypes.c_uint32)]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [("max_active", ctypes.c_uint64), ("memory_high_water_bytes", ctypes.c_uint64),
+                ("groups", ctypes.c_uint64)]
+
+
+class ServeConfig(ctypes.Structure):
+    _fields_ = [("nstreams", ctypes.c_uint32), ("streams", ctypes.POINTER(_vp)), ("nslots", ctypes.c_uint32),
+                ("slot_out", ctypes.POINTER(_vp)), ("slot_work", ctypes.POINTER(_vp)),
+                ("budget_bytes", ctypes.c_uint64), ("max_group", ctypes.c_uint32),
+                ("stats", ctypes.POINTER(ServeStats))]
+
+
+SERVE_PENDING, SERVE_RUNNING, SERVE_DONE, SERVE_REJECTED = 0, 1, 2, 3
+
+
+def hefx_serve_run(ctx, batch, requests, streams, slot_out, slot_work, budget_bytes: int, max_group: int):
+    """Native serving loop.  requests: (arrival_s, plan, d_a0, d_a1, d_b0, d_b1, bytes) tuples
+    sorted by arrival; streams: CUDA streams (objects with .cuda_stream or handles); slot_out /
+    slot_work: the result slots' device buffers.  Returns (results, stats) as ctypes arrays."""
+    n = len(requests)
+    reqs = (ServeRequest * max(n, 1))()
+    for i, (t, plan, a0, a1, b0, b1, nbytes) in enumerate(requests):
+        reqs[i] = ServeRequest(float(t), plan, _ptr(a0), _ptr(a1), _ptr(b0), _ptr(b1), int(nbytes))
+    res = (ServeResult * max(n, 1))()
+    stats = ServeStats()
+    st_arr = (_vp * len(streams))(*[_stream(x) for x in streams])
+    so = _ptr_array(slot_out)
+    sw = _ptr_array(slot_work)
+    pv = ctypes.POINTER(_vp)
+    cfg = ServeConfig(len(streams), ctypes.cast(st_arr, pv), len(slot_out), ctypes.cast(so, pv), ctypes.cast(sw, pv),
+                      int(budget_bytes), int(max_group), ctypes.pointer(stats))
+    _check(ctx, load().hefx_serve_run(ctx, batch, ctypes.cast(reqs, _vp), n, ctypes.byref(cfg), ctypes.cast(res, _vp)))
+    return res, stats
+

@@ -384,6 +384,51 @@ def _serve(requests, executor, budget_bytes, max_slots, keep_outputs):
     }
 
 
+def serve_native(requests, executor, budget_bytes: int = 40 << 30, max_slots: int | None = None,
+                 keep_outputs: bool = False):
+    """serve() with the request loop in native code (hefx_serve_run): the same admission,
+    grouping and completion rules, for a resident grouped executor.  The result slots are the
+    executor's (at most max_slots, default 4 per stream); with keep_outputs the results are
+    read from their slots after the run (give at least as many slots as requests)."""
+    assert executor.resident and executor.grouped, "the native loop serves resident, grouped requests"
+    hefx, torch = executor.hefx, executor.torch
+    requests = sorted(requests, key=lambda r: r.arrival)
+    nslots = max_slots if max_slots is not None else 4 * len(executor.streams)
+    slots = [executor._slot() for _ in range(nslots)]
+    try:
+        rows = []
+        for req in requests:
+            res = executor.shape(req.logn, req.L)
+            a0, a1, b0, b1 = executor.pool(req.logn)["dev_in"][req.variant % executor.variants]
+            rows.append((req.arrival, res["mp"], a0, a1, b0, b1, request_bytes(req.logn, req.L)))
+        outs = [sl["d"] for sl in slots]
+        # the workspace after the largest request's outputs ([4L + 2K][N] at L = 36, N = 2^16)
+        works = [sl["d"][(4 * len(executor.qprimes) + 2 * N_SPECIAL) << 16:] for sl in slots]
+        torch.cuda.synchronize()
+        res_arr, stats = hefx.hefx_serve_run(executor.ctx, executor.batch, rows, executor.streams, outs, works,
+                                             budget_bytes, executor.max_group)
+        torch.cuda.synchronize()
+        for k, req in enumerate(requests):
+            r = res_arr[k]
+            req.status = {hefx.SERVE_DONE: "done", hefx.SERVE_REJECTED: "rejected"}.get(r.status, "failed")
+            req.admitted, req.completed = r.admitted_s, r.completed_s
+            if keep_outputs and req.status == "done":
+                req.outputs = executor.outputs(req, {"slot": slots[r.slot]})
+    finally:
+        executor.free_slots.extend(slots)
+    done = [r for r in requests if r.status == "done"]
+    lat = np.array([r.completed - r.arrival for r in done]) if done else np.zeros(1)
+    span = (max(r.completed for r in done) - min(r.arrival for r in done)) if done else 0.0
+    return {
+        "requests": len(requests), "completed": len(done),
+        "rejected": sum(r.status == "rejected" for r in requests),
+        "throughput_rps": len(done) / span if span > 0 else 0.0,
+        "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+        "max_active": int(stats.max_active), "memory_high_water_bytes": int(stats.memory_high_water_bytes),
+        "groups": int(stats.groups),
+    }
+
+
 def poisson_requests(seed: int, count: int, rate_hz: float, logn_choices=(13, 14, 15, 16), lmin=8, lmax=36,
                      variants: int = 2):
     """Seeded Poisson arrivals with N and L drawn uniformly per request."""

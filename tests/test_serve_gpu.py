@@ -5,7 +5,8 @@ import pytest
 
 import oracle
 from paper_2501_07047_gb300 import hefx, inputs
-from paper_2501_07047_gb300.serve import GpuExecutor, N_SPECIAL, Request, poisson_requests, request_bytes, serve
+from paper_2501_07047_gb300.serve import (GpuExecutor, N_SPECIAL, Request, poisson_requests, request_bytes, serve,
+                                          serve_native)
 
 pytestmark = pytest.mark.gpu
 
@@ -233,4 +234,41 @@ def test_front_batch_validation(ctx):
         hefx.hefx_bconv_plan_destroy(bc)
         hefx.hefx_params_destroy(pq)
         hefx.hefx_params_destroy(pp)
+
+
+def test_native_loop_equals_python_and_oracle(ctx):
+    """The native request loop (hefx_serve_run) on resident ciphertexts: every output equals the
+    host-buffer path's, the small requests the oracle's; a Poisson run completes every request
+    with several in flight inside the budget, and an oversize request is rejected."""
+    shapes = [(13, 8), (14, 20), (16, 36), (15, 11), (13, 30), (16, 9), (14, 8), (13, 12)]
+    host_ex = GpuExecutor(ctx, nstreams=2, seed=14)
+    ex = GpuExecutor(ctx, nstreams=4, seed=14, grouped=True, max_group=4, resident=True)
+    try:
+        ref = []
+        for k, (logn, L) in enumerate(shapes):
+            r = Request(k, logn, L, 0.0, variant=k % 2)
+            serve([r], host_ex, keep_outputs=True)
+            ref.append(r.outputs)
+        mix = [Request(k, logn, L, 0.0, variant=k % 2) for k, (logn, L) in enumerate(shapes)]
+        st = serve_native(mix, ex, keep_outputs=True, max_slots=len(shapes))
+        assert st["completed"] == len(shapes) and st["groups"] < len(shapes)  # some requests shared launches
+        for r, exp_out in zip(mix, ref):
+            for got, exp in zip(r.outputs, exp_out):
+                assert (got == exp).all(), (r.rid, r.logn, r.L)
+            if r.logn == 13:
+                for got, exp in zip(r.outputs, oracle_request(ex, r)):
+                    assert (got == exp).all(), (r.rid, r.L)
+        reqs = poisson_requests(15, 80, rate_hz=20000.0, logn_choices=(13, 14), lmin=8, lmax=16)
+        for r in reqs:
+            ex.warm(r.logn, r.L)
+        budget = 6 * request_bytes(14, 16)
+        st = serve_native(reqs, ex, budget_bytes=budget, max_slots=16)
+        assert st["completed"] == 80 and st["max_active"] >= 2 and st["memory_high_water_bytes"] <= budget
+        big = Request(99, 16, 36, 0.0)
+        ex.warm(16, 36)
+        st = serve_native([big], ex, budget_bytes=budget)
+        assert big.status == "rejected" and st["rejected"] == 1
+    finally:
+        host_ex.close()
+        ex.close()
 
