@@ -82,10 +82,13 @@ def time_candidates(ctx: int, params: int, logn: int, primes, batch: int = 4, re
         path = cand[0]
         if hefx.raw_status("hefx_ntt_fwd", ctx, params, d.data_ptr(), 0, hefx.PATHS[path], s.cuda_stream) != 0:
             continue
-        if path == "tensor":
-            hefx.hefx_params_set_tensor_config(ctx, params, cand[1], cand[3], cand[2])
-        else:
-            hefx.hefx_params_set_cc_schedule(ctx, params, CC_SCHEDULES[cand[1]])
+        try:
+            if path == "tensor":
+                hefx.hefx_params_set_tensor_config(ctx, params, cand[1], cand[3], cand[2])
+            else:
+                hefx.hefx_params_set_cc_schedule(ctx, params, CC_SCHEDULES[cand[1]])
+        except hefx.HefxError:
+            continue  # not built for this parameter set (e.g. a split 30-bit moduli cannot take)
         d.copy_(d0)
         hefx.hefx_ntt_fwd(ctx, params, d, batch, path, s)
         hefx.hefx_ntt_inv(ctx, params, d, batch, path, s)

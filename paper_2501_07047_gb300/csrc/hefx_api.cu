@@ -72,7 +72,7 @@ hefx_status ensure_tc(hefx_ctx* ctx, const hefx_params* pc) {
     if (!tc_supported(p))
         return fail(ctx, HEFX_EUNSUPPORTED, "tensor path not available for N = 2^%u with these moduli", p->log2n);
     std::lock_guard<std::mutex> g(p->tc_mu);
-    if (!p->tc) {
+    if (!p->tc && tc_narrow(p)) {  // the single-pass form's tables (no-allocation product)
         cudaError_t e = tc_prepare(p);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "tensor-path tables");
     }
@@ -890,8 +890,9 @@ hefx_status hefx_poly_mul_noalloc(hefx_ctx* ctx, const hefx_params* p, const uin
     if ((st = check_ntt_args(ctx, p, b, "d_b")) != HEFX_OK) return st;
     if ((st = check_ntt_args(ctx, p, c, "d_c")) != HEFX_OK) return st;
     if ((st = use_device(ctx)) != HEFX_OK) return st;
-    if (!tc_supported(p))
-        return fail(ctx, HEFX_EUNSUPPORTED, "tensor path not available for N = 2^%u with these moduli", p->log2n);
+    if (!tc_narrow(p))
+        return fail(ctx, HEFX_EUNSUPPORTED,
+                    "hefx_poly_mul_noalloc needs N = 2^14 .. 2^16 and moduli below 2^28 (N = 2^%u here)", p->log2n);
     if (p->red_ntt != HEFX_RED_SHOUP)
         return fail(ctx, HEFX_EUNSUPPORTED, "hefx_poly_mul_noalloc uses the default (Shoup) NTT reduction only");
     {
@@ -964,6 +965,10 @@ hefx_status hefx_params_set_tensor_config(hefx_params* p, uint32_t log2r, uint32
     }
     if (tile_outputs != 32 && tile_outputs != 64)
         return fail(p->ctx, HEFX_EINVAL, "tile_outputs must be 32 or 64, not %u", tile_outputs);
+    if (tc2_wide(p) && (log2r2 == 0 || log2r > 6 || log2r2 > 6 || (int)logn - (int)log2r - (int)log2r2 > 6))
+        return fail(p->ctx, HEFX_EUNSUPPORTED,
+                    "moduli of 29-30 bits take 8-bit digits, whose fp32 sums are exact for reduction lengths "
+                    "<= 64 only: a three-factor split with every factor <= 64 (64 x 32 x 32 at N = 2^16)");
     hefx_status st = use_device(p->ctx);
     if (st != HEFX_OK) return st;
     std::lock_guard<std::mutex> g(p->tc_mu);

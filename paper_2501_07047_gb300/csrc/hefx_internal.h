@@ -242,7 +242,12 @@ cudaError_t launch_mod_up(const hefx_modup_plan* plan, const uint32_t* c, uint32
 void bconv_plan_free(hefx_bconv_plan* plan);
 
 // Tensor-core path (ntt_tc.cu / bconv_tc.cu).
+// The pipelined tensor NTT (ntt_tc2.cu) runs N = 2^14 .. 2^16 for every modulus below 2^30
+// (8-bit digits above 2^28); the single-pass form (ntt_tc.cu, the no-allocation product)
+// needs moduli below 2^28.
 bool tc_supported(const hefx_params* p);
+bool tc_narrow(const hefx_params* p);
+inline bool tc2_wide(const hefx_params* p) { return p->max_prime >= (1u << 28); }
 cudaError_t tc_prepare(hefx_params* p);
 void tc_free(hefx_params* p);
 cudaError_t tc_check(const hefx_params* p, cudaStream_t stream, uint32_t* code);

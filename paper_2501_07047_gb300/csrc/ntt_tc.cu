@@ -338,11 +338,10 @@ bool encode_map_2d(CUtensorMap* map, CUtensorMapDataType dtype, void* base, uint
                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-bool tc_supported(const hefx_params* p) {
-    if (p->log2n < 14 || p->log2n > 16 || !encode_fn()) return false;
-    for (uint32_t q : p->primes)
-        if (q >= (1u << 28)) return false;  // 4 digits of 7 bits
-    return true;
+bool tc_supported(const hefx_params* p) { return p->log2n >= 14 && p->log2n <= 16 && encode_fn(); }
+
+bool tc_narrow(const hefx_params* p) {
+    return tc_supported(p) && p->max_prime < (1u << 28);  // the single-pass form's 6-bit chunks
 }
 
 void tc_free(hefx_params* p) {

@@ -5,8 +5,10 @@
 //
 // with the data digits as the A operand (128 data rows per CTA) and the BAT-compiled constant
 // (Alg. 2, OfflineCompileLeft) as the B operand: 64 outputs x 4 chunks = 256 columns per tile.
-// Data digits and constant chunks are both 7 bits (fp16-exact), so partial sums stay below
-// 4 * 256 * 127 * 127 < 2^24 and the fp32 accumulation is exact; cvt.rni recovers them.
+// Data digits and constant chunks are both W bits (fp16-exact): W = 7 for moduli below 2^28,
+// where partial sums stay below 4 * 256 * 127 * 127 < 2^24 for reduction lengths up to 256;
+// W = 8 for moduli below 2^30, below 4 * 64 * 255 * 255 < 2^24 for reduction lengths up to 64
+// (three-factor splits only).  The fp32 accumulation is exact; cvt.rni recovers the sums.
 //
 // GB300 mapping
 //  - A (data digits, K-major) and B (constant, K-major) both arrive by TMA with the 128-byte
@@ -14,15 +16,15 @@
 //    constant matrices of a limb (2 MiB per step at N = 2^16) stay resident in L2 while the
 //    limb's data blocks stream past them.
 //  - Two 256-column TMEM accumulators: the epilogue of one 64-output tile overlaps the MMAs
-//    of the next.  The epilogue merges the 4 chunk sums (sum_o p_o 2^(7o) < 2^46), reduces
+//    of the next.  The epilogue merges the 4 chunk sums (sum_o p_o 2^(W o) < 2^48), reduces
 //    with one Montgomery REDC (2^32 folded into the constants), applies the twiddle or
 //    Hadamard product and writes either the final residues or -- after a first step -- the
-//    7-bit digits of the next step's A operand, already transposed where that step needs it.
+//    W-bit digits of the next step's A operand, already transposed where that step needs it.
 //  - Persistent CTAs (as many as fit at once) walk the work items (limb, data block); the
 //    two accumulators carry across items, so an item's last epilogue overlaps the next
 //    item's MMAs.
-//  - Warp roles: warp 0 TMA producer, warp 1 MMA issuer and TMEM owner, warps 2-9 epilogue
-//    (two per TMEM lane quadrant, splitting the columns).  Every mbarrier wait is bounded.
+//  - Warp roles: warp 0 TMA producer, warp 1 MMA issuer and TMEM owner, warps 2-17 epilogue
+//    (four per TMEM lane quadrant, splitting the columns).  Every mbarrier wait is bounded.
 #include <cuda.h>
 
 #include <algorithm>
@@ -44,7 +46,7 @@ namespace tc2 {
 
 constexpr int BM = 128;                // data rows per CTA (MMA M)
 constexpr int OUTS = 64;               // outputs per tile (the default tile; 32 is the other choice)
-constexpr int KO = 4;                  // 7-bit constant chunks
+constexpr int KO = 4;                  // W-bit constant chunks
 constexpr int BN = OUTS * KO;          // 256 (MMA N)
 constexpr int BK = 64;                 // K elements per stage (128 bytes of fp16)
 constexpr int STAGES = 4;
@@ -101,7 +103,7 @@ struct Args {
     uint32_t logDd, rA, rB, rC, kB, kC, klen, orows;
 };
 
-template <int OUTK, int MUL, int TO>
+template <int OUTK, int MUL, int TO, int W>
 __global__ void __launch_bounds__(THREADS, 1)
     gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bmap, Args a) {
     constexpr int BN = Tile<TO>::BN, OUTS = TO;
@@ -266,8 +268,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                         const uint32_t p1 = __float2uint_rn(__uint_as_float(r[4 * u + 1]));
                         const uint32_t p2 = __float2uint_rn(__uint_as_float(r[4 * u + 2]));
                         const uint32_t p3 = __float2uint_rn(__uint_as_float(r[4 * u + 3]));
-                        const uint64_t z =
-                            (uint64_t)p0 + ((uint64_t)p1 << 7) + ((uint64_t)p2 << 14) + ((uint64_t)p3 << 21);
+                        const uint64_t z = (uint64_t)p0 + ((uint64_t)p1 << W) + ((uint64_t)p2 << (2 * W)) +
+                                           ((uint64_t)p3 << (3 * W));
                         const uint32_t zl = (uint32_t)z, zh = (uint32_t)(z >> 32);
                         uint32_t v = zh + __umulhi(zl * lc.qinv_neg, lc.q) + (zl != 0u);  // z 2^-32 mod q, [0, 2q)
                         const uint32_t out = out0 + u;
@@ -285,7 +287,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                     if constexpr (OUTK == OUT_DIGITS) {
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
-                            const uint2 d = tc::split_digits4(res[u]);
+                            const uint2 d = tc::split_digits4<W>(res[u]);
                             *reinterpret_cast<uint2*>(dgb + (size_t)(out0 + u) * a.rA * (4ull * a.klen)) = d;
                         }
                     } else if constexpr (OUTK == OUT_U32_ROW_DATA) {
@@ -312,6 +314,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 
 // Digits of the first step's A operand where its rows are the data's rows (inverse step 1):
 // 4 elements per thread, coalesced 16-byte loads and 32-byte stores.
+template <int W>
 __global__ void __launch_bounds__(256) digitize_kernel(const uint32_t* __restrict__ in, uint16_t* __restrict__ dig,
                                                        uint32_t R, uint32_t C, size_t mats) {
     const size_t per = (size_t)R * C / 4;  // 4 elements per thread
@@ -319,8 +322,8 @@ __global__ void __launch_bounds__(256) digitize_kernel(const uint32_t* __restric
         const size_t m = t / per, w = t % per;
         const uint4 v = __ldg(reinterpret_cast<const uint4*>(in + m * R * C) + w);
         const uint32_t r = (uint32_t)((w * 4) / C), c0 = (uint32_t)((w * 4) % C);
-        const uint2 d0 = tc::split_digits4(v.x), d1 = tc::split_digits4(v.y);
-        const uint2 d2 = tc::split_digits4(v.z), d3 = tc::split_digits4(v.w);
+        const uint2 d0 = tc::split_digits4<W>(v.x), d1 = tc::split_digits4<W>(v.y);
+        const uint2 d2 = tc::split_digits4<W>(v.z), d3 = tc::split_digits4<W>(v.w);
         uint4* o = reinterpret_cast<uint4*>(dig + m * R * C * 4 + (size_t)r * (4 * C) + 4 * c0);
         o[0] = make_uint4(d0.x, d0.y, d1.x, d1.y);
         o[1] = make_uint4(d2.x, d2.y, d3.x, d3.y);
@@ -348,6 +351,7 @@ __device__ __forceinline__ void load_tile64(const uint32_t* __restrict__ in, uin
 // Column c of the data matrix becomes A row (c mod pr3) pr2 + c div pr3 (pr3 = 1: row c): the
 // three-factor split orders its first step's rows (j2, j3) as (j3, j2) so that the step's
 // epilogue writes its digits lane-contiguously.
+template <int W>
 __global__ void __launch_bounds__(256) digitize_t64_kernel(const uint32_t* __restrict__ in, uint16_t* __restrict__ dig,
                                                            uint32_t R, uint32_t C, size_t mats, uint32_t pr2,
                                                            uint32_t pr3) {
@@ -374,7 +378,7 @@ __global__ void __launch_bounds__(256) digitize_t64_kernel(const uint32_t* __res
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             const uint32_t c = warp + 8 * k;  // this warp's column of the tile
-            const uint2 lo = tc::split_digits4(tile[2 * lane][c]), hi = tc::split_digits4(tile[2 * lane + 1][c]);
+            const uint2 lo = tc::split_digits4<W>(tile[2 * lane][c]), hi = tc::split_digits4<W>(tile[2 * lane + 1][c]);
             // A row of column c0 + c, K = 4 (r0 + 2 lane) .. + 7
             const uint32_t col = c0 + c, arow = (col % pr3) * pr2 + col / pr3;
             *reinterpret_cast<uint4*>(dst + (size_t)arow * (4 * R) + 4 * (r0 + 2 * lane)) =
@@ -404,6 +408,7 @@ uint16_t half_bits_small(uint32_t d) {
 // The inverse runs the mirror with the negated exponents and N^-1 folded into its last step.
 struct Tc2Tables {
     uint32_t nsteps = 0;
+    int W = 7;                        // digit and chunk width: 7 bits (moduli < 2^28) or 8 (< 2^30)
     uint32_t f[3] = {0, 0, 0};
     uint16_t* cst[6] = {};            // fp16 BAT digit matrices: forward steps, then inverse steps
     uint32_t cst_out[6] = {}, cst_v[6] = {};
@@ -423,9 +428,18 @@ int tile_index(uint32_t tile) { return tile >= 64 ? 0 : tile == 32 ? 1 : 2; }
 
 }  // namespace
 
-// The split a parameter set uses: log2 of its factors, from (tc_log2r, tc_log2r2).
+// The split a parameter set uses: log2 of its factors, from (tc_log2r, tc_log2r2).  Moduli of
+// 29 or 30 bits take 8-bit digits, whose fp32 sums stay exact only for reduction lengths up to
+// 64: their default is the three-factor split 64 x 32 x N/2048 (64 x 16 x 16 at N = 2^14).
 void tc2_split(const hefx_params* p, uint32_t f[3], uint32_t* nsteps) {
     const uint32_t logn = p->log2n;
+    if (tc2_wide(p) && !p->tc_log2r2) {
+        f[0] = 64;
+        f[1] = logn >= 15 ? 32 : 16;
+        f[2] = (1u << logn) / (64 * f[1]);
+        *nsteps = 3;
+        return;
+    }
     const uint32_t l1 = p->tc_log2r ? p->tc_log2r : logn / 2;
     if (p->tc_log2r2) {
         f[0] = 1u << l1;
@@ -440,7 +454,7 @@ void tc2_split(const hefx_params* p, uint32_t f[3], uint32_t* nsteps) {
     }
 }
 
-// Offline precompute: BAT digit matrices with 7-bit input digits and 7-bit output chunks,
+// Offline precompute: BAT digit matrices with W-bit input digits and W-bit output chunks,
 // constants times 2^32 (Montgomery), rows (out, chunk) interleaved so that one output's four
 // chunk sums land in four consecutive accumulator columns; Shoup twiddles.
 cudaError_t tc2_prepare(hefx_params* p) {
@@ -448,6 +462,8 @@ cudaError_t tc2_prepare(hefx_params* p) {
     const uint32_t N = p->n, L = p->nlimbs;
     Tc2Tables* t = new Tc2Tables();
     tc2_split(p, t->f, &t->nsteps);
+    t->W = tc2_wide(p) ? 8 : 7;
+    const int W = t->W;
     const uint32_t ns = t->nsteps;
     const uint32_t R = t->f[0], C = N / R;  // step 1 and the rest (C = R2 R3 with three factors)
     const uint32_t R2 = t->f[1], R3 = ns == 3 ? t->f[2] : 1;
@@ -484,10 +500,10 @@ cudaError_t tc2_prepare(hefx_params* p) {
             uint64_t c = mul_mod(w, r32, q);
             for (uint32_t i = 0; i < 4; ++i) {
                 for (int o = 0; o < KO; ++o) {
-                    const uint32_t chunk = (uint32_t)((c >> (7 * o)) & 127u);
+                    const uint32_t chunk = (uint32_t)((c >> (W * o)) & ((1u << W) - 1u));
                     hc[m][(((size_t)l * t->cst_out[m] + out) * KO + o) * K + v * 4 + i] = half_bits_small(chunk);
                 }
-                c = (c << 7) % q;
+                c = (c << W) % q;
             }
         };
         auto shoup2 = [&](uint64_t w) { return make_uint2((uint32_t)w, shoup(w, q)); };
@@ -616,10 +632,10 @@ cudaError_t ensure_workspace(Tc2Tables* t, size_t elems) {
     return e;
 }
 
-template <int OUTK, int MUL, int TO>
+template <int OUTK, int MUL, int TO, int W>
 cudaError_t launch_gemm_t(const CUtensorMap& amap, const CUtensorMap& bmap, const tc2::Args& g, cudaStream_t s) {
     using namespace tc2;
-    auto kern = gemm_kernel<OUTK, MUL, TO>;
+    auto kern = gemm_kernel<OUTK, MUL, TO, W>;
     constexpr size_t SMEM_BYTES = Tile<TO>::SMEM_BYTES;
     static bool attr = false;
     if (!attr) {
@@ -655,12 +671,19 @@ cudaError_t launch_gemm_t(const CUtensorMap& amap, const CUtensorMap& bmap, cons
     return cudaLaunchKernelEx(&cfg, kern, amap, bmap, g);
 }
 
+template <int OUTK, int MUL, int W>
+cudaError_t launch_gemm_w(const CUtensorMap* bmaps, uint32_t tile, const CUtensorMap& amap, const tc2::Args& g,
+                          cudaStream_t s) {
+    if (tile >= 64) return launch_gemm_t<OUTK, MUL, 64, W>(amap, bmaps[0], g, s);
+    if (tile == 32) return launch_gemm_t<OUTK, MUL, 32, W>(amap, bmaps[1], g, s);
+    return launch_gemm_t<OUTK, MUL, 16, W>(amap, bmaps[2], g, s);
+}
+
 template <int OUTK, int MUL>
-cudaError_t launch_gemm(const CUtensorMap* bmaps, uint32_t tile, const CUtensorMap& amap, const tc2::Args& g,
+cudaError_t launch_gemm(const CUtensorMap* bmaps, uint32_t tile, int W, const CUtensorMap& amap, const tc2::Args& g,
                         cudaStream_t s) {
-    if (tile >= 64) return launch_gemm_t<OUTK, MUL, 64>(amap, bmaps[0], g, s);
-    if (tile == 32) return launch_gemm_t<OUTK, MUL, 32>(amap, bmaps[1], g, s);
-    return launch_gemm_t<OUTK, MUL, 16>(amap, bmaps[2], g, s);
+    return W == 8 ? launch_gemm_w<OUTK, MUL, 8>(bmaps, tile, amap, g, s)
+                  : launch_gemm_w<OUTK, MUL, 7>(bmaps, tile, amap, g, s);
 }
 
 int ilog2(uint32_t x) { return 31 - __builtin_clz(x); }
@@ -710,12 +733,13 @@ cudaError_t run_step(const hefx_params* p, const StepSpec& st, const uint16_t* a
         return cudaErrorInvalidValue;
     const uint32_t tile = std::min<uint32_t>(p->tc_tile == 32 ? 32u : 64u, g.OUT);
     const CUtensorMap* b3 = t->bmaps[st.m];
-    if (st.outk == OUT_DIGITS) return launch_gemm<OUT_DIGITS, MUL_TW>(b3, tile, amap, g, s);
-    if (st.outk == OUT_U32_ROW_OUT) return launch_gemm<OUT_U32_ROW_OUT, MUL_NONE>(b3, tile, amap, g, s);
+    const int W = t->W;
+    if (st.outk == OUT_DIGITS) return launch_gemm<OUT_DIGITS, MUL_TW>(b3, tile, W, amap, g, s);
+    if (st.outk == OUT_U32_ROW_OUT) return launch_gemm<OUT_U32_ROW_OUT, MUL_NONE>(b3, tile, W, amap, g, s);
     switch (st.mul) {
-        case MUL_HAD: return launch_gemm<OUT_U32_ROW_DATA, MUL_HAD>(b3, tile, amap, g, s);
-        case MUL_SQUARE: return launch_gemm<OUT_U32_ROW_DATA, MUL_SQUARE>(b3, tile, amap, g, s);
-        default: return launch_gemm<OUT_U32_ROW_DATA, MUL_NONE>(b3, tile, amap, g, s);
+        case MUL_HAD: return launch_gemm<OUT_U32_ROW_DATA, MUL_HAD>(b3, tile, W, amap, g, s);
+        case MUL_SQUARE: return launch_gemm<OUT_U32_ROW_DATA, MUL_SQUARE>(b3, tile, W, amap, g, s);
+        default: return launch_gemm<OUT_U32_ROW_DATA, MUL_NONE>(b3, tile, W, amap, g, s);
     }
 }
 
@@ -730,10 +754,16 @@ cudaError_t digitize(const hefx_params* p, const uint32_t* in, uint16_t* dig, bo
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         // persistent: 8 blocks of 256 threads per SM (16.6 KiB of shared memory each)
-        tc2::digitize_t64_kernel<<<(unsigned)std::min<size_t>(tiles, (size_t)sms * 8), 256, 0, s>>>(in, dig, R, C,
-                                                                                                   mats, pr2, pr3);
-    } else
-        tc2::digitize_kernel<<<grid, 256, 0, s>>>(in, dig, R, C, mats);
+        const unsigned blocks = (unsigned)std::min<size_t>(tiles, (size_t)sms * 8);
+        if (p->tc2->W == 8)
+            tc2::digitize_t64_kernel<8><<<blocks, 256, 0, s>>>(in, dig, R, C, mats, pr2, pr3);
+        else
+            tc2::digitize_t64_kernel<7><<<blocks, 256, 0, s>>>(in, dig, R, C, mats, pr2, pr3);
+    } else if (p->tc2->W == 8) {
+        tc2::digitize_kernel<8><<<grid, 256, 0, s>>>(in, dig, R, C, mats);
+    } else {
+        tc2::digitize_kernel<7><<<grid, 256, 0, s>>>(in, dig, R, C, mats);
+    }
     return cudaGetLastError();
 }
 

@@ -181,9 +181,12 @@ __device__ __forceinline__ uint32_t digits_to_half2(uint32_t d_lo, uint32_t d_hi
     return *reinterpret_cast<uint32_t*>(&h);
 }
 
-// The four 7-bit digits of x < 2^28 as two packed half2 words (digit 0 lowest).
+// The four W-bit digits of x < 2^(4W) as two packed half2 words (digit 0 lowest): W = 7 for
+// moduli below 2^28, W = 8 for moduli below 2^30 (every digit below 2^11, exact in fp16).
+template <int W = 7>
 __device__ __forceinline__ uint2 split_digits4(uint32_t x) {
-    const uint32_t d0 = x & 127u, d1 = (x >> 7) & 127u, d2 = (x >> 14) & 127u, d3 = x >> 21;
+    constexpr uint32_t M = (1u << W) - 1u;
+    const uint32_t d0 = x & M, d1 = (x >> W) & M, d2 = (x >> (2 * W)) & M, d3 = x >> (3 * W);
     return make_uint2(digits_to_half2(d0, d1), digits_to_half2(d2, d3));
 }
 

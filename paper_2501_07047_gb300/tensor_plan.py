@@ -2,8 +2,10 @@
 
 # digit split of the layout-invariant matrix NTT (Sec. IV-A / IV-B) as run by the pipelined
 # tensor kernels: data residues < 2^28 in K_IN digits of 7 bits, constants in K_OUT chunks of
-# 7 bits (partial sums below 2^24, exact in fp32)
+# 7 bits (partial sums below 2^24, exact in fp32); residues of 29-30-bit moduli in digits and
+# chunks of W_WIDE = 8 bits, exact for reduction lengths up to MAX_FACTOR_WIDE
 K_IN, W_IN, K_OUT, W_OUT = 4, 7, 4, 7
+W_WIDE, MAX_FACTOR_WIDE = 8, 64
 
 
 def split(logn: int, log2r: int = 0, log2r2: int = 0):
@@ -23,6 +25,12 @@ def splits(logn: int) -> list:
     two = [(r, 0) for r in (7, 8) if 7 <= logn - r <= 8]
     three = [(a, b) for a in (6, 7, 8) for b in (4, 5, 6, 7, 8) if 4 <= logn - a - b <= 8]
     return two + three
+
+
+def splits_wide(logn: int) -> list:
+    """(log2r, log2r2) of the splits the tensor path accepts for moduli of 29-30 bits: three
+    factors, each at most 64 (4 * 64 * 255 * 255 < 2^24), the first exactly 64."""
+    return [(a, b) for a, b in splits(logn) if b and a == 6 and b <= 6 and logn - a - b <= 6]
 
 
 def tuned_splits(logn: int) -> list:

@@ -105,6 +105,10 @@ def test_tuner_candidates_and_cached_choice(tmp_path, monkeypatch):
     assert tensor_plan.tuned_splits(16) == [(8, 0), (6, 5)]            # 256 x 256 and 64 x 32 x 32
     assert tensor_plan.tuned_splits(14) == [(7, 0), (6, 4)]            # 128 x 128 and 64 x 16 x 16
     assert tensor_plan.splits(13) == [] and tensor_plan.splits(12) == []
+    # 8-bit digits (moduli of 29-30 bits): exact fp32 sums need every factor <= 64
+    assert tensor_plan.splits_wide(16) == [(6, 4), (6, 5), (6, 6)]
+    assert tensor_plan.splits_wide(15) == [(6, 4), (6, 5)] and tensor_plan.splits_wide(14) == [(6, 4)]
+    assert 4 * tensor_plan.MAX_FACTOR_WIDE * 255 * 255 < 2 ** 24 < 4 * 2 * tensor_plan.MAX_FACTOR_WIDE * 255 * 255
     assert autotune.candidates(13) == [("cudacore", 0, 0, 0)]
     assert autotune.candidates(16)[:2] == [("cudacore", 1, 0, 0), ("cudacore", 2, 0, 0)]  # both schedules
     assert autotune.candidates(15)[0] == ("cudacore", 0, 0, 0) and autotune.candidates(15)[1][0] == "tensor"

@@ -343,6 +343,51 @@ def test_tensor_configs_bit_exact(ctx, logn):
 
 # ----------------------------------------------------------------------------- N = 2^17
 
+@pytest.mark.parametrize("logn", [14, 15, 16])
+def test_tensor_30bit_moduli(ctx, logn):
+    """Moduli of 29-30 bits on the tensor path (8-bit digits and chunks): every split it
+    accepts (three factors, each at most 64) with both tile widths gives the oracle's forward
+    and inverse transforms and products; two-factor splits are refused, as is the
+    single-pass no-allocation product."""
+    from paper_2501_07047_gb300 import tensor_plan
+    primes = inputs.special_primes(3)
+    n = 1 << logn
+    p = make_params(ctx, logn, primes)
+    try:
+        a = inputs.residue_tensor(inputs.derive_seed(16, logn, 0), 2, primes, n)
+        b = inputs.residue_tensor(inputs.derive_seed(16, logn, 1), 2, primes, n)
+        # extreme residues: q - 1 everywhere in one limb
+        a[1, 2, :] = primes[2] - 1
+        want_f = oracle.ntt_batch(a, primes)
+        want_m = oracle.polymul_batch(a, b, primes)
+        rnd = inputs.residue_tensor(inputs.derive_seed(17, logn), 1, primes, n)
+        want_i = oracle.ntt_batch(rnd, primes, inverse=True)
+        # the default split of a 30-bit parameter set
+        assert (run_fwd(ctx, p, a, "tensor") == want_f).all()
+        for log2r, log2r2 in tensor_plan.splits_wide(logn):
+            for tile in (64, 32):
+                hefx.hefx_params_set_tensor_config(ctx, p, log2r, tile, log2r2)
+                got = run_fwd(ctx, p, a, "tensor")
+                assert (got == want_f).all(), (log2r, log2r2, tile)
+                assert (run_inv(ctx, p, got, "tensor") == a).all(), (log2r, log2r2, tile)
+                assert (run_inv(ctx, p, rnd, "tensor") == want_i).all(), (log2r, log2r2, tile)
+                da, db, dc = to_dev(a), to_dev(b), empty_dev(a.shape)
+                hefx.hefx_poly_mul(ctx, p, da, db, dc, 2, "tensor")
+                assert (to_host(dc).reshape(a.shape) == want_m).all(), (log2r, log2r2, tile)
+        with pytest.raises(hefx.HefxError) as e:
+            hefx.hefx_params_set_tensor_config(ctx, p, logn // 2, 64, 0)
+        assert e.value.status == hefx.HEFX_EUNSUPPORTED
+        if logn >= 15:
+            with pytest.raises(hefx.HefxError) as e:  # a factor above 64
+                hefx.hefx_params_set_tensor_config(ctx, p, 7, 64, 4)
+            assert e.value.status == hefx.HEFX_EUNSUPPORTED
+        d = to_dev(a)
+        assert hefx.raw_status("hefx_poly_mul_noalloc", ctx, p, d.data_ptr(), d.data_ptr(), d.data_ptr(), 2, None) \
+            == hefx.HEFX_EUNSUPPORTED
+    finally:
+        hefx.hefx_params_destroy(p)
+
+
 @pytest.mark.parametrize("bits", [28, 30])
 def test_n_2_17(ctx, bits):
     """N = 2^17 (primes = 1 mod 2^18) on the CUDA cores: 28-bit moduli take the lazy
