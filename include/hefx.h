@@ -107,9 +107,15 @@ hefx_status hefx_params_set_auto_path(hefx_params* params, hefx_path path);
  *    16 N (R + C)), one more epilogue.
  *  - tile_outputs: outputs per GEMM tile, 64 (256 accumulator columns) or 32 (128); steps with
  *    fewer outputs take a tile of their output count (16 or 32).
+ *  - A parameter set with a modulus of 29 or 30 bits runs the tensor path on 8-bit digits and
+ *    chunks, whose fp32 sums stay exact only for reduction lengths up to 64 (4 * 64 * 255 *
+ *    255 < 2^24): it takes three-factor splits with every factor at most 64 (R1 = 64; its
+ *    default is 64 x 32 x 32 at N = 2^16, 64 x 32 x 16 at 2^15, 64 x 16 x 16 at 2^14); other
+ *    splits give EUNSUPPORTED.
  * Results do not depend on any of these choices.  Changing the split drops the parameter set's
  * pipelined tensor tables (after a device synchronization); the next tensor-path call builds
- * them for the new split.  Errors: EINVAL (no such split or tile), ECUDA.
+ * them for the new split.  Errors: EINVAL (no such split or tile), EUNSUPPORTED (see above),
+ * ECUDA.
  */
 hefx_status hefx_params_set_tensor_config(hefx_params* params, uint32_t log2r, uint32_t log2r2,
                                           uint32_t tile_outputs);
@@ -209,7 +215,9 @@ hefx_status hefx_poly_mul(hefx_ctx* ctx, const hefx_params* params, const uint32
  *    it fully before reading it, so nothing needs clearing).  Calls whose work overlaps on
  *    the GPU (different streams, or different host threads) race on it: serialize them.
  *  - Like hefx_poly_mul, it takes the default (Shoup) NTT reduction only: a parameter set
- *    switched to another reduction gets HEFX_EUNSUPPORTED.
+ *    switched to another reduction gets HEFX_EUNSUPPORTED.  It runs the single-pass tensor
+ *    form, built for moduli below 2^28: a parameter set with a larger modulus gets
+ *    HEFX_EUNSUPPORTED.
  *  - Layout, aliasing (d_c may alias d_a and/or d_b) and errors otherwise as for
  *    hefx_poly_mul.
  */
