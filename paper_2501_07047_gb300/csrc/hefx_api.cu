@@ -949,10 +949,10 @@ hefx_status hefx_params_set_tensor_config(hefx_params* p, uint32_t log2r, uint32
     if (log2r == 0) log2r = logn / 2;
     if (log2r2 == 0) {
         const uint32_t logc = logn >= log2r ? logn - log2r : 0;
-        if (log2r < 7 || log2r > 8 || logc < 7 || logc > 8)
+        if (log2r < 6 || log2r > 8 || logc < 6 || logc > 8)
             return fail(p->ctx, HEFX_EINVAL,
-                        "tensor split 2^%u x 2^%u of N = 2^%u: both factors must be 128 or 256 (128-row data "
-                        "blocks; exact fp32 sums need reduction lengths <= 256)",
+                        "tensor split 2^%u x 2^%u of N = 2^%u: both factors must be 64 .. 256 (the transposing "
+                        "digit split takes 64-wide tiles; exact fp32 sums need reduction lengths <= 256)",
                         log2r, logc, logn);
     } else {
         const int log3 = (int)logn - (int)log2r - (int)log2r2;
@@ -965,10 +965,10 @@ hefx_status hefx_params_set_tensor_config(hefx_params* p, uint32_t log2r, uint32
     }
     if (tile_outputs != 32 && tile_outputs != 64)
         return fail(p->ctx, HEFX_EINVAL, "tile_outputs must be 32 or 64, not %u", tile_outputs);
-    if (tc2_wide(p) && (log2r2 == 0 || log2r > 6 || log2r2 > 6 || (int)logn - (int)log2r - (int)log2r2 > 6))
+    if (tc2_wide(p) && (log2r > 6 || log2r2 > 6 || (int)logn - (int)log2r - (int)log2r2 > 6))
         return fail(p->ctx, HEFX_EUNSUPPORTED,
                     "moduli of 29-30 bits take 8-bit digits, whose fp32 sums are exact for reduction lengths "
-                    "<= 64 only: a three-factor split with every factor <= 64 (64 x 32 x 32 at N = 2^16)");
+                    "<= 64 only: every factor <= 64 (64 x 64 at N = 2^12, 64 x 32 x 32 at N = 2^16)");
     hefx_status st = use_device(p->ctx);
     if (st != HEFX_OK) return st;
     std::lock_guard<std::mutex> g(p->tc_mu);

@@ -338,10 +338,14 @@ bool encode_map_2d(CUtensorMap* map, CUtensorMapDataType dtype, void* base, uint
                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-bool tc_supported(const hefx_params* p) { return p->log2n >= 14 && p->log2n <= 16 && encode_fn(); }
+bool tc_supported(const hefx_params* p) {
+    // 8-bit digits (moduli above 2^28) need every factor <= 64: no split of 2^13 has that
+    return p->log2n >= 12 && p->log2n <= 16 && encode_fn() && !(tc2_wide(p) && p->log2n == 13);
+}
 
 bool tc_narrow(const hefx_params* p) {
-    return tc_supported(p) && p->max_prime < (1u << 28);  // the single-pass form's 6-bit chunks
+    // the single-pass form: N = 2^14 .. 2^16, 6-bit chunks of 28-bit moduli
+    return tc_supported(p) && p->log2n >= 14 && p->max_prime < (1u << 28);
 }
 
 void tc_free(hefx_params* p) {

@@ -118,19 +118,22 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 1);
 
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // work items: (limb, data block of that limb); a data block is a (poly, 128-row block)
-    // pair.  Consecutive items share the limb (and so the L2-resident constant); CTAs walk the
-    // items with a stride.
-    const uint32_t blocks_per_limb = a.batch * (a.DN / BM);
+    // work items: (limb, data block of that limb).  A data block is 128 A rows of one limb: a
+    // 128-row part of one polynomial's DN rows, or (DN < 128) the DN rows of PB = 128 / DN
+    // consecutive polynomials; the digit buffers are limb-major ([limb][poly][DN][K]) so that
+    // those rows are contiguous and share the limb's constant.  Consecutive items share the limb
+    // (and so the L2-resident constant); CTAs walk the items with a stride.
+    const uint32_t PB = a.DN >= BM ? 1u : BM / a.DN;
+    const uint32_t blocks_per_poly = a.DN >= BM ? a.DN / BM : 1u;
+    const uint32_t blocks_per_limb = a.DN >= BM ? a.batch * blocks_per_poly : (a.batch + PB - 1) / PB;
     const uint32_t items = a.L * blocks_per_limb;
     const uint32_t cid = blockIdx.x, nctas = gridDim.x;
     const uint32_t ntiles = a.OUT / OUTS, kstages = a.K / BK;
-    auto item_rows = [&](uint32_t item, uint32_t& limb, uint32_t& pl, uint32_t& drow0) {
+    auto item_rows = [&](uint32_t item, uint32_t& limb, uint32_t& poly0, uint32_t& drow0) {
         limb = item / blocks_per_limb;
         const uint32_t blk = item % blocks_per_limb;
-        const uint32_t poly = blk / (a.DN / BM);
-        drow0 = (blk % (a.DN / BM)) * BM;
-        pl = poly * a.L + limb;
+        poly0 = a.DN >= BM ? blk / blocks_per_poly : blk * PB;
+        drow0 = a.DN >= BM ? (blk % blocks_per_poly) * BM : 0u;
     };
 
     if (threadIdx.x == 0) {
@@ -164,9 +167,9 @@ __global__ void __launch_bounds__(THREADS, 1)
             uint32_t stage = 0, phase = 0;
             bool ok = true;
             for (uint32_t item = cid; item < items && ok; item += nctas) {
-                uint32_t limb, pl, drow0;
-                item_rows(item, limb, pl, drow0);
-                const uint32_t a_row0 = pl * a.DN + drow0;   // A rows: [poly][limb][DN]
+                uint32_t limb, poly0, drow0;
+                item_rows(item, limb, poly0, drow0);
+                const uint32_t a_row0 = (limb * a.batch + poly0) * a.DN + drow0;  // A rows: [limb][poly][DN]
                 const uint32_t b_row0 = limb * a.OUT * KO;  // B rows: [limb][OUT x KO]
                 for (uint32_t nt = 0; nt < ntiles && ok; ++nt)
                     for (uint32_t kc = 0; kc < kstages; ++kc) {
@@ -226,9 +229,14 @@ __global__ void __launch_bounds__(THREADS, 1)
         static_assert(SLICE % 16 == 0, "whole 16-column TMEM reads per warp");
         uint32_t t = 0;
         for (uint32_t item = cid; item < items; item += nctas) {
-            uint32_t limb, pl, drow0;
-            item_rows(item, limb, pl, drow0);
-            const uint32_t drow = drow0 + quad * 32 + lane;  // data row held by this thread
+            uint32_t limb, poly0, drow0;
+            item_rows(item, limb, poly0, drow0);
+            const uint32_t r = quad * 32 + lane;  // A row of the block held by this thread
+            const uint32_t poly = poly0 + (PB > 1 ? r / a.DN : 0u);
+            const uint32_t drow = PB > 1 ? r % a.DN : drow0 + r;  // data row within its polynomial limb
+            const bool live = poly < a.batch;  // a block of several polynomials may run past the batch
+            const uint32_t pl = (live ? poly : poly0) * a.L + limb;      // [poly][limb]: residues
+            const uint32_t lp = limb * a.batch + (live ? poly : poly0);  // [limb][poly]: digits
             const Limb lc = a.limbs[limb];
             const size_t mat = (size_t)pl * a.DN * a.OUT;   // start of this polynomial limb
             // the data row's parts of the twiddle and digit index maps
@@ -240,7 +248,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             uint16_t* dgb = nullptr;
             if constexpr (OUTK == OUT_DIGITS)
                 dgb = a.out_digits +
-                      ((size_t)pl * a.orows + (size_t)dd_lo * a.rB + (size_t)dd_hi * a.rC) * (4ull * a.klen) +
+                      ((size_t)lp * a.orows + (size_t)dd_lo * a.rB + (size_t)dd_hi * a.rC) * (4ull * a.klen) +
                       4ull * ((size_t)dd_lo * a.kB + (size_t)dd_hi * a.kC);
             bool ok = true;
             for (uint32_t nt = 0; nt < ntiles; ++nt, ++t) {
@@ -284,7 +292,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                         }
                         res[u] = csub(v, lc.q);
                     }
-                    if constexpr (OUTK == OUT_DIGITS) {
+                    if (!live) {
+                    } else if constexpr (OUTK == OUT_DIGITS) {
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
                             const uint2 d = tc::split_digits4<W>(res[u]);
@@ -312,19 +321,26 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
 }
 
+// Matrix m = poly L + limb of the [poly][limb] data goes to digit matrix limb batch + poly (the
+// digit buffers are limb-major, see gemm_kernel).
+__device__ __forceinline__ size_t limb_major(size_t m, uint32_t L, uint32_t batch) {
+    return (m % L) * batch + m / L;
+}
+
 // Digits of the first step's A operand where its rows are the data's rows (inverse step 1):
 // 4 elements per thread, coalesced 16-byte loads and 32-byte stores.
 template <int W>
 __global__ void __launch_bounds__(256) digitize_kernel(const uint32_t* __restrict__ in, uint16_t* __restrict__ dig,
-                                                       uint32_t R, uint32_t C, size_t mats) {
+                                                       uint32_t R, uint32_t C, uint32_t L, uint32_t batch) {
     const size_t per = (size_t)R * C / 4;  // 4 elements per thread
+    const size_t mats = (size_t)L * batch;
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < mats * per; t += (size_t)gridDim.x * blockDim.x) {
         const size_t m = t / per, w = t % per;
         const uint4 v = __ldg(reinterpret_cast<const uint4*>(in + m * R * C) + w);
         const uint32_t r = (uint32_t)((w * 4) / C), c0 = (uint32_t)((w * 4) % C);
         const uint2 d0 = tc::split_digits4<W>(v.x), d1 = tc::split_digits4<W>(v.y);
         const uint2 d2 = tc::split_digits4<W>(v.z), d3 = tc::split_digits4<W>(v.w);
-        uint4* o = reinterpret_cast<uint4*>(dig + m * R * C * 4 + (size_t)r * (4 * C) + 4 * c0);
+        uint4* o = reinterpret_cast<uint4*>(dig + limb_major(m, L, batch) * R * C * 4 + (size_t)r * (4 * C) + 4 * c0);
         o[0] = make_uint4(d0.x, d0.y, d1.x, d1.y);
         o[1] = make_uint4(d2.x, d2.y, d3.x, d3.y);
     }
@@ -353,10 +369,11 @@ __device__ __forceinline__ void load_tile64(const uint32_t* __restrict__ in, uin
 // epilogue writes its digits lane-contiguously.
 template <int W>
 __global__ void __launch_bounds__(256) digitize_t64_kernel(const uint32_t* __restrict__ in, uint16_t* __restrict__ dig,
-                                                           uint32_t R, uint32_t C, size_t mats, uint32_t pr2,
-                                                           uint32_t pr3) {
+                                                           uint32_t R, uint32_t C, uint32_t L, uint32_t batch,
+                                                           uint32_t pr2, uint32_t pr3) {
     __shared__ uint32_t tile[64][65];
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const size_t mats = (size_t)L * batch;
     const size_t tiles_per = (size_t)(R / 64) * (C / 64), total = mats * tiles_per;
     size_t t = blockIdx.x;
     uint4 v[4];
@@ -374,7 +391,7 @@ __global__ void __launch_bounds__(256) digitize_t64_kernel(const uint32_t* __res
         if (t + gridDim.x < total) load_tile64(in, R, C, tiles_per, t + gridDim.x, v);  // in flight during the stores
         const size_t m = t / tiles_per, w = t % tiles_per;
         const uint32_t r0 = (uint32_t)(w / (C / 64)) * 64, c0 = (uint32_t)(w % (C / 64)) * 64;
-        uint16_t* dst = dig + m * R * C * 4;
+        uint16_t* dst = dig + limb_major(m, L, batch) * R * C * 4;
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             const uint32_t c = warp + 8 * k;  // this warp's column of the tile
@@ -430,9 +447,16 @@ int tile_index(uint32_t tile) { return tile >= 64 ? 0 : tile == 32 ? 1 : 2; }
 
 // The split a parameter set uses: log2 of its factors, from (tc_log2r, tc_log2r2).  Moduli of
 // 29 or 30 bits take 8-bit digits, whose fp32 sums stay exact only for reduction lengths up to
-// 64: their default is the three-factor split 64 x 32 x N/2048 (64 x 16 x 16 at N = 2^14).
+// 64: their default is 64 x 64 at N = 2^12 and the three-factor split 64 x 32 x N/2048 (64 x 16
+// x 16 at N = 2^14) from 2^14 on (N = 2^13 has no such split).
 void tc2_split(const hefx_params* p, uint32_t f[3], uint32_t* nsteps) {
     const uint32_t logn = p->log2n;
+    if (tc2_wide(p) && !p->tc_log2r2 && logn == 12) {
+        f[0] = f[1] = 64;
+        f[2] = 0;
+        *nsteps = 2;
+        return;
+    }
     if (tc2_wide(p) && !p->tc_log2r2) {
         f[0] = 64;
         f[1] = logn >= 15 ? 32 : 16;
@@ -645,7 +669,8 @@ cudaError_t launch_gemm_t(const CUtensorMap& amap, const CUtensorMap& bmap, cons
     }
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
-    const uint32_t items = g.L * g.batch * (g.DN / BM);
+    const uint32_t pb = g.DN >= BM ? 1u : BM / g.DN;  // as in the kernel
+    const uint32_t items = g.L * (g.DN >= BM ? g.batch * (g.DN / BM) : (g.batch + pb - 1) / pb);
     // persistent: as many CTAs as can be resident at once (one per SM: the pipeline's shared
     // memory), cached per device
     static int max_ctas[64] = {};
@@ -755,14 +780,15 @@ cudaError_t digitize(const hefx_params* p, const uint32_t* in, uint16_t* dig, bo
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         // persistent: 8 blocks of 256 threads per SM (16.6 KiB of shared memory each)
         const unsigned blocks = (unsigned)std::min<size_t>(tiles, (size_t)sms * 8);
+        const uint32_t L = p->nlimbs, B = (uint32_t)batch;
         if (p->tc2->W == 8)
-            tc2::digitize_t64_kernel<8><<<blocks, 256, 0, s>>>(in, dig, R, C, mats, pr2, pr3);
+            tc2::digitize_t64_kernel<8><<<blocks, 256, 0, s>>>(in, dig, R, C, L, B, pr2, pr3);
         else
-            tc2::digitize_t64_kernel<7><<<blocks, 256, 0, s>>>(in, dig, R, C, mats, pr2, pr3);
+            tc2::digitize_t64_kernel<7><<<blocks, 256, 0, s>>>(in, dig, R, C, L, B, pr2, pr3);
     } else if (p->tc2->W == 8) {
-        tc2::digitize_kernel<8><<<grid, 256, 0, s>>>(in, dig, R, C, mats);
+        tc2::digitize_kernel<8><<<grid, 256, 0, s>>>(in, dig, R, C, p->nlimbs, (uint32_t)batch);
     } else {
-        tc2::digitize_kernel<7><<<grid, 256, 0, s>>>(in, dig, R, C, mats);
+        tc2::digitize_kernel<7><<<grid, 256, 0, s>>>(in, dig, R, C, p->nlimbs, (uint32_t)batch);
     }
     return cudaGetLastError();
 }

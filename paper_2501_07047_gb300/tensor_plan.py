@@ -19,18 +19,19 @@ def split(logn: int, log2r: int = 0, log2r2: int = 0):
 
 def splits(logn: int) -> list:
     """(log2r, log2r2) of every split the tensor path accepts at N = 2^logn.
-    Two factors: both 128 or 256 (128-row data blocks; exact fp32 sums of 7-bit digit products
-    need reduction lengths of at most 256: 4 * 256 * 127 * 127 < 2^24).  Three factors: the
-    first 64 .. 256 (64-wide transposing digit split), the others 16 .. 256."""
-    two = [(r, 0) for r in (7, 8) if 7 <= logn - r <= 8]
+    Two factors: both 64 .. 256 (64-wide transposing digit split; exact fp32 sums of 7-bit
+    digit products need reduction lengths of at most 256: 4 * 256 * 127 * 127 < 2^24; a step
+    with 64 data rows per limb packs two polynomials into one 128-row block).  Three factors:
+    the first 64 .. 256, the others 16 .. 256."""
+    two = [(r, 0) for r in (6, 7, 8) if 6 <= logn - r <= 8]
     three = [(a, b) for a in (6, 7, 8) for b in (4, 5, 6, 7, 8) if 4 <= logn - a - b <= 8]
     return two + three
 
 
 def splits_wide(logn: int) -> list:
-    """(log2r, log2r2) of the splits the tensor path accepts for moduli of 29-30 bits: three
-    factors, each at most 64 (4 * 64 * 255 * 255 < 2^24), the first exactly 64."""
-    return [(a, b) for a, b in splits(logn) if b and a == 6 and b <= 6 and logn - a - b <= 6]
+    """(log2r, log2r2) of the splits the tensor path accepts for moduli of 29-30 bits: every
+    factor at most 64 (4 * 64 * 255 * 255 < 2^24), the first exactly 64."""
+    return [(a, b) for a, b in splits(logn) if a == 6 and b <= 6 and logn - a - b <= 6]
 
 
 def tuned_splits(logn: int) -> list:

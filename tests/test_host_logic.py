@@ -103,23 +103,25 @@ def test_tuner_candidates_and_cached_choice(tmp_path, monkeypatch):
     assert [s for s in tensor_plan.splits(15) if not s[1]] == [(7, 0), (8, 0)]
     assert [s for s in tensor_plan.splits(16) if not s[1]] == [(8, 0)]
     assert tensor_plan.tuned_splits(16) == [(8, 0), (6, 5)]            # 256 x 256 and 64 x 32 x 32
-    assert tensor_plan.tuned_splits(14) == [(7, 0), (6, 4)]            # 128 x 128 and 64 x 16 x 16
-    assert tensor_plan.splits(13) == [] and tensor_plan.splits(12) == []
+    assert tensor_plan.tuned_splits(14) == [(6, 0), (7, 0), (8, 0), (6, 4)]  # 64 x 256 .. 256 x 64, 64 x 16 x 16
+    assert tensor_plan.splits(13) == [(6, 0), (7, 0)] and tensor_plan.splits(12) == [(6, 0)]
+    assert tensor_plan.splits(11) == []
     # 8-bit digits (moduli of 29-30 bits): exact fp32 sums need every factor <= 64
     assert tensor_plan.splits_wide(16) == [(6, 4), (6, 5), (6, 6)]
     assert tensor_plan.splits_wide(15) == [(6, 4), (6, 5)] and tensor_plan.splits_wide(14) == [(6, 4)]
+    assert tensor_plan.splits_wide(13) == [] and tensor_plan.splits_wide(12) == [(6, 0)]
     assert 4 * tensor_plan.MAX_FACTOR_WIDE * 255 * 255 < 2 ** 24 < 4 * 2 * tensor_plan.MAX_FACTOR_WIDE * 255 * 255
-    assert autotune.candidates(13) == [("cudacore", 0, 0, 0)]
+    assert autotune.candidates(11) == [("cudacore", 0, 0, 0)]
     assert autotune.candidates(16)[:2] == [("cudacore", 1, 0, 0), ("cudacore", 2, 0, 0)]  # both schedules
     assert autotune.candidates(15)[0] == ("cudacore", 0, 0, 0) and autotune.candidates(15)[1][0] == "tensor"
-    for logn in (14, 15, 16):
+    for logn in (12, 13, 14, 15, 16):
         for log2r, log2r2 in tensor_plan.splits(logn):  # every split multiplies out to N within bounds
             f = tensor_plan.split(logn, log2r, log2r2)
             assert int(np.prod(f)) == 1 << logn
             if log2r2:
                 assert 64 <= f[0] <= 256 and all(16 <= x <= 256 for x in f[1:])
             else:
-                assert all(x in (128, 256) for x in f)
+                assert all(x in (64, 128, 256) for x in f)
         for cand in autotune.candidates(logn)[2 if logn == 16 else 1:]:
             assert cand[0] == "tensor" and cand[3] in autotune.TILES
             assert autotune.parse(autotune.key_of(cand)) == cand

@@ -309,7 +309,7 @@ def test_autotune_sets_auto_path(ctx, tmp_path, monkeypatch, logn):
         hefx.hefx_params_destroy(p)
 
 
-@pytest.mark.parametrize("logn", [14, 15, 16])
+@pytest.mark.parametrize("logn", [12, 13, 14, 15, 16])
 def test_tensor_configs_bit_exact(ctx, logn):
     """Every tensor-path split (two factors, and every three-factor split) with both tile widths
     gives the oracle's transforms and products; invalid splits and tiles are refused."""
@@ -343,12 +343,13 @@ def test_tensor_configs_bit_exact(ctx, logn):
 
 # ----------------------------------------------------------------------------- N = 2^17
 
-@pytest.mark.parametrize("logn", [14, 15, 16])
+@pytest.mark.parametrize("logn", [12, 14, 15, 16])
 def test_tensor_30bit_moduli(ctx, logn):
     """Moduli of 29-30 bits on the tensor path (8-bit digits and chunks): every split it
-    accepts (three factors, each at most 64) with both tile widths gives the oracle's forward
-    and inverse transforms and products; two-factor splits are refused, as is the
-    single-pass no-allocation product."""
+    accepts (every factor at most 64: 64 x 64 at 2^12, three factors above) with both tile
+    widths gives the oracle's forward and inverse transforms and products; splits with a
+    larger factor are refused, as is the single-pass no-allocation product; N = 2^13 (no such
+    split) stays on the CUDA cores."""
     from paper_2501_07047_gb300 import tensor_plan
     primes = inputs.special_primes(3)
     n = 1 << logn
@@ -374,9 +375,10 @@ def test_tensor_30bit_moduli(ctx, logn):
                 da, db, dc = to_dev(a), to_dev(b), empty_dev(a.shape)
                 hefx.hefx_poly_mul(ctx, p, da, db, dc, 2, "tensor")
                 assert (to_host(dc).reshape(a.shape) == want_m).all(), (log2r, log2r2, tile)
-        with pytest.raises(hefx.HefxError) as e:
-            hefx.hefx_params_set_tensor_config(ctx, p, logn // 2, 64, 0)
-        assert e.value.status == hefx.HEFX_EUNSUPPORTED
+        if logn >= 14:
+            with pytest.raises(hefx.HefxError) as e:
+                hefx.hefx_params_set_tensor_config(ctx, p, logn // 2, 64, 0)
+            assert e.value.status == hefx.HEFX_EUNSUPPORTED
         if logn >= 15:
             with pytest.raises(hefx.HefxError) as e:  # a factor above 64
                 hefx.hefx_params_set_tensor_config(ctx, p, 7, 64, 4)
@@ -386,6 +388,11 @@ def test_tensor_30bit_moduli(ctx, logn):
             == hefx.HEFX_EUNSUPPORTED
     finally:
         hefx.hefx_params_destroy(p)
+    p13 = make_params(ctx, 13, primes)
+    try:
+        assert not supported(ctx, p13, "tensor", 1, 3, 1 << 13)
+    finally:
+        hefx.hefx_params_destroy(p13)
 
 
 @pytest.mark.parametrize("bits", [28, 30])
