@@ -430,7 +430,7 @@ def run_gpu(args):
     torch.cuda.empty_cache()
     if not args.no_extras and world == 1:
         runs = {"bconv_config3": bench_bconv, "batch_config4": bench_batch, "he_mult": bench_he_mult,
-                "reduction_ablation": bench_reduction_ablation}
+                "reduction_ablation": bench_reduction_ablation, "paper_ntt_table": bench_paper_ntt_table}
         chosen = [k for k in runs if args.extras is None or k in args.extras.split(",")]
         line["extra"] = {k: runs[k](ctx, args) for k in chosen}
         if not args.no_serve and (args.extras is None or "serving_config5" in args.extras.split(",")):
@@ -518,6 +518,43 @@ def bench_bconv(ctx, args):
         hefx.hefx_bconv_plan_destroy(plan2)
     out["paper_shapes_n65536"] = shapes
     out["paper_context_us"] = "TPU v6e one tensor core, BAT: 12->28 135.91, 12->36 147.28, 16->40 65.77, 24->56 94.67"
+    return out
+
+
+def bench_paper_ntt_table(ctx, args):
+    """The shapes of the paper's NTT-throughput table (Sec. V-B): Sets A / B / C, N = 2^12 /
+    2^13 / 2^14 with L = 4 / 8 / 15 limbs of 28-bit primes, forward NTTs of a batch of
+    polynomials (the paper's batches for one TPU v6e tensor core, 32 / 16 / 16, and batches that
+    fill the GPU), every path that is built; thousands of polynomial NTTs (all L limbs) and of
+    limb-NTTs per second."""
+    import torch
+    from paper_2501_07047_gb300 import hefx, inputs
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    s = torch.cuda.current_stream()
+    out = {"paper_context_KNTT_s": {"A": {"TPU v6e-8": 14668, "TPU v4-4": 1284, "WarpDrive A100": 12181},
+                                    "B": {"TPU v6e-8": 3850, "TPU v4-4": 323, "WarpDrive A100": 4675},
+                                    "C": {"TPU v6e-8": 793, "TPU v4-4": 75, "WarpDrive A100": 2088}}}
+    for name, logn, Lset, pbatch in (("A", 12, 4, 32), ("B", 13, 8, 16), ("C", 14, 15, 16)):
+        primes = inputs.source_primes(Lset)
+        params = hefx.hefx_params_create(ctx, logn, primes)
+        res = {"N": 1 << logn, "L": Lset}
+        for batch in (pbatch, 16 * pbatch, 64 * pbatch):
+            host = inputs.residue_tensor(inputs.derive_seed(6, logn, batch), batch, primes, 1 << logn)
+            d0 = torch.from_numpy(host.view(np.int32).copy()).cuda()
+            for path in ("cudacore", "tensor"):
+                d = d0.clone()
+                if hefx.raw_status("hefx_ntt_fwd", ctx, params, d.data_ptr(), 0, hefx.PATHS[path], s.cuda_stream) != 0:
+                    continue
+                hefx.hefx_ntt_fwd(ctx, params, d, batch, path, s)
+                hefx.hefx_ntt_inv(ctx, params, d, batch, path, s)
+                torch.cuda.synchronize()
+                assert torch.equal(d, d0), f"paper table {name} {path}: round trip mismatch"
+                ms = _events_time(lambda: hefx.hefx_ntt_fwd(ctx, params, d, batch, path, s), 20, flush, s)
+                res[f"{path}_batch{batch}"] = {"us": round(ms * 1e3, 2),
+                                               "KNTT_s_polys": round(batch / (ms / 1e3) / 1e3, 1),
+                                               "K_limb_NTT_s": round(batch * Lset / (ms / 1e3) / 1e3, 1)}
+        hefx.hefx_params_destroy(params)
+        out[name] = res
     return out
 
 

@@ -25,7 +25,8 @@
  *    and releases them in the matching *_destroy call.
  *  - Moduli: primes q with q = 1 (mod 2N) and 2^3 < q < 2^30 (the lazy butterflies keep
  *    values below 4q < 2^32).  N = 2^log2n with 3 <= log2n <= 17 (the tensor path covers
- *    14 <= log2n <= 16; N = 2^17 needs q = 1 mod 2^18 and runs on the CUDA cores).
+ *    12 <= log2n <= 16, with moduli above 2^28 all of them but 2^13; N = 2^17 needs
+ *    q = 1 mod 2^18 and runs on the CUDA cores).
  *  - Paths: HEFX_PATH_CUDACORE is the radix-2 Cooley-Tukey / Gentleman-Sande transform on
  *    the CUDA cores (App. A, "Radix-2 Cooley-Tukey NTT").  HEFX_PATH_TENSOR is the
  *    layout-invariant matrix NTT of Sec. IV-B with its modular matrix products split into
@@ -97,9 +98,11 @@ hefx_status hefx_params_set_auto_path(hefx_params* params, hefx_path path);
  * Tensor-path configuration of a parameter set, for the autotuner (Sec. V-A sweeps the
  * (R, C) split of each operator; deeper splits and the GEMM tile are this library's own):
  *  - log2r2 == 0: the matrix NTT's split N = R x C with R = 2^log2r (0: R = 2^floor(log2n /
- *    2)); both R and C must be 128 or 256: the GEMMs take 128-row data blocks, and the fp32
- *    accumulation of 7-bit digit products stays exact only for reduction lengths up to 256.
- *    So N = 2^15 has two such splits, 2^14 and 2^16 one each.
+ *    2)); both R and C must be 64 .. 256: the transposing digit split works on 64-wide tiles,
+ *    and the fp32 accumulation of 7-bit digit products stays exact only for reduction lengths
+ *    up to 256 (a step with 64 data rows per limb packs two polynomials into one of the GEMM's
+ *    128-row blocks).  So N = 2^12 has one such split, 2^13 two, 2^14 three, 2^15 two, 2^16
+ *    one.
  *  - log2r2 > 0: three factors N = R1 x R2 x R3, R1 = 2^log2r (64 .. 256: the transposing
  *    digit split works on 64-wide tiles), R2 = 2^log2r2 and R3 = N / (R1 R2) (16 .. 256): step
  *    1 over R1 as before, then the remaining cyclic transform of each row as two digit GEMMs
@@ -109,9 +112,9 @@ hefx_status hefx_params_set_auto_path(hefx_params* params, hefx_path path);
  *    fewer outputs take a tile of their output count (16 or 32).
  *  - A parameter set with a modulus of 29 or 30 bits runs the tensor path on 8-bit digits and
  *    chunks, whose fp32 sums stay exact only for reduction lengths up to 64 (4 * 64 * 255 *
- *    255 < 2^24): it takes three-factor splits with every factor at most 64 (R1 = 64; its
- *    default is 64 x 32 x 32 at N = 2^16, 64 x 32 x 16 at 2^15, 64 x 16 x 16 at 2^14); other
- *    splits give EUNSUPPORTED.
+ *    255 < 2^24): it takes splits with every factor at most 64 (R1 = 64; its default is 64 x 64
+ *    at N = 2^12, 64 x 32 x 32 at 2^16, 64 x 32 x 16 at 2^15, 64 x 16 x 16 at 2^14; 2^13 has
+ *    none and stays on the CUDA cores); other splits give EUNSUPPORTED.
  * Results do not depend on any of these choices.  Changing the split drops the parameter set's
  * pipelined tensor tables (after a device synchronization); the next tensor-path call builds
  * them for the new split.  Errors: EINVAL (no such split or tile), EUNSUPPORTED (see above),
