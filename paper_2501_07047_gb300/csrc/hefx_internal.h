@@ -188,12 +188,11 @@ cudaError_t launch_pdl(void (*kern)(Params...), dim3 grid, dim3 block, size_t sm
 // limb i and the last limb of the same coefficient-form polynomial and rescales on the way in.
 enum NttMode { MODE_FWD = 0, MODE_INV = 1, MODE_FWD_HAD_INV = 2, MODE_HAD_INV = 3, MODE_RS_FWD = 4 };
 
-// Two-pass CUDA-core transform of contiguous N = 2^16 rows (forward or inverse; in may equal
-// out); row0 is the index of in's first row in the [batch][L] layout (it fixes the rows'
-// limbs).  cudaErrorNotSupported where ntt_cc_2p_supported is false.
+// Two-pass CUDA-core transform of contiguous N = 2^16 rows [batch][L][N] (forward or inverse;
+// in may equal out).  cudaErrorNotSupported where ntt_cc_2p_supported is false.
 bool ntt_cc_2p_supported(const hefx_params* p, NttMode mode);
 cudaError_t launch_ntt_cc_2p(const hefx_params* p, NttMode mode, const uint32_t* in, uint32_t* out, size_t rows,
-                             cudaStream_t stream, size_t row0 = 0);
+                             cudaStream_t stream);
 cudaError_t launch_ntt_cc(const hefx_params* p, NttMode mode, const uint32_t* in, const uint32_t* had, uint32_t* out,
                           size_t rows, cudaStream_t stream);
 // Elementwise products of the HE-Mult request (elementwise.cu).

@@ -47,7 +47,6 @@ struct Args2 {
     const uint2* tw;  // [L][N]: the direction's table in the two-pass layout
     const LimbConst* lc;
     uint32_t L;
-    uint32_t row0;  // index of the launch's first row in the [batch][L] layout (its limb is row0 mod L)
 };
 
 // Shared layout of a 256 x 16 column tile: element (r, c) at word 32 (r >> 1) + 16 h + c with
@@ -112,7 +111,7 @@ __global__ void __launch_bounds__(THREADS, HEFX_2P_MINB) fwd_cols_kernel(const A
     griddep_wait();
     const uint32_t row = blockIdx.x / TASKS_PER_ROW;
     const uint32_t c0 = (blockIdx.x % TASKS_PER_ROW) * 16;
-    const uint32_t limb = (a.row0 + row) % a.L;
+    const uint32_t limb = row % a.L;
     const LimbConst& lc = a.lc[limb];
     const uint2* tw = a.tw + (size_t)limb * N;
     const int c = threadIdx.x & 15, t = threadIdx.x >> 4;
@@ -146,7 +145,7 @@ __global__ void __launch_bounds__(THREADS, HEFX_2P_MINB) fwd_rows_kernel(const A
     __shared__ __align__(16) uint32_t sm[16 * 256];
     griddep_wait();
     const uint32_t row = blockIdx.x / TASKS_PER_ROW;
-    const uint32_t limb = (a.row0 + row) % a.L;
+    const uint32_t limb = row % a.L;
     const LimbConst& lc = a.lc[limb];
     const uint2* tw = a.tw + (size_t)limb * N;
     const int bl = threadIdx.x >> 4, i = threadIdx.x & 15;
@@ -187,7 +186,7 @@ __global__ void __launch_bounds__(THREADS, HEFX_2P_MINB) inv_rows_kernel(const A
     __shared__ __align__(16) uint32_t sm[16 * 256];
     griddep_wait();
     const uint32_t row = blockIdx.x / TASKS_PER_ROW;
-    const uint32_t limb = (a.row0 + row) % a.L;
+    const uint32_t limb = row % a.L;
     const LimbConst& lc = a.lc[limb];
     const uint2* tw = a.tw + (size_t)limb * N;
     const int bl = threadIdx.x >> 4, i = threadIdx.x & 15;
@@ -229,7 +228,7 @@ __global__ void __launch_bounds__(THREADS, HEFX_2P_MINB) inv_cols_kernel(const A
     griddep_wait();
     const uint32_t row = blockIdx.x / TASKS_PER_ROW;
     const uint32_t c0 = (blockIdx.x % TASKS_PER_ROW) * 16;
-    const uint32_t limb = (a.row0 + row) % a.L;
+    const uint32_t limb = row % a.L;
     const LimbConst& lc = a.lc[limb];
     const uint2* tw = a.tw + (size_t)limb * N;
     const int c = threadIdx.x & 15, t = threadIdx.x >> 4;
@@ -296,13 +295,12 @@ bool ntt_cc_2p_supported(const hefx_params* p, NttMode mode) {
 }
 
 cudaError_t launch_ntt_cc_2p(const hefx_params* p, NttMode mode, const uint32_t* in, uint32_t* out, size_t rows,
-                             cudaStream_t stream, size_t row0) {
+                             cudaStream_t stream) {
     if (!ntt_cc_2p_supported(p, mode)) return cudaErrorNotSupported;
     if (rows == 0) return cudaSuccess;
     if (rows > (1u << 26)) return cudaErrorNotSupported;  // grid size stays in 32 bits
-    const uint32_t r0 = (uint32_t)(row0 % p->nlimbs);     // only the limb phase matters
-    cc2::Args2 fa = {in, out, p->d_tw2_fwd, p->d_lc, p->nlimbs, r0};
-    cc2::Args2 ia = {in, out, p->d_tw2_inv, p->d_lc, p->nlimbs, r0};
+    cc2::Args2 fa = {in, out, p->d_tw2_fwd, p->d_lc, p->nlimbs};
+    cc2::Args2 ia = {in, out, p->d_tw2_inv, p->d_lc, p->nlimbs};
     const bool lazy = p->max_prime < (1u << 28);
     return lazy ? cc2::launch_f<2>(mode, fa, ia, rows, stream) : cc2::launch_f<0>(mode, fa, ia, rows, stream);
 }
