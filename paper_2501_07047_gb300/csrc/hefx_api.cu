@@ -317,6 +317,9 @@ hefx_status hefx_params_create(hefx_ctx* ctx, uint32_t log2n, const uint32_t* pr
         c.ninvRw_sh = shoup(vals[3], q);
         c.r2 = (uint32_t)mul_mod(r32, r32, q);
         c.one_sh = shoup(1, q);
+        c.q2 = (uint32_t)(2 * q);
+        c.q4 = (uint32_t)(4 * q);
+        c.q8 = (uint32_t)(8 * q);  // wraps for q >= 2^29: used only where q < 2^28 (lazy ranges)
         const uint64_t mu = (uint64_t)((((unsigned __int128)1) << 64) / q);
         c.bar_lo = (uint32_t)mu;
         c.bar_hi = (uint32_t)(mu >> 32);

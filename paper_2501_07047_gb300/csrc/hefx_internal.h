@@ -27,8 +27,13 @@ struct LimbConst {
     uint32_t one_sh;              // floor(2^32 / q), Shoup companion of 1: any x < 2^32 -> [0, 2q)
     uint32_t rs_inv, rs_inv_sh;   // q_{L-1}^-1 mod q (Rescale by the set's last prime) and companion
     uint32_t bar_lo, bar_hi;      // floor(2^64 / q) (Barrett reduction variant)
+    // 2q, 4q, 8q, read from memory by the NTT butterflies (the lazy offsets X - Y + c q): as
+    // loaded values they stay in registers and each offset add is one three-input add,
+    // where a multiple of q the compiler derives itself is recomputed with a shift-add
+    uint32_t q2, q4, q8;
+    uint32_t pad_[13];
 };
-static_assert(sizeof(LimbConst) == 64, "LimbConst is one 64-byte line");
+static_assert(sizeof(LimbConst) == 128, "LimbConst is one 128-byte line");
 
 // Number of stages in the CUDA-core NTT's smallest-stride register pass for N = 2^log2n.
 // The twiddle entries of those stages are stored permuted (see hefx_params_create) so that

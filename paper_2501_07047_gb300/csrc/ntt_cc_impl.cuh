@@ -86,6 +86,16 @@ __device__ __forceinline__ int swz_elem(int j0, int k) {
 #ifndef HEFX_CC_SPLIT_MINB
 #define HEFX_CC_SPLIT_MINB 5
 #endif
+// log2 of the sub-transforms a thread of a one-row CTA runs together in a strided register
+// pass (0: one at a time), and the kernel modes (bit 1 << MODE) that do so: measured faster
+// for the transforms alone, slower for the fused product (NTT, Hadamard and INTT in one
+// kernel, whose registers it crowds).
+#ifndef HEFX_CC_LOGPW
+#define HEFX_CC_LOGPW 1
+#endif
+#ifndef HEFX_CC_WIDE_MODES
+#define HEFX_CC_WIDE_MODES 0x1b
+#endif
 
 // F & 16 selects the configuration of the fused batch kernel (every ring degree in CTAs of
 // 128 threads and 2^13 elements, clusters of 8: one row of 2^16, two of 2^15, four of 2^14, or
@@ -350,6 +360,11 @@ __device__ __forceinline__ uint32_t twmul(uint32_t x, uint2 w, const LimbConst& 
     }
 }
 
+// c q for the lazy inverse offsets (c = 2, 4 or 8), from the limb's constants.
+__device__ __forceinline__ uint32_t q_multiple(const LimbConst& lc, int c) {
+    return c == 2 ? lc.q2 : c == 4 ? lc.q4 : c == 8 ? lc.q8 : (uint32_t)c * lc.q;
+}
+
 // R forward (Cooley-Tukey) stages s0 .. s0+R-1 on registers; stage s pairs j, j + N/2^(s+1)
 // and uses twiddle psi^brv(2^s + G) for group G (one load per group, reused by its
 // butterflies).  Without F & 2 every butterfly keeps Harvey's [0, 4q) range (q < 2^30).
@@ -358,7 +373,7 @@ __device__ __forceinline__ void fwd_stages(uint32_t (&x)[1 << R], uint32_t g0, c
     // the smallest-stride pass reads the group-major part of the table
     constexpr bool PERM = (s0 + R == LOGN);
     constexpr bool LAZY = (F & 2) != 0;
-    const uint32_t q = lc.q, two_q = 2 * q;
+    const uint32_t q = lc.q, two_q = lc.q2;
 #pragma unroll
     for (int v = 0; v < R; ++v) {
         const int half = 1 << (R - 1 - v);
@@ -389,14 +404,14 @@ __device__ __forceinline__ void inv_stages(uint32_t (&x)[1 << R], uint32_t gbase
     constexpr int N = 1 << LOGN;
     constexpr bool PERM = (e0 == 0);  // the smallest-stride pass reads the group-major table part
     constexpr bool LAZY = (F & 2) != 0;
-    const uint32_t q = lc.q, two_q = 2 * q;
+    const uint32_t q = lc.q, two_q = lc.q2;
     const uint32_t J = (gbase >> R) + (uint32_t)j_hi;  // global index of the sub-transform (e0 == 0)
 #pragma unroll
     for (int v = 0; v < R; ++v) {
         const int e = e0 + v;
         const int h = 1 << v;
         // X - Y + c q >= 0 for Y below c q; the sum is reduced where its bound passes 8q
-        const uint32_t cq = LAZY ? (uint32_t)inv_bound_in(e) * q : two_q;
+        const uint32_t cq = LAZY ? q_multiple(lc, inv_bound_in(e)) : two_q;
         const bool red = !LAZY || 2 * inv_bound_in(e) > 8;
         if (SCALE && e == LOGN - 1) {
             const uint32_t s = SCALE == 1 ? lc.ninv : lc.ninvR, ssh = SCALE == 1 ? lc.ninv_sh : lc.ninvR_sh;
@@ -446,7 +461,7 @@ template <int R, int LOGN, int s0, int F>
 __device__ __forceinline__ void fwd_stages_w(uint32_t (&x)[1 << R], const uint2 (&w)[(1 << R) - 1],
                                              const LimbConst& lc) {
     constexpr bool LAZY = (F & 2) != 0;
-    const uint32_t q = lc.q, two_q = 2 * q;
+    const uint32_t q = lc.q, two_q = lc.q2;
 #pragma unroll
     for (int v = 0; v < R; ++v) {
         const int half = 1 << (R - 1 - v);
@@ -490,12 +505,12 @@ template <int R, int LOGN, int SCALE, int e0, int F>
 __device__ __forceinline__ void inv_stages_w(uint32_t (&x)[1 << R], const uint2 (&w)[(1 << R) - 1],
                                              const LimbConst& lc) {
     constexpr bool LAZY = (F & 2) != 0;
-    const uint32_t q = lc.q, two_q = 2 * q;
+    const uint32_t q = lc.q, two_q = lc.q2;
 #pragma unroll
     for (int v = 0; v < R; ++v) {
         const int e = e0 + v;
         const int h = 1 << v;
-        const uint32_t cq = LAZY ? (uint32_t)inv_bound_in(e) * q : two_q;
+        const uint32_t cq = LAZY ? q_multiple(lc, inv_bound_in(e)) : two_q;
         const bool red = !LAZY || 2 * inv_bound_in(e) > 8;
         if (SCALE && e == LOGN - 1) {
             const uint32_t s = SCALE == 1 ? lc.ninv : lc.ninvR, ssh = SCALE == 1 ? lc.ninv_sh : lc.ninvR_sh;
@@ -521,6 +536,42 @@ __device__ __forceinline__ void inv_stages_w(uint32_t (&x)[1 << R], const uint2 
     }
 }
 
+// Flag bit of F, set by run_task for the passes of the modes in HEFX_CC_WIDE_MODES: the
+// strided passes run 2^HEFX_CC_LOGPW sub-transforms per thread together.
+constexpr int kWide = 32;
+
+// The 2^LW adjacent sub-transforms j0, j0 + 1, ... (j0 a multiple of 2^LW, smallest stride
+// 2^logs >= 2^LW) of a strided pass, element k of all of them as one 8- or 16-byte access: the
+// swizzle permutes 16-byte chunks only, so the 2^LW words stay adjacent and aligned.
+template <int R, int LW, int logs, int ROWS>
+__device__ __forceinline__ void load_wide(uint32_t (&x)[1 << LW][1 << R], const uint32_t* sm, int j0) {
+    static_assert(LW == 1 || LW == 2, "pairs or quads");
+#pragma unroll
+    for (int k = 0; k < (1 << R); ++k) {
+        const uint32_t* p = &sm[swz_elem<R, logs, ROWS>(j0, k)];
+        if constexpr (LW == 1) {
+            const uint2 v = *reinterpret_cast<const uint2*>(p);
+            x[0][k] = v.x;
+            x[1][k] = v.y;
+        } else {
+            const uint4 v = *reinterpret_cast<const uint4*>(p);
+            x[0][k] = v.x;
+            x[1][k] = v.y;
+            x[2][k] = v.z;
+            x[3][k] = v.w;
+        }
+    }
+}
+template <int R, int LW, int logs, int ROWS>
+__device__ __forceinline__ void store_wide(const uint32_t (&x)[1 << LW][1 << R], uint32_t* sm, int j0) {
+#pragma unroll
+    for (int k = 0; k < (1 << R); ++k) {
+        uint32_t* p = &sm[swz_elem<R, logs, ROWS>(j0, k)];
+        if constexpr (LW == 1) *reinterpret_cast<uint2*>(p) = make_uint2(x[0][k], x[1][k]);
+        else *reinterpret_cast<uint4*>(p) = make_uint4(x[0][k], x[1][k], x[2][k], x[3][k]);
+    }
+}
+
 // Forward register pass over stages s0 .. s0+R-1 of every sub-transform of the CTA.
 template <int R, int LOGN, int s0, int SRC, int DST, int F>
 __device__ __forceinline__ void fwd_pass(uint32_t* sm, const Seg& sg, const KArgs& a) {
@@ -529,7 +580,28 @@ __device__ __forceinline__ void fwd_pass(uint32_t* sm, const Seg& sg, const KArg
     constexpr int logtl = LOGN - s0 - R;  // log2 of the smallest stride of the pass
     constexpr int lognsub = C::logm - R;
     constexpr int nsub = 1 << lognsub;
-    if constexpr (R <= 4 && C::rows == 1) {
+    constexpr int LW = (F & kWide) ? HEFX_CC_LOGPW : 0;
+    if constexpr (R <= 4 && C::rows == 1 && LW > 0 && logtl >= LW && SRC == SRC_SMEM && DST == DST_SMEM) {
+        // one row, shared memory in and out: a thread runs the 2^LW sub-transforms j_lo ..
+        // j_lo + 2^LW - 1 together (same group, so the same twiddles, loaded once)
+        const LimbConst& lc = row_lc<F>(a, sg.row0);
+        const uint2* tw = row_twf<N, F>(a, sg.row0);
+        constexpr bool ONE = logtl >= lognsub;  // every sub-transform of the CTA in one group
+        uint2 w[(1 << R) - 1];
+        if constexpr (ONE) load_tw_fwd<R, LOGN, s0>(w, sg.gbase >> (logtl + R), tw);
+#pragma unroll 1
+        for (int u = threadIdx.x; u < (nsub >> LW); u += C::threads) {
+            const int j_lo = (u & ((1 << (logtl - LW)) - 1)) << LW;
+            const int j_hi = u >> (logtl - LW);
+            if constexpr (!ONE) load_tw_fwd<R, LOGN, s0>(w, (sg.gbase >> (logtl + R)) + (uint32_t)j_hi, tw);
+            const int jb = (j_hi << (logtl + R)) + j_lo;
+            uint32_t x[1 << LW][1 << R];
+            load_wide<R, LW, logtl, C::rows>(x, sm, jb);
+#pragma unroll
+            for (int c = 0; c < (1 << LW); ++c) fwd_stages_w<R, LOGN, s0, F>(x[c], w, lc);
+            store_wide<R, LW, logtl, C::rows>(x, sm, jb);
+        }
+    } else if constexpr (R <= 4 && C::rows == 1) {
         // one row: every sub-transform shares the limb; each sub-transform's twiddles are all
         // requested before its data is read, so their latency is paid once per sub-transform
         // rather than once per stage
@@ -573,7 +645,27 @@ __device__ __forceinline__ void inv_pass(uint32_t* sm, const Seg& sg, const KArg
     constexpr int N = 1 << LOGN;
     constexpr int lognsub = C::logm - R;
     constexpr int nsub = 1 << lognsub;
-    if constexpr (R <= 4 && C::rows == 1) {
+    constexpr int LW = (F & kWide) ? HEFX_CC_LOGPW : 0;
+    if constexpr (R <= 4 && C::rows == 1 && LW > 0 && e0 >= LW && SRC == SRC_SMEM && DST == DST_SMEM) {
+        // as fwd_pass: 2^LW adjacent sub-transforms per thread, one twiddle set
+        const LimbConst& lc = row_lc<F>(a, sg.row0);
+        const uint2* tw = row_twi<N, F>(a, sg.row0);
+        constexpr bool ONE = e0 >= lognsub;  // every sub-transform of the CTA in one group
+        uint2 w[(1 << R) - 1];
+        if constexpr (ONE) load_tw_inv<R, LOGN, SCALE, e0>(w, sg.gbase, 0, tw);
+#pragma unroll 1
+        for (int u = threadIdx.x; u < (nsub >> LW); u += C::threads) {
+            const int j_lo = (u & ((1 << (e0 - LW)) - 1)) << LW;
+            const int j_hi = u >> (e0 - LW);
+            if constexpr (!ONE) load_tw_inv<R, LOGN, SCALE, e0>(w, sg.gbase, j_hi, tw);
+            const int jb = (j_hi << (e0 + R)) + j_lo;
+            uint32_t x[1 << LW][1 << R];
+            load_wide<R, LW, e0, C::rows>(x, sm, jb);
+#pragma unroll
+            for (int c = 0; c < (1 << LW); ++c) inv_stages_w<R, LOGN, SCALE, e0, F>(x[c], w, lc);
+            store_wide<R, LW, e0, C::rows>(x, sm, jb);
+        }
+    } else if constexpr (R <= 4 && C::rows == 1) {
         // as fwd_pass: a sub-transform's twiddles are all requested before its data is read
         const LimbConst& lc = row_lc<F>(a, sg.row0);
         const uint2* tw = row_twi<N, F>(a, sg.row0);
@@ -700,17 +792,18 @@ __device__ __forceinline__ void inv_big(uint32_t* sm, const Seg& sg, const KArgs
     }
 }
 
+// x_i -> (x_i - [x_{L-1}]_{q_i}) q_{L-1}^-1 mod q_i (Rescale by the set's last prime; canonical).
+__device__ __forceinline__ uint32_t rescale_one(uint32_t x, uint32_t last_raw, const LimbConst& c) {
+    const uint32_t last = csub(mul_shoup_lazy(last_raw, 1u, c.one_sh, c.q), c.q);
+    return csub(mul_shoup_lazy(x + c.q - last, c.rs_inv, c.rs_inv_sh, c.q), c.q);
+}
+
 // Forward stages 0 .. logP-1 of a split row, whose butterflies pair elements of different
 // CTAs: position j' < N/P is owned by one thread of the cluster (four consecutive positions
 // per thread, moved as uint4), which reads the P inputs j' + t N/P from global memory, runs
 // the radix-P step and stores output t into CTA t's shared memory.  Ends with a cluster
 // barrier (outputs visible; every global read of the row done before any CTA writes it,
 // so in-place transforms are safe).
-// x_i -> (x_i - [x_{L-1}]_{q_i}) q_{L-1}^-1 mod q_i (Rescale by the set's last prime; canonical).
-__device__ __forceinline__ uint32_t rescale_one(uint32_t x, uint32_t last_raw, const LimbConst& c) {
-    const uint32_t last = csub(mul_shoup_lazy(last_raw, 1u, c.one_sh, c.q), c.q);
-    return csub(mul_shoup_lazy(x + c.q - last, c.rs_inv, c.rs_inv_sh, c.q), c.q);
-}
 
 template <int LOGN, int F, bool RS = false>
 __device__ __forceinline__ void fwd_cross_pass(uint32_t* sm, const Seg& sg, const KArgs& a) {
@@ -928,6 +1021,7 @@ __device__ __forceinline__ void run_task(uint32_t* sm, const Seg& sg, const KArg
     constexpr int RS = C::r_small;
     constexpr int S_FIRST = C::logP;              // first stage run inside the CTA
     constexpr int S_SMALL = LOGN - RS;            // first stage of the smallest-stride pass
+    constexpr int FW = F | (((HEFX_CC_WIDE_MODES >> MODE) & 1) ? kWide : 0);  // F of the big-stride passes
 
     if constexpr (MODE == MODE_FWD || MODE == MODE_RS_FWD) {
         constexpr bool TMA = tma_output<LOGN, MODE, F>();
@@ -937,7 +1031,7 @@ __device__ __forceinline__ void run_task(uint32_t* sm, const Seg& sg, const KArg
             static_assert(!TMA, "TMA output needs the smallest-stride pass to follow a shared-memory pass");
             fwd_pass<RS, LOGN, S_FIRST, C::split ? SRC_SMEM : SRC_GLOBAL, DST_GLOBAL_REDUCE, F>(sm, sg, a);
         } else {
-            fwd_big<LOGN, 0, S_FIRST, F>(sm, sg, a);
+            fwd_big<LOGN, 0, S_FIRST, FW>(sm, sg, a);
             fwd_pass<RS, LOGN, S_SMALL, SRC_SMEM, DST_SMEM_REDUCE, F>(sm, sg, a);
             if constexpr (TMA) store_part_tma<LOGN>(sm, sg, a);
             else copy_out<LOGN, F>(sm, sg, a);
@@ -953,7 +1047,7 @@ __device__ __forceinline__ void run_task(uint32_t* sm, const Seg& sg, const KArg
             else copy_in<LOGN, F, MODE == MODE_HAD_INV>(sm, sg, a);
             inv_pass<RS, LOGN, C::split ? 0 : SCALE, 0, SRC, DST_SMEM, F>(sm, sg, a);
             __syncthreads();
-            inv_big<LOGN, SCALE, C::nrest - 1, RS, F>(sm, sg, a);
+            inv_big<LOGN, SCALE, C::nrest - 1, RS, FW>(sm, sg, a);
             if constexpr (C::split) inv_cross_pass<LOGN, SCALE, F>(sm, sg, a);
         }
     } else {  // MODE_FWD_HAD_INV
@@ -961,10 +1055,10 @@ __device__ __forceinline__ void run_task(uint32_t* sm, const Seg& sg, const KArg
             fwd_had_inv_pass<RS, LOGN, S_SMALL, SRC_GLOBAL, DST_GLOBAL, F>(sm, sg, a);
         } else {
             if constexpr (C::split) fwd_cross_pass<LOGN, F>(sm, sg, a);
-            fwd_big<LOGN, 0, S_FIRST, F>(sm, sg, a);
+            fwd_big<LOGN, 0, S_FIRST, FW>(sm, sg, a);
             fwd_had_inv_pass<RS, LOGN, S_SMALL, SRC_SMEM, DST_SMEM, F>(sm, sg, a);
             __syncthreads();
-            inv_big<LOGN, 2, C::nrest - 1, RS, F>(sm, sg, a);
+            inv_big<LOGN, 2, C::nrest - 1, RS, FW>(sm, sg, a);
             if constexpr (C::split) inv_cross_pass<LOGN, 2, F>(sm, sg, a);
         }
     }
