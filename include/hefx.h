@@ -258,6 +258,15 @@ hefx_status hefx_basis_convert(hefx_ctx* ctx, const hefx_bconv_plan* plan, const
                                size_t batch, hefx_path path, void* stream);
 
 /*
+ * Waits for `stream`, then reports whether a bounded device-side wait of the pipelined
+ * conversion kernels launched with `plan` (the tensor path, and the CUDA-core path where its
+ * tiles arrive by TMA: L <= 48 and N >= 2^8) expired since the last check (HEFX_ETIMEOUT; the
+ * results of those calls are invalid) and clears that record, as hefx_stream_check does for
+ * a parameter set.  Errors: EINVAL, ECUDA, ETIMEOUT.
+ */
+hefx_status hefx_bconv_check(hefx_ctx* ctx, const hefx_bconv_plan* plan, void* stream);
+
+/*
  * ModUp of hybrid key switching (the HE-Mult / Relin. of Sec. V-A and V-C, "Effects of
  * Security Parameters", built from BConv per App. A; the formulas are textbook RNS-CKKS):
  * the ciphertext basis Q = q[0..L) is cut into dnum = ceil(L / alpha) digits D_j = limbs

@@ -79,6 +79,8 @@ cudaError_t bconv_plan_upload(hefx_bconv_plan* plan) {
     cudaError_t e = cudaMalloc(&plan->d_const, sizeof(BConvConst));
     if (e != cudaSuccess) return e;
     e = cudaMemcpy(plan->d_const, &h, sizeof(BConvConst), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&plan->d_err, 4);
+    if (e == cudaSuccess) e = cudaMemset(plan->d_err, 0, 4);
     if (e != cudaSuccess) return e;
     return bconv_tc_upload(plan, h);
 }
@@ -106,6 +108,8 @@ cudaError_t modup_plan_upload(hefx_modup_plan* mp) {
 void bconv_plan_free(hefx_bconv_plan* plan) {
     if (plan->d_const) cudaFree(plan->d_const);
     plan->d_const = nullptr;
+    if (plan->d_err) cudaFree(plan->d_err);
+    plan->d_err = nullptr;
     bconv_tc_free(plan);
 }
 
@@ -393,9 +397,18 @@ cudaError_t launch_bconv_cc_list(const BcListEntry* d_list, uint32_t count, uint
                       (size_t)0, (size_t)0, (size_t)0);
 }
 
+// The plain conversion takes the TMA-fed kernel (bconv_cc_tma.cu) where it applies.
+#ifndef HEFX_BC_TMA
+#define HEFX_BC_TMA 1
+#endif
+
 cudaError_t launch_bconv_cc(const hefx_bconv_plan* plan, const uint32_t* in, uint32_t* out, size_t batch,
                             cudaStream_t stream) {
     if (batch == 0) return cudaSuccess;
+    if (HEFX_BC_TMA) {
+        const cudaError_t e = launch_bconv_cc_tma(plan, in, out, batch, plan->d_err, stream);
+        if (e != cudaErrorNotSupported) return e;
+    }
     return launch_cc<BC_FAST>(plan, in, out, nullptr, batch, (size_t)plan->L << plan->log2n, stream);
 }
 

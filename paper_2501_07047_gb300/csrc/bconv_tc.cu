@@ -50,7 +50,6 @@ struct BcTcPlan {
     uint8_t* d_bimage = nullptr;  // constant B operand, already in the swizzled smem layout
     uint32_t bimage_bytes = 0;
     uint32_t kpad = 0, npad = 0, tmem_cols = 0;
-    uint32_t* d_err = nullptr;
 };
 
 uint16_t half_bits_small(uint32_t d) {
@@ -300,8 +299,6 @@ cudaError_t bconv_tc_upload(hefx_bconv_plan* plan, const BConvConst& h) {
     if (e == cudaSuccess) e = cudaMemcpy(tp->d_const, &hc, sizeof hc, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&tp->d_bimage, img.size());
     if (e == cudaSuccess) e = cudaMemcpy(tp->d_bimage, img.data(), img.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMalloc(&tp->d_err, 4);
-    if (e == cudaSuccess) e = cudaMemset(tp->d_err, 0, 4);
     plan->d_bat = tp;
     if (e != cudaSuccess) {
         bconv_tc_free(plan);
@@ -315,7 +312,6 @@ void bconv_tc_free(hefx_bconv_plan* plan) {
     if (!tp) return;
     if (tp->d_const) cudaFree(tp->d_const);
     if (tp->d_bimage) cudaFree(tp->d_bimage);
-    if (tp->d_err) cudaFree(tp->d_err);
     delete tp;
     plan->d_bat = nullptr;
 }
@@ -344,7 +340,7 @@ cudaError_t launch_bconv_tc(const hefx_bconv_plan* plan, const uint32_t* in, uin
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const unsigned grid = (unsigned)std::min<size_t>(ntiles, (size_t)sms);
     bconv_tc_kernel<<<grid, THREADS, smem, stream>>>(in_map, tp->d_const, tp->d_bimage, tp->bimage_bytes, out, n,
-                                                      (uint32_t)batch, tp->tmem_cols, tp->d_err);
+                                                      (uint32_t)batch, tp->tmem_cols, plan->d_err);
     return cudaGetLastError();
 }
 

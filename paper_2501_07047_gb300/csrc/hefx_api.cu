@@ -586,6 +586,24 @@ hefx_status hefx_basis_convert(hefx_ctx* ctx, const hefx_bconv_plan* plan, const
     return HEFX_OK;
 }
 
+hefx_status hefx_bconv_check(hefx_ctx* ctx, const hefx_bconv_plan* plan, void* stream) {
+    if (!ctx) return HEFX_EINVAL;
+    if (!plan || plan->ctx != ctx) return fail(ctx, HEFX_EINVAL, "plan is null or belongs to another context");
+    hefx_status st = use_device(ctx);
+    if (st != HEFX_OK) return st;
+    uint32_t code = 0;
+    cudaError_t e = cudaSuccess;
+    if (plan->d_err) {
+        e = cudaMemcpyAsync(&code, plan->d_err, 4, cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+        if (e == cudaSuccess && code) e = cudaMemsetAsync(plan->d_err, 0, 4, (cudaStream_t)stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "hefx_bconv_check");
+    if (code) return fail(ctx, HEFX_ETIMEOUT, "a bounded device wait of a basis conversion expired (code %u); results are invalid", code);
+    return HEFX_OK;
+}
+
 hefx_status hefx_basis_convert_exact(hefx_ctx* ctx, const hefx_bconv_plan* plan, const uint32_t* in, uint32_t* out,
                                      size_t batch, void* stream) {
     if (!ctx) return HEFX_EINVAL;

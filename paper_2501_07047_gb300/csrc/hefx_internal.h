@@ -150,6 +150,7 @@ struct hefx_bconv_plan {
     std::vector<uint32_t> src, dst;
     void* d_const = nullptr;          // BConvConst (see bconv.cu)
     void* d_bat = nullptr;            // BAT digit matrix of step 2 (fp16), see bconv.cu
+    uint32_t* d_err = nullptr;        // bounded-wait error flag of the pipelined kernels (0 = none)
 };
 
 // ModUp of hybrid key switching (bconv.cu): one plan for every digit of (Q, P, alpha).
@@ -238,6 +239,10 @@ cudaError_t launch_mod_down(const hefx_bconv_plan* plan, const uint32_t* x, uint
                             cudaStream_t stream);
 cudaError_t launch_bconv_cc(const hefx_bconv_plan* plan, const uint32_t* in, uint32_t* out, size_t batch,
                             cudaStream_t stream);
+// The plain conversion with TMA-fed tiles (bconv_cc_tma.cu): L <= 48 sources, N >= 2^8;
+// cudaErrorNotSupported otherwise.
+cudaError_t launch_bconv_cc_tma(const hefx_bconv_plan* plan, const uint32_t* in, uint32_t* out, size_t batch,
+                                uint32_t* err, cudaStream_t stream);
 cudaError_t bconv_plan_upload(hefx_bconv_plan* plan);
 cudaError_t modup_plan_upload(hefx_modup_plan* plan);
 // U[b][j] = ModUp digit j of c[b] ([batch][L][N] -> [batch][dnum][L + K][N], coefficient form)

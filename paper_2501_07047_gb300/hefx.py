@@ -48,6 +48,7 @@ SIGNATURES = {
     "hefx_tensor_product": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "hefx_vec_mod_add": (_i32, [_vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "hefx_basis_convert_exact": (_i32, [_vp, _vp, _vp, _vp, _sz, _vp]),
+    "hefx_bconv_check": (_i32, [_vp, _vp, _vp]),
     "hefx_key_inner_product": (_i32, [_vp, _vp, _vp, _vp, _vp, _u32, _sz, _vp]),
     "hefx_mod_down": (_i32, [_vp, _vp, _vp, _vp, _sz, _vp]),
     "hefx_modup_plan_create": (_i32, [_vp, _u32, _u32p, _u32, _u32p, _u32, _u32, ctypes.POINTER(_vp)]),
@@ -243,6 +244,11 @@ def hefx_vec_mod_add(ctx, params, x, y, z, batch, stream=None) -> None:
 def hefx_key_inner_product(ctx, params, digits, evk, out, dnum, batch, stream=None) -> None:
     _check(ctx, load().hefx_key_inner_product(ctx, params, _ptr(digits), _ptr(evk), _ptr(out), dnum, batch,
                                               _stream(stream)))
+
+
+def hefx_bconv_check(ctx, plan, stream=None) -> None:
+    """Raises HefxError(ETIMEOUT) if a bounded wait of a conversion launched with `plan` expired."""
+    _check(ctx, load().hefx_bconv_check(ctx, plan, _stream(stream)))
 
 
 def hefx_basis_convert_exact(ctx, plan, x, out, batch, stream=None) -> None:

@@ -166,3 +166,20 @@ def test_bconv_paper_shapes_tensor_path(ctx, Lq, Lp):
         assert (convert(ctx, plan, a, Lp, "auto") == want).all()
     finally:
         hefx.hefx_bconv_plan_destroy(plan)
+
+
+@pytest.mark.parametrize("logn,L,Lp,batch", [(16, 48, 8, 2), (16, 24, 56, 2), (8, 48, 17, 3), (13, 1, 1, 5)])
+def test_bconv_cudacore_tiled_shapes(ctx, logn, L, Lp, batch):
+    """The CUDA-core conversion whose 256-coefficient tiles arrive by TMA (up to 48 sources):
+    the most sources, several target chunks (step 1 kept in place between chunks), a single
+    source; every output against the oracle, and no bounded wait expired."""
+    qs, ps = inputs.source_primes(L), inputs.special_primes(Lp)
+    n = 1 << logn
+    plan = hefx.hefx_bconv_plan_create(ctx, logn, qs, ps)
+    try:
+        a = inputs.residue_tensor(inputs.derive_seed(42, logn, L, Lp), batch, qs, n)
+        got = convert(ctx, plan, a, Lp, "cudacore")
+        hefx.hefx_bconv_check(ctx, plan)
+        assert (got == oracle.bconv(a, qs, ps)).all()
+    finally:
+        hefx.hefx_bconv_plan_destroy(plan)
