@@ -5,9 +5,9 @@
 // with the arithmetic of bconv.cu (step 1 a Shoup product, step 2 64-bit multiply-accumulates
 // over 8 target limbs at a time, one Barrett reduction per output) and the memory side taken
 // off the compute threads.  A persistent CTA streams tiles of 256 coefficients x L source limbs
-// (one 2D tensor copy of L KiB each) through a ring of shared-memory stages: one thread keeps
-// the copies of the next tiles in flight while eight warps convert the current one, a
-// coefficient per thread, reading the residues from shared memory.  bconv.cu's direct-load
+// (one 2D tensor copy of L KiB each) through a ring of shared-memory stages (two per CTA,
+// three CTAs per SM): one thread keeps the next copy in flight while eight warps convert the
+// current one, a coefficient per thread, reading the residues from shared memory.  bconv.cu's direct-load
 // kernel waits for one DRAM round trip per group of source limbs in every thread; here the
 // copies of later tiles overlap the arithmetic of earlier ones.
 #include <algorithm>
@@ -21,7 +21,15 @@ namespace hefx {
 namespace {
 
 constexpr int kTile = 256;                 // coefficients per tile: one box of 256 words x L rows
-constexpr int kStages = 3;                 // tiles in flight per CTA
+// Stages per CTA and CTAs per SM (registers sized for them): measured on 16 x 24 -> 8 limbs of
+// 2^16, 2 stages at 3 CTAs per SM 53.9 us, 3 at 2 56.0 us, 4 at 2 (one CTA fits) 64.2 us.
+#ifndef HEFX_BCT_STAGES
+#define HEFX_BCT_STAGES 2
+#endif
+#ifndef HEFX_BCT_MINB
+#define HEFX_BCT_MINB 3
+#endif
+constexpr int kStages = HEFX_BCT_STAGES;   // tiles in flight per CTA
 constexpr int kCompWarps = kTile / 32;     // one coefficient per compute thread
 constexpr int kThreads = (kCompWarps + 1) * 32;
 constexpr int kJ = 8;                      // target limbs per accumulation pass
@@ -82,7 +90,7 @@ __device__ __forceinline__ void store_chunk(const uint64_t (&acc)[kJ], uint32_t*
 // eight compute warps have finished with it (empty[s], one arrival per warp).  Every wait is
 // bounded: on a timeout the flag is set and the thread leaves its loop.
 template <bool MULTI>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, HEFX_BCT_MINB)
     bconv_cc_tma_kernel(const __grid_constant__ CUtensorMap in_map, const BConvConst* __restrict__ gc,
                         uint32_t* __restrict__ out, uint32_t log2n, uint32_t batch, uint32_t* err) {
     extern __shared__ __align__(128) uint8_t stage_raw[];

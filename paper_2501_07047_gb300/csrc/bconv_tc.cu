@@ -238,8 +238,8 @@ bool bconv_tc_available(const hefx_bconv_plan* plan) {
 
 bool bconv_prefer_tc(const hefx_bconv_plan* plan, size_t batch) {
     // measured at N = 2^16: the tensor kernel wins only where many targets share each source
-    // digit (24 -> 56 at batch 8: 130 vs 175 us); 8 to 40 targets and small calls favour the
-    // CUDA-core kernel (24 -> 8: 72 vs 58 us, 16 -> 40 at batch 8: 97 vs 93 us)
+    // digit (24 -> 56 at batch 8: 132 vs 138 us); 8 to 40 targets and small calls favour the
+    // CUDA-core kernel (24 -> 8: 76 vs 54 us, 16 -> 40 at batch 8: 97 vs 81 us)
     return bconv_tc_available(plan) && plan->Lp >= 48 && ((batch * plan->L) << plan->log2n) >= ((size_t)96 << 16);
 }
 
