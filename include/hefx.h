@@ -20,6 +20,10 @@
  *    kernels launch with programmatic stream serialization: their set-up may overlap the
  *    drain of the stream's preceding kernel, and each waits for that kernel to complete
  *    before touching memory, so the ordering against earlier stream work is unchanged.
+ *  - Tensor-path transforms keep a digit workspace in their parameter set: tensor-path calls
+ *    with the same params whose work overlaps on the GPU (different streams) race on it.
+ *    Issue them on one stream, or give each stream its own parameter set.  The CUDA-core
+ *    kernels keep no state between launches, and their calls may overlap freely.
  *  - The caller owns every data buffer (device pointers from any allocator).  hefx owns
  *    the context, parameter sets and plans it creates (and the device tables inside them),
  *    and releases them in the matching *_destroy call.
