@@ -537,6 +537,31 @@ def _events_time(fn, steps, flush, stream):
     return statistics.median(ms)
 
 
+def _pipelined_time(fn, bufs, calls, stream):
+    """Milliseconds per call of `calls` calls fn(buf, stream_i), call k on stream k mod 2 with
+    buffer k mod len(bufs), neighbouring calls overlapping (device time, CUDA events)."""
+    import torch
+    sts = [torch.cuda.Stream() for _ in range(2)]
+    for k in range(4):
+        fn(bufs[k % len(bufs)], sts[k % 2])
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    for st in sts:
+        st.wait_stream(stream)
+    e0.record(stream)
+    for st in sts:
+        st.wait_stream(stream)
+    for k in range(calls):
+        fn(bufs[k % len(bufs)], sts[k % 2])
+    for st in sts:
+        stream.wait_stream(st)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / calls
+
+
 def bench_bconv(ctx, args):
     """RNS basis conversion 16 x 24 limbs x 2^16 -> 8 limbs, both paths."""
     import torch
@@ -634,6 +659,13 @@ def bench_paper_ntt_table(ctx, args):
                 res[f"{path}_batch{batch}"] = {"us": round(ms * 1e3, 2),
                                                "KNTT_s_polys": round(batch / (ms / 1e3) / 1e3, 1),
                                                "K_limb_NTT_s": round(batch * Lset / (ms / 1e3) / 1e3, 1)}
+                if path == "cudacore" and batch == 64 * pbatch:
+                    # a stream of such calls: two streams, two batches of at least 128 MiB (more
+                    # than L2 together), neighbouring calls overlapping
+                    pm = _pipelined_time(lambda b, st: hefx.hefx_ntt_fwd(ctx, params, b, batch, path, st),
+                                         [d, d0.clone()], 20, s)
+                    res[f"{path}_batch{batch}_stream"] = {"us_per_call": round(pm * 1e3, 2),
+                                                          "KNTT_s_polys": round(batch / (pm / 1e3) / 1e3, 1)}
         hefx.hefx_params_destroy(params)
         out[name] = res
     return out
