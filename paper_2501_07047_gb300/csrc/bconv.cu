@@ -118,12 +118,6 @@ namespace {
 constexpr int kJChunk = 8;  // target limbs accumulated per pass over the source limbs
 constexpr int kIGroup = 8;  // source limbs whose loads are in flight together
 
-__device__ __forceinline__ uint32_t barrett64(uint64_t x, uint32_t p, uint64_t mu) {
-    const uint64_t qt = __umul64hi(x, mu);  // floor(x / p) or one less
-    uint64_t r = x - qt * p;
-    return (uint32_t)(r >= p ? r - p : r);
-}
-
 // kCoef coefficients per thread: each constant load serves kCoef products.
 // Polynomial b's source limbs start at in + b * in_stride, its outputs at out + b * out_stride.
 // MODE 1 (ModDown): the epilogue returns (x_j - conv_j) * P^-1 mod p_j, x_j at

@@ -35,12 +35,6 @@ constexpr int kThreads = (kCompWarps + 1) * 32;
 constexpr int kJ = 8;                      // target limbs per accumulation pass
 constexpr uint32_t kMaxL = 48;             // a stage of 48 rows is 48 KiB
 
-__device__ __forceinline__ uint32_t barrett64_t(uint64_t x, uint32_t p, uint64_t mu) {
-    const uint64_t qt = __umul64hi(x, mu);  // floor(x / p) or one less
-    const uint64_t r = x - qt * p;
-    return (uint32_t)(r >= p ? r - p : r);
-}
-
 // Targets j0 .. j0+7 of one coefficient: acc[jj] = sum_i b_i [qhat_i]_{p_j}, b_i read from the
 // stage (raw: this thread's column, stride kTile words).  STEP1: the stage holds a_i and b_i is
 // computed here (Shoup product), and KEEP writes it back for the later target chunks.  Full
@@ -80,7 +74,7 @@ __device__ __forceinline__ void store_chunk(const uint64_t (&acc)[kJ], uint32_t*
 #pragma unroll
     for (int jj = 0; jj < kJ; ++jj) {
         const uint32_t j = j0 + jj;
-        if (j < Lp) dst[(size_t)j << log2n] = barrett64_t(acc[jj], c.p[j], c.p_mu[j]);
+        if (j < Lp) dst[(size_t)j << log2n] = barrett64(acc[jj], c.p[j], c.p_mu[j]);
     }
 }
 

@@ -30,6 +30,14 @@ struct BConvConst {
 // 16-byte aligned rows: the kernels read the matrix and copy the struct as uint4
 static_assert(offsetof(BConvConst, qhat_p) % 16 == 0 && sizeof(BConvConst) % 16 == 0, "BConvConst layout");
 
+// x mod p for a 64-bit x, with mu = floor(2^64 / p) (Barrett): the estimated quotient is
+// floor(x / p) or one less, so one conditional subtraction finishes.
+__device__ __forceinline__ uint32_t barrett64(uint64_t x, uint32_t p, uint64_t mu) {
+    const uint64_t qt = __umul64hi(x, mu);
+    const uint64_t r = x - qt * p;
+    return (uint32_t)(r >= p ? r - p : r);
+}
+
 // Host: the plan constants of a conversion from src[0..L) to dst[0..Lp) (skip fields 0).
 void fill_bconv_const(const uint32_t* src, uint32_t L, const uint32_t* dst, uint32_t Lp, BConvConst& h);
 
