@@ -444,3 +444,44 @@ def test_large_batch_sampled(ctx):
         assert torch.equal(d, d0)
     finally:
         hefx.hefx_params_destroy(p)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_overlapping_streams(ctx, path):
+    """Independent batches whose transforms overlap on two streams (the benchmark's whole-job
+    loop): the CUDA-core path shares one parameter set between the streams, the tensor path
+    takes one per stream (its digit workspace lives in the parameter set).  Every forward
+    result equals the oracle's and every round trip returns its batch."""
+    import torch
+    L, B, logn = 24, 3, 16
+    n = 1 << logn
+    primes = inputs.source_primes(L)
+    nparams = 2 if path == "tensor" else 1
+    params = [make_params(ctx, logn, primes) for _ in range(nparams)]
+    try:
+        if hefx.raw_status("hefx_ntt_fwd", ctx, params[0], empty_dev((1, L, n)).data_ptr(), 0,
+                           hefx.PATHS[path], 0) != hefx.HEFX_OK:
+            pytest.skip(f"{path} path not built at N = 2^{logn}")
+        host = [inputs.residue_tensor(inputs.derive_seed(43, k), B, primes, n) for k in range(4)]
+        bufs = [to_dev(h) for h in host]
+        fwd = [empty_dev((B, L, n)) for _ in range(4)]
+        streams = [torch.cuda.Stream() for _ in range(2)]
+        torch.cuda.synchronize()
+        for rep in range(3):
+            for k in range(4):
+                s, p = streams[k % 2], params[k % nparams]
+                hefx.hefx_ntt_fwd(ctx, p, bufs[k], B, path, s)
+                if rep == 0:
+                    with torch.cuda.stream(s):
+                        fwd[k].copy_(bufs[k])
+                hefx.hefx_ntt_inv(ctx, p, bufs[k], B, path, s)
+        torch.cuda.synchronize()
+        for p in params:
+            hefx.hefx_stream_check(ctx, p)
+        for k in range(4):
+            assert (to_host(bufs[k]).reshape(host[k].shape) == host[k]).all(), k
+        for k in (0, 3):
+            assert (to_host(fwd[k]).reshape(host[k].shape) == oracle.ntt_batch(host[k], primes)).all(), k
+    finally:
+        for p in params:
+            hefx.hefx_params_destroy(p)
