@@ -164,6 +164,7 @@ def test_bconv_paper_shapes_tensor_path(ctx, Lq, Lp):
         want = oracle.bconv(a, qs, ps)
         assert (convert(ctx, plan, a, Lp, "tensor") == want).all()
         assert (convert(ctx, plan, a, Lp, "auto") == want).all()
+        hefx.hefx_bconv_check(ctx, plan)  # no bounded wait of the pipelined kernels expired
     finally:
         hefx.hefx_bconv_plan_destroy(plan)
 
