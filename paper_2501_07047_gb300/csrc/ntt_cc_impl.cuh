@@ -87,9 +87,10 @@ __device__ __forceinline__ int swz_elem(int j0, int k) {
 #define HEFX_CC_SPLIT_MINB 5
 #endif
 // log2 of the sub-transforms a thread of a one-row CTA runs together in a strided register
-// pass (0: one at a time), for the per-size kernels and for the fused batch kernel, and the
-// kernel modes (bit 1 << MODE) that do so.  Measured on config 2 (fwd + inv, us per step):
-// 99.0 serialized / 74.0 pipelined with pairs, 96.1 / 72.3 with quads; the fused product
+// pass (0: one at a time), for the split-row per-size kernels and for the fused batch kernel
+// (one-CTA rows of 2^13 take pairs), and the kernel modes (bit 1 << MODE) that do so.
+// Measured on config 2 (fwd + inv, us per step): 99.0 serialized / 74.0 pipelined with
+// pairs, 96.1 / 72.3 with quads; one-CTA rows of 2^13 lost 3 % with quads; the fused product
 // (NTT, Hadamard and INTT in one kernel, whose registers it crowds) is slower with either,
 // and the batch kernel, which holds every ring degree's passes, keeps pairs.
 #ifndef HEFX_CC_LOGPW
@@ -542,8 +543,8 @@ __device__ __forceinline__ void inv_stages_w(uint32_t (&x)[1 << R], const uint2 
 }
 
 // Flag bit of F, set by run_task for the passes of the modes in HEFX_CC_WIDE_MODES: the
-// strided passes run 2^HEFX_CC_LOGPW (batch kernel: 2^HEFX_CC_LOGPW_BATCH) sub-transforms per
-// thread together.
+// strided passes run 2^HEFX_CC_LOGPW (batch kernel: 2^HEFX_CC_LOGPW_BATCH; one-CTA rows: 2)
+// sub-transforms per thread together.
 constexpr int kWide = 32;
 
 // The 2^LW adjacent sub-transforms j0, j0 + 1, ... (j0 a multiple of 2^LW, smallest stride
@@ -586,7 +587,7 @@ __device__ __forceinline__ void fwd_pass(uint32_t* sm, const Seg& sg, const KArg
     constexpr int logtl = LOGN - s0 - R;  // log2 of the smallest stride of the pass
     constexpr int lognsub = C::logm - R;
     constexpr int nsub = 1 << lognsub;
-    constexpr int LW = (F & kWide) ? (C::unified ? HEFX_CC_LOGPW_BATCH : HEFX_CC_LOGPW) : 0;
+    constexpr int LW = (F & kWide) ? (C::unified ? HEFX_CC_LOGPW_BATCH : C::split ? HEFX_CC_LOGPW : 1) : 0;
     if constexpr (R <= 4 && C::rows == 1 && LW > 0 && logtl >= LW && SRC == SRC_SMEM && DST == DST_SMEM) {
         // one row, shared memory in and out: a thread runs the 2^LW sub-transforms j_lo ..
         // j_lo + 2^LW - 1 together (same group, so the same twiddles, loaded once)
@@ -651,7 +652,7 @@ __device__ __forceinline__ void inv_pass(uint32_t* sm, const Seg& sg, const KArg
     constexpr int N = 1 << LOGN;
     constexpr int lognsub = C::logm - R;
     constexpr int nsub = 1 << lognsub;
-    constexpr int LW = (F & kWide) ? (C::unified ? HEFX_CC_LOGPW_BATCH : HEFX_CC_LOGPW) : 0;
+    constexpr int LW = (F & kWide) ? (C::unified ? HEFX_CC_LOGPW_BATCH : C::split ? HEFX_CC_LOGPW : 1) : 0;
     if constexpr (R <= 4 && C::rows == 1 && LW > 0 && e0 >= LW && SRC == SRC_SMEM && DST == DST_SMEM) {
         // as fwd_pass: 2^LW adjacent sub-transforms per thread, one twiddle set
         const LimbConst& lc = row_lc<F>(a, sg.row0);
