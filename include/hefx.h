@@ -250,7 +250,9 @@ void hefx_bconv_plan_destroy(hefx_bconv_plan* plan);
  * d_out[batch][Lp][n] = BConv(d_in[batch][L][n]).  d_out must not overlap d_in.
  * HEFX_PATH_TENSOR runs step 2 as a digit-split matrix product on the tensor cores
  * (Sec. IV-A3, "High-Precision MatModMul in BConv"); HEFX_PATH_CUDACORE as 64-bit
- * multiply-accumulates.  Results are identical.  The plan has the tensor path when every
+ * multiply-accumulates (with L <= 48 and N >= 2^8, over tiles that TMA streams into shared
+ * memory; both pipelined kernels report an expired bounded wait through hefx_bconv_check).
+ * Results are identical.  The plan has the tensor path when every
  * source prime is below 2^28, L <= 48, Lp <= 64 (one 256-column MMA: four 8-bit chunk
  * columns per target) and the kernel's tiles fit one CTA's shared memory; otherwise
  * HEFX_PATH_TENSOR returns HEFX_EUNSUPPORTED.  HEFX_PATH_AUTO takes the tensor path only when
